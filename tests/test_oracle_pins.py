@@ -1,0 +1,370 @@
+"""Pins for the FP64 oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against something fixed by the paper's problem
+statement (Section II) or by mathematics: a hand-derived worked example,
+brute-force ancestor walks, star-tree closed forms that reduce to textbook
+distances computed by scipy (Jaccard, Bray-Curtis), Faith's phylogenetic
+diversity, the tip-depth identity of the weighted denominator, and metric
+invariants.  A dropped term, wrong sign, wrong index or swapped operand in the
+oracle fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.spatial.distance as ssd
+
+import oracle
+from paper_2107_05397_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+UW, WN = oracle.UNWEIGHTED, oracle.WEIGHTED_NORMALIZED
+
+
+def _children(parent):
+    kids = [[] for _ in range(parent.shape[0])]
+    for v, p in enumerate(parent):
+        if p >= 0:
+            kids[p].append(v)
+    return kids
+
+
+def brute_embedding(tree, table):
+    """w[node, sample], p[node, sample] by walking up from every tip."""
+    n = tree.n_nodes
+    dense = table.dense()
+    N = table.n_samples
+    tot = dense.sum(axis=0).astype(np.float64)
+    w = np.zeros((n, N))
+    cnt = np.zeros((n, N))
+    for f in range(table.n_features):
+        v = int(table.feature_node[f])
+        while v >= 0:  # every ancestor, including the tip itself
+            cnt[v] += dense[f]
+            v = int(tree.parent[v])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        w = np.where(tot > 0, cnt / np.where(tot > 0, tot, 1), 0.0)
+    return w, (cnt > 0).astype(np.uint8)
+
+
+def branch_sets(tree, table):
+    """Set of non-root branches on the root paths of each sample's tips."""
+    dense = table.dense()
+    root = tree.n_nodes - 1
+    sets = []
+    for i in range(table.n_samples):
+        s = set()
+        for f in np.nonzero(dense[:, i])[0]:
+            v = int(table.feature_node[f])
+            while v != root:
+                s.add(v)
+                v = int(tree.parent[v])
+        sets.append(s)
+    return sets
+
+
+def depth(tree):
+    """Root-to-node path length, root branch excluded."""
+    d = np.zeros(tree.n_nodes)
+    for v in range(tree.n_nodes - 2, -1, -1):  # parents before children
+        d[v] = d[tree.parent[v]] + tree.length[v]
+    return d
+
+
+def cases():
+    out = []
+    for seed in range(6):
+        rng = np.random.default_rng(1000 + seed)
+        general = seed % 2 == 1
+        tree, table = synth.random_case(rng, n_tips=4 + 2 * seed, n_samples=7,
+                                        density=0.35, general=general,
+                                        empty_samples=1 if seed == 2 else 0)
+        out.append((tree, table))
+    return out
+
+
+# ---------------------------------------------------------------- worked example
+
+def test_worked_example_golden():
+    g = json.load(open(os.path.join(GOLDEN, "worked_example_7node.json")))
+    tree = synth.Tree(parent=np.array(g["parent"], np.int32), length=np.array(g["length"]))
+    table = synth.dense_to_table(np.array(g["dense_counts_features_by_samples"]),
+                                 np.array(g["feature_node"], np.int32))
+    np.testing.assert_allclose(oracle.unifrac_full(tree, table, UW), g["unweighted"],
+                               rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oracle.unifrac_full(tree, table, WN), g["weighted_normalized"],
+                               rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- embedding
+
+@pytest.mark.parametrize("k", range(6))
+def test_embedding_matches_ancestor_walk(k):
+    tree, table = cases()[k]
+    w_ref, p_ref = brute_embedding(tree, table)
+    for i in range(table.n_samples):
+        w, p = oracle.embedding(tree, table, i)
+        np.testing.assert_allclose(w, w_ref[:, i], rtol=0, atol=1e-15)
+        np.testing.assert_array_equal(p, p_ref[:, i])
+
+
+def test_embedding_postorder_range_identity():
+    """In postorder numbering a subtree is the node range [b-size_b+1, b]."""
+    rng = np.random.default_rng(7)
+    tree, table = synth.random_case(rng, n_tips=12, n_samples=5, general=True)
+    n = tree.n_nodes
+    size = np.ones(n, dtype=np.int64)
+    for v in range(n - 1):
+        size[tree.parent[v]] += size[v]
+    dense = table.dense()
+    tip_count = np.zeros((n, table.n_samples))
+    tip_count[table.feature_node] = dense
+    prefix = np.vstack([np.zeros((1, table.n_samples)), np.cumsum(tip_count, axis=0)])
+    tot = dense.sum(axis=0)
+    for i in range(table.n_samples):
+        w, _ = oracle.embedding(tree, table, i)
+        below = prefix[np.arange(n) + 1, i] - prefix[np.arange(n) + 1 - size, i]
+        np.testing.assert_allclose(w, below / tot[i] if tot[i] else 0 * below,
+                                   rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("equal", [True, False])
+def test_star_tree_unweighted_is_jaccard(equal):
+    rng = np.random.default_rng(11)
+    F, N = 15, 9
+    tree = synth.star_tree(F, 0.7)
+    if not equal:
+        tree.length[:-1] = rng.exponential(0.5, size=F)
+    dense = (rng.random((F, N)) < 0.4) * rng.integers(1, 9, size=(F, N))
+    table = synth.dense_to_table(dense, np.arange(F, dtype=np.int32))
+    d = oracle.unifrac_full(tree, table, UW)
+    for i in range(N):
+        for j in range(N):
+            a, b = dense[:, i] > 0, dense[:, j] > 0
+            if not (a | b).any():
+                ref = 0.0
+            else:
+                ref = ssd.jaccard(a, b, w=tree.length[:-1])
+            assert abs(d[i, j] - ref) < 1e-14, (i, j, d[i, j], ref)
+
+
+@pytest.mark.parametrize("equal", [True, False])
+def test_star_tree_weighted_is_bray_curtis(equal):
+    rng = np.random.default_rng(12)
+    F, N = 13, 8
+    tree = synth.star_tree(F, 0.3)
+    if not equal:
+        tree.length[:-1] = rng.exponential(0.5, size=F)
+    dense = (rng.random((F, N)) < 0.5) * rng.integers(1, 50, size=(F, N))
+    dense[:, 0] = 0
+    dense[3, 0] = 4  # at least one non-empty
+    table = synth.dense_to_table(dense, np.arange(F, dtype=np.int32))
+    d = oracle.unifrac_full(tree, table, WN)
+    for i in range(N):
+        for j in range(N):
+            u, v = dense[:, i].astype(float), dense[:, j].astype(float)
+            if u.sum() == 0 and v.sum() == 0:
+                ref = 0.0
+            else:
+                u = u / u.sum() if u.sum() else u
+                v = v / v.sum() if v.sum() else v
+                ref = ssd.braycurtis(u, v, w=tree.length[:-1])
+            assert abs(d[i, j] - ref) < 1e-14, (i, j, d[i, j], ref)
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_unweighted_from_branch_sets(k):
+    """Unweighted = length of symmetric difference / length of union of the
+    two samples' branch sets; Faith's PD is the length of one set."""
+    tree, table = cases()[k]
+    sets = branch_sets(tree, table)
+    L = tree.length
+    d = oracle.unifrac_full(tree, table, UW)
+    for i in range(table.n_samples):
+        for j in range(table.n_samples):
+            sym = sum(L[b] for b in sets[i] ^ sets[j])
+            uni = sum(L[b] for b in sets[i] | sets[j])
+            ref = sym / uni if uni > 0 else 0.0
+            assert abs(d[i, j] - ref) < 1e-13
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_weighted_denominator_tip_depth_identity(k):
+    """sum_b len_b w_bi = sum_f (c_fi / C_i) depth(tip_f); with a sample that
+    has nothing in common, the weighted distance is 1 and its denominator is
+    the sum of both mean tip depths."""
+    tree, table = cases()[k]
+    dep = depth(tree)
+    dense = table.dense().astype(float)
+    for i in range(table.n_samples):
+        w, _ = oracle.embedding(tree, table, i)
+        lhs = float(np.dot(tree.length[:-1], w[:-1]))
+        tot = dense[:, i].sum()
+        rhs = float(np.dot(dense[:, i] / tot, dep[table.feature_node])) if tot else 0.0
+        assert abs(lhs - rhs) < 1e-13
+
+
+def test_faith_pd_golden():
+    g = json.load(open(os.path.join(GOLDEN, "worked_example_7node.json")))
+    tree = synth.Tree(parent=np.array(g["parent"], np.int32), length=np.array(g["length"]))
+    table = synth.dense_to_table(np.array(g["dense_counts_features_by_samples"]),
+                                 np.array(g["feature_node"], np.int32))
+    for i, (pd, td) in enumerate(zip(g["faith_pd"], g["tip_depth_mean"])):
+        w, p = oracle.embedding(tree, table, i)
+        assert abs(np.dot(tree.length[:-1], p[:-1]) - pd) < 1e-15
+        assert abs(np.dot(tree.length[:-1], w[:-1]) - td) < 1e-15
+
+
+def test_root_disjoint_samples_unweighted_one():
+    """Features under different children of the root share no branch."""
+    rng = np.random.default_rng(5)
+    tree = synth.yule_tree(16, rng, 0.2)
+    root = tree.n_nodes - 1
+    kids = _children(tree.parent)[root]
+    assert len(kids) == 2
+    size = np.ones(tree.n_nodes, dtype=np.int64)
+    for v in range(tree.n_nodes - 1):
+        size[tree.parent[v]] += size[v]
+    left = set(range(kids[0] - size[kids[0]] + 1, kids[0] + 1))
+    tips = tree.tips()
+    lt = [t for t in tips if t in left]
+    rt = [t for t in tips if t not in left]
+    fnode = np.array(lt + rt, dtype=np.int32)
+    dense = np.zeros((len(fnode), 2), dtype=np.int64)
+    dense[: len(lt), 0] = rng.integers(1, 5, size=len(lt))
+    dense[len(lt):, 1] = rng.integers(1, 5, size=len(rt))
+    table = synth.dense_to_table(dense, fnode)
+    assert abs(oracle.unifrac_full(tree, table, UW)[0, 1] - 1.0) < 1e-15
+    assert abs(oracle.unifrac_full(tree, table, WN)[0, 1] - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("variant", [UW, WN])
+@pytest.mark.parametrize("k", range(6))
+def test_metric_properties(variant, k):
+    tree, table = cases()[k]
+    d = oracle.unifrac_full(tree, table, variant)
+    assert np.all(np.diag(d) == 0)
+    np.testing.assert_array_equal(d, d.T)
+    assert d.min() >= 0 and d.max() <= 1 + 1e-15
+    if variant == UW:  # weighted Jaccard on branch sets is a metric
+        N = d.shape[0]
+        for a in range(N):
+            for b in range(N):
+                assert np.all(d[a, b] <= d[a, :] + d[:, b] + 1e-12)
+
+
+@pytest.mark.parametrize("variant", [UW, WN])
+def test_permuting_samples_permutes_matrix(variant):
+    rng = np.random.default_rng(21)
+    tree, table = synth.random_case(rng, n_tips=10, n_samples=9)
+    dense = table.dense()
+    perm = rng.permutation(table.n_samples)
+    t2 = synth.dense_to_table(dense[:, perm], table.feature_node)
+    d1 = oracle.unifrac_full(tree, table, variant)
+    d2 = oracle.unifrac_full(tree, t2, variant)
+    np.testing.assert_allclose(d2, d1[np.ix_(perm, perm)], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("variant", [UW, WN])
+def test_feature_relabel_and_count_scaling(variant):
+    rng = np.random.default_rng(22)
+    tree, table = synth.random_case(rng, n_tips=10, n_samples=6)
+    dense = table.dense()
+    fperm = rng.permutation(table.n_features)
+    t2 = synth.dense_to_table(dense[fperm], table.feature_node[fperm])
+    scale = rng.integers(1, 7, size=table.n_samples)
+    t3 = synth.dense_to_table(dense * scale[None, :], table.feature_node)
+    d1 = oracle.unifrac_full(tree, table, variant)
+    np.testing.assert_allclose(oracle.unifrac_full(tree, t2, variant), d1, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oracle.unifrac_full(tree, t3, variant), d1, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("variant", [UW, WN])
+def test_unary_split_and_zero_length_branch_change_nothing(variant):
+    """Splitting a branch into two pieces of the same total length, or adding a
+    zero-length pendant tip with no feature, leaves every distance unchanged."""
+    rng = np.random.default_rng(23)
+    tree, table = synth.random_case(rng, n_tips=8, n_samples=6)
+    d1 = oracle.unifrac_full(tree, table, variant)
+    n = tree.n_nodes
+    v = int(rng.integers(0, n - 1))
+    # build explicitly in postorder: insert u right after v (subtree of v stays contiguous)
+    new_parent = np.empty(n + 1, np.int32)
+    new_len = np.empty(n + 1)
+    remap = np.arange(n) + (np.arange(n) > v)  # old id -> new id
+    for k in range(n):
+        p = int(tree.parent[k])
+        new_parent[remap[k]] = -1 if p < 0 else remap[p]
+        new_len[remap[k]] = tree.length[k]
+    u = v + 1
+    new_parent[u] = remap[tree.parent[v]]
+    new_parent[v] = u
+    new_len[u] = tree.length[v] * 0.3
+    new_len[v] = tree.length[v] * 0.7
+    t2 = synth.Tree(parent=new_parent, length=new_len)
+    table2 = synth.coo_to_table(table.n_features, table.n_samples,
+                                *np.nonzero(table.dense()),
+                                table.dense()[np.nonzero(table.dense())],
+                                remap[table.feature_node].astype(np.int32))
+    np.testing.assert_allclose(oracle.unifrac_full(t2, table2, variant), d1, rtol=0, atol=1e-13)
+    # zero-length pendant tip without a feature: appended as node 0
+    p3 = np.concatenate([[tree.parent[0] + 1], tree.parent + 1]).astype(np.int32)
+    p3[-1] = -1
+    l3 = np.concatenate([[0.0], tree.length])
+    t3 = synth.Tree(parent=p3, length=l3)
+    table3 = synth.Table(table.n_features, table.n_samples, table.indptr, table.indices,
+                         table.counts, (table.feature_node + 1).astype(np.int32))
+    np.testing.assert_allclose(oracle.unifrac_full(t3, table3, variant), d1, rtol=0, atol=1e-15)
+
+
+def test_empty_samples():
+    rng = np.random.default_rng(24)
+    tree, table = synth.random_case(rng, n_tips=9, n_samples=5, empty_samples=2)
+    dense = table.dense()
+    empty = np.nonzero(dense.sum(axis=0) == 0)[0]
+    full = np.nonzero(dense.sum(axis=0) > 0)[0]
+    assert len(empty) == 2 and len(full) > 0
+    for variant in (UW, WN):
+        d = oracle.unifrac_full(tree, table, variant)
+        assert d[empty[0], empty[1]] == 0.0
+        for j in full:
+            assert d[empty[0], j] == 1.0
+
+
+def test_rows_equal_pairs_and_thread_count():
+    rng = np.random.default_rng(25)
+    tree, table = synth.random_case(rng, n_tips=20, n_samples=12)
+    rows = [3, 0, 11]
+    out, used = oracle.unifrac_rows(tree, table, WN, rows, n_threads=2)
+    assert used >= 1
+    pi = np.repeat(rows, table.n_samples)
+    pj = np.tile(np.arange(table.n_samples), len(rows))
+    np.testing.assert_array_equal(oracle.unifrac_pairs(tree, table, WN, pi, pj),
+                                  out.reshape(-1))
+
+
+def test_invalid_inputs_rejected():
+    tree = synth.Tree(parent=np.array([2, 2, -1], np.int32), length=np.ones(3))
+    table = synth.dense_to_table(np.array([[1], [2]]), np.array([0, 1], np.int32))
+    bad_tree = synth.Tree(parent=np.array([2, 0, -1], np.int32), length=np.ones(3))
+    with pytest.raises(ValueError):
+        oracle.unifrac_full(bad_tree, table, UW)
+    internal = synth.dense_to_table(np.array([[1], [2]]), np.array([0, 2], np.int32))
+    with pytest.raises(ValueError):
+        oracle.unifrac_full(tree, internal, UW)
+
+
+@pytest.mark.parametrize("variant", [UW, WN])
+def test_root_branch_length_is_ignored(variant):
+    """Reading of the paper's silence on the root: its length never counts."""
+    rng = np.random.default_rng(26)
+    tree, table = synth.random_case(rng, n_tips=9, n_samples=6)
+    d1 = oracle.unifrac_full(tree, table, variant)
+    t2 = synth.Tree(parent=tree.parent, length=tree.length.copy())
+    t2.length[-1] = 5.0
+    np.testing.assert_array_equal(oracle.unifrac_full(t2, table, variant), d1)
