@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the all-pairs UniFrac path on B300 GPUs.
+
+One step = the whole hot path over one synthetic study: the branch embedding
+(level-synchronous postorder sums), packing, and the pair kernels of BOTH
+variants (unweighted on tensor cores, weighted normalized on the CUDA cores),
+in mixed precision, writing the condensed N(N-1)/2 matrices.  The metric is
+pair-branch updates per second: each variant counts C(N,2) * B, B the branches
+kept after pruning (observed below, non-zero length).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded row sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "tips32768_samples4096"
+METRIC = "UniFrac pair-branch updates/s (both variants, mixed precision)"
+UNIT = "pair-branch updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-rows", type=int, default=256,
+                    help="rows of the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ufb_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample(w, rows):
+    """Time the FP64 oracle (as it stands) on `rows` x all samples, both variants."""
+    import oracle
+    t0 = time.perf_counter()
+    out = {}
+    threads = 1
+    for v in (oracle.UNWEIGHTED, oracle.WEIGHTED_NORMALIZED):
+        out[v], threads = oracle.unifrac_rows(w.tree, w.table, v, rows)
+    dt = time.perf_counter() - t0
+    return out, dt, threads
+
+
+def kept_branches(w):
+    """Branches with a sample below them and non-zero length (B of the metric)."""
+    n = w.tree.n_nodes
+    reached = np.zeros(n, dtype=bool)
+    reached[w.table.feature_node[np.diff(w.table.indptr) > 0]] = True
+    for k in range(n - 1):  # postorder: children first
+        if reached[k]:
+            reached[w.tree.parent[k]] = True
+    reached[n - 1] = False
+    return int(np.count_nonzero(reached & (w.tree.length > 0)))
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_2107_05397_b300 import synth
+    w = synth.make_workload(args.workload)
+    N = w.table.n_samples
+    B = kept_branches(w)
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(N, size=min(args.cpu_rows, N), replace=False))
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(w, rows[:1])
+    times = []
+    threads = 1
+    for _ in range(args.steps):
+        _, dt, threads = oracle_sample(w, rows)
+        times.append(dt)
+    units = 2.0 * len(rows) * (N - 1) * B
+    value = units * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "samples": N, "branches": B,
+                   "sample": f"{len(rows)} seeded rows x {N} columns, both variants"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{len(rows)} rows x {N} columns x 2 variants per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    from paper_2107_05397_b300 import binding as ub
+    from paper_2107_05397_b300 import synth
+
+    rank, world, local_rank = env_rank()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = synth.make_workload(args.workload)
+    N = w.table.n_samples
+    stream = torch.cuda.current_stream()
+    ctx = ub.Context(w.tree, w.table, stream=stream)
+    nb_cond = ctx.output_bytes(ub.MIXED, ub.OUT_CONDENSED)
+    out_uw = torch.empty(nb_cond // 4, dtype=torch.float32, device="cuda")
+    out_wn = torch.empty(nb_cond // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    pair_branch = ctx.stat(ub.STAT_PAIR_BRANCH)
+    units_per_step = 2.0 * pair_branch  # both variants
+
+    def step(precision=ub.MIXED, a=out_uw, b=out_wn):
+        ctx.run(ub.UNWEIGHTED, precision, ub.OUT_CONDENSED, out=a)
+        launches = ctx.stat(ub.STAT_KERNEL_LAUNCHES)
+        ctx.run(ub.WEIGHTED_NORMALIZED, precision, ub.OUT_CONDENSED, out=b)
+        return launches + ctx.stat(ub.STAT_KERNEL_LAUNCHES)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    step_ms, pair_wn_ms, pair_uw_ms, sel_wn = [], [], [], []
+    launches = 0
+    peaks = measured_peaks()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        barrier()
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush, outside the event pair
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches += step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pair_uw_ms.append(ctx.stat(ub.STAT_PAIR_MS_UNWEIGHTED))
+            pair_wn_ms.append(ctx.stat(ub.STAT_PAIR_MS_WEIGHTED))
+            sel_wn.append(ctx.stat(ub.STAT_SELECTED_UPDATES))
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    clk = clocks.summary()
+    dev_err = ctx.stat(ub.STAT_DEVICE_ERROR)
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units_per_step * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (weighted pair kernel, FP32 ALU bound):
+    # 2 FP32 ops (min, add) per pair-branch update it performs
+    wn_ms = float(np.mean(pair_wn_ms))
+    ops = 2.0 * float(np.mean(sel_wn))
+    achieved = ops / (wn_ms / 1e3) / 1e12
+    sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * sm_max * 1e6 / 1e12
+    roofline = {
+        "kernel": "k_pairs_weighted<float>", "bound": "alu", "achieved": achieved,
+        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "traffic": recorded_traffic("k_pairs_weighted<float>"),
+        "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max clock)",
+        "work": "2 FP32 ops per selected pair-branch update",
+        "dense_equivalent_tflops": 2.0 * pair_branch / (wn_ms / 1e3) / 1e12,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16(int digits)+f64 reductions", "data": "synthetic",
+        "config": {"workload": args.workload, "samples": N,
+                   "branches_kept": ctx.stat(ub.STAT_BRANCHES_KEPT),
+                   "levels": ctx.stat(ub.STAT_LEVELS), "layout": "condensed",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "description": w.description},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "breakdown_ms": {"pair_unweighted": float(np.mean(pair_uw_ms)),
+                         "pair_weighted": wn_ms},
+        "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
+        "wall_s_timed_loop": t_wall,
+        "device_error": dev_err,
+    }
+
+    if rank == 0 and not args.no_fp64:
+        # the plain FP64 path (lookup unweighted + FP64 weighted) on the same GPU
+        out64a = torch.empty(nb_cond // 2, dtype=torch.float64, device="cuda")
+        out64b = torch.empty(nb_cond // 2, dtype=torch.float64, device="cuda")
+        step(ub.FP64, out64a, out64b)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(ub.FP64, out64a, out64b)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        line["fp64_plain"] = {"ms_per_step": ms64,
+                              "value": units_per_step / (ms64 / 1e3),
+                              "mixed_speedup": ms64 / ms_per_step}
+        del out64a, out64b
+
+    # end to end through the public API with host buffers
+    if rank == 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        host_in = [pin(w.tree.parent), pin(w.tree.length), pin(w.table.feature_node),
+                   pin(w.table.indptr), pin(w.table.indices), pin(w.table.counts)]
+        h2d = int(sum(a.nbytes for a in host_in))
+        res_a = torch.empty(nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
+        res_b = torch.empty(nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
+        e2e_t = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ub.unifrac_create(*host_in, n_samples=N, stream=stream)
+            ub.unifrac_run(h, ub.UNWEIGHTED, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res_a)
+            ub.unifrac_run(h, ub.WEIGHTED_NORMALIZED, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res_b)
+            ub.unifrac_destroy(h)
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+        t_e2e = float(np.median(e2e_t))
+        line["e2e"] = {"value": units_per_step / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(2 * nb_cond),
+                       "s_per_step": t_e2e,
+                       "includes": "create (validation, host prep, upload) + 2 runs + "
+                                   "D2H of both condensed matrices + destroy"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(7)
+        rows = np.sort(rng.choice(N, size=min(args.cpu_rows, N), replace=False))
+        ref, dt, threads = oracle_sample(w, rows)
+        B = kept_branches(w)
+        units = 2.0 * len(rows) * (N - 1) * B
+        line["cpu_baseline"] = {"value": units / dt, "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{len(rows)} seeded rows x {N} columns, both "
+                                          f"variants ({dt:.1f} s)"}
+        # error of this run's outputs on the same rows
+        errs = {}
+        for name, v, t in (("unweighted", 0, out_uw), ("weighted_normalized", 1, out_wn)):
+            got = t.cpu().numpy().astype(np.float64)
+            e = 0.0
+            for r, i in enumerate(rows):
+                j = np.arange(N)
+                a_, b_ = np.minimum(i, j), np.maximum(i, j)
+                idx = a_ * N - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
+                vals = np.where(i == j, 0.0, got[np.where(i == j, 0, idx)])
+                e = max(e, float(np.max(np.abs(vals - ref[v][r]))))
+            errs[name] = e
+        line["max_abs_err_vs_oracle"] = errs
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

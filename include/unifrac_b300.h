@@ -1,0 +1,202 @@
+/*
+ * unifrac_b300 -- all-pairs UniFrac distance matrices on one NVIDIA B300.
+ *
+ * C ABI of the library.  The operation is the one the paper (Section II)
+ * names as the core of microbiome beta-diversity analysis: for N samples of a
+ * feature x sample count table placed on a rooted phylogenetic tree, compute
+ * the N x N matrix of UniFrac distances, unweighted or weighted normalized,
+ * optionally split into stripes of the matrix that are computed separately
+ * and merged (Section II, "split the problem in smaller pieces, i.e. a set of
+ * stripes").  With, for every non-root branch b and sample i,
+ *
+ *   w[b,i] = (count of sample i on the tips below b) / (total count of i)
+ *   p[b,i] = 1 if w[b,i] > 0 else 0
+ *
+ *   unweighted          d_ij = sum_b len_b (p_bi XOR p_bj) / sum_b len_b (p_bi OR p_bj)
+ *   weighted normalized d_ij = sum_b len_b |w_bi - w_bj|  / sum_b len_b (w_bi + w_bj)
+ *
+ * (standard definitions; a zero denominator gives 0, the root branch is
+ * ignored).  Every call returns 0 on success or a negative UNIFRAC_E_* code;
+ * no call aborts, throws or prints.  A context is not thread-safe: use one
+ * context per host thread / stream.
+ */
+#ifndef UNIFRAC_B300_H
+#define UNIFRAC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct unifrac_ctx unifrac_ctx; /* opaque */
+
+/* Which distance (Section II: "both unweighted and the weighted normalized"). */
+enum unifrac_variant {
+  UNIFRAC_UNWEIGHTED = 0,
+  UNIFRAC_WEIGHTED_NORMALIZED = 1
+};
+
+/* Arithmetic (Section II: "fp32 compute support").
+ * UNIFRAC_FP64:  double output; every sum in FP64 (max abs error vs an FP64
+ *                reference <= 1e-12).
+ * UNIFRAC_MIXED: float output; FP32 bulk arithmetic (weighted) or exact
+ *                integer-digit BF16 tensor-core Gram (unweighted), with FP64
+ *                reductions (max abs error vs FP64 <= 2e-6). */
+enum unifrac_precision { UNIFRAC_FP64 = 0, UNIFRAC_MIXED = 1 };
+
+/* Output layouts.  Element type is double (FP64) or float (MIXED).
+ * STRIPES:   rows [stripe_start, stripe_stop) of the stripe form: stripe s in
+ *            [0, ceil((N-1)/2)), element k in [0, N) holds d(k, (k+s+1) mod N);
+ *            out is [(stripe_stop-stripe_start) x N] row-major.  The union of
+ *            all stripes covers every unordered pair (for even N the last
+ *            stripe holds each of its pairs twice).
+ * CONDENSED: upper triangle i<j, row-major, N(N-1)/2 elements.
+ * FULL:      N x N row-major, symmetric, zero diagonal.
+ * For CONDENSED and FULL the stripe range selects which pairs are computed
+ * and written; other elements of the caller's buffer are left untouched, so
+ * runs over disjoint stripe ranges merge into the full result. */
+enum unifrac_layout {
+  UNIFRAC_OUT_STRIPES = 0,
+  UNIFRAC_OUT_CONDENSED = 1,
+  UNIFRAC_OUT_FULL = 2
+};
+
+enum unifrac_status {
+  UNIFRAC_OK = 0,
+  UNIFRAC_E_INVALID_ARG = -1,    /* NULL pointer, bad enum, bad size */
+  UNIFRAC_E_BAD_TREE = -2,       /* not postorder, several roots, negative/NaN length,
+                                    feature on an internal node */
+  UNIFRAC_E_BAD_TABLE = -3,      /* CSR malformed, sample id out of range, negative
+                                    count, duplicate (feature, sample), two features
+                                    on one tip, a sample total >= 2^32 */
+  UNIFRAC_E_STRIPE_RANGE = -4,   /* stripe range outside [0, n_stripes] or reversed */
+  UNIFRAC_E_BUFFER_TOO_SMALL = -5,
+  UNIFRAC_E_CUDA = -6,           /* a CUDA runtime call failed */
+  UNIFRAC_E_OOM = -7,            /* device or host allocation failed */
+  UNIFRAC_E_DEVICE_TIMEOUT = -8, /* a bounded device-side wait gave up */
+  UNIFRAC_E_UNSUPPORTED = -9     /* combination not supported (message explains) */
+};
+
+/*
+ * unifrac_create -- validate and upload one problem: a tree, a table and the
+ * studies the samples belong to.  Section II: the input is a table of
+ * microbiome profiles (sparse: most features absent from most samples) and the
+ * tree of evolutionary relationships between its features.
+ *
+ *  n_nodes        nodes of the rooted tree, >= 1.
+ *  parent[n]      postorder parent array: parent[k] > k for k < n-1 and
+ *                 parent[n-1] = -1 (the root is the last node).  Host memory.
+ *  length[n]      FP64 branch length above each node (>= 0, finite); the
+ *                 root's is ignored.  Host memory.
+ *  n_features     rows of the table, >= 0.
+ *  feature_node[F] tip node of each feature (a node with no children; at
+ *                 most one feature per tip).  Host memory.
+ *  n_samples      columns of the table, >= 0.
+ *  indptr[F+1], indices[nnz], counts[nnz]
+ *                 CSR table, rows = features, indices = sample ids in
+ *                 [0, n_samples), counts >= 0 (0 means absent), no duplicate
+ *                 (feature, sample).  int64 / int32 / int32, host memory.
+ *  n_studies      >= 1.  With n_studies > 1 the samples are the concatenation
+ *                 of independent studies that share the tree; distances are
+ *                 formed only within a study.
+ *  study_offsets  [n_studies+1] sample offsets (0 ... n_samples, non-decreasing),
+ *                 or NULL when n_studies == 1.  Host memory.
+ *  cuda_stream    cudaStream_t on which every later device operation of this
+ *                 context is enqueued (NULL = legacy default stream).  The
+ *                 current CUDA device at create time is the context's device.
+ *  out            receives the new context.
+ *
+ * Every input is copied; the caller keeps ownership and may free its buffers
+ * when the call returns.  Host-side work: validation, node levels, per-branch
+ * presence counts (which branches any sample reaches), the branch order and
+ * the tensor-core length digits; O(n + nnz + size of the presence sets).
+ */
+int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
+                   int32_t n_features, const int32_t *feature_node,
+                   int32_t n_samples, const int64_t *indptr,
+                   const int32_t *indices, const int32_t *counts,
+                   int32_t n_studies, const int32_t *study_offsets,
+                   void *cuda_stream, unifrac_ctx **out);
+
+/*
+ * unifrac_run -- compute distances into `out`.
+ *
+ *  variant        enum unifrac_variant.
+ *  precision      enum unifrac_precision.
+ *  stripe_start, stripe_stop
+ *                 stripe range [start, stop); stop = -1 means "to the last
+ *                 stripe".  With n_studies > 1 only the whole range (0, -1) is
+ *                 accepted and layout must be CONDENSED or FULL; the output is
+ *                 each study's block in study order.
+ *  layout         enum unifrac_layout.
+ *  out            device pointer (enqueued on the context's stream, returns
+ *                 before completion) or host pointer (staged through device
+ *                 memory; the call returns after the copy has completed).
+ *  out_bytes      capacity of `out`; must be >= unifrac_output_bytes(...).
+ *
+ * Pipeline (all on the device): embedding of every branch (level-synchronous
+ * postorder sums, skipping all-zero branch tiles), packing for the chosen
+ * kernel, the pair kernel, and the epilogue writing `out`.  Work buffers are
+ * allocated on first use and kept in the context.
+ */
+int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
+                int32_t stripe_start, int32_t stripe_stop, int layout,
+                void *out, size_t out_bytes);
+
+/* Frees the context and its device buffers (synchronises its stream first).
+ * NULL-safe. */
+void unifrac_destroy(unifrac_ctx *ctx);
+
+/* Static message for a status code (never NULL).  The most recent failure of a
+ * context has a detailed message in unifrac_last_error(ctx). */
+const char *unifrac_strerror(int status);
+const char *unifrac_last_error(const unifrac_ctx *ctx);
+
+/* Number of stripes ceil((n-1)/2) of study `study` (n = its sample count). */
+int unifrac_n_stripes(const unifrac_ctx *ctx, int32_t study, int32_t *out);
+
+/* Bytes `out` must hold for the given layout / precision / stripe range. */
+int unifrac_output_bytes(const unifrac_ctx *ctx, int precision, int layout,
+                         int32_t stripe_start, int32_t stripe_stop,
+                         size_t *out);
+
+/* Tuning options (the autotuner sets these; defaults are chosen per shape).
+ * Values are validated; a bad key or value returns UNIFRAC_E_INVALID_ARG. */
+enum unifrac_option {
+  UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL = 0, /* 0 auto (tensor core), 1 tensor core,
+                                              2 bit-packed lookup (FP64 sums) */
+  UNIFRAC_OPT_WEIGHTED_FLUSH = 1,         /* FP32 branches per FP64 flush, 16..4096 */
+  UNIFRAC_OPT_PERSISTENT = 2,             /* 0 one CTA per tile pair, 1 persistent
+                                              work queue (default for many studies) */
+  UNIFRAC_OPT_CTAS_PER_SM = 3,            /* persistent grid = SMs x this, 1..8 */
+  UNIFRAC_OPT_USE_GRAPH = 4               /* 1 = capture the level loop in a CUDA graph */
+};
+int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
+
+/* Statistics of the context / its last run. */
+enum unifrac_stat {
+  UNIFRAC_STAT_KERNEL_LAUNCHES = 0, /* kernels launched by the last run */
+  UNIFRAC_STAT_PAIR_BRANCH = 1,     /* sum over studies of C(n_s,2) * B_s */
+  UNIFRAC_STAT_USEFUL = 2,          /* sum over studies and branches of C(n_b,2) */
+  UNIFRAC_STAT_BRANCHES_KEPT = 3,   /* branches with a sample below and length > 0 */
+  UNIFRAC_STAT_LEVELS = 4,          /* levels of the postorder embedding */
+  UNIFRAC_STAT_TILE_PAIRS = 5,      /* 128 x 128 pair tiles of the last run */
+  UNIFRAC_STAT_SELECTED_UPDATES = 6,/* pair-branch updates the last pair kernel did
+                                       (after skipping all-zero branch tiles) */
+  UNIFRAC_STAT_PAIR_KERNEL_MS = 7,  /* device time of the last pair kernel (ms) */
+  UNIFRAC_STAT_EMBED_MS = 8,        /* device time of the last embedding + pack (ms) */
+  UNIFRAC_STAT_DEVICE_BYTES = 9,    /* device memory held by the context */
+  UNIFRAC_STAT_PAIR_MS_UNWEIGHTED = 10, /* device time of the pair kernel of the last */
+  UNIFRAC_STAT_PAIR_MS_WEIGHTED = 11,   /*   unweighted / weighted run (ms)          */
+  UNIFRAC_STAT_DEVICE_ERROR = 12    /* 0, or the UNIFRAC_E_* code a kernel of the last run
+                                       raised (synchronises the context's stream) */
+};
+int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNIFRAC_B300_H */

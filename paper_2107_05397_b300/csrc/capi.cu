@@ -1,0 +1,752 @@
+// C ABI of unifrac_b300: context creation (host-side validation and tree /
+// table preparation), the run pipeline and the small helper calls.
+//
+// Section II of the paper frames the problem: a table of microbiome profiles
+// that is sparse, a phylogenetic tree over its features, and the all-pairs
+// UniFrac distance matrix, computable in stripes that merge into the whole.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ufb_internal.cuh"
+
+namespace ufb {
+
+int fail(unifrac_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+int cuda_fail(unifrac_ctx *ctx, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, UNIFRAC_E_OOM, m);
+  return fail(ctx, UNIFRAC_E_CUDA, m);
+}
+
+int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b.bytes >= bytes) return UNIFRAC_OK;
+  if (b.p) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before reallocation");
+    cudaFree(b.p);
+    ctx->device_bytes -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return cuda_fail(ctx, e, "device allocation");
+  }
+  b.bytes = bytes;
+  ctx->device_bytes += bytes;
+  return UNIFRAC_OK;
+}
+
+namespace {
+
+// Keeps the caller's current device unchanged across a library call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+int upload(unifrac_ctx *ctx, T **dst, const std::vector<T> &src) {
+  size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (inputs)");
+  ctx->device_bytes += bytes;
+  if (!src.empty()) {
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload inputs");
+  }
+  return UNIFRAC_OK;
+}
+
+void free_ctx(unifrac_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  void *ptrs[] = {ctx->d_level_nodes, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
+                  ctx->d_frow_ptr,    ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
+                  ctx->d_col_ptr,     ctx->d_col_cnt,   ctx->d_col_depth, ctx->d_perm,
+                  ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
+                         &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
+                         &ctx->studies, &ctx->stage,     &ctx->tables};
+  for (auto *b : bufs)
+    if (b->p) cudaFree(b->p);
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto &pr : ctx->ev_pair)
+    for (auto &e : pr)
+      if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int64_t n_pairs_layout(int layout, int64_t n, int32_t s0, int32_t s1) {
+  if (layout == UNIFRAC_OUT_FULL) return n * n;
+  if (layout == UNIFRAC_OUT_CONDENSED) return n * (n - 1) / 2;
+  return (int64_t)(s1 - s0) * n;
+}
+
+// Tile pairs (I <= J) of a study that hold at least one pair of the stripe
+// range, plus the diagonal tiles when the layout writes a diagonal.
+void study_items(int32_t study, int32_t n, int32_t tile0, int layout, int32_t s0, int32_t s1,
+                 std::vector<WorkItem> &items) {
+  if (n <= 0) return;
+  if (n == 1 && layout != UNIFRAC_OUT_FULL) return;
+  const int32_t T = (n + TILE - 1) / TILE;
+  for (int32_t I = 0; I < T; ++I) {
+    for (int32_t J = I; J < T; ++J) {
+      bool need = (I == J && layout == UNIFRAC_OUT_FULL);
+      if (!need) {
+        // differences delta = lj - li of pairs li < lj in the tile pair
+        const int64_t i0 = (int64_t)I * TILE, i1 = std::min<int64_t>(i0 + TILE, n) - 1;
+        const int64_t j0 = (int64_t)J * TILE, j1 = std::min<int64_t>(j0 + TILE, n) - 1;
+        const int64_t dlo = std::max<int64_t>(1, j0 - i1), dhi = j1 - i0;
+        if (dlo <= dhi) {
+          // stripe of delta: min(delta-1, n-delta-1) in [s0, s1)
+          //   delta in [s0+1, s1]  or  delta in [n-s1, n-s0-1]
+          const int64_t a0 = std::max<int64_t>(dlo, s0 + 1), a1 = std::min<int64_t>(dhi, s1);
+          const int64_t b0 = std::max<int64_t>(dlo, (int64_t)n - s1),
+                        b1 = std::min<int64_t>(dhi, (int64_t)n - s0 - 1);
+          need = (a0 <= a1) || (b0 <= b1);
+        }
+      }
+      if (need) items.push_back(WorkItem{tile0 + I, tile0 + J, study, 0});
+    }
+  }
+}
+
+}  // namespace
+}  // namespace ufb
+
+using namespace ufb;
+
+extern "C" {
+
+const char *unifrac_strerror(int status) {
+  switch (status) {
+    case UNIFRAC_OK: return "success";
+    case UNIFRAC_E_INVALID_ARG: return "invalid argument";
+    case UNIFRAC_E_BAD_TREE: return "malformed tree";
+    case UNIFRAC_E_BAD_TABLE: return "malformed table";
+    case UNIFRAC_E_STRIPE_RANGE: return "stripe range out of bounds";
+    case UNIFRAC_E_BUFFER_TOO_SMALL: return "output buffer too small";
+    case UNIFRAC_E_CUDA: return "CUDA error";
+    case UNIFRAC_E_OOM: return "out of memory";
+    case UNIFRAC_E_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case UNIFRAC_E_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+  }
+}
+
+const char *unifrac_last_error(const unifrac_ctx *ctx) {
+  return ctx ? ctx->last_error.c_str() : "no context";
+}
+
+static int create_impl(int32_t n_nodes, const int32_t *parent, const double *length,
+                       int32_t n_features, const int32_t *feature_node, int32_t n_samples,
+                       const int64_t *indptr, const int32_t *indices, const int32_t *counts,
+                       int32_t n_studies, const int32_t *study_offsets, void *cuda_stream,
+                       unifrac_ctx *ctx) {
+  // ---------------------------------------------------------------- arguments
+  if (n_nodes < 1 || !parent || !length) return fail(ctx, UNIFRAC_E_INVALID_ARG, "tree arrays");
+  if (n_features < 0 || n_samples < 0 || !indptr)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "table sizes / indptr");
+  if (n_features > 0 && !feature_node)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "feature_node is NULL");
+  if (n_studies < 1) return fail(ctx, UNIFRAC_E_INVALID_ARG, "n_studies < 1");
+  if (n_studies > 1 && !study_offsets)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "study_offsets is NULL with several studies");
+  const int64_t nnz = indptr[n_features];
+  if (indptr[0] != 0 || nnz < 0) return fail(ctx, UNIFRAC_E_BAD_TABLE, "indptr[0] != 0");
+  if (nnz > 0 && (!indices || !counts))
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "indices / counts NULL");
+  if (n_samples > (INT32_MAX / 2)) return fail(ctx, UNIFRAC_E_INVALID_ARG, "too many samples");
+
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->n_nodes = n_nodes;
+  ctx->n_features = n_features;
+  ctx->n_samples = n_samples;
+  ctx->n_studies = n_studies;
+  ctx->nnz = nnz;
+  const int32_t root = n_nodes - 1;
+
+  // ---------------------------------------------------------------- tree
+  for (int32_t k = 0; k < root; ++k) {
+    if (parent[k] <= k || parent[k] >= n_nodes)
+      return fail(ctx, UNIFRAC_E_BAD_TREE,
+                  "parent[" + std::to_string(k) + "] is not a later node (postorder required)");
+    if (!std::isfinite(length[k]) || length[k] < 0.0)
+      return fail(ctx, UNIFRAC_E_BAD_TREE,
+                  "length[" + std::to_string(k) + "] is negative or not finite");
+  }
+  if (parent[root] != -1) return fail(ctx, UNIFRAC_E_BAD_TREE, "the last node must be the root");
+  std::vector<int32_t> child_ptr(n_nodes + 1, 0), child_idx(std::max(root, 1));
+  for (int32_t k = 0; k < root; ++k) child_ptr[parent[k] + 1]++;
+  for (int32_t v = 0; v < n_nodes; ++v) child_ptr[v + 1] += child_ptr[v];
+  {
+    std::vector<int32_t> fill(child_ptr.begin(), child_ptr.end() - 1);
+    for (int32_t k = 0; k < root; ++k) child_idx[fill[parent[k]]++] = k;
+  }
+  // levels: tips 0, internal nodes 1 + highest child
+  std::vector<int32_t> level(n_nodes, 0);
+  for (int32_t k = 0; k < root; ++k) level[parent[k]] = std::max(level[parent[k]], level[k] + 1);
+  int32_t max_level = 0;
+  for (int32_t k = 0; k < root; ++k) max_level = std::max(max_level, level[k]);
+  ctx->n_levels = max_level;
+  ctx->level_ptr.assign(max_level + 1, 0);
+  for (int32_t k = 0; k < root; ++k)
+    if (level[k] >= 1) ctx->level_ptr[level[k]]++;
+  for (int32_t L = 0; L < max_level; ++L) ctx->level_ptr[L + 1] += ctx->level_ptr[L];
+  std::vector<int32_t> level_nodes(ctx->level_ptr[max_level]);
+  {
+    std::vector<int32_t> fill(ctx->level_ptr.begin(), ctx->level_ptr.end());
+    for (int32_t k = 0; k < root; ++k)
+      if (level[k] >= 1) level_nodes[fill[level[k] - 1]++] = k;
+  }
+  // root-to-node path length (root branch excluded), parents before children
+  std::vector<double> depth(n_nodes, 0.0);
+  for (int32_t k = root - 1; k >= 0; --k) depth[k] = depth[parent[k]] + length[k];
+
+  // ---------------------------------------------------------------- studies
+  std::vector<int32_t> soff(n_studies + 1, 0);
+  if (study_offsets) {
+    for (int32_t s = 0; s <= n_studies; ++s) soff[s] = study_offsets[s];
+  } else {
+    soff[1] = n_samples;
+  }
+  if (soff[0] != 0 || soff[n_studies] != n_samples)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "study_offsets must run from 0 to n_samples");
+  for (int32_t s = 0; s < n_studies; ++s)
+    if (soff[s + 1] < soff[s]) return fail(ctx, UNIFRAC_E_INVALID_ARG, "study_offsets decrease");
+  ctx->study_off = soff;
+  ctx->study_col0.assign(n_studies, 0);
+  int64_t cols = 0;
+  for (int32_t s = 0; s < n_studies; ++s) {
+    ctx->study_col0[s] = (int32_t)cols;
+    cols += ((int64_t)(soff[s + 1] - soff[s]) + TILE - 1) / TILE * TILE;
+  }
+  if (cols > INT32_MAX / 2) return fail(ctx, UNIFRAC_E_INVALID_ARG, "too many samples");
+  ctx->n_cols = (int32_t)cols;
+  ctx->n_tiles = ctx->n_cols / TILE;
+  ctx->col_of_sample.assign(n_samples, 0);
+  std::vector<int32_t> study_of(n_samples, 0);
+  for (int32_t s = 0; s < n_studies; ++s)
+    for (int32_t i = soff[s]; i < soff[s + 1]; ++i) {
+      ctx->col_of_sample[i] = ctx->study_col0[s] + (i - soff[s]);
+      study_of[i] = s;
+    }
+
+  // ---------------------------------------------------------------- table
+  std::vector<char> tip_used(n_nodes, 0);
+  for (int32_t f = 0; f < n_features; ++f) {
+    const int32_t t = feature_node[f];
+    if (t < 0 || t >= n_nodes)
+      return fail(ctx, UNIFRAC_E_BAD_TREE, "feature_node[" + std::to_string(f) + "] out of range");
+    if (child_ptr[t + 1] != child_ptr[t])
+      return fail(ctx, UNIFRAC_E_BAD_TREE,
+                  "feature " + std::to_string(f) + " sits on an internal node");
+    if (tip_used[t])
+      return fail(ctx, UNIFRAC_E_BAD_TABLE, "two features on tip " + std::to_string(t));
+    tip_used[t] = 1;
+  }
+  std::vector<int64_t> total(n_samples, 0);
+  std::vector<int32_t> frow_tip;
+  std::vector<int64_t> frow_ptr(1, 0);
+  std::vector<int32_t> fent_col;
+  std::vector<uint32_t> fent_cnt;
+  std::vector<int64_t> s_ptr(n_samples + 1, 0);  // per-sample entries (for marking)
+  std::vector<std::pair<int32_t, int32_t>> row;  // (sample, count)
+  for (int32_t f = 0; f < n_features; ++f) {
+    const int64_t lo = indptr[f], hi = indptr[f + 1];
+    if (hi < lo || hi > nnz) return fail(ctx, UNIFRAC_E_BAD_TABLE, "indptr not monotone");
+    row.clear();
+    for (int64_t e = lo; e < hi; ++e) {
+      const int32_t s = indices[e];
+      if (s < 0 || s >= n_samples)
+        return fail(ctx, UNIFRAC_E_BAD_TABLE, "sample index out of range in row " + std::to_string(f));
+      if (counts[e] < 0) return fail(ctx, UNIFRAC_E_BAD_TABLE, "negative count");
+      if (counts[e] > 0) row.emplace_back(s, counts[e]);
+    }
+    if (!std::is_sorted(row.begin(), row.end())) std::sort(row.begin(), row.end());
+    for (size_t q = 1; q < row.size(); ++q)
+      if (row[q].first == row[q - 1].first)
+        return fail(ctx, UNIFRAC_E_BAD_TABLE,
+                    "duplicate (feature, sample) entry in row " + std::to_string(f));
+    // explicit zeros are absent features, but duplicates including zeros are still malformed
+    for (int64_t e = lo + 1; e < hi; ++e)
+      if (indices[e] == indices[e - 1])
+        return fail(ctx, UNIFRAC_E_BAD_TABLE,
+                    "duplicate (feature, sample) entry in row " + std::to_string(f));
+    if (row.empty()) continue;
+    frow_tip.push_back(feature_node[f]);
+    for (auto &pr : row) {
+      fent_col.push_back(ctx->col_of_sample[pr.first]);
+      fent_cnt.push_back((uint32_t)pr.second);
+      total[pr.first] += pr.second;
+      s_ptr[pr.first + 1]++;
+    }
+    frow_ptr.push_back((int64_t)fent_col.size());
+  }
+  for (int32_t i = 0; i < n_samples; ++i)
+    if (total[i] > (int64_t)UINT32_MAX)
+      return fail(ctx, UNIFRAC_E_BAD_TABLE,
+                  "sample " + std::to_string(i) + " has a total count >= 2^32");
+  ctx->n_frows = (int32_t)frow_tip.size();
+  for (int32_t i = 0; i < n_samples; ++i) s_ptr[i + 1] += s_ptr[i];
+  // per-sample tips (sample-major), built from the feature-major entries
+  std::vector<int32_t> s_tip(fent_col.size());
+  std::vector<uint32_t> s_cnt(fent_col.size());
+  {
+    std::vector<int64_t> fill(s_ptr.begin(), s_ptr.end() - 1);
+    std::vector<int32_t> sample_of_col(ctx->n_cols, -1);
+    for (int32_t i = 0; i < n_samples; ++i) sample_of_col[ctx->col_of_sample[i]] = i;
+    for (int32_t r = 0; r < ctx->n_frows; ++r)
+      for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e) {
+        const int32_t i = sample_of_col[fent_col[e]];
+        s_tip[fill[i]] = frow_tip[r];
+        s_cnt[fill[i]] = fent_cnt[e];
+        fill[i]++;
+      }
+  }
+
+  // ------------------------------------------- presence counts and pruning
+  // A sample reaches every branch on the root paths of its tips.  Walking up
+  // from each tip and stopping at the first node already reached by the same
+  // sample visits each reached branch once per sample.
+  ctx->nb.assign(n_nodes, 0);
+  std::vector<int32_t> mark(n_nodes, -1);
+  std::vector<int64_t> nb_study(n_nodes, 0);
+  std::vector<int32_t> touched;
+  double pair_branch = 0.0, useful = 0.0;
+  for (int32_t s = 0; s < n_studies; ++s) {
+    touched.clear();
+    for (int32_t i = soff[s]; i < soff[s + 1]; ++i) {
+      for (int64_t e = s_ptr[i]; e < s_ptr[i + 1]; ++e) {
+        int32_t v = s_tip[e];
+        while (v != root && mark[v] != i) {
+          mark[v] = i;
+          if (nb_study[v] == 0) touched.push_back(v);
+          nb_study[v]++;
+          v = parent[v];
+        }
+      }
+    }
+    int64_t B_s = 0;
+    for (int32_t v : touched) {
+      if (length[v] > 0.0) {
+        B_s++;
+        useful += 0.5 * (double)nb_study[v] * (double)(nb_study[v] - 1);
+      }
+      ctx->nb[v] += nb_study[v];
+      nb_study[v] = 0;
+    }
+    const double n_s = (double)(soff[s + 1] - soff[s]);
+    pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
+  }
+  ctx->stat_pair_branch = pair_branch;
+  ctx->stat_useful = useful;
+  std::vector<int32_t> perm;
+  for (int32_t v = 0; v < root; ++v)
+    if (ctx->nb[v] > 0 && length[v] > 0.0) perm.push_back(v);
+  std::stable_sort(perm.begin(), perm.end(),
+                   [&](int32_t x, int32_t y) { return ctx->nb[x] > ctx->nb[y]; });
+  ctx->K = (int32_t)perm.size();
+  ctx->K_pad = std::max<int32_t>(64, (ctx->K + 63) / 64 * 64);
+  std::vector<double> len_perm(ctx->K_pad, 0.0);
+  for (int32_t k = 0; k < ctx->K; ++k) len_perm[k] = length[perm[k]];
+  perm.resize(ctx->K_pad, -1);
+  // base-256 digits of len / sigma for the tensor-core Gram (24-bit fixed
+  // point, sigma the power of two just above the longest kept branch)
+  double maxlen = 0.0;
+  for (int32_t k = 0; k < ctx->K; ++k) maxlen = std::max(maxlen, len_perm[k]);
+  int ex = 0;
+  if (maxlen > 0.0) std::frexp(maxlen, &ex);  // maxlen < 2^ex
+  const double sigma = std::ldexp(1.0, ex);
+  ctx->tc_scale = std::ldexp(sigma, -24);
+  std::vector<uint8_t> digits(3 * (size_t)ctx->K_pad, 0);
+  for (int32_t k = 0; k < ctx->K; ++k) {
+    int64_t q = std::llround(std::ldexp(len_perm[k] / sigma, 24));
+    q = std::min<int64_t>(std::max<int64_t>(q, 0), (1 << 24) - 1);
+    digits[k] = (uint8_t)(q >> 16);
+    digits[ctx->K_pad + k] = (uint8_t)((q >> 8) & 255);
+    digits[2 * (size_t)ctx->K_pad + k] = (uint8_t)(q & 255);
+  }
+
+  // per-column reciprocal totals and the column-sorted table
+  std::vector<double> inv_total(ctx->n_cols, 0.0);
+  for (int32_t i = 0; i < n_samples; ++i)
+    if (total[i] > 0) inv_total[ctx->col_of_sample[i]] = 1.0 / (double)total[i];
+  std::vector<int64_t> col_ptr(ctx->n_cols + 1, 0);
+  for (int32_t i = 0; i < n_samples; ++i)
+    col_ptr[ctx->col_of_sample[i] + 1] = s_ptr[i + 1] - s_ptr[i];
+  for (int32_t c = 0; c < ctx->n_cols; ++c) col_ptr[c + 1] += col_ptr[c];
+  std::vector<uint32_t> col_cnt(s_cnt.size());
+  std::vector<double> col_depth(s_cnt.size());
+  for (int32_t i = 0; i < n_samples; ++i) {
+    int64_t at = col_ptr[ctx->col_of_sample[i]];
+    for (int64_t e = s_ptr[i]; e < s_ptr[i + 1]; ++e, ++at) {
+      col_cnt[at] = s_cnt[e];
+      col_depth[at] = depth[s_tip[e]];
+    }
+  }
+
+  // ---------------------------------------------------------------- device
+  if (cudaGetDevice(&ctx->device) != cudaSuccess)
+    return fail(ctx, UNIFRAC_E_CUDA, "no CUDA device");
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device properties");
+  ctx->sm_count = prop.multiProcessorCount;
+  int rc;
+  if ((rc = upload(ctx, &ctx->d_level_nodes, level_nodes))) return rc;
+  if ((rc = upload(ctx, &ctx->d_child_ptr, child_ptr))) return rc;
+  if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
+  if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
+  if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
+  if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
+  if ((rc = upload(ctx, &ctx->d_fent_cnt, fent_cnt))) return rc;
+  if ((rc = upload(ctx, &ctx->d_inv_total, inv_total))) return rc;
+  if ((rc = upload(ctx, &ctx->d_col_ptr, col_ptr))) return rc;
+  if ((rc = upload(ctx, &ctx->d_col_cnt, col_cnt))) return rc;
+  if ((rc = upload(ctx, &ctx->d_col_depth, col_depth))) return rc;
+  if ((rc = upload(ctx, &ctx->d_perm, perm))) return rc;
+  if ((rc = upload(ctx, &ctx->d_len_perm, len_perm))) return rc;
+  if ((rc = upload(ctx, &ctx->d_digits, digits))) return rc;
+  std::vector<unsigned long long> zero4(4, 0ull);
+  if ((rc = upload(ctx, &ctx->d_counter, zero4))) return rc;
+  for (auto &ev : ctx->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+  }
+  for (auto &pr : ctx->ev_pair)
+    for (auto &ev : pr) {
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+    }
+  return UNIFRAC_OK;
+}
+
+int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
+                   int32_t n_features, const int32_t *feature_node, int32_t n_samples,
+                   const int64_t *indptr, const int32_t *indices, const int32_t *counts,
+                   int32_t n_studies, const int32_t *study_offsets, void *cuda_stream,
+                   unifrac_ctx **out) {
+  if (!out) return UNIFRAC_E_INVALID_ARG;
+  *out = nullptr;
+  unifrac_ctx *ctx = new (std::nothrow) unifrac_ctx();
+  if (!ctx) return UNIFRAC_E_OOM;
+  int rc;
+  try {
+    rc = create_impl(n_nodes, parent, length, n_features, feature_node, n_samples, indptr,
+                     indices, counts, n_studies, study_offsets, cuda_stream, ctx);
+  } catch (const std::bad_alloc &) {
+    rc = UNIFRAC_E_OOM;
+  } catch (...) {
+    rc = UNIFRAC_E_INVALID_ARG;
+  }
+  if (rc != UNIFRAC_OK) {
+    free_ctx(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return UNIFRAC_OK;
+}
+
+void unifrac_destroy(unifrac_ctx *ctx) { free_ctx(ctx); }
+
+int unifrac_n_stripes(const unifrac_ctx *ctx, int32_t study, int32_t *out) {
+  if (!ctx || !out || study < 0 || study >= ctx->n_studies) return UNIFRAC_E_INVALID_ARG;
+  *out = (ctx->study_off[study + 1] - ctx->study_off[study]) / 2;
+  return UNIFRAC_OK;
+}
+
+static int resolve_range(const unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1,
+                         int32_t *r0, int32_t *r1) {
+  if (ctx->n_studies > 1) {
+    if (layout == UNIFRAC_OUT_STRIPES || s0 != 0 || s1 != -1) return UNIFRAC_E_UNSUPPORTED;
+    *r0 = 0;
+    *r1 = INT32_MAX;
+    return UNIFRAC_OK;
+  }
+  const int32_t nst = ctx->n_samples / 2;
+  if (s1 == -1) s1 = nst;
+  if (s0 < 0 || s1 < s0 || s1 > nst) return UNIFRAC_E_STRIPE_RANGE;
+  *r0 = s0;
+  *r1 = s1;
+  return UNIFRAC_OK;
+}
+
+int unifrac_output_bytes(const unifrac_ctx *ctx, int precision, int layout,
+                         int32_t stripe_start, int32_t stripe_stop, size_t *out) {
+  if (!ctx || !out) return UNIFRAC_E_INVALID_ARG;
+  if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED) return UNIFRAC_E_INVALID_ARG;
+  if (layout < UNIFRAC_OUT_STRIPES || layout > UNIFRAC_OUT_FULL) return UNIFRAC_E_INVALID_ARG;
+  int32_t s0, s1;
+  int rc = resolve_range(ctx, layout, stripe_start, stripe_stop, &s0, &s1);
+  if (rc) return rc;
+  int64_t elems = 0;
+  for (int32_t s = 0; s < ctx->n_studies; ++s)
+    elems += n_pairs_layout(layout, ctx->study_off[s + 1] - ctx->study_off[s], s0, s1);
+  *out = (size_t)elems * (precision == UNIFRAC_FP64 ? 8 : 4);
+  return UNIFRAC_OK;
+}
+
+static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_start,
+                    int32_t stripe_stop, int layout, void *out, size_t out_bytes) {
+  if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "variant");
+  if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "precision");
+  if (layout < UNIFRAC_OUT_STRIPES || layout > UNIFRAC_OUT_FULL)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "layout");
+  int32_t s0, s1;
+  int rc = resolve_range(ctx, layout, stripe_start, stripe_stop, &s0, &s1);
+  if (rc == UNIFRAC_E_UNSUPPORTED)
+    return fail(ctx, rc, "several studies need layout CONDENSED or FULL and the range (0, -1)");
+  if (rc) return fail(ctx, rc, "stripe range");
+  size_t need = 0;
+  unifrac_output_bytes(ctx, precision, layout, stripe_start, stripe_stop, &need);
+  if (need > 0 && !out) return fail(ctx, UNIFRAC_E_INVALID_ARG, "out is NULL");
+  if (out_bytes < need)
+    return fail(ctx, UNIFRAC_E_BUFFER_TOO_SMALL,
+                "out holds " + std::to_string(out_bytes) + " bytes, needs " + std::to_string(need));
+  const bool f64 = precision == UNIFRAC_FP64;
+  ctx->stat_launches = 0;
+
+  // where does `out` live?
+  bool device_out = false;
+  if (need > 0) {
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, out);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      attr.type = cudaMemoryTypeUnregistered;
+    }
+    device_out = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  }
+  const bool whole = (layout == UNIFRAC_OUT_STRIPES) ||
+                     (s0 == 0 && (ctx->n_studies > 1 || s1 == ctx->n_samples / 2));
+  void *dst = out;
+  if (!device_out && need > 0) {
+    if ((rc = grow(ctx, ctx->stage, need))) return rc;
+    dst = ctx->stage.p;
+    if (!whole) {  // untouched elements keep the caller's values
+      cudaError_t e = cudaMemcpyAsync(dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "stage output");
+    }
+  }
+
+  // work items and study descriptors
+  std::vector<WorkItem> items;
+  std::vector<StudyDev> studies(ctx->n_studies);
+  int64_t off = 0;
+  for (int32_t s = 0; s < ctx->n_studies; ++s) {
+    const int32_t n = ctx->study_off[s + 1] - ctx->study_off[s];
+    studies[s] = StudyDev{off, n, ctx->study_col0[s]};
+    off += n_pairs_layout(layout, n, s0, s1);
+    study_items(s, n, ctx->study_col0[s] / TILE, layout, s0, s1, items);
+  }
+  ctx->stat_tile_pairs = (double)items.size();
+  if ((rc = grow(ctx, ctx->items, items.size() * sizeof(WorkItem)))) return rc;
+  if ((rc = grow(ctx, ctx->studies, studies.size() * sizeof(StudyDev)))) return rc;
+  cudaError_t e;
+  if (!items.empty()) {
+    e = cudaMemcpyAsync(ctx->items.p, items.data(), items.size() * sizeof(WorkItem),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload work items");
+  }
+  e = cudaMemcpyAsync(ctx->studies.p, studies.data(), studies.size() * sizeof(StudyDev),
+                      cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload studies");
+  e = cudaMemsetAsync(ctx->d_counter, 0, 4 * sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
+  OutSpec o;
+  o.out = dst;
+  o.studies = static_cast<const StudyDev *>(ctx->studies.p);
+  o.layout = layout;
+  o.s0 = s0;
+  o.s1 = s1;
+  o.is_f64 = f64 ? 1 : 0;
+
+  // embedding
+  const size_t cnt_bytes = (size_t)ctx->n_nodes * ctx->n_cols * sizeof(uint32_t);
+  if ((rc = grow(ctx, ctx->cnt, cnt_bytes))) return rc;
+  if ((rc = grow(ctx, ctx->flag, (size_t)ctx->n_nodes * ctx->n_tiles))) return rc;
+  uint32_t *cnt = static_cast<uint32_t *>(ctx->cnt.p);
+  uint8_t *flag = static_cast<uint8_t *>(ctx->flag.p);
+  cudaEventRecord(ctx->ev[0], ctx->stream);
+  if ((rc = embed_counts(ctx, cnt, flag))) return rc;
+
+  const WorkItem *d_items = static_cast<const WorkItem *>(ctx->items.p);
+  const int32_t n_items = (int32_t)items.size();
+  if (variant == UNIFRAC_WEIGHTED_NORMALIZED) {
+    const size_t elem = f64 ? 8 : 4;
+    if ((rc = grow(ctx, ctx->vals, (size_t)ctx->K_pad * ctx->n_cols * elem))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * (ctx->K_pad / WORD) * 4))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    double *S = static_cast<double *>(ctx->persample.p);
+    uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
+    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, S))) return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 1.0;
+    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, S, d_items, n_items, o))) return rc;
+  } else {
+    const int32_t G = ctx->K_pad / 8;
+    const int32_t g_words = (G + WORD - 1) / WORD;
+    if ((rc = grow(ctx, ctx->vals, (size_t)G * ctx->n_cols))) return rc;
+    if ((rc = grow(ctx, ctx->tables, (size_t)G * 256 * 8))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * g_words * 4))) return rc;
+    if ((rc = grow(ctx, ctx->partial, (size_t)((G + 31) / 32) * ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    double *a = static_cast<double *>(ctx->persample.p);
+    uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
+    double *tables = static_cast<double *>(ctx->tables.p);
+    uint32_t *gbits = static_cast<uint32_t *>(ctx->bits.p);
+    if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 8.0;
+    if ((rc = pairs_lookup(ctx, bytes, tables, gbits, a, d_items, n_items, o))) return rc;
+  }
+  cudaEventRecord(ctx->ev[2], ctx->stream);
+  cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
+  ctx->ev_valid = true;
+  ctx->ev_pair_valid[variant] = true;
+
+  if (!device_out && need > 0) {
+    e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "run");
+  return UNIFRAC_OK;
+}
+
+int unifrac_run(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_start,
+                int32_t stripe_stop, int layout, void *out, size_t out_bytes) {
+  if (!ctx) return UNIFRAC_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, UNIFRAC_E_CUDA, "cannot select the context's device");
+  try {
+    return run_impl(ctx, variant, precision, stripe_start, stripe_stop, layout, out, out_bytes);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, UNIFRAC_E_OOM, "host allocation");
+  } catch (...) {
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "unexpected failure");
+  }
+}
+
+int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
+  if (!ctx) return UNIFRAC_E_INVALID_ARG;
+  switch (option) {
+    case UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL:
+      if (value < 0 || value > 2) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_uw_kernel = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_WEIGHTED_FLUSH:
+      if (value < 16 || value > 4096) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_flush = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_PERSISTENT:
+      if (value < -1 || value > 1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_persistent = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_CTAS_PER_SM:
+      if (value < 1 || value > 8) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_ctas_per_sm = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_USE_GRAPH:
+      if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_use_graph = (int)value;
+      return UNIFRAC_OK;
+    default:
+      return UNIFRAC_E_INVALID_ARG;
+  }
+}
+
+int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
+  if (!ctx_c || !value) return UNIFRAC_E_INVALID_ARG;
+  unifrac_ctx *ctx = const_cast<unifrac_ctx *>(ctx_c);
+  switch (stat) {
+    case UNIFRAC_STAT_KERNEL_LAUNCHES: *value = ctx->stat_launches; return UNIFRAC_OK;
+    case UNIFRAC_STAT_PAIR_BRANCH: *value = ctx->stat_pair_branch; return UNIFRAC_OK;
+    case UNIFRAC_STAT_USEFUL: *value = ctx->stat_useful; return UNIFRAC_OK;
+    case UNIFRAC_STAT_BRANCHES_KEPT: *value = ctx->K; return UNIFRAC_OK;
+    case UNIFRAC_STAT_LEVELS: *value = ctx->n_levels; return UNIFRAC_OK;
+    case UNIFRAC_STAT_TILE_PAIRS: *value = ctx->stat_tile_pairs; return UNIFRAC_OK;
+    case UNIFRAC_STAT_DEVICE_BYTES: *value = (double)ctx->device_bytes; return UNIFRAC_OK;
+    case UNIFRAC_STAT_SELECTED_UPDATES:
+    case UNIFRAC_STAT_PAIR_KERNEL_MS:
+    case UNIFRAC_STAT_EMBED_MS: {
+      if (!ctx->ev_valid) return fail(ctx, UNIFRAC_E_INVALID_ARG, "no run yet");
+      DeviceGuard g(ctx->device);
+      cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+      if (stat == UNIFRAC_STAT_SELECTED_UPDATES) {
+        unsigned long long c = 0;
+        e = cudaMemcpy(&c, ctx->d_counter, sizeof(c), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
+        *value = (double)c * ctx->sel_unit * (double)TILE * (double)TILE;
+        return UNIFRAC_OK;
+      }
+      float ms = 0.f;
+      if (stat == UNIFRAC_STAT_PAIR_KERNEL_MS)
+        e = cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+      else
+        e = cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "elapsed time");
+      *value = ms;
+      return UNIFRAC_OK;
+    }
+    case UNIFRAC_STAT_PAIR_MS_UNWEIGHTED:
+    case UNIFRAC_STAT_PAIR_MS_WEIGHTED: {
+      const int v = stat == UNIFRAC_STAT_PAIR_MS_UNWEIGHTED ? 0 : 1;
+      if (!ctx->ev_pair_valid[v]) return fail(ctx, UNIFRAC_E_INVALID_ARG, "no run of that variant");
+      DeviceGuard g(ctx->device);
+      cudaError_t e = cudaEventSynchronize(ctx->ev_pair[v][1]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ctx->ev_pair[v][0], ctx->ev_pair[v][1]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "elapsed time");
+      *value = ms;
+      return UNIFRAC_OK;
+    }
+    case UNIFRAC_STAT_DEVICE_ERROR: {
+      DeviceGuard g(ctx->device);
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+      unsigned long long c[2] = {0, 0};
+      e = cudaMemcpy(c, ctx->d_counter, sizeof(c), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
+      *value = -(double)c[1];
+      return UNIFRAC_OK;
+    }
+    default:
+      return UNIFRAC_E_INVALID_ARG;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// K1: per-branch embedding of every sample, and the packing kernels that turn
+// it into the operand layout of each pair kernel.
+//
+// Section II of the paper: UniFrac accounts for the evolutionary relationships
+// between microbes -- a sample's abundance below a branch counts toward that
+// branch.  For branch b and sample i the embedding is the count of sample i on
+// the tips below b; the relative abundance is that count over the sample total.
+//
+// The tree is in postorder, so a node's children are finished before it.  The
+// kernels here are level-synchronous: level 0 holds the tips, level L the nodes
+// whose highest child is on level L-1, and one launch sums the children of all
+// nodes of one level.  Data is branch-major (a row of n_cols u32 counts per
+// node), processed in 128-column tiles by one warp each (16-byte loads); a
+// (node, tile) flag records whether the tile has any non-zero count, and tiles
+// whose children are all zero are neither read nor written (the sparse-aware
+// step: most features are absent from most samples).  Counts are summed as
+// exact integers; the division by the sample total happens once, in packing.
+#include "ufb_internal.cuh"
+
+namespace ufb {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+// Tip rows: one warp per table row (a feature on a tip).  Each 128-column tile
+// that holds an entry is zeroed, flagged and then receives the counts.
+__global__ void k_tip_rows(int32_t n_frows, const int32_t *__restrict__ frow_tip,
+                           const int64_t *__restrict__ frow_ptr,
+                           const int32_t *__restrict__ ent_col,
+                           const uint32_t *__restrict__ ent_cnt, uint32_t *cnt,
+                           uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_frows) return;
+  const int32_t tip = frow_tip[warp];
+  const int64_t lo = frow_ptr[warp], hi = frow_ptr[warp + 1];
+  uint32_t *row = cnt + (int64_t)tip * ldc;
+  for (int64_t e = lo + lane; e < hi; e += 32) {
+    const int32_t t = ent_col[e] / TILE;
+    if (e == lo || ent_col[e - 1] / TILE != t) {
+      uint4 *p = reinterpret_cast<uint4 *>(row + (int64_t)t * TILE);
+#pragma unroll 4
+      for (int q = 0; q < TILE / 4; ++q) p[q] = make_uint4(0u, 0u, 0u, 0u);
+      flag[(int64_t)tip * n_tiles + t] = 1;
+    }
+  }
+  __syncwarp();
+  for (int64_t e = lo + lane; e < hi; e += 32) row[ent_col[e]] = ent_cnt[e];
+}
+
+// One level: for every (node of the level, column tile), sum the flagged
+// children's tiles.  A warp owns one (node, tile): 32 lanes x uint4 = 128 columns.
+__global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
+                        const int32_t *__restrict__ child_ptr,
+                        const int32_t *__restrict__ child_idx, uint32_t *cnt,
+                        uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+  const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (item >= (int64_t)n_level * n_tiles) return;
+  const int32_t node = nodes[item / n_tiles];
+  const int32_t t = (int32_t)(item % n_tiles);
+  uint4 s = make_uint4(0u, 0u, 0u, 0u);
+  bool any = false;
+  const int32_t c1 = child_ptr[node + 1];
+  for (int32_t c = child_ptr[node]; c < c1; ++c) {
+    const int32_t ch = child_idx[c];
+    if (flag[(int64_t)ch * n_tiles + t]) {
+      any = true;
+      const uint4 v =
+          reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + (int64_t)t * TILE)[lane];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+  }
+  if (lane == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
+  if (any) reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)t * TILE)[lane] = s;
+}
+
+// Weighted packing.  Block (column tile t, branch block kb) of 8 warps; warp w
+// handles positions k = kb*KR + w, +8, ...; lane l owns 4 columns.  Writes
+// v[k][col] = len_k * cnt[perm[k]][col] / C_col for the flagged (k, t) rows and
+// the (t, k) bitmap words.  The mixed form computes v in FP32 (<= 3 roundings);
+// the FP64 form in FP64.
+constexpr int KR = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack_weighted(
+    int32_t K, const int32_t *__restrict__ perm, const double *__restrict__ len_perm,
+    const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
+    int32_t n_tiles, const double *__restrict__ inv_total, T *__restrict__ vals,
+    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words) {
+  const int t = blockIdx.x;
+  const int k0 = blockIdx.y * KR;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t col = (int64_t)t * TILE + lane * 4;
+  const int k1 = min(k0 + KR, K);
+  if constexpr (sizeof(T) == 4) {
+    float inv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) inv[q] = (float)inv_total[col + q];
+    for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
+      const int32_t b = perm[k];
+      if (!flag[(int64_t)b * n_tiles + t]) continue;
+      const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
+      const float L = (float)len_perm[k];
+      float4 v;
+      v.x = L * ((float)c.x * inv[0]);
+      v.y = L * ((float)c.y * inv[1]);
+      v.z = L * ((float)c.z * inv[2]);
+      v.w = L * ((float)c.w * inv[3]);
+      *reinterpret_cast<float4 *>(vals + (int64_t)k * ldv + col) = v;
+    }
+  } else {
+    double inv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) inv[q] = inv_total[col + q];
+    for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
+      const int32_t b = perm[k];
+      if (!flag[(int64_t)b * n_tiles + t]) continue;
+      const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
+      const double L = len_perm[k];
+      double2 v0, v1;
+      v0.x = L * ((double)c.x * inv[0]);
+      v0.y = L * ((double)c.y * inv[1]);
+      v1.x = L * ((double)c.z * inv[2]);
+      v1.y = L * ((double)c.w * inv[3]);
+      double2 *dst = reinterpret_cast<double2 *>(vals + (int64_t)k * ldv + col);
+      dst[0] = v0;
+      dst[1] = v1;
+    }
+  }
+  // bitmap words of this block: bit (k mod 32) of word k/32 = flag of branch k
+  if (threadIdx.x < KR / WORD) {
+    const int kw = k0 + threadIdx.x * WORD;
+    uint32_t word = 0;
+    for (int j = 0; j < WORD; ++j) {
+      const int k = kw + j;
+      if (k < K && flag[(int64_t)perm[k] * n_tiles + t]) word |= 1u << j;
+    }
+    if (kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
+  }
+}
+
+// Per-column sums S_col = sum_k v[k][col] through the tip-depth identity
+// S_i = (1 / C_i) * sum_f c_fi * depth(tip_f): one warp per column over that
+// column's table entries (column-sorted copy of the table), FP64, fixed order.
+__global__ void k_weighted_sums(int32_t n_cols, const int64_t *__restrict__ col_ptr,
+                                const uint32_t *__restrict__ col_cnt,
+                                const double *__restrict__ col_depth,
+                                const double *__restrict__ inv_total, double *__restrict__ S) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_cols) return;
+  double acc = 0.0;
+  for (int64_t e = col_ptr[warp] + lane; e < col_ptr[warp + 1]; e += 32)
+    acc += (double)col_cnt[e] * col_depth[e];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) S[warp] = acc * inv_total[warp];
+}
+
+// Lookup packing.  Block (column tile t, group block gb) of 128 threads, one
+// column each.  Group g holds positions 8g..8g+7; the byte of (g, col) has bit
+// j set when branch 8g+j is present in col.  Also the (t, g) group bitmap and
+// FP64 partial sums of a_col = sum_k len_k p[k][col] per group block.
+constexpr int GR = 32;  // groups per block
+
+__global__ void __launch_bounds__(128) k_pack_lookup(
+    int32_t K, int32_t G, const int32_t *__restrict__ perm,
+    const double *__restrict__ len_perm, const uint32_t *__restrict__ cnt,
+    const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_cols, int32_t n_tiles,
+    uint8_t *__restrict__ bytes, uint32_t *__restrict__ gbits, int32_t g_words,
+    double *__restrict__ partial) {
+  const int t = blockIdx.x;
+  const int g0 = blockIdx.y * GR;
+  const int64_t col = (int64_t)t * TILE + threadIdx.x;
+  double a = 0.0;
+  uint32_t gword = 0;
+  for (int gi = 0; gi < GR; ++gi) {
+    const int g = g0 + gi;
+    if (g >= G) break;
+    uint32_t byte = 0;
+    bool anyflag = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * g + j;
+      if (k < K) {
+        const int32_t b = perm[k];
+        if (flag[(int64_t)b * n_tiles + t]) {
+          anyflag = true;
+          if (cnt[(int64_t)b * ldc + col] != 0u) {
+            byte |= 1u << j;
+            a += len_perm[k];
+          }
+        }
+      }
+    }
+    bytes[(int64_t)g * n_cols + col] = (uint8_t)byte;
+    if (anyflag) gword |= 1u << gi;
+  }
+  if (threadIdx.x == 0 && g0 / WORD < g_words) gbits[(int64_t)t * g_words + g0 / WORD] = gword;
+  partial[(int64_t)blockIdx.y * n_cols + col] = a;
+}
+
+// T[g][m] = sum of len of the branches whose bit is set in m (FP64, bit order).
+__global__ void k_lookup_tables(int32_t K, const double *__restrict__ len_perm,
+                                double *__restrict__ tables) {
+  const int g = blockIdx.x;
+  const int m = threadIdx.x;  // 256 threads
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = 8 * g + j;
+    if ((m >> j) & 1) s += (k < K) ? len_perm[k] : 0.0;
+  }
+  tables[(int64_t)g * 256 + m] = s;
+}
+
+// a_col = sum over blocks of the partials, in block order (deterministic).
+__global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
+                                  const double *__restrict__ partial, double *__restrict__ a) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n_cols) return;
+  double s = 0.0;
+  for (int b = 0; b < n_blocks; ++b) s += partial[(int64_t)b * n_cols + col];
+  a[col] = s;
+}
+
+}  // namespace
+
+int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
+  cudaStream_t st = ctx->stream;
+  const int64_t ldc = ctx->n_cols;
+  cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)ctx->n_nodes * ctx->n_tiles, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset flags");
+  ctx->stat_launches += 1;
+  if (ctx->n_frows > 0 && ctx->n_tiles > 0) {
+    const int64_t threads = (int64_t)ctx->n_frows * 32;
+    const int blocks = (int)((threads + 255) / 256);
+    k_tip_rows<<<blocks, 256, 0, st>>>(ctx->n_frows, ctx->d_frow_tip, ctx->d_frow_ptr,
+                                       ctx->d_fent_col, ctx->d_fent_cnt, cnt, flag, ldc,
+                                       ctx->n_tiles);
+    ctx->stat_launches += 1;
+  }
+  for (int L = 0; L < ctx->n_levels && ctx->n_tiles > 0; ++L) {
+    const int32_t lo = ctx->level_ptr[L], hi = ctx->level_ptr[L + 1];
+    const int64_t items = (int64_t)(hi - lo) * ctx->n_tiles;
+    if (items == 0) continue;
+    const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_level<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(
+        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, flag, ldc,
+        ctx->n_tiles);
+    ctx->stat_launches += 1;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "embedding kernels");
+  return UNIFRAC_OK;
+}
+
+int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bool f64,
+                  void *vals, uint32_t *bits, double *S) {
+  cudaStream_t st = ctx->stream;
+  const int32_t n_words = ctx->K_pad / WORD;
+  if (ctx->K > 0 && ctx->n_tiles > 0) {
+    dim3 grid(ctx->n_tiles, (ctx->K + KR - 1) / KR);
+    if (f64)
+      k_pack_weighted<double><<<grid, 256, 0, st>>>(
+          ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words);
+    else
+      k_pack_weighted<float><<<grid, 256, 0, st>>>(
+          ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words);
+    ctx->stat_launches += 1;
+  }
+  if (ctx->n_cols > 0) {
+    const int64_t threads = (int64_t)ctx->n_cols * 32;
+    k_weighted_sums<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        ctx->n_cols, ctx->d_col_ptr, ctx->d_col_cnt, ctx->d_col_depth, ctx->d_inv_total, S);
+    ctx->stat_launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted packing");
+  return UNIFRAC_OK;
+}
+
+int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, uint8_t *bytes,
+                double *tables, uint32_t *gbits, double *a) {
+  cudaStream_t st = ctx->stream;
+  const int32_t G = ctx->K_pad / 8;
+  const int32_t g_words = (G + WORD - 1) / WORD;
+  const int32_t n_gblocks = (G + GR - 1) / GR;
+  double *partial = static_cast<double *>(ctx->partial.p);
+  if (G > 0 && ctx->n_tiles > 0) {
+    k_lookup_tables<<<G, 256, 0, st>>>(ctx->K, ctx->d_len_perm, tables);
+    dim3 grid(ctx->n_tiles, n_gblocks);
+    k_pack_lookup<<<grid, 128, 0, st>>>(ctx->K, G, ctx->d_perm, ctx->d_len_perm, cnt, flag,
+                                        ctx->n_cols, ctx->n_cols, ctx->n_tiles, bytes, gbits,
+                                        g_words, partial);
+    ctx->stat_launches += 2;
+  }
+  if (ctx->n_cols > 0) {
+    k_reduce_partials<<<(ctx->n_cols + 255) / 256, 256, 0, st>>>(
+        ctx->n_cols, G > 0 && ctx->n_tiles > 0 ? n_gblocks : 0, partial, a);
+    ctx->stat_launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lookup packing");
+  return UNIFRAC_OK;
+}
+
+}  // namespace ufb

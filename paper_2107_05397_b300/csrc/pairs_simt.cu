@@ -1,0 +1,406 @@
+// Pair kernels on the CUDA cores: weighted normalized UniFrac (FP32 with FP64
+// flushes, or all-FP64) and the bit-packed lookup form of unweighted UniFrac.
+//
+// Section II of the paper: the distance is formed for every pair of samples,
+// giving an N x N matrix, in a weighted normalized and an unweighted variant.
+// Both kernels compute a 128 x 128 block of pairs per CTA (thread micro-tile
+// 8 x 8 in registers) and sweep the branch dimension in windows of 1024
+// branches.  A branch enters the sweep only if it is non-zero somewhere in the
+// row tile AND somewhere in the column tile (AND of the two tiles' bitmaps),
+// which is the sparse-aware skipping of Hybrid UniFrac: both kernels only need
+// branches that the two samples share (see the identities below).  Selected
+// rows are staged into shared memory with cp.async in a two-stage pipeline.
+//
+// Weighted normalized, with v[b,i] = len_b * w[b,i] and S_i = sum_b v[b,i]:
+//   sum_b len_b |w_bi - w_bj| = S_i + S_j - 2 * sum_b min(v_bi, v_bj)
+//   sum_b len_b (w_bi + w_bj) = S_i + S_j
+// (|x - y| = x + y - 2 min(x, y)), so only co-present branches contribute to the
+// pair sum M_ij = sum_b min(v_bi, v_bj); S comes from the embedding.
+// Unweighted, with a_i = sum_b len_b p_bi and G_ij = sum_b len_b p_bi p_bj:
+//   sum_b len_b (p_bi XOR p_bj) = a_i + a_j - 2 G_ij
+//   sum_b len_b (p_bi OR p_bj)  = a_i + a_j - G_ij
+// and the lookup form evaluates G_ij 8 branches at a time from a byte of
+// presence bits: G_ij = sum_g T_g[x_gi AND x_gj], T_g[m] = sum of the lengths
+// of the branches whose bits are set in m.
+#include "epilogue.cuh"
+
+namespace ufb {
+
+namespace {
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kThreads = 256;
+constexpr int kWinWords = 32;  // bitmap words per window (1024 branches)
+
+// Warp 0 turns the AND of the two tiles' bitmap words [w0, w0+32) into an
+// ascending list of selected indices; returns the count through *list_n.
+__device__ __forceinline__ void build_window(const uint32_t *__restrict__ bI,
+                                             const uint32_t *__restrict__ bJ, int n_words,
+                                             int w0, int32_t *list, int32_t *list_n) {
+  const int lane = threadIdx.x;
+  const int w = w0 + lane;
+  uint32_t m = (w < n_words) ? (bI[w] & bJ[w]) : 0u;
+  const int c = __popc(m);
+  int incl = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  int pos = incl - c;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    m &= m - 1;
+    list[pos++] = w * WORD + b;
+  }
+  if (lane == 31) *list_n = incl;
+}
+
+// Rows owned by thread (ty, tx) of the 16 x 16 thread grid: 4 consecutive
+// rows in each half of the tile, so the operand loads are 16-byte vectors.
+__device__ __forceinline__ int own_row(int t16, int q) { return (q < 4) ? t16 * 4 + q : 64 + t16 * 4 + (q - 4); }
+
+// ----------------------------------------------------------------------------
+// weighted normalized
+
+constexpr int BK = 16;  // branches per pipeline stage
+
+template <typename T>
+__device__ __forceinline__ void load8(const T *row, int t16, T (&x)[8]);
+
+template <>
+__device__ __forceinline__ void load8<float>(const float *row, int t16, float (&x)[8]) {
+  const float4 lo = *reinterpret_cast<const float4 *>(row + t16 * 4);
+  const float4 hi = *reinterpret_cast<const float4 *>(row + 64 + t16 * 4);
+  x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+  x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+template <>
+__device__ __forceinline__ void load8<double>(const double *row, int t16, double (&x)[8]) {
+  const double2 a = *reinterpret_cast<const double2 *>(row + t16 * 4);
+  const double2 b = *reinterpret_cast<const double2 *>(row + t16 * 4 + 2);
+  const double2 c = *reinterpret_cast<const double2 *>(row + 64 + t16 * 4);
+  const double2 d = *reinterpret_cast<const double2 *>(row + 64 + t16 * 4 + 2);
+  x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  x[4] = c.x; x[5] = c.y; x[6] = d.x; x[7] = d.y;
+}
+
+// T = float: FP32 partial sums, added into FP64 every `flush` selected branches.
+// T = double: FP64 throughout.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
+                     int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
+                     const double *__restrict__ S, int32_t flush, OutSpec o,
+                     unsigned long long *__restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
+  int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
+  __shared__ int32_t list_n;
+
+  const WorkItem it = items[blockIdx.x];
+  const StudyDev sd = o.studies[it.study];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
+  const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
+  const int64_t colI = (int64_t)it.tile_i * TILE, colJ = (int64_t)it.tile_j * TILE;
+  constexpr int CPR = TILE * sizeof(T) / 16;  // 16-byte chunks per row
+  constexpr int kEl = 16 / sizeof(T);
+
+  // FP32 form: part (FP32, current chunk) + acc (FP64).  FP64 form: part only.
+  constexpr int AD = (sizeof(T) == 4) ? 8 : 1;
+  double acc[AD][AD];
+  T part[8][8];
+#pragma unroll
+  for (int i = 0; i < AD; ++i)
+#pragma unroll
+    for (int j = 0; j < AD; ++j) acc[i][j] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[i][j] = T(0);
+  int since_flush = 0;
+  unsigned long long nsel = 0;
+
+  auto load_stage = [&](int s, int buf, int n) {
+    for (int c = tid; c < BK * 2 * CPR; c += kThreads) {
+      const int r = c / (2 * CPR);
+      const int side = (c / CPR) & 1;
+      const int q = c % CPR;
+      const int li = s * BK + r;
+      if (li < n) {
+        const int32_t k = list[li];
+        const T *src = vals + (int64_t)k * ldv + (side ? colJ : colI) + q * kEl;
+        T *dst = sbuf + ((int64_t)(buf * BK + r) * 2 + side) * TILE + q * kEl;
+        cp_async16(dst, src);
+      }
+    }
+  };
+  auto flush_part = [&]() {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acc[i][j] += (double)part[i][j];
+          part[i][j] = T(0);
+        }
+    }
+  };
+
+  for (int w0 = 0; w0 < n_words; w0 += kWinWords) {
+    if (tid < 32) build_window(bI, bJ, n_words, w0, list, &list_n);
+    __syncthreads();
+    const int n = list_n;
+    nsel += (unsigned long long)n;
+    const int ns = (n + BK - 1) / BK;
+    if (ns > 0) {
+      load_stage(0, 0, n);
+      cp_commit();
+      for (int s = 0; s < ns; ++s) {
+        if (s + 1 < ns) {
+          load_stage(s + 1, (s + 1) & 1, n);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncthreads();
+        const int rows = min(BK, n - s * BK);
+        const T *base = sbuf + (int64_t)((s & 1) * BK) * 2 * TILE;
+        for (int r = 0; r < rows; ++r) {
+          T a[8], b[8];
+          load8<T>(base + (r * 2 + 0) * TILE, ty, a);
+          load8<T>(base + (r * 2 + 1) * TILE, tx, b);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part[i][j] += (a[i] < b[j] ? a[i] : b[j]);
+        }
+        if constexpr (sizeof(T) == 4) {
+          since_flush += rows;
+          if (since_flush >= flush) {
+            flush_part();
+            since_flush = 0;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  flush_part();
+  if (tid == 0 && counter) atomicAdd(counter, nsel);
+
+  // epilogue: d = (S_i + S_j - 2 M) / (S_i + S_j)
+#pragma unroll
+  for (int qi = 0; qi < 8; ++qi) {
+    const int i = own_row(ty, qi);
+    const int li = (int)(colI + i) - sd.col0;
+    if (li >= sd.n) continue;
+    const double Si = S[colI + i];
+#pragma unroll
+    for (int qj = 0; qj < 8; ++qj) {
+      const int j = own_row(tx, qj);
+      const int lj = (int)(colJ + j) - sd.col0;
+      if (lj >= sd.n) continue;
+      if (li < lj) {
+        const double den = Si + S[colJ + j];
+        double M;
+        if constexpr (sizeof(T) == 4)
+          M = acc[qi][qj];
+        else
+          M = part[qi][qj];
+        put_pair(o, sd, li, lj, ratio01(den - 2.0 * M, den));
+      } else if (li == lj) {
+        put_diag(o, sd, li);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// unweighted, bit-packed lookup (FP64 sums)
+
+constexpr int BG = 8;                              // groups per stage
+constexpr int kGroupBytes = 256 * 8 + 2 * TILE;    // table + I bytes + J bytes
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_pairs_lookup(const WorkItem *__restrict__ items, const uint8_t *__restrict__ bytes,
+                   int64_t ldb, const double *__restrict__ tables,
+                   const uint32_t *__restrict__ gbits, int32_t g_words,
+                   const double *__restrict__ a, OutSpec o,
+                   unsigned long long *__restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char *sbuf = smem_raw;  // [2][BG][kGroupBytes]
+  int32_t *list = reinterpret_cast<int32_t *>(smem_raw + 2 * BG * kGroupBytes);
+  __shared__ int32_t list_n;
+
+  const WorkItem it = items[blockIdx.x];
+  const StudyDev sd = o.studies[it.study];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const uint32_t *bI = gbits + (int64_t)it.tile_i * g_words;
+  const uint32_t *bJ = gbits + (int64_t)it.tile_j * g_words;
+  const int64_t colI = (int64_t)it.tile_i * TILE, colJ = (int64_t)it.tile_j * TILE;
+  constexpr int kTabChunks = 256 * 8 / 16;  // 128
+  constexpr int kByteChunks = TILE / 16;    // 8
+  constexpr int kChunks = kTabChunks + 2 * kByteChunks;
+
+  double acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+  unsigned long long nsel = 0;
+
+  auto load_stage = [&](int s, int buf, int n) {
+    for (int c = tid; c < BG * kChunks; c += kThreads) {
+      const int r = c / kChunks;
+      const int q = c % kChunks;
+      const int li = s * BG + r;
+      if (li < n) {
+        const int32_t g = list[li];
+        unsigned char *dst = sbuf + (buf * BG + r) * kGroupBytes;
+        const void *src;
+        if (q < kTabChunks) {
+          src = tables + (int64_t)g * 256 + q * 2;
+          dst += q * 16;
+        } else if (q < kTabChunks + kByteChunks) {
+          src = bytes + (int64_t)g * ldb + colI + (q - kTabChunks) * 16;
+          dst += 2048 + (q - kTabChunks) * 16;
+        } else {
+          src = bytes + (int64_t)g * ldb + colJ + (q - kTabChunks - kByteChunks) * 16;
+          dst += 2048 + TILE + (q - kTabChunks - kByteChunks) * 16;
+        }
+        cp_async16(dst, src);
+      }
+    }
+  };
+
+  for (int w0 = 0; w0 < g_words; w0 += kWinWords) {
+    if (tid < 32) build_window(bI, bJ, g_words, w0, list, &list_n);
+    __syncthreads();
+    const int n = list_n;
+    nsel += (unsigned long long)n;
+    const int ns = (n + BG - 1) / BG;
+    if (ns > 0) {
+      load_stage(0, 0, n);
+      cp_commit();
+      for (int s = 0; s < ns; ++s) {
+        if (s + 1 < ns) {
+          load_stage(s + 1, (s + 1) & 1, n);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncthreads();
+        const int rows = min(BG, n - s * BG);
+        for (int r = 0; r < rows; ++r) {
+          const unsigned char *grp = sbuf + ((s & 1) * BG + r) * kGroupBytes;
+          const double *T = reinterpret_cast<const double *>(grp);
+          const uint32_t xi0 = *reinterpret_cast<const uint32_t *>(grp + 2048 + ty * 4);
+          const uint32_t xi1 = *reinterpret_cast<const uint32_t *>(grp + 2048 + 64 + ty * 4);
+          const uint32_t xj0 = *reinterpret_cast<const uint32_t *>(grp + 2048 + TILE + tx * 4);
+          const uint32_t xj1 = *reinterpret_cast<const uint32_t *>(grp + 2048 + TILE + 64 + tx * 4);
+#pragma unroll
+          for (int qj = 0; qj < 8; ++qj) {
+            const uint32_t xj = (qj < 4) ? xj0 : xj1;
+            const uint32_t rep = ((xj >> (8 * (qj & 3))) & 0xffu) * 0x01010101u;
+            const uint32_t m0 = xi0 & rep, m1 = xi1 & rep;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[q][qj] += T[(m0 >> (8 * q)) & 0xffu];
+              acc[4 + q][qj] += T[(m1 >> (8 * q)) & 0xffu];
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && counter) atomicAdd(counter, nsel);
+
+  // epilogue: d = (a_i + a_j - 2 G) / (a_i + a_j - G)
+#pragma unroll
+  for (int qi = 0; qi < 8; ++qi) {
+    const int i = own_row(ty, qi);
+    const int li = (int)(colI + i) - sd.col0;
+    if (li >= sd.n) continue;
+    const double ai = a[colI + i];
+#pragma unroll
+    for (int qj = 0; qj < 8; ++qj) {
+      const int j = own_row(tx, qj);
+      const int lj = (int)(colJ + j) - sd.col0;
+      if (lj >= sd.n) continue;
+      if (li < lj) {
+        const double A = ai + a[colJ + j];
+        const double G = acc[qi][qj];
+        put_pair(o, sd, li, lj, ratio01(A - 2.0 * G, A - G));
+      } else if (li == lj) {
+        put_diag(o, sd, li);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
+                   const double *S, const WorkItem *items, int32_t n_items, const OutSpec &o) {
+  if (n_items <= 0) return UNIFRAC_OK;
+  const int32_t n_words = ctx->K_pad / WORD;
+  const size_t elem = f64 ? sizeof(double) : sizeof(float);
+  const size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
+  cudaError_t e;
+  if (f64) {
+    e = cudaFuncSetAttribute(k_pairs_weighted<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
+    k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
+        items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, S, 0, o,
+        ctx->d_counter);
+  } else {
+    e = cudaFuncSetAttribute(k_pairs_weighted<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
+    k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
+        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, S, ctx->opt_flush,
+        o, ctx->d_counter);
+  }
+  ctx->stat_launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted pair kernel");
+  return UNIFRAC_OK;
+}
+
+int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
+                 const uint32_t *gbits, const double *a, const WorkItem *items, int32_t n_items,
+                 const OutSpec &o) {
+  if (n_items <= 0) return UNIFRAC_OK;
+  const int32_t G = ctx->K_pad / 8;
+  const int32_t g_words = (G + WORD - 1) / WORD;
+  const size_t smem = 2 * BG * kGroupBytes + sizeof(int32_t) * kWinWords * WORD;
+  cudaError_t e = cudaFuncSetAttribute(k_pairs_lookup,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lookup kernel attribute");
+  k_pairs_lookup<<<n_items, kThreads, smem, ctx->stream>>>(items, bytes, ctx->n_cols, tables,
+                                                           gbits, g_words, a, o, ctx->d_counter);
+  ctx->stat_launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lookup pair kernel");
+  return UNIFRAC_OK;
+}
+
+}  // namespace ufb

@@ -1,0 +1,155 @@
+// Internal declarations of the unifrac_b300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "unifrac_b300.h"
+
+namespace ufb {
+
+// Samples per pair tile and per column tile of the embedding.  Every study's
+// columns start on a multiple of TILE so that no tile straddles two studies.
+constexpr int TILE = 128;
+// Branches per 32-bit word of the (tile, branch) nonzero bitmaps.
+constexpr int WORD = 32;
+
+// One 128 x 128 block of sample pairs, I-tile <= J-tile, both in one study.
+struct WorkItem {
+  int32_t tile_i;  // global column tile of the rows
+  int32_t tile_j;  // global column tile of the columns
+  int32_t study;
+  int32_t pad;
+};
+
+// Where a study's samples live in the embedding and its block in `out`.
+struct StudyDev {
+  int64_t out_off;  // element offset of the study's output block
+  int32_t n;        // samples
+  int32_t col0;     // first embedding column (multiple of TILE)
+};
+
+// Epilogue parameters shared by every pair kernel.
+struct OutSpec {
+  void *out;
+  const StudyDev *studies;
+  int32_t layout;  // enum unifrac_layout
+  int32_t s0, s1;  // stripe range [s0, s1)
+  int32_t is_f64;
+};
+
+// Device buffers that only grow; released by the context.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace ufb
+
+struct unifrac_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  std::string last_error;
+
+  // ---- problem shape
+  int32_t n_nodes = 0, n_features = 0, n_samples = 0, n_studies = 1;
+  int64_t nnz = 0;
+  std::vector<int32_t> study_off;   // [S+1] sample offsets
+  std::vector<int32_t> study_col0;  // [S] first embedding column
+  int32_t n_cols = 0;               // embedding columns (multiple of TILE)
+  int32_t n_tiles = 0;              // n_cols / TILE
+  std::vector<int32_t> col_of_sample;  // [N]
+
+  // ---- tree levels (host) and device copies
+  int32_t n_levels = 0;               // levels above the tips (root excluded)
+  std::vector<int32_t> level_ptr;     // [n_levels+1] into d_level_nodes
+  int32_t *d_level_nodes = nullptr;   // internal non-root nodes grouped by level
+  int32_t *d_child_ptr = nullptr;     // [n_nodes+1]
+  int32_t *d_child_idx = nullptr;     // [n_nodes-1]
+
+  // ---- table on the device (rows = features that sit on a tip, non-empty)
+  int32_t n_frows = 0;
+  int32_t *d_frow_tip = nullptr;      // [n_frows] tip node of the row
+  int64_t *d_frow_ptr = nullptr;      // [n_frows+1]
+  int32_t *d_fent_col = nullptr;      // [nnz'] embedding column (sorted per row)
+  uint32_t *d_fent_cnt = nullptr;     // [nnz'] count (> 0)
+  double *d_inv_total = nullptr;      // [n_cols] 1 / C_i (0 for empty or padding)
+  // column-sorted copy of the table for the per-sample weighted denominators
+  int64_t *d_col_ptr = nullptr;       // [n_cols+1]
+  uint32_t *d_col_cnt = nullptr;      // [nnz'] count
+  double *d_col_depth = nullptr;      // [nnz'] root-to-tip length of the entry's tip
+
+  // ---- kept branches (postorder ids), ordered by presence count descending
+  int32_t K = 0;                      // kept branches
+  int32_t K_pad = 0;                  // K rounded up to 64
+  int32_t *d_perm = nullptr;          // [K_pad] node of each position (-1 padding)
+  double *d_len_perm = nullptr;       // [K_pad] FP64 length (0 padding)
+  uint8_t *d_digits = nullptr;        // [3][K_pad] base-256 digits of len / sigma
+  double tc_scale = 0.0;              // sigma * 2^-24
+  std::vector<int64_t> nb;            // presence count per node (all studies)
+
+  // ---- statistics
+  double stat_pair_branch = 0, stat_useful = 0;
+  double stat_launches = 0, stat_tile_pairs = 0;
+  unsigned long long *d_counter = nullptr;  // [4] device counters
+  double sel_unit = 1.0;                    // branches per counted selection unit
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool ev_valid = false;
+  // pair-kernel events of the last run of each variant
+  cudaEvent_t ev_pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool ev_pair_valid[2] = {false, false};
+
+  // ---- options
+  int opt_uw_kernel = 0;
+  int opt_flush = 256;
+  int opt_persistent = -1;  // -1 auto
+  int opt_ctas_per_sm = 1;
+  int opt_use_graph = 0;
+
+  // ---- work buffers (grown on demand)
+  ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables;
+  size_t device_bytes = 0;
+};
+
+namespace ufb {
+
+int fail(unifrac_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(unifrac_ctx *ctx, cudaError_t e, const char *what);
+int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes);
+
+// embedding (K1) ------------------------------------------------------------
+// Fills cnt[node][col] (u32 counts below each branch) and flag[node][tile]
+// (1 if any column of the tile is non-zero) for every non-root node.
+int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
+
+// packing ---------------------------------------------------------------------
+// Branch-major values v[k][col] = len_k * cnt / C_col (float or double), the
+// (tile, k) nonzero bitmaps, and per-column sums S_col = sum_k v[k][col] (FP64).
+int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
+                  bool f64, void *vals, uint32_t *bits, double *S);
+// Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
+// [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
+int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
+                uint8_t *bytes, double *tables, uint32_t *gbits, double *a);
+// Sample-major BF16 operands for the tensor-core Gram: X[col][k] in {0,1} and
+// three digit planes D_p[col][k] = digit_p(k) * X[col][k]; K-tile bitmaps;
+// a_col = tc_scale * sum_k q_k p[k][col] (exact).
+int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
+            uint16_t *X, uint16_t *D, uint32_t *kbits, double *a);
+
+// pair kernels ------------------------------------------------------------
+int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
+                   const uint32_t *bits, const double *S, const WorkItem *items,
+                   int32_t n_items, const OutSpec &o);
+int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
+                 const uint32_t *gbits, const double *a, const WorkItem *items,
+                 int32_t n_items, const OutSpec &o);
+int pairs_tc(unifrac_ctx *ctx, const uint16_t *X, const uint16_t *D,
+             const uint32_t *kbits, const double *a, const WorkItem *items,
+             int32_t n_items, const OutSpec &o);
+
+}  // namespace ufb

@@ -1,0 +1,105 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+that include/unifrac_b300.h declares, and rejects malformed inputs with the
+documented status codes before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2107_05397_b300 import binding as ub
+from paper_2107_05397_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "unifrac_b300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(unifrac_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ub.load()
+    names = declared_functions()
+    assert len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(ub.EXPORTED) <= set(names)
+
+
+def test_strerror_covers_codes():
+    for code in range(0, -10, -1):
+        s = ub.unifrac_strerror(code)
+        assert s and s != "unknown status"
+    assert ub.unifrac_strerror(-99) == "unknown status"
+
+
+def _tiny():
+    tree = synth.Tree(parent=np.array([2, 2, 4, 4, -1], np.int32),
+                      length=np.array([1.0, 2.0, 0.5, 1.5, 0.0]))
+    table = synth.dense_to_table(np.array([[1, 0, 3], [2, 1, 0], [0, 4, 1]]),
+                                 np.array([0, 1, 3], np.int32))
+    return tree, table
+
+
+def _create(tree, table, **kw):
+    args = dict(parent=tree.parent, length=tree.length, feature_node=table.feature_node,
+                indptr=table.indptr, indices=table.indices, counts=table.counts,
+                n_samples=table.n_samples, study_offsets=table.study_offsets, stream=0)
+    args.update(kw)
+    return ub.unifrac_create(**args)
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda t, b: dict(parent=np.array([2, 0, 4, 4, -1], np.int32)), -2),   # not postorder
+    (lambda t, b: dict(parent=np.array([2, 2, 4, 4, 3], np.int32)), -2),    # root has a parent
+    (lambda t, b: dict(length=np.array([1.0, -2.0, 0.5, 1.5, 0.0])), -2),   # negative length
+    (lambda t, b: dict(length=np.array([1.0, np.nan, 0.5, 1.5, 0.0])), -2), # NaN length
+    (lambda t, b: dict(feature_node=np.array([0, 2, 3], np.int32)), -2),    # internal node
+    (lambda t, b: dict(feature_node=np.array([0, 0, 3], np.int32)), -3),    # two features on a tip
+    (lambda t, b: dict(feature_node=np.array([0, 1, 7], np.int32)), -2),    # out of range
+    (lambda t, b: dict(indices=np.where(b.indices == 2, 5, b.indices).astype(np.int32)), -3),
+    (lambda t, b: dict(counts=np.where(np.arange(b.nnz) == 1, -4, b.counts).astype(np.int32)), -3),
+    (lambda t, b: dict(study_offsets=np.array([0, 2, 1, 3], np.int32)), -1),
+    (lambda t, b: dict(study_offsets=np.array([0, 2], np.int32)), -1),
+])
+def test_create_rejects_malformed_inputs(mutate, code):
+    tree, table = _tiny()
+    with pytest.raises(ub.UniFracError) as ei:
+        _create(tree, table, **mutate(tree, table))
+    assert ei.value.status == code
+
+
+def test_create_rejects_duplicate_entries():
+    tree, table = _tiny()
+    indptr = np.array([0, 3, 5, 7], np.int64)
+    indices = np.array([0, 0, 2, 0, 1, 1, 2], np.int32)
+    counts = np.ones(7, np.int32)
+    with pytest.raises(ub.UniFracError) as ei:
+        _create(tree, table, indptr=indptr, indices=indices, counts=counts)
+    assert ei.value.status == -3
+
+
+def test_create_rejects_huge_sample_totals():
+    tree, _ = _tiny()
+    table = synth.dense_to_table(np.array([[1, 1, 3], [2, 1, 0], [0, 4, 1]]),
+                                 np.array([0, 1, 3], np.int32))
+    counts = np.full(table.nnz, 2**31 - 1, np.int32)
+    with pytest.raises(ub.UniFracError) as ei:
+        _create(tree, table, counts=counts)
+    assert ei.value.status == -3
+
+
+def test_null_pointers_rejected():
+    lib = ub.load()
+    out = ctypes.c_void_p()
+    assert lib.unifrac_create(5, None, None, 0, None, 0, None, None, None, 1, None, None,
+                              ctypes.byref(out)) == -1
+    assert lib.unifrac_run(None, 0, 0, 0, -1, 0, None, 0) == -1
+    lib.unifrac_destroy(None)
+    v = ctypes.c_double()
+    assert lib.unifrac_get_stat(None, 0, ctypes.byref(v)) == -1
+    assert lib.unifrac_set_option(None, 0, 0) == -1

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (max abs over every compared element): 1e-12 in FP64 mode and
+2e-6 in mixed mode, the bounds the library documents for its two precisions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05397_b300 import binding as ub
+from paper_2107_05397_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ub.FP64: 1e-12, ub.MIXED: 2e-6}
+VARIANTS = [ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED]
+PRECISIONS = [ub.FP64, ub.MIXED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ub.load()
+
+
+def run(tree, table, variant, precision, layout=ub.OUT_FULL, s0=0, s1=-1, host=False,
+        options=None):
+    import torch
+    with ub.Context(tree, table) as ctx:
+        for k, v in (options or {}).items():
+            ctx.set_option(k, v)
+        if host:
+            nbytes = ctx.output_bytes(precision, layout, s0, s1)
+            out = np.zeros(nbytes // (8 if precision == ub.FP64 else 4),
+                           np.float64 if precision == ub.FP64 else np.float32)
+            ctx.run(variant, precision, layout, s0, s1, out=out)
+            return out.astype(np.float64)
+        out = ctx.run(variant, precision, layout, s0, s1)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64)
+
+
+def condensed_to_full(c, n):
+    m = np.zeros((n, n))
+    iu = np.triu_indices(n, 1)
+    m[iu] = c
+    return m + m.T
+
+
+def check_full(got, ref, precision):
+    err = np.max(np.abs(got - ref)) if ref.size else 0.0
+    assert err <= TOL[precision], f"max abs err {err:.3e}"
+    return err
+
+
+# ------------------------------------------------------------------ small workload
+
+@pytest.fixture(scope="module")
+def small():
+    w = synth.make_workload("tips1024_samples256")
+    ref = {v: oracle.unifrac_full(w.tree, w.table, v) for v in VARIANTS}
+    return w, ref
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_workload_full_matrix(small, variant, precision):
+    w, ref = small
+    N = w.table.n_samples
+    got = run(w.tree, w.table, variant, precision).reshape(N, N)
+    check_full(got, ref[variant], precision)
+    assert np.all(np.diag(got) == 0)
+    np.testing.assert_array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_workload_condensed_and_host_output(small, variant, precision):
+    w, ref = small
+    N = w.table.n_samples
+    dev = run(w.tree, w.table, variant, precision, ub.OUT_CONDENSED)
+    host = run(w.tree, w.table, variant, precision, ub.OUT_CONDENSED, host=True)
+    np.testing.assert_array_equal(dev, host)
+    check_full(condensed_to_full(dev, N), ref[variant], precision)
+
+
+# ------------------------------------------------------------------ ragged shapes
+
+CASES = [
+    # (seed, tips, samples, general tree, empty samples)
+    (1, 6, 1, False, 0),
+    (2, 6, 2, False, 0),
+    (3, 9, 3, True, 0),
+    (4, 40, 127, False, 3),
+    (5, 40, 128, True, 0),
+    (6, 64, 129, False, 2),
+    (7, 300, 300, True, 5),
+    (8, 200, 257, False, 0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"N{c[2]}{'g' if c[3] else ''}" for c in CASES])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ragged_random_cases(case, variant, precision):
+    seed, tips, N, general, empty = case
+    rng = np.random.default_rng(seed)
+    tree, table = synth.random_case(rng, tips, N, density=0.2, general=general,
+                                    empty_samples=empty)
+    if general:  # zero-length branches too
+        tree.length[rng.random(tree.n_nodes) < 0.1] = 0.0
+        tree.length[-1] = 0.0
+    ref = oracle.unifrac_full(tree, table, variant)
+    got = run(tree, table, variant, precision).reshape(N, N)
+    check_full(got, ref, precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_deep_caterpillar_tree(variant, precision):
+    """A caterpillar (every internal node has one tip child): depth = tips."""
+    n_tips = 400
+    parent = []
+    # postorder: tip0, tip1, int(0,1), tip2, int, tip3, int, ...
+    nodes = 2 * n_tips - 1
+    parent = np.full(nodes, -1, np.int32)
+    parent[0] = 2
+    parent[1] = 2
+    cur = 2
+    for t in range(2, n_tips):
+        tip = 2 * t - 1
+        new = 2 * t
+        parent[cur] = new
+        parent[tip] = new
+        cur = new
+    rng = np.random.default_rng(9)
+    length = rng.exponential(0.2, nodes)
+    length[-1] = 0.0
+    tree = synth.Tree(parent=parent, length=length)
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], 150)) < 0.05) * rng.integers(1, 9, (tips.shape[0], 150))
+    table = synth.dense_to_table(dense, tips)
+    ref = oracle.unifrac_full(tree, table, variant)
+    got = run(tree, table, variant, precision).reshape(150, 150)
+    check_full(got, ref, precision)
+
+
+def test_star_tree_disjoint_samples_unweighted_is_one():
+    F, N = 200, 64
+    tree = synth.star_tree(F, 0.25)
+    dense = np.zeros((F, N), np.int64)
+    for i in range(N):  # disjoint feature blocks
+        dense[3 * i:3 * i + 3, i] = i + 1
+    table = synth.dense_to_table(dense, np.arange(F, dtype=np.int32))
+    for p in PRECISIONS:
+        got = run(tree, table, ub.UNWEIGHTED, p).reshape(N, N)
+        off = got[~np.eye(N, dtype=bool)]
+        assert np.all(np.abs(off - 1.0) <= TOL[p])
+
+
+# ------------------------------------------------------------------ layouts / stripes
+
+@pytest.mark.parametrize("N", [130, 131])
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_stripes_layout_and_merge(N, variant, precision):
+    rng = np.random.default_rng(100 + N)
+    tree, table = synth.random_case(rng, 120, N, density=0.15)
+    ref = oracle.unifrac_full(tree, table, variant)
+    nst = N // 2
+    st = run(tree, table, variant, precision, ub.OUT_STRIPES, 0, -1).reshape(nst, N)
+    k = np.arange(N)
+    for s in range(nst):
+        exp = ref[k, (k + s + 1) % N]
+        assert np.max(np.abs(st[s] - exp)) <= TOL[precision]
+    # partial stripe range
+    part = run(tree, table, variant, precision, ub.OUT_STRIPES, 3, 17).reshape(14, N)
+    np.testing.assert_array_equal(part, st[3:17])
+    # condensed runs over disjoint stripe ranges merge into the whole
+    import torch
+    dt = torch.float64 if precision == ub.FP64 else torch.float32
+    with ub.Context(tree, table) as ctx:
+        nb = ctx.output_bytes(precision, ub.OUT_CONDENSED)
+        buf = torch.full((nb // (8 if precision == ub.FP64 else 4),), -7.0, dtype=dt, device="cuda")
+        a = nst // 3
+        ctx.run(variant, precision, ub.OUT_CONDENSED, 0, a, out=buf)
+        touched = buf.cpu().numpy() != -7.0
+        assert 0 < touched.sum() < buf.numel()
+        ctx.run(variant, precision, ub.OUT_CONDENSED, a, nst, out=buf)
+        merged = buf.cpu().numpy().astype(np.float64)
+        whole = ctx.run(variant, precision, ub.OUT_CONDENSED).cpu().numpy().astype(np.float64)
+        np.testing.assert_array_equal(merged, whole)
+        full = torch.full((N * N,), -7.0, dtype=dt, device="cuda")
+        ctx.run(variant, precision, ub.OUT_FULL, 0, a, out=full)
+        ctx.run(variant, precision, ub.OUT_FULL, a, nst, out=full)
+        np.testing.assert_array_equal(condensed_to_full(whole, N),
+                                      full.cpu().numpy().astype(np.float64).reshape(N, N))
+
+
+# ------------------------------------------------------------------ studies
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("layout", [ub.OUT_CONDENSED, ub.OUT_FULL])
+def test_several_studies(variant, precision, layout):
+    rng = np.random.default_rng(55)
+    tree = synth.yule_tree(500, rng, 0.1)
+    sizes = [130, 0, 1, 2, 257, 40]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    N = int(offs[-1])
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], N)) < 0.03) * rng.integers(1, 30, (tips.shape[0], N))
+    table = synth.dense_to_table(dense, tips)
+    table.study_offsets = offs
+    got = run(tree, table, variant, precision, layout)
+    pos = 0
+    for s, n in enumerate(sizes):
+        sub = synth.dense_to_table(dense[:, offs[s]:offs[s + 1]], tips)
+        ref = oracle.unifrac_full(tree, sub, variant) if n else np.zeros((0, 0))
+        if layout == ub.OUT_FULL:
+            blk = got[pos:pos + n * n].reshape(n, n)
+            pos += n * n
+        else:
+            blk = condensed_to_full(got[pos:pos + n * (n - 1) // 2], n)
+            pos += n * (n - 1) // 2
+        check_full(blk, ref, precision)
+    assert pos == got.shape[0]
+
+
+# ------------------------------------------------------------------ full-size workload
+
+@pytest.fixture(scope="module")
+def large():
+    return synth.make_workload("tips32768_samples4096")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_large_workload_sampled_rows(large, variant, precision):
+    """Full condensed run on 4,096 samples; sampled rows against the oracle."""
+    w = large
+    N = w.table.n_samples
+    got = run(w.tree, w.table, variant, precision, ub.OUT_CONDENSED)
+    assert got.shape[0] == N * (N - 1) // 2
+    assert got.min() >= 0.0 and got.max() <= 1.0
+    rows = np.random.default_rng(3).choice(N, size=4, replace=False)
+    ref, _ = oracle.unifrac_rows(w.tree, w.table, variant, rows)
+    for r, i in enumerate(rows):
+        j = np.arange(N)
+        a, b = np.minimum(i, j), np.maximum(i, j)
+        idx = a * N - a * (a + 1) // 2 + (b - a - 1)
+        vals = np.where(i == j, 0.0, got[np.where(i == j, 0, idx)])
+        assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
+
+
+def test_repeat_runs_bit_identical(small):
+    w, _ = small
+    for v in VARIANTS:
+        for p in PRECISIONS:
+            a = run(w.tree, w.table, v, p)
+            b = run(w.tree, w.table, v, p)
+            np.testing.assert_array_equal(a, b)
+
+
+def test_run_argument_errors(small):
+    import torch
+    w, _ = small
+    with ub.Context(w.tree, w.table) as ctx:
+        small_buf = torch.zeros(10, dtype=torch.float32, device="cuda")
+        with pytest.raises(ub.UniFracError) as ei:
+            ctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL, out=small_buf)
+        assert ei.value.status == -5
+        with pytest.raises(ub.UniFracError) as ei:
+            ctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_STRIPES, 5, 3)
+        assert ei.value.status == -4
+        with pytest.raises(ub.UniFracError) as ei:
+            ctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_STRIPES, 0, 10_000)
+        assert ei.value.status == -4
+        with pytest.raises(ub.UniFracError) as ei:
+            ub.unifrac_run(ctx.handle, 7, ub.MIXED, 0, -1, ub.OUT_FULL,
+                           torch.zeros(w.table.n_samples ** 2, device="cuda"))
+        assert ei.value.status == -1
