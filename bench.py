@@ -45,6 +45,9 @@ def parse():
                     help="rows of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--samples", type=int, default=None,
+                    help="truncate the workload to this many samples (profiling runs)")
     return ap.parse_args()
 
 
@@ -220,7 +223,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = synth.make_workload(args.workload)
+    w = synth.make_workload(args.workload, n_samples=args.samples)
     N = w.table.n_samples
     stream = torch.cuda.current_stream()
     ctx = ub.Context(w.tree, w.table, stream=stream)
@@ -241,7 +244,7 @@ def main():
         step()
     barrier()
 
-    step_ms, pair_wn_ms, pair_uw_ms, sel_wn = [], [], [], []
+    step_ms, pair_wn_ms, pair_uw_ms, sel_wn, sel_uw = [], [], [], [], []
     launches = 0
     peaks = measured_peaks()
     with ClockSampler(torch.cuda.current_device()) as clocks:
@@ -258,7 +261,8 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             pair_uw_ms.append(ctx.stat(ub.STAT_PAIR_MS_UNWEIGHTED))
             pair_wn_ms.append(ctx.stat(ub.STAT_PAIR_MS_WEIGHTED))
-            sel_wn.append(ctx.stat(ub.STAT_SELECTED_UPDATES))
+            sel_wn.append(ctx.stat(ub.STAT_SELECTED_WEIGHTED))
+            sel_uw.append(ctx.stat(ub.STAT_SELECTED_UNWEIGHTED))
         barrier()
         t_wall = time.perf_counter() - t_wall0
     clk = clocks.summary()
@@ -287,21 +291,33 @@ def main():
         "work": "2 FP32 ops per selected pair-branch update",
         "dense_equivalent_tflops": 2.0 * pair_branch / (wn_ms / 1e3) / 1e12,
     }
+    # the tensor-core Gram: 3 BF16 digit planes x 2 flops per selected pair-branch
+    uw_ms = float(np.mean(pair_uw_ms))
+    tc_flops = 6.0 * float(np.mean(sel_uw))
+    tc_ach = tc_flops / (uw_ms / 1e3) / 1e12
+    tc_peak = (peaks or {}).get("bf16_tflops", 1766.4)
+    roofline_tc = {"kernel": "k_pairs_tc", "bound": "tensor", "achieved": tc_ach,
+                   "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_ach / tc_peak,
+                   "traffic": recorded_traffic("k_pairs_tc"),
+                   "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                   "work": "3 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+bf16(int digits)+f64 reductions", "data": "synthetic",
-        "config": {"workload": args.workload, "samples": N,
+        "config": {"workload": args.workload if args.samples is None
+                   else f"{args.workload} truncated to {N} samples", "samples": N,
                    "branches_kept": ctx.stat(ub.STAT_BRANCHES_KEPT),
                    "levels": ctx.stat(ub.STAT_LEVELS), "layout": "condensed",
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) before every timed step",
                    "description": w.description},
         "roofline": roofline,
+        "roofline_unweighted_tensor": roofline_tc,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "breakdown_ms": {"pair_unweighted": float(np.mean(pair_uw_ms)),
+        "breakdown_ms": {"pair_unweighted": uw_ms,
                          "pair_weighted": wn_ms},
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
         "wall_s_timed_loop": t_wall,
@@ -327,7 +343,7 @@ def main():
         del out64a, out64b
 
     # end to end through the public API with host buffers
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         host_in = [pin(w.tree.parent), pin(w.tree.length), pin(w.table.feature_node),
                    pin(w.table.indptr), pin(w.table.indices), pin(w.table.counts)]

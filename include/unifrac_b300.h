@@ -190,8 +190,10 @@ enum unifrac_stat {
   UNIFRAC_STAT_DEVICE_BYTES = 9,    /* device memory held by the context */
   UNIFRAC_STAT_PAIR_MS_UNWEIGHTED = 10, /* device time of the pair kernel of the last */
   UNIFRAC_STAT_PAIR_MS_WEIGHTED = 11,   /*   unweighted / weighted run (ms)          */
-  UNIFRAC_STAT_DEVICE_ERROR = 12    /* 0, or the UNIFRAC_E_* code a kernel of the last run
+  UNIFRAC_STAT_DEVICE_ERROR = 12,   /* 0, or the UNIFRAC_E_* code a kernel of the last run
                                        raised (synchronises the context's stream) */
+  UNIFRAC_STAT_SELECTED_UNWEIGHTED = 13, /* UNIFRAC_STAT_SELECTED_UPDATES of the last */
+  UNIFRAC_STAT_SELECTED_WEIGHTED = 14    /*   unweighted / weighted run               */
 };
 int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
 

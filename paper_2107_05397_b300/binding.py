@@ -43,6 +43,8 @@ STAT_DEVICE_BYTES = 9
 STAT_PAIR_MS_UNWEIGHTED = 10
 STAT_PAIR_MS_WEIGHTED = 11
 STAT_DEVICE_ERROR = 12
+STAT_SELECTED_UNWEIGHTED = 13
+STAT_SELECTED_WEIGHTED = 14
 
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",

@@ -341,15 +341,18 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   for (int32_t s = 0; s < n_studies; ++s) {
     touched.clear();
     for (int32_t i = soff[s]; i < soff[s + 1]; ++i) {
+      int64_t reach = 0;
       for (int64_t e = s_ptr[i]; e < s_ptr[i + 1]; ++e) {
         int32_t v = s_tip[e];
         while (v != root && mark[v] != i) {
           mark[v] = i;
           if (nb_study[v] == 0) touched.push_back(v);
           nb_study[v]++;
+          reach++;
           v = parent[v];
         }
       }
+      ctx->max_reach = std::max(ctx->max_reach, reach);
     }
     int64_t B_s = 0;
     for (int32_t v : touched) {
@@ -578,7 +581,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   e = cudaMemcpyAsync(ctx->studies.p, studies.data(), studies.size() * sizeof(StudyDev),
                       cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload studies");
-  e = cudaMemsetAsync(ctx->d_counter, 0, 4 * sizeof(unsigned long long), ctx->stream);
+  e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
   OutSpec o;
   o.out = dst;
@@ -611,6 +614,26 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
     cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
     ctx->sel_unit = 1.0;
     if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, S, d_items, n_items, o))) return rc;
+  } else if (!f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793) {
+    // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while
+    // no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
+    const int32_t n_kt = ctx->K_pad / 64;
+    const int32_t k_words = (n_kt + 31) / 32;
+    const size_t plane = (size_t)ctx->n_cols * ctx->K_pad * 2;
+    if ((rc = grow(ctx, ctx->vals, plane))) return rc;
+    if ((rc = grow(ctx, ctx->vals2, 3 * plane))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
+    if ((rc = grow(ctx, ctx->partial, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    uint16_t *X = static_cast<uint16_t *>(ctx->vals.p);
+    uint16_t *D = static_cast<uint16_t *>(ctx->vals2.p);
+    uint32_t *kbits = static_cast<uint32_t *>(ctx->bits.p);
+    double *a = static_cast<double *>(ctx->persample.p);
+    if ((rc = pack_tc(ctx, cnt, flag, X, D, kbits, a))) return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 64.0;
+    if ((rc = pairs_tc(ctx, X, D, kbits, a, d_items, n_items, o))) return rc;
   } else {
     const int32_t G = ctx->K_pad / 8;
     const int32_t g_words = (G + WORD - 1) / WORD;
@@ -631,6 +654,10 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   }
   cudaEventRecord(ctx->ev[2], ctx->stream);
   cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
+  e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
+                      cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
+  ctx->sel_unit_v[variant] = ctx->sel_unit;
   ctx->ev_valid = true;
   ctx->ev_pair_valid[variant] = true;
 
@@ -732,6 +759,19 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       e = cudaEventElapsedTime(&ms, ctx->ev_pair[v][0], ctx->ev_pair[v][1]);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "elapsed time");
       *value = ms;
+      return UNIFRAC_OK;
+    }
+    case UNIFRAC_STAT_SELECTED_UNWEIGHTED:
+    case UNIFRAC_STAT_SELECTED_WEIGHTED: {
+      const int v = stat == UNIFRAC_STAT_SELECTED_UNWEIGHTED ? 0 : 1;
+      if (!ctx->ev_pair_valid[v]) return fail(ctx, UNIFRAC_E_INVALID_ARG, "no run of that variant");
+      DeviceGuard g(ctx->device);
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+      unsigned long long c = 0;
+      e = cudaMemcpy(&c, ctx->d_counter + 2 + v, sizeof(c), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
+      *value = (double)c * ctx->sel_unit_v[v] * (double)TILE * (double)TILE;
       return UNIFRAC_OK;
     }
     case UNIFRAC_STAT_DEVICE_ERROR: {

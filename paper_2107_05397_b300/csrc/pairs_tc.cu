@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; j < 32; ++j) r0[j] = r1[j] = r2[j] = 0u;
       }
       if (li >= sd.n) continue;
-#pragma unroll 4
+#pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int col = c * 32 + j;
         const int lj = (int)(colJ + col) - sd.col0;

@@ -91,12 +91,14 @@ struct unifrac_ctx {
   uint8_t *d_digits = nullptr;        // [3][K_pad] base-256 digits of len / sigma
   double tc_scale = 0.0;              // sigma * 2^-24
   std::vector<int64_t> nb;            // presence count per node (all studies)
+  int64_t max_reach = 0;              // most branches reached by one sample
 
   // ---- statistics
   double stat_pair_branch = 0, stat_useful = 0;
   double stat_launches = 0, stat_tile_pairs = 0;
   unsigned long long *d_counter = nullptr;  // [4] device counters
   double sel_unit = 1.0;                    // branches per counted selection unit
+  double sel_unit_v[2] = {1.0, 1.0};        // same, last run of each variant
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ev_valid = false;
   // pair-kernel events of the last run of each variant
@@ -148,6 +150,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);
+size_t tc_smem_bytes();
 int pairs_tc(unifrac_ctx *ctx, const uint16_t *X, const uint16_t *D,
              const uint32_t *kbits, const double *a, const WorkItem *items,
              int32_t n_items, const OutSpec &o);

@@ -255,6 +255,17 @@ def test_large_workload_sampled_rows(large, variant, precision):
         assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_unweighted_mixed_kernel_choice(small, kernel):
+    """Both unweighted mixed-precision kernels (tensor-core Gram, bit-packed
+    lookup) agree with the oracle."""
+    w, ref = small
+    N = w.table.n_samples
+    got = run(w.tree, w.table, ub.UNWEIGHTED, ub.MIXED,
+              options={ub.OPT_UNWEIGHTED_MIXED_KERNEL: kernel}).reshape(N, N)
+    check_full(got, ref[ub.UNWEIGHTED], ub.MIXED)
+
+
 def test_repeat_runs_bit_identical(small):
     w, _ = small
     for v in VARIANTS:
