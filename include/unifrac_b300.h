@@ -197,6 +197,44 @@ enum unifrac_stat {
 };
 int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
 
+/*
+ * unifrac_dense_noalloc -- the full N x N FP64 matrix of a small problem,
+ * computed without allocating anything.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (a real-time or
+ * embedded pipeline that reserves all device memory at start-up, a plug-in
+ * running inside an application that owns the memory pool, code that must not
+ * risk the device-wide synchronisation an allocation can cause).
+ * unifrac_create allocates, so those callers use this call instead.
+ *
+ *  variant      enum unifrac_variant.
+ *  n_nodes      nodes of the tree; parent[n_nodes] (int32) and length[n_nodes]
+ *               (FP64) are DEVICE arrays in the postorder form of
+ *               unifrac_create (parent[k] > k, root last; root length ignored).
+ *  n_samples    samples, 0 .. UNIFRAC_NOALLOC_MAX_SAMPLES.
+ *  tip_counts   DEVICE array [n_nodes x n_samples] (node-major, u32): the count
+ *               of each sample on each tip; rows of internal nodes must be 0.
+ *               Each sample total must stay below 2^32.
+ *  out          DEVICE array [n_samples x n_samples] FP64, row-major; receives
+ *               the symmetric matrix with a zero diagonal.
+ *  cuda_stream  stream the two kernels are enqueued on (asynchronous).
+ *
+ * Work space: one fixed device array of UNIFRAC_NOALLOC_MAX_CELLS 32-bit
+ * counts inside the library (4 MB, held by every GPU that loads the library
+ * until the process exits).  n_nodes * n_samples above that, or n_samples above
+ * UNIFRAC_NOALLOC_MAX_SAMPLES, returns UNIFRAC_E_UNSUPPORTED.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) with
+ * that device current; make the first call on each device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and
+ * corrupt each other's results -- serialise them (one stream, or events).
+ * Nothing carries over between calls.  Allocates no device or host memory.
+ */
+#define UNIFRAC_NOALLOC_MAX_CELLS (1u << 20)
+#define UNIFRAC_NOALLOC_MAX_SAMPLES 4096
+int unifrac_dense_noalloc(int variant, int32_t n_nodes, const int32_t *parent,
+                          const double *length, int32_t n_samples,
+                          const uint32_t *tip_counts, double *out,
+                          void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
