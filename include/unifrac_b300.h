@@ -171,7 +171,10 @@ enum unifrac_option {
   UNIFRAC_OPT_PERSISTENT = 2,             /* 0 one CTA per tile pair, 1 persistent
                                               work queue (default for many studies) */
   UNIFRAC_OPT_CTAS_PER_SM = 3,            /* persistent grid = SMs x this, 1..8 */
-  UNIFRAC_OPT_USE_GRAPH = 4               /* 1 = capture the level loop in a CUDA graph */
+  UNIFRAC_OPT_USE_GRAPH = 4,              /* 1 = capture the level loop in a CUDA graph */
+  UNIFRAC_OPT_SPARSE_THRESHOLD = 5        /* weighted mixed kernel: branches present in fewer
+                                              samples than this run through the sparse phase;
+                                              -1 auto (largest study / 8), 0 all dense */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 

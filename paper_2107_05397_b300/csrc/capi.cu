@@ -89,7 +89,7 @@ void free_ctx(unifrac_ctx *ctx) {
     if (p) cudaFree(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
                          &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
-                         &ctx->studies, &ctx->stage,     &ctx->tables};
+                         &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->masks};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &e : ctx->ev)
@@ -374,6 +374,19 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::stable_sort(perm.begin(), perm.end(),
                    [&](int32_t x, int32_t y) { return ctx->nb[x] > ctx->nb[y]; });
   ctx->K = (int32_t)perm.size();
+  ctx->nb_perm.resize(perm.size());
+  for (size_t k = 0; k < perm.size(); ++k) ctx->nb_perm[k] = ctx->nb[perm[k]];
+  for (int32_t s = 0; s < n_studies; ++s)
+    ctx->max_study_n = std::max(ctx->max_study_n, soff[s + 1] - soff[s]);
+  // fixed-point scale of the sparse weighted sums: every pair sum is at most
+  // the deepest tip's depth D, so D * scale < 2^62 keeps u64 sums exact
+  {
+    double dmax = 0.0;
+    for (int32_t f = 0; f < n_features; ++f) dmax = std::max(dmax, depth[feature_node[f]]);
+    int ed = 0;
+    if (dmax > 0.0) std::frexp(dmax, &ed);  // dmax < 2^ed
+    ctx->sp_scale = std::ldexp(1.0f, std::min(100, 62 - ed));
+  }
   ctx->K_pad = std::max<int32_t>(64, (ctx->K + 63) / 64 * 64);
   std::vector<double> len_perm(ctx->K_pad, 0.0);
   for (int32_t k = 0; k < ctx->K; ++k) len_perm[k] = length[perm[k]];
@@ -609,11 +622,31 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
     if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
     double *S = static_cast<double *>(ctx->persample.p);
     uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
-    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, S))) return rc;
+    // dense / sparse split at a multiple of 32 positions (FP32 form only)
+    const int32_t n_words = ctx->K_pad / WORD;
+    int32_t kf_words = n_words;
+    if (!f64 && ctx->opt_sparse_threshold != 0) {
+      const int64_t th = ctx->opt_sparse_threshold > 0
+                             ? ctx->opt_sparse_threshold
+                             : std::max<int64_t>(32, ctx->max_study_n / 8);
+      int32_t kf = 0;
+      while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
+      kf_words = kf / WORD;
+    }
+    uint4 *masks = nullptr;
+    if (kf_words < n_words) {
+      if ((rc = grow(ctx, ctx->masks, (size_t)ctx->n_tiles * ctx->K_pad * sizeof(uint4))))
+        return rc;
+      masks = static_cast<uint4 *>(ctx->masks.p);
+    }
+    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, masks, kf_words * WORD, S)))
+      return rc;
     cudaEventRecord(ctx->ev[1], ctx->stream);
     cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
     ctx->sel_unit = 1.0;
-    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, S, d_items, n_items, o))) return rc;
+    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, masks, kf_words, S, d_items, n_items,
+                             o)))
+      return rc;
   } else if (!f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793) {
     // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while
     // no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
@@ -708,6 +741,10 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
     case UNIFRAC_OPT_USE_GRAPH:
       if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_use_graph = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_SPARSE_THRESHOLD:
+      if (value < -1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_sparse_threshold = value;
       return UNIFRAC_OK;
     default:
       return UNIFRAC_E_INVALID_ARG;

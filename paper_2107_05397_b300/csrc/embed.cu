@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
     int32_t K, const int32_t *__restrict__ perm, const double *__restrict__ len_perm,
     const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
     int32_t n_tiles, const double *__restrict__ inv_total, T *__restrict__ vals,
-    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words) {
+    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words, uint4 *__restrict__ masks,
+    int32_t k_mask0, int32_t k_pad) {
   const int t = blockIdx.x;
   const int k0 = blockIdx.y * KR;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -112,6 +113,14 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
       v.z = L * ((float)c.z * inv[2]);
       v.w = L * ((float)c.w * inv[3]);
       *reinterpret_cast<float4 *>(vals + (int64_t)k * ldv + col) = v;
+      if (masks && k >= k_mask0) {
+        // lane-major row mask: bit l of word q <=> column 4l + q of the tile
+        const uint32_t m0 = __ballot_sync(0xffffffffu, c.x != 0u);
+        const uint32_t m1 = __ballot_sync(0xffffffffu, c.y != 0u);
+        const uint32_t m2 = __ballot_sync(0xffffffffu, c.z != 0u);
+        const uint32_t m3 = __ballot_sync(0xffffffffu, c.w != 0u);
+        if (lane == 0) masks[(int64_t)t * k_pad + k] = make_uint4(m0, m1, m2, m3);
+      }
     }
   } else {
     double inv[4];
@@ -261,7 +270,7 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
 }
 
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bool f64,
-                  void *vals, uint32_t *bits, double *S) {
+                  void *vals, uint32_t *bits, uint4 *masks, int32_t k_mask0, double *S) {
   cudaStream_t st = ctx->stream;
   const int32_t n_words = ctx->K_pad / WORD;
   if (ctx->K > 0 && ctx->n_tiles > 0) {
@@ -269,11 +278,13 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bo
     if (f64)
       k_pack_weighted<double><<<grid, 256, 0, st>>>(
           ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
-          ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words);
+          ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words, nullptr,
+          ctx->K_pad, ctx->K_pad);
     else
       k_pack_weighted<float><<<grid, 256, 0, st>>>(
           ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
-          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words);
+          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words, masks,
+          k_mask0, ctx->K_pad);
     ctx->stat_launches += 1;
   }
   if (ctx->n_cols > 0) {

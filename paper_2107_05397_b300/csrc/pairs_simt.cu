@@ -95,18 +95,80 @@ __device__ __forceinline__ void load8<double>(const double *row, int t16, double
   x[4] = c.x; x[5] = c.y; x[6] = d.x; x[7] = d.y;
 }
 
+// Register micro-tile of min-sums.  FP32: FMNMX per pair and packed two-wide
+// adds (add.f32x2), the min on the ALU pipe, the adds on the FMA pipe.
+// FP64: fmin + add.
+template <typename T>
+struct MinAcc;
+
+template <>
+struct MinAcc<float> {
+  float2 p[8][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[i][j] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void add(const float (&a)[8], const float (&b)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        p[i][j] = __fadd2_rn(p[i][j], make_float2(fminf(a[i], b[2 * j]), fminf(a[i], b[2 * j + 1])));
+  }
+  __device__ __forceinline__ double get(int i, int j) const {
+    return (j & 1) ? (double)p[i][j >> 1].y : (double)p[i][j >> 1].x;
+  }
+};
+
+template <>
+struct MinAcc<double> {
+  double p[8][8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) p[i][j] = 0.0;
+  }
+  __device__ __forceinline__ void add(const double (&a)[8], const double (&b)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) p[i][j] += fmin(a[i], b[j]);
+  }
+  __device__ __forceinline__ double get(int i, int j) const { return p[i][j]; }
+};
+
 // T = float: FP32 partial sums, added into FP64 every `flush` selected branches.
 // T = double: FP64 throughout.
+//
+// Hybrid split (FP32 form): positions [0, 32*kf_words) are the frequently
+// present branches and run through the dense register tile above; the rest,
+// present in few samples, run sparsely: for each such branch selected for the
+// tile pair, the warp enumerates the non-zero rows of each tile from 128-bit
+// row masks and adds min(v_bi, v_bj) for exactly those pairs into a 128 x 128
+// shared-memory accumulator of 64-bit integers (value * 2^s, exact for every
+// term >= 2^(24-s), so the sum is exact and independent of atomic order).
+constexpr int kSparseBytes = TILE * TILE * 8 + 8 * 2 * TILE * 5;
+constexpr int kSB = 8;  // sparse branches a warp keeps in flight
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
-                     const double *__restrict__ S, int32_t flush, OutSpec o,
-                     unsigned long long *__restrict__ counter) {
+                     int32_t kf_words, const uint4 *__restrict__ masks, int32_t k_pad,
+                     float sp_scale, double sp_inv, const double *__restrict__ S,
+                     int32_t flush, OutSpec o, unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
   int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
+  unsigned long long *sacc = reinterpret_cast<unsigned long long *>(
+      smem_raw + sizeof(T) * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD);
+  float *sw_val = reinterpret_cast<float *>(sacc + TILE * TILE);       // [8 warps][2][TILE]
+  uint8_t *sw_row = reinterpret_cast<uint8_t *>(sw_val + 8 * 2 * TILE);  // [8 warps][2][TILE]
   __shared__ int32_t list_n;
+  const bool sparse = (sizeof(T) == 4) && kf_words < n_words;
 
   const WorkItem it = items[blockIdx.x];
   const StudyDev sd = o.studies[it.study];
@@ -117,18 +179,114 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int CPR = TILE * sizeof(T) / 16;  // 16-byte chunks per row
   constexpr int kEl = 16 / sizeof(T);
 
+  // ---------------------------------------------------------------- sparse phase
+  // (first, while the dense accumulators are not yet live).  Each warp takes
+  // kSB selected branches at a time: lanes 0..2*kSB-1 fetch the row masks of
+  // the batch, then every lane fetches its 4 values of each (branch, tile) it
+  // has a row in -- all loads of a batch are independent and in flight
+  // together -- and the warp walks the batch's pairs.
+  if (sparse) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int x = tid; x < TILE * TILE; x += kThreads) sacc[x] = 0ull;
+    float *myv = sw_val + warp * 2 * TILE;
+    uint8_t *myr = sw_row + warp * 2 * TILE;
+    const float *fv = reinterpret_cast<const float *>(vals);
+    __syncthreads();
+    for (int w0 = kf_words; w0 < n_words; w0 += kWinWords) {
+      if (tid < 32) build_window(bI, bJ, n_words, w0, list, &list_n);
+      __syncthreads();
+      const int n = list_n;
+      for (int base = warp * kSB; base < n; base += (kThreads / 32) * kSB) {
+        uint4 mk = make_uint4(0u, 0u, 0u, 0u);
+        {
+          const int e = base + (lane >> 1);
+          if (lane < 2 * kSB && e < n)
+            mk = masks[(int64_t)((lane & 1) ? it.tile_j : it.tile_i) * k_pad + list[e]];
+        }
+        uint32_t mine[kSB][2];
+        float4 vv[kSB][2];
+#pragma unroll
+        for (int q = 0; q < kSB; ++q) {
+          const int e = base + q;
+          const int32_t k = (e < n) ? list[e] : 0;
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const int src = 2 * q + side;
+            const uint32_t m0 = __shfl_sync(0xffffffffu, mk.x, src);
+            const uint32_t m1 = __shfl_sync(0xffffffffu, mk.y, src);
+            const uint32_t m2 = __shfl_sync(0xffffffffu, mk.z, src);
+            const uint32_t m3 = __shfl_sync(0xffffffffu, mk.w, src);
+            // lane-major masks: bit l of word w <=> row 4l + w of the tile
+            const uint32_t b = ((m0 >> lane) & 1u) | (((m1 >> lane) & 1u) << 1) |
+                               (((m2 >> lane) & 1u) << 2) | (((m3 >> lane) & 1u) << 3);
+            mine[q][side] = b;
+            vv[q][side] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (b)
+              vv[q][side] = *reinterpret_cast<const float4 *>(
+                  fv + (int64_t)k * ldv + (int64_t)(side ? it.tile_j : it.tile_i) * TILE +
+                  4 * lane);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kSB; ++q) {
+          if (base + q >= n) break;
+          int cnt[2];
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const uint32_t b = mine[q][side];
+            const int c = __popc(b);
+            int incl = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, incl, off);
+              if (lane >= off) incl += y;
+            }
+            cnt[side] = __shfl_sync(0xffffffffu, incl, 31);
+            int pos = incl - c;
+            const float v4[4] = {vv[q][side].x, vv[q][side].y, vv[q][side].z, vv[q][side].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+              if ((b >> w) & 1u) {
+                myv[side * TILE + pos] = v4[w];
+                myr[side * TILE + pos] = (uint8_t)(4 * lane + w);
+                ++pos;
+              }
+          }
+          __syncwarp();
+          const int nI = cnt[0], nJ = cnt[1];
+          const int total = nI * nJ;
+          if (total > 0) {
+            // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
+            int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
+            const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
+            for (int p = lane; p < total; p += 32) {
+              const float mv = fminf(myv[a], myv[TILE + bb]);
+              const unsigned long long qv = __float2ull_rn(mv * sp_scale);
+              atomicAdd(&sacc[(int)myr[a] * TILE + (int)myr[TILE + bb]], qv);
+              a += da;
+              bb += db;
+              if (bb >= nJ) {
+                bb -= nJ;
+                ++a;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+    }
+  }
+
   // FP32 form: part (FP32, current chunk) + acc (FP64).  FP64 form: part only.
   constexpr int AD = (sizeof(T) == 4) ? 8 : 1;
   double acc[AD][AD];
-  T part[8][8];
+  MinAcc<T> part;
 #pragma unroll
   for (int i = 0; i < AD; ++i)
 #pragma unroll
     for (int j = 0; j < AD; ++j) acc[i][j] = 0.0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) part[i][j] = T(0);
+  part.zero();
   int since_flush = 0;
   unsigned long long nsel = 0;
 
@@ -151,15 +309,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          acc[i][j] += (double)part[i][j];
-          part[i][j] = T(0);
-        }
+        for (int j = 0; j < 8; ++j) acc[i][j] += part.get(i, j);
+      part.zero();
     }
   };
 
-  for (int w0 = 0; w0 < n_words; w0 += kWinWords) {
-    if (tid < 32) build_window(bI, bJ, n_words, w0, list, &list_n);
+  for (int w0 = 0; w0 < kf_words; w0 += kWinWords) {
+    if (tid < 32) build_window(bI, bJ, kf_words, w0, list, &list_n);
     __syncthreads();
     const int n = list_n;
     nsel += (unsigned long long)n;
@@ -182,10 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           T a[8], b[8];
           load8<T>(base + (r * 2 + 0) * TILE, ty, a);
           load8<T>(base + (r * 2 + 1) * TILE, tx, b);
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) part[i][j] += (a[i] < b[j] ? a[i] : b[j]);
+          part.add(a, b);
         }
         if constexpr (sizeof(T) == 4) {
           since_flush += rows;
@@ -200,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
   }
   flush_part();
+
   if (tid == 0 && counter) atomicAdd(counter, nsel);
 
   // epilogue: d = (S_i + S_j - 2 M) / (S_i + S_j)
@@ -217,10 +371,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (li < lj) {
         const double den = Si + S[colJ + j];
         double M;
-        if constexpr (sizeof(T) == 4)
+        if constexpr (sizeof(T) == 4) {
           M = acc[qi][qj];
-        else
-          M = part[qi][qj];
+          if (sparse) M += (double)sacc[i * TILE + j] * sp_inv;
+        } else {
+          M = part.get(qi, qj);
+        }
         put_pair(o, sd, li, lj, ratio01(den - 2.0 * M, den));
       } else if (li == lj) {
         put_diag(o, sd, li);
@@ -358,26 +514,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
-                   const double *S, const WorkItem *items, int32_t n_items, const OutSpec &o) {
+                   const uint4 *masks, int32_t kf_words, const double *S, const WorkItem *items,
+                   int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const size_t elem = f64 ? sizeof(double) : sizeof(float);
-  const size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
+  size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
   cudaError_t e;
   if (f64) {
     e = cudaFuncSetAttribute(k_pairs_weighted<double>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, S, 0, o,
-        ctx->d_counter);
+        items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
+        ctx->K_pad, 1.0f, 1.0, S, 0, o, ctx->d_counter);
   } else {
+    if (kf_words < n_words) smem += kSparseBytes;
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, S, ctx->opt_flush,
-        o, ctx->d_counter);
+        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words, masks,
+        ctx->K_pad, ctx->sp_scale, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
+        ctx->d_counter);
   }
   ctx->stat_launches += 1;
   e = cudaGetLastError();

@@ -91,6 +91,8 @@ struct unifrac_ctx {
   uint8_t *d_digits = nullptr;        // [3][K_pad] base-256 digits of len / sigma
   double tc_scale = 0.0;              // sigma * 2^-24
   std::vector<int64_t> nb;            // presence count per node (all studies)
+  std::vector<int64_t> nb_perm;       // presence count of each kept position
+  int32_t max_study_n = 0;            // largest study
   int64_t max_reach = 0;              // most branches reached by one sample
 
   // ---- statistics
@@ -111,9 +113,12 @@ struct unifrac_ctx {
   int opt_persistent = -1;  // -1 auto
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
+  int64_t opt_sparse_threshold = -1;  // presence count below which a branch runs sparse
+  float sp_scale = 1.0f;              // fixed-point scale of the sparse sums (power of 2)
 
   // ---- work buffers (grown on demand)
-  ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables;
+  ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
+      masks;
   size_t device_bytes = 0;
 };
 
@@ -131,8 +136,10 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 // packing ---------------------------------------------------------------------
 // Branch-major values v[k][col] = len_k * cnt / C_col (float or double), the
 // (tile, k) nonzero bitmaps, and per-column sums S_col = sum_k v[k][col] (FP64).
+// FP32 form also writes 128-bit row masks [n_tiles][K_pad] for positions >= k_mask0.
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                  bool f64, void *vals, uint32_t *bits, double *S);
+                  bool f64, void *vals, uint32_t *bits, uint4 *masks, int32_t k_mask0,
+                  double *S);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
@@ -145,8 +152,9 @@ int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
 
 // pair kernels ------------------------------------------------------------
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
-                   const uint32_t *bits, const double *S, const WorkItem *items,
-                   int32_t n_items, const OutSpec &o);
+                   const uint32_t *bits, const uint4 *masks, int32_t kf_words,
+                   const double *S, const WorkItem *items, int32_t n_items,
+                   const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);

@@ -255,6 +255,25 @@ def test_large_workload_sampled_rows(large, variant, precision):
         assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
 
 
+@pytest.mark.parametrize("threshold", [0, 1, 40, 10**9])
+@pytest.mark.parametrize("case", [0, 1])
+def test_weighted_dense_sparse_split(small, threshold, case):
+    """Every dense / sparse split of the weighted mixed kernel (all dense, a
+    split, all sparse) agrees with the oracle."""
+    if case == 0:
+        w, ref = small
+        tree, table, r = w.tree, w.table, ref[ub.WEIGHTED_NORMALIZED]
+    else:
+        rng = np.random.default_rng(77)
+        tree, table = synth.random_case(rng, 300, 261, density=0.05, general=True,
+                                        empty_samples=2)
+        r = oracle.unifrac_full(tree, table, ub.WEIGHTED_NORMALIZED)
+    N = table.n_samples
+    got = run(tree, table, ub.WEIGHTED_NORMALIZED, ub.MIXED,
+              options={ub.OPT_SPARSE_THRESHOLD: threshold}).reshape(N, N)
+    check_full(got, r, ub.MIXED)
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_unweighted_mixed_kernel_choice(small, kernel):
     """Both unweighted mixed-precision kernels (tensor-core Gram, bit-packed
