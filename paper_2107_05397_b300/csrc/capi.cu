@@ -379,13 +379,14 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   for (int32_t s = 0; s < n_studies; ++s)
     ctx->max_study_n = std::max(ctx->max_study_n, soff[s + 1] - soff[s]);
   // fixed-point scale of the sparse weighted sums: every pair sum is at most
-  // the deepest tip's depth D, so D * scale < 2^62 keeps u64 sums exact
+  // the deepest tip's depth D < 2^ed, so scale = 2^(30 - ed) keeps each u32
+  // sum (plus at most half a unit per term) below 2^31
   {
     double dmax = 0.0;
     for (int32_t f = 0; f < n_features; ++f) dmax = std::max(dmax, depth[feature_node[f]]);
     int ed = 0;
     if (dmax > 0.0) std::frexp(dmax, &ed);  // dmax < 2^ed
-    ctx->sp_scale = std::ldexp(1.0f, std::min(100, 62 - ed));
+    ctx->sp_scale = std::ldexp(1.0f, std::max(-100, std::min(100, 30 - ed)));
   }
   ctx->K_pad = std::max<int32_t>(64, (ctx->K + 63) / 64 * 64);
   std::vector<double> len_perm(ctx->K_pad, 0.0);

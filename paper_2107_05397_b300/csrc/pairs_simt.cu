@@ -148,9 +148,11 @@ struct MinAcc<double> {
 // present in few samples, run sparsely: for each such branch selected for the
 // tile pair, the warp enumerates the non-zero rows of each tile from 128-bit
 // row masks and adds min(v_bi, v_bj) for exactly those pairs into a 128 x 128
-// shared-memory accumulator of 64-bit integers (value * 2^s, exact for every
-// term >= 2^(24-s), so the sum is exact and independent of atomic order).
-constexpr int kSparseBytes = TILE * TILE * 8 + 8 * 2 * TILE * 5;
+// shared-memory accumulator of 32-bit fixed-point integers (round(value * 2^s),
+// 2^s the largest power of two that keeps every pair sum below 2^31: integer
+// sums make the result independent of the order of the atomics; the rounding
+// of each term is at most 2^-(s+1)).
+constexpr int kSparseBytes = TILE * TILE * 4 + 8 * 2 * TILE * 5;
 constexpr int kSB = 8;  // sparse branches a warp keeps in flight
 
 template <typename T>
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
   int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
-  unsigned long long *sacc = reinterpret_cast<unsigned long long *>(
+  uint32_t *sacc = reinterpret_cast<uint32_t *>(
       smem_raw + sizeof(T) * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD);
   float *sw_val = reinterpret_cast<float *>(sacc + TILE * TILE);       // [8 warps][2][TILE]
   uint8_t *sw_row = reinterpret_cast<uint8_t *>(sw_val + 8 * 2 * TILE);  // [8 warps][2][TILE]
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // together -- and the warp walks the batch's pairs.
   if (sparse) {
     const int warp = tid >> 5, lane = tid & 31;
-    for (int x = tid; x < TILE * TILE; x += kThreads) sacc[x] = 0ull;
+    for (int x = tid; x < TILE * TILE; x += kThreads) sacc[x] = 0u;
     float *myv = sw_val + warp * 2 * TILE;
     uint8_t *myr = sw_row + warp * 2 * TILE;
     const float *fv = reinterpret_cast<const float *>(vals);
@@ -231,25 +233,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int q = 0; q < kSB; ++q) {
           if (base + q >= n) break;
           int cnt[2];
+          const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
             const uint32_t b = mine[q][side];
-            const int c = __popc(b);
-            int incl = c;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, incl, off);
-              if (lane >= off) incl += y;
-            }
-            cnt[side] = __shfl_sync(0xffffffffu, incl, 31);
-            int pos = incl - c;
+            // rows ordered by (word w, lane): word-w rows of lower lanes first
+            const uint32_t B0 = __ballot_sync(0xffffffffu, b & 1u);
+            const uint32_t B1 = __ballot_sync(0xffffffffu, (b >> 1) & 1u);
+            const uint32_t B2 = __ballot_sync(0xffffffffu, (b >> 2) & 1u);
+            const uint32_t B3 = __ballot_sync(0xffffffffu, (b >> 3) & 1u);
+            const int c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2), c3 = __popc(B3);
+            cnt[side] = c0 + c1 + c2 + c3;
+            const int pos[4] = {__popc(B0 & lt), c0 + __popc(B1 & lt),
+                                c0 + c1 + __popc(B2 & lt), c0 + c1 + c2 + __popc(B3 & lt)};
             const float v4[4] = {vv[q][side].x, vv[q][side].y, vv[q][side].z, vv[q][side].w};
 #pragma unroll
             for (int w = 0; w < 4; ++w)
               if ((b >> w) & 1u) {
-                myv[side * TILE + pos] = v4[w];
-                myr[side * TILE + pos] = (uint8_t)(4 * lane + w);
-                ++pos;
+                myv[side * TILE + pos[w]] = v4[w];
+                myr[side * TILE + pos[w]] = (uint8_t)(4 * lane + w);
               }
           }
           __syncwarp();
@@ -261,8 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
             for (int p = lane; p < total; p += 32) {
               const float mv = fminf(myv[a], myv[TILE + bb]);
-              const unsigned long long qv = __float2ull_rn(mv * sp_scale);
-              atomicAdd(&sacc[(int)myr[a] * TILE + (int)myr[TILE + bb]], qv);
+              atomicAdd(&sacc[(int)myr[a] * TILE + (int)myr[TILE + bb]],
+                        __float2uint_rn(mv * sp_scale));
               a += da;
               bb += db;
               if (bb >= nJ) {
