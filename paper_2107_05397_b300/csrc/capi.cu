@@ -50,6 +50,8 @@ int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes) {
 
 namespace {
 
+constexpr int32_t kWinWordsHost = kRareWin / WORD;
+
 // Keeps the caller's current device unchanged across a library call.
 struct DeviceGuard {
   int prev = -1;
@@ -89,7 +91,8 @@ void free_ctx(unifrac_ctx *ctx) {
     if (p) cudaFree(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
                          &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
-                         &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->masks};
+                         &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->rc,
+                         &ctx->bsize,   &ctx->boff,      &ctx->blocks};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &e : ctx->ev)
@@ -634,19 +637,40 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
       while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
       kf_words = kf / WORD;
     }
-    uint4 *masks = nullptr;
-    if (kf_words < n_words) {
-      if ((rc = grow(ctx, ctx->masks, (size_t)ctx->n_tiles * ctx->K_pad * sizeof(uint4))))
-        return rc;
-      masks = static_cast<uint4 *>(ctx->masks.p);
+    uint8_t *rcb = nullptr, *blocks = nullptr;
+    uint32_t *bsize = nullptr;
+    unsigned long long *boff = nullptr;
+    const int32_t n_win = (n_words - kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    if (n_win > 0) {
+      // upper bound of the sparse blocks: every sample is in one tile, so a
+      // branch has at most n_b entries and min(n_b, tiles) flagged rows
+      uint64_t rows = 0, ents = 0;
+      for (int32_t k = kf_words * WORD; k < ctx->K; ++k) {
+        rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
+        ents += (uint64_t)ctx->nb_perm[k];
+      }
+      const uint64_t nblk = (uint64_t)ctx->n_tiles * n_win;
+      const uint64_t bound = nblk * 80 + 4 * rows + 5 * ents + 64;
+      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
+      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
+      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
+      rcb = static_cast<uint8_t *>(ctx->rc.p);
+      bsize = static_cast<uint32_t *>(ctx->bsize.p);
+      boff = static_cast<unsigned long long *>(ctx->boff.p);
+      blocks = static_cast<uint8_t *>(ctx->blocks.p);
     }
-    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, masks, kf_words * WORD, S)))
+    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, rcb, kf_words * WORD, S)))
+      return rc;
+    if (n_win > 0 &&
+        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), bits, rcb, kf_words,
+                                n_win, bsize, boff, blocks)))
       return rc;
     cudaEventRecord(ctx->ev[1], ctx->stream);
     cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
     ctx->sel_unit = 1.0;
-    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, masks, kf_words, S, d_items, n_items,
-                             o)))
+    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, kf_words, blocks, boff, n_win, S,
+                             d_items, n_items, o)))
       return rc;
   } else if (!f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793) {
     // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while

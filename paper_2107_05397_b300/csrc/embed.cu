@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
     int32_t K, const int32_t *__restrict__ perm, const double *__restrict__ len_perm,
     const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
     int32_t n_tiles, const double *__restrict__ inv_total, T *__restrict__ vals,
-    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words, uint4 *__restrict__ masks,
-    int32_t k_mask0, int32_t k_pad) {
+    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words, uint8_t *__restrict__ rc,
+    int32_t k_rare0, int32_t k_pad) {
   const int t = blockIdx.x;
   const int k0 = blockIdx.y * KR;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,13 +113,13 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
       v.z = L * ((float)c.z * inv[2]);
       v.w = L * ((float)c.w * inv[3]);
       *reinterpret_cast<float4 *>(vals + (int64_t)k * ldv + col) = v;
-      if (masks && k >= k_mask0) {
-        // lane-major row mask: bit l of word q <=> column 4l + q of the tile
-        const uint32_t m0 = __ballot_sync(0xffffffffu, c.x != 0u);
-        const uint32_t m1 = __ballot_sync(0xffffffffu, c.y != 0u);
-        const uint32_t m2 = __ballot_sync(0xffffffffu, c.z != 0u);
-        const uint32_t m3 = __ballot_sync(0xffffffffu, c.w != 0u);
-        if (lane == 0) masks[(int64_t)t * k_pad + k] = make_uint4(m0, m1, m2, m3);
+      if (rc && k >= k_rare0) {
+        // non-zero columns of the (branch, tile) row, for the sparse blocks
+        const int nz = __popc(__ballot_sync(0xffffffffu, v.x != 0.f)) +
+                       __popc(__ballot_sync(0xffffffffu, v.y != 0.f)) +
+                       __popc(__ballot_sync(0xffffffffu, v.z != 0.f)) +
+                       __popc(__ballot_sync(0xffffffffu, v.w != 0.f));
+        if (lane == 0) rc[(int64_t)t * k_pad + k] = (uint8_t)nz;
       }
     }
   } else {
@@ -238,7 +238,205 @@ __global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
   a[col] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Sparse blocks of the weighted kernel.  For every column tile t and window j of
+// kRareWin positions starting at p0 (the first rarely present position), one
+// block holds the tile's non-zero entries of the window's flagged rows:
+//   u32 nrows, nent, off_ri, off_val        (16-byte header)
+//   u32 rowstart[nrows + 1]                 entry offset of each flagged row
+//   u8  ri[nent]       at off_ri            row of the tile (0..127) of each entry
+//   f32 val[nent]      at off_val           v[k][col] of each entry
+// Flagged rows appear in position order and a row's local index is the count
+// of flagged positions of the tile before it in the window, so the pair kernel
+// finds a branch's entries from the tile bitmap alone.
+
+__device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
+                             const uint32_t *__restrict__ bits, int32_t n_words,
+                             const uint8_t *__restrict__ rc, int32_t k_pad,
+                             uint32_t *__restrict__ bsize) {
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= (int64_t)n_tiles * n_win) return;
+  const int64_t t = item / n_win;
+  const int j = (int)(item % n_win);
+  const int kb = p0 + kRareWin * j;
+  uint32_t nrows = 0, nent = 0;
+  for (int q = lane; q < kRareWin; q += 32) {
+    const int k = kb + q;
+    if (k >= K) break;
+    if ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u) {
+      ++nrows;
+      nent += rc[t * k_pad + k];
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    nrows += __shfl_xor_sync(0xffffffffu, nrows, off);
+    nent += __shfl_xor_sync(0xffffffffu, nent, off);
+  }
+  if (lane == 0) {
+    const uint32_t off_ri = align16(16u + 4u * (nrows + 1u));
+    const uint32_t off_val = align16(off_ri + nent);
+    bsize[item] = align16(off_val + 4u * nent);
+  }
+}
+
+// Exclusive scan of the block sizes into byte offsets (one CTA of 1024 threads,
+// contiguous chunks per thread); boff[n] receives the total.
+__global__ void __launch_bounds__(1024) k_scan_sizes(int64_t n, const uint32_t *__restrict__ bsize,
+                                                     unsigned long long *__restrict__ boff) {
+  __shared__ unsigned long long part[1024];
+  const int tid = threadIdx.x;
+  const int64_t chunk = (n + 1023) / 1024;
+  const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
+  unsigned long long sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += bsize[i];
+  part[tid] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned long long v = tid >= off ? part[tid - off] : 0ull;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[tid] - sum;  // exclusive prefix of this chunk
+  for (int64_t i = lo; i < hi; ++i) {
+    boff[i] = run;
+    run += bsize[i];
+  }
+  if (tid == 1023) boff[n] = part[1023];
+}
+
+// Fill one block per warp: rows in position order; each row's non-zero
+// columns are compacted with four ballots (column 4l + w of lane l).
+__global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
+                            const uint32_t *__restrict__ bits, int32_t n_words,
+                            const uint8_t *__restrict__ rc, int32_t k_pad,
+                            const float *__restrict__ vals, int64_t ldv,
+                            const unsigned long long *__restrict__ boff,
+                            uint8_t *__restrict__ blocks) {
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= (int64_t)n_tiles * n_win) return;
+  const int64_t t = item / n_win;
+  const int j = (int)(item % n_win);
+  const int kb = p0 + kRareWin * j;
+  uint8_t *blk = blocks + boff[item];
+  // header: count again (same loop as the size kernel)
+  uint32_t nrows = 0, nent = 0;
+  for (int q = lane; q < kRareWin; q += 32) {
+    const int k = kb + q;
+    if (k >= K) break;
+    if ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u) {
+      ++nrows;
+      nent += rc[t * k_pad + k];
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    nrows += __shfl_xor_sync(0xffffffffu, nrows, off);
+    nent += __shfl_xor_sync(0xffffffffu, nent, off);
+  }
+  const uint32_t off_ri = align16(16u + 4u * (nrows + 1u));
+  const uint32_t off_val = align16(off_ri + nent);
+  uint32_t *hdr = reinterpret_cast<uint32_t *>(blk);
+  uint32_t *rowstart = hdr + 4;
+  uint8_t *ri = blk + off_ri;
+  float *val = reinterpret_cast<float *>(blk + off_val);
+  if (lane == 0) {
+    hdr[0] = nrows;
+    hdr[1] = nent;
+    hdr[2] = off_ri;
+    hdr[3] = off_val;
+    rowstart[nrows] = nent;
+  }
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t r0 = 0, e0 = 0;  // rows / entries before the current chunk
+  for (int s = 0; s < kRareWin / 32; ++s) {
+    const int k = kb + 32 * s + lane;
+    const bool fl = k < K && ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u);
+    const uint32_t c = fl ? rc[t * k_pad + k] : 0u;
+    const uint32_t fb = __ballot_sync(0xffffffffu, fl);
+    uint32_t incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const uint32_t my_e = e0 + incl - c;
+    if (fl) rowstart[r0 + __popc(fb & lt)] = my_e;
+    // entries of each flagged row of this chunk, 8 rows in flight at a time
+    uint32_t m = fb;
+    while (m) {
+      int src[8];
+      int nb = 0;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        src[g] = -1;
+        if (m) {
+          src[g] = __ffs(m) - 1;
+          m &= m - 1;
+          ++nb;
+        }
+      }
+      float4 v[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        v[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src[g] >= 0)
+          v[g] = *reinterpret_cast<const float4 *>(
+              vals + (int64_t)(kb + 32 * s + src[g]) * ldv + t * TILE + 4 * lane);
+      }
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        if (src[g] < 0) break;
+        const uint32_t base = __shfl_sync(0xffffffffu, my_e, src[g]);
+        const float vv[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
+        const uint32_t B0 = __ballot_sync(0xffffffffu, vv[0] != 0.f);
+        const uint32_t B1 = __ballot_sync(0xffffffffu, vv[1] != 0.f);
+        const uint32_t B2 = __ballot_sync(0xffffffffu, vv[2] != 0.f);
+        const uint32_t B3 = __ballot_sync(0xffffffffu, vv[3] != 0.f);
+        const uint32_t c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2);
+        const uint32_t pos[4] = {(uint32_t)__popc(B0 & lt), c0 + (uint32_t)__popc(B1 & lt),
+                                 c0 + c1 + (uint32_t)__popc(B2 & lt),
+                                 c0 + c1 + c2 + (uint32_t)__popc(B3 & lt)};
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          if (vv[w] != 0.f) {
+            ri[base + pos[w]] = (uint8_t)(4 * lane + w);
+            val[base + pos[w]] = vv[w];
+          }
+      }
+      (void)nb;
+    }
+    r0 += __popc(fb);
+    e0 += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
 }  // namespace
+
+int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *bits,
+                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
+                      unsigned long long *boff, uint8_t *blocks) {
+  cudaStream_t st = ctx->stream;
+  const int64_t items = (int64_t)ctx->n_tiles * n_win;
+  if (items <= 0) return UNIFRAC_OK;
+  const int32_t n_words = ctx->K_pad / WORD;
+  const int32_t p0 = kf_words * WORD;
+  const unsigned grid = (unsigned)((items * 32 + 255) / 256);
+  k_rare_sizes<<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                     ctx->K_pad, bsize);
+  k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
+  k_rare_fill<<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                    ctx->K_pad, vals, ctx->n_cols, boff, blocks);
+  ctx->stat_launches += 3;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse blocks");
+  return UNIFRAC_OK;
+}
 
 int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
   cudaStream_t st = ctx->stream;
@@ -270,7 +468,7 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
 }
 
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bool f64,
-                  void *vals, uint32_t *bits, uint4 *masks, int32_t k_mask0, double *S) {
+                  void *vals, uint32_t *bits, uint8_t *rc, int32_t k_rare0, double *S) {
   cudaStream_t st = ctx->stream;
   const int32_t n_words = ctx->K_pad / WORD;
   if (ctx->K > 0 && ctx->n_tiles > 0) {
@@ -283,8 +481,8 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bo
     else
       k_pack_weighted<float><<<grid, 256, 0, st>>>(
           ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
-          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words, masks,
-          k_mask0, ctx->K_pad);
+          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words, rc,
+          k_rare0, ctx->K_pad);
     ctx->stat_launches += 1;
   }
   if (ctx->n_cols > 0) {

@@ -152,14 +152,15 @@ struct MinAcc<double> {
 // 2^s the largest power of two that keeps every pair sum below 2^31: integer
 // sums make the result independent of the order of the atomics; the rounding
 // of each term is at most 2^-(s+1)).
-constexpr int kSparseBytes = TILE * TILE * 4 + 8 * 2 * TILE * 5;
-constexpr int kSB = 8;  // sparse branches a warp keeps in flight
+constexpr int kStageBytes = 24 * 1024;  // staging of one tile's sparse block
+constexpr int kSparseBytes = TILE * TILE * 4 + 2 * kStageBytes;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
-                     int32_t kf_words, const uint4 *__restrict__ masks, int32_t k_pad,
+                     int32_t kf_words, const uint8_t *__restrict__ blocks,
+                     const unsigned long long *__restrict__ boff, int32_t n_win,
                      float sp_scale, double sp_inv, const double *__restrict__ S,
                      int32_t flush, OutSpec o, unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -167,8 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
   uint32_t *sacc = reinterpret_cast<uint32_t *>(
       smem_raw + sizeof(T) * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD);
-  float *sw_val = reinterpret_cast<float *>(sacc + TILE * TILE);       // [8 warps][2][TILE]
-  uint8_t *sw_row = reinterpret_cast<uint8_t *>(sw_val + 8 * 2 * TILE);  // [8 warps][2][TILE]
+  uint8_t *stage = reinterpret_cast<uint8_t *>(sacc + TILE * TILE);  // [2][kStageBytes]
+  __shared__ uint32_t swI[kWinWords], swJ[kWinWords];
+  __shared__ int32_t spI[kWinWords], spJ[kWinWords];
   __shared__ int32_t list_n;
   const bool sparse = (sizeof(T) == 4) && kf_words < n_words;
 
@@ -182,98 +184,81 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kEl = 16 / sizeof(T);
 
   // ---------------------------------------------------------------- sparse phase
-  // (first, while the dense accumulators are not yet live).  Each warp takes
-  // kSB selected branches at a time: lanes 0..2*kSB-1 fetch the row masks of
-  // the batch, then every lane fetches its 4 values of each (branch, tile) it
-  // has a row in -- all loads of a batch are independent and in flight
-  // together -- and the warp walks the batch's pairs.
+  // (first, while the dense accumulators are not yet live).  Per window of
+  // kRareWin positions: warp 0 lists the branches present in both tiles and
+  // keeps the two tiles' bitmap words and their prefix popcounts; all threads
+  // copy the two tiles' sparse blocks into shared memory (blocks larger than
+  // the staging area are read in place); each warp then takes branches and
+  // walks the nI x nJ pairs of their entries.
   if (sparse) {
     const int warp = tid >> 5, lane = tid & 31;
     for (int x = tid; x < TILE * TILE; x += kThreads) sacc[x] = 0u;
-    float *myv = sw_val + warp * 2 * TILE;
-    uint8_t *myr = sw_row + warp * 2 * TILE;
-    const float *fv = reinterpret_cast<const float *>(vals);
-    __syncthreads();
-    for (int w0 = kf_words; w0 < n_words; w0 += kWinWords) {
-      if (tid < 32) build_window(bI, bJ, n_words, w0, list, &list_n);
+    for (int j = 0; kf_words + j * kWinWords < n_words; ++j) {
+      const int w0 = kf_words + j * kWinWords;
+      if (tid < 32) {
+        build_window(bI, bJ, n_words, w0, list, &list_n);
+        const int w = w0 + tid;
+        const uint32_t mi = (w < n_words) ? bI[w] : 0u, mj = (w < n_words) ? bJ[w] : 0u;
+        swI[tid] = mi;
+        swJ[tid] = mj;
+        int ci = __popc(mi), cj = __popc(mj);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int yi = __shfl_up_sync(0xffffffffu, ci, off);
+          const int yj = __shfl_up_sync(0xffffffffu, cj, off);
+          if (tid >= off) {
+            ci += yi;
+            cj += yj;
+          }
+        }
+        spI[tid] = ci - __popc(mi);
+        spJ[tid] = cj - __popc(mj);
+      }
+      const int64_t itemI = (int64_t)it.tile_i * n_win + j, itemJ = (int64_t)it.tile_j * n_win + j;
+      const unsigned long long oI = boff[itemI], oJ = boff[itemJ];
+      const uint32_t zI = (uint32_t)(boff[itemI + 1] - oI), zJ = (uint32_t)(boff[itemJ + 1] - oJ);
+      const bool stI = zI <= kStageBytes, stJ = zJ <= kStageBytes;
+      if (stI)
+        for (uint32_t c = tid; c < zI / 16; c += kThreads) cp_async16(stage + 16 * c, blocks + oI + 16 * c);
+      if (stJ)
+        for (uint32_t c = tid; c < zJ / 16; c += kThreads)
+          cp_async16(stage + kStageBytes + 16 * c, blocks + oJ + 16 * c);
+      cp_commit();
+      cp_wait<0>();
       __syncthreads();
+      const uint8_t *blkI = stI ? stage : blocks + oI;
+      const uint8_t *blkJ = stJ ? stage + kStageBytes : blocks + oJ;
+      const uint32_t *hI = reinterpret_cast<const uint32_t *>(blkI);
+      const uint32_t *hJ = reinterpret_cast<const uint32_t *>(blkJ);
+      const uint32_t *rsI = hI + 4, *rsJ = hJ + 4;
+      const uint8_t *riI = blkI + hI[2], *riJ = blkJ + hJ[2];
+      const float *vI = reinterpret_cast<const float *>(blkI + hI[3]);
+      const float *vJ = reinterpret_cast<const float *>(blkJ + hJ[3]);
       const int n = list_n;
-      for (int base = warp * kSB; base < n; base += (kThreads / 32) * kSB) {
-        uint4 mk = make_uint4(0u, 0u, 0u, 0u);
-        {
-          const int e = base + (lane >> 1);
-          if (lane < 2 * kSB && e < n)
-            mk = masks[(int64_t)((lane & 1) ? it.tile_j : it.tile_i) * k_pad + list[e]];
-        }
-        uint32_t mine[kSB][2];
-        float4 vv[kSB][2];
-#pragma unroll
-        for (int q = 0; q < kSB; ++q) {
-          const int e = base + q;
-          const int32_t k = (e < n) ? list[e] : 0;
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const int src = 2 * q + side;
-            const uint32_t m0 = __shfl_sync(0xffffffffu, mk.x, src);
-            const uint32_t m1 = __shfl_sync(0xffffffffu, mk.y, src);
-            const uint32_t m2 = __shfl_sync(0xffffffffu, mk.z, src);
-            const uint32_t m3 = __shfl_sync(0xffffffffu, mk.w, src);
-            // lane-major masks: bit l of word w <=> row 4l + w of the tile
-            const uint32_t b = ((m0 >> lane) & 1u) | (((m1 >> lane) & 1u) << 1) |
-                               (((m2 >> lane) & 1u) << 2) | (((m3 >> lane) & 1u) << 3);
-            mine[q][side] = b;
-            vv[q][side] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b)
-              vv[q][side] = *reinterpret_cast<const float4 *>(
-                  fv + (int64_t)k * ldv + (int64_t)(side ? it.tile_j : it.tile_i) * TILE +
-                  4 * lane);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kSB; ++q) {
-          if (base + q >= n) break;
-          int cnt[2];
-          const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            const uint32_t b = mine[q][side];
-            // rows ordered by (word w, lane): word-w rows of lower lanes first
-            const uint32_t B0 = __ballot_sync(0xffffffffu, b & 1u);
-            const uint32_t B1 = __ballot_sync(0xffffffffu, (b >> 1) & 1u);
-            const uint32_t B2 = __ballot_sync(0xffffffffu, (b >> 2) & 1u);
-            const uint32_t B3 = __ballot_sync(0xffffffffu, (b >> 3) & 1u);
-            const int c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2), c3 = __popc(B3);
-            cnt[side] = c0 + c1 + c2 + c3;
-            const int pos[4] = {__popc(B0 & lt), c0 + __popc(B1 & lt),
-                                c0 + c1 + __popc(B2 & lt), c0 + c1 + c2 + __popc(B3 & lt)};
-            const float v4[4] = {vv[q][side].x, vv[q][side].y, vv[q][side].z, vv[q][side].w};
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-              if ((b >> w) & 1u) {
-                myv[side * TILE + pos[w]] = v4[w];
-                myr[side * TILE + pos[w]] = (uint8_t)(4 * lane + w);
-              }
-          }
-          __syncwarp();
-          const int nI = cnt[0], nJ = cnt[1];
-          const int total = nI * nJ;
-          if (total > 0) {
-            // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
-            int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
-            const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
-            for (int p = lane; p < total; p += 32) {
-              const float mv = fminf(myv[a], myv[TILE + bb]);
-              atomicAdd(&sacc[(int)myr[a] * TILE + (int)myr[TILE + bb]],
-                        __float2uint_rn(mv * sp_scale));
-              a += da;
-              bb += db;
-              if (bb >= nJ) {
-                bb -= nJ;
-                ++a;
-              }
+      for (int e = warp; e < n; e += kThreads / 32) {
+        const int q = list[e] - w0 * WORD;  // position inside the window
+        const int wq = q >> 5;
+        const uint32_t below = (1u << (q & 31)) - 1u;
+        const int rI = spI[wq] + __popc(swI[wq] & below);
+        const int rJ = spJ[wq] + __popc(swJ[wq] & below);
+        const uint32_t sI = rsI[rI], sJ = rsJ[rJ];
+        const int nI = (int)(rsI[rI + 1] - sI), nJ = (int)(rsJ[rJ + 1] - sJ);
+        const int total = nI * nJ;
+        if (total > 0) {
+          // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
+          int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
+          const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
+          for (int p = lane; p < total; p += 32) {
+            const float mv = fminf(vI[sI + a], vJ[sJ + bb]);
+            atomicAdd(&sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]],
+                      __float2uint_rn(mv * sp_scale));
+            a += da;
+            bb += db;
+            if (bb >= nJ) {
+              bb -= nJ;
+              ++a;
             }
           }
-          __syncwarp();
         }
       }
       __syncthreads();
@@ -516,8 +501,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
-                   const uint4 *masks, int32_t kf_words, const double *S, const WorkItem *items,
-                   int32_t n_items, const OutSpec &o) {
+                   int32_t kf_words, const uint8_t *blocks, const unsigned long long *boff,
+                   int32_t n_win, const double *S, const WorkItem *items, int32_t n_items,
+                   const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const size_t elem = f64 ? sizeof(double) : sizeof(float);
@@ -529,15 +515,15 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
-        ctx->K_pad, 1.0f, 1.0, S, 0, o, ctx->d_counter);
+        nullptr, 0, 1.0f, 1.0, S, 0, o, ctx->d_counter);
   } else {
     if (kf_words < n_words) smem += kSparseBytes;
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words, masks,
-        ctx->K_pad, ctx->sp_scale, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
+        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words, blocks,
+        boff, n_win, ctx->sp_scale, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
         ctx->d_counter);
   }
   ctx->stat_launches += 1;

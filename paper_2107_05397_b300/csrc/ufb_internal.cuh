@@ -16,6 +16,8 @@ namespace ufb {
 constexpr int TILE = 128;
 // Branches per 32-bit word of the (tile, branch) nonzero bitmaps.
 constexpr int WORD = 32;
+// Positions per window of the weighted kernel's sparse phase (32 bitmap words).
+constexpr int kRareWin = 1024;
 
 // One 128 x 128 block of sample pairs, I-tile <= J-tile, both in one study.
 struct WorkItem {
@@ -118,7 +120,7 @@ struct unifrac_ctx {
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
-      masks;
+      rc, bsize, boff, blocks;
   size_t device_bytes = 0;
 };
 
@@ -136,10 +138,16 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 // packing ---------------------------------------------------------------------
 // Branch-major values v[k][col] = len_k * cnt / C_col (float or double), the
 // (tile, k) nonzero bitmaps, and per-column sums S_col = sum_k v[k][col] (FP64).
-// FP32 form also writes 128-bit row masks [n_tiles][K_pad] for positions >= k_mask0.
+// FP32 form also writes the non-zero count rc[n_tiles][K_pad] of each flagged
+// (branch, tile) row at positions >= k_rare0.
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                  bool f64, void *vals, uint32_t *bits, uint4 *masks, int32_t k_mask0,
+                  bool f64, void *vals, uint32_t *bits, uint8_t *rc, int32_t k_rare0,
                   double *S);
+// Sparse blocks of positions >= 32 * kf_words, one per (tile, window of
+// kRareWin positions): sizes, byte offsets boff[n_tiles * n_win + 1] and fill.
+int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *bits,
+                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
+                      unsigned long long *boff, uint8_t *blocks);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
@@ -152,9 +160,9 @@ int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
 
 // pair kernels ------------------------------------------------------------
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
-                   const uint32_t *bits, const uint4 *masks, int32_t kf_words,
-                   const double *S, const WorkItem *items, int32_t n_items,
-                   const OutSpec &o);
+                   const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
+                   const unsigned long long *boff, int32_t n_win, const double *S,
+                   const WorkItem *items, int32_t n_items, const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);
