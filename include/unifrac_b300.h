@@ -174,9 +174,25 @@ enum unifrac_option {
   UNIFRAC_OPT_USE_GRAPH = 4,              /* 1 = capture the level loop in a CUDA graph */
   UNIFRAC_OPT_SPARSE_THRESHOLD = 5        /* weighted mixed kernel: branches present in fewer
                                               samples than this run through the sparse phase;
-                                              -1 auto (largest study / 8), 0 all dense */
+                                              -1 auto (largest study / 4), 0 all dense */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
+int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
+
+/*
+ * unifrac_autotune -- pick the kernel settings of one (variant, precision)
+ * for this context by timing candidates on the device, and keep the fastest
+ * as the context's options.  Candidates: the dense / sparse split of the
+ * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
+ * largest study) and the unweighted mixed kernel (tensor core or lookup).
+ * Each candidate runs `repeats` times (>= 1, after one warm-up run) into
+ * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
+ * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the
+ * time compared is embedding + packing + pair kernels (CUDA events).
+ * Synchronises the context's stream.  FP64 has nothing to tune (returns 0).
+ */
+int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
+                     size_t out_bytes, int repeats);
 
 /* Statistics of the context / its last run. */
 enum unifrac_stat {

@@ -1,0 +1,92 @@
+"""Autotuner driver: persistent cache of the library's tuned kernel settings.
+
+The library times the candidates itself (`unifrac_autotune`, on the device,
+CUDA events).  This module keys the winner by problem shape and keeps it in a
+JSON file, so later contexts of similar shape start tuned without re-timing:
+
+    key = variant, precision, largest-study bucket (power of 2), kept-branch
+          bucket (power of 2), SM count
+
+The weighted split is stored as a fraction of the largest study so that it
+carries over between sizes in the same bucket.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+from typing import Optional
+
+from . import binding as ub
+
+
+def _bucket(x: float) -> int:
+    return int(2 ** math.ceil(math.log2(max(1.0, float(x)))))
+
+
+def _max_study(ctx: "ub.Context") -> int:
+    so = ctx.study_offsets
+    if so is None:
+        return int(ctx.n_samples)
+    return int(max(int(so[i + 1]) - int(so[i]) for i in range(len(so) - 1)))
+
+
+def shape_key(ctx: "ub.Context", variant: int, precision: int) -> str:
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    kept = ctx.stat(ub.STAT_BRANCHES_KEPT)
+    return (f"v{variant}-p{precision}-n{_bucket(_max_study(ctx))}-b{_bucket(kept)}-sm{sms}")
+
+
+def get_option(ctx: "ub.Context", option: int) -> int:
+    lib = ub.load()
+    lib.unifrac_get_option.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64)]
+    lib.unifrac_get_option.restype = ctypes.c_int
+    v = ctypes.c_int64()
+    rc = lib.unifrac_get_option(ctx.handle, option, ctypes.byref(v))
+    if rc:
+        raise ub.UniFracError(rc, ub.unifrac_strerror(rc))
+    return int(v.value)
+
+
+def tune(ctx: "ub.Context", variant: int, precision: int,
+         cache_path: Optional[str] = None, repeats: int = 2) -> dict:
+    """Apply cached settings for this shape, or time candidates and cache them."""
+    import torch
+    key = shape_key(ctx, variant, precision)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    n = _max_study(ctx)
+    if key in cache:
+        rec = cache[key]
+        if "sparse_fraction" in rec:
+            ctx.set_option(ub.OPT_SPARSE_THRESHOLD, max(2, int(round(rec["sparse_fraction"] * n))))
+        if "unweighted_kernel" in rec:
+            ctx.set_option(ub.OPT_UNWEIGHTED_MIXED_KERNEL, rec["unweighted_kernel"])
+        return dict(rec, cached=True)
+    nbytes = ctx.output_bytes(precision, ub.OUT_CONDENSED)
+    out = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device="cuda")
+    lib = ub.load()
+    lib.unifrac_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    lib.unifrac_autotune.restype = ctypes.c_int
+    rc = lib.unifrac_autotune(ctx.handle, variant, precision, ctypes.c_void_p(out.data_ptr()),
+                              out.numel() * 4, repeats)
+    if rc:
+        raise ub.UniFracError(rc, ub.unifrac_strerror(rc) + ": " + ub.unifrac_last_error(ctx.handle))
+    rec = {}
+    if variant == ub.WEIGHTED_NORMALIZED and precision == ub.MIXED:
+        rec["sparse_fraction"] = get_option(ctx, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)
+    if variant == ub.UNWEIGHTED and precision == ub.MIXED:
+        rec["unweighted_kernel"] = get_option(ctx, ub.OPT_UNWEIGHTED_MIXED_KERNEL)
+    if cache_path:
+        cache[key] = rec
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return dict(rec, cached=False)

@@ -49,7 +49,8 @@ STAT_SELECTED_WEIGHTED = 14
 
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",
-            "unifrac_set_option", "unifrac_get_stat")
+            "unifrac_set_option", "unifrac_get_option", "unifrac_get_stat",
+            "unifrac_autotune")
 
 
 class UniFracError(RuntimeError):

@@ -44,6 +44,7 @@ int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes) {
     return cuda_fail(ctx, e, "device allocation");
   }
   b.bytes = bytes;
+  ctx->buf_generation++;  // a captured graph may hold the old address
   ctx->device_bytes += bytes;
   return UNIFRAC_OK;
 }
@@ -92,7 +93,7 @@ void free_ctx(unifrac_ctx *ctx) {
   ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
                          &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
                          &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->rc,
-                         &ctx->bsize,   &ctx->boff,      &ctx->blocks};
+                         &ctx->bsize,   &ctx->boff,      &ctx->blocks, &ctx->spart};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &e : ctx->ev)
@@ -100,6 +101,10 @@ void free_ctx(unifrac_ctx *ctx) {
   for (auto &pr : ctx->ev_pair)
     for (auto &e : pr)
       if (e) cudaEventDestroy(e);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -531,6 +536,249 @@ int unifrac_output_bytes(const unifrac_ctx *ctx, int precision, int layout,
   return UNIFRAC_OK;
 }
 
+// Everything a run needs that is decided on the host.  Buffers are grown and
+// the work list uploaded before any device work is enqueued, so the enqueue
+// step issues only kernels, memsets, device-to-device copies and event
+// records -- the form a CUDA graph can capture.
+struct RunPlan {
+  int variant, precision, layout;
+  int32_t s0, s1;
+  bool f64;
+  enum Kind { WEIGHTED, TENSOR, LOOKUP } kind;
+  int32_t kf_words = 0, n_win = 0;
+  void *dst = nullptr;
+  int32_t n_items = 0;
+};
+
+static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
+  // the work list depends only on (layout, stripe range): rebuild when it changes
+  if (ctx->items_valid && ctx->items_layout == layout && ctx->items_s0 == s0 &&
+      ctx->items_s1 == s1)
+    return UNIFRAC_OK;
+  std::vector<WorkItem> items;
+  std::vector<StudyDev> studies(ctx->n_studies);
+  int64_t off = 0;
+  for (int32_t s = 0; s < ctx->n_studies; ++s) {
+    const int32_t n = ctx->study_off[s + 1] - ctx->study_off[s];
+    studies[s] = StudyDev{off, n, ctx->study_col0[s]};
+    off += n_pairs_layout(layout, n, s0, s1);
+    study_items(s, n, ctx->study_col0[s] / TILE, layout, s0, s1, items);
+  }
+  int rc;
+  if ((rc = grow(ctx, ctx->items, items.size() * sizeof(WorkItem)))) return rc;
+  if ((rc = grow(ctx, ctx->studies, studies.size() * sizeof(StudyDev)))) return rc;
+  cudaError_t e;
+  if (!items.empty()) {
+    e = cudaMemcpyAsync(ctx->items.p, items.data(), items.size() * sizeof(WorkItem),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload work items");
+  }
+  e = cudaMemcpyAsync(ctx->studies.p, studies.data(), studies.size() * sizeof(StudyDev),
+                      cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload studies");
+  // pageable sources: the copies above are staged before returning
+  ctx->n_items = (int32_t)items.size();
+  ctx->items_valid = true;
+  ctx->items_layout = layout;
+  ctx->items_s0 = s0;
+  ctx->items_s1 = s1;
+  return UNIFRAC_OK;
+}
+
+// Grow every buffer the plan touches (may synchronise / allocate).
+static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
+  int rc;
+  if ((rc = grow(ctx, ctx->cnt, (size_t)ctx->n_nodes * ctx->n_cols * sizeof(uint32_t)))) return rc;
+  if ((rc = grow(ctx, ctx->flag, (size_t)ctx->n_nodes * ctx->n_tiles))) return rc;
+  if (P.kind == RunPlan::WEIGHTED) {
+    const size_t elem = P.f64 ? 8 : 4;
+    const int32_t n_words = ctx->K_pad / WORD;
+    if ((rc = grow(ctx, ctx->vals, (size_t)ctx->K_pad * ctx->n_cols * elem))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    P.kf_words = n_words;
+    if (!P.f64 && ctx->opt_sparse_threshold != 0) {
+      // dense / sparse split at a multiple of 32 positions (FP32 form only)
+      const int64_t th = ctx->opt_sparse_threshold > 0
+                             ? ctx->opt_sparse_threshold
+                             : std::max<int64_t>(32, ctx->max_study_n / 4);
+      int32_t kf = 0;
+      while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
+      P.kf_words = kf / WORD;
+    }
+    P.n_win = (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    if (P.n_win > 0) {
+      // upper bound of the sparse blocks: every sample is in one tile, so a
+      // branch has at most n_b entries and min(n_b, tiles) flagged rows
+      uint64_t rows = 0, ents = 0;
+      for (int32_t k = P.kf_words * WORD; k < ctx->K; ++k) {
+        rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
+        ents += (uint64_t)ctx->nb_perm[k];
+      }
+      const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
+      const uint64_t bound = nblk * 80 + 4 * rows + 5 * ents + 64;
+      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
+      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
+      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
+      if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 4)))
+        return rc;
+    }
+  } else if (P.kind == RunPlan::TENSOR) {
+    const int32_t n_kt = ctx->K_pad / 64;
+    const int32_t k_words = (n_kt + 31) / 32;
+    const size_t plane = (size_t)ctx->n_cols * ctx->K_pad * 2;
+    if ((rc = grow(ctx, ctx->vals, plane))) return rc;
+    if ((rc = grow(ctx, ctx->vals2, 3 * plane))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
+    if ((rc = grow(ctx, ctx->partial, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+  } else {
+    const int32_t G = ctx->K_pad / 8;
+    const int32_t g_words = (G + WORD - 1) / WORD;
+    if ((rc = grow(ctx, ctx->vals, (size_t)G * ctx->n_cols))) return rc;
+    if ((rc = grow(ctx, ctx->tables, (size_t)G * 256 * 8))) return rc;
+    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * g_words * 4))) return rc;
+    if ((rc = grow(ctx, ctx->partial, (size_t)((G + 31) / 32) * ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+  }
+  return UNIFRAC_OK;
+}
+
+// Device work of one run on ctx->stream (no allocation, no host copy, no sync).
+static int enqueue_run(unifrac_ctx *ctx, const RunPlan &P) {
+  int rc;
+  cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
+  OutSpec o;
+  o.out = P.dst;
+  o.studies = static_cast<const StudyDev *>(ctx->studies.p);
+  o.layout = P.layout;
+  o.s0 = P.s0;
+  o.s1 = P.s1;
+  o.is_f64 = P.f64 ? 1 : 0;
+  uint32_t *cnt = static_cast<uint32_t *>(ctx->cnt.p);
+  uint8_t *flag = static_cast<uint8_t *>(ctx->flag.p);
+  cudaEventRecord(ctx->ev[0], ctx->stream);
+  if ((rc = embed_counts(ctx, cnt, flag))) return rc;
+  const WorkItem *d_items = static_cast<const WorkItem *>(ctx->items.p);
+  const int32_t n_items = P.n_items;
+  const int variant = P.variant;
+  if (P.kind == RunPlan::WEIGHTED) {
+    double *S = static_cast<double *>(ctx->persample.p);
+    uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
+    uint8_t *rcb = P.n_win > 0 ? static_cast<uint8_t *>(ctx->rc.p) : nullptr;
+    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, rcb, P.kf_words * WORD, S)))
+      return rc;
+    if (P.n_win > 0 &&
+        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), bits, rcb,
+                                P.kf_words, P.n_win, static_cast<uint32_t *>(ctx->bsize.p),
+                                static_cast<unsigned long long *>(ctx->boff.p),
+                                static_cast<uint8_t *>(ctx->blocks.p))))
+      return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 1.0;
+    if ((rc = pairs_weighted(ctx, P.f64, ctx->vals.p, bits, P.kf_words,
+                             static_cast<const uint8_t *>(ctx->blocks.p),
+                             static_cast<const unsigned long long *>(ctx->boff.p), P.n_win,
+                             P.n_win > 0 ? static_cast<uint32_t *>(ctx->spart.p) : nullptr, S,
+                             d_items, n_items, o)))
+      return rc;
+  } else if (P.kind == RunPlan::TENSOR) {
+    uint16_t *X = static_cast<uint16_t *>(ctx->vals.p);
+    uint16_t *D = static_cast<uint16_t *>(ctx->vals2.p);
+    uint32_t *kbits = static_cast<uint32_t *>(ctx->bits.p);
+    double *a = static_cast<double *>(ctx->persample.p);
+    if ((rc = pack_tc(ctx, cnt, flag, X, D, kbits, a))) return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 64.0;
+    if ((rc = pairs_tc(ctx, X, D, kbits, a, d_items, n_items, o))) return rc;
+  } else {
+    double *a = static_cast<double *>(ctx->persample.p);
+    uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
+    double *tables = static_cast<double *>(ctx->tables.p);
+    uint32_t *gbits = static_cast<uint32_t *>(ctx->bits.p);
+    if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    ctx->sel_unit = 8.0;
+    if ((rc = pairs_lookup(ctx, bytes, tables, gbits, a, d_items, n_items, o))) return rc;
+  }
+  cudaEventRecord(ctx->ev[2], ctx->stream);
+  cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
+  e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
+                      cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
+  return UNIFRAC_OK;
+}
+
+// Graph replay of a captured run.  The legacy default stream cannot be
+// captured, so capture and replay use the context's private stream, ordered
+// after / before the caller's stream with events.
+static int graph_key_matches(const unifrac_ctx *ctx, const RunPlan &P) {
+  return ctx->graph_exec && ctx->gk_variant == P.variant && ctx->gk_precision == P.precision &&
+         ctx->gk_layout == P.layout && ctx->gk_s0 == P.s0 && ctx->gk_s1 == P.s1 &&
+         ctx->gk_dst == P.dst && ctx->gk_opts == ctx->opt_generation &&
+         ctx->gk_bufs == ctx->buf_generation;
+}
+
+static int graph_launch(unifrac_ctx *ctx) {
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap_stream, ctx->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ctx->graph_exec, ctx->cap_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+  return UNIFRAC_OK;
+}
+
+static int graph_capture(unifrac_ctx *ctx, const RunPlan &P) {
+  cudaError_t e;
+  if (!ctx->cap_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph stream");
+  }
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  cudaStream_t user = ctx->stream;
+  const double launches = ctx->stat_launches;
+  ctx->stream = ctx->cap_stream;
+  e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = UNIFRAC_OK;
+  if (e == cudaSuccess) rc = enqueue_run(ctx, P);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  ctx->stream = user;
+  ctx->stat_launches = launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "end capture");
+  e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    ctx->graph_exec = nullptr;
+    return cuda_fail(ctx, e, "graph instantiate");
+  }
+  ctx->gk_variant = P.variant;
+  ctx->gk_precision = P.precision;
+  ctx->gk_layout = P.layout;
+  ctx->gk_s0 = P.s0;
+  ctx->gk_s1 = P.s1;
+  ctx->gk_dst = P.dst;
+  ctx->gk_opts = ctx->opt_generation;
+  ctx->gk_bufs = ctx->buf_generation;
+  return UNIFRAC_OK;
+}
+
 static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_start,
                     int32_t stripe_stop, int layout, void *out, size_t out_bytes) {
   if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED)
@@ -550,8 +798,21 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   if (out_bytes < need)
     return fail(ctx, UNIFRAC_E_BUFFER_TOO_SMALL,
                 "out holds " + std::to_string(out_bytes) + " bytes, needs " + std::to_string(need));
-  const bool f64 = precision == UNIFRAC_FP64;
-  ctx->stat_launches = 0;
+  RunPlan P;
+  P.variant = variant;
+  P.precision = precision;
+  P.layout = layout;
+  P.s0 = s0;
+  P.s1 = s1;
+  P.f64 = precision == UNIFRAC_FP64;
+  if (variant == UNIFRAC_WEIGHTED_NORMALIZED)
+    P.kind = RunPlan::WEIGHTED;
+  else if (!P.f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793)
+    // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while
+    // no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
+    P.kind = RunPlan::TENSOR;
+  else
+    P.kind = RunPlan::LOOKUP;
 
   // where does `out` live?
   bool device_out = false;
@@ -566,161 +827,39 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   }
   const bool whole = (layout == UNIFRAC_OUT_STRIPES) ||
                      (s0 == 0 && (ctx->n_studies > 1 || s1 == ctx->n_samples / 2));
-  void *dst = out;
+  P.dst = out;
   if (!device_out && need > 0) {
     if ((rc = grow(ctx, ctx->stage, need))) return rc;
-    dst = ctx->stage.p;
-    if (!whole) {  // untouched elements keep the caller's values
-      cudaError_t e = cudaMemcpyAsync(dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "stage output");
-    }
+    P.dst = ctx->stage.p;
+  }
+  if ((rc = plan_items(ctx, layout, s0, s1))) return rc;
+  P.n_items = ctx->n_items;
+  ctx->stat_tile_pairs = (double)P.n_items;
+  if ((rc = plan_buffers(ctx, P))) return rc;
+  if (!device_out && need > 0 && !whole) {  // untouched elements keep the caller's values
+    cudaError_t e = cudaMemcpyAsync(P.dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage output");
   }
 
-  // work items and study descriptors
-  std::vector<WorkItem> items;
-  std::vector<StudyDev> studies(ctx->n_studies);
-  int64_t off = 0;
-  for (int32_t s = 0; s < ctx->n_studies; ++s) {
-    const int32_t n = ctx->study_off[s + 1] - ctx->study_off[s];
-    studies[s] = StudyDev{off, n, ctx->study_col0[s]};
-    off += n_pairs_layout(layout, n, s0, s1);
-    study_items(s, n, ctx->study_col0[s] / TILE, layout, s0, s1, items);
-  }
-  ctx->stat_tile_pairs = (double)items.size();
-  if ((rc = grow(ctx, ctx->items, items.size() * sizeof(WorkItem)))) return rc;
-  if ((rc = grow(ctx, ctx->studies, studies.size() * sizeof(StudyDev)))) return rc;
-  cudaError_t e;
-  if (!items.empty()) {
-    e = cudaMemcpyAsync(ctx->items.p, items.data(), items.size() * sizeof(WorkItem),
-                        cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload work items");
-  }
-  e = cudaMemcpyAsync(ctx->studies.p, studies.data(), studies.size() * sizeof(StudyDev),
-                      cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload studies");
-  e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
-  OutSpec o;
-  o.out = dst;
-  o.studies = static_cast<const StudyDev *>(ctx->studies.p);
-  o.layout = layout;
-  o.s0 = s0;
-  o.s1 = s1;
-  o.is_f64 = f64 ? 1 : 0;
-
-  // embedding
-  const size_t cnt_bytes = (size_t)ctx->n_nodes * ctx->n_cols * sizeof(uint32_t);
-  if ((rc = grow(ctx, ctx->cnt, cnt_bytes))) return rc;
-  if ((rc = grow(ctx, ctx->flag, (size_t)ctx->n_nodes * ctx->n_tiles))) return rc;
-  uint32_t *cnt = static_cast<uint32_t *>(ctx->cnt.p);
-  uint8_t *flag = static_cast<uint8_t *>(ctx->flag.p);
-  cudaEventRecord(ctx->ev[0], ctx->stream);
-  if ((rc = embed_counts(ctx, cnt, flag))) return rc;
-
-  const WorkItem *d_items = static_cast<const WorkItem *>(ctx->items.p);
-  const int32_t n_items = (int32_t)items.size();
-  if (variant == UNIFRAC_WEIGHTED_NORMALIZED) {
-    const size_t elem = f64 ? 8 : 4;
-    if ((rc = grow(ctx, ctx->vals, (size_t)ctx->K_pad * ctx->n_cols * elem))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * (ctx->K_pad / WORD) * 4))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
-    double *S = static_cast<double *>(ctx->persample.p);
-    uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
-    // dense / sparse split at a multiple of 32 positions (FP32 form only)
-    const int32_t n_words = ctx->K_pad / WORD;
-    int32_t kf_words = n_words;
-    if (!f64 && ctx->opt_sparse_threshold != 0) {
-      const int64_t th = ctx->opt_sparse_threshold > 0
-                             ? ctx->opt_sparse_threshold
-                             : std::max<int64_t>(32, ctx->max_study_n / 8);
-      int32_t kf = 0;
-      while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
-      kf_words = kf / WORD;
-    }
-    uint8_t *rcb = nullptr, *blocks = nullptr;
-    uint32_t *bsize = nullptr;
-    unsigned long long *boff = nullptr;
-    const int32_t n_win = (n_words - kf_words + kWinWordsHost - 1) / kWinWordsHost;
-    if (n_win > 0) {
-      // upper bound of the sparse blocks: every sample is in one tile, so a
-      // branch has at most n_b entries and min(n_b, tiles) flagged rows
-      uint64_t rows = 0, ents = 0;
-      for (int32_t k = kf_words * WORD; k < ctx->K; ++k) {
-        rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
-        ents += (uint64_t)ctx->nb_perm[k];
-      }
-      const uint64_t nblk = (uint64_t)ctx->n_tiles * n_win;
-      const uint64_t bound = nblk * 80 + 4 * rows + 5 * ents + 64;
-      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
-      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
-      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
-      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
-      rcb = static_cast<uint8_t *>(ctx->rc.p);
-      bsize = static_cast<uint32_t *>(ctx->bsize.p);
-      boff = static_cast<unsigned long long *>(ctx->boff.p);
-      blocks = static_cast<uint8_t *>(ctx->blocks.p);
-    }
-    if ((rc = pack_weighted(ctx, cnt, flag, f64, ctx->vals.p, bits, rcb, kf_words * WORD, S)))
-      return rc;
-    if (n_win > 0 &&
-        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), bits, rcb, kf_words,
-                                n_win, bsize, boff, blocks)))
-      return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
-    ctx->sel_unit = 1.0;
-    if ((rc = pairs_weighted(ctx, f64, ctx->vals.p, bits, kf_words, blocks, boff, n_win, S,
-                             d_items, n_items, o)))
-      return rc;
-  } else if (!f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793) {
-    // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while
-    // no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
-    const int32_t n_kt = ctx->K_pad / 64;
-    const int32_t k_words = (n_kt + 31) / 32;
-    const size_t plane = (size_t)ctx->n_cols * ctx->K_pad * 2;
-    if ((rc = grow(ctx, ctx->vals, plane))) return rc;
-    if ((rc = grow(ctx, ctx->vals2, 3 * plane))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
-    if ((rc = grow(ctx, ctx->partial, (size_t)ctx->n_cols * 8))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
-    uint16_t *X = static_cast<uint16_t *>(ctx->vals.p);
-    uint16_t *D = static_cast<uint16_t *>(ctx->vals2.p);
-    uint32_t *kbits = static_cast<uint32_t *>(ctx->bits.p);
-    double *a = static_cast<double *>(ctx->persample.p);
-    if ((rc = pack_tc(ctx, cnt, flag, X, D, kbits, a))) return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
-    ctx->sel_unit = 64.0;
-    if ((rc = pairs_tc(ctx, X, D, kbits, a, d_items, n_items, o))) return rc;
+  const bool use_graph = ctx->opt_use_graph && device_out;
+  if (use_graph && graph_key_matches(ctx, P)) {
+    if ((rc = graph_launch(ctx))) return rc;
+    ctx->stat_launches = ctx->graph_launches;
   } else {
-    const int32_t G = ctx->K_pad / 8;
-    const int32_t g_words = (G + WORD - 1) / WORD;
-    if ((rc = grow(ctx, ctx->vals, (size_t)G * ctx->n_cols))) return rc;
-    if ((rc = grow(ctx, ctx->tables, (size_t)G * 256 * 8))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * g_words * 4))) return rc;
-    if ((rc = grow(ctx, ctx->partial, (size_t)((G + 31) / 32) * ctx->n_cols * 8))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
-    double *a = static_cast<double *>(ctx->persample.p);
-    uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
-    double *tables = static_cast<double *>(ctx->tables.p);
-    uint32_t *gbits = static_cast<uint32_t *>(ctx->bits.p);
-    if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
-    ctx->sel_unit = 8.0;
-    if ((rc = pairs_lookup(ctx, bytes, tables, gbits, a, d_items, n_items, o))) return rc;
+    ctx->stat_launches = 0;
+    if ((rc = enqueue_run(ctx, P))) return rc;
+    if (use_graph) {  // this run executed eagerly; later identical runs replay the graph
+      ctx->graph_launches = ctx->stat_launches;
+      if ((rc = graph_capture(ctx, P))) return rc;
+    }
   }
-  cudaEventRecord(ctx->ev[2], ctx->stream);
-  cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
-  e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
-                      cudaMemcpyDeviceToDevice, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
   ctx->sel_unit_v[variant] = ctx->sel_unit;
   ctx->ev_valid = true;
   ctx->ev_pair_valid[variant] = true;
 
+  cudaError_t e;
   if (!device_out && need > 0) {
-    e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(out, P.dst, need, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
@@ -746,6 +885,7 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_sta
 
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
   if (!ctx) return UNIFRAC_E_INVALID_ARG;
+  ctx->opt_generation++;  // invalidates a captured graph
   switch (option) {
     case UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL:
       if (value < 0 || value > 2) return UNIFRAC_E_INVALID_ARG;
@@ -774,6 +914,71 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
     default:
       return UNIFRAC_E_INVALID_ARG;
   }
+}
+
+int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
+  if (!ctx || !value) return UNIFRAC_E_INVALID_ARG;
+  switch (option) {
+    case UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL: *value = ctx->opt_uw_kernel; return UNIFRAC_OK;
+    case UNIFRAC_OPT_WEIGHTED_FLUSH: *value = ctx->opt_flush; return UNIFRAC_OK;
+    case UNIFRAC_OPT_PERSISTENT: *value = ctx->opt_persistent; return UNIFRAC_OK;
+    case UNIFRAC_OPT_CTAS_PER_SM: *value = ctx->opt_ctas_per_sm; return UNIFRAC_OK;
+    case UNIFRAC_OPT_USE_GRAPH: *value = ctx->opt_use_graph; return UNIFRAC_OK;
+    case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
+    default: return UNIFRAC_E_INVALID_ARG;
+  }
+}
+
+int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, size_t out_bytes,
+                     int repeats) {
+  if (!ctx || !out || repeats < 1) return UNIFRAC_E_INVALID_ARG;
+  if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED)
+    return UNIFRAC_E_INVALID_ARG;
+  if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED) return UNIFRAC_E_INVALID_ARG;
+  if (precision == UNIFRAC_FP64) return UNIFRAC_OK;
+  DeviceGuard g(ctx->device);
+  std::vector<std::pair<int, int64_t>> cands;  // (option, value)
+  int option;
+  if (variant == UNIFRAC_WEIGHTED_NORMALIZED) {
+    option = UNIFRAC_OPT_SPARSE_THRESHOLD;
+    const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
+    for (int64_t num : {1, 2, 4, 8, 12}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
+  } else {
+    option = UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL;
+    cands.push_back({option, 1});
+    cands.push_back({option, 2});
+  }
+  const int saved_graph = ctx->opt_use_graph;
+  ctx->opt_use_graph = 0;
+  double best = 1e300;
+  int64_t best_v = cands[0].second;
+  for (auto &c : cands) {
+    int rc = unifrac_set_option(ctx, c.first, c.second);
+    if (rc) break;
+    double t = 1e300;
+    for (int r = 0; r <= repeats; ++r) {
+      rc = unifrac_run(ctx, variant, precision, 0, -1, UNIFRAC_OUT_CONDENSED, out, out_bytes);
+      if (rc) break;
+      cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
+      if (e != cudaSuccess) {
+        ctx->opt_use_graph = saved_graph;
+        return cuda_fail(ctx, e, "autotune");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
+      if (r > 0) t = std::min(t, (double)ms);  // first run is the warm-up
+    }
+    if (rc) {
+      ctx->opt_use_graph = saved_graph;
+      return rc;
+    }
+    if (t < best) {
+      best = t;
+      best_v = c.second;
+    }
+  }
+  ctx->opt_use_graph = saved_graph;
+  return unifrac_set_option(ctx, option, best_v);
 }
 
 int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {

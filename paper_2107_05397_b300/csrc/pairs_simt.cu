@@ -144,35 +144,21 @@ struct MinAcc<double> {
 // T = double: FP64 throughout.
 //
 // Hybrid split (FP32 form): positions [0, 32*kf_words) are the frequently
-// present branches and run through the dense register tile above; the rest,
-// present in few samples, run sparsely: for each such branch selected for the
-// tile pair, the warp enumerates the non-zero rows of each tile from 128-bit
-// row masks and adds min(v_bi, v_bj) for exactly those pairs into a 128 x 128
-// shared-memory accumulator of 32-bit fixed-point integers (round(value * 2^s),
-// 2^s the largest power of two that keeps every pair sum below 2^31: integer
-// sums make the result independent of the order of the atomics; the rounding
-// of each term is at most 2^-(s+1)).
-constexpr int kStageBytes = 24 * 1024;  // staging of one tile's sparse block
-constexpr int kSparseBytes = TILE * TILE * 4 + 2 * kStageBytes;
-
+// present branches and run through the dense register tile here; the rest,
+// present in few samples, were summed by k_pairs_weighted_sparse into spart
+// (per tile pair, 32-bit fixed point, scale 1 / sp_inv), added in the epilogue.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
-                     int32_t kf_words, const uint8_t *__restrict__ blocks,
-                     const unsigned long long *__restrict__ boff, int32_t n_win,
-                     float sp_scale, double sp_inv, const double *__restrict__ S,
+                     int32_t kf_words, const uint32_t *__restrict__ spart, double sp_inv,
+                     const double *__restrict__ S,
                      int32_t flush, OutSpec o, unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
   int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
-  uint32_t *sacc = reinterpret_cast<uint32_t *>(
-      smem_raw + sizeof(T) * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD);
-  uint8_t *stage = reinterpret_cast<uint8_t *>(sacc + TILE * TILE);  // [2][kStageBytes]
-  __shared__ uint32_t swI[kWinWords], swJ[kWinWords];
-  __shared__ int32_t spI[kWinWords], spJ[kWinWords];
   __shared__ int32_t list_n;
-  const bool sparse = (sizeof(T) == 4) && kf_words < n_words;
+  const bool sparse = (sizeof(T) == 4) && spart != nullptr;
 
   const WorkItem it = items[blockIdx.x];
   const StudyDev sd = o.studies[it.study];
@@ -182,88 +168,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t colI = (int64_t)it.tile_i * TILE, colJ = (int64_t)it.tile_j * TILE;
   constexpr int CPR = TILE * sizeof(T) / 16;  // 16-byte chunks per row
   constexpr int kEl = 16 / sizeof(T);
-
-  // ---------------------------------------------------------------- sparse phase
-  // (first, while the dense accumulators are not yet live).  Per window of
-  // kRareWin positions: warp 0 lists the branches present in both tiles and
-  // keeps the two tiles' bitmap words and their prefix popcounts; all threads
-  // copy the two tiles' sparse blocks into shared memory (blocks larger than
-  // the staging area are read in place); each warp then takes branches and
-  // walks the nI x nJ pairs of their entries.
-  if (sparse) {
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int x = tid; x < TILE * TILE; x += kThreads) sacc[x] = 0u;
-    for (int j = 0; kf_words + j * kWinWords < n_words; ++j) {
-      const int w0 = kf_words + j * kWinWords;
-      if (tid < 32) {
-        build_window(bI, bJ, n_words, w0, list, &list_n);
-        const int w = w0 + tid;
-        const uint32_t mi = (w < n_words) ? bI[w] : 0u, mj = (w < n_words) ? bJ[w] : 0u;
-        swI[tid] = mi;
-        swJ[tid] = mj;
-        int ci = __popc(mi), cj = __popc(mj);
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int yi = __shfl_up_sync(0xffffffffu, ci, off);
-          const int yj = __shfl_up_sync(0xffffffffu, cj, off);
-          if (tid >= off) {
-            ci += yi;
-            cj += yj;
-          }
-        }
-        spI[tid] = ci - __popc(mi);
-        spJ[tid] = cj - __popc(mj);
-      }
-      const int64_t itemI = (int64_t)it.tile_i * n_win + j, itemJ = (int64_t)it.tile_j * n_win + j;
-      const unsigned long long oI = boff[itemI], oJ = boff[itemJ];
-      const uint32_t zI = (uint32_t)(boff[itemI + 1] - oI), zJ = (uint32_t)(boff[itemJ + 1] - oJ);
-      const bool stI = zI <= kStageBytes, stJ = zJ <= kStageBytes;
-      if (stI)
-        for (uint32_t c = tid; c < zI / 16; c += kThreads) cp_async16(stage + 16 * c, blocks + oI + 16 * c);
-      if (stJ)
-        for (uint32_t c = tid; c < zJ / 16; c += kThreads)
-          cp_async16(stage + kStageBytes + 16 * c, blocks + oJ + 16 * c);
-      cp_commit();
-      cp_wait<0>();
-      __syncthreads();
-      const uint8_t *blkI = stI ? stage : blocks + oI;
-      const uint8_t *blkJ = stJ ? stage + kStageBytes : blocks + oJ;
-      const uint32_t *hI = reinterpret_cast<const uint32_t *>(blkI);
-      const uint32_t *hJ = reinterpret_cast<const uint32_t *>(blkJ);
-      const uint32_t *rsI = hI + 4, *rsJ = hJ + 4;
-      const uint8_t *riI = blkI + hI[2], *riJ = blkJ + hJ[2];
-      const float *vI = reinterpret_cast<const float *>(blkI + hI[3]);
-      const float *vJ = reinterpret_cast<const float *>(blkJ + hJ[3]);
-      const int n = list_n;
-      for (int e = warp; e < n; e += kThreads / 32) {
-        const int q = list[e] - w0 * WORD;  // position inside the window
-        const int wq = q >> 5;
-        const uint32_t below = (1u << (q & 31)) - 1u;
-        const int rI = spI[wq] + __popc(swI[wq] & below);
-        const int rJ = spJ[wq] + __popc(swJ[wq] & below);
-        const uint32_t sI = rsI[rI], sJ = rsJ[rJ];
-        const int nI = (int)(rsI[rI + 1] - sI), nJ = (int)(rsJ[rJ + 1] - sJ);
-        const int total = nI * nJ;
-        if (total > 0) {
-          // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
-          int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
-          const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
-          for (int p = lane; p < total; p += 32) {
-            const float mv = fminf(vI[sI + a], vJ[sJ + bb]);
-            atomicAdd(&sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]],
-                      __float2uint_rn(mv * sp_scale));
-            a += da;
-            bb += db;
-            if (bb >= nJ) {
-              bb -= nJ;
-              ++a;
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
 
   // FP32 form: part (FP32, current chunk) + acc (FP64).  FP64 form: part only.
   constexpr int AD = (sizeof(T) == 4) ? 8 : 1;
@@ -360,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         double M;
         if constexpr (sizeof(T) == 4) {
           M = acc[qi][qj];
-          if (sparse) M += (double)sacc[i * TILE + j] * sp_inv;
+          if (sparse) M += (double)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j] * sp_inv;
         } else {
           M = part.get(qi, qj);
         }
@@ -370,6 +274,143 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
+}
+
+// ----------------------------------------------------------------------------
+// weighted normalized, rarely present branches (FP32 form)
+//
+// For every tile pair, the branches at positions >= 32*kf_words present in both
+// tiles contribute min(v_bi, v_bj) only for the rows that hold them.  A CTA of
+// 32 warps walks the windows of kRareWin positions: warp 0 lists the branches
+// present in both tiles and keeps the tiles' bitmap words and prefix
+// popcounts; all threads copy the two tiles' compact sparse blocks of the next
+// window into shared memory while the current one is processed (blocks
+// larger than the staging area are read in place); each warp takes branches,
+// finds their entries by popcount rank and walks the nI x nJ pairs, adding
+// round(min * 2^s) into a 128 x 128 shared accumulator of 32-bit integers
+// (2^s keeps every pair sum below 2^31; integer sums make the result
+// independent of the order of the atomics).  The accumulator goes to spart.
+
+constexpr int kSpThreads = 1024;
+constexpr int kStageBytes = 24 * 1024;  // one tile's block of one window
+constexpr size_t kSpSmem = (size_t)TILE * TILE * 4 + 4 * kStageBytes + 2 * sizeof(int32_t) * kRareWin;
+
+__global__ void __launch_bounds__(kSpThreads, 1)
+    k_pairs_weighted_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
+                            int32_t n_words, int32_t kf_words, int32_t n_win,
+                            const uint8_t *__restrict__ blocks,
+                            const unsigned long long *__restrict__ boff, float sp_scale,
+                            uint32_t *__restrict__ spart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *sacc = reinterpret_cast<uint32_t *>(smem_raw);
+  uint8_t *stage = smem_raw + (size_t)TILE * TILE * 4;  // [2 bufs][2 tiles][kStageBytes]
+  int32_t *lists = reinterpret_cast<int32_t *>(stage + 4 * kStageBytes);  // [2][kRareWin]
+  __shared__ uint32_t swI[2][kWinWords], swJ[2][kWinWords];
+  __shared__ int32_t spI[2][kWinWords], spJ[2][kWinWords];
+  __shared__ int32_t list_n[2];
+  __shared__ unsigned long long boI[2], boJ[2];
+  __shared__ int32_t inI[2], inJ[2];  // 1 = block staged in shared memory
+
+  const WorkItem it = items[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
+  const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
+  for (int x = tid; x < TILE * TILE; x += kSpThreads) sacc[x] = 0u;
+
+  auto prepare = [&](int j, int buf) {
+    const int w0 = kf_words + j * kWinWords;
+    if (warp == 0) {
+      build_window(bI, bJ, n_words, w0, lists + buf * kRareWin, &list_n[buf]);
+      const int w = w0 + lane;
+      const uint32_t mi = (w < n_words) ? bI[w] : 0u, mj = (w < n_words) ? bJ[w] : 0u;
+      swI[buf][lane] = mi;
+      swJ[buf][lane] = mj;
+      int ci = __popc(mi), cj = __popc(mj);
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int yi = __shfl_up_sync(0xffffffffu, ci, off);
+        const int yj = __shfl_up_sync(0xffffffffu, cj, off);
+        if (lane >= off) {
+          ci += yi;
+          cj += yj;
+        }
+      }
+      spI[buf][lane] = ci - __popc(mi);
+      spJ[buf][lane] = cj - __popc(mj);
+    }
+    const int64_t itemI = (int64_t)it.tile_i * n_win + j, itemJ = (int64_t)it.tile_j * n_win + j;
+    const unsigned long long oI = boff[itemI], oJ = boff[itemJ];
+    const uint32_t zI = (uint32_t)(boff[itemI + 1] - oI), zJ = (uint32_t)(boff[itemJ + 1] - oJ);
+    if (tid == 0) {
+      boI[buf] = oI;
+      boJ[buf] = oJ;
+      inI[buf] = zI <= kStageBytes;
+      inJ[buf] = zJ <= kStageBytes;
+    }
+    uint8_t *dI = stage + (size_t)(2 * buf) * kStageBytes, *dJ = dI + kStageBytes;
+    if (zI <= kStageBytes)
+      for (uint32_t c = tid; c < zI / 16; c += kSpThreads) cp_async16(dI + 16 * c, blocks + oI + 16 * c);
+    if (zJ <= kStageBytes)
+      for (uint32_t c = tid; c < zJ / 16; c += kSpThreads) cp_async16(dJ + 16 * c, blocks + oJ + 16 * c);
+  };
+
+  if (n_win > 0) {
+    prepare(0, 0);
+    cp_commit();
+  }
+  for (int j = 0; j < n_win; ++j) {
+    const int buf = j & 1;
+    if (j + 1 < n_win) {
+      prepare(j + 1, buf ^ 1);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const uint8_t *blkI = inI[buf] ? stage + (size_t)(2 * buf) * kStageBytes : blocks + boI[buf];
+    const uint8_t *blkJ =
+        inJ[buf] ? stage + (size_t)(2 * buf + 1) * kStageBytes : blocks + boJ[buf];
+    const uint32_t *hI = reinterpret_cast<const uint32_t *>(blkI);
+    const uint32_t *hJ = reinterpret_cast<const uint32_t *>(blkJ);
+    const uint32_t *rsI = hI + 4, *rsJ = hJ + 4;
+    const uint8_t *riI = blkI + hI[2], *riJ = blkJ + hJ[2];
+    const float *vI = reinterpret_cast<const float *>(blkI + hI[3]);
+    const float *vJ = reinterpret_cast<const float *>(blkJ + hJ[3]);
+    const int32_t *list = lists + buf * kRareWin;
+    const int n = list_n[buf];
+    const int wbase = (kf_words + j * kWinWords) * WORD;
+    for (int e = warp; e < n; e += kSpThreads / 32) {
+      const int q = list[e] - wbase;  // position inside the window
+      const int wq = q >> 5;
+      const uint32_t below = (1u << (q & 31)) - 1u;
+      const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
+      const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
+      const uint32_t sI = rsI[rI], sJ = rsJ[rJ];
+      const int nI = (int)(rsI[rI + 1] - sI), nJ = (int)(rsJ[rJ + 1] - sJ);
+      const int total = nI * nJ;
+      if (total > 0) {
+        // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
+        int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
+        const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
+        for (int p = lane; p < total; p += 32) {
+          const float mv = fminf(vI[sI + a], vJ[sJ + bb]);
+          atomicAdd(&sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]],
+                    __float2uint_rn(mv * sp_scale));
+          a += da;
+          bb += db;
+          if (bb >= nJ) {
+            bb -= nJ;
+            ++a;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  uint4 *dst = reinterpret_cast<uint4 *>(spart + (int64_t)blockIdx.x * TILE * TILE);
+  const uint4 *src = reinterpret_cast<const uint4 *>(sacc);
+  for (int x = tid; x < TILE * TILE / 4; x += kSpThreads) dst[x] = src[x];
 }
 
 // ----------------------------------------------------------------------------
@@ -502,12 +543,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
                    int32_t kf_words, const uint8_t *blocks, const unsigned long long *boff,
-                   int32_t n_win, const double *S, const WorkItem *items, int32_t n_items,
-                   const OutSpec &o) {
+                   int32_t n_win, uint32_t *spart, const double *S, const WorkItem *items,
+                   int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const size_t elem = f64 ? sizeof(double) : sizeof(float);
-  size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
+  const size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
   cudaError_t e;
   if (f64) {
     e = cudaFuncSetAttribute(k_pairs_weighted<double>,
@@ -515,18 +556,27 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
-        nullptr, 0, 1.0f, 1.0, S, 0, o, ctx->d_counter);
+        1.0, S, 0, o, ctx->d_counter);
+    ctx->stat_launches += 1;
   } else {
-    if (kf_words < n_words) smem += kSparseBytes;
+    const bool sparse = n_win > 0;
+    if (sparse) {
+      e = cudaFuncSetAttribute(k_pairs_weighted_sparse,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
+      k_pairs_weighted_sparse<<<n_items, kSpThreads, kSpSmem, ctx->stream>>>(
+          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, spart);
+      ctx->stat_launches += 1;
+    }
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words, blocks,
-        boff, n_win, ctx->sp_scale, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
+        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
+        sparse ? spart : nullptr, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
         ctx->d_counter);
+    ctx->stat_launches += 1;
   }
-  ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted pair kernel");
   return UNIFRAC_OK;

@@ -118,9 +118,24 @@ struct unifrac_ctx {
   int64_t opt_sparse_threshold = -1;  // presence count below which a branch runs sparse
   float sp_scale = 1.0f;              // fixed-point scale of the sparse sums (power of 2)
 
+  // ---- cached work list (depends on layout and stripe range only)
+  bool items_valid = false;
+  int items_layout = -1;
+  int32_t items_s0 = 0, items_s1 = 0, n_items = 0;
+
+  // ---- CUDA graph of the last run (UNIFRAC_OPT_USE_GRAPH)
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int gk_variant = -1, gk_precision = -1, gk_layout = -1;
+  int32_t gk_s0 = 0, gk_s1 = 0;
+  void *gk_dst = nullptr;
+  int64_t gk_opts = -1, opt_generation = 0, gk_bufs = -1, buf_generation = 0;
+  double graph_launches = 0;
+
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
-      rc, bsize, boff, blocks;
+      rc, bsize, boff, blocks, spart;
   size_t device_bytes = 0;
 };
 
@@ -159,10 +174,12 @@ int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
             uint16_t *X, uint16_t *D, uint32_t *kbits, double *a);
 
 // pair kernels ------------------------------------------------------------
+// spart: [n_items][TILE * TILE] u32 partial sums of the sparse kernel.
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
                    const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
-                   const unsigned long long *boff, int32_t n_win, const double *S,
-                   const WorkItem *items, int32_t n_items, const OutSpec &o);
+                   const unsigned long long *boff, int32_t n_win, uint32_t *spart,
+                   const double *S, const WorkItem *items, int32_t n_items,
+                   const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);

@@ -285,6 +285,38 @@ def test_unweighted_mixed_kernel_choice(small, kernel):
     check_full(got, ref[ub.UNWEIGHTED], ub.MIXED)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_graph_replay_matches_eager(small, variant):
+    """With CUDA-graph replay on, the first run executes eagerly and captures;
+    later identical runs replay the graph.  Results must be bit-identical, and
+    a change of layout, option or output buffer must not replay a stale graph."""
+    import torch
+    w, ref = small
+    N = w.table.n_samples
+    with ub.Context(w.tree, w.table) as ctx:
+        eager = ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED).cpu().numpy()
+        ctx.set_option(ub.OPT_USE_GRAPH, 1)
+        out = torch.full((N * (N - 1) // 2,), -1.0, device="cuda")
+        for rep in range(3):
+            out.fill_(-1.0)
+            ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED, out=out)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), eager)
+        full = ctx.run(variant, ub.MIXED, ub.OUT_FULL)
+        full2 = ctx.run(variant, ub.MIXED, ub.OUT_FULL, out=full.clone().fill_(-1.0))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(full.cpu().numpy(), full2.cpu().numpy())
+        check_full(full.cpu().numpy().reshape(N, N).astype(np.float64), ref[variant], ub.MIXED)
+        other = 1 - variant
+        o2 = ctx.run(other, ub.MIXED, ub.OUT_CONDENSED)
+        check_full(condensed_to_full(o2.cpu().numpy().astype(np.float64), N), ref[other], ub.MIXED)
+        ctx.set_option(ub.OPT_SPARSE_THRESHOLD, 7)
+        o3 = ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED, out=out)
+        o3 = ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED, out=out)
+        torch.cuda.synchronize()
+        check_full(condensed_to_full(o3.cpu().numpy().astype(np.float64), N), ref[variant], ub.MIXED)
+
+
 def test_repeat_runs_bit_identical(small):
     w, _ = small
     for v in VARIANTS:
@@ -312,3 +344,22 @@ def test_run_argument_errors(small):
             ub.unifrac_run(ctx.handle, 7, ub.MIXED, 0, -1, ub.OUT_FULL,
                            torch.zeros(w.table.n_samples ** 2, device="cuda"))
         assert ei.value.status == -1
+
+
+def test_autotune_and_cache(small, tmp_path):
+    """The tuner picks one of its candidates, caches it, and the tuned context
+    still matches the oracle; a second context reuses the cached setting."""
+    import torch
+    from paper_2107_05397_b300 import autotune
+    w, ref = small
+    N = w.table.n_samples
+    cache = str(tmp_path / "tune.json")
+    for variant in VARIANTS:
+        with ub.Context(w.tree, w.table) as ctx:
+            rec = autotune.tune(ctx, variant, ub.MIXED, cache_path=cache)
+            assert rec["cached"] is False
+            got = ctx.run(variant, ub.MIXED, ub.OUT_FULL).cpu().numpy().astype(np.float64)
+            check_full(got.reshape(N, N), ref[variant], ub.MIXED)
+        with ub.Context(w.tree, w.table) as ctx:
+            rec2 = autotune.tune(ctx, variant, ub.MIXED, cache_path=cache)
+            assert rec2["cached"] is True
