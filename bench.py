@@ -1,10 +1,10 @@
 #!/usr/bin/env python
 """Benchmark of the all-pairs UniFrac path on B300 GPUs.
 
-One step = the whole hot path over one synthetic study: the branch embedding
-(level-synchronous postorder sums), packing, and the pair kernels of BOTH
-variants (unweighted on tensor cores, weighted normalized on the CUDA cores),
-in mixed precision, writing the condensed N(N-1)/2 matrices.  The metric is
+One step = the whole hot path over one synthetic study, one C-ABI call: the
+branch embedding (level-synchronous postorder sums), packing, and the pair
+kernels of BOTH variants (unweighted on tensor cores, weighted normalized on
+the CUDA cores), in mixed precision, writing the condensed N(N-1)/2 matrices.  The metric is
 pair-branch updates per second: each variant counts C(N,2) * B, B the branches
 kept after pruning (observed below, non-zero length).
 
@@ -228,17 +228,16 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = ub.Context(w.tree, w.table, stream=stream)
     nb_cond = ctx.output_bytes(ub.MIXED, ub.OUT_CONDENSED)
-    out_uw = torch.empty(nb_cond // 4, dtype=torch.float32, device="cuda")
-    out_wn = torch.empty(nb_cond // 4, dtype=torch.float32, device="cuda")
+    out_both = torch.empty(2 * nb_cond // 4, dtype=torch.float32, device="cuda")
+    out_uw, out_wn = out_both[: nb_cond // 4], out_both[nb_cond // 4:]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     pair_branch = ctx.stat(ub.STAT_PAIR_BRANCH)
     units_per_step = 2.0 * pair_branch  # both variants
 
-    def step(precision=ub.MIXED, a=out_uw, b=out_wn):
-        ctx.run(ub.UNWEIGHTED, precision, ub.OUT_CONDENSED, out=a)
-        launches = ctx.stat(ub.STAT_KERNEL_LAUNCHES)
-        ctx.run(ub.WEIGHTED_NORMALIZED, precision, ub.OUT_CONDENSED, out=b)
-        return launches + ctx.stat(ub.STAT_KERNEL_LAUNCHES)
+    def step(precision=ub.MIXED, out=out_both):
+        # both variants from one embedding pass, one C-ABI call
+        ctx.run(ub.BOTH, precision, ub.OUT_CONDENSED, out=out)
+        return ctx.stat(ub.STAT_KERNEL_LAUNCHES)
 
     for _ in range(args.warmup):
         step()
@@ -326,21 +325,20 @@ def main():
 
     if rank == 0 and not args.no_fp64:
         # the plain FP64 path (lookup unweighted + FP64 weighted) on the same GPU
-        out64a = torch.empty(nb_cond // 2, dtype=torch.float64, device="cuda")
-        out64b = torch.empty(nb_cond // 2, dtype=torch.float64, device="cuda")
-        step(ub.FP64, out64a, out64b)
+        out64 = torch.empty(nb_cond, dtype=torch.float64, device="cuda")
+        step(ub.FP64, out64)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step(ub.FP64, out64a, out64b)
+        step(ub.FP64, out64)
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
         line["fp64_plain"] = {"ms_per_step": ms64,
                               "value": units_per_step / (ms64 / 1e3),
                               "mixed_speedup": ms64 / ms_per_step}
-        del out64a, out64b
+        del out64
 
     # end to end through the public API with host buffers
     if rank == 0 and not args.no_e2e:
@@ -348,15 +346,13 @@ def main():
         host_in = [pin(w.tree.parent), pin(w.tree.length), pin(w.table.feature_node),
                    pin(w.table.indptr), pin(w.table.indices), pin(w.table.counts)]
         h2d = int(sum(a.nbytes for a in host_in))
-        res_a = torch.empty(nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
-        res_b = torch.empty(nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
+        res = torch.empty(2 * nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
         e2e_t = []
         for rep in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = ub.unifrac_create(*host_in, n_samples=N, stream=stream)
-            ub.unifrac_run(h, ub.UNWEIGHTED, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res_a)
-            ub.unifrac_run(h, ub.WEIGHTED_NORMALIZED, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res_b)
+            ub.unifrac_run(h, ub.BOTH, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res)
             ub.unifrac_destroy(h)
             torch.cuda.synchronize()
             e2e_t.append(time.perf_counter() - t0)
@@ -364,8 +360,8 @@ def main():
         line["e2e"] = {"value": units_per_step / t_e2e, "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(2 * nb_cond),
                        "s_per_step": t_e2e,
-                       "includes": "create (validation, host prep, upload) + 2 runs + "
-                                   "D2H of both condensed matrices + destroy"}
+                       "includes": "create (validation, host prep, upload) + one run of both "
+                                   "variants + D2H of both condensed matrices + destroy"}
 
     if rank == 0 and not args.no_cpu_baseline:
         rng = np.random.default_rng(7)

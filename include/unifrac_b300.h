@@ -32,10 +32,14 @@ extern "C" {
 
 typedef struct unifrac_ctx unifrac_ctx; /* opaque */
 
-/* Which distance (Section II: "both unweighted and the weighted normalized"). */
+/* Which distance (Section II: "both unweighted and the weighted normalized").
+ * UNIFRAC_BOTH computes the two from one embedding pass; `out` then holds the
+ * unweighted result followed by the weighted one, each of
+ * unifrac_output_bytes(...) bytes. */
 enum unifrac_variant {
   UNIFRAC_UNWEIGHTED = 0,
-  UNIFRAC_WEIGHTED_NORMALIZED = 1
+  UNIFRAC_WEIGHTED_NORMALIZED = 1,
+  UNIFRAC_BOTH = 2
 };
 
 /* Arithmetic (Section II: "fp32 compute support").
@@ -123,7 +127,8 @@ int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
 /*
  * unifrac_run -- compute distances into `out`.
  *
- *  variant        enum unifrac_variant.
+ *  variant        enum unifrac_variant (UNIFRAC_BOTH: two results, one after
+ *                 the other in `out`).
  *  precision      enum unifrac_precision.
  *  stripe_start, stripe_stop
  *                 stripe range [start, stop); stop = -1 means "to the last
@@ -134,7 +139,8 @@ int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
  *  out            device pointer (enqueued on the context's stream, returns
  *                 before completion) or host pointer (staged through device
  *                 memory; the call returns after the copy has completed).
- *  out_bytes      capacity of `out`; must be >= unifrac_output_bytes(...).
+ *  out_bytes      capacity of `out`; must be >= unifrac_output_bytes(...)
+ *                 (twice that for UNIFRAC_BOTH).
  *
  * Pipeline (all on the device): embedding of every branch (level-synchronous
  * postorder sums, skipping all-zero branch tiles), packing for the chosen

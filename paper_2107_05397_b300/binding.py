@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libunifrac_
 
 UNWEIGHTED = 0
 WEIGHTED_NORMALIZED = 1
+BOTH = 2
 FP64 = 0
 MIXED = 1
 OUT_STRIPES = 0
@@ -249,6 +250,8 @@ class Context:
         if out is None:
             import torch
             nbytes = self.output_bytes(precision, layout, stripe_start, stripe_stop)
+            if variant == BOTH:
+                nbytes *= 2
             dt = torch.float64 if precision == FP64 else torch.float32
             out = torch.zeros(nbytes // (8 if precision == FP64 else 4), dtype=dt, device=device)
         unifrac_run(self.handle, variant, precision, stripe_start, stripe_stop, layout, out)

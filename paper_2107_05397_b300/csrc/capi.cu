@@ -645,8 +645,9 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
   return UNIFRAC_OK;
 }
 
-// Device work of one run on ctx->stream (no allocation, no host copy, no sync).
-static int enqueue_run(unifrac_ctx *ctx, const RunPlan &P) {
+// Device work of one variant after the embedding (no allocation, no host copy,
+// no sync).
+static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   int rc;
   cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
@@ -659,8 +660,6 @@ static int enqueue_run(unifrac_ctx *ctx, const RunPlan &P) {
   o.is_f64 = P.f64 ? 1 : 0;
   uint32_t *cnt = static_cast<uint32_t *>(ctx->cnt.p);
   uint8_t *flag = static_cast<uint8_t *>(ctx->flag.p);
-  cudaEventRecord(ctx->ev[0], ctx->stream);
-  if ((rc = embed_counts(ctx, cnt, flag))) return rc;
   const WorkItem *d_items = static_cast<const WorkItem *>(ctx->items.p);
   const int32_t n_items = P.n_items;
   const int variant = P.variant;
@@ -711,14 +710,27 @@ static int enqueue_run(unifrac_ctx *ctx, const RunPlan &P) {
   e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
                       cudaMemcpyDeviceToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
+  ctx->sel_unit_v[variant] = ctx->sel_unit;
+  return UNIFRAC_OK;
+}
+
+// The embedding once, then each variant's packing and pair kernels.
+static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
+  int rc;
+  cudaEventRecord(ctx->ev[0], ctx->stream);
+  if ((rc = embed_counts(ctx, static_cast<uint32_t *>(ctx->cnt.p),
+                         static_cast<uint8_t *>(ctx->flag.p))))
+    return rc;
+  for (int i = 0; i < n_plans; ++i)
+    if ((rc = enqueue_variant(ctx, plans[i]))) return rc;
   return UNIFRAC_OK;
 }
 
 // Graph replay of a captured run.  The legacy default stream cannot be
 // captured, so capture and replay use the context's private stream, ordered
 // after / before the caller's stream with events.
-static int graph_key_matches(const unifrac_ctx *ctx, const RunPlan &P) {
-  return ctx->graph_exec && ctx->gk_variant == P.variant && ctx->gk_precision == P.precision &&
+static int graph_key_matches(const unifrac_ctx *ctx, const RunPlan &P, int variant_arg) {
+  return ctx->graph_exec && ctx->gk_variant == variant_arg && ctx->gk_precision == P.precision &&
          ctx->gk_layout == P.layout && ctx->gk_s0 == P.s0 && ctx->gk_s1 == P.s1 &&
          ctx->gk_dst == P.dst && ctx->gk_opts == ctx->opt_generation &&
          ctx->gk_bufs == ctx->buf_generation;
@@ -734,7 +746,8 @@ static int graph_launch(unifrac_ctx *ctx) {
   return UNIFRAC_OK;
 }
 
-static int graph_capture(unifrac_ctx *ctx, const RunPlan &P) {
+static int graph_capture(unifrac_ctx *ctx, const RunPlan *plans, int n_plans, int variant_arg) {
+  const RunPlan &P = plans[0];
   cudaError_t e;
   if (!ctx->cap_stream) {
     e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
@@ -751,7 +764,7 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan &P) {
   ctx->stream = ctx->cap_stream;
   e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
   int rc = UNIFRAC_OK;
-  if (e == cudaSuccess) rc = enqueue_run(ctx, P);
+  if (e == cudaSuccess) rc = enqueue_run(ctx, plans, n_plans);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
   ctx->stream = user;
@@ -768,7 +781,7 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan &P) {
     ctx->graph_exec = nullptr;
     return cuda_fail(ctx, e, "graph instantiate");
   }
-  ctx->gk_variant = P.variant;
+  ctx->gk_variant = variant_arg;
   ctx->gk_precision = P.precision;
   ctx->gk_layout = P.layout;
   ctx->gk_s0 = P.s0;
@@ -781,38 +794,45 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan &P) {
 
 static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_start,
                     int32_t stripe_stop, int layout, void *out, size_t out_bytes) {
-  if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED)
+  if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED &&
+      variant != UNIFRAC_BOTH)
     return fail(ctx, UNIFRAC_E_INVALID_ARG, "variant");
   if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED)
     return fail(ctx, UNIFRAC_E_INVALID_ARG, "precision");
   if (layout < UNIFRAC_OUT_STRIPES || layout > UNIFRAC_OUT_FULL)
     return fail(ctx, UNIFRAC_E_INVALID_ARG, "layout");
+  const int n_plans = variant == UNIFRAC_BOTH ? 2 : 1;
   int32_t s0, s1;
   int rc = resolve_range(ctx, layout, stripe_start, stripe_stop, &s0, &s1);
   if (rc == UNIFRAC_E_UNSUPPORTED)
     return fail(ctx, rc, "several studies need layout CONDENSED or FULL and the range (0, -1)");
   if (rc) return fail(ctx, rc, "stripe range");
-  size_t need = 0;
-  unifrac_output_bytes(ctx, precision, layout, stripe_start, stripe_stop, &need);
+  size_t one = 0;
+  unifrac_output_bytes(ctx, precision, layout, stripe_start, stripe_stop, &one);
+  const size_t need = one * n_plans;
   if (need > 0 && !out) return fail(ctx, UNIFRAC_E_INVALID_ARG, "out is NULL");
   if (out_bytes < need)
     return fail(ctx, UNIFRAC_E_BUFFER_TOO_SMALL,
                 "out holds " + std::to_string(out_bytes) + " bytes, needs " + std::to_string(need));
-  RunPlan P;
-  P.variant = variant;
-  P.precision = precision;
-  P.layout = layout;
-  P.s0 = s0;
-  P.s1 = s1;
-  P.f64 = precision == UNIFRAC_FP64;
-  if (variant == UNIFRAC_WEIGHTED_NORMALIZED)
-    P.kind = RunPlan::WEIGHTED;
-  else if (!P.f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793)
-    // tensor-core Gram: exact while every plane sum stays below 2^24, i.e. while
-    // no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
-    P.kind = RunPlan::TENSOR;
-  else
-    P.kind = RunPlan::LOOKUP;
+  RunPlan plans[2];
+  for (int i = 0; i < n_plans; ++i) {
+    RunPlan &P = plans[i];
+    P.variant = variant == UNIFRAC_BOTH ? i : variant;
+    P.precision = precision;
+    P.layout = layout;
+    P.s0 = s0;
+    P.s1 = s1;
+    P.f64 = precision == UNIFRAC_FP64;
+    if (P.variant == UNIFRAC_WEIGHTED_NORMALIZED)
+      P.kind = RunPlan::WEIGHTED;
+    else if (!P.f64 && ctx->opt_uw_kernel != 2 && ctx->max_reach < 65793)
+      // tensor-core Gram: exact while every plane sum stays below 2^24, i.e.
+      // while no sample reaches 65,793 branches (255 * 65,793 >= 2^24)
+      P.kind = RunPlan::TENSOR;
+    else
+      P.kind = RunPlan::LOOKUP;
+  }
+  RunPlan &P = plans[0];
 
   // where does `out` live?
   bool device_out = false;
@@ -827,39 +847,46 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   }
   const bool whole = (layout == UNIFRAC_OUT_STRIPES) ||
                      (s0 == 0 && (ctx->n_studies > 1 || s1 == ctx->n_samples / 2));
-  P.dst = out;
+  void *dst = out;
   if (!device_out && need > 0) {
     if ((rc = grow(ctx, ctx->stage, need))) return rc;
-    P.dst = ctx->stage.p;
+    dst = ctx->stage.p;
   }
   if ((rc = plan_items(ctx, layout, s0, s1))) return rc;
-  P.n_items = ctx->n_items;
-  ctx->stat_tile_pairs = (double)P.n_items;
-  if ((rc = plan_buffers(ctx, P))) return rc;
+  ctx->stat_tile_pairs = (double)ctx->n_items;
+  for (int i = 0; i < n_plans; ++i) {
+    plans[i].dst = static_cast<char *>(dst) + (size_t)i * one;
+    plans[i].n_items = ctx->n_items;
+    if ((rc = plan_buffers(ctx, plans[i]))) return rc;
+  }
   if (!device_out && need > 0 && !whole) {  // untouched elements keep the caller's values
-    cudaError_t e = cudaMemcpyAsync(P.dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stage output");
   }
 
   const bool use_graph = ctx->opt_use_graph && device_out;
-  if (use_graph && graph_key_matches(ctx, P)) {
+  if (use_graph && graph_key_matches(ctx, P, variant)) {
     if ((rc = graph_launch(ctx))) return rc;
     ctx->stat_launches = ctx->graph_launches;
   } else {
     ctx->stat_launches = 0;
-    if ((rc = enqueue_run(ctx, P))) return rc;
+    if ((rc = enqueue_run(ctx, plans, n_plans))) return rc;
     if (use_graph) {  // this run executed eagerly; later identical runs replay the graph
       ctx->graph_launches = ctx->stat_launches;
-      if ((rc = graph_capture(ctx, P))) return rc;
+      if ((rc = graph_capture(ctx, plans, n_plans, variant))) return rc;
     }
   }
-  ctx->sel_unit_v[variant] = ctx->sel_unit;
+  for (int i = 0; i < n_plans; ++i) {
+    ctx->sel_unit_v[plans[i].variant] = plans[i].kind == RunPlan::WEIGHTED ? 1.0
+                                        : plans[i].kind == RunPlan::TENSOR ? 64.0
+                                                                           : 8.0;
+    ctx->ev_pair_valid[plans[i].variant] = true;
+  }
   ctx->ev_valid = true;
-  ctx->ev_pair_valid[variant] = true;
 
   cudaError_t e;
   if (!device_out && need > 0) {
-    e = cudaMemcpyAsync(out, P.dst, need, cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");

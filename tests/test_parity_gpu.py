@@ -32,7 +32,7 @@ def run(tree, table, variant, precision, layout=ub.OUT_FULL, s0=0, s1=-1, host=F
         for k, v in (options or {}).items():
             ctx.set_option(k, v)
         if host:
-            nbytes = ctx.output_bytes(precision, layout, s0, s1)
+            nbytes = ctx.output_bytes(precision, layout, s0, s1) * (2 if variant == ub.BOTH else 1)
             out = np.zeros(nbytes // (8 if precision == ub.FP64 else 4),
                            np.float64 if precision == ub.FP64 else np.float32)
             ctx.run(variant, precision, layout, s0, s1, out=out)
@@ -363,3 +363,17 @@ def test_autotune_and_cache(small, tmp_path):
         with ub.Context(w.tree, w.table) as ctx:
             rec2 = autotune.tune(ctx, variant, ub.MIXED, cache_path=cache)
             assert rec2["cached"] is True
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("layout", [ub.OUT_CONDENSED, ub.OUT_FULL, ub.OUT_STRIPES])
+def test_both_variants_in_one_run(small, precision, layout):
+    """UNIFRAC_BOTH (one embedding pass) equals the two single-variant runs."""
+    w, _ = small
+    with ub.Context(w.tree, w.table) as ctx:
+        both = ctx.run(ub.BOTH, precision, layout).cpu().numpy()
+        uw = ctx.run(ub.UNWEIGHTED, precision, layout).cpu().numpy()
+        wn = ctx.run(ub.WEIGHTED_NORMALIZED, precision, layout).cpu().numpy()
+    np.testing.assert_array_equal(both, np.concatenate([uw, wn]))
+    host = run(w.tree, w.table, ub.BOTH, precision, layout, host=True)
+    np.testing.assert_array_equal(host, np.concatenate([uw, wn]).astype(np.float64))
