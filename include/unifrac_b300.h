@@ -178,9 +178,12 @@ enum unifrac_option {
                                               work queue (default for many studies) */
   UNIFRAC_OPT_CTAS_PER_SM = 3,            /* persistent grid = SMs x this, 1..8 */
   UNIFRAC_OPT_USE_GRAPH = 4,              /* 1 = capture the level loop in a CUDA graph */
-  UNIFRAC_OPT_SPARSE_THRESHOLD = 5        /* weighted mixed kernel: branches present in fewer
+  UNIFRAC_OPT_SPARSE_THRESHOLD = 5,       /* weighted mixed kernel: branches present in fewer
                                               samples than this run through the sparse phase;
                                               -1 auto (largest study / 4), 0 all dense */
+  UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6 /* unweighted tensor-core kernel: same split;
+                                              -1 auto (largest study / 4 above 8,192
+                                              samples, else all tensor core), 0 all tensor */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
@@ -190,7 +193,8 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * for this context by timing candidates on the device, and keep the fastest
  * as the context's options.  Candidates: the dense / sparse split of the
  * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
- * largest study) and the unweighted mixed kernel (tensor core or lookup).
+ * largest study) and of the unweighted tensor-core kernel
+ * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/8 .. 1/2).
  * Each candidate runs `repeats` times (>= 1, after one warm-up run) into
  * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
  * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the

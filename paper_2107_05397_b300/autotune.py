@@ -65,8 +65,10 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
         rec = cache[key]
         if "sparse_fraction" in rec:
             ctx.set_option(ub.OPT_SPARSE_THRESHOLD, max(2, int(round(rec["sparse_fraction"] * n))))
-        if "unweighted_kernel" in rec:
-            ctx.set_option(ub.OPT_UNWEIGHTED_MIXED_KERNEL, rec["unweighted_kernel"])
+        if "uw_sparse_fraction" in rec:
+            f = rec["uw_sparse_fraction"]
+            ctx.set_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD,
+                           0 if f == 0 else max(2, int(round(f * n))))
         return dict(rec, cached=True)
     nbytes = ctx.output_bytes(precision, ub.OUT_CONDENSED)
     out = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device="cuda")
@@ -82,7 +84,7 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
     if variant == ub.WEIGHTED_NORMALIZED and precision == ub.MIXED:
         rec["sparse_fraction"] = get_option(ctx, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)
     if variant == ub.UNWEIGHTED and precision == ub.MIXED:
-        rec["unweighted_kernel"] = get_option(ctx, ub.OPT_UNWEIGHTED_MIXED_KERNEL)
+        rec["uw_sparse_fraction"] = get_option(ctx, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD) / max(n, 1)
     if cache_path:
         cache[key] = rec
         tmp = cache_path + ".tmp"

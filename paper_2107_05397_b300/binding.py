@@ -31,6 +31,7 @@ OPT_PERSISTENT = 2
 OPT_CTAS_PER_SM = 3
 OPT_USE_GRAPH = 4
 OPT_SPARSE_THRESHOLD = 5
+OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1

@@ -87,13 +87,14 @@ void free_ctx(unifrac_ctx *ctx) {
   void *ptrs[] = {ctx->d_level_nodes, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
                   ctx->d_frow_ptr,    ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_col_ptr,     ctx->d_col_cnt,   ctx->d_col_depth, ctx->d_perm,
-                  ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter};
+                  ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
                          &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
                          &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->rc,
-                         &ctx->bsize,   &ctx->boff,      &ctx->blocks, &ctx->spart};
+                         &ctx->bsize,   &ctx->boff,      &ctx->blocks, &ctx->spart,
+                         &ctx->rbits};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &e : ctx->ev)
@@ -457,6 +458,13 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   if ((rc = upload(ctx, &ctx->d_perm, perm))) return rc;
   if ((rc = upload(ctx, &ctx->d_len_perm, len_perm))) return rc;
   if ((rc = upload(ctx, &ctx->d_digits, digits))) return rc;
+  {
+    std::vector<uint32_t> qperm(ctx->K_pad, 0u);
+    for (int32_t k = 0; k < ctx->K; ++k)
+      qperm[k] = ((uint32_t)digits[k] << 16) | ((uint32_t)digits[ctx->K_pad + k] << 8) |
+                 (uint32_t)digits[2 * (size_t)ctx->K_pad + k];
+    if ((rc = upload(ctx, &ctx->d_qperm, qperm))) return rc;
+  }
   std::vector<unsigned long long> zero4(4, 0ull);
   if ((rc = upload(ctx, &ctx->d_counter, zero4))) return rc;
   for (auto &ev : ctx->ev) {
@@ -546,6 +554,7 @@ struct RunPlan {
   bool f64;
   enum Kind { WEIGHTED, TENSOR, LOOKUP } kind;
   int32_t kf_words = 0, n_win = 0;
+  int32_t k_tc = 0;  // tensor-core positions (TENSOR)
   void *dst = nullptr;
   int32_t n_items = 0;
 };
@@ -625,14 +634,41 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
         return rc;
     }
   } else if (P.kind == RunPlan::TENSOR) {
-    const int32_t n_kt = ctx->K_pad / 64;
+    // positions [0, k_tc) on the tensor cores, the rarely present rest sparse
+    int64_t th = ctx->opt_uw_sparse_threshold;
+    if (th < 0) th = ctx->max_study_n > 8192 ? ctx->max_study_n / 4 : 0;
+    int32_t kf = ctx->K;
+    if (th > 0) {
+      kf = 0;
+      while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
+    }
+    P.k_tc = std::min<int32_t>(ctx->K_pad, std::max<int32_t>(64, (kf + 63) / 64 * 64));
+    const int32_t n_words = ctx->K_pad / WORD;
+    P.kf_words = P.k_tc / WORD;
+    P.n_win = P.k_tc >= ctx->K ? 0 : (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    const int32_t n_kt = P.k_tc / 64;
     const int32_t k_words = (n_kt + 31) / 32;
-    const size_t plane = (size_t)ctx->n_cols * ctx->K_pad * 2;
+    const size_t plane = (size_t)ctx->n_cols * P.k_tc * 2;
     if ((rc = grow(ctx, ctx->vals, plane))) return rc;
     if ((rc = grow(ctx, ctx->vals2, 3 * plane))) return rc;
     if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
     if ((rc = grow(ctx, ctx->partial, (size_t)ctx->n_cols * 8))) return rc;
     if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    if (P.n_win > 0) {
+      uint64_t rows = 0, ents = 0;
+      for (int32_t k = P.kf_words * WORD; k < ctx->K; ++k) {
+        rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
+        ents += (uint64_t)ctx->nb_perm[k];
+      }
+      const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
+      const uint64_t bound = nblk * 80 + 4 * rows + ents + 64;
+      if ((rc = grow(ctx, ctx->rbits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
+      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
+      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
+      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
+      if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 8))) return rc;
+    }
   } else {
     const int32_t G = ctx->K_pad / 8;
     const int32_t g_words = (G + WORD - 1) / WORD;
@@ -670,7 +706,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
     if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, rcb, P.kf_words * WORD, S)))
       return rc;
     if (P.n_win > 0 &&
-        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), bits, rcb,
+        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), nullptr, bits, rcb,
                                 P.kf_words, P.n_win, static_cast<uint32_t *>(ctx->bsize.p),
                                 static_cast<unsigned long long *>(ctx->boff.p),
                                 static_cast<uint8_t *>(ctx->blocks.p))))
@@ -689,11 +725,33 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
     uint16_t *D = static_cast<uint16_t *>(ctx->vals2.p);
     uint32_t *kbits = static_cast<uint32_t *>(ctx->bits.p);
     double *a = static_cast<double *>(ctx->persample.p);
-    if ((rc = pack_tc(ctx, cnt, flag, X, D, kbits, a))) return rc;
+    unsigned long long *aq = static_cast<unsigned long long *>(ctx->partial.p);
+    e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear per-sample sums");
+    if ((rc = pack_tc(ctx, cnt, flag, P.k_tc, X, D, kbits, aq))) return rc;
+    unsigned long long *spart = nullptr;
+    if (P.n_win > 0) {
+      uint32_t *rbits = static_cast<uint32_t *>(ctx->rbits.p);
+      uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
+      if ((rc = pack_rare_presence(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
+      if ((rc = build_rare_blocks(ctx, nullptr, cnt, rbits, rcb, P.kf_words, P.n_win,
+                                  static_cast<uint32_t *>(ctx->bsize.p),
+                                  static_cast<unsigned long long *>(ctx->boff.p),
+                                  static_cast<uint8_t *>(ctx->blocks.p))))
+        return rc;
+      spart = static_cast<unsigned long long *>(ctx->spart.p);
+    }
+    if ((rc = finish_tc_a(ctx, aq, a))) return rc;
     cudaEventRecord(ctx->ev[1], ctx->stream);
     cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
     ctx->sel_unit = 64.0;
-    if ((rc = pairs_tc(ctx, X, D, kbits, a, d_items, n_items, o))) return rc;
+    if (spart &&
+        (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(ctx->rbits.p), P.kf_words,
+                                    static_cast<const uint8_t *>(ctx->blocks.p),
+                                    static_cast<const unsigned long long *>(ctx->boff.p),
+                                    P.n_win, spart, d_items, n_items)))
+      return rc;
+    if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, a, spart, d_items, n_items, o))) return rc;
   } else {
     double *a = static_cast<double *>(ctx->persample.p);
     uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
@@ -938,6 +996,10 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < -1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_sparse_threshold = value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
+      if (value < -1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_uw_sparse_threshold = value;
+      return UNIFRAC_OK;
     default:
       return UNIFRAC_E_INVALID_ARG;
   }
@@ -952,6 +1014,9 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
     case UNIFRAC_OPT_CTAS_PER_SM: *value = ctx->opt_ctas_per_sm; return UNIFRAC_OK;
     case UNIFRAC_OPT_USE_GRAPH: *value = ctx->opt_use_graph; return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
+    case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
+      *value = ctx->opt_uw_sparse_threshold;
+      return UNIFRAC_OK;
     default: return UNIFRAC_E_INVALID_ARG;
   }
 }
@@ -971,9 +1036,10 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
     const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
     for (int64_t num : {1, 2, 4, 8, 12}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
   } else {
-    option = UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL;
-    cands.push_back({option, 1});
-    cands.push_back({option, 2});
+    option = UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD;
+    const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
+    cands.push_back({option, 0});  // everything on the tensor cores
+    for (int64_t num : {2, 4, 8}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
   }
   const int saved_graph = ctx->opt_use_graph;
   ctx->opt_use_graph = 0;

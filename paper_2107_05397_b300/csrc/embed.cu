@@ -252,6 +252,8 @@ __global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
 
 __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
+// VALUES = false (presence blocks): no value section.
+template <bool VALUES>
 __global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                              const uint32_t *__restrict__ bits, int32_t n_words,
                              const uint8_t *__restrict__ rc, int32_t k_pad,
@@ -279,7 +281,7 @@ __global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t
   if (lane == 0) {
     const uint32_t off_ri = align16(16u + 4u * (nrows + 1u));
     const uint32_t off_val = align16(off_ri + nent);
-    bsize[item] = align16(off_val + 4u * nent);
+    bsize[item] = VALUES ? align16(off_val + 4u * nent) : off_val;
   }
 }
 
@@ -311,10 +313,14 @@ __global__ void __launch_bounds__(1024) k_scan_sizes(int64_t n, const uint32_t *
 
 // Fill one block per warp: rows in position order; each row's non-zero
 // columns are compacted with four ballots (column 4l + w of lane l).
+// VALUES: entries carry v from vals[k][col]; otherwise presences read from the
+// counts cnt[perm[k]][col] (no value section).
+template <bool VALUES>
 __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                             const uint32_t *__restrict__ bits, int32_t n_words,
                             const uint8_t *__restrict__ rc, int32_t k_pad,
                             const float *__restrict__ vals, int64_t ldv,
+                            const uint32_t *__restrict__ cnt, const int32_t *__restrict__ perm,
                             const unsigned long long *__restrict__ boff,
                             uint8_t *__restrict__ blocks) {
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -385,9 +391,16 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         v[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (src[g] >= 0)
-          v[g] = *reinterpret_cast<const float4 *>(
-              vals + (int64_t)(kb + 32 * s + src[g]) * ldv + t * TILE + 4 * lane);
+        if (src[g] >= 0) {
+          const int64_t k = kb + 32 * s + src[g];
+          if constexpr (VALUES) {
+            v[g] = *reinterpret_cast<const float4 *>(vals + k * ldv + t * TILE + 4 * lane);
+          } else {
+            const uint4 c = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[k] * ldv +
+                                                             t * TILE + 4 * lane);
+            v[g] = make_float4(c.x ? 1.f : 0.f, c.y ? 1.f : 0.f, c.z ? 1.f : 0.f, c.w ? 1.f : 0.f);
+          }
+        }
       }
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
@@ -406,7 +419,7 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
         for (int w = 0; w < 4; ++w)
           if (vv[w] != 0.f) {
             ri[base + pos[w]] = (uint8_t)(4 * lane + w);
-            val[base + pos[w]] = vv[w];
+            if constexpr (VALUES) val[base + pos[w]] = vv[w];
           }
       }
       (void)nb;
@@ -416,22 +429,97 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
   }
 }
 
+// Presence packing of the rarely present positions [p0, K) for the unweighted
+// sparse kernel.  Block (column tile t, KR positions), warp per position: the
+// row's non-zero count rc, the (t, position) bitmap words (positions below p0
+// are never read) and aq[col] += q_k for every column where branch k is present.
+__global__ void __launch_bounds__(256) k_pack_rare_presence(
+    int32_t K, int32_t p0, const int32_t *__restrict__ perm, const uint32_t *__restrict__ qperm,
+    const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
+    int32_t n_tiles, uint32_t *__restrict__ bits, int32_t n_words, uint8_t *__restrict__ rc,
+    int32_t k_pad, unsigned long long *__restrict__ aq) {
+  __shared__ unsigned long long red[kWarpsPerBlock][TILE];
+  const int t = blockIdx.x;
+  const int k0 = p0 + blockIdx.y * KR;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t col = (int64_t)t * TILE + lane * 4;
+  const int k1 = min(k0 + KR, K);
+  unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+  for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
+    const int32_t b = perm[k];
+    if (!flag[(int64_t)b * n_tiles + t]) continue;
+    const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
+    const unsigned long long q = qperm[k];
+    acc[0] += c.x ? q : 0ull;
+    acc[1] += c.y ? q : 0ull;
+    acc[2] += c.z ? q : 0ull;
+    acc[3] += c.w ? q : 0ull;
+    const int nz = __popc(__ballot_sync(0xffffffffu, c.x != 0u)) +
+                   __popc(__ballot_sync(0xffffffffu, c.y != 0u)) +
+                   __popc(__ballot_sync(0xffffffffu, c.z != 0u)) +
+                   __popc(__ballot_sync(0xffffffffu, c.w != 0u));
+    if (lane == 0) rc[(int64_t)t * k_pad + k] = (uint8_t)nz;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[w][lane * 4 + q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    unsigned long long sum = 0;
+    for (int ww = 0; ww < kWarpsPerBlock; ++ww) sum += red[ww][threadIdx.x];
+    if (sum) atomicAdd(aq + (int64_t)t * TILE + threadIdx.x, sum);
+  }
+  // bitmap words of this block (k0 is a multiple of 32)
+  if (threadIdx.x < KR / WORD) {
+    const int kw = k0 + threadIdx.x * WORD;
+    uint32_t word = 0;
+    for (int j = 0; j < WORD; ++j) {
+      const int k = kw + j;
+      if (k < K && flag[(int64_t)perm[k] * n_tiles + t]) word |= 1u << j;
+    }
+    if (kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
+  }
+}
+
 }  // namespace
 
-int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *bits,
-                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint8_t *blocks) {
+int pack_rare_presence(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
+                       int32_t kf_words, uint32_t *bits, uint8_t *rc, unsigned long long *aq) {
+  const int32_t p0 = kf_words * WORD;
+  if (p0 >= ctx->K || ctx->n_tiles == 0) return UNIFRAC_OK;
+  dim3 grid(ctx->n_tiles, (ctx->K - p0 + KR - 1) / KR);
+  k_pack_rare_presence<<<grid, 256, 0, ctx->stream>>>(
+      ctx->K, p0, ctx->d_perm, ctx->d_qperm, cnt, flag, ctx->n_cols, ctx->n_tiles, bits,
+      ctx->K_pad / WORD, rc, ctx->K_pad, aq);
+  ctx->stat_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "presence packing");
+  return UNIFRAC_OK;
+}
+
+int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *cnt,
+                      const uint32_t *bits, const uint8_t *rc, int32_t kf_words, int32_t n_win,
+                      uint32_t *bsize, unsigned long long *boff, uint8_t *blocks) {
   cudaStream_t st = ctx->stream;
   const int64_t items = (int64_t)ctx->n_tiles * n_win;
   if (items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const int32_t p0 = kf_words * WORD;
   const unsigned grid = (unsigned)((items * 32 + 255) / 256);
-  k_rare_sizes<<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                     ctx->K_pad, bsize);
-  k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
-  k_rare_fill<<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                    ctx->K_pad, vals, ctx->n_cols, boff, blocks);
+  if (vals) {
+    k_rare_sizes<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                             ctx->K_pad, bsize);
+    k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
+    k_rare_fill<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                            ctx->K_pad, vals, ctx->n_cols, nullptr, nullptr,
+                                            boff, blocks);
+  } else {
+    k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                              ctx->K_pad, bsize);
+    k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
+    k_rare_fill<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+                                             ctx->K_pad, nullptr, ctx->n_cols, cnt, ctx->d_perm,
+                                             boff, blocks);
+  }
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse blocks");

@@ -22,6 +22,8 @@
 // and the lookup form evaluates G_ij 8 branches at a time from a byte of
 // presence bits: G_ij = sum_g T_g[x_gi AND x_gj], T_g[m] = sum of the lengths
 // of the branches whose bits are set in m.
+#include <type_traits>
+
 #include "epilogue.cuh"
 
 namespace ufb {
@@ -145,7 +147,7 @@ struct MinAcc<double> {
 //
 // Hybrid split (FP32 form): positions [0, 32*kf_words) are the frequently
 // present branches and run through the dense register tile here; the rest,
-// present in few samples, were summed by k_pairs_weighted_sparse into spart
+// present in few samples, were summed by k_pairs_sparse<false> into spart
 // (per tile pair, 32-bit fixed point, scale 1 / sp_inv), added in the epilogue.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -292,18 +294,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 // independent of the order of the atomics).  The accumulator goes to spart.
 
 constexpr int kSpThreads = 1024;
-constexpr int kStageBytes = 24 * 1024;  // one tile's block of one window
-constexpr size_t kSpSmem = (size_t)TILE * TILE * 4 + 4 * kStageBytes + 2 * sizeof(int32_t) * kRareWin;
 
+// PRES = false: weighted form, entries carry v; adds round(min(v_i, v_j) * 2^s)
+//               into 32-bit accumulators (spart: u32 per pair).
+// PRES = true:  unweighted form, entries are presences; adds the branch's
+//               24-bit length q[k] into 64-bit accumulators (spart: u64 per
+//               pair), exact -- the tensor-core epilogue adds it to its digit sums.
+template <bool PRES>
+struct SparseCfg {
+  using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
+  static constexpr int kStage = PRES ? 16 * 1024 : 24 * 1024;  // one tile's block
+  static constexpr size_t kSmem =
+      (size_t)TILE * TILE * sizeof(Acc) + 4 * kStage + 2 * sizeof(int32_t) * kRareWin;
+};
+
+template <bool PRES>
 __global__ void __launch_bounds__(kSpThreads, 1)
-    k_pairs_weighted_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
-                            int32_t n_words, int32_t kf_words, int32_t n_win,
-                            const uint8_t *__restrict__ blocks,
-                            const unsigned long long *__restrict__ boff, float sp_scale,
-                            uint32_t *__restrict__ spart) {
+    k_pairs_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
+                   int32_t n_words, int32_t kf_words, int32_t n_win,
+                   const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
+                   float sp_scale, const uint32_t *__restrict__ qlen,
+                   typename SparseCfg<PRES>::Acc *__restrict__ spart) {
+  using Acc = typename SparseCfg<PRES>::Acc;
+  constexpr int kStageBytes = SparseCfg<PRES>::kStage;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t *sacc = reinterpret_cast<uint32_t *>(smem_raw);
-  uint8_t *stage = smem_raw + (size_t)TILE * TILE * 4;  // [2 bufs][2 tiles][kStageBytes]
+  Acc *sacc = reinterpret_cast<Acc *>(smem_raw);
+  uint8_t *stage = smem_raw + (size_t)TILE * TILE * sizeof(Acc);  // [2 bufs][2 tiles][kStageBytes]
   int32_t *lists = reinterpret_cast<int32_t *>(stage + 4 * kStageBytes);  // [2][kRareWin]
   __shared__ uint32_t swI[2][kWinWords], swJ[2][kWinWords];
   __shared__ int32_t spI[2][kWinWords], spJ[2][kWinWords];
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
   const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
-  for (int x = tid; x < TILE * TILE; x += kSpThreads) sacc[x] = 0u;
+  for (int x = tid; x < TILE * TILE; x += kSpThreads) sacc[x] = Acc(0);
 
   auto prepare = [&](int j, int buf) {
     const int w0 = kf_words + j * kWinWords;
@@ -344,13 +360,13 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     if (tid == 0) {
       boI[buf] = oI;
       boJ[buf] = oJ;
-      inI[buf] = zI <= kStageBytes;
-      inJ[buf] = zJ <= kStageBytes;
+      inI[buf] = zI <= (uint32_t)kStageBytes;
+      inJ[buf] = zJ <= (uint32_t)kStageBytes;
     }
     uint8_t *dI = stage + (size_t)(2 * buf) * kStageBytes, *dJ = dI + kStageBytes;
-    if (zI <= kStageBytes)
+    if (zI <= (uint32_t)kStageBytes)
       for (uint32_t c = tid; c < zI / 16; c += kSpThreads) cp_async16(dI + 16 * c, blocks + oI + 16 * c);
-    if (zJ <= kStageBytes)
+    if (zJ <= (uint32_t)kStageBytes)
       for (uint32_t c = tid; c < zJ / 16; c += kSpThreads) cp_async16(dJ + 16 * c, blocks + oJ + 16 * c);
   };
 
@@ -381,22 +397,29 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     const int n = list_n[buf];
     const int wbase = (kf_words + j * kWinWords) * WORD;
     for (int e = warp; e < n; e += kSpThreads / 32) {
-      const int q = list[e] - wbase;  // position inside the window
+      const int k = list[e];
+      const int q = k - wbase;  // position inside the window
       const int wq = q >> 5;
       const uint32_t below = (1u << (q & 31)) - 1u;
       const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
       const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
+      if (rI >= (int)hI[0] || rJ >= (int)hJ[0]) continue;  // defensive: row must exist
       const uint32_t sI = rsI[rI], sJ = rsJ[rJ];
       const int nI = (int)(rsI[rI + 1] - sI), nJ = (int)(rsJ[rJ + 1] - sJ);
       const int total = nI * nJ;
       if (total > 0) {
+        unsigned long long qk = 0;
+        if constexpr (PRES) qk = __ldg(qlen + k);
         // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
         int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
         const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
         for (int p = lane; p < total; p += 32) {
-          const float mv = fminf(vI[sI + a], vJ[sJ + bb]);
-          atomicAdd(&sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]],
-                    __float2uint_rn(mv * sp_scale));
+          Acc *dst = &sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]];
+          if constexpr (PRES) {
+            atomicAdd(dst, qk);
+          } else {
+            atomicAdd(dst, __float2uint_rn(fminf(vI[sI + a], vJ[sJ + bb]) * sp_scale));
+          }
           a += da;
           bb += db;
           if (bb >= nJ) {
@@ -410,7 +433,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   }
   uint4 *dst = reinterpret_cast<uint4 *>(spart + (int64_t)blockIdx.x * TILE * TILE);
   const uint4 *src = reinterpret_cast<const uint4 *>(sacc);
-  for (int x = tid; x < TILE * TILE / 4; x += kSpThreads) dst[x] = src[x];
+  for (int x = tid; x < TILE * TILE * (int)sizeof(Acc) / 16; x += kSpThreads) dst[x] = src[x];
 }
 
 // ----------------------------------------------------------------------------
@@ -561,11 +584,12 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
   } else {
     const bool sparse = n_win > 0;
     if (sparse) {
-      e = cudaFuncSetAttribute(k_pairs_weighted_sparse,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem);
+      constexpr size_t kSm = SparseCfg<false>::kSmem;
+      e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSm);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
-      k_pairs_weighted_sparse<<<n_items, kSpThreads, kSpSmem, ctx->stream>>>(
-          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, spart);
+      k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
+          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, nullptr, spart);
       ctx->stat_launches += 1;
     }
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
@@ -579,6 +603,23 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted pair kernel");
+  return UNIFRAC_OK;
+}
+
+int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
+                          const uint8_t *blocks, const unsigned long long *boff, int32_t n_win,
+                          unsigned long long *spart, const WorkItem *items, int32_t n_items) {
+  if (n_items <= 0 || n_win <= 0) return UNIFRAC_OK;
+  const int32_t n_words = ctx->K_pad / WORD;
+  constexpr size_t kSm = SparseCfg<true>::kSmem;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_pairs_sparse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSm);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
+  k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
+      items, bits, n_words, kf_words, n_win, blocks, boff, 1.0f, ctx->d_qperm, spart);
+  ctx->stat_launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel");
   return UNIFRAC_OK;
 }
 

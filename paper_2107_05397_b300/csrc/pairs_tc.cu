@@ -21,7 +21,10 @@
 // issues tcgen05.mma (M=128, N=128, K=16, BF16 -> FP32) into three TMEM
 // accumulators of 128 columns; warps 2-5 read TMEM back (tcgen05.ld) and write
 // the distances.  K-tiles where the row tile or the column tile has no
-// presence at all are skipped (AND of the two tiles' K-tile bitmaps).  Every
+// presence at all are skipped (AND of the two tiles' K-tile bitmaps).  Only the
+// frequently present branches (positions below k_tc) go through the tensor
+// cores when a sparse split is set; the integer sums of the rest come from the
+// sparse kernel (spart) and are added before scaling, still exactly.  Every
 // wait on an mbarrier is bounded (1 s); a timeout records UNIFRAC_E_DEVICE_TIMEOUT,
 // drains outstanding copies, frees TMEM and returns.
 #include <cuda.h>
@@ -183,8 +186,9 @@ __device__ __forceinline__ void tmem_ld_wait() {
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_d,
                const WorkItem *__restrict__ items, const uint32_t *__restrict__ kbits,
-               int32_t k_words, int32_t n_cols, const double *__restrict__ a, double scale,
-               OutSpec o, unsigned long long *__restrict__ counter) {
+               int32_t k_words, int32_t n_cols, const double *__restrict__ a,
+               const unsigned long long *__restrict__ spart, double scale, OutSpec o,
+               unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcShared &sh = *reinterpret_cast<TcShared *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -314,9 +318,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int lj = (int)(colJ + col) - sd.col0;
         if (lj >= sd.n) continue;
         if (li < lj) {
-          const double g = scale * ((double)__uint_as_float(r0[j]) * 65536.0 +
-                                    (double)__uint_as_float(r1[j]) * 256.0 +
-                                    (double)__uint_as_float(r2[j]));
+          double qsum = (double)__uint_as_float(r0[j]) * 65536.0 +
+                        (double)__uint_as_float(r1[j]) * 256.0 + (double)__uint_as_float(r2[j]);
+          if (spart) qsum += (double)spart[(int64_t)blockIdx.x * TC_BM * TC_BN + row * TC_BN + col];
+          const double g = scale * qsum;
           const double A = ai + a[colJ + col];
           put_pair(o, sd, li, lj, ratio01(A - 2.0 * g, A - g));
         } else if (li == lj) {
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 constexpr int PK_KT = 4;
 
 __global__ void __launch_bounds__(256)
-    k_pack_tc(int32_t K, int32_t K_pad, const int32_t *__restrict__ perm,
+    k_pack_tc(int32_t K, int32_t K_pad, int32_t dig_ld, const int32_t *__restrict__ perm,
               const uint8_t *__restrict__ digits, const uint32_t *__restrict__ cnt,
               const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_cols, int32_t n_tiles,
               uint16_t *__restrict__ X, uint16_t *__restrict__ D, uint32_t *__restrict__ kbits,
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(256)
       uint32_t q = 0;
 #pragma unroll
       for (int p = 0; p < TC_PLANES; ++p) {
-        const uint32_t dv = digits[(int64_t)p * K_pad + k];
+        const uint32_t dv = digits[(int64_t)p * dig_ld + k];
         dg[p][tid] = __bfloat16_as_ushort(__float2bfloat16_rn((float)dv));
         q = (q << 8) | dv;
       }
@@ -485,45 +490,53 @@ bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows) {
 
 }  // namespace
 
-int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, uint16_t *X, uint16_t *D,
-            uint32_t *kbits, double *a) {
+int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t k_tc,
+            uint16_t *X, uint16_t *D, uint32_t *kbits, unsigned long long *aq) {
   cudaStream_t st = ctx->stream;
-  const int32_t n_kt = ctx->K_pad / TC_BK;
+  const int32_t n_kt = k_tc / TC_BK;
   const int32_t k_words = (n_kt + 31) / 32;
-  unsigned long long *aq = static_cast<unsigned long long *>(ctx->partial.p);
   cudaError_t e = cudaMemsetAsync(kbits, 0, (size_t)ctx->n_tiles * k_words * 4, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "clear tensor-core packing");
-  ctx->stat_launches += 2;
-  if (ctx->n_tiles > 0) {
+  ctx->stat_launches += 1;
+  if (ctx->n_tiles > 0 && n_kt > 0) {
     dim3 grid(ctx->n_tiles, (n_kt + PK_KT - 1) / PK_KT);
-    k_pack_tc<<<grid, 256, 0, st>>>(ctx->K, ctx->K_pad, ctx->d_perm, ctx->d_digits, cnt, flag,
-                                    ctx->n_cols, ctx->n_cols, ctx->n_tiles, X, D, kbits, k_words,
-                                    aq);
-    k_aq_to_a<<<(ctx->n_cols + 255) / 256, 256, 0, st>>>(ctx->n_cols, aq, ctx->tc_scale, a);
-    ctx->stat_launches += 2;
+    k_pack_tc<<<grid, 256, 0, st>>>(ctx->K, k_tc, ctx->K_pad, ctx->d_perm, ctx->d_digits, cnt,
+                                    flag, ctx->n_cols, ctx->n_cols, ctx->n_tiles, X, D, kbits,
+                                    k_words, aq);
+    ctx->stat_launches += 1;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core packing");
   return UNIFRAC_OK;
 }
 
+int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a) {
+  if (ctx->n_cols <= 0) return UNIFRAC_OK;
+  k_aq_to_a<<<(ctx->n_cols + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_cols, aq, ctx->tc_scale, a);
+  ctx->stat_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core per-sample sums");
+  return UNIFRAC_OK;
+}
+
 size_t tc_smem_bytes() { return TC_SMEM; }
 
-int pairs_tc(unifrac_ctx *ctx, const uint16_t *X, const uint16_t *D, const uint32_t *kbits,
-             const double *a, const WorkItem *items, int32_t n_items, const OutSpec &o) {
+int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *D,
+             const uint32_t *kbits, const double *a, const unsigned long long *spart,
+             const WorkItem *items, int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
-  const int32_t n_kt = ctx->K_pad / TC_BK;
+  if (k_tc < TC_BK || k_tc % TC_BK) return fail(ctx, UNIFRAC_E_INVALID_ARG, "tensor-core K split");
+  const int32_t n_kt = k_tc / TC_BK;
   const int32_t k_words = (n_kt + 31) / 32;
   CUtensorMap mx, md;
-  if (!make_map(&mx, const_cast<uint16_t *>(X), ctx->K_pad, ctx->n_cols) ||
-      !make_map(&md, const_cast<uint16_t *>(D), ctx->K_pad, (uint64_t)TC_PLANES * ctx->n_cols))
+  if (!make_map(&mx, const_cast<uint16_t *>(X), k_tc, ctx->n_cols) ||
+      !make_map(&md, const_cast<uint16_t *>(D), k_tc, (uint64_t)TC_PLANES * ctx->n_cols))
     return fail(ctx, UNIFRAC_E_CUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e =
       cudaFuncSetAttribute(k_pairs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core kernel attribute");
   k_pairs_tc<<<n_items, TC_THREADS, TC_SMEM, ctx->stream>>>(
-      mx, md, items, kbits, k_words, ctx->n_cols, a, ctx->tc_scale, o, ctx->d_counter);
+      mx, md, items, kbits, k_words, ctx->n_cols, a, spart, ctx->tc_scale, o, ctx->d_counter);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core pair kernel");

@@ -91,6 +91,7 @@ struct unifrac_ctx {
   int32_t *d_perm = nullptr;          // [K_pad] node of each position (-1 padding)
   double *d_len_perm = nullptr;       // [K_pad] FP64 length (0 padding)
   uint8_t *d_digits = nullptr;        // [3][K_pad] base-256 digits of len / sigma
+  uint32_t *d_qperm = nullptr;        // [K_pad] 24-bit fixed-point length q_k
   double tc_scale = 0.0;              // sigma * 2^-24
   std::vector<int64_t> nb;            // presence count per node (all studies)
   std::vector<int64_t> nb_perm;       // presence count of each kept position
@@ -116,6 +117,7 @@ struct unifrac_ctx {
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
   int64_t opt_sparse_threshold = -1;  // presence count below which a branch runs sparse
+  int64_t opt_uw_sparse_threshold = -1;  // same, unweighted tensor-core form
   float sp_scale = 1.0f;              // fixed-point scale of the sparse sums (power of 2)
 
   // ---- cached work list (depends on layout and stripe range only)
@@ -135,7 +137,7 @@ struct unifrac_ctx {
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
-      rc, bsize, boff, blocks, spart;
+      rc, bsize, boff, blocks, spart, rbits;
   size_t device_bytes = 0;
 };
 
@@ -160,9 +162,18 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
                   double *S);
 // Sparse blocks of positions >= 32 * kf_words, one per (tile, window of
 // kRareWin positions): sizes, byte offsets boff[n_tiles * n_win + 1] and fill.
-int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *bits,
-                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint8_t *blocks);
+// Values come from vals (weighted) or, when vals is null, presences from cnt.
+int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *cnt,
+                      const uint32_t *bits, const uint8_t *rc, int32_t kf_words, int32_t n_win,
+                      uint32_t *bsize, unsigned long long *boff, uint8_t *blocks);
+// Presence packing of positions >= 32 * kf_words for the unweighted sparse
+// kernel: bitmap words, row non-zero counts and aq[col] += q_k.
+int pack_rare_presence(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
+                       int32_t kf_words, uint32_t *bits, uint8_t *rc, unsigned long long *aq);
+// Unweighted sparse pairs (u64 per pair) of positions >= 32 * kf_words.
+int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
+                          const uint8_t *blocks, const unsigned long long *boff, int32_t n_win,
+                          unsigned long long *spart, const WorkItem *items, int32_t n_items);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
@@ -170,8 +181,11 @@ int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
 // Sample-major BF16 operands for the tensor-core Gram: X[col][k] in {0,1} and
 // three digit planes D_p[col][k] = digit_p(k) * X[col][k]; K-tile bitmaps;
 // a_col = tc_scale * sum_k q_k p[k][col] (exact).
-int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-            uint16_t *X, uint16_t *D, uint32_t *kbits, double *a);
+// Positions [0, k_tc) (a multiple of 64): X and D have rows of k_tc elements.
+// aq (u64 per column) must be zeroed by the caller; finish_tc_a turns it into a.
+int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t k_tc,
+            uint16_t *X, uint16_t *D, uint32_t *kbits, unsigned long long *aq);
+int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a);
 
 // pair kernels ------------------------------------------------------------
 // spart: [n_items][TILE * TILE] u32 partial sums of the sparse kernel.
@@ -184,8 +198,9 @@ int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);
 size_t tc_smem_bytes();
-int pairs_tc(unifrac_ctx *ctx, const uint16_t *X, const uint16_t *D,
-             const uint32_t *kbits, const double *a, const WorkItem *items,
-             int32_t n_items, const OutSpec &o);
+// spart: null, or [n_items][TILE * TILE] u64 sums of q over the sparse positions.
+int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *D,
+             const uint32_t *kbits, const double *a, const unsigned long long *spart,
+             const WorkItem *items, int32_t n_items, const OutSpec &o);
 
 }  // namespace ufb

@@ -274,6 +274,25 @@ def test_weighted_dense_sparse_split(small, threshold, case):
     check_full(got, r, ub.MIXED)
 
 
+@pytest.mark.parametrize("threshold", [0, 1, 40, 10**9])
+@pytest.mark.parametrize("case", [0, 1])
+def test_unweighted_tensor_sparse_split(small, threshold, case):
+    """Every split of the unweighted tensor-core path (all tensor core, a
+    split, everything but one K-tile sparse) agrees with the oracle."""
+    if case == 0:
+        w, ref = small
+        tree, table, r = w.tree, w.table, ref[ub.UNWEIGHTED]
+    else:
+        rng = np.random.default_rng(78)
+        tree, table = synth.random_case(rng, 300, 261, density=0.05, general=True,
+                                        empty_samples=2)
+        r = oracle.unifrac_full(tree, table, ub.UNWEIGHTED)
+    N = table.n_samples
+    got = run(tree, table, ub.UNWEIGHTED, ub.MIXED,
+              options={ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: threshold}).reshape(N, N)
+    check_full(got, r, ub.MIXED)
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_unweighted_mixed_kernel_choice(small, kernel):
     """Both unweighted mixed-precision kernels (tensor-core Gram, bit-packed
