@@ -182,7 +182,7 @@ enum unifrac_option {
                                               samples than this run through the sparse phase;
                                               -1 auto (largest study / 4), 0 all dense */
   UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6 /* unweighted tensor-core kernel: same split;
-                                              -1 auto (largest study / 4 above 8,192
+                                              -1 auto (largest study / 16 above 8,192
                                               samples, else all tensor core), 0 all tensor */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
@@ -194,7 +194,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * as the context's options.  Candidates: the dense / sparse split of the
  * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
  * largest study) and of the unweighted tensor-core kernel
- * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/8 .. 1/2).
+ * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/16 .. 1/4).
  * Each candidate runs `repeats` times (>= 1, after one warm-up run) into
  * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
  * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the
@@ -222,7 +222,11 @@ enum unifrac_stat {
   UNIFRAC_STAT_DEVICE_ERROR = 12,   /* 0, or the UNIFRAC_E_* code a kernel of the last run
                                        raised (synchronises the context's stream) */
   UNIFRAC_STAT_SELECTED_UNWEIGHTED = 13, /* UNIFRAC_STAT_SELECTED_UPDATES of the last */
-  UNIFRAC_STAT_SELECTED_WEIGHTED = 14    /*   unweighted / weighted run               */
+  UNIFRAC_STAT_SELECTED_WEIGHTED = 14,   /*   unweighted / weighted run (dense part)  */
+  UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED = 15, /* device time of the sparse pair kernel of */
+  UNIFRAC_STAT_SPARSE_MS_WEIGHTED = 16,   /*   the last run of each variant (ms)     */
+  UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED = 17, /* pair updates it did (co-present      */
+  UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED = 18    /*   (pair, branch) of the sparse part) */
 };
 int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
 

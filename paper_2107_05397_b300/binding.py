@@ -48,6 +48,10 @@ STAT_PAIR_MS_WEIGHTED = 11
 STAT_DEVICE_ERROR = 12
 STAT_SELECTED_UNWEIGHTED = 13
 STAT_SELECTED_WEIGHTED = 14
+STAT_SPARSE_MS_UNWEIGHTED = 15
+STAT_SPARSE_MS_WEIGHTED = 16
+STAT_SPARSE_UPDATES_UNWEIGHTED = 17
+STAT_SPARSE_UPDATES_WEIGHTED = 18
 
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",

@@ -102,6 +102,9 @@ void free_ctx(unifrac_ctx *ctx) {
   for (auto &pr : ctx->ev_pair)
     for (auto &e : pr)
       if (e) cudaEventDestroy(e);
+  for (auto &pr : ctx->ev_sp)
+    for (auto &e : pr)
+      if (e) cudaEventDestroy(e);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -465,13 +468,18 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
                  (uint32_t)digits[2 * (size_t)ctx->K_pad + k];
     if ((rc = upload(ctx, &ctx->d_qperm, qperm))) return rc;
   }
-  std::vector<unsigned long long> zero4(4, 0ull);
-  if ((rc = upload(ctx, &ctx->d_counter, zero4))) return rc;
+  std::vector<unsigned long long> zero8(8, 0ull);
+  if ((rc = upload(ctx, &ctx->d_counter, zero8))) return rc;
   for (auto &ev : ctx->ev) {
     e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
   }
   for (auto &pr : ctx->ev_pair)
+    for (auto &ev : pr) {
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+    }
+  for (auto &pr : ctx->ev_sp)
     for (auto &ev : pr) {
       e = cudaEventCreate(&ev);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
@@ -636,7 +644,7 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
   } else if (P.kind == RunPlan::TENSOR) {
     // positions [0, k_tc) on the tensor cores, the rarely present rest sparse
     int64_t th = ctx->opt_uw_sparse_threshold;
-    if (th < 0) th = ctx->max_study_n > 8192 ? ctx->max_study_n / 4 : 0;
+    if (th < 0) th = ctx->max_study_n > 8192 ? ctx->max_study_n / 16 : 0;
     int32_t kf = ctx->K;
     if (th > 0) {
       kf = 0;
@@ -686,6 +694,8 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
 static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   int rc;
   cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(ctx->d_counter + 4, 0, sizeof(unsigned long long), ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
   OutSpec o;
   o.out = P.dst;
@@ -745,12 +755,14 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
     cudaEventRecord(ctx->ev[1], ctx->stream);
     cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
     ctx->sel_unit = 64.0;
+    cudaEventRecord(ctx->ev_sp[0][0], ctx->stream);
     if (spart &&
         (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(ctx->rbits.p), P.kf_words,
                                     static_cast<const uint8_t *>(ctx->blocks.p),
                                     static_cast<const unsigned long long *>(ctx->boff.p),
                                     P.n_win, spart, d_items, n_items)))
       return rc;
+    cudaEventRecord(ctx->ev_sp[0][1], ctx->stream);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, a, spart, d_items, n_items, o))) return rc;
   } else {
     double *a = static_cast<double *>(ctx->persample.p);
@@ -767,6 +779,9 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
   e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
                       cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_counter + 5 + variant, ctx->d_counter + 4,
+                        sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
   ctx->sel_unit_v[variant] = ctx->sel_unit;
   return UNIFRAC_OK;
@@ -1039,7 +1054,7 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
     option = UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD;
     const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
     cands.push_back({option, 0});  // everything on the tensor cores
-    for (int64_t num : {2, 4, 8}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
+    for (int64_t num : {1, 2, 4}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
   }
   const int saved_graph = ctx->opt_use_graph;
   ctx->opt_use_graph = 0;
@@ -1132,6 +1147,32 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       e = cudaMemcpy(&c, ctx->d_counter + 2 + v, sizeof(c), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
       *value = (double)c * ctx->sel_unit_v[v] * (double)TILE * (double)TILE;
+      return UNIFRAC_OK;
+    }
+    case UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED:
+    case UNIFRAC_STAT_SPARSE_MS_WEIGHTED:
+    case UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED:
+    case UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED: {
+      const int v = (stat == UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED ||
+                     stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED) ? 0 : 1;
+      if (!ctx->ev_pair_valid[v]) return fail(ctx, UNIFRAC_E_INVALID_ARG, "no run of that variant");
+      DeviceGuard g(ctx->device);
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+      if (stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED ||
+          stat == UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED) {
+        unsigned long long c = 0;
+        e = cudaMemcpy(&c, ctx->d_counter + 5 + v, sizeof(c), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
+        *value = (double)c;
+        return UNIFRAC_OK;
+      }
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->ev_sp[v][0], ctx->ev_sp[v][1]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;  // no sparse phase in that run
+      }
+      *value = ms;
       return UNIFRAC_OK;
     }
     case UNIFRAC_STAT_DEVICE_ERROR: {

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // independent of the order of the atomics).  The accumulator goes to spart.
 
 constexpr int kSpThreads = 1024;
+constexpr int kSmall = 16;  // pairs a single lane walks alone
 
 // PRES = false: weighted form, entries carry v; adds round(min(v_i, v_j) * 2^s)
 //               into 32-bit accumulators (spart: u32 per pair).
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(kSpThreads, 1)
                    int32_t n_words, int32_t kf_words, int32_t n_win,
                    const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
                    float sp_scale, const uint32_t *__restrict__ qlen,
-                   typename SparseCfg<PRES>::Acc *__restrict__ spart) {
+                   typename SparseCfg<PRES>::Acc *__restrict__ spart,
+                   unsigned long long *__restrict__ n_updates) {
   using Acc = typename SparseCfg<PRES>::Acc;
   constexpr int kStageBytes = SparseCfg<PRES>::kStage;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,6 +333,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
   const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
+  unsigned long long my_updates = 0;
   for (int x = tid; x < TILE * TILE; x += kSpThreads) sacc[x] = Acc(0);
 
   auto prepare = [&](int j, int buf) {
@@ -396,34 +399,69 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     const int32_t *list = lists + buf * kRareWin;
     const int n = list_n[buf];
     const int wbase = (kf_words + j * kWinWords) * WORD;
-    for (int e = warp; e < n; e += kSpThreads / 32) {
-      const int k = list[e];
-      const int q = k - wbase;  // position inside the window
-      const int wq = q >> 5;
-      const uint32_t below = (1u << (q & 31)) - 1u;
-      const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
-      const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
-      if (rI >= (int)hI[0] || rJ >= (int)hJ[0]) continue;  // defensive: row must exist
-      const uint32_t sI = rsI[rI], sJ = rsJ[rJ];
-      const int nI = (int)(rsI[rI + 1] - sI), nJ = (int)(rsJ[rJ + 1] - sJ);
+    // Each lane takes one branch of the list; a branch with at most kSmall
+    // pairs is walked by its lane alone, larger ones by the whole warp.
+    for (int base = warp * 32; base < n; base += kSpThreads) {
+      const int e = base + lane;
+      int k = 0, nI = 0, nJ = 0;
+      uint32_t sI = 0, sJ = 0;
+      if (e < n) {
+        k = list[e];
+        const int q = k - wbase;  // position inside the window
+        const int wq = q >> 5;
+        const uint32_t below = (1u << (q & 31)) - 1u;
+        const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
+        const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
+        if (rI < (int)hI[0] && rJ < (int)hJ[0]) {  // defensive: the rows must exist
+          sI = rsI[rI];
+          sJ = rsJ[rJ];
+          nI = (int)(rsI[rI + 1] - sI);
+          nJ = (int)(rsJ[rJ + 1] - sJ);
+        }
+      }
       const int total = nI * nJ;
-      if (total > 0) {
-        unsigned long long qk = 0;
-        if constexpr (PRES) qk = __ldg(qlen + k);
-        // pairs p = lane, lane+32, ... walked as (a, b) = (p / nJ, p % nJ)
-        int a = lane / nJ, bb = lane - (lane / nJ) * nJ;
-        const int da = 32 / nJ, db = 32 - (32 / nJ) * nJ;
-        for (int p = lane; p < total; p += 32) {
-          Acc *dst = &sacc[(int)riI[sI + a] * TILE + (int)riJ[sJ + bb]];
+      my_updates += (unsigned long long)total;
+      unsigned long long qk = 0;
+      if constexpr (PRES) qk = (total > 0) ? __ldg(qlen + k) : 0ull;
+      if (total > 0 && total <= kSmall) {
+        for (int a = 0; a < nI; ++a) {
+          const int ra = (int)riI[sI + a] * TILE;
+          float va = 0.f;
+          if constexpr (!PRES) va = vI[sI + a];
+          for (int b = 0; b < nJ; ++b) {
+            Acc *dst = &sacc[ra + (int)riJ[sJ + b]];
+            if constexpr (PRES) {
+              atomicAdd(dst, qk);
+            } else {
+              atomicAdd(dst, __float2uint_rn(fminf(va, vJ[sJ + b]) * sp_scale));
+            }
+          }
+        }
+      }
+      uint32_t big = __ballot_sync(0xffffffffu, total > kSmall);
+      while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const int bnI = __shfl_sync(0xffffffffu, nI, src);
+        const int bnJ = __shfl_sync(0xffffffffu, nJ, src);
+        const uint32_t bsI = __shfl_sync(0xffffffffu, sI, src);
+        const uint32_t bsJ = __shfl_sync(0xffffffffu, sJ, src);
+        const unsigned long long bq = __shfl_sync(0xffffffffu, qk, src);
+        const int btotal = bnI * bnJ;
+        // pairs p = lane, lane+32, ... walked as (a, b) = (p / bnJ, p % bnJ)
+        int a = lane / bnJ, bb = lane - (lane / bnJ) * bnJ;
+        const int da = 32 / bnJ, db = 32 - (32 / bnJ) * bnJ;
+        for (int p = lane; p < btotal; p += 32) {
+          Acc *dst = &sacc[(int)riI[bsI + a] * TILE + (int)riJ[bsJ + bb]];
           if constexpr (PRES) {
-            atomicAdd(dst, qk);
+            atomicAdd(dst, bq);
           } else {
-            atomicAdd(dst, __float2uint_rn(fminf(vI[sI + a], vJ[sJ + bb]) * sp_scale));
+            atomicAdd(dst, __float2uint_rn(fminf(vI[bsI + a], vJ[bsJ + bb]) * sp_scale));
           }
           a += da;
           bb += db;
-          if (bb >= nJ) {
-            bb -= nJ;
+          if (bb >= bnJ) {
+            bb -= bnJ;
             ++a;
           }
         }
@@ -434,6 +472,10 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   uint4 *dst = reinterpret_cast<uint4 *>(spart + (int64_t)blockIdx.x * TILE * TILE);
   const uint4 *src = reinterpret_cast<const uint4 *>(sacc);
   for (int x = tid; x < TILE * TILE * (int)sizeof(Acc) / 16; x += kSpThreads) dst[x] = src[x];
+  // pair updates done (statistics)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) my_updates += __shfl_xor_sync(0xffffffffu, my_updates, off);
+  if (lane == 0 && n_updates && my_updates) atomicAdd(n_updates, my_updates);
 }
 
 // ----------------------------------------------------------------------------
@@ -583,15 +625,18 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     ctx->stat_launches += 1;
   } else {
     const bool sparse = n_win > 0;
+    cudaEventRecord(ctx->ev_sp[1][0], ctx->stream);
     if (sparse) {
       constexpr size_t kSm = SparseCfg<false>::kSmem;
       e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSm);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
       k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
-          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, nullptr, spart);
+          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, nullptr, spart,
+          ctx->d_counter + 4);
       ctx->stat_launches += 1;
     }
+    cudaEventRecord(ctx->ev_sp[1][1], ctx->stream);
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
@@ -616,7 +661,8 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
       cudaFuncSetAttribute(k_pairs_sparse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSm);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
   k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
-      items, bits, n_words, kf_words, n_win, blocks, boff, 1.0f, ctx->d_qperm, spart);
+      items, bits, n_words, kf_words, n_win, blocks, boff, 1.0f, ctx->d_qperm, spart,
+      ctx->d_counter + 4);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel");

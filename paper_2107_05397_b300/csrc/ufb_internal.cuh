@@ -101,13 +101,14 @@ struct unifrac_ctx {
   // ---- statistics
   double stat_pair_branch = 0, stat_useful = 0;
   double stat_launches = 0, stat_tile_pairs = 0;
-  unsigned long long *d_counter = nullptr;  // [4] device counters
+  unsigned long long *d_counter = nullptr;  // [8] device counters
   double sel_unit = 1.0;                    // branches per counted selection unit
   double sel_unit_v[2] = {1.0, 1.0};        // same, last run of each variant
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ev_valid = false;
-  // pair-kernel events of the last run of each variant
+  // pair-kernel events of the last run of each variant, and of its sparse kernel
   cudaEvent_t ev_pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t ev_sp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool ev_pair_valid[2] = {false, false};
 
   // ---- options
