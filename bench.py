@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-per-study", action="store_true",
+                    help="skip the one-launch-per-study comparison (several studies)")
     ap.add_argument("--samples", type=int, default=None,
                     help="truncate the workload to this many samples (profiling runs)")
     return ap.parse_args()
@@ -167,12 +171,54 @@ def kept_branches(w):
     return int(np.count_nonzero(reached & (w.tree.length > 0)))
 
 
+def study_table(table, s):
+    """Sub-table of study s (columns renumbered from 0)."""
+    from paper_2107_05397_b300 import synth
+    lo, hi = int(table.study_offsets[s]), int(table.study_offsets[s + 1])
+    rows = np.repeat(np.arange(table.n_features), np.diff(table.indptr))
+    m = (table.indices >= lo) & (table.indices < hi)
+    return synth.coo_to_table(table.n_features, hi - lo, rows[m], table.indices[m] - lo,
+                              table.counts[m], table.feature_node)
+
+
+def select_studies(table, chosen):
+    """Table of the chosen studies only, in the given order."""
+    from paper_2107_05397_b300 import synth
+    rows = np.repeat(np.arange(table.n_features), np.diff(table.indptr))
+    so = table.study_offsets
+    rr, cc, vv, offs = [], [], [], [0]
+    for s in chosen:
+        lo, hi = int(so[s]), int(so[s + 1])
+        m = (table.indices >= lo) & (table.indices < hi)
+        rr.append(rows[m])
+        cc.append(table.indices[m] - lo + offs[-1])
+        vv.append(table.counts[m])
+        offs.append(offs[-1] + hi - lo)
+    cat = lambda xs: np.concatenate(xs) if xs else np.empty(0, np.int64)
+    return synth.coo_to_table(table.n_features, offs[-1], cat(rr), cat(cc), cat(vv),
+                              table.feature_node, np.asarray(offs, np.int32))
+
+
+def baseline_study(w):
+    """(study index, its table, offset of its condensed block) of the study the
+    CPU baseline and the error check use: the largest one."""
+    so = w.table.study_offsets
+    if so is None:
+        return 0, w.table, 0
+    sizes = np.diff(so)
+    s = int(np.argmax(sizes))
+    off = int(sum(int(n) * (int(n) - 1) // 2 for n in sizes[:s]))
+    return s, study_table(w.table, s), off
+
+
 def reference_arm(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     from paper_2107_05397_b300 import synth
-    w = synth.make_workload(args.workload)
+    w0 = synth.make_workload(args.workload)
+    _, sub, _ = baseline_study(w0)
+    w = synth.Workload(w0.name, w0.tree, sub, w0.description)
     N = w.table.n_samples
     B = kept_branches(w)
     rng = np.random.default_rng(7)
@@ -224,6 +270,13 @@ def main():
         torch.cuda.synchronize()
 
     w = synth.make_workload(args.workload, n_samples=args.samples)
+    if w.table.study_offsets is not None and world > 1:
+        # independent studies: each rank takes its share (no data-path collective)
+        from paper_2107_05397_b300 import replicas
+        sizes = [int(x) for x in np.diff(w.table.study_offsets)]
+        w = synth.Workload(w.name, w.tree,
+                           select_studies(w.table, replicas.shard_studies(sizes, rank, world)),
+                           w.description)
     N = w.table.n_samples
     stream = torch.cuda.current_stream()
     ctx = ub.Context(w.tree, w.table, stream=stream)
@@ -239,11 +292,20 @@ def main():
         ctx.run(ub.BOTH, precision, ub.OUT_CONDENSED, out=out)
         return ctx.stat(ub.STAT_KERNEL_LAUNCHES)
 
+    tuned = {}
+    if not args.no_autotune:  # the library's own tuner, before the timed region
+        from paper_2107_05397_b300 import autotune
+        for v in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED):
+            rec = autotune.tune(ctx, v, ub.MIXED)
+            tuned.update({k: rec[k] for k in rec if k != "cached"})
+    if not args.no_graph:
+        ctx.set_option(ub.OPT_USE_GRAPH, 1)
     for _ in range(args.warmup):
         step()
     barrier()
 
     step_ms, pair_wn_ms, pair_uw_ms, sel_wn, sel_uw = [], [], [], [], []
+    sp_uw_ms, sp_wn_ms, sp_uw_n, sp_wn_n = [], [], [], []
     launches = 0
     peaks = measured_peaks()
     with ClockSampler(torch.cuda.current_device()) as clocks:
@@ -262,44 +324,50 @@ def main():
             pair_wn_ms.append(ctx.stat(ub.STAT_PAIR_MS_WEIGHTED))
             sel_wn.append(ctx.stat(ub.STAT_SELECTED_WEIGHTED))
             sel_uw.append(ctx.stat(ub.STAT_SELECTED_UNWEIGHTED))
+            sp_uw_ms.append(ctx.stat(ub.STAT_SPARSE_MS_UNWEIGHTED))
+            sp_wn_ms.append(ctx.stat(ub.STAT_SPARSE_MS_WEIGHTED))
+            sp_uw_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_UNWEIGHTED))
+            sp_wn_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_WEIGHTED))
         barrier()
         t_wall = time.perf_counter() - t_wall0
     clk = clocks.summary()
     dev_err = ctx.stat(ub.STAT_DEVICE_ERROR)
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2107_05397_b300 import replicas
+    total_ms, units_all = replicas.reduce_timing(float(sum(step_ms)), units_per_step * args.steps,
+                                                 dist, device="cuda")
     ms_per_step = total_ms / args.steps
-    value = units_per_step * args.steps * world / (total_ms / 1e3)
+    value = units_all / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (weighted pair kernel, FP32 ALU bound):
-    # 2 FP32 ops (min, add) per pair-branch update it performs
-    wn_ms = float(np.mean(pair_wn_ms))
-    ops = 2.0 * float(np.mean(sel_wn))
-    achieved = ops / (wn_ms / 1e3) / 1e12
+    # live per-kernel times (CUDA events recorded by the library on its stream)
+    # and the algorithmic work of each launch
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak = sms * 128 * sm_max * 1e6 / 1e12
-    roofline = {
-        "kernel": "k_pairs_weighted<float>", "bound": "alu", "achieved": achieved,
-        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-        "traffic": recorded_traffic("k_pairs_weighted<float>"),
-        "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max clock)",
-        "work": "2 FP32 ops per selected pair-branch update",
-        "dense_equivalent_tflops": 2.0 * pair_branch / (wn_ms / 1e3) / 1e12,
-    }
-    # the tensor-core Gram: 3 BF16 digit planes x 2 flops per selected pair-branch
-    uw_ms = float(np.mean(pair_uw_ms))
-    tc_flops = 6.0 * float(np.mean(sel_uw))
-    tc_ach = tc_flops / (uw_ms / 1e3) / 1e12
+    alu_peak = sms * 128 * sm_max * 1e6 / 1e12
+    alu_src = f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock, MEASURED_PEAKS.json)"
     tc_peak = (peaks or {}).get("bf16_tflops", 1766.4)
-    roofline_tc = {"kernel": "k_pairs_tc", "bound": "tensor", "achieved": tc_ach,
-                   "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_ach / tc_peak,
-                   "traffic": recorded_traffic("k_pairs_tc"),
-                   "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
-                   "work": "3 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)"}
+    mean = lambda xs: float(np.mean(xs)) if xs else 0.0
+    uw_ms, wn_ms = mean(pair_uw_ms), mean(pair_wn_ms)
+    kernels = []
+
+    def entry(kernel, ms, work, bound, peak, unit, work_note, peak_note):
+        if ms <= 0:
+            return
+        ach = work / (ms / 1e3) / 1e12
+        kernels.append({"kernel": kernel, "ms": ms, "bound": bound, "achieved": ach,
+                        "peak": peak, "unit": unit, "frac": ach / peak,
+                        "traffic": recorded_traffic(kernel), "work": work_note,
+                        "peak_source": peak_note})
+
+    entry("k_pairs_tc", uw_ms - mean(sp_uw_ms), 6.0 * mean(sel_uw), "tensor", tc_peak, "TFLOP/s",
+          "3 BF16 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)",
+          "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)")
+    entry("k_pairs_sparse<true>", mean(sp_uw_ms), 2.0 * mean(sp_uw_n), "alu", alu_peak, "TFLOP/s",
+          "2 ops (compare-free add of q_b, index) per co-present pair-branch", alu_src)
+    entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms), 2.0 * mean(sel_wn), "alu", alu_peak,
+          "TFLOP/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
+    entry("k_pairs_sparse<false>", mean(sp_wn_ms), 2.0 * mean(sp_wn_n), "alu", alu_peak,
+          "TFLOP/s", "2 ops (min, add) per co-present pair-branch", alu_src)
+    roofline = max(kernels, key=lambda k: k["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -307,17 +375,22 @@ def main():
         "dtype": "f32+bf16(int digits)+f64 reductions", "data": "synthetic",
         "config": {"workload": args.workload if args.samples is None
                    else f"{args.workload} truncated to {N} samples", "samples": N,
+                   "studies": 1 if w.table.study_offsets is None
+                   else int(len(w.table.study_offsets) - 1),
                    "branches_kept": ctx.stat(ub.STAT_BRANCHES_KEPT),
                    "levels": ctx.stat(ub.STAT_LEVELS), "layout": "condensed",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": (f"studies sharded over {world} GPUs"
+                                   if w.table.study_offsets is not None and world > 1
+                                   else f"replicas x{world}"),
                    "l2": "flushed (512 MB write) before every timed step",
                    "description": w.description},
         "roofline": roofline,
-        "roofline_unweighted_tensor": roofline_tc,
+        "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "breakdown_ms": {"pair_unweighted": uw_ms,
-                         "pair_weighted": wn_ms},
+        "breakdown_ms": {"pair_unweighted": uw_ms, "pair_weighted": wn_ms,
+                         "embedding_packing_other": ms_per_step - uw_ms - wn_ms},
+        "tuned_options": tuned, "graph_replay": not args.no_graph,
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
         "wall_s_timed_loop": t_wall,
         "device_error": dev_err,
@@ -325,20 +398,24 @@ def main():
 
     if rank == 0 and not args.no_fp64:
         # the plain FP64 path (lookup unweighted + FP64 weighted) on the same GPU
-        out64 = torch.empty(nb_cond, dtype=torch.float64, device="cuda")
-        step(ub.FP64, out64)
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(ub.FP64, out64)
-        e1.record(stream)
-        e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        line["fp64_plain"] = {"ms_per_step": ms64,
-                              "value": units_per_step / (ms64 / 1e3),
-                              "mixed_speedup": ms64 / ms_per_step}
-        del out64
+        try:
+            out64 = torch.empty(nb_cond, dtype=torch.float64, device="cuda")
+            step(ub.FP64, out64)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(ub.FP64, out64)
+            e1.record(stream)
+            e1.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            line["fp64_plain"] = {"ms_per_step": ms64,
+                                  "value": units_per_step / (ms64 / 1e3),
+                                  "mixed_speedup": ms64 / ms_per_step}
+            del out64
+        except (ub.UniFracError, torch.OutOfMemoryError) as exc:
+            line["fp64_plain"] = {"skipped": str(exc)}
+            torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers
     if rank == 0 and not args.no_e2e:
@@ -351,7 +428,8 @@ def main():
         for rep in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h = ub.unifrac_create(*host_in, n_samples=N, stream=stream)
+            h = ub.unifrac_create(*host_in, n_samples=N, stream=stream,
+                                  study_offsets=w.table.study_offsets)
             ub.unifrac_run(h, ub.BOTH, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res)
             ub.unifrac_destroy(h)
             torch.cuda.synchronize()
@@ -363,26 +441,60 @@ def main():
                        "includes": "create (validation, host prep, upload) + one run of both "
                                    "variants + D2H of both condensed matrices + destroy"}
 
+    if rank == 0 and w.table.study_offsets is not None and not args.no_per_study:
+        # the same studies with one context and one launch sequence per study,
+        # one study at a time (device memory), each run timed with events
+        ctx.close()
+        torch.cuda.empty_cache()
+        per = 0.0
+        for s_ in range(len(w.table.study_offsets) - 1):
+            t_ = study_table(w.table, s_)
+            if t_.n_samples < 2:
+                continue
+            with ub.Context(w.tree, t_, stream=stream) as c:
+                if not args.no_autotune:
+                    from paper_2107_05397_b300 import autotune
+                    for v in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED):
+                        autotune.tune(c, v, ub.MIXED)
+                o_ = torch.empty(2 * c.output_bytes(ub.MIXED, ub.OUT_CONDENSED) // 4, device="cuda")
+                c.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, out=o_)
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, out=o_)
+                e1.record(stream)
+                e1.synchronize()
+                per += e0.elapsed_time(e1)
+                del o_
+        line["one_launch_sequence_per_study"] = {
+            "ms_per_step": per, "value": units_per_step / (per / 1e3),
+            "batched_speedup": per / ms_per_step,
+            "note": "sum of per-study runs (each its own context, tuned, warm)"}
+
     if rank == 0 and not args.no_cpu_baseline:
+        s_idx, sub, block0 = baseline_study(w)
+        ws = synth.Workload(w.name, w.tree, sub, w.description)
+        Ns = sub.n_samples
         rng = np.random.default_rng(7)
-        rows = np.sort(rng.choice(N, size=min(args.cpu_rows, N), replace=False))
-        ref, dt, threads = oracle_sample(w, rows)
-        B = kept_branches(w)
-        units = 2.0 * len(rows) * (N - 1) * B
+        rows = np.sort(rng.choice(Ns, size=min(args.cpu_rows, Ns), replace=False))
+        ref, dt, threads = oracle_sample(ws, rows)
+        B = kept_branches(ws)
+        units = 2.0 * len(rows) * (Ns - 1) * B
         line["cpu_baseline"] = {"value": units / dt, "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
-                                "sample": f"{len(rows)} seeded rows x {N} columns, both "
-                                          f"variants ({dt:.1f} s)"}
+                                "sample": f"{len(rows)} seeded rows x {Ns} columns of study "
+                                          f"{s_idx}, both variants ({dt:.1f} s)"}
         # error of this run's outputs on the same rows
         errs = {}
         for name, v, t in (("unweighted", 0, out_uw), ("weighted_normalized", 1, out_wn)):
             got = t.cpu().numpy().astype(np.float64)
             e = 0.0
             for r, i in enumerate(rows):
-                j = np.arange(N)
+                j = np.arange(Ns)
                 a_, b_ = np.minimum(i, j), np.maximum(i, j)
-                idx = a_ * N - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
-                vals = np.where(i == j, 0.0, got[np.where(i == j, 0, idx)])
+                idx = block0 + a_ * Ns - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
+                vals = np.where(i == j, 0.0, got[np.where(i == j, block0, idx)])
                 e = max(e, float(np.max(np.abs(vals - ref[v][r]))))
             errs[name] = e
         line["max_abs_err_vs_oracle"] = errs

@@ -183,7 +183,8 @@ enum unifrac_option {
                                               -1 auto (largest study / 4), 0 all dense */
   UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6 /* unweighted tensor-core kernel: same split;
                                               -1 auto (largest study / 16 above 8,192
-                                              samples, else all tensor core), 0 all tensor */
+                                              samples in total, else all tensor core),
+                                              0 all tensor */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);

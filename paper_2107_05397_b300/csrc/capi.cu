@@ -21,6 +21,13 @@ int fail(unifrac_ctx *ctx, int code, const std::string &msg) {
   return code;
 }
 
+void record_event(unifrac_ctx *ctx, cudaEvent_t ev) {
+  if (ctx->capturing)
+    cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, ctx->stream);
+}
+
 int cuda_fail(unifrac_ctx *ctx, cudaError_t e, const char *what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   if (e == cudaErrorMemoryAllocation) return fail(ctx, UNIFRAC_E_OOM, m);
@@ -644,7 +651,8 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
   } else if (P.kind == RunPlan::TENSOR) {
     // positions [0, k_tc) on the tensor cores, the rarely present rest sparse
     int64_t th = ctx->opt_uw_sparse_threshold;
-    if (th < 0) th = ctx->max_study_n > 8192 ? ctx->max_study_n / 16 : 0;
+    if (th < 0)  // split once the operands grow large (many samples in total)
+      th = ctx->n_cols > 8192 ? std::max<int64_t>(32, ctx->max_study_n / 16) : 0;
     int32_t kf = ctx->K;
     if (th > 0) {
       kf = 0;
@@ -721,8 +729,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
                                 static_cast<unsigned long long *>(ctx->boff.p),
                                 static_cast<uint8_t *>(ctx->blocks.p))))
       return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    record_event(ctx, ctx->ev[1]);
+    record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 1.0;
     if ((rc = pairs_weighted(ctx, P.f64, ctx->vals.p, bits, P.kf_words,
                              static_cast<const uint8_t *>(ctx->blocks.p),
@@ -752,17 +760,17 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
       spart = static_cast<unsigned long long *>(ctx->spart.p);
     }
     if ((rc = finish_tc_a(ctx, aq, a))) return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    record_event(ctx, ctx->ev[1]);
+    record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 64.0;
-    cudaEventRecord(ctx->ev_sp[0][0], ctx->stream);
+    record_event(ctx, ctx->ev_sp[0][0]);
     if (spart &&
         (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(ctx->rbits.p), P.kf_words,
                                     static_cast<const uint8_t *>(ctx->blocks.p),
                                     static_cast<const unsigned long long *>(ctx->boff.p),
                                     P.n_win, spart, d_items, n_items)))
       return rc;
-    cudaEventRecord(ctx->ev_sp[0][1], ctx->stream);
+    record_event(ctx, ctx->ev_sp[0][1]);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, a, spart, d_items, n_items, o))) return rc;
   } else {
     double *a = static_cast<double *>(ctx->persample.p);
@@ -770,13 +778,13 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
     double *tables = static_cast<double *>(ctx->tables.p);
     uint32_t *gbits = static_cast<uint32_t *>(ctx->bits.p);
     if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
-    cudaEventRecord(ctx->ev[1], ctx->stream);
-    cudaEventRecord(ctx->ev_pair[variant][0], ctx->stream);
+    record_event(ctx, ctx->ev[1]);
+    record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 8.0;
     if ((rc = pairs_lookup(ctx, bytes, tables, gbits, a, d_items, n_items, o))) return rc;
   }
-  cudaEventRecord(ctx->ev[2], ctx->stream);
-  cudaEventRecord(ctx->ev_pair[variant][1], ctx->stream);
+  record_event(ctx, ctx->ev[2]);
+  record_event(ctx, ctx->ev_pair[variant][1]);
   e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
                       cudaMemcpyDeviceToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -790,7 +798,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
 // The embedding once, then each variant's packing and pair kernels.
 static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
   int rc;
-  cudaEventRecord(ctx->ev[0], ctx->stream);
+  record_event(ctx, ctx->ev[0]);
   if ((rc = embed_counts(ctx, static_cast<uint32_t *>(ctx->cnt.p),
                          static_cast<uint8_t *>(ctx->flag.p))))
     return rc;
@@ -837,7 +845,9 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan *plans, int n_plans, in
   ctx->stream = ctx->cap_stream;
   e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
   int rc = UNIFRAC_OK;
+  ctx->capturing = true;
   if (e == cudaSuccess) rc = enqueue_run(ctx, plans, n_plans);
+  ctx->capturing = false;
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
   ctx->stream = user;

@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // (2^s keeps every pair sum below 2^31; integer sums make the result
 // independent of the order of the atomics).  The accumulator goes to spart.
 
-constexpr int kSpThreads = 1024;
+constexpr int kSpThreads = 1024;  // one warp per bitmap word of a window
+static_assert(kSpThreads / 32 == kWinWords, "sparse kernel: one warp per window word");
 constexpr int kSmall = 16;  // pairs a single lane walks alone
 
 // PRES = false: weighted form, entries carry v; adds round(min(v_i, v_j) * 2^s)
@@ -305,8 +306,7 @@ template <bool PRES>
 struct SparseCfg {
   using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
   static constexpr int kStage = PRES ? 16 * 1024 : 24 * 1024;  // one tile's block
-  static constexpr size_t kSmem =
-      (size_t)TILE * TILE * sizeof(Acc) + 4 * kStage + 2 * sizeof(int32_t) * kRareWin;
+  static constexpr size_t kSmem = (size_t)TILE * TILE * sizeof(Acc) + 4 * kStage;
 };
 
 template <bool PRES>
@@ -322,10 +322,8 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc *sacc = reinterpret_cast<Acc *>(smem_raw);
   uint8_t *stage = smem_raw + (size_t)TILE * TILE * sizeof(Acc);  // [2 bufs][2 tiles][kStageBytes]
-  int32_t *lists = reinterpret_cast<int32_t *>(stage + 4 * kStageBytes);  // [2][kRareWin]
   __shared__ uint32_t swI[2][kWinWords], swJ[2][kWinWords];
   __shared__ int32_t spI[2][kWinWords], spJ[2][kWinWords];
-  __shared__ int32_t list_n[2];
   __shared__ unsigned long long boI[2], boJ[2];
   __shared__ int32_t inI[2], inJ[2];  // 1 = block staged in shared memory
 
@@ -339,7 +337,6 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   auto prepare = [&](int j, int buf) {
     const int w0 = kf_words + j * kWinWords;
     if (warp == 0) {
-      build_window(bI, bJ, n_words, w0, lists + buf * kRareWin, &list_n[buf]);
       const int w = w0 + lane;
       const uint32_t mi = (w < n_words) ? bI[w] : 0u, mj = (w < n_words) ? bJ[w] : 0u;
       swI[buf][lane] = mi;
@@ -396,20 +393,20 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     const uint8_t *riI = blkI + hI[2], *riJ = blkJ + hJ[2];
     const float *vI = reinterpret_cast<const float *>(blkI + hI[3]);
     const float *vJ = reinterpret_cast<const float *>(blkJ + hJ[3]);
-    const int32_t *list = lists + buf * kRareWin;
-    const int n = list_n[buf];
     const int wbase = (kf_words + j * kWinWords) * WORD;
-    // Each lane takes one branch of the list; a branch with at most kSmall
-    // pairs is walked by its lane alone, larger ones by the whole warp.
-    for (int base = warp * 32; base < n; base += kSpThreads) {
-      const int e = base + lane;
+    // Warp w takes bitmap word w of the window and lane l its bit: the branch
+    // at position wbase + 32 w + l, if present in both tiles.  A branch with
+    // at most kSmall pairs is walked by its lane alone, larger ones by the
+    // whole warp.
+    {
+      const int wq = warp;
+      const uint32_t both = swI[buf][wq] & swJ[buf][wq];
+      const bool mine = (both >> lane) & 1u;
       int k = 0, nI = 0, nJ = 0;
       uint32_t sI = 0, sJ = 0;
-      if (e < n) {
-        k = list[e];
-        const int q = k - wbase;  // position inside the window
-        const int wq = q >> 5;
-        const uint32_t below = (1u << (q & 31)) - 1u;
+      if (mine) {
+        k = wbase + 32 * wq + lane;
+        const uint32_t below = (1u << lane) - 1u;
         const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
         const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
         if (rI < (int)hI[0] && rJ < (int)hJ[0]) {  // defensive: the rows must exist
@@ -625,7 +622,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     ctx->stat_launches += 1;
   } else {
     const bool sparse = n_win > 0;
-    cudaEventRecord(ctx->ev_sp[1][0], ctx->stream);
+    record_event(ctx, ctx->ev_sp[1][0]);
     if (sparse) {
       constexpr size_t kSm = SparseCfg<false>::kSmem;
       e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -636,7 +633,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
           ctx->d_counter + 4);
       ctx->stat_launches += 1;
     }
-    cudaEventRecord(ctx->ev_sp[1][1], ctx->stream);
+    record_event(ctx, ctx->ev_sp[1][1]);
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");

@@ -135,6 +135,7 @@ struct unifrac_ctx {
   void *gk_dst = nullptr;
   int64_t gk_opts = -1, opt_generation = 0, gk_bufs = -1, buf_generation = 0;
   double graph_launches = 0;
+  bool capturing = false;
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
@@ -145,6 +146,10 @@ struct unifrac_ctx {
 namespace ufb {
 
 int fail(unifrac_ctx *ctx, int code, const std::string &msg);
+// Event record on the context's stream; while a CUDA graph is being captured
+// the record becomes a graph node (external event record), so replays
+// record the event too and it can be queried afterwards.
+void record_event(unifrac_ctx *ctx, cudaEvent_t ev);
 int cuda_fail(unifrac_ctx *ctx, cudaError_t e, const char *what);
 int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes);
 

@@ -321,6 +321,10 @@ def test_graph_replay_matches_eager(small, variant):
             ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED, out=out)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(out.cpu().numpy(), eager)
+            # timing events recorded inside the replayed graph stay queryable
+            stat = ub.STAT_PAIR_MS_UNWEIGHTED if variant == ub.UNWEIGHTED else ub.STAT_PAIR_MS_WEIGHTED
+            assert ctx.stat(stat) > 0
+            assert ctx.stat(ub.STAT_EMBED_MS) > 0
         full = ctx.run(variant, ub.MIXED, ub.OUT_FULL)
         full2 = ctx.run(variant, ub.MIXED, ub.OUT_FULL, out=full.clone().fill_(-1.0))
         torch.cuda.synchronize()
@@ -396,3 +400,37 @@ def test_both_variants_in_one_run(small, precision, layout):
     np.testing.assert_array_equal(both, np.concatenate([uw, wn]))
     host = run(w.tree, w.table, ub.BOTH, precision, layout, host=True)
     np.testing.assert_array_equal(host, np.concatenate([uw, wn]).astype(np.float64))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_paper_scale_workload_sampled_rows(variant):
+    """25,000 samples on a 200,000-tip tree (EMP-sized; about 396k kept
+    branches): one mixed-precision run of both variants, sampled rows
+    against the oracle, and every value in [0, 1]."""
+    import torch
+    w = _paper_scale()
+    N = w.table.n_samples
+    with ub.Context(w.tree, w.table) as ctx:
+        nb = ctx.output_bytes(ub.MIXED, ub.OUT_CONDENSED)
+        out = ctx.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED)
+        torch.cuda.synchronize()
+        got = out[variant * (nb // 4):(variant + 1) * (nb // 4)].cpu().numpy().astype(np.float64)
+        del out
+    assert got.min() >= 0.0 and got.max() <= 1.0
+    rows = np.random.default_rng(11 + variant).choice(N, size=2, replace=False)
+    ref, _ = oracle.unifrac_rows(w.tree, w.table, variant, rows)
+    for r, i in enumerate(rows):
+        j = np.arange(N)
+        a, b = np.minimum(i, j), np.maximum(i, j)
+        idx = a * N - a * (a + 1) // 2 + (b - a - 1)
+        vals = np.where(i == j, 0.0, got[np.where(i == j, 0, idx)])
+        assert np.max(np.abs(vals - ref[r])) <= TOL[ub.MIXED]
+
+
+_PAPER_SCALE = []
+
+
+def _paper_scale():
+    if not _PAPER_SCALE:
+        _PAPER_SCALE.append(synth.make_workload("tips200000_samples25000"))
+    return _PAPER_SCALE[0]
