@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--sparse-fraction", type=float, default=None,
+                    help="weighted dense/sparse split as a fraction of the largest study "
+                         "(instead of the autotuner)")
+    ap.add_argument("--uw-sparse-fraction", type=float, default=None,
+                    help="unweighted tensor-core/sparse split, same convention (0 = all "
+                         "tensor core)")
     ap.add_argument("--no-per-study", action="store_true",
                     help="skip the one-launch-per-study comparison (several studies)")
     ap.add_argument("--samples", type=int, default=None,
@@ -298,6 +304,14 @@ def main():
         for v in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED):
             rec = autotune.tune(ctx, v, ub.MIXED)
             tuned.update({k: rec[k] for k in rec if k != "cached"})
+    n_max = int(max(np.diff(w.table.study_offsets))) if w.table.study_offsets is not None else N
+    if args.sparse_fraction is not None:
+        ctx.set_option(ub.OPT_SPARSE_THRESHOLD, max(1, int(round(args.sparse_fraction * n_max))))
+        tuned["sparse_fraction"] = args.sparse_fraction
+    if args.uw_sparse_fraction is not None:
+        f = args.uw_sparse_fraction
+        ctx.set_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD, 0 if f == 0 else max(1, int(round(f * n_max))))
+        tuned["uw_sparse_fraction"] = f
     if not args.no_graph:
         ctx.set_option(ub.OPT_USE_GRAPH, 1)
     for _ in range(args.warmup):
@@ -417,6 +431,38 @@ def main():
             line["fp64_plain"] = {"skipped": str(exc)}
             torch.cuda.empty_cache()
 
+    if rank == 0 and not args.no_cpu_baseline:
+        s_idx, sub, block0 = baseline_study(w)
+        ws = synth.Workload(w.name, w.tree, sub, w.description)
+        Ns = sub.n_samples
+        rng = np.random.default_rng(7)
+        rows = np.sort(rng.choice(Ns, size=min(args.cpu_rows, Ns), replace=False))
+        ref, dt, threads = oracle_sample(ws, rows)
+        B = kept_branches(ws)
+        units = 2.0 * len(rows) * (Ns - 1) * B
+        line["cpu_baseline"] = {"value": units / dt, "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{len(rows)} seeded rows x {Ns} columns of study "
+                                          f"{s_idx}, both variants ({dt:.1f} s)"}
+        # error of this run's outputs on the same rows
+        errs = {}
+        for name, v, t in (("unweighted", 0, out_uw), ("weighted_normalized", 1, out_wn)):
+            got = t.cpu().numpy().astype(np.float64)
+            e = 0.0
+            for r, i in enumerate(rows):
+                j = np.arange(Ns)
+                a_, b_ = np.minimum(i, j), np.maximum(i, j)
+                idx = block0 + a_ * Ns - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
+                vals = np.where(i == j, 0.0, got[np.where(i == j, block0, idx)])
+                e = max(e, float(np.max(np.abs(vals - ref[v][r]))))
+            errs[name] = e
+        line["max_abs_err_vs_oracle"] = errs
+
+    # the device memory of the timed context is released before the
+    # end-to-end and per-study runs create contexts of their own
+    ctx.close()
+    torch.cuda.empty_cache()
+
     # end to end through the public API with host buffers
     if rank == 0 and not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -444,8 +490,6 @@ def main():
     if rank == 0 and w.table.study_offsets is not None and not args.no_per_study:
         # the same studies with one context and one launch sequence per study,
         # one study at a time (device memory), each run timed with events
-        ctx.close()
-        torch.cuda.empty_cache()
         per = 0.0
         for s_ in range(len(w.table.study_offsets) - 1):
             t_ = study_table(w.table, s_)
@@ -471,33 +515,6 @@ def main():
             "ms_per_step": per, "value": units_per_step / (per / 1e3),
             "batched_speedup": per / ms_per_step,
             "note": "sum of per-study runs (each its own context, tuned, warm)"}
-
-    if rank == 0 and not args.no_cpu_baseline:
-        s_idx, sub, block0 = baseline_study(w)
-        ws = synth.Workload(w.name, w.tree, sub, w.description)
-        Ns = sub.n_samples
-        rng = np.random.default_rng(7)
-        rows = np.sort(rng.choice(Ns, size=min(args.cpu_rows, Ns), replace=False))
-        ref, dt, threads = oracle_sample(ws, rows)
-        B = kept_branches(ws)
-        units = 2.0 * len(rows) * (Ns - 1) * B
-        line["cpu_baseline"] = {"value": units / dt, "unit": UNIT, "cores": threads,
-                                "kind": "oracle",
-                                "sample": f"{len(rows)} seeded rows x {Ns} columns of study "
-                                          f"{s_idx}, both variants ({dt:.1f} s)"}
-        # error of this run's outputs on the same rows
-        errs = {}
-        for name, v, t in (("unweighted", 0, out_uw), ("weighted_normalized", 1, out_wn)):
-            got = t.cpu().numpy().astype(np.float64)
-            e = 0.0
-            for r, i in enumerate(rows):
-                j = np.arange(Ns)
-                a_, b_ = np.minimum(i, j), np.maximum(i, j)
-                idx = block0 + a_ * Ns - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
-                vals = np.where(i == j, 0.0, got[np.where(i == j, block0, idx)])
-                e = max(e, float(np.max(np.abs(vals - ref[v][r]))))
-            errs[name] = e
-        line["max_abs_err_vs_oracle"] = errs
 
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -195,7 +195,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * as the context's options.  Candidates: the dense / sparse split of the
  * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
  * largest study) and of the unweighted tensor-core kernel
- * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/16 .. 1/4).
+ * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/32 .. 1/4).
  * Each candidate runs `repeats` times (>= 1, after one warm-up run) into
  * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
  * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the

@@ -771,7 +771,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
                                     P.n_win, spart, d_items, n_items)))
       return rc;
     record_event(ctx, ctx->ev_sp[0][1]);
-    if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, a, spart, d_items, n_items, o))) return rc;
+    if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, aq, spart, d_items, n_items, o))) return rc;
   } else {
     double *a = static_cast<double *>(ctx->persample.p);
     uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
@@ -1064,7 +1064,7 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
     option = UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD;
     const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
     cands.push_back({option, 0});  // everything on the tensor cores
-    for (int64_t num : {1, 2, 4}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
+    for (int64_t num : {1, 2, 4, 8}) cands.push_back({option, std::max<int64_t>(2, n * num / 32)});
   }
   const int saved_graph = ctx->opt_use_graph;
   ctx->opt_use_graph = 0;

@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int j = 0; j < AD; ++j) acc[i][j] = 0.0;
   part.zero();
-  int since_flush = 0;
+  // warps start their FP64 flush counters staggered, so the slow FP64 adds of
+  // one warp overlap the FP32 work of the others
+  int since_flush = (sizeof(T) == 4) ? (tid >> 5) * (flush / (kThreads / 32)) : 0;
   unsigned long long nsel = 0;
 
   auto load_stage = [&](int s, int buf, int n) {
@@ -227,11 +229,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         const int rows = min(BK, n - s * BK);
         const T *base = sbuf + (int64_t)((s & 1) * BK) * 2 * TILE;
-        for (int r = 0; r < rows; ++r) {
-          T a[8], b[8];
-          load8<T>(base + (r * 2 + 0) * TILE, ty, a);
-          load8<T>(base + (r * 2 + 1) * TILE, tx, b);
-          part.add(a, b);
+        if (rows == BK) {
+          // full stage: operands of the next branch are loaded before the
+          // current one is accumulated, so shared-memory latency overlaps math
+          T a[2][8], b[2][8];
+          load8<T>(base, ty, a[0]);
+          load8<T>(base + TILE, tx, b[0]);
+#pragma unroll
+          for (int r = 0; r < BK; ++r) {
+            if (r + 1 < BK) {
+              load8<T>(base + ((r + 1) * 2 + 0) * TILE, ty, a[(r + 1) & 1]);
+              load8<T>(base + ((r + 1) * 2 + 1) * TILE, tx, b[(r + 1) & 1]);
+            }
+            part.add(a[r & 1], b[r & 1]);
+          }
+        } else {
+          for (int r = 0; r < rows; ++r) {
+            T a[8], b[8];
+            load8<T>(base + (r * 2 + 0) * TILE, ty, a);
+            load8<T>(base + (r * 2 + 1) * TILE, tx, b);
+            part.add(a, b);
+          }
         }
         if constexpr (sizeof(T) == 4) {
           since_flush += rows;
@@ -263,14 +281,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lj >= sd.n) continue;
       if (li < lj) {
         const double den = Si + S[colJ + j];
-        double M;
         if constexpr (sizeof(T) == 4) {
-          M = acc[qi][qj];
+          // FP64 sums, FP32 quotient (the output precision)
+          double M = acc[qi][qj];
           if (sparse) M += (double)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j] * sp_inv;
+          put_pair(o, sd, li, lj, (double)ratio01_f32((float)(den - 2.0 * M), (float)den));
         } else {
-          M = part.get(qi, qj);
+          put_pair(o, sd, li, lj, ratio01(den - 2.0 * part.get(qi, qj), den));
         }
-        put_pair(o, sd, li, lj, ratio01(den - 2.0 * M, den));
       } else if (li == lj) {
         put_diag(o, sd, li);
       }

@@ -11,9 +11,11 @@
 // Digits and 0/1 presences are exact in BF16, so each plane's Gram
 // G_p = X diag(d_p) X^T is a sum of integers below 2^24 (as long as a sample
 // reaches fewer than 65,793 branches) and is exact in the FP32 TMEM
-// accumulator whatever its rounding.  The epilogue combines the planes in FP64:
-// G = sigma 2^-24 (65536 G_1 + 256 G_2 + G_3), again exact, and a_i uses the
-// same q_b, so the only error is the 2^-25 sigma quantisation of each length.
+// accumulator whatever its rounding.  The epilogue combines the planes in
+// 64-bit integers, G = 65536 G_1 + 256 G_2 + G_3 in units of sigma 2^-24, and
+// a_i uses the same q_b, so both sums of the ratio are exact; only the final
+// quotient is rounded (FP32, the output precision).  The error is the 2^-25
+// sigma quantisation of each length plus that last rounding.
 //
 // CTA = one 128 x 128 tile of sample pairs.  Warp 0 issues TMA loads (128B
 // swizzle) of a 64-branch K-tile of X for the row tile and of the three digit
@@ -186,8 +188,8 @@ __device__ __forceinline__ void tmem_ld_wait() {
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_d,
                const WorkItem *__restrict__ items, const uint32_t *__restrict__ kbits,
-               int32_t k_words, int32_t n_cols, const double *__restrict__ a,
-               const unsigned long long *__restrict__ spart, double scale, OutSpec o,
+               int32_t k_words, int32_t n_cols, const unsigned long long *__restrict__ aq,
+               const unsigned long long *__restrict__ spart, OutSpec o,
                unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcShared &sh = *reinterpret_cast<TcShared *>(
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const StudyDev sd = o.studies[it.study];
     const int64_t colI = (int64_t)it.tile_i * TC_BM, colJ = (int64_t)it.tile_j * TC_BN;
     const int li = (int)(colI + row) - sd.col0;
-    const double ai = a[colI + row];
+    const unsigned long long ai = aq[colI + row];
     for (int c = 0; c < TC_BN / 32; ++c) {
       uint32_t r0[32], r1[32], r2[32];
       if (n_sel > 0 && ok) {
@@ -318,12 +320,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int lj = (int)(colJ + col) - sd.col0;
         if (lj >= sd.n) continue;
         if (li < lj) {
-          double qsum = (double)__uint_as_float(r0[j]) * 65536.0 +
-                        (double)__uint_as_float(r1[j]) * 256.0 + (double)__uint_as_float(r2[j]);
-          if (spart) qsum += (double)spart[(int64_t)blockIdx.x * TC_BM * TC_BN + row * TC_BN + col];
-          const double g = scale * qsum;
-          const double A = ai + a[colJ + col];
-          put_pair(o, sd, li, lj, ratio01(A - 2.0 * g, A - g));
+          // all sums in units of the 24-bit lengths, exact 64-bit integers:
+          // G = 65536 G1 + 256 G2 + G3 (+ sparse part), A = a_i + a_j
+          unsigned long long g = ((unsigned long long)__float2uint_rn(__uint_as_float(r0[j])) << 16) +
+                                 ((unsigned long long)__float2uint_rn(__uint_as_float(r1[j])) << 8) +
+                                 (unsigned long long)__float2uint_rn(__uint_as_float(r2[j]));
+          if (spart) g += spart[(int64_t)blockIdx.x * TC_BM * TC_BN + row * TC_BN + col];
+          const unsigned long long A = ai + aq[colJ + col];
+          const float d = ratio01_f32((float)(A - 2 * g), (float)(A - g));
+          put_pair(o, sd, li, lj, (double)d);
         } else if (li == lj) {
           put_diag(o, sd, li);
         }
@@ -522,8 +527,9 @@ int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a) {
 size_t tc_smem_bytes() { return TC_SMEM; }
 
 int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *D,
-             const uint32_t *kbits, const double *a, const unsigned long long *spart,
-             const WorkItem *items, int32_t n_items, const OutSpec &o) {
+             const uint32_t *kbits, const unsigned long long *aq,
+             const unsigned long long *spart, const WorkItem *items, int32_t n_items,
+             const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   if (k_tc < TC_BK || k_tc % TC_BK) return fail(ctx, UNIFRAC_E_INVALID_ARG, "tensor-core K split");
   const int32_t n_kt = k_tc / TC_BK;
@@ -536,7 +542,7 @@ int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *
       cudaFuncSetAttribute(k_pairs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core kernel attribute");
   k_pairs_tc<<<n_items, TC_THREADS, TC_SMEM, ctx->stream>>>(
-      mx, md, items, kbits, k_words, ctx->n_cols, a, spart, ctx->tc_scale, o, ctx->d_counter);
+      mx, md, items, kbits, k_words, ctx->n_cols, aq, spart, o, ctx->d_counter);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core pair kernel");

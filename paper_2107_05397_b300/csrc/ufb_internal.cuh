@@ -113,7 +113,7 @@ struct unifrac_ctx {
 
   // ---- options
   int opt_uw_kernel = 0;
-  int opt_flush = 256;
+  int opt_flush = 512;
   int opt_persistent = -1;  // -1 auto
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
@@ -205,8 +205,10 @@ int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  int32_t n_items, const OutSpec &o);
 size_t tc_smem_bytes();
 // spart: null, or [n_items][TILE * TILE] u64 sums of q over the sparse positions.
+// aq: per-sample sums of the 24-bit lengths of the branches present (exact).
 int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *D,
-             const uint32_t *kbits, const double *a, const unsigned long long *spart,
-             const WorkItem *items, int32_t n_items, const OutSpec &o);
+             const uint32_t *kbits, const unsigned long long *aq,
+             const unsigned long long *spart, const WorkItem *items, int32_t n_items,
+             const OutSpec &o);
 
 }  // namespace ufb
