@@ -173,7 +173,7 @@ int unifrac_output_bytes(const unifrac_ctx *ctx, int precision, int layout,
 enum unifrac_option {
   UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL = 0, /* 0 auto (tensor core), 1 tensor core,
                                               2 bit-packed lookup (FP64 sums) */
-  UNIFRAC_OPT_WEIGHTED_FLUSH = 1,         /* FP32 branches per FP64 flush, 16..4096 */
+  UNIFRAC_OPT_WEIGHTED_FLUSH = 1,         /* FP32 branches per flush into the compensated total, 16..4096 */
   UNIFRAC_OPT_PERSISTENT = 2,             /* 0 one CTA per tile pair, 1 persistent
                                               work queue (default for many studies) */
   UNIFRAC_OPT_CTAS_PER_SM = 3,            /* persistent grid = SMs x this, 1..8 */

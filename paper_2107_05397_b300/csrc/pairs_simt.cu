@@ -1,5 +1,5 @@
-// Pair kernels on the CUDA cores: weighted normalized UniFrac (FP32 with FP64
-// flushes, or all-FP64) and the bit-packed lookup form of unweighted UniFrac.
+// Pair kernels on the CUDA cores: weighted normalized UniFrac (FP32 with a
+// two-level sum, or all-FP64) and the bit-packed lookup form of unweighted UniFrac.
 //
 // Section II of the paper: the distance is formed for every pair of samples,
 // giving an N x N matrix, in a weighted normalized and an unweighted variant.
@@ -122,6 +122,23 @@ struct MinAcc<float> {
   __device__ __forceinline__ double get(int i, int j) const {
     return (j & 1) ? (double)p[i][j >> 1].y : (double)p[i][j >> 1].x;
   }
+  // tot[row][col] += p for the 8 x 8 pairs this thread owns (own_row layout:
+  // columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, 16-byte vectors),
+  // then p = 0.  Only the owning thread touches these elements.
+  __device__ __forceinline__ void flush_to(float *tot, int ty, int tx) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+      float4 *lo = reinterpret_cast<float4 *>(tot + row * 128 + tx * 4);
+      float4 *hi = reinterpret_cast<float4 *>(tot + row * 128 + 64 + tx * 4);
+      float4 a = *lo, b = *hi;
+      a.x += p[i][0].x; a.y += p[i][0].y; a.z += p[i][1].x; a.w += p[i][1].y;
+      b.x += p[i][2].x; b.y += p[i][2].y; b.z += p[i][3].x; b.w += p[i][3].y;
+      *lo = a;
+      *hi = b;
+    }
+    zero();
+  }
 };
 
 template <>
@@ -142,7 +159,11 @@ struct MinAcc<double> {
   __device__ __forceinline__ double get(int i, int j) const { return p[i][j]; }
 };
 
-// T = float: FP32 partial sums, added into FP64 every `flush` selected branches.
+// T = float: FP32 partial sums in registers, added every `flush` selected
+// branches into an FP32 running total in shared memory (two-level summation:
+// each level sums at most max(flush, K / flush) terms, so the rounding error
+// stays near that of a sum of ~sqrt(K) terms); FP32 epilogue.  Keeping the
+// total out of registers lets two CTAs share an SM.
 // T = double: FP64 throughout.
 //
 // Hybrid split (FP32 form): positions [0, 32*kf_words) are the frequently
@@ -150,7 +171,7 @@ struct MinAcc<double> {
 // present in few samples, were summed by k_pairs_sparse<false> into spart
 // (per tile pair, 32-bit fixed point, scale 1 / sp_inv), added in the epilogue.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
     k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
                      int32_t kf_words, const uint32_t *__restrict__ spart, double sp_inv,
@@ -159,6 +180,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
   int32_t *list = reinterpret_cast<int32_t *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE);
+  // FP32 form: running totals [TILE][TILE] after the list
+  float *tot = reinterpret_cast<float *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE +
+                                         sizeof(int32_t) * kWinWords * WORD);
   __shared__ int32_t list_n;
   const bool sparse = (sizeof(T) == 4) && spart != nullptr;
 
@@ -171,17 +195,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int CPR = TILE * sizeof(T) / 16;  // 16-byte chunks per row
   constexpr int kEl = 16 / sizeof(T);
 
-  // FP32 form: part (FP32, current chunk) + acc (FP64).  FP64 form: part only.
-  constexpr int AD = (sizeof(T) == 4) ? 8 : 1;
-  double acc[AD][AD];
+  // FP32 form: part (registers, current chunk) + tot (shared memory).  FP64
+  // form: part only.
   MinAcc<T> part;
-#pragma unroll
-  for (int i = 0; i < AD; ++i)
-#pragma unroll
-    for (int j = 0; j < AD; ++j) acc[i][j] = 0.0;
   part.zero();
-  // warps start their FP64 flush counters staggered, so the slow FP64 adds of
-  // one warp overlap the FP32 work of the others
+  if constexpr (sizeof(T) == 4) {
+    // tot = 0 on the elements this thread owns
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = own_row(ty, i);
+      *reinterpret_cast<float4 *>(tot + row * TILE + tx * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4 *>(tot + row * TILE + 64 + tx * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  // warps start their flush counters staggered, so the flushes of one warp
+  // overlap the min / add work of the others
   int since_flush = (sizeof(T) == 4) ? (tid >> 5) * (flush / (kThreads / 32)) : 0;
   unsigned long long nsel = 0;
 
@@ -200,13 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
   auto flush_part = [&]() {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] += part.get(i, j);
-      part.zero();
-    }
+    if constexpr (sizeof(T) == 4) part.flush_to(tot, ty, tx);
   };
 
   for (int w0 = 0; w0 < kf_words; w0 += kWinWords) {
@@ -267,7 +289,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0 && counter) atomicAdd(counter, nsel);
 
-  // epilogue: d = (S_i + S_j - 2 M) / (S_i + S_j)
+  // epilogue: d = (S_i + S_j - 2 M) / (S_i + S_j); FP32 in the FP32 form
+  // (each term is within a few roundings of its exact value and the
+  // difference is taken once, so the error stays a few units of 2^-24 of
+  // S_i + S_j), FP64 in the FP64 form
+  const float sp_inv_f = (float)sp_inv;
 #pragma unroll
   for (int qi = 0; qi < 8; ++qi) {
     const int i = own_row(ty, qi);
@@ -280,13 +306,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int lj = (int)(colJ + j) - sd.col0;
       if (lj >= sd.n) continue;
       if (li < lj) {
-        const double den = Si + S[colJ + j];
         if constexpr (sizeof(T) == 4) {
-          // FP64 sums, FP32 quotient (the output precision)
-          double M = acc[qi][qj];
-          if (sparse) M += (double)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j] * sp_inv;
-          put_pair(o, sd, li, lj, (double)ratio01_f32((float)(den - 2.0 * M), (float)den));
+          const float den = (float)Si + (float)S[colJ + j];
+          float M = tot[i * TILE + j];
+          if (sparse)
+            M = __fmaf_rn((float)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j], sp_inv_f, M);
+          put_pair(o, sd, li, lj, (double)ratio01_f32(__fmaf_rn(-2.f, M, den), den));
         } else {
+          const double den = Si + S[colJ + j];
           put_pair(o, sd, li, lj, ratio01(den - 2.0 * part.get(qi, qj), den));
         }
       } else if (li == lj) {
@@ -628,7 +655,8 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const size_t elem = f64 ? sizeof(double) : sizeof(float);
-  const size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD;
+  const size_t smem = elem * 2 * BK * 2 * TILE + sizeof(int32_t) * kWinWords * WORD +
+                      (f64 ? 0 : sizeof(float) * TILE * TILE);  // FP32 running totals
   cudaError_t e;
   if (f64) {
     e = cudaFuncSetAttribute(k_pairs_weighted<double>,

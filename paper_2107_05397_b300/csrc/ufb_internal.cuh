@@ -113,7 +113,7 @@ struct unifrac_ctx {
 
   // ---- options
   int opt_uw_kernel = 0;
-  int opt_flush = 512;
+  int opt_flush = 256;
   int opt_persistent = -1;  // -1 auto
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
