@@ -720,15 +720,19 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   if (P.kind == RunPlan::WEIGHTED) {
     double *S = static_cast<double *>(ctx->persample.p);
     uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
-    uint8_t *rcb = P.n_win > 0 ? static_cast<uint8_t *>(ctx->rc.p) : nullptr;
-    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, rcb, P.kf_words * WORD, S)))
-      return rc;
-    if (P.n_win > 0 &&
-        (rc = build_rare_blocks(ctx, static_cast<const float *>(ctx->vals.p), nullptr, bits, rcb,
-                                P.kf_words, P.n_win, static_cast<uint32_t *>(ctx->bsize.p),
-                                static_cast<unsigned long long *>(ctx->boff.p),
-                                static_cast<uint8_t *>(ctx->blocks.p))))
-      return rc;
+    // dense values for the frequently present positions, sparse blocks built
+    // from the counts for the rest
+    const int32_t k_end = P.n_win > 0 ? P.kf_words * WORD : ctx->K;
+    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, k_end, S))) return rc;
+    if (P.n_win > 0) {
+      uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
+      if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, bits, rcb, nullptr))) return rc;
+      if ((rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words, P.n_win,
+                                  static_cast<uint32_t *>(ctx->bsize.p),
+                                  static_cast<unsigned long long *>(ctx->boff.p),
+                                  static_cast<uint8_t *>(ctx->blocks.p))))
+        return rc;
+    }
     record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 1.0;
@@ -751,8 +755,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
     if (P.n_win > 0) {
       uint32_t *rbits = static_cast<uint32_t *>(ctx->rbits.p);
       uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
-      if ((rc = pack_rare_presence(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
-      if ((rc = build_rare_blocks(ctx, nullptr, cnt, rbits, rcb, P.kf_words, P.n_win,
+      if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
+      if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
                                   static_cast<uint32_t *>(ctx->bsize.p),
                                   static_cast<unsigned long long *>(ctx->boff.p),
                                   static_cast<uint8_t *>(ctx->blocks.p))))

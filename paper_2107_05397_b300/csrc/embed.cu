@@ -79,25 +79,27 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
   if (any) reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)t * TILE)[lane] = s;
 }
 
-// Weighted packing.  Block (column tile t, branch block kb) of 8 warps; warp w
-// handles positions k = kb*KR + w, +8, ...; lane l owns 4 columns.  Writes
-// v[k][col] = len_k * cnt[perm[k]][col] / C_col for the flagged (k, t) rows and
-// the (t, k) bitmap words.  The mixed form computes v in FP32 (<= 3 roundings);
-// the FP64 form in FP64.
+// Weighted packing of the positions [0, k_end) (all of them, or the frequently
+// present ones when the rest go to the sparse blocks).  Block (column tile t,
+// branch block kb) of 8 warps; warp w handles positions k = kb*KR + w, +8, ...;
+// lane l owns 4 columns.  Writes v[k][col] = len_k * cnt[perm[k]][col] / C_col
+// for the flagged (k, t) rows and the (t, k) bitmap words.  The mixed form
+// computes v in FP32 (<= 3 roundings); the FP64 form in FP64.  k_end is K or a
+// multiple of 32, so bitmap words never straddle it.
 constexpr int KR = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack_weighted(
-    int32_t K, const int32_t *__restrict__ perm, const double *__restrict__ len_perm,
-    const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
-    int32_t n_tiles, const double *__restrict__ inv_total, T *__restrict__ vals,
-    int64_t ldv, uint32_t *__restrict__ bits, int32_t n_words, uint8_t *__restrict__ rc,
-    int32_t k_rare0, int32_t k_pad) {
+    int32_t K, int32_t k_end, const int32_t *__restrict__ perm,
+    const double *__restrict__ len_perm, const uint32_t *__restrict__ cnt,
+    const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_tiles,
+    const double *__restrict__ inv_total, T *__restrict__ vals, int64_t ldv,
+    uint32_t *__restrict__ bits, int32_t n_words) {
   const int t = blockIdx.x;
   const int k0 = blockIdx.y * KR;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t col = (int64_t)t * TILE + lane * 4;
-  const int k1 = min(k0 + KR, K);
+  const int k1 = min(k0 + KR, min(K, k_end));
   if constexpr (sizeof(T) == 4) {
     float inv[4];
 #pragma unroll
@@ -113,14 +115,6 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
       v.z = L * ((float)c.z * inv[2]);
       v.w = L * ((float)c.w * inv[3]);
       *reinterpret_cast<float4 *>(vals + (int64_t)k * ldv + col) = v;
-      if (rc && k >= k_rare0) {
-        // non-zero columns of the (branch, tile) row, for the sparse blocks
-        const int nz = __popc(__ballot_sync(0xffffffffu, v.x != 0.f)) +
-                       __popc(__ballot_sync(0xffffffffu, v.y != 0.f)) +
-                       __popc(__ballot_sync(0xffffffffu, v.z != 0.f)) +
-                       __popc(__ballot_sync(0xffffffffu, v.w != 0.f));
-        if (lane == 0) rc[(int64_t)t * k_pad + k] = (uint8_t)nz;
-      }
     }
   } else {
     double inv[4];
@@ -149,7 +143,7 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
       const int k = kw + j;
       if (k < K && flag[(int64_t)perm[k] * n_tiles + t]) word |= 1u << j;
     }
-    if (kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
+    if (kw < k_end && kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
   }
 }
 
@@ -239,13 +233,16 @@ __global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
 }
 
 // ---------------------------------------------------------------------------
-// Sparse blocks of the weighted kernel.  For every column tile t and window j of
-// kRareWin positions starting at p0 (the first rarely present position), one
-// block holds the tile's non-zero entries of the window's flagged rows:
+// Sparse blocks of the rarely present positions.  For every column tile t and
+// window j of kRareWin positions starting at p0 (the first rarely present
+// position), one block holds the tile's non-zero entries of the window's
+// flagged rows:
 //   u32 nrows, nent, off_ri, off_val        (16-byte header)
 //   u32 rowstart[nrows + 1]                 entry offset of each flagged row
 //   u8  ri[nent]       at off_ri            row of the tile (0..127) of each entry
-//   f32 val[nent]      at off_val           v[k][col] of each entry
+//   u32 val[nent]      at off_val           weighted blocks only: round(v * 2^s),
+//                                           v = len_k * cnt / C_col in FP32
+// An entry is a column with a non-zero count (its value may round to 0).
 // Flagged rows appear in position order and a row's local index is the count
 // of flagged positions of the tile before it in the window, so the pair kernel
 // finds a branch's entries from the tile bitmap alone.
@@ -312,15 +309,18 @@ __global__ void __launch_bounds__(1024) k_scan_sizes(int64_t n, const uint32_t *
 }
 
 // Fill one block per warp: rows in position order; each row's non-zero
-// columns are compacted with four ballots (column 4l + w of lane l).
-// VALUES: entries carry v from vals[k][col]; otherwise presences read from the
-// counts cnt[perm[k]][col] (no value section).
+// columns are compacted with four ballots (column 4l + w of lane l), reading
+// the counts cnt[perm[k]][col].  VALUES: entries also carry round(v * scale)
+// with v = len_k * (cnt * (1 / C_col)) in FP32, the same roundings as the
+// dense packing; scale is a power of two.
 template <bool VALUES>
 __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                             const uint32_t *__restrict__ bits, int32_t n_words,
                             const uint8_t *__restrict__ rc, int32_t k_pad,
-                            const float *__restrict__ vals, int64_t ldv,
-                            const uint32_t *__restrict__ cnt, const int32_t *__restrict__ perm,
+                            const uint32_t *__restrict__ cnt, int64_t ldc,
+                            const int32_t *__restrict__ perm,
+                            const double *__restrict__ len_perm,
+                            const double *__restrict__ inv_total, float scale,
                             const unsigned long long *__restrict__ boff,
                             uint8_t *__restrict__ blocks) {
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -329,6 +329,11 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
   const int64_t t = item / n_win;
   const int j = (int)(item % n_win);
   const int kb = p0 + kRareWin * j;
+  float inv[4] = {0.f, 0.f, 0.f, 0.f};
+  if constexpr (VALUES) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) inv[q] = (float)inv_total[t * TILE + 4 * lane + q];
+  }
   uint8_t *blk = blocks + boff[item];
   // header: count again (same loop as the size kernel)
   uint32_t nrows = 0, nent = 0;
@@ -350,7 +355,7 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
   uint32_t *hdr = reinterpret_cast<uint32_t *>(blk);
   uint32_t *rowstart = hdr + 4;
   uint8_t *ri = blk + off_ri;
-  float *val = reinterpret_cast<float *>(blk + off_val);
+  uint32_t *val = reinterpret_cast<uint32_t *>(blk + off_val);
   if (lane == 0) {
     hdr[0] = nrows;
     hdr[1] = nent;
@@ -387,39 +392,39 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
           ++nb;
         }
       }
-      float4 v[8];
+      uint4 c[8];
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
-        v[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        c[g] = make_uint4(0u, 0u, 0u, 0u);
         if (src[g] >= 0) {
           const int64_t k = kb + 32 * s + src[g];
-          if constexpr (VALUES) {
-            v[g] = *reinterpret_cast<const float4 *>(vals + k * ldv + t * TILE + 4 * lane);
-          } else {
-            const uint4 c = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[k] * ldv +
-                                                             t * TILE + 4 * lane);
-            v[g] = make_float4(c.x ? 1.f : 0.f, c.y ? 1.f : 0.f, c.z ? 1.f : 0.f, c.w ? 1.f : 0.f);
-          }
+          c[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[k] * ldc + t * TILE +
+                                                  4 * lane);
         }
       }
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         if (src[g] < 0) break;
         const uint32_t base = __shfl_sync(0xffffffffu, my_e, src[g]);
-        const float vv[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
-        const uint32_t B0 = __ballot_sync(0xffffffffu, vv[0] != 0.f);
-        const uint32_t B1 = __ballot_sync(0xffffffffu, vv[1] != 0.f);
-        const uint32_t B2 = __ballot_sync(0xffffffffu, vv[2] != 0.f);
-        const uint32_t B3 = __ballot_sync(0xffffffffu, vv[3] != 0.f);
+        const uint32_t cc[4] = {c[g].x, c[g].y, c[g].z, c[g].w};
+        const uint32_t B0 = __ballot_sync(0xffffffffu, cc[0] != 0u);
+        const uint32_t B1 = __ballot_sync(0xffffffffu, cc[1] != 0u);
+        const uint32_t B2 = __ballot_sync(0xffffffffu, cc[2] != 0u);
+        const uint32_t B3 = __ballot_sync(0xffffffffu, cc[3] != 0u);
         const uint32_t c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2);
         const uint32_t pos[4] = {(uint32_t)__popc(B0 & lt), c0 + (uint32_t)__popc(B1 & lt),
                                  c0 + c1 + (uint32_t)__popc(B2 & lt),
                                  c0 + c1 + c2 + (uint32_t)__popc(B3 & lt)};
+        float L = 0.f;
+        if constexpr (VALUES) L = (float)len_perm[kb + 32 * s + src[g]];
 #pragma unroll
         for (int w = 0; w < 4; ++w)
-          if (vv[w] != 0.f) {
+          if (cc[w] != 0u) {
             ri[base + pos[w]] = (uint8_t)(4 * lane + w);
-            if constexpr (VALUES) val[base + pos[w]] = vv[w];
+            if constexpr (VALUES) {
+              const float v = L * ((float)cc[w] * inv[w]);
+              val[base + pos[w]] = __float2uint_rn(v * scale);
+            }
           }
       }
       (void)nb;
@@ -429,11 +434,12 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
   }
 }
 
-// Presence packing of the rarely present positions [p0, K) for the unweighted
-// sparse kernel.  Block (column tile t, KR positions), warp per position: the
-// row's non-zero count rc, the (t, position) bitmap words (positions below p0
-// are never read) and aq[col] += q_k for every column where branch k is present.
-__global__ void __launch_bounds__(256) k_pack_rare_presence(
+// Packing of the rarely present positions [p0, K) for the sparse kernels.
+// Block (column tile t, KR positions), warp per position: the row's count of
+// non-zero columns rc, the (t, position) bitmap words (p0 is a multiple of 32;
+// words below it belong to the dense packing) and, when aq is given,
+// aq[col] += q_k for every column where branch k is present.
+__global__ void __launch_bounds__(256) k_pack_rare(
     int32_t K, int32_t p0, const int32_t *__restrict__ perm, const uint32_t *__restrict__ qperm,
     const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
     int32_t n_tiles, uint32_t *__restrict__ bits, int32_t n_words, uint8_t *__restrict__ rc,
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(256) k_pack_rare_presence(
     const int32_t b = perm[k];
     if (!flag[(int64_t)b * n_tiles + t]) continue;
     const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
-    const unsigned long long q = qperm[k];
+    const unsigned long long q = aq ? qperm[k] : 0ull;
     acc[0] += c.x ? q : 0ull;
     acc[1] += c.y ? q : 0ull;
     acc[2] += c.z ? q : 0ull;
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(256) k_pack_rare_presence(
 #pragma unroll
   for (int q = 0; q < 4; ++q) red[w][lane * 4 + q] = acc[q];
   __syncthreads();
-  if (threadIdx.x < TILE) {
+  if (aq && threadIdx.x < TILE) {
     unsigned long long sum = 0;
     for (int ww = 0; ww < kWarpsPerBlock; ++ww) sum += red[ww][threadIdx.x];
     if (sum) atomicAdd(aq + (int64_t)t * TILE + threadIdx.x, sum);
@@ -482,43 +488,44 @@ __global__ void __launch_bounds__(256) k_pack_rare_presence(
 
 }  // namespace
 
-int pack_rare_presence(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                       int32_t kf_words, uint32_t *bits, uint8_t *rc, unsigned long long *aq) {
+int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t kf_words,
+              uint32_t *bits, uint8_t *rc, unsigned long long *aq) {
   const int32_t p0 = kf_words * WORD;
   if (p0 >= ctx->K || ctx->n_tiles == 0) return UNIFRAC_OK;
   dim3 grid(ctx->n_tiles, (ctx->K - p0 + KR - 1) / KR);
-  k_pack_rare_presence<<<grid, 256, 0, ctx->stream>>>(
-      ctx->K, p0, ctx->d_perm, ctx->d_qperm, cnt, flag, ctx->n_cols, ctx->n_tiles, bits,
-      ctx->K_pad / WORD, rc, ctx->K_pad, aq);
+  k_pack_rare<<<grid, 256, 0, ctx->stream>>>(ctx->K, p0, ctx->d_perm, ctx->d_qperm, cnt, flag,
+                                             ctx->n_cols, ctx->n_tiles, bits, ctx->K_pad / WORD,
+                                             rc, ctx->K_pad, aq);
   ctx->stat_launches += 1;
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "presence packing");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse packing");
   return UNIFRAC_OK;
 }
 
-int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *cnt,
-                      const uint32_t *bits, const uint8_t *rc, int32_t kf_words, int32_t n_win,
-                      uint32_t *bsize, unsigned long long *boff, uint8_t *blocks) {
+int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
+                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
+                      unsigned long long *boff, uint8_t *blocks) {
   cudaStream_t st = ctx->stream;
   const int64_t items = (int64_t)ctx->n_tiles * n_win;
   if (items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const int32_t p0 = kf_words * WORD;
   const unsigned grid = (unsigned)((items * 32 + 255) / 256);
-  if (vals) {
+  if (values) {
     k_rare_sizes<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                              ctx->K_pad, bsize);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                            ctx->K_pad, vals, ctx->n_cols, nullptr, nullptr,
+                                            ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm,
+                                            ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale,
                                             boff, blocks);
   } else {
     k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                               ctx->K_pad, bsize);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                             ctx->K_pad, nullptr, ctx->n_cols, cnt, ctx->d_perm,
-                                             boff, blocks);
+                                             ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm, nullptr,
+                                             nullptr, 1.f, boff, blocks);
   }
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();
@@ -556,21 +563,20 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
 }
 
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bool f64,
-                  void *vals, uint32_t *bits, uint8_t *rc, int32_t k_rare0, double *S) {
+                  void *vals, uint32_t *bits, int32_t k_end, double *S) {
   cudaStream_t st = ctx->stream;
   const int32_t n_words = ctx->K_pad / WORD;
-  if (ctx->K > 0 && ctx->n_tiles > 0) {
-    dim3 grid(ctx->n_tiles, (ctx->K + KR - 1) / KR);
+  k_end = min(k_end, ctx->K);
+  if (k_end > 0 && ctx->n_tiles > 0) {
+    dim3 grid(ctx->n_tiles, (k_end + KR - 1) / KR);
     if (f64)
       k_pack_weighted<double><<<grid, 256, 0, st>>>(
-          ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
-          ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words, nullptr,
-          ctx->K_pad, ctx->K_pad);
+          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words);
     else
       k_pack_weighted<float><<<grid, 256, 0, st>>>(
-          ctx->K, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
-          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words, rc,
-          k_rare0, ctx->K_pad);
+          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words);
     ctx->stat_launches += 1;
   }
   if (ctx->n_cols > 0) {

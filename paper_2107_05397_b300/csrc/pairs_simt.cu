@@ -324,196 +324,230 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
 }
 
 // ----------------------------------------------------------------------------
-// weighted normalized, rarely present branches (FP32 form)
+// rarely present branches: weighted normalized (FP32 form) and unweighted
 //
 // For every tile pair, the branches at positions >= 32*kf_words present in both
-// tiles contribute min(v_bi, v_bj) only for the rows that hold them.  A CTA of
-// 32 warps walks the windows of kRareWin positions: warp 0 lists the branches
-// present in both tiles and keeps the tiles' bitmap words and prefix
-// popcounts; all threads copy the two tiles' compact sparse blocks of the next
-// window into shared memory while the current one is processed (blocks
-// larger than the staging area are read in place); each warp takes branches,
-// finds their entries by popcount rank and walks the nI x nJ pairs, adding
-// round(min * 2^s) into a 128 x 128 shared accumulator of 32-bit integers
-// (2^s keeps every pair sum below 2^31; integer sums make the result
-// independent of the order of the atomics).  The accumulator goes to spart.
+// tiles contribute only for the rows that hold them: min(V_bi, V_bj) (weighted)
+// or the 24-bit length q_b (unweighted) for every pair of a row of tile I and
+// a row of tile J holding b.  The compact blocks (one per tile and window of
+// kRareWin positions) list each flagged row's entries; the weighted blocks hold
+// V = round(v * 2^s), and rounding is monotone, so
+// min(V_bi, V_bj) = round(min(v_bi, v_bj) * 2^s); 2^s keeps every pair sum
+// below 2^31.  Sums go into a 128 x 128 shared accumulator of integers (exact,
+// independent of the order of the atomics), rows padded to TILE + 1 words so
+// that lanes on one column of different rows use different banks; it is
+// copied to spart at the end.
+//
+// A CTA of 32 warps per tile pair; each warp walks its own bitmap words
+// (kf_words + warp, + 32, ...) with no CTA-wide barrier in the loop.  For a
+// word, the rank of its first flagged row in the window's block is the
+// popcount of the block's earlier words; lane l takes the branch of bit l when
+// it is flagged in both tiles.  An incidence of at most kSmall pairs is walked
+// by its lane alone, reading the block (read-only global loads).  A larger one
+// is walked by the whole warp: one tile's rows (the "lane side") are held in
+// registers, lane (g, b) = (lane / nL, lane % nL) holding row b, and the other
+// tile's rows (staged by the warp in its shared scratch as packed (value, row)
+// entries) are swept a = g, g + G, ... with G = 32 / nL groups (rows beyond
+// 32 on the lane side in further passes), so each update is one broadcast
+// shared load, a min and one shared atomic.  The lane side is the tile whose
+// row count fills more lanes.
 
-constexpr int kSpThreads = 1024;  // one warp per bitmap word of a window
-static_assert(kSpThreads / 32 == kWinWords, "sparse kernel: one warp per window word");
-constexpr int kSmall = 16;  // pairs a single lane walks alone
+constexpr int kSpThreads = 1024;
+static_assert(kRareWin == kWinWords * WORD, "sparse blocks: one window is kWinWords bitmap words");
+constexpr int kSpWarps = kSpThreads / 32;
+constexpr int kSmall = 16;         // pairs a single lane walks alone
+constexpr int kAccLd = TILE + 1;   // padded accumulator row
 
-// PRES = false: weighted form, entries carry v; adds round(min(v_i, v_j) * 2^s)
-//               into 32-bit accumulators (spart: u32 per pair).
-// PRES = true:  unweighted form, entries are presences; adds the branch's
-//               24-bit length q[k] into 64-bit accumulators (spart: u64 per
-//               pair), exact -- the tensor-core epilogue adds it to its digit sums.
+// PRES = false: weighted form, entries carry V; 32-bit accumulators (spart u32).
+// PRES = true:  unweighted form, entries are presences; adds q[k] into 64-bit
+//               accumulators (spart u64), exact -- the tensor-core epilogue adds
+//               it to its digit sums.
 template <bool PRES>
 struct SparseCfg {
   using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
-  static constexpr int kStage = PRES ? 16 * 1024 : 24 * 1024;  // one tile's block
-  static constexpr size_t kSmem = (size_t)TILE * TILE * sizeof(Acc) + 4 * kStage;
+  static constexpr size_t kAccBytes = ((size_t)TILE * kAccLd * sizeof(Acc) + 15) / 16 * 16;
+  // one side of an incidence staged per warp: (value << 32 | row) u64 entries
+  // (weighted) or row bytes (unweighted), TILE at most
+  static constexpr size_t kScratch = (size_t)TILE * (PRES ? 1 : 8);
+  static constexpr size_t kSmem = kAccBytes + (size_t)kSpWarps * kScratch;
 };
 
 template <bool PRES>
 __global__ void __launch_bounds__(kSpThreads, 1)
     k_pairs_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
-                   int32_t n_words, int32_t kf_words, int32_t n_win,
+                   int32_t n_words, int32_t kf_words, int32_t k_words, int32_t n_win,
                    const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
-                   float sp_scale, const uint32_t *__restrict__ qlen,
+                   const uint32_t *__restrict__ qlen,
                    typename SparseCfg<PRES>::Acc *__restrict__ spart,
                    unsigned long long *__restrict__ n_updates) {
   using Acc = typename SparseCfg<PRES>::Acc;
-  constexpr int kStageBytes = SparseCfg<PRES>::kStage;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc *sacc = reinterpret_cast<Acc *>(smem_raw);
-  uint8_t *stage = smem_raw + (size_t)TILE * TILE * sizeof(Acc);  // [2 bufs][2 tiles][kStageBytes]
-  __shared__ uint32_t swI[2][kWinWords], swJ[2][kWinWords];
-  __shared__ int32_t spI[2][kWinWords], spJ[2][kWinWords];
-  __shared__ unsigned long long boI[2], boJ[2];
-  __shared__ int32_t inI[2], inJ[2];  // 1 = block staged in shared memory
+  Acc *sacc = reinterpret_cast<Acc *>(smem_raw);  // [TILE][kAccLd]
+  // (p / n, p % n) for lanes p < 32 and n = 1..32: group and row of a lane when
+  // the lane side has n rows; gtab[n-1] = 32 / n groups; fillv[n-1] = lanes a
+  // lane side of n rows keeps busy (n > 32: n / passes) -- no divisions later
+  __shared__ uint16_t divtab[32][32];
+  __shared__ uint8_t gtab[32];
+  __shared__ uint8_t fillv[TILE];
 
   const WorkItem it = items[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
-  const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
+  unsigned char *scr = smem_raw + SparseCfg<PRES>::kAccBytes + warp * SparseCfg<PRES>::kScratch;
+  unsigned long long *eS = reinterpret_cast<unsigned long long *>(scr);  // weighted
+  uint8_t *rS = scr;                                                     // unweighted
   unsigned long long my_updates = 0;
-  for (int x = tid; x < TILE * TILE; x += kSpThreads) sacc[x] = Acc(0);
-
-  auto prepare = [&](int j, int buf) {
-    const int w0 = kf_words + j * kWinWords;
-    if (warp == 0) {
-      const int w = w0 + lane;
-      const uint32_t mi = (w < n_words) ? bI[w] : 0u, mj = (w < n_words) ? bJ[w] : 0u;
-      swI[buf][lane] = mi;
-      swJ[buf][lane] = mj;
-      int ci = __popc(mi), cj = __popc(mj);
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int yi = __shfl_up_sync(0xffffffffu, ci, off);
-        const int yj = __shfl_up_sync(0xffffffffu, cj, off);
-        if (lane >= off) {
-          ci += yi;
-          cj += yj;
-        }
-      }
-      spI[buf][lane] = ci - __popc(mi);
-      spJ[buf][lane] = cj - __popc(mj);
+  for (int x = tid; x < TILE * kAccLd; x += kSpThreads) sacc[x] = Acc(0);
+  {
+    const int n = tid / 32 + 1, p = tid % 32;  // kSpThreads == 32 * 32
+    divtab[n - 1][p] = (uint16_t)(((p / n) << 8) | (p % n));
+    if (tid < 32) gtab[tid] = (uint8_t)(32 / (tid + 1));
+    if (tid < TILE) {
+      const int m = tid + 1;
+      fillv[tid] = (uint8_t)(m <= 32 ? (32 / m) * m : m / ((m + 31) / 32));
     }
-    const int64_t itemI = (int64_t)it.tile_i * n_win + j, itemJ = (int64_t)it.tile_j * n_win + j;
-    const unsigned long long oI = boff[itemI], oJ = boff[itemJ];
-    const uint32_t zI = (uint32_t)(boff[itemI + 1] - oI), zJ = (uint32_t)(boff[itemJ + 1] - oJ);
-    if (tid == 0) {
-      boI[buf] = oI;
-      boJ[buf] = oJ;
-      inI[buf] = zI <= (uint32_t)kStageBytes;
-      inJ[buf] = zJ <= (uint32_t)kStageBytes;
-    }
-    uint8_t *dI = stage + (size_t)(2 * buf) * kStageBytes, *dJ = dI + kStageBytes;
-    if (zI <= (uint32_t)kStageBytes)
-      for (uint32_t c = tid; c < zI / 16; c += kSpThreads) cp_async16(dI + 16 * c, blocks + oI + 16 * c);
-    if (zJ <= (uint32_t)kStageBytes)
-      for (uint32_t c = tid; c < zJ / 16; c += kSpThreads) cp_async16(dJ + 16 * c, blocks + oJ + 16 * c);
-  };
-
-  if (n_win > 0) {
-    prepare(0, 0);
-    cp_commit();
   }
-  for (int j = 0; j < n_win; ++j) {
-    const int buf = j & 1;
-    if (j + 1 < n_win) {
-      prepare(j + 1, buf ^ 1);
-      cp_commit();
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
+  __syncthreads();
+
+  const int64_t tI = it.tile_i, tJ = it.tile_j;
+  const uint32_t *bI = bits + tI * n_words;
+  const uint32_t *bJ = bits + tJ * n_words;
+  const uint32_t below = (1u << lane) - 1u;
+  for (int w = kf_words + warp; w < k_words; w += kSpWarps) {
+    const uint32_t mI = __ldg(bI + w), mJ = __ldg(bJ + w);
+    const uint32_t both = mI & mJ;
+    if (both == 0u) continue;  // warp-uniform
+    const int j = (w - kf_words) / kWinWords;
+    const int wq = (w - kf_words) - j * kWinWords;
+    const int w0 = kf_words + j * kWinWords;
+    // rows of the window's blocks before this word
+    int cI = 0, cJ = 0;
+    if (lane < wq) {
+      cI = __popc(__ldg(bI + w0 + lane));
+      cJ = __popc(__ldg(bJ + w0 + lane));
     }
-    __syncthreads();
-    const uint8_t *blkI = inI[buf] ? stage + (size_t)(2 * buf) * kStageBytes : blocks + boI[buf];
-    const uint8_t *blkJ =
-        inJ[buf] ? stage + (size_t)(2 * buf + 1) * kStageBytes : blocks + boJ[buf];
-    const uint32_t *hI = reinterpret_cast<const uint32_t *>(blkI);
-    const uint32_t *hJ = reinterpret_cast<const uint32_t *>(blkJ);
-    const uint32_t *rsI = hI + 4, *rsJ = hJ + 4;
-    const uint8_t *riI = blkI + hI[2], *riJ = blkJ + hJ[2];
-    const float *vI = reinterpret_cast<const float *>(blkI + hI[3]);
-    const float *vJ = reinterpret_cast<const float *>(blkJ + hJ[3]);
-    const int wbase = (kf_words + j * kWinWords) * WORD;
-    // Warp w takes bitmap word w of the window and lane l its bit: the branch
-    // at position wbase + 32 w + l, if present in both tiles.  A branch with
-    // at most kSmall pairs is walked by its lane alone, larger ones by the
-    // whole warp.
-    {
-      const int wq = warp;
-      const uint32_t both = swI[buf][wq] & swJ[buf][wq];
-      const bool mine = (both >> lane) & 1u;
-      int k = 0, nI = 0, nJ = 0;
-      uint32_t sI = 0, sJ = 0;
-      if (mine) {
-        k = wbase + 32 * wq + lane;
-        const uint32_t below = (1u << lane) - 1u;
-        const int rI = spI[buf][wq] + __popc(swI[buf][wq] & below);
-        const int rJ = spJ[buf][wq] + __popc(swJ[buf][wq] & below);
-        if (rI < (int)hI[0] && rJ < (int)hJ[0]) {  // defensive: the rows must exist
-          sI = rsI[rI];
-          sJ = rsJ[rJ];
-          nI = (int)(rsI[rI + 1] - sI);
-          nJ = (int)(rsJ[rJ + 1] - sJ);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      cI += __shfl_xor_sync(0xffffffffu, cI, off);
+      cJ += __shfl_xor_sync(0xffffffffu, cJ, off);
+    }
+    const uint8_t *blkI = blocks + boff[tI * n_win + j];
+    const uint8_t *blkJ = blocks + boff[tJ * n_win + j];
+    const uint4 hI = __ldg(reinterpret_cast<const uint4 *>(blkI));
+    const uint4 hJ = __ldg(reinterpret_cast<const uint4 *>(blkJ));
+    const uint32_t *rsI = reinterpret_cast<const uint32_t *>(blkI) + 4;
+    const uint32_t *rsJ = reinterpret_cast<const uint32_t *>(blkJ) + 4;
+    const uint8_t *riI = blkI + hI.z, *riJ = blkJ + hJ.z;
+    const uint32_t *vI = reinterpret_cast<const uint32_t *>(blkI + hI.w);
+    const uint32_t *vJ = reinterpret_cast<const uint32_t *>(blkJ + hJ.w);
+
+    int nI = 0, nJ = 0;
+    uint32_t sI = 0, sJ = 0;
+    uint32_t qk = 0;
+    if ((both >> lane) & 1u) {
+      const int rI = cI + __popc(mI & below);
+      const int rJ = cJ + __popc(mJ & below);
+      if (rI < (int)hI.x && rJ < (int)hJ.x) {  // defensive: the rows must exist
+        sI = __ldg(rsI + rI);
+        sJ = __ldg(rsJ + rJ);
+        nI = (int)(__ldg(rsI + rI + 1) - sI);
+        nJ = (int)(__ldg(rsJ + rJ + 1) - sJ);
+        // a row of a tile has 1..TILE entries; anything else is skipped
+        if (nI < 1 || nI > TILE || nJ < 1 || nJ > TILE) nI = nJ = 0;
+      }
+      if constexpr (PRES) qk = __ldg(qlen + 32 * w + lane);
+    }
+    const int total = nI * nJ;
+    my_updates += (unsigned long long)total;
+    if (total > 0 && total <= kSmall) {
+      for (int a = 0; a < nI; ++a) {
+        const int ra = (int)__ldg(riI + sI + a) * kAccLd;
+        uint32_t va = 0u;
+        if constexpr (!PRES) va = __ldg(vI + sI + a);
+        for (int b = 0; b < nJ; ++b) {
+          Acc *dst = &sacc[ra + (int)__ldg(riJ + sJ + b)];
+          if constexpr (PRES) {
+            atomicAdd(dst, (unsigned long long)qk);
+          } else {
+            atomicAdd(dst, min(va, __ldg(vJ + sJ + b)));
+          }
         }
       }
-      const int total = nI * nJ;
-      my_updates += (unsigned long long)total;
-      unsigned long long qk = 0;
-      if constexpr (PRES) qk = (total > 0) ? __ldg(qlen + k) : 0ull;
-      if (total > 0 && total <= kSmall) {
-        for (int a = 0; a < nI; ++a) {
-          const int ra = (int)riI[sI + a] * TILE;
-          float va = 0.f;
-          if constexpr (!PRES) va = vI[sI + a];
-          for (int b = 0; b < nJ; ++b) {
-            Acc *dst = &sacc[ra + (int)riJ[sJ + b]];
+    }
+    // warp-walked incidences: the owning lane picks the lane side (the tile
+    // whose row count fills more lanes) and packs the descriptor
+    const bool is_big = total > kSmall;
+    uint32_t desc = 0, sL = 0, sT = 0;
+    if (is_big) {
+      const bool lJ = fillv[nJ - 1] >= fillv[nI - 1];
+      desc = lJ ? ((uint32_t)nJ | ((uint32_t)nI << 8) | (1u << 16))
+                : ((uint32_t)nI | ((uint32_t)nJ << 8));
+      sL = lJ ? sJ : sI;
+      sT = lJ ? sI : sJ;
+    }
+    uint32_t big = __ballot_sync(0xffffffffu, is_big);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t d = __shfl_sync(0xffffffffu, desc, src);
+      const uint32_t bsL = __shfl_sync(0xffffffffu, sL, src);
+      const uint32_t bsT = __shfl_sync(0xffffffffu, sT, src);
+      uint32_t bq = 0;
+      if constexpr (PRES) bq = __shfl_sync(0xffffffffu, qk, src);
+      const int nL = (int)(d & 0xffu), nT = (int)((d >> 8) & 0xffu);
+      const bool laneJ = (d >> 16) != 0u;
+      const uint8_t *riL = laneJ ? riJ : riI, *riT = laneJ ? riI : riJ;
+      const uint32_t *vL = laneJ ? vJ : vI, *vT = laneJ ? vI : vJ;
+      const int mL = laneJ ? 1 : kAccLd, mT = laneJ ? kAccLd : 1;  // accumulator strides
+      // stage the swept side: (value << 32 | row) or the row byte
+      for (int x = lane; x < nT; x += 32) {
+        if constexpr (PRES) {
+          rS[x] = __ldg(riT + bsT + x);
+        } else {
+          eS[x] = ((unsigned long long)__ldg(vT + bsT + x) << 32) | __ldg(riT + bsT + x);
+        }
+      }
+      __syncwarp();
+      if (nL <= 32) {
+        const uint32_t t0 = divtab[nL - 1][lane];
+        const int g = (int)(t0 >> 8), b = (int)(t0 & 0xffu), G = gtab[nL - 1];
+        if (g < G) {
+          const int base = (int)__ldg(riL + bsL + b) * mL;
+          uint32_t vb = 0u;
+          if constexpr (!PRES) vb = __ldg(vL + bsL + b);
+#pragma unroll 2
+          for (int a = g; a < nT; a += G) {
             if constexpr (PRES) {
-              atomicAdd(dst, qk);
+              atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
             } else {
-              atomicAdd(dst, __float2uint_rn(fminf(va, vJ[sJ + b]) * sp_scale));
+              const unsigned long long e = eS[a];
+              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT],
+                        min(vb, (uint32_t)(e >> 32)));
+            }
+          }
+        }
+      } else {
+        for (int b = lane; b < nL; b += 32) {
+          const int base = (int)__ldg(riL + bsL + b) * mL;
+          uint32_t vb = 0u;
+          if constexpr (!PRES) vb = __ldg(vL + bsL + b);
+#pragma unroll 2
+          for (int a = 0; a < nT; ++a) {
+            if constexpr (PRES) {
+              atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
+            } else {
+              const unsigned long long e = eS[a];
+              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT],
+                        min(vb, (uint32_t)(e >> 32)));
             }
           }
         }
       }
-      uint32_t big = __ballot_sync(0xffffffffu, total > kSmall);
-      while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const int bnI = __shfl_sync(0xffffffffu, nI, src);
-        const int bnJ = __shfl_sync(0xffffffffu, nJ, src);
-        const uint32_t bsI = __shfl_sync(0xffffffffu, sI, src);
-        const uint32_t bsJ = __shfl_sync(0xffffffffu, sJ, src);
-        const unsigned long long bq = __shfl_sync(0xffffffffu, qk, src);
-        const int btotal = bnI * bnJ;
-        // pairs p = lane, lane+32, ... walked as (a, b) = (p / bnJ, p % bnJ)
-        int a = lane / bnJ, bb = lane - (lane / bnJ) * bnJ;
-        const int da = 32 / bnJ, db = 32 - (32 / bnJ) * bnJ;
-        for (int p = lane; p < btotal; p += 32) {
-          Acc *dst = &sacc[(int)riI[bsI + a] * TILE + (int)riJ[bsJ + bb]];
-          if constexpr (PRES) {
-            atomicAdd(dst, bq);
-          } else {
-            atomicAdd(dst, __float2uint_rn(fminf(vI[bsI + a], vJ[bsJ + bb]) * sp_scale));
-          }
-          a += da;
-          bb += db;
-          if (bb >= bnJ) {
-            bb -= bnJ;
-            ++a;
-          }
-        }
-      }
+      __syncwarp();  // scratch is rewritten by the next incidence
     }
-    __syncthreads();
   }
-  uint4 *dst = reinterpret_cast<uint4 *>(spart + (int64_t)blockIdx.x * TILE * TILE);
-  const uint4 *src = reinterpret_cast<const uint4 *>(sacc);
-  for (int x = tid; x < TILE * TILE * (int)sizeof(Acc) / 16; x += kSpThreads) dst[x] = src[x];
+  __syncthreads();
+  Acc *dst = spart + (int64_t)blockIdx.x * TILE * TILE;
+  for (int x = tid; x < TILE * TILE; x += kSpThreads) dst[x] = sacc[(x / TILE) * kAccLd + x % TILE];
   // pair updates done (statistics)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) my_updates += __shfl_xor_sync(0xffffffffu, my_updates, off);
@@ -675,7 +709,8 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
                                (int)kSm);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
       k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
-          items, bits, n_words, kf_words, n_win, blocks, boff, ctx->sp_scale, nullptr, spart,
+          items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+          nullptr, spart,
           ctx->d_counter + 4);
       ctx->stat_launches += 1;
     }
@@ -704,7 +739,8 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
       cudaFuncSetAttribute(k_pairs_sparse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSm);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
   k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
-      items, bits, n_words, kf_words, n_win, blocks, boff, 1.0f, ctx->d_qperm, spart,
+      items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+      ctx->d_qperm, spart,
       ctx->d_counter + 4);
   ctx->stat_launches += 1;
   e = cudaGetLastError();

@@ -159,23 +159,23 @@ int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes);
 int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 
 // packing ---------------------------------------------------------------------
-// Branch-major values v[k][col] = len_k * cnt / C_col (float or double), the
-// (tile, k) nonzero bitmaps, and per-column sums S_col = sum_k v[k][col] (FP64).
-// FP32 form also writes the non-zero count rc[n_tiles][K_pad] of each flagged
-// (branch, tile) row at positions >= k_rare0.
+// Branch-major values v[k][col] = len_k * cnt / C_col (float or double) and the
+// (tile, k) nonzero bitmap words of the positions k < k_end (k_end: K, or a
+// multiple of 32), and per-column sums S_col = sum_k v[k][col] (FP64).
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                  bool f64, void *vals, uint32_t *bits, uint8_t *rc, int32_t k_rare0,
-                  double *S);
+                  bool f64, void *vals, uint32_t *bits, int32_t k_end, double *S);
 // Sparse blocks of positions >= 32 * kf_words, one per (tile, window of
 // kRareWin positions): sizes, byte offsets boff[n_tiles * n_win + 1] and fill.
 // Values come from vals (weighted) or, when vals is null, presences from cnt.
-int build_rare_blocks(unifrac_ctx *ctx, const float *vals, const uint32_t *cnt,
-                      const uint32_t *bits, const uint8_t *rc, int32_t kf_words, int32_t n_win,
-                      uint32_t *bsize, unsigned long long *boff, uint8_t *blocks);
-// Presence packing of positions >= 32 * kf_words for the unweighted sparse
-// kernel: bitmap words, row non-zero counts and aq[col] += q_k.
-int pack_rare_presence(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                       int32_t kf_words, uint32_t *bits, uint8_t *rc, unsigned long long *aq);
+// values: weighted blocks (fixed-point values round(v * sp_scale)); else
+// presence blocks.  Both read the counts.
+int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
+                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
+                      unsigned long long *boff, uint8_t *blocks);
+// Packing of positions >= 32 * kf_words for the sparse kernels: bitmap words,
+// row non-zero counts and, when aq is given, aq[col] += q_k.
+int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t kf_words,
+              uint32_t *bits, uint8_t *rc, unsigned long long *aq);
 // Unweighted sparse pairs (u64 per pair) of positions >= 32 * kf_words.
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
                           const uint8_t *blocks, const unsigned long long *boff, int32_t n_win,
