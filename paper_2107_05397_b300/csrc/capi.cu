@@ -639,8 +639,10 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
         rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
         ents += (uint64_t)ctx->nb_perm[k];
       }
+      // per block: 16-byte header, rowstart, two 16-byte alignments (<= 80 in
+      // all); 8 bytes per (value, row) entry
       const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
-      const uint64_t bound = nblk * 80 + 4 * rows + 5 * ents + 64;
+      const uint64_t bound = nblk * 80 + 4 * rows + 8 * ents + 64;
       if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
       if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
       if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
@@ -676,6 +678,8 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
         rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
         ents += (uint64_t)ctx->nb_perm[k];
       }
+      // per block: 16-byte header, rowstart, two 16-byte alignments (<= 80 in
+      // all); 1 byte per row entry
       const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
       const uint64_t bound = nblk * 80 + 4 * rows + ents + 64;
       if ((rc = grow(ctx, ctx->rbits, (size_t)ctx->n_tiles * n_words * 4))) return rc;

@@ -237,11 +237,12 @@ __global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
 // window j of kRareWin positions starting at p0 (the first rarely present
 // position), one block holds the tile's non-zero entries of the window's
 // flagged rows:
-//   u32 nrows, nent, off_ri, off_val        (16-byte header)
+//   u32 nrows, nent, off_ent, 0             (16-byte header)
 //   u32 rowstart[nrows + 1]                 entry offset of each flagged row
-//   u8  ri[nent]       at off_ri            row of the tile (0..127) of each entry
-//   u32 val[nent]      at off_val           weighted blocks only: round(v * 2^s),
-//                                           v = len_k * cnt / C_col in FP32
+//   entries at off_ent (16-byte aligned), one per non-zero column:
+//     weighted blocks: u64 (V << 32) | r, V = round(v * 2^s) with
+//                      v = len_k * cnt / C_col in FP32, r the row of the tile
+//     presence blocks: u8 r
 // An entry is a column with a non-zero count (its value may round to 0).
 // Flagged rows appear in position order and a row's local index is the count
 // of flagged positions of the tile before it in the window, so the pair kernel
@@ -276,9 +277,8 @@ __global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t
     nent += __shfl_xor_sync(0xffffffffu, nent, off);
   }
   if (lane == 0) {
-    const uint32_t off_ri = align16(16u + 4u * (nrows + 1u));
-    const uint32_t off_val = align16(off_ri + nent);
-    bsize[item] = VALUES ? align16(off_val + 4u * nent) : off_val;
+    const uint32_t off_ent = align16(16u + 4u * (nrows + 1u));
+    bsize[item] = align16(off_ent + (VALUES ? 8u : 1u) * nent);
   }
 }
 
@@ -322,10 +322,19 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
                             const double *__restrict__ len_perm,
                             const double *__restrict__ inv_total, float scale,
                             const unsigned long long *__restrict__ boff,
-                            uint8_t *__restrict__ blocks) {
+                            uint8_t *__restrict__ blocks, unsigned long long cap,
+                            unsigned long long *__restrict__ err) {
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (item >= (int64_t)n_tiles * n_win) return;
+  const int64_t n_items = (int64_t)n_tiles * n_win;
+  if (item >= n_items) return;
+  // the host sizes the buffer from an upper bound; should the blocks ever
+  // exceed it, nothing is written and the run reports the error
+  if (boff[n_items] > cap) {
+    if (item == 0 && lane == 0 && err)
+      atomicExch(err, (unsigned long long)(-UNIFRAC_E_BUFFER_TOO_SMALL));
+    return;
+  }
   const int64_t t = item / n_win;
   const int j = (int)(item % n_win);
   const int kb = p0 + kRareWin * j;
@@ -350,17 +359,16 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
     nrows += __shfl_xor_sync(0xffffffffu, nrows, off);
     nent += __shfl_xor_sync(0xffffffffu, nent, off);
   }
-  const uint32_t off_ri = align16(16u + 4u * (nrows + 1u));
-  const uint32_t off_val = align16(off_ri + nent);
+  const uint32_t off_ent = align16(16u + 4u * (nrows + 1u));
   uint32_t *hdr = reinterpret_cast<uint32_t *>(blk);
   uint32_t *rowstart = hdr + 4;
-  uint8_t *ri = blk + off_ri;
-  uint32_t *val = reinterpret_cast<uint32_t *>(blk + off_val);
+  uint8_t *ri = blk + off_ent;                                                // presence
+  unsigned long long *ent = reinterpret_cast<unsigned long long *>(blk + off_ent);  // weighted
   if (lane == 0) {
     hdr[0] = nrows;
     hdr[1] = nent;
-    hdr[2] = off_ri;
-    hdr[3] = off_val;
+    hdr[2] = off_ent;
+    hdr[3] = 0u;
     rowstart[nrows] = nent;
   }
   const uint32_t lt = (1u << lane) - 1u;
@@ -420,10 +428,12 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
 #pragma unroll
         for (int w = 0; w < 4; ++w)
           if (cc[w] != 0u) {
-            ri[base + pos[w]] = (uint8_t)(4 * lane + w);
             if constexpr (VALUES) {
               const float v = L * ((float)cc[w] * inv[w]);
-              val[base + pos[w]] = __float2uint_rn(v * scale);
+              ent[base + pos[w]] = ((unsigned long long)__float2uint_rn(v * scale) << 32) |
+                                   (unsigned long long)(4 * lane + w);
+            } else {
+              ri[base + pos[w]] = (uint8_t)(4 * lane + w);
             }
           }
       }
@@ -518,14 +528,15 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
     k_rare_fill<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                             ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm,
                                             ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale,
-                                            boff, blocks);
+                                            boff, blocks, ctx->blocks.bytes, ctx->d_counter + 1);
   } else {
     k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                               ctx->K_pad, bsize);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                              ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm, nullptr,
-                                             nullptr, 1.f, boff, blocks);
+                                             nullptr, 1.f, boff, blocks, ctx->blocks.bytes,
+                                             ctx->d_counter + 1);
   }
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();

@@ -342,15 +342,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
 // (kf_words + warp, + 32, ...) with no CTA-wide barrier in the loop.  For a
 // word, the rank of its first flagged row in the window's block is the
 // popcount of the block's earlier words; lane l takes the branch of bit l when
-// it is flagged in both tiles.  An incidence of at most kSmall pairs is walked
-// by its lane alone, reading the block (read-only global loads).  A larger one
-// is walked by the whole warp: one tile's rows (the "lane side") are held in
-// registers, lane (g, b) = (lane / nL, lane % nL) holding row b, and the other
-// tile's rows (staged by the warp in its shared scratch as packed (value, row)
-// entries) are swept a = g, g + G, ... with G = 32 / nL groups (rows beyond
-// 32 on the lane side in further passes), so each update is one broadcast
-// shared load, a min and one shared atomic.  The lane side is the tile whose
-// row count fills more lanes.
+// it is flagged in both tiles.  A weighted entry is one 8-byte (value, row)
+// word.  An incidence of at most kSmall pairs is walked by its lane alone,
+// reading the blocks (read-only loads through L1).  A larger one is walked by
+// the whole warp: one tile's rows (the "lane side") are held in registers,
+// lane (g, b) = (lane / nL, lane % nL) holding row b, and the other tile's
+// entries, copied by the warp into its own shared scratch, are swept
+// a = g, g + G, ... with G = 32 / nL groups (rows beyond 32 on the lane side
+// in further passes), so each update is one broadcast shared load, a min and
+// one shared atomic.  The lane side is the tile whose row count fills more
+// lanes.
 
 constexpr int kSpThreads = 1024;
 static_assert(kRareWin == kWinWords * WORD, "sparse blocks: one window is kWinWords bitmap words");
@@ -366,8 +367,8 @@ template <bool PRES>
 struct SparseCfg {
   using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
   static constexpr size_t kAccBytes = ((size_t)TILE * kAccLd * sizeof(Acc) + 15) / 16 * 16;
-  // one side of an incidence staged per warp: (value << 32 | row) u64 entries
-  // (weighted) or row bytes (unweighted), TILE at most
+  // the swept side of one incidence per warp: TILE entries of 8 (weighted) or
+  // 1 (unweighted) bytes
   static constexpr size_t kScratch = (size_t)TILE * (PRES ? 1 : 8);
   static constexpr size_t kSmem = kAccBytes + (size_t)kSpWarps * kScratch;
 };
@@ -377,6 +378,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     k_pairs_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
                    int32_t n_words, int32_t kf_words, int32_t k_words, int32_t n_win,
                    const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
+                   unsigned long long blocks_cap, int32_t n_tiles,
                    const uint32_t *__restrict__ qlen,
                    typename SparseCfg<PRES>::Acc *__restrict__ spart,
                    unsigned long long *__restrict__ n_updates) {
@@ -412,7 +414,10 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   const uint32_t *bI = bits + tI * n_words;
   const uint32_t *bJ = bits + tJ * n_words;
   const uint32_t below = (1u << lane) - 1u;
-  for (int w = kf_words + warp; w < k_words; w += kSpWarps) {
+  // blocks that did not fit their buffer were not written (the fill reported
+  // it): read none of them
+  const int w_end = boff[(int64_t)n_tiles * n_win] > blocks_cap ? kf_words : k_words;
+  for (int w = kf_words + warp; w < w_end; w += kSpWarps) {
     const uint32_t mI = __ldg(bI + w), mJ = __ldg(bJ + w);
     const uint32_t both = mI & mJ;
     if (both == 0u) continue;  // warp-uniform
@@ -436,9 +441,9 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     const uint4 hJ = __ldg(reinterpret_cast<const uint4 *>(blkJ));
     const uint32_t *rsI = reinterpret_cast<const uint32_t *>(blkI) + 4;
     const uint32_t *rsJ = reinterpret_cast<const uint32_t *>(blkJ) + 4;
-    const uint8_t *riI = blkI + hI.z, *riJ = blkJ + hJ.z;
-    const uint32_t *vI = reinterpret_cast<const uint32_t *>(blkI + hI.w);
-    const uint32_t *vJ = reinterpret_cast<const uint32_t *>(blkJ + hJ.w);
+    const uint8_t *riI = blkI + hI.z, *riJ = blkJ + hJ.z;  // presence entries
+    const unsigned long long *eI = reinterpret_cast<const unsigned long long *>(blkI + hI.z);
+    const unsigned long long *eJ = reinterpret_cast<const unsigned long long *>(blkJ + hJ.z);
 
     int nI = 0, nJ = 0;
     uint32_t sI = 0, sJ = 0;
@@ -460,15 +465,17 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     my_updates += (unsigned long long)total;
     if (total > 0 && total <= kSmall) {
       for (int a = 0; a < nI; ++a) {
-        const int ra = (int)__ldg(riI + sI + a) * kAccLd;
-        uint32_t va = 0u;
-        if constexpr (!PRES) va = __ldg(vI + sI + a);
-        for (int b = 0; b < nJ; ++b) {
-          Acc *dst = &sacc[ra + (int)__ldg(riJ + sJ + b)];
-          if constexpr (PRES) {
-            atomicAdd(dst, (unsigned long long)qk);
-          } else {
-            atomicAdd(dst, min(va, __ldg(vJ + sJ + b)));
+        if constexpr (PRES) {
+          const int ra = (int)__ldg(riI + sI + a) * kAccLd;
+          for (int b = 0; b < nJ; ++b)
+            atomicAdd(&sacc[ra + (int)__ldg(riJ + sJ + b)], (unsigned long long)qk);
+        } else {
+          const unsigned long long ea = __ldg(eI + sI + a);
+          const int ra = (int)(uint32_t)(ea & 0xffu) * kAccLd;
+          const uint32_t va = (uint32_t)(ea >> 32);
+          for (int b = 0; b < nJ; ++b) {
+            const unsigned long long eb = __ldg(eJ + sJ + b);
+            atomicAdd(&sacc[ra + (int)(uint32_t)(eb & 0xffu)], min(va, (uint32_t)(eb >> 32)));
           }
         }
       }
@@ -495,54 +502,48 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       if constexpr (PRES) bq = __shfl_sync(0xffffffffu, qk, src);
       const int nL = (int)(d & 0xffu), nT = (int)((d >> 8) & 0xffu);
       const bool laneJ = (d >> 16) != 0u;
-      const uint8_t *riL = laneJ ? riJ : riI, *riT = laneJ ? riI : riJ;
-      const uint32_t *vL = laneJ ? vJ : vI, *vT = laneJ ? vI : vJ;
       const int mL = laneJ ? 1 : kAccLd, mT = laneJ ? kAccLd : 1;  // accumulator strides
-      // stage the swept side: (value << 32 | row) or the row byte
-      for (int x = lane; x < nT; x += 32) {
-        if constexpr (PRES) {
-          rS[x] = __ldg(riT + bsT + x);
-        } else {
-          eS[x] = ((unsigned long long)__ldg(vT + bsT + x) << 32) | __ldg(riT + bsT + x);
-        }
+      // copy the swept side into the scratch
+      if constexpr (PRES) {
+        const uint8_t *rT = (laneJ ? riI : riJ) + bsT;
+        for (int x = lane; x < nT; x += 32) rS[x] = __ldg(rT + x);
+      } else {
+        const unsigned long long *qT = (laneJ ? eI : eJ) + bsT;
+        for (int x = lane; x < nT; x += 32) eS[x] = __ldg(qT + x);
       }
       __syncwarp();
+      int g, G, b;
       if (nL <= 32) {
         const uint32_t t0 = divtab[nL - 1][lane];
-        const int g = (int)(t0 >> 8), b = (int)(t0 & 0xffu), G = gtab[nL - 1];
-        if (g < G) {
-          const int base = (int)__ldg(riL + bsL + b) * mL;
-          uint32_t vb = 0u;
-          if constexpr (!PRES) vb = __ldg(vL + bsL + b);
-#pragma unroll 2
-          for (int a = g; a < nT; a += G) {
-            if constexpr (PRES) {
-              atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
-            } else {
-              const unsigned long long e = eS[a];
-              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT],
-                        min(vb, (uint32_t)(e >> 32)));
-            }
-          }
-        }
+        g = (int)(t0 >> 8);
+        b = (int)(t0 & 0xffu);
+        G = gtab[nL - 1];
       } else {
-        for (int b = lane; b < nL; b += 32) {
-          const int base = (int)__ldg(riL + bsL + b) * mL;
-          uint32_t vb = 0u;
-          if constexpr (!PRES) vb = __ldg(vL + bsL + b);
+        g = 0;
+        b = lane;
+        G = 1;
+      }
+      for (; b < nL; b += 32) {  // one pass when nL <= 32
+        if (g < G) {
+          if constexpr (PRES) {
+            const int base = (int)__ldg((laneJ ? riJ : riI) + bsL + b) * mL;
 #pragma unroll 2
-          for (int a = 0; a < nT; ++a) {
-            if constexpr (PRES) {
+            for (int a = g; a < nT; a += G)
               atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
-            } else {
+          } else {
+            const unsigned long long eb = __ldg((laneJ ? eJ : eI) + bsL + b);
+            const int base = (int)(uint32_t)(eb & 0xffu) * mL;
+            const uint32_t vb = (uint32_t)(eb >> 32);
+#pragma unroll 2
+            for (int a = g; a < nT; a += G) {
               const unsigned long long e = eS[a];
-              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT],
-                        min(vb, (uint32_t)(e >> 32)));
+              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT], min(vb, (uint32_t)(e >> 32)));
             }
           }
         }
+        if (nL <= 32) break;
       }
-      __syncwarp();  // scratch is rewritten by the next incidence
+      __syncwarp();  // the scratch is rewritten by the next incidence
     }
   }
   __syncthreads();
@@ -710,7 +711,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
       k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
           items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-          nullptr, spart,
+          ctx->blocks.bytes, ctx->n_tiles, nullptr, spart,
           ctx->d_counter + 4);
       ctx->stat_launches += 1;
     }
@@ -740,7 +741,7 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
   k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
       items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-      ctx->d_qperm, spart,
+      ctx->blocks.bytes, ctx->n_tiles, ctx->d_qperm, spart,
       ctx->d_counter + 4);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
