@@ -91,7 +91,7 @@ void free_ctx(unifrac_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->d_level_nodes, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
+  void *ptrs[] = {ctx->d_level_nodes, ctx->d_level_ptr, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
                   ctx->d_frow_ptr,    ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_col_ptr,     ctx->d_col_cnt,   ctx->d_col_depth, ctx->d_perm,
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
@@ -101,7 +101,7 @@ void free_ctx(unifrac_ctx *ctx) {
                          &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
                          &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->rc,
                          &ctx->bsize,   &ctx->boff,      &ctx->blocks, &ctx->spart,
-                         &ctx->rbits};
+                         &ctx->rbits,   &ctx->cpre};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &e : ctx->ev)
@@ -455,6 +455,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   ctx->sm_count = prop.multiProcessorCount;
   int rc;
   if ((rc = upload(ctx, &ctx->d_level_nodes, level_nodes))) return rc;
+  if ((rc = upload(ctx, &ctx->d_level_ptr, ctx->level_ptr))) return rc;
   if ((rc = upload(ctx, &ctx->d_child_ptr, child_ptr))) return rc;
   if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
   if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
@@ -645,6 +646,7 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       const uint64_t bound = nblk * 80 + 4 * rows + 8 * ents + 64;
       if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
       if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, ctx->cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
       if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
       if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
       if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 4)))
@@ -685,6 +687,7 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       if ((rc = grow(ctx, ctx->rbits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
       if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
       if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, ctx->cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
       if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
       if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
       if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 8))) return rc;
@@ -734,6 +737,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
       if ((rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words, P.n_win,
                                   static_cast<uint32_t *>(ctx->bsize.p),
                                   static_cast<unsigned long long *>(ctx->boff.p),
+                                  static_cast<uint2 *>(ctx->cpre.p),
                                   static_cast<uint8_t *>(ctx->blocks.p))))
         return rc;
     }
@@ -763,6 +767,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
       if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
                                   static_cast<uint32_t *>(ctx->bsize.p),
                                   static_cast<unsigned long long *>(ctx->boff.p),
+                                  static_cast<uint2 *>(ctx->cpre.p),
                                   static_cast<uint8_t *>(ctx->blocks.p))))
         return rc;
       spart = static_cast<unsigned long long *>(ctx->spart.p);

@@ -79,13 +79,56 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
   if (any) reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)t * TILE)[lane] = s;
 }
 
+// The upper levels hold few nodes each, too few to fill the GPU one launch per
+// level.  k_levels_tail walks levels [L0, L1) in one launch: CTA (t, q) owns
+// the 32 columns 128 t + 32 q .. +31, and each warp takes four nodes of a
+// level at a time (eight lanes x 16 bytes per node); __syncthreads separates
+// the levels, since a level reads only what earlier levels wrote for the same
+// columns.  Global memory is read with plain (coherent) loads.  A node's flag
+// is the same for the four quarters of its tile, so their stores agree.
+constexpr int kTailThreads = 1024;
+
+__global__ void __launch_bounds__(kTailThreads) k_levels_tail(
+    const int32_t *__restrict__ nodes, const int32_t *__restrict__ level_ptr, int32_t L0,
+    int32_t L1, const int32_t *__restrict__ child_ptr, const int32_t *__restrict__ child_idx,
+    uint32_t *cnt, uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+  const int t = blockIdx.x >> 2, q = blockIdx.x & 3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 3, l8 = lane & 7;
+  const int64_t col = (int64_t)t * TILE + q * 32 + l8 * 4;
+  for (int L = L0; L < L1; ++L) {
+    const int32_t lo = level_ptr[L], hi = level_ptr[L + 1];
+    for (int32_t i = lo + warp * 4 + g; i < hi; i += (kTailThreads / 32) * 4) {
+      const int32_t node = nodes[i];
+      uint4 s = make_uint4(0u, 0u, 0u, 0u);
+      bool any = false;
+      const int32_t c1 = child_ptr[node + 1];
+      for (int32_t c = child_ptr[node]; c < c1; ++c) {
+        const int32_t ch = child_idx[c];
+        if (flag[(int64_t)ch * n_tiles + t]) {
+          any = true;
+          const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
+          s.x += v.x;
+          s.y += v.y;
+          s.z += v.z;
+          s.w += v.w;
+        }
+      }
+      if (l8 == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
+      if (any) *reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + col) = s;
+    }
+    __syncthreads();
+  }
+}
+
 // Weighted packing of the positions [0, k_end) (all of them, or the frequently
 // present ones when the rest go to the sparse blocks).  Block (column tile t,
-// branch block kb) of 8 warps; warp w handles positions k = kb*KR + w, +8, ...;
-// lane l owns 4 columns.  Writes v[k][col] = len_k * cnt[perm[k]][col] / C_col
-// for the flagged (k, t) rows and the (t, k) bitmap words.  The mixed form
-// computes v in FP32 (<= 3 roundings); the FP64 form in FP64.  k_end is K or a
-// multiple of 32, so bitmap words never straddle it.
+// KR positions), warp w per bitmap word: lane l tests position 32 w + l and
+// the ballot is the (t, word) bitmap word; the flagged rows are then read four
+// at a time (16 bytes per lane) and written as
+// v[k][col] = len_k * cnt[perm[k]][col] / C_col.  The mixed form computes v in
+// FP32 (<= 3 roundings); the FP64 form in FP64.  k_end is K or a multiple of
+// 32, so bitmap words never straddle it.
 constexpr int KR = 256;
 
 template <typename T>
@@ -96,54 +139,63 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
     const double *__restrict__ inv_total, T *__restrict__ vals, int64_t ldv,
     uint32_t *__restrict__ bits, int32_t n_words) {
   const int t = blockIdx.x;
-  const int k0 = blockIdx.y * KR;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kw = blockIdx.y * KR + w * WORD;
+  if (kw >= k_end) return;  // warp-uniform
   const int64_t col = (int64_t)t * TILE + lane * 4;
-  const int k1 = min(k0 + KR, min(K, k_end));
-  if constexpr (sizeof(T) == 4) {
-    float inv[4];
+  const int k = kw + lane;
+  const int k1 = min(K, k_end);
+  const int32_t b = k < k1 ? perm[k] : 0;
+  const bool fl = k < k1 && flag[(int64_t)b * n_tiles + t];
+  const uint32_t word = __ballot_sync(0xffffffffu, fl);
+  if (lane == 0 && kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
+  T inv[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) inv[q] = (float)inv_total[col + q];
-    for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
-      const int32_t b = perm[k];
-      if (!flag[(int64_t)b * n_tiles + t]) continue;
-      const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
-      const float L = (float)len_perm[k];
-      float4 v;
-      v.x = L * ((float)c.x * inv[0]);
-      v.y = L * ((float)c.y * inv[1]);
-      v.z = L * ((float)c.z * inv[2]);
-      v.w = L * ((float)c.w * inv[3]);
-      *reinterpret_cast<float4 *>(vals + (int64_t)k * ldv + col) = v;
-    }
-  } else {
-    double inv[4];
+  for (int q = 0; q < 4; ++q) inv[q] = (T)inv_total[col + q];
+  uint32_t m = word;
+  while (m) {
+    constexpr int kU = 4;
+    int src[kU];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) inv[q] = inv_total[col + q];
-    for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
-      const int32_t b = perm[k];
-      if (!flag[(int64_t)b * n_tiles + t]) continue;
-      const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
-      const double L = len_perm[k];
-      double2 v0, v1;
-      v0.x = L * ((double)c.x * inv[0]);
-      v0.y = L * ((double)c.y * inv[1]);
-      v1.x = L * ((double)c.z * inv[2]);
-      v1.y = L * ((double)c.w * inv[3]);
-      double2 *dst = reinterpret_cast<double2 *>(vals + (int64_t)k * ldv + col);
-      dst[0] = v0;
-      dst[1] = v1;
+    for (int u = 0; u < kU; ++u) {
+      src[u] = -1;
+      if (m) {
+        src[u] = __ffs(m) - 1;
+        m &= m - 1;
+      }
     }
-  }
-  // bitmap words of this block: bit (k mod 32) of word k/32 = flag of branch k
-  if (threadIdx.x < KR / WORD) {
-    const int kw = k0 + threadIdx.x * WORD;
-    uint32_t word = 0;
-    for (int j = 0; j < WORD; ++j) {
-      const int k = kw + j;
-      if (k < K && flag[(int64_t)perm[k] * n_tiles + t]) word |= 1u << j;
+    uint4 c[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      c[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (src[u] >= 0) {
+        const int32_t bu = __shfl_sync(0xffffffffu, b, src[u]);
+        c[u] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)bu * ldc + col);
+      }
     }
-    if (kw < k_end && kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (src[u] < 0) break;
+      const int kk = kw + src[u];
+      const T L = (T)len_perm[kk];
+      if constexpr (sizeof(T) == 4) {
+        float4 v;
+        v.x = L * ((float)c[u].x * inv[0]);
+        v.y = L * ((float)c[u].y * inv[1]);
+        v.z = L * ((float)c[u].z * inv[2]);
+        v.w = L * ((float)c[u].w * inv[3]);
+        *reinterpret_cast<float4 *>(vals + (int64_t)kk * ldv + col) = v;
+      } else {
+        double2 v0, v1;
+        v0.x = L * ((double)c[u].x * inv[0]);
+        v0.y = L * ((double)c[u].y * inv[1]);
+        v1.x = L * ((double)c[u].z * inv[2]);
+        v1.y = L * ((double)c[u].w * inv[3]);
+        double2 *dst = reinterpret_cast<double2 *>(vals + (int64_t)kk * ldv + col);
+        dst[0] = v0;
+        dst[1] = v1;
+      }
+    }
   }
 }
 
@@ -250,12 +302,16 @@ __global__ void k_reduce_partials(int32_t n_cols, int32_t n_blocks,
 
 __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-// VALUES = false (presence blocks): no value section.
+// One warp per block: its size, and the rows / entries before each of its
+// kChunks chunks of 32 positions, cpre[item][c] = (rows, entries), with the
+// block's totals in cpre[item][kChunks].  VALUES: 8-byte entries, else 1 byte.
+constexpr int kChunks = kRareWin / 32;
+
 template <bool VALUES>
 __global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                              const uint32_t *__restrict__ bits, int32_t n_words,
                              const uint8_t *__restrict__ rc, int32_t k_pad,
-                             uint32_t *__restrict__ bsize) {
+                             uint32_t *__restrict__ bsize, uint2 *__restrict__ cpre) {
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (item >= (int64_t)n_tiles * n_win) return;
@@ -263,20 +319,19 @@ __global__ void k_rare_sizes(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t
   const int j = (int)(item % n_win);
   const int kb = p0 + kRareWin * j;
   uint32_t nrows = 0, nent = 0;
-  for (int q = lane; q < kRareWin; q += 32) {
-    const int k = kb + q;
-    if (k >= K) break;
-    if ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u) {
-      ++nrows;
-      nent += rc[t * k_pad + k];
-    }
-  }
+  for (int c = 0; c < kChunks; ++c) {
+    const int k = kb + 32 * c + lane;
+    const bool fl = k < K && ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u);
+    uint32_t e = fl ? rc[t * k_pad + k] : 0u;
+    const uint32_t r = __popc(__ballot_sync(0xffffffffu, fl));
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    nrows += __shfl_xor_sync(0xffffffffu, nrows, off);
-    nent += __shfl_xor_sync(0xffffffffu, nent, off);
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+    if (lane == 0) cpre[item * (kChunks + 1) + c] = make_uint2(nrows, nent);
+    nrows += r;
+    nent += e;
   }
   if (lane == 0) {
+    cpre[item * (kChunks + 1) + kChunks] = make_uint2(nrows, nent);
     const uint32_t off_ent = align16(16u + 4u * (nrows + 1u));
     bsize[item] = align16(off_ent + (VALUES ? 8u : 1u) * nent);
   }
@@ -308,11 +363,12 @@ __global__ void __launch_bounds__(1024) k_scan_sizes(int64_t n, const uint32_t *
   if (tid == 1023) boff[n] = part[1023];
 }
 
-// Fill one block per warp: rows in position order; each row's non-zero
-// columns are compacted with four ballots (column 4l + w of lane l), reading
-// the counts cnt[perm[k]][col].  VALUES: entries also carry round(v * scale)
-// with v = len_k * (cnt * (1 / C_col)) in FP32, the same roundings as the
-// dense packing; scale is a power of two.
+// Fill: one warp per chunk of 32 positions of a block, at the offsets
+// cpre gives; the chunk's flagged rows get their rowstart entries and their
+// non-zero columns, compacted with four ballots (column 4l + w of lane l),
+// reading the counts cnt[perm[k]][col].  VALUES: entries also carry
+// round(v * scale) with v = len_k * (cnt * (1 / C_col)) in FP32, the same
+// roundings as the dense packing; scale is a power of two.
 template <bool VALUES>
 __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                             const uint32_t *__restrict__ bits, int32_t n_words,
@@ -322,133 +378,116 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
                             const double *__restrict__ len_perm,
                             const double *__restrict__ inv_total, float scale,
                             const unsigned long long *__restrict__ boff,
-                            uint8_t *__restrict__ blocks, unsigned long long cap,
-                            unsigned long long *__restrict__ err) {
-  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                            const uint2 *__restrict__ cpre, uint8_t *__restrict__ blocks,
+                            unsigned long long cap, unsigned long long *__restrict__ err) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t n_items = (int64_t)n_tiles * n_win;
-  if (item >= n_items) return;
+  if (gw >= n_items * kChunks) return;
   // the host sizes the buffer from an upper bound; should the blocks ever
   // exceed it, nothing is written and the run reports the error
   if (boff[n_items] > cap) {
-    if (item == 0 && lane == 0 && err)
+    if (gw == 0 && lane == 0 && err)
       atomicExch(err, (unsigned long long)(-UNIFRAC_E_BUFFER_TOO_SMALL));
     return;
   }
+  const int64_t item = gw / kChunks;
+  const int ch = (int)(gw % kChunks);
   const int64_t t = item / n_win;
   const int j = (int)(item % n_win);
-  const int kb = p0 + kRareWin * j;
-  float inv[4] = {0.f, 0.f, 0.f, 0.f};
-  if constexpr (VALUES) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) inv[q] = (float)inv_total[t * TILE + 4 * lane + q];
-  }
+  const int kc = p0 + kRareWin * j + 32 * ch;  // first position of the chunk
+  const uint2 tot = cpre[item * (kChunks + 1) + kChunks];
+  const uint2 pre = cpre[item * (kChunks + 1) + ch];
+  const uint32_t nrows = tot.x, nent = tot.y;
   uint8_t *blk = blocks + boff[item];
-  // header: count again (same loop as the size kernel)
-  uint32_t nrows = 0, nent = 0;
-  for (int q = lane; q < kRareWin; q += 32) {
-    const int k = kb + q;
-    if (k >= K) break;
-    if ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u) {
-      ++nrows;
-      nent += rc[t * k_pad + k];
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    nrows += __shfl_xor_sync(0xffffffffu, nrows, off);
-    nent += __shfl_xor_sync(0xffffffffu, nent, off);
-  }
   const uint32_t off_ent = align16(16u + 4u * (nrows + 1u));
   uint32_t *hdr = reinterpret_cast<uint32_t *>(blk);
   uint32_t *rowstart = hdr + 4;
-  uint8_t *ri = blk + off_ent;                                                // presence
+  uint8_t *ri = blk + off_ent;                                                      // presence
   unsigned long long *ent = reinterpret_cast<unsigned long long *>(blk + off_ent);  // weighted
-  if (lane == 0) {
+  if (ch == 0 && lane == 0) {
     hdr[0] = nrows;
     hdr[1] = nent;
     hdr[2] = off_ent;
     hdr[3] = 0u;
     rowstart[nrows] = nent;
   }
+  const int k = kc + lane;
+  const bool fl = k < K && ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u);
+  const uint32_t fb = __ballot_sync(0xffffffffu, fl);
+  if (fb == 0u) return;
+  const uint32_t c = fl ? rc[t * k_pad + k] : 0u;
+  uint32_t incl = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t r0 = 0, e0 = 0;  // rows / entries before the current chunk
-  for (int s = 0; s < kRareWin / 32; ++s) {
-    const int k = kb + 32 * s + lane;
-    const bool fl = k < K && ((bits[t * n_words + (k >> 5)] >> (k & 31)) & 1u);
-    const uint32_t c = fl ? rc[t * k_pad + k] : 0u;
-    const uint32_t fb = __ballot_sync(0xffffffffu, fl);
-    uint32_t incl = c;
+  const uint32_t my_e = pre.y + incl - c;
+  if (fl) rowstart[pre.x + __popc(fb & lt)] = my_e;
+  float inv[4] = {0.f, 0.f, 0.f, 0.f};
+  if constexpr (VALUES) {
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += y;
+    for (int q = 0; q < 4; ++q) inv[q] = (float)inv_total[t * TILE + 4 * lane + q];
+  }
+  // entries of each flagged row of the chunk, 8 rows in flight at a time
+  uint32_t m = fb;
+  while (m) {
+    int src[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      src[g] = -1;
+      if (m) {
+        src[g] = __ffs(m) - 1;
+        m &= m - 1;
+      }
     }
-    const uint32_t my_e = e0 + incl - c;
-    if (fl) rowstart[r0 + __popc(fb & lt)] = my_e;
-    // entries of each flagged row of this chunk, 8 rows in flight at a time
-    uint32_t m = fb;
-    while (m) {
-      int src[8];
-      int nb = 0;
+    uint4 cv[8];
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        src[g] = -1;
-        if (m) {
-          src[g] = __ffs(m) - 1;
-          m &= m - 1;
-          ++nb;
-        }
-      }
-      uint4 c[8];
+    for (int g = 0; g < 8; ++g) {
+      cv[g] = make_uint4(0u, 0u, 0u, 0u);
+      if (src[g] >= 0)
+        cv[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[kc + src[g]] * ldc +
+                                                 t * TILE + 4 * lane);
+    }
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        c[g] = make_uint4(0u, 0u, 0u, 0u);
-        if (src[g] >= 0) {
-          const int64_t k = kb + 32 * s + src[g];
-          c[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[k] * ldc + t * TILE +
-                                                  4 * lane);
-        }
-      }
+    for (int g = 0; g < 8; ++g) {
+      if (src[g] < 0) break;
+      const uint32_t base = __shfl_sync(0xffffffffu, my_e, src[g]);
+      const uint32_t cc[4] = {cv[g].x, cv[g].y, cv[g].z, cv[g].w};
+      const uint32_t B0 = __ballot_sync(0xffffffffu, cc[0] != 0u);
+      const uint32_t B1 = __ballot_sync(0xffffffffu, cc[1] != 0u);
+      const uint32_t B2 = __ballot_sync(0xffffffffu, cc[2] != 0u);
+      const uint32_t B3 = __ballot_sync(0xffffffffu, cc[3] != 0u);
+      const uint32_t c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2);
+      const uint32_t pos[4] = {(uint32_t)__popc(B0 & lt), c0 + (uint32_t)__popc(B1 & lt),
+                               c0 + c1 + (uint32_t)__popc(B2 & lt),
+                               c0 + c1 + c2 + (uint32_t)__popc(B3 & lt)};
+      float L = 0.f;
+      if constexpr (VALUES) L = (float)len_perm[kc + src[g]];
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        if (src[g] < 0) break;
-        const uint32_t base = __shfl_sync(0xffffffffu, my_e, src[g]);
-        const uint32_t cc[4] = {c[g].x, c[g].y, c[g].z, c[g].w};
-        const uint32_t B0 = __ballot_sync(0xffffffffu, cc[0] != 0u);
-        const uint32_t B1 = __ballot_sync(0xffffffffu, cc[1] != 0u);
-        const uint32_t B2 = __ballot_sync(0xffffffffu, cc[2] != 0u);
-        const uint32_t B3 = __ballot_sync(0xffffffffu, cc[3] != 0u);
-        const uint32_t c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2);
-        const uint32_t pos[4] = {(uint32_t)__popc(B0 & lt), c0 + (uint32_t)__popc(B1 & lt),
-                                 c0 + c1 + (uint32_t)__popc(B2 & lt),
-                                 c0 + c1 + c2 + (uint32_t)__popc(B3 & lt)};
-        float L = 0.f;
-        if constexpr (VALUES) L = (float)len_perm[kb + 32 * s + src[g]];
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-          if (cc[w] != 0u) {
-            if constexpr (VALUES) {
-              const float v = L * ((float)cc[w] * inv[w]);
-              ent[base + pos[w]] = ((unsigned long long)__float2uint_rn(v * scale) << 32) |
-                                   (unsigned long long)(4 * lane + w);
-            } else {
-              ri[base + pos[w]] = (uint8_t)(4 * lane + w);
-            }
+      for (int w = 0; w < 4; ++w)
+        if (cc[w] != 0u) {
+          if constexpr (VALUES) {
+            const float v = L * ((float)cc[w] * inv[w]);
+            ent[base + pos[w]] = ((unsigned long long)__float2uint_rn(v * scale) << 32) |
+                                 (unsigned long long)(4 * lane + w);
+          } else {
+            ri[base + pos[w]] = (uint8_t)(4 * lane + w);
           }
-      }
-      (void)nb;
+        }
     }
-    r0 += __popc(fb);
-    e0 += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
 // Packing of the rarely present positions [p0, K) for the sparse kernels.
-// Block (column tile t, KR positions), warp per position: the row's count of
-// non-zero columns rc, the (t, position) bitmap words (p0 is a multiple of 32;
-// words below it belong to the dense packing) and, when aq is given,
-// aq[col] += q_k for every column where branch k is present.
+// Block (column tile t, KR positions), warp w per bitmap word: lane l tests
+// position 32 w + l, the ballot is the (t, word) bitmap word (p0 is a multiple
+// of 32; words below it belong to the dense packing); then the flagged
+// positions' rows are read four at a time (16 bytes per lane) for the row's
+// count of non-zero columns rc and, when aq is given, aq[col] += q_k for every
+// column where branch k is present.
 __global__ void __launch_bounds__(256) k_pack_rare(
     int32_t K, int32_t p0, const int32_t *__restrict__ perm, const uint32_t *__restrict__ qperm,
     const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
@@ -456,43 +495,60 @@ __global__ void __launch_bounds__(256) k_pack_rare(
     int32_t k_pad, unsigned long long *__restrict__ aq) {
   __shared__ unsigned long long red[kWarpsPerBlock][TILE];
   const int t = blockIdx.x;
-  const int k0 = p0 + blockIdx.y * KR;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kw = p0 + blockIdx.y * KR + w * WORD;  // first position of this warp's word
   const int64_t col = (int64_t)t * TILE + lane * 4;
-  const int k1 = min(k0 + KR, K);
+  const int k = kw + lane;
+  const int32_t b = k < K ? perm[k] : 0;
+  const bool fl = k < K && flag[(int64_t)b * n_tiles + t];
+  const uint32_t word = __ballot_sync(0xffffffffu, fl);
+  if (lane == 0 && kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
   unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
-  for (int k = k0 + w; k < k1; k += kWarpsPerBlock) {
-    const int32_t b = perm[k];
-    if (!flag[(int64_t)b * n_tiles + t]) continue;
-    const uint4 c = reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + col)[0];
-    const unsigned long long q = aq ? qperm[k] : 0ull;
-    acc[0] += c.x ? q : 0ull;
-    acc[1] += c.y ? q : 0ull;
-    acc[2] += c.z ? q : 0ull;
-    acc[3] += c.w ? q : 0ull;
-    const int nz = __popc(__ballot_sync(0xffffffffu, c.x != 0u)) +
-                   __popc(__ballot_sync(0xffffffffu, c.y != 0u)) +
-                   __popc(__ballot_sync(0xffffffffu, c.z != 0u)) +
-                   __popc(__ballot_sync(0xffffffffu, c.w != 0u));
-    if (lane == 0) rc[(int64_t)t * k_pad + k] = (uint8_t)nz;
+  uint32_t m = word;
+  while (m) {
+    constexpr int kU = 4;
+    int src[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      src[u] = -1;
+      if (m) {
+        src[u] = __ffs(m) - 1;
+        m &= m - 1;
+      }
+    }
+    uint4 c[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      c[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (src[u] >= 0) {
+        const int32_t bu = __shfl_sync(0xffffffffu, b, src[u]);
+        c[u] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)bu * ldc + col);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (src[u] < 0) break;
+      const int kk = kw + src[u];
+      const unsigned long long q = aq ? qperm[kk] : 0ull;
+      acc[0] += c[u].x ? q : 0ull;
+      acc[1] += c[u].y ? q : 0ull;
+      acc[2] += c[u].z ? q : 0ull;
+      acc[3] += c[u].w ? q : 0ull;
+      const int nz = __popc(__ballot_sync(0xffffffffu, c[u].x != 0u)) +
+                     __popc(__ballot_sync(0xffffffffu, c[u].y != 0u)) +
+                     __popc(__ballot_sync(0xffffffffu, c[u].z != 0u)) +
+                     __popc(__ballot_sync(0xffffffffu, c[u].w != 0u));
+      if (lane == 0) rc[(int64_t)t * k_pad + kk] = (uint8_t)nz;
+    }
   }
+  if (!aq) return;  // block-uniform
 #pragma unroll
   for (int q = 0; q < 4; ++q) red[w][lane * 4 + q] = acc[q];
   __syncthreads();
-  if (aq && threadIdx.x < TILE) {
+  if (threadIdx.x < TILE) {
     unsigned long long sum = 0;
     for (int ww = 0; ww < kWarpsPerBlock; ++ww) sum += red[ww][threadIdx.x];
     if (sum) atomicAdd(aq + (int64_t)t * TILE + threadIdx.x, sum);
-  }
-  // bitmap words of this block (k0 is a multiple of 32)
-  if (threadIdx.x < KR / WORD) {
-    const int kw = k0 + threadIdx.x * WORD;
-    uint32_t word = 0;
-    for (int j = 0; j < WORD; ++j) {
-      const int k = kw + j;
-      if (k < K && flag[(int64_t)perm[k] * n_tiles + t]) word |= 1u << j;
-    }
-    if (kw / WORD < n_words) bits[(int64_t)t * n_words + kw / WORD] = word;
   }
 }
 
@@ -514,29 +570,30 @@ int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_
 
 int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
                       const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint8_t *blocks) {
+                      unsigned long long *boff, uint2 *cpre, uint8_t *blocks) {
   cudaStream_t st = ctx->stream;
   const int64_t items = (int64_t)ctx->n_tiles * n_win;
   if (items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const int32_t p0 = kf_words * WORD;
   const unsigned grid = (unsigned)((items * 32 + 255) / 256);
+  const unsigned grid_fill = (unsigned)((items * kChunks * 32 + 255) / 256);
   if (values) {
     k_rare_sizes<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                             ctx->K_pad, bsize);
+                                             ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
-    k_rare_fill<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                            ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm,
-                                            ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale,
-                                            boff, blocks, ctx->blocks.bytes, ctx->d_counter + 1);
+    k_rare_fill<true><<<grid_fill, 256, 0, st>>>(
+        ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre, blocks,
+        ctx->blocks.bytes, ctx->d_counter + 1);
   } else {
     k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                              ctx->K_pad, bsize);
+                                              ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
-    k_rare_fill<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
-                                             ctx->K_pad, cnt, ctx->n_cols, ctx->d_perm, nullptr,
-                                             nullptr, 1.f, boff, blocks, ctx->blocks.bytes,
-                                             ctx->d_counter + 1);
+    k_rare_fill<false><<<grid_fill, 256, 0, st>>>(
+        ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks, ctx->blocks.bytes,
+        ctx->d_counter + 1);
   }
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();
@@ -558,7 +615,12 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
                                        ctx->n_tiles);
     ctx->stat_launches += 1;
   }
-  for (int L = 0; L < ctx->n_levels && ctx->n_tiles > 0; ++L) {
+  // one launch per level while the levels are large, then the rest in one
+  // launch (levels from the first with at most kTailNodes nodes)
+  constexpr int32_t kTailNodes = 1024;
+  int32_t L0 = 0;
+  while (L0 < ctx->n_levels && ctx->level_ptr[L0 + 1] - ctx->level_ptr[L0] > kTailNodes) ++L0;
+  for (int L = 0; L < L0 && ctx->n_tiles > 0; ++L) {
     const int32_t lo = ctx->level_ptr[L], hi = ctx->level_ptr[L + 1];
     const int64_t items = (int64_t)(hi - lo) * ctx->n_tiles;
     if (items == 0) continue;
@@ -566,6 +628,12 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
     k_level<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(
         ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, flag, ldc,
         ctx->n_tiles);
+    ctx->stat_launches += 1;
+  }
+  if (L0 < ctx->n_levels && ctx->n_tiles > 0) {
+    k_levels_tail<<<(unsigned)ctx->n_tiles * 4, kTailThreads, 0, st>>>(
+        ctx->d_level_nodes, ctx->d_level_ptr, L0, ctx->n_levels, ctx->d_child_ptr,
+        ctx->d_child_idx, cnt, flag, ldc, ctx->n_tiles);
     ctx->stat_launches += 1;
   }
   e = cudaGetLastError();

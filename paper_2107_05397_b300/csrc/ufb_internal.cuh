@@ -70,6 +70,7 @@ struct unifrac_ctx {
   int32_t n_levels = 0;               // levels above the tips (root excluded)
   std::vector<int32_t> level_ptr;     // [n_levels+1] into d_level_nodes
   int32_t *d_level_nodes = nullptr;   // internal non-root nodes grouped by level
+  int32_t *d_level_ptr = nullptr;     // device copy of level_ptr
   int32_t *d_child_ptr = nullptr;     // [n_nodes+1]
   int32_t *d_child_idx = nullptr;     // [n_nodes-1]
 
@@ -139,7 +140,7 @@ struct unifrac_ctx {
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
-      rc, bsize, boff, blocks, spart, rbits;
+      rc, bsize, boff, blocks, spart, rbits, cpre;
   size_t device_bytes = 0;
 };
 
@@ -169,9 +170,11 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
 // Values come from vals (weighted) or, when vals is null, presences from cnt.
 // values: weighted blocks (fixed-point values round(v * sp_scale)); else
 // presence blocks.  Both read the counts.
+// cpre: [n_tiles * n_win][kRareWin / 32 + 1] (rows, entries) before each
+// chunk of 32 positions of a block, totals last.
 int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
                       const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint8_t *blocks);
+                      unsigned long long *boff, uint2 *cpre, uint8_t *blocks);
 // Packing of positions >= 32 * kf_words for the sparse kernels: bitmap words,
 // row non-zero counts and, when aq is given, aq[col] += q_k.
 int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t kf_words,
