@@ -56,6 +56,9 @@ def parse():
                          "tensor core)")
     ap.add_argument("--no-per-study", action="store_true",
                     help="skip the one-launch-per-study comparison (several studies)")
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="write profiles/traffic.json from an ncu --csv capture of "
+                         "dram__bytes_read.sum / dram__bytes_write.sum and exit")
     ap.add_argument("--samples", type=int, default=None,
                     help="truncate the workload to this many samples (profiling runs)")
     return ap.parse_args()
@@ -73,25 +76,66 @@ def measured_peaks():
         return None
 
 
-def kernel_source_hash():
+# source files each pair kernel is built from (traffic records are void once
+# any of them changes)
+KERNEL_SOURCES = {
+    "k_pairs_tc": ("pairs_tc.cu", "epilogue.cuh", "ufb_internal.cuh"),
+    "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"),
+    "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh"),
+    "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh"),
+}
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_source_hash(kernel: str):
     h = hashlib.sha256()
-    for name in ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"):
+    for name in KERNEL_SOURCES.get(kernel, ("pairs_simt.cu", "pairs_tc.cu", "epilogue.cuh",
+                                            "ufb_internal.cuh")):
         with open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the
-    current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch from a committed ncu capture of the
+    bench workload, if the kernel's sources are unchanged since (else None)."""
     try:
-        rec = json.load(open(path)).get(kernel)
+        rec = json.load(open(TRAFFIC_PATH)).get(kernel)
     except Exception:
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec.get("bytes_per_launch")
+
+
+def record_traffic(csv_path: str, workload: str, capture: str):
+    """Writes profiles/traffic.json from an ncu --csv capture with the metrics
+    dram__bytes_read.sum and dram__bytes_write.sum: mean bytes per launch of
+    each pair kernel, with the hash of its current sources."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, ii, mi, vi = (h.index("Kernel Name"), h.index("ID"), h.index("Metric Name"),
+                      h.index("Metric Value"))
+    per = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        name = r[ki].split("(")[0].split("::")[-1].replace("<1>", "<true>").replace("<0>", "<false>")
+        if name not in KERNEL_SOURCES:
+            continue
+        per.setdefault(name, {}).setdefault(r[ii], 0.0)
+        per[name][r[ii]] += float(r[vi].replace(",", ""))
+    out = {"workload": workload, "capture": capture}
+    for name, launches in sorted(per.items()):
+        vals = list(launches.values())
+        out[name] = {"bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
+                     "source_hash": kernel_source_hash(name)}
+    with open(TRAFFIC_PATH, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
 
 
 class ClockSampler:
@@ -255,6 +299,11 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args.workload,
+                              "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+                              "--clock-control none -k regex:k_pairs on bench.py --workload "
+                              + args.workload)
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -470,20 +519,26 @@ def main():
                    pin(w.table.indptr), pin(w.table.indices), pin(w.table.counts)]
         h2d = int(sum(a.nbytes for a in host_in))
         res = torch.empty(2 * nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
-        e2e_t = []
+        e2e_t, parts = [], []
         for rep in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = ub.unifrac_create(*host_in, n_samples=N, stream=stream,
                                   study_offsets=w.table.study_offsets)
+            t1 = time.perf_counter()
             ub.unifrac_run(h, ub.BOTH, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res)
+            t2 = time.perf_counter()
             ub.unifrac_destroy(h)
             torch.cuda.synchronize()
-            e2e_t.append(time.perf_counter() - t0)
+            t3 = time.perf_counter()
+            e2e_t.append(t3 - t0)
+            parts.append((t1 - t0, t2 - t1, t3 - t2))
         t_e2e = float(np.median(e2e_t))
+        med = np.median(np.array(parts), axis=0)
         line["e2e"] = {"value": units_per_step / t_e2e, "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(2 * nb_cond),
                        "s_per_step": t_e2e,
+                       "s_create_run_destroy": [round(float(x), 5) for x in med],
                        "includes": "create (validation, host prep, upload) + one run of both "
                                    "variants + D2H of both condensed matrices + destroy"}
 

@@ -227,7 +227,13 @@ enum unifrac_stat {
   UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED = 15, /* device time of the sparse pair kernel of */
   UNIFRAC_STAT_SPARSE_MS_WEIGHTED = 16,   /*   the last run of each variant (ms)     */
   UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED = 17, /* pair updates it did (co-present      */
-  UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED = 18    /*   (pair, branch) of the sparse part) */
+  UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED = 18,   /*   (pair, branch) of the sparse part) */
+  UNIFRAC_STAT_CREATE_HOST_MS = 19,   /* unifrac_create: validation and host preparation (ms) */
+  UNIFRAC_STAT_CREATE_DEVICE_MS = 20, /* unifrac_create: device set-up and uploads (ms) */
+  UNIFRAC_STAT_MAX_REACH = 21         /* most non-root branches one sample reaches: exact
+                                         when the tree has >= 65,793 of them, else that
+                                         count (an upper bound; the tensor-core path
+                                         needs < 65,793) */
 };
 int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
 

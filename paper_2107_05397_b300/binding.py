@@ -52,6 +52,9 @@ STAT_SPARSE_MS_UNWEIGHTED = 15
 STAT_SPARSE_MS_WEIGHTED = 16
 STAT_SPARSE_UPDATES_UNWEIGHTED = 17
 STAT_SPARSE_UPDATES_WEIGHTED = 18
+STAT_CREATE_HOST_MS = 19
+STAT_CREATE_DEVICE_MS = 20
+STAT_MAX_REACH = 21
 
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",

@@ -5,9 +5,13 @@
 // that is sparse, a phylogenetic tree over its features, and the all-pairs
 // UniFrac distance matrix, computable in stripes that merge into the whole.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -87,13 +91,35 @@ int upload(unifrac_ctx *ctx, T **dst, const std::vector<T> &src) {
   return UNIFRAC_OK;
 }
 
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Host threads for the O(entries) preparation: one below ~64k entries, else
+// up to the hardware's count (at most 32).
+int host_threads(int64_t work) {
+  if (work < (1 << 16)) return 1;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(32u, hw ? hw : 1u));
+}
+
+// Runs fn(0) .. fn(T-1) on T threads (fn(0) on the calling thread).
+template <typename F>
+void run_threads(int T, F &&fn) {
+  std::vector<std::thread> th;
+  th.reserve(T > 1 ? T - 1 : 0);
+  for (int t = 1; t < T; ++t) th.emplace_back(fn, t);
+  fn(0);
+  for (auto &x : th) x.join();
+}
+
 void free_ctx(unifrac_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->d_level_nodes, ctx->d_level_ptr, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
                   ctx->d_frow_ptr,    ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
-                  ctx->d_col_ptr,     ctx->d_col_cnt,   ctx->d_col_depth, ctx->d_perm,
+                  ctx->d_S,           ctx->d_perm,
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -186,6 +212,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
                        const int64_t *indptr, const int32_t *indices, const int32_t *counts,
                        int32_t n_studies, const int32_t *study_offsets, void *cuda_stream,
                        unifrac_ctx *ctx) {
+  const auto t_create0 = std::chrono::steady_clock::now();
   // ---------------------------------------------------------------- arguments
   if (n_nodes < 1 || !parent || !length) return fail(ctx, UNIFRAC_E_INVALID_ARG, "tree arrays");
   if (n_features < 0 || n_samples < 0 || !indptr)
@@ -293,11 +320,100 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<int64_t> frow_ptr(1, 0);
   std::vector<int32_t> fent_col;
   std::vector<uint32_t> fent_cnt;
-  std::vector<int64_t> s_ptr(n_samples + 1, 0);  // per-sample entries (for marking)
   std::vector<std::pair<int32_t, int32_t>> row;  // (sample, count)
+  // Parallel pass for the usual table: every row's sample indices strictly
+  // increasing and in range, counts >= 0.  Threads check and count their
+  // rows, a prefix sum places them, threads fill them; per-thread sample
+  // totals are added in thread order (integers).  Any other table takes the
+  // sequential pass below, which reports what is wrong.
+  bool table_done = false;
+  {
+    const int T = host_threads(nnz);
+    std::vector<int64_t> nzr(n_features, 0);
+    std::vector<uint8_t> bad(T, 0);
+    run_threads(T, [&](int t) {
+      for (int32_t f = (int32_t)((int64_t)n_features * t / T);
+           f < (int32_t)((int64_t)n_features * (t + 1) / T); ++f) {
+        const int64_t lo = indptr[f], hi = indptr[f + 1];
+        if (hi < lo || lo < 0 || hi > nnz) {
+          bad[t] = 1;
+          return;
+        }
+        int64_t nz = 0;
+        for (int64_t e = lo; e < hi; ++e) {
+          if (indices[e] < 0 || indices[e] >= n_samples || counts[e] < 0 ||
+              (e > lo && indices[e] <= indices[e - 1])) {
+            bad[t] = 1;
+            return;
+          }
+          nz += counts[e] > 0;
+        }
+        nzr[f] = nz;
+      }
+    });
+    if (std::find(bad.begin(), bad.end(), 1) == bad.end()) {
+      std::vector<int64_t> at(n_features, -1);  // entry offset of each non-empty row
+      int64_t ne = 0;
+      for (int32_t f = 0; f < n_features; ++f)
+        if (nzr[f] > 0) {
+          at[f] = ne;
+          frow_tip.push_back(feature_node[f]);
+          ne += nzr[f];
+          frow_ptr.push_back(ne);
+        }
+      fent_col.resize(ne);
+      fent_cnt.resize(ne);
+      std::vector<std::vector<int64_t>> tot(T);
+      run_threads(T, [&](int t) {
+        std::vector<int64_t> &tt = tot[t];
+        tt.assign(n_samples, 0);
+        for (int32_t f = (int32_t)((int64_t)n_features * t / T);
+             f < (int32_t)((int64_t)n_features * (t + 1) / T); ++f) {
+          if (at[f] < 0) continue;
+          int64_t o = at[f];
+          for (int64_t e = indptr[f]; e < indptr[f + 1]; ++e) {
+            if (counts[e] == 0) continue;
+            const int32_t i = indices[e];
+            fent_col[o] = ctx->col_of_sample[i];
+            fent_cnt[o] = (uint32_t)counts[e];
+            tt[i] += counts[e];
+            ++o;
+          }
+        }
+      });
+      for (int t = 0; t < T; ++t)
+        for (int32_t i = 0; i < n_samples; ++i) total[i] += tot[t][i];
+      table_done = true;
+    }
+  }
+  if (!table_done) {
+  frow_tip.reserve(n_features);
+  frow_ptr.reserve((size_t)n_features + 1);
+  fent_col.reserve((size_t)nnz);
+  fent_cnt.reserve((size_t)nnz);
   for (int32_t f = 0; f < n_features; ++f) {
     const int64_t lo = indptr[f], hi = indptr[f + 1];
     if (hi < lo || hi > nnz) return fail(ctx, UNIFRAC_E_BAD_TABLE, "indptr not monotone");
+    // fast path: sample indices strictly increasing and in range (no sort,
+    // no duplicates possible)
+    bool ordered = true;
+    for (int64_t e = lo; e < hi && ordered; ++e)
+      ordered = indices[e] >= 0 && indices[e] < n_samples && counts[e] >= 0 &&
+                (e == lo || indices[e] > indices[e - 1]);
+    if (ordered) {
+      const size_t before = fent_col.size();
+      for (int64_t e = lo; e < hi; ++e) {
+        if (counts[e] == 0) continue;
+        const int32_t i = indices[e];
+        fent_col.push_back(ctx->col_of_sample[i]);
+        fent_cnt.push_back((uint32_t)counts[e]);
+        total[i] += counts[e];
+      }
+      if (fent_col.size() == before) continue;
+      frow_tip.push_back(feature_node[f]);
+      frow_ptr.push_back((int64_t)fent_col.size());
+      continue;
+    }
     row.clear();
     for (int64_t e = lo; e < hi; ++e) {
       const int32_t s = indices[e];
@@ -322,68 +438,124 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       fent_col.push_back(ctx->col_of_sample[pr.first]);
       fent_cnt.push_back((uint32_t)pr.second);
       total[pr.first] += pr.second;
-      s_ptr[pr.first + 1]++;
     }
     frow_ptr.push_back((int64_t)fent_col.size());
   }
+  }  // sequential pass
   for (int32_t i = 0; i < n_samples; ++i)
     if (total[i] > (int64_t)UINT32_MAX)
       return fail(ctx, UNIFRAC_E_BAD_TABLE,
                   "sample " + std::to_string(i) + " has a total count >= 2^32");
   ctx->n_frows = (int32_t)frow_tip.size();
-  for (int32_t i = 0; i < n_samples; ++i) s_ptr[i + 1] += s_ptr[i];
-  // per-sample tips (sample-major), built from the feature-major entries
-  std::vector<int32_t> s_tip(fent_col.size());
-  std::vector<uint32_t> s_cnt(fent_col.size());
-  {
-    std::vector<int64_t> fill(s_ptr.begin(), s_ptr.end() - 1);
-    std::vector<int32_t> sample_of_col(ctx->n_cols, -1);
-    for (int32_t i = 0; i < n_samples; ++i) sample_of_col[ctx->col_of_sample[i]] = i;
-    for (int32_t r = 0; r < ctx->n_frows; ++r)
-      for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e) {
-        const int32_t i = sample_of_col[fent_col[e]];
-        s_tip[fill[i]] = frow_tip[r];
-        s_cnt[fill[i]] = fent_cnt[e];
-        fill[i]++;
-      }
-  }
-
   // ------------------------------------------- presence counts and pruning
-  // A sample reaches every branch on the root paths of its tips.  Walking up
-  // from each tip and stopping at the first node already reached by the same
-  // sample visits each reached branch once per sample.
+  // n_b: the samples with a non-zero count below branch b.  Bitsets of those
+  // samples per node, one block of columns at a time (about 64 MiB of bitsets
+  // at most): a tip's bits come from its table row, an internal node's are the
+  // OR of its children's (every node ORed into its parent in postorder).  Studies start on 128-column boundaries, so a study's count at a
+  // node is a popcount over whole 64-bit words.  The most branches one sample
+  // reaches (the exactness bound of the tensor-core path) comes from
+  // bit-sliced column counters.
   ctx->nb.assign(n_nodes, 0);
-  std::vector<int32_t> mark(n_nodes, -1);
-  std::vector<int64_t> nb_study(n_nodes, 0);
-  std::vector<int32_t> touched;
   double pair_branch = 0.0, useful = 0.0;
-  for (int32_t s = 0; s < n_studies; ++s) {
-    touched.clear();
-    for (int32_t i = soff[s]; i < soff[s + 1]; ++i) {
-      int64_t reach = 0;
-      for (int64_t e = s_ptr[i]; e < s_ptr[i + 1]; ++e) {
-        int32_t v = s_tip[e];
-        while (v != root && mark[v] != i) {
-          mark[v] = i;
-          if (nb_study[v] == 0) touched.push_back(v);
-          nb_study[v]++;
-          reach++;
-          v = parent[v];
+  {
+    const int32_t W = ctx->n_cols / 64;
+    int32_t WB = (int32_t)std::min<int64_t>(
+        W, std::max<int64_t>(2, ((int64_t)8 << 20) / (8 * (int64_t)n_nodes)));
+    WB -= WB & 1;  // whole 128-column tiles (W is even)
+    const int T = host_threads((int64_t)n_nodes * std::max(W, 1));
+    constexpr int kPlanes = 32;
+    // a sample reaches at most root branches: count exactly only when that
+    // bound does not already settle the tensor-core exactness test
+    const bool count_reach = (int64_t)root >= 65793;
+    if (!count_reach) ctx->max_reach = root;
+    std::unique_ptr<uint64_t[]> bits(new uint64_t[(size_t)n_nodes * std::max(WB, 2)]);
+    std::vector<std::vector<uint64_t>> planes(T);
+    std::vector<int32_t> sw0(n_studies), sw1(n_studies);
+    for (int32_t st = 0; st < n_studies; ++st) {
+      sw0[st] = ctx->study_col0[st] / 64;
+      sw1[st] = sw0[st] + (int32_t)(((int64_t)(soff[st + 1] - soff[st]) + TILE - 1) / TILE * 2);
+    }
+    std::vector<std::vector<int32_t>> acc(n_studies);
+    std::vector<int64_t> cur(frow_ptr.begin(), frow_ptr.end() - 1);  // next entry of each row
+    int32_t s_open = 0;
+    for (int32_t b0 = 0; b0 < W; b0 += WB) {
+      const int32_t b1 = std::min(W, b0 + WB), wb = b1 - b0;
+      std::memset(bits.get(), 0, sizeof(uint64_t) * (size_t)n_nodes * std::max(WB, 2));
+      // tips: the row's entries in this block (rows are column-sorted)
+      const int32_t R = ctx->n_frows;
+      run_threads(T, [&](int t) {
+        for (int32_t r = (int32_t)((int64_t)R * t / T); r < (int32_t)((int64_t)R * (t + 1) / T); ++r) {
+          uint64_t *d = &bits[(size_t)frow_tip[r] * WB];
+          int64_t e = cur[r];
+          for (; e < frow_ptr[r + 1] && fent_col[e] < 64 * b1; ++e)
+            d[fent_col[e] / 64 - b0] |= 1ull << (fent_col[e] & 63);
+          cur[r] = e;
         }
+      });
+      // internal nodes: each ORed into its parent in postorder (children first)
+      for (int32_t v = 0; v < root; ++v) {
+        const uint64_t *src = &bits[(size_t)v * WB];
+        uint64_t *d = &bits[(size_t)parent[v] * WB];
+        for (int32_t j = 0; j < wb; ++j) d[j] |= src[j];
       }
-      ctx->max_reach = std::max(ctx->max_reach, reach);
-    }
-    int64_t B_s = 0;
-    for (int32_t v : touched) {
-      if (length[v] > 0.0) {
-        B_s++;
-        useful += 0.5 * (double)nb_study[v] * (double)(nb_study[v] - 1);
+      // counts per node (all, and per study open in this block) and the
+      // column counters
+      int32_t s_end = s_open;
+      while (s_end < n_studies && sw0[s_end] < b1) ++s_end;
+      for (int32_t st = s_open; st < s_end; ++st)
+        if (acc[st].empty()) acc[st].assign(n_nodes, 0);
+      run_threads(T, [&](int t) {
+        std::vector<uint64_t> &pl = planes[t];
+        if (count_reach) pl.assign((size_t)kPlanes * wb, 0ull);
+        for (int32_t v = (int32_t)((int64_t)root * t / T); v < (int32_t)((int64_t)root * (t + 1) / T);
+             ++v) {
+          const uint64_t *d = &bits[(size_t)v * WB];
+          int64_t all = 0;
+          for (int32_t j = 0; j < wb; ++j) {
+            uint64_t x = d[j];
+            all += __builtin_popcountll(x);
+            if (!count_reach) continue;
+            for (int p = 0; x && p < kPlanes; ++p) {  // carry-save add into the planes
+              const uint64_t c = pl[(size_t)p * wb + j] & x;
+              pl[(size_t)p * wb + j] ^= x;
+              x = c;
+            }
+          }
+          if (!all) continue;
+          ctx->nb[v] += all;
+          for (int32_t st = s_open; st < s_end; ++st) {
+            const int32_t j0 = std::max(sw0[st], b0) - b0, j1 = std::min(sw1[st], b1) - b0;
+            int32_t c = 0;
+            for (int32_t j = j0; j < j1; ++j) c += __builtin_popcountll(d[j]);
+            acc[st][v] += c;
+          }
+        }
+      });
+      for (int32_t j = 0; j < (count_reach ? wb : 0); ++j)
+        for (int q = 0; q < 64; ++q) {
+          int64_t r = 0;
+          for (int t = 0; t < T; ++t) {
+            if (planes[t].empty()) continue;
+            for (int p = 0; p < kPlanes; ++p)
+              r += (int64_t)((planes[t][(size_t)p * wb + j] >> q) & 1ull) << p;
+          }
+          ctx->max_reach = std::max(ctx->max_reach, r);
+        }
+      // studies that end in this block
+      while (s_open < s_end && sw1[s_open] <= b1) {
+        const std::vector<int32_t> &a = acc[s_open];
+        int64_t B_s = 0;
+        for (int32_t v = 0; v < root; ++v)
+          if (a[v] > 0 && length[v] > 0.0) {
+            B_s++;
+            useful += 0.5 * (double)a[v] * (double)(a[v] - 1);
+          }
+        const double n_s = (double)(soff[s_open + 1] - soff[s_open]);
+        pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
+        std::vector<int32_t>().swap(acc[s_open]);
+        ++s_open;
       }
-      ctx->nb[v] += nb_study[v];
-      nb_study[v] = 0;
     }
-    const double n_s = (double)(soff[s + 1] - soff[s]);
-    pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
   }
   ctx->stat_pair_branch = pair_branch;
   ctx->stat_useful = useful;
@@ -432,27 +604,25 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<double> inv_total(ctx->n_cols, 0.0);
   for (int32_t i = 0; i < n_samples; ++i)
     if (total[i] > 0) inv_total[ctx->col_of_sample[i]] = 1.0 / (double)total[i];
-  std::vector<int64_t> col_ptr(ctx->n_cols + 1, 0);
-  for (int32_t i = 0; i < n_samples; ++i)
-    col_ptr[ctx->col_of_sample[i] + 1] = s_ptr[i + 1] - s_ptr[i];
-  for (int32_t c = 0; c < ctx->n_cols; ++c) col_ptr[c + 1] += col_ptr[c];
-  std::vector<uint32_t> col_cnt(s_cnt.size());
-  std::vector<double> col_depth(s_cnt.size());
-  for (int32_t i = 0; i < n_samples; ++i) {
-    int64_t at = col_ptr[ctx->col_of_sample[i]];
-    for (int64_t e = s_ptr[i]; e < s_ptr[i + 1]; ++e, ++at) {
-      col_cnt[at] = s_cnt[e];
-      col_depth[at] = depth[s_tip[e]];
-    }
+  // Per-column weighted sums S_col = sum_b v[b][col] through the tip-depth
+  // identity (every count below a branch is a tip count, and a tip's count
+  // appears once for every branch on its root path):
+  // S_i = (1 / C_i) * sum_f c_fi * depth(tip_f), FP64, entries in row order;
+  // fixed for the context, so computed once here.
+  std::vector<double> S(ctx->n_cols, 0.0);
+  for (int32_t r = 0; r < ctx->n_frows; ++r) {
+    const double dep = depth[frow_tip[r]];
+    for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e) S[fent_col[e]] += (double)fent_cnt[e] * dep;
   }
+  for (int32_t c = 0; c < ctx->n_cols; ++c) S[c] *= inv_total[c];
+  ctx->create_host_ms = ms_since(t_create0);
 
   // ---------------------------------------------------------------- device
   if (cudaGetDevice(&ctx->device) != cudaSuccess)
     return fail(ctx, UNIFRAC_E_CUDA, "no CUDA device");
-  cudaDeviceProp prop;
-  cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "device properties");
-  ctx->sm_count = prop.multiProcessorCount;
+  cudaError_t e =
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device attribute");
   int rc;
   if ((rc = upload(ctx, &ctx->d_level_nodes, level_nodes))) return rc;
   if ((rc = upload(ctx, &ctx->d_level_ptr, ctx->level_ptr))) return rc;
@@ -463,9 +633,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
   if ((rc = upload(ctx, &ctx->d_fent_cnt, fent_cnt))) return rc;
   if ((rc = upload(ctx, &ctx->d_inv_total, inv_total))) return rc;
-  if ((rc = upload(ctx, &ctx->d_col_ptr, col_ptr))) return rc;
-  if ((rc = upload(ctx, &ctx->d_col_cnt, col_cnt))) return rc;
-  if ((rc = upload(ctx, &ctx->d_col_depth, col_depth))) return rc;
+  if ((rc = upload(ctx, &ctx->d_S, S))) return rc;
   if ((rc = upload(ctx, &ctx->d_perm, perm))) return rc;
   if ((rc = upload(ctx, &ctx->d_len_perm, len_perm))) return rc;
   if ((rc = upload(ctx, &ctx->d_digits, digits))) return rc;
@@ -492,6 +660,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       e = cudaEventCreate(&ev);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
     }
+  ctx->create_device_ms = ms_since(t_create0) - ctx->create_host_ms;
   return UNIFRAC_OK;
 }
 
@@ -725,12 +894,12 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   const int32_t n_items = P.n_items;
   const int variant = P.variant;
   if (P.kind == RunPlan::WEIGHTED) {
-    double *S = static_cast<double *>(ctx->persample.p);
+    const double *S = ctx->d_S;
     uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
     // dense values for the frequently present positions, sparse blocks built
     // from the counts for the rest
     const int32_t k_end = P.n_win > 0 ? P.kf_words * WORD : ctx->K;
-    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, k_end, S))) return rc;
+    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, k_end))) return rc;
     if (P.n_win > 0) {
       uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
       if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, bits, rcb, nullptr))) return rc;
@@ -1174,6 +1343,9 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
     }
     case UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED:
     case UNIFRAC_STAT_SPARSE_MS_WEIGHTED:
+    case UNIFRAC_STAT_CREATE_HOST_MS: *value = ctx->create_host_ms; return UNIFRAC_OK;
+    case UNIFRAC_STAT_CREATE_DEVICE_MS: *value = ctx->create_device_ms; return UNIFRAC_OK;
+    case UNIFRAC_STAT_MAX_REACH: *value = (double)ctx->max_reach; return UNIFRAC_OK;
     case UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED:
     case UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED: {
       const int v = (stat == UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED ||

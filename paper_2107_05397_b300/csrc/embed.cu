@@ -199,24 +199,6 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
   }
 }
 
-// Per-column sums S_col = sum_k v[k][col] through the tip-depth identity
-// S_i = (1 / C_i) * sum_f c_fi * depth(tip_f): one warp per column over that
-// column's table entries (column-sorted copy of the table), FP64, fixed order.
-__global__ void k_weighted_sums(int32_t n_cols, const int64_t *__restrict__ col_ptr,
-                                const uint32_t *__restrict__ col_cnt,
-                                const double *__restrict__ col_depth,
-                                const double *__restrict__ inv_total, double *__restrict__ S) {
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_cols) return;
-  double acc = 0.0;
-  for (int64_t e = col_ptr[warp] + lane; e < col_ptr[warp + 1]; e += 32)
-    acc += (double)col_cnt[e] * col_depth[e];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) S[warp] = acc * inv_total[warp];
-}
-
 // Lookup packing.  Block (column tile t, group block gb) of 128 threads, one
 // column each.  Group g holds positions 8g..8g+7; the byte of (g, col) has bit
 // j set when branch 8g+j is present in col.  Also the (t, g) group bitmap and
@@ -642,7 +624,7 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
 }
 
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bool f64,
-                  void *vals, uint32_t *bits, int32_t k_end, double *S) {
+                  void *vals, uint32_t *bits, int32_t k_end) {
   cudaStream_t st = ctx->stream;
   const int32_t n_words = ctx->K_pad / WORD;
   k_end = min(k_end, ctx->K);
@@ -656,12 +638,6 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bo
       k_pack_weighted<float><<<grid, 256, 0, st>>>(
           ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
           ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words);
-    ctx->stat_launches += 1;
-  }
-  if (ctx->n_cols > 0) {
-    const int64_t threads = (int64_t)ctx->n_cols * 32;
-    k_weighted_sums<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        ctx->n_cols, ctx->d_col_ptr, ctx->d_col_cnt, ctx->d_col_depth, ctx->d_inv_total, S);
     ctx->stat_launches += 1;
   }
   cudaError_t e = cudaGetLastError();

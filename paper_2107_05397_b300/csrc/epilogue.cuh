@@ -6,9 +6,12 @@
 
 namespace ufb {
 
-__device__ __forceinline__ void put_value(const OutSpec &o, int64_t idx, double d) {
+// V = float (mixed-precision kernels, FP32 outputs) or double (FP64 kernels);
+// a value is converted only when its type differs from the output's.
+template <typename V>
+__device__ __forceinline__ void put_value(const OutSpec &o, int64_t idx, V d) {
   if (o.is_f64)
-    static_cast<double *>(o.out)[idx] = d;
+    static_cast<double *>(o.out)[idx] = static_cast<double>(d);
   else
     static_cast<float *>(o.out)[idx] = static_cast<float>(d);
 }
@@ -37,8 +40,9 @@ __device__ __forceinline__ float ratio01_f32(float num, float den) {
 //   when that stripe exists (s < ceil((n-1)/2)) and lies in [s0, s1).
 //   condensed / full: written when its stripe min(lj-li-1, n-(lj-li)-1) is in
 //   [s0, s1).
+template <typename V>
 __device__ __forceinline__ void put_pair(const OutSpec &o, const StudyDev &st, int li,
-                                         int lj, double d) {
+                                         int lj, V d) {
   const int n = st.n;
   const int delta = lj - li;
   const int sa = delta - 1;
@@ -64,7 +68,7 @@ __device__ __forceinline__ void put_pair(const OutSpec &o, const StudyDev &st, i
 
 // Full layout only: the zero diagonal, written by the diagonal tiles.
 __device__ __forceinline__ void put_diag(const OutSpec &o, const StudyDev &st, int li) {
-  if (o.layout == UNIFRAC_OUT_FULL) put_value(o, st.out_off + (int64_t)li * st.n + li, 0.0);
+  if (o.layout == UNIFRAC_OUT_FULL) put_value(o, st.out_off + (int64_t)li * st.n + li, 0.f);
 }
 
 }  // namespace ufb

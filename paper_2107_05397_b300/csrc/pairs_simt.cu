@@ -294,6 +294,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
   // difference is taken once, so the error stays a few units of 2^-24 of
   // S_i + S_j), FP64 in the FP64 form
   const float sp_inv_f = (float)sp_inv;
+  float Sj_f[8];  // this thread's column sums, converted once
+#pragma unroll
+  for (int qj = 0; qj < 8; ++qj) Sj_f[qj] = (sizeof(T) == 4) ? (float)S[colJ + own_row(tx, qj)] : 0.f;
 #pragma unroll
   for (int qi = 0; qi < 8; ++qi) {
     const int i = own_row(ty, qi);
@@ -307,11 +310,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
       if (lj >= sd.n) continue;
       if (li < lj) {
         if constexpr (sizeof(T) == 4) {
-          const float den = (float)Si + (float)S[colJ + j];
+          const float den = (float)Si + Sj_f[qj];
           float M = tot[i * TILE + j];
           if (sparse)
             M = __fmaf_rn((float)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j], sp_inv_f, M);
-          put_pair(o, sd, li, lj, (double)ratio01_f32(__fmaf_rn(-2.f, M, den), den));
+          put_pair(o, sd, li, lj, ratio01_f32(__fmaf_rn(-2.f, M, den), den));
         } else {
           const double den = Si + S[colJ + j];
           put_pair(o, sd, li, lj, ratio01(den - 2.0 * part.get(qi, qj), den));

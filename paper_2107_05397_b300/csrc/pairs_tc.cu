@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (spart) g += spart[(int64_t)blockIdx.x * TC_BM * TC_BN + row * TC_BN + col];
           const unsigned long long A = ai + aq[colJ + col];
           const float d = ratio01_f32((float)(A - 2 * g), (float)(A - g));
-          put_pair(o, sd, li, lj, (double)d);
+          put_pair(o, sd, li, lj, d);
         } else if (li == lj) {
           put_diag(o, sd, li);
         }

@@ -81,10 +81,7 @@ struct unifrac_ctx {
   int32_t *d_fent_col = nullptr;      // [nnz'] embedding column (sorted per row)
   uint32_t *d_fent_cnt = nullptr;     // [nnz'] count (> 0)
   double *d_inv_total = nullptr;      // [n_cols] 1 / C_i (0 for empty or padding)
-  // column-sorted copy of the table for the per-sample weighted denominators
-  int64_t *d_col_ptr = nullptr;       // [n_cols+1]
-  uint32_t *d_col_cnt = nullptr;      // [nnz'] count
-  double *d_col_depth = nullptr;      // [nnz'] root-to-tip length of the entry's tip
+  double *d_S = nullptr;              // [n_cols] weighted sums S_col (FP64), set at create
 
   // ---- kept branches (postorder ids), ordered by presence count descending
   int32_t K = 0;                      // kept branches
@@ -115,6 +112,8 @@ struct unifrac_ctx {
   // ---- options
   int opt_uw_kernel = 0;
   int opt_flush = 256;
+  double create_host_ms = 0.0;        // unifrac_create: validation and host preparation
+  double create_device_ms = 0.0;      // unifrac_create: device set-up and uploads
   int opt_persistent = -1;  // -1 auto
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
@@ -162,9 +161,9 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 // packing ---------------------------------------------------------------------
 // Branch-major values v[k][col] = len_k * cnt / C_col (float or double) and the
 // (tile, k) nonzero bitmap words of the positions k < k_end (k_end: K, or a
-// multiple of 32), and per-column sums S_col = sum_k v[k][col] (FP64).
+// multiple of 32).
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
-                  bool f64, void *vals, uint32_t *bits, int32_t k_end, double *S);
+                  bool f64, void *vals, uint32_t *bits, int32_t k_end);
 // Sparse blocks of positions >= 32 * kf_words, one per (tile, window of
 // kRareWin positions): sizes, byte offsets boff[n_tiles * n_win + 1] and fill.
 // Values come from vals (weighted) or, when vals is null, presences from cnt.

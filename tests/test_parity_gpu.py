@@ -434,3 +434,68 @@ def _paper_scale():
     if not _PAPER_SCALE:
         _PAPER_SCALE.append(synth.make_workload("tips200000_samples25000"))
     return _PAPER_SCALE[0]
+
+
+# ------------------------------------------------------------------ create statistics
+
+def _presence(tree, table):
+    """[n_nodes, N] presence of every node in every sample, from the oracle."""
+    return np.stack([oracle.embedding(tree, table, i)[1] for i in range(table.n_samples)],
+                    axis=1).astype(bool)
+
+
+def _expected_stats(tree, table, offs):
+    P = _presence(tree, table)
+    n = tree.parent.shape[0]
+    root = n - 1
+    eligible = (np.arange(n) < root) & (tree.length > 0)
+    pair_branch = useful = 0.0
+    for s in range(len(offs) - 1):
+        sub = P[:, offs[s]:offs[s + 1]]
+        ns = sub.shape[1]
+        nb = sub.sum(axis=1)
+        pair_branch += ns * (ns - 1) / 2 * int(np.count_nonzero(eligible & (nb > 0)))
+        useful += float(np.sum(nb[eligible] * (nb[eligible] - 1) / 2))
+    kept = int(np.count_nonzero(eligible & P.any(axis=1)))
+    reach = int(P[:root].sum(axis=0).max()) if P.shape[1] else 0
+    return pair_branch, useful, kept, reach
+
+
+def test_create_statistics_several_studies():
+    # pair x branch, co-present pairs and kept branches, per study, from the
+    # oracle's presence embedding; zero-length branches and empty studies
+    rng = np.random.default_rng(91)
+    tree = synth.yule_tree(400, rng, 0.1)
+    tree.length[rng.choice(tree.parent.shape[0] - 1, 40, replace=False)] = 0.0
+    sizes = [130, 0, 1, 2, 200, 40]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], int(offs[-1]))) < 0.04) * \
+        rng.integers(1, 30, (tips.shape[0], int(offs[-1])))
+    table = synth.dense_to_table(dense, tips)
+    table.study_offsets = offs
+    pb, us, kept, reach = _expected_stats(tree, table, offs)
+    with ub.Context(tree, table) as ctx:
+        assert ctx.stat(ub.STAT_PAIR_BRANCH) == pb
+        assert ctx.stat(ub.STAT_USEFUL) == us
+        assert ctx.stat(ub.STAT_BRANCHES_KEPT) == kept
+        assert ctx.stat(ub.STAT_MAX_REACH) >= reach  # small tree: the bound
+        assert ctx.stat(ub.STAT_CREATE_HOST_MS) >= 0.0
+
+
+def test_create_statistics_large_tree_exact_reach():
+    # a tree with more than 65,793 branches: the reach is counted exactly
+    # (bit-sliced column counters over several column blocks)
+    rng = np.random.default_rng(92)
+    tree = synth.yule_tree(34000, rng, 0.1)
+    N = 1100  # 18 words of columns: more than one 8 MiB block of bitsets
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], N)) < 0.01) * rng.integers(1, 9, (tips.shape[0], N))
+    dense[:, 5] = 0  # an empty sample
+    table = synth.dense_to_table(dense, tips)
+    pb, us, kept, reach = _expected_stats(tree, table, [0, N])
+    with ub.Context(tree, table) as ctx:
+        assert ctx.stat(ub.STAT_PAIR_BRANCH) == pb
+        assert ctx.stat(ub.STAT_USEFUL) == us
+        assert ctx.stat(ub.STAT_BRANCHES_KEPT) == kept
+        assert ctx.stat(ub.STAT_MAX_REACH) == reach
