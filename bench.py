@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="run the two variants one after the other in the headline loop")
     ap.add_argument("--sparse-fraction", type=float, default=None,
                     help="weighted dense/sparse split as a fraction of the largest study "
                          "(instead of the autotuner)")
@@ -367,22 +369,42 @@ def main():
         step()
     barrier()
 
+    ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0 if args.no_overlap else 1)
+    for _ in range(args.warmup):  # (re-)capture with the headline setting
+        step()
     step_ms, pair_wn_ms, pair_uw_ms, sel_wn, sel_uw = [], [], [], [], []
-    sp_uw_ms, sp_wn_ms, sp_uw_n, sp_wn_n = [], [], [], []
+    sp_uw_ms, sp_wn_ms, sp_uw_n, sp_wn_n, serial_ms = [], [], [], [], []
     launches = 0
     peaks = measured_peaks()
+
+    def timed_step():
+        flush.zero_()  # L2 flush, outside the event pair
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = step()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), n
+
     with ClockSampler(torch.cuda.current_device()) as clocks:
+        # headline: the whole step as a user runs it (variants overlapped on two
+        # streams unless --no-overlap)
         barrier()
         t_wall0 = time.perf_counter()
         for _ in range(args.steps):
-            flush.zero_()  # L2 flush, outside the event pair
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            launches += step()
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
+            ms, n = timed_step()
+            step_ms.append(ms)
+            launches += n
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+        # per-kernel times for the rooflines: the same steps with the variants
+        # one after the other, so that no kernel shares the GPU with another
+        ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0)
+        step()
+        for _ in range(args.steps):
+            ms, _n = timed_step()
+            serial_ms.append(ms)
             pair_uw_ms.append(ctx.stat(ub.STAT_PAIR_MS_UNWEIGHTED))
             pair_wn_ms.append(ctx.stat(ub.STAT_PAIR_MS_WEIGHTED))
             sel_wn.append(ctx.stat(ub.STAT_SELECTED_WEIGHTED))
@@ -391,8 +413,7 @@ def main():
             sp_wn_ms.append(ctx.stat(ub.STAT_SPARSE_MS_WEIGHTED))
             sp_uw_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_UNWEIGHTED))
             sp_wn_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_WEIGHTED))
-        barrier()
-        t_wall = time.perf_counter() - t_wall0
+        ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0 if args.no_overlap else 1)
     clk = clocks.summary()
     dev_err = ctx.stat(ub.STAT_DEVICE_ERROR)
     from paper_2107_05397_b300 import replicas
@@ -451,8 +472,14 @@ def main():
         "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "breakdown_ms": {"pair_unweighted": uw_ms, "pair_weighted": wn_ms,
-                         "embedding_packing_other": ms_per_step - uw_ms - wn_ms},
+        "breakdown_ms": {"serial_step": mean(serial_ms), "pair_unweighted": uw_ms,
+                         "pair_weighted": wn_ms,
+                         "embedding_packing_other": mean(serial_ms) - uw_ms - wn_ms,
+                         "note": "per-kernel and breakdown times from a second timed loop "
+                                 "with the variants one after the other (no kernel shares "
+                                 "the GPU); ms_per_step is the headline loop, variants "
+                                 "overlapped on two streams" if not args.no_overlap else
+                                 "variants one after the other in both loops"},
         "tuned_options": tuned, "graph_replay": not args.no_graph,
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
         "wall_s_timed_loop": t_wall,

@@ -181,10 +181,13 @@ enum unifrac_option {
   UNIFRAC_OPT_SPARSE_THRESHOLD = 5,       /* weighted mixed kernel: branches present in fewer
                                               samples than this run through the sparse phase;
                                               -1 auto (largest study / 4), 0 all dense */
-  UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6 /* unweighted tensor-core kernel: same split;
+  UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6, /* unweighted tensor-core kernel: same split;
                                               -1 auto (largest study / 16 above 8,192
                                               samples in total, else all tensor core),
                                               0 all tensor */
+  UNIFRAC_OPT_OVERLAP_VARIANTS = 7  /* UNIFRAC_BOTH: 1 (default) runs the two variants'
+                                       packing and pair kernels on two streams after the
+                                       shared embedding; 0 one after the other */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
@@ -195,8 +198,8 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * as the context's options.  Candidates: the dense / sparse split of the
  * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
  * largest study) and of the unweighted tensor-core kernel
- * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/32 .. 1/4).
- * Each candidate runs `repeats` times (>= 1, after one warm-up run) into
+ * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/32 .. 1/4),
+ * then 3/4 and 3/2 of the best of those.  Each candidate runs `repeats` times (>= 1, after one warm-up run) into
  * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
  * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the
  * time compared is embedding + packing + pair kernels (CUDA events).
@@ -215,8 +218,11 @@ enum unifrac_stat {
   UNIFRAC_STAT_TILE_PAIRS = 5,      /* 128 x 128 pair tiles of the last run */
   UNIFRAC_STAT_SELECTED_UPDATES = 6,/* pair-branch updates the last pair kernel did
                                        (after skipping all-zero branch tiles) */
-  UNIFRAC_STAT_PAIR_KERNEL_MS = 7,  /* device time of the last pair kernel (ms) */
-  UNIFRAC_STAT_EMBED_MS = 8,        /* device time of the last embedding + pack (ms) */
+  UNIFRAC_STAT_PAIR_KERNEL_MS = 7,  /* device time of the last pair kernel (ms); after an
+                                       overlapped UNIFRAC_BOTH run: everything after the
+                                       embedding */
+  UNIFRAC_STAT_EMBED_MS = 8,        /* device time of the last embedding + pack (ms); after
+                                       an overlapped UNIFRAC_BOTH run: the embedding */
   UNIFRAC_STAT_DEVICE_BYTES = 9,    /* device memory held by the context */
   UNIFRAC_STAT_PAIR_MS_UNWEIGHTED = 10, /* device time of the pair kernel of the last */
   UNIFRAC_STAT_PAIR_MS_WEIGHTED = 11,   /*   unweighted / weighted run (ms)          */

@@ -32,6 +32,7 @@ OPT_CTAS_PER_SM = 3
 OPT_USE_GRAPH = 4
 OPT_SPARSE_THRESHOLD = 5
 OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6
+OPT_OVERLAP_VARIANTS = 7
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1
@@ -104,6 +105,8 @@ def load() -> ctypes.CDLL:
         lib.unifrac_output_bytes.restype = ctypes.c_int
         lib.unifrac_set_option.argtypes = [vp, ctypes.c_int, i64]
         lib.unifrac_set_option.restype = ctypes.c_int
+        lib.unifrac_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        lib.unifrac_get_option.restype = ctypes.c_int
         lib.unifrac_get_stat.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.unifrac_get_stat.restype = ctypes.c_int
         _lib = lib
@@ -216,6 +219,12 @@ def unifrac_set_option(ctx, option: int, value: int) -> None:
     _check(load().unifrac_set_option(ctx, option, int(value)), ctx)
 
 
+def unifrac_get_option(ctx, option: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().unifrac_get_option(ctx, option, ctypes.byref(v)), ctx)
+    return int(v.value)
+
+
 def unifrac_get_stat(ctx, stat: int) -> float:
     v = ctypes.c_double()
     _check(load().unifrac_get_stat(ctx, stat, ctypes.byref(v)), ctx)
@@ -267,6 +276,9 @@ class Context:
 
     def set_option(self, option, value) -> None:
         unifrac_set_option(self.handle, option, value)
+
+    def get_option(self, option) -> int:
+        return unifrac_get_option(self.handle, option)
 
     def stat(self, stat) -> float:
         return unifrac_get_stat(self.handle, stat)

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -123,13 +124,19 @@ void free_ctx(unifrac_ctx *ctx) {
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  ufb::DevBuf *bufs[] = {&ctx->cnt,     &ctx->flag,      &ctx->vals,  &ctx->vals2,
-                         &ctx->bits,    &ctx->partial,   &ctx->persample, &ctx->items,
-                         &ctx->studies, &ctx->stage,     &ctx->tables, &ctx->rc,
-                         &ctx->bsize,   &ctx->boff,      &ctx->blocks, &ctx->spart,
-                         &ctx->rbits,   &ctx->cpre};
+  ufb::DevBuf *bufs[] = {&ctx->cnt, &ctx->flag, &ctx->items, &ctx->studies, &ctx->stage,
+                         &ctx->tables};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
+  for (auto &V : ctx->vb) {
+    ufb::DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
+                            &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits};
+    for (auto *b : vbufs)
+      if (b->p) cudaFree(b->p);
+  }
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+  if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+  if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto &pr : ctx->ev_pair)
@@ -322,16 +329,23 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<uint32_t> fent_cnt;
   std::vector<std::pair<int32_t, int32_t>> row;  // (sample, count)
   // Parallel pass for the usual table: every row's sample indices strictly
-  // increasing and in range, counts >= 0.  Threads check and count their
-  // rows, a prefix sum places them, threads fill them; per-thread sample
-  // totals are added in thread order (integers).  Any other table takes the
-  // sequential pass below, which reports what is wrong.
+  // increasing and in range, counts >= 0.  Threads check their rows and write
+  // the entries in place (CSR positions), with per-thread sample totals added
+  // in thread order (integers); explicit zeros, if any, are squeezed out
+  // afterwards.  Any other table takes the sequential pass below, which
+  // reports what is wrong.
   bool table_done = false;
   {
     const int T = host_threads(nnz);
-    std::vector<int64_t> nzr(n_features, 0);
     std::vector<uint8_t> bad(T, 0);
+    std::vector<int64_t> zeros(T, 0);
+    std::vector<std::vector<int64_t>> tot(T);
+    fent_col.resize((size_t)nnz);
+    fent_cnt.resize((size_t)nnz);
     run_threads(T, [&](int t) {
+      std::vector<int64_t> &tt = tot[t];
+      tt.assign(n_samples, 0);
+      int64_t z = 0;  // local: one shared counter per thread would share a cache line
       for (int32_t f = (int32_t)((int64_t)n_features * t / T);
            f < (int32_t)((int64_t)n_features * (t + 1) / T); ++f) {
         const int64_t lo = indptr[f], hi = indptr[f + 1];
@@ -339,51 +353,49 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
           bad[t] = 1;
           return;
         }
-        int64_t nz = 0;
         for (int64_t e = lo; e < hi; ++e) {
-          if (indices[e] < 0 || indices[e] >= n_samples || counts[e] < 0 ||
-              (e > lo && indices[e] <= indices[e - 1])) {
+          const int32_t i = indices[e];
+          if (i < 0 || i >= n_samples || counts[e] < 0 || (e > lo && i <= indices[e - 1])) {
             bad[t] = 1;
             return;
           }
-          nz += counts[e] > 0;
+          fent_col[e] = ctx->col_of_sample[i];
+          fent_cnt[e] = (uint32_t)counts[e];
+          tt[i] += counts[e];
+          z += counts[e] == 0;
         }
-        nzr[f] = nz;
       }
+      zeros[t] = z;
     });
-    if (std::find(bad.begin(), bad.end(), 1) == bad.end()) {
-      std::vector<int64_t> at(n_features, -1);  // entry offset of each non-empty row
-      int64_t ne = 0;
-      for (int32_t f = 0; f < n_features; ++f)
-        if (nzr[f] > 0) {
-          at[f] = ne;
+    if (std::find(bad.begin(), bad.end(), 1) == bad.end() && indptr[0] == 0 &&
+        indptr[n_features] == nnz) {
+      const bool has_zeros = std::accumulate(zeros.begin(), zeros.end(), (int64_t)0) > 0;
+      int64_t out = 0;
+      for (int32_t f = 0; f < n_features; ++f) {
+        const int64_t start_f = out;
+        if (has_zeros) {
+          for (int64_t e = indptr[f]; e < indptr[f + 1]; ++e)
+            if (fent_cnt[e] != 0) {
+              fent_col[out] = fent_col[e];
+              fent_cnt[out] = fent_cnt[e];
+              ++out;
+            }
+        } else {
+          out = indptr[f + 1];
+        }
+        if (out > start_f) {
           frow_tip.push_back(feature_node[f]);
-          ne += nzr[f];
-          frow_ptr.push_back(ne);
+          frow_ptr.push_back(out);
         }
-      fent_col.resize(ne);
-      fent_cnt.resize(ne);
-      std::vector<std::vector<int64_t>> tot(T);
-      run_threads(T, [&](int t) {
-        std::vector<int64_t> &tt = tot[t];
-        tt.assign(n_samples, 0);
-        for (int32_t f = (int32_t)((int64_t)n_features * t / T);
-             f < (int32_t)((int64_t)n_features * (t + 1) / T); ++f) {
-          if (at[f] < 0) continue;
-          int64_t o = at[f];
-          for (int64_t e = indptr[f]; e < indptr[f + 1]; ++e) {
-            if (counts[e] == 0) continue;
-            const int32_t i = indices[e];
-            fent_col[o] = ctx->col_of_sample[i];
-            fent_cnt[o] = (uint32_t)counts[e];
-            tt[i] += counts[e];
-            ++o;
-          }
-        }
-      });
+      }
+      fent_col.resize(out);
+      fent_cnt.resize(out);
       for (int t = 0; t < T; ++t)
         for (int32_t i = 0; i < n_samples; ++i) total[i] += tot[t][i];
       table_done = true;
+    } else {
+      fent_col.clear();
+      fent_cnt.clear();
     }
   }
   if (!table_done) {
@@ -449,66 +461,74 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   ctx->n_frows = (int32_t)frow_tip.size();
   // ------------------------------------------- presence counts and pruning
   // n_b: the samples with a non-zero count below branch b.  Bitsets of those
-  // samples per node, one block of columns at a time (about 64 MiB of bitsets
-  // at most): a tip's bits come from its table row, an internal node's are the
-  // OR of its children's (every node ORed into its parent in postorder).  Studies start on 128-column boundaries, so a study's count at a
-  // node is a popcount over whole 64-bit words.  The most branches one sample
-  // reaches (the exactness bound of the tensor-core path) comes from
-  // bit-sliced column counters.
+  // samples per node over blocks of columns: a tip's bits come from its table
+  // row (rows are column-sorted, so a block's entries are found by binary
+  // search), an internal node's are the OR of its children's (every node ORed
+  // into its parent in postorder).  Host threads take whole blocks, each with
+  // its own bitsets and counts, merged at the end.  Studies start on
+  // 128-column boundaries, so a study's count at a node is a popcount over
+  // whole 64-bit words.  The most branches one sample reaches (the exactness
+  // bound of the tensor-core path) comes from bit-sliced column counters.
   ctx->nb.assign(n_nodes, 0);
   double pair_branch = 0.0, useful = 0.0;
   {
     const int32_t W = ctx->n_cols / 64;
-    int32_t WB = (int32_t)std::min<int64_t>(
-        W, std::max<int64_t>(2, ((int64_t)8 << 20) / (8 * (int64_t)n_nodes)));
-    WB -= WB & 1;  // whole 128-column tiles (W is even)
-    const int T = host_threads((int64_t)n_nodes * std::max(W, 1));
+    // block width: enough blocks for every thread, and at most
+    // max(16 words, ~8 MiB of bitsets) per block
+    const int T_hw = host_threads((int64_t)n_nodes * std::max(W, 1));
+    const int64_t wb_max = std::max<int64_t>(16, ((int64_t)8 << 20) / (8 * (int64_t)n_nodes));
+    int32_t WB = (int32_t)std::min<int64_t>(W, std::min<int64_t>(wb_max, (W + T_hw - 1) / T_hw));
+    WB = std::max<int32_t>(std::min<int32_t>(W, 2), WB + (WB & 1));  // whole 128-column tiles
+    const int32_t n_blocks = WB > 0 ? (W + WB - 1) / WB : 0;
+    const int T = std::max(1, std::min<int>(T_hw, n_blocks));
     constexpr int kPlanes = 32;
     // a sample reaches at most root branches: count exactly only when that
     // bound does not already settle the tensor-core exactness test
     const bool count_reach = (int64_t)root >= 65793;
     if (!count_reach) ctx->max_reach = root;
-    std::unique_ptr<uint64_t[]> bits(new uint64_t[(size_t)n_nodes * std::max(WB, 2)]);
-    std::vector<std::vector<uint64_t>> planes(T);
     std::vector<int32_t> sw0(n_studies), sw1(n_studies);
     for (int32_t st = 0; st < n_studies; ++st) {
       sw0[st] = ctx->study_col0[st] / 64;
       sw1[st] = sw0[st] + (int32_t)(((int64_t)(soff[st + 1] - soff[st]) + TILE - 1) / TILE * 2);
     }
-    std::vector<std::vector<int32_t>> acc(n_studies);
-    std::vector<int64_t> cur(frow_ptr.begin(), frow_ptr.end() - 1);  // next entry of each row
-    int32_t s_open = 0;
-    for (int32_t b0 = 0; b0 < W; b0 += WB) {
-      const int32_t b1 = std::min(W, b0 + WB), wb = b1 - b0;
-      std::memset(bits.get(), 0, sizeof(uint64_t) * (size_t)n_nodes * std::max(WB, 2));
-      // tips: the row's entries in this block (rows are column-sorted)
-      const int32_t R = ctx->n_frows;
-      run_threads(T, [&](int t) {
-        for (int32_t r = (int32_t)((int64_t)R * t / T); r < (int32_t)((int64_t)R * (t + 1) / T); ++r) {
+    struct Worker {
+      std::unique_ptr<uint64_t[]> bits;
+      std::vector<int64_t> nb;
+      std::vector<std::vector<int32_t>> acc;  // per study, for the studies it touched
+      std::vector<uint64_t> planes;
+      int64_t max_reach = 0;
+    };
+    std::vector<Worker> wk(T);
+    std::atomic<int32_t> next{0};
+    run_threads(T, [&](int t) {
+      Worker &w = wk[t];
+      if (n_blocks == 0) return;
+      w.bits.reset(new uint64_t[(size_t)n_nodes * WB]);
+      w.nb.assign(n_nodes, 0);
+      w.acc.resize(n_studies);
+      uint64_t *bits = w.bits.get();
+      for (int32_t blk; (blk = next.fetch_add(1)) < n_blocks;) {
+        const int32_t b0 = blk * WB, b1 = std::min(W, b0 + WB), wb = b1 - b0;
+        std::memset(bits, 0, sizeof(uint64_t) * (size_t)n_nodes * WB);
+        for (int32_t r = 0; r < ctx->n_frows; ++r) {
+          const int32_t *c0 = fent_col.data() + frow_ptr[r], *c1 = fent_col.data() + frow_ptr[r + 1];
           uint64_t *d = &bits[(size_t)frow_tip[r] * WB];
-          int64_t e = cur[r];
-          for (; e < frow_ptr[r + 1] && fent_col[e] < 64 * b1; ++e)
-            d[fent_col[e] / 64 - b0] |= 1ull << (fent_col[e] & 63);
-          cur[r] = e;
+          for (const int32_t *c = std::lower_bound(c0, c1, 64 * b0); c < c1 && *c < 64 * b1; ++c)
+            d[*c / 64 - b0] |= 1ull << (*c & 63);
         }
-      });
-      // internal nodes: each ORed into its parent in postorder (children first)
-      for (int32_t v = 0; v < root; ++v) {
-        const uint64_t *src = &bits[(size_t)v * WB];
-        uint64_t *d = &bits[(size_t)parent[v] * WB];
-        for (int32_t j = 0; j < wb; ++j) d[j] |= src[j];
-      }
-      // counts per node (all, and per study open in this block) and the
-      // column counters
-      int32_t s_end = s_open;
-      while (s_end < n_studies && sw0[s_end] < b1) ++s_end;
-      for (int32_t st = s_open; st < s_end; ++st)
-        if (acc[st].empty()) acc[st].assign(n_nodes, 0);
-      run_threads(T, [&](int t) {
-        std::vector<uint64_t> &pl = planes[t];
-        if (count_reach) pl.assign((size_t)kPlanes * wb, 0ull);
-        for (int32_t v = (int32_t)((int64_t)root * t / T); v < (int32_t)((int64_t)root * (t + 1) / T);
-             ++v) {
+        for (int32_t v = 0; v < root; ++v) {  // postorder: children before parents
+          const uint64_t *src = &bits[(size_t)v * WB];
+          uint64_t *d = &bits[(size_t)parent[v] * WB];
+          for (int32_t j = 0; j < wb; ++j) d[j] |= src[j];
+        }
+        int32_t s_lo = 0;  // studies intersecting the block: [s_lo, s_hi)
+        while (s_lo < n_studies && sw1[s_lo] <= b0) ++s_lo;
+        int32_t s_hi = s_lo;
+        while (s_hi < n_studies && sw0[s_hi] < b1) ++s_hi;
+        for (int32_t st = s_lo; st < s_hi; ++st)
+          if (sw1[st] > sw0[st] && w.acc[st].empty()) w.acc[st].assign(n_nodes, 0);
+        if (count_reach) w.planes.assign((size_t)kPlanes * wb, 0ull);
+        for (int32_t v = 0; v < root; ++v) {
           const uint64_t *d = &bits[(size_t)v * WB];
           int64_t all = 0;
           for (int32_t j = 0; j < wb; ++j) {
@@ -516,45 +536,54 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
             all += __builtin_popcountll(x);
             if (!count_reach) continue;
             for (int p = 0; x && p < kPlanes; ++p) {  // carry-save add into the planes
-              const uint64_t c = pl[(size_t)p * wb + j] & x;
-              pl[(size_t)p * wb + j] ^= x;
+              const uint64_t c = w.planes[(size_t)p * wb + j] & x;
+              w.planes[(size_t)p * wb + j] ^= x;
               x = c;
             }
           }
           if (!all) continue;
-          ctx->nb[v] += all;
-          for (int32_t st = s_open; st < s_end; ++st) {
+          w.nb[v] += all;
+          for (int32_t st = s_lo; st < s_hi; ++st) {
             const int32_t j0 = std::max(sw0[st], b0) - b0, j1 = std::min(sw1[st], b1) - b0;
             int32_t c = 0;
             for (int32_t j = j0; j < j1; ++j) c += __builtin_popcountll(d[j]);
-            acc[st][v] += c;
+            if (c) w.acc[st][v] += c;
           }
         }
-      });
-      for (int32_t j = 0; j < (count_reach ? wb : 0); ++j)
-        for (int q = 0; q < 64; ++q) {
-          int64_t r = 0;
-          for (int t = 0; t < T; ++t) {
-            if (planes[t].empty()) continue;
-            for (int p = 0; p < kPlanes; ++p)
-              r += (int64_t)((planes[t][(size_t)p * wb + j] >> q) & 1ull) << p;
-          }
-          ctx->max_reach = std::max(ctx->max_reach, r);
+        if (count_reach)
+          for (int32_t j = 0; j < wb; ++j)
+            for (int q = 0; q < 64; ++q) {
+              int64_t r = 0;
+              for (int p = 0; p < kPlanes; ++p)
+                r += (int64_t)((w.planes[(size_t)p * wb + j] >> q) & 1ull) << p;
+              w.max_reach = std::max(w.max_reach, r);
+            }
+      }
+    });
+    // merge: node counts, then per study (studies' statistics in study order)
+    std::vector<int32_t> a(n_nodes);
+    for (auto &w : wk) {
+      for (int32_t v = 0; v < root && !w.nb.empty(); ++v) ctx->nb[v] += w.nb[v];
+      ctx->max_reach = std::max(ctx->max_reach, w.max_reach);
+    }
+    for (int32_t st = 0; st < n_studies; ++st) {
+      std::fill(a.begin(), a.end(), 0);
+      bool any = false;
+      for (auto &w : wk)
+        if (st < (int32_t)w.acc.size() && !w.acc[st].empty()) {
+          any = true;
+          for (int32_t v = 0; v < root; ++v) a[v] += w.acc[st][v];
+          std::vector<int32_t>().swap(w.acc[st]);
         }
-      // studies that end in this block
-      while (s_open < s_end && sw1[s_open] <= b1) {
-        const std::vector<int32_t> &a = acc[s_open];
-        int64_t B_s = 0;
+      int64_t B_s = 0;
+      if (any)
         for (int32_t v = 0; v < root; ++v)
           if (a[v] > 0 && length[v] > 0.0) {
             B_s++;
             useful += 0.5 * (double)a[v] * (double)(a[v] - 1);
           }
-        const double n_s = (double)(soff[s_open + 1] - soff[s_open]);
-        pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
-        std::vector<int32_t>().swap(acc[s_open]);
-        ++s_open;
-      }
+      const double n_s = (double)(soff[st + 1] - soff[st]);
+      pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
     }
   }
   ctx->stat_pair_branch = pair_branch;
@@ -609,10 +638,28 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   // appears once for every branch on its root path):
   // S_i = (1 / C_i) * sum_f c_fi * depth(tip_f), FP64, entries in row order;
   // fixed for the context, so computed once here.
+  // (64 fixed chunks of rows, summed in chunk order: the same result
+  // whatever the number of host threads)
   std::vector<double> S(ctx->n_cols, 0.0);
-  for (int32_t r = 0; r < ctx->n_frows; ++r) {
-    const double dep = depth[frow_tip[r]];
-    for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e) S[fent_col[e]] += (double)fent_cnt[e] * dep;
+  {
+    const int32_t R = ctx->n_frows;
+    const int kChunks = R >= 4096 ? 64 : 1;
+    std::vector<std::vector<double>> part(kChunks);
+    std::atomic<int> next_chunk{0};
+    run_threads(std::min(kChunks, host_threads((int64_t)fent_col.size())), [&](int) {
+      for (int c; (c = next_chunk.fetch_add(1)) < kChunks;) {
+        std::vector<double> &P = part[c];
+        P.assign(ctx->n_cols, 0.0);
+        for (int32_t r = (int32_t)((int64_t)R * c / kChunks);
+             r < (int32_t)((int64_t)R * (c + 1) / kChunks); ++r) {
+          const double dep = depth[frow_tip[r]];
+          for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e)
+            P[fent_col[e]] += (double)fent_cnt[e] * dep;
+        }
+      }
+    });
+    for (int c = 0; c < kChunks; ++c)
+      for (int32_t col = 0; col < ctx->n_cols; ++col) S[col] += part[c][col];
   }
   for (int32_t c = 0; c < ctx->n_cols; ++c) S[c] *= inv_total[c];
   ctx->create_host_ms = ms_since(t_create0);
@@ -644,8 +691,8 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
                  (uint32_t)digits[2 * (size_t)ctx->K_pad + k];
     if ((rc = upload(ctx, &ctx->d_qperm, qperm))) return rc;
   }
-  std::vector<unsigned long long> zero8(8, 0ull);
-  if ((rc = upload(ctx, &ctx->d_counter, zero8))) return rc;
+  std::vector<unsigned long long> zero_counters(kCounters, 0ull);
+  if ((rc = upload(ctx, &ctx->d_counter, zero_counters))) return rc;
   for (auto &ev : ctx->ev) {
     e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
@@ -782,14 +829,14 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
 // Grow every buffer the plan touches (may synchronise / allocate).
 static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
   int rc;
+  VarBufs &V = ctx->vb[P.variant];
   if ((rc = grow(ctx, ctx->cnt, (size_t)ctx->n_nodes * ctx->n_cols * sizeof(uint32_t)))) return rc;
   if ((rc = grow(ctx, ctx->flag, (size_t)ctx->n_nodes * ctx->n_tiles))) return rc;
   if (P.kind == RunPlan::WEIGHTED) {
     const size_t elem = P.f64 ? 8 : 4;
     const int32_t n_words = ctx->K_pad / WORD;
-    if ((rc = grow(ctx, ctx->vals, (size_t)ctx->K_pad * ctx->n_cols * elem))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, V.bits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
+    if ((rc = grow(ctx, V.persample, (size_t)ctx->n_cols * 8))) return rc;
     P.kf_words = n_words;
     if (!P.f64 && ctx->opt_sparse_threshold != 0) {
       // dense / sparse split at a multiple of 32 positions (FP32 form only)
@@ -801,6 +848,10 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       P.kf_words = kf / WORD;
     }
     P.n_win = (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    // dense values for the positions below the split only (all of them when
+    // there is no sparse part)
+    const size_t dense_rows = P.n_win > 0 ? (size_t)P.kf_words * WORD : (size_t)ctx->K_pad;
+    if ((rc = grow(ctx, V.vals, std::max<size_t>(dense_rows, 1) * ctx->n_cols * elem))) return rc;
     if (P.n_win > 0) {
       // upper bound of the sparse blocks: every sample is in one tile, so a
       // branch has at most n_b entries and min(n_b, tiles) flagged rows
@@ -813,12 +864,12 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       // all); 8 bytes per (value, row) entry
       const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
       const uint64_t bound = nblk * 80 + 4 * rows + 8 * ents + 64;
-      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
-      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
-      if ((rc = grow(ctx, ctx->cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
-      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
-      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
-      if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 4)))
+      if ((rc = grow(ctx, V.rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
+      if ((rc = grow(ctx, V.bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, V.cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
+      if ((rc = grow(ctx, V.boff, (nblk + 1) * 8))) return rc;
+      if ((rc = grow(ctx, V.blocks, bound))) return rc;
+      if ((rc = grow(ctx, V.spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 4)))
         return rc;
     }
   } else if (P.kind == RunPlan::TENSOR) {
@@ -838,11 +889,11 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
     const int32_t n_kt = P.k_tc / 64;
     const int32_t k_words = (n_kt + 31) / 32;
     const size_t plane = (size_t)ctx->n_cols * P.k_tc * 2;
-    if ((rc = grow(ctx, ctx->vals, plane))) return rc;
-    if ((rc = grow(ctx, ctx->vals2, 3 * plane))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
-    if ((rc = grow(ctx, ctx->partial, (size_t)ctx->n_cols * 8))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, V.vals, plane))) return rc;
+    if ((rc = grow(ctx, V.vals2, 3 * plane))) return rc;
+    if ((rc = grow(ctx, V.bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
+    if ((rc = grow(ctx, V.partial, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, V.persample, (size_t)ctx->n_cols * 8))) return rc;
     if (P.n_win > 0) {
       uint64_t rows = 0, ents = 0;
       for (int32_t k = P.kf_words * WORD; k < ctx->K; ++k) {
@@ -853,33 +904,34 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       // all); 1 byte per row entry
       const uint64_t nblk = (uint64_t)ctx->n_tiles * P.n_win;
       const uint64_t bound = nblk * 80 + 4 * rows + ents + 64;
-      if ((rc = grow(ctx, ctx->rbits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
-      if ((rc = grow(ctx, ctx->rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
-      if ((rc = grow(ctx, ctx->bsize, nblk * 4))) return rc;
-      if ((rc = grow(ctx, ctx->cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
-      if ((rc = grow(ctx, ctx->boff, (nblk + 1) * 8))) return rc;
-      if ((rc = grow(ctx, ctx->blocks, bound))) return rc;
-      if ((rc = grow(ctx, ctx->spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 8))) return rc;
+      if ((rc = grow(ctx, V.rbits, (size_t)ctx->n_tiles * n_words * 4))) return rc;
+      if ((rc = grow(ctx, V.rc, (size_t)ctx->n_tiles * ctx->K_pad))) return rc;
+      if ((rc = grow(ctx, V.bsize, nblk * 4))) return rc;
+      if ((rc = grow(ctx, V.cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
+      if ((rc = grow(ctx, V.boff, (nblk + 1) * 8))) return rc;
+      if ((rc = grow(ctx, V.blocks, bound))) return rc;
+      if ((rc = grow(ctx, V.spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 8))) return rc;
     }
   } else {
     const int32_t G = ctx->K_pad / 8;
     const int32_t g_words = (G + WORD - 1) / WORD;
-    if ((rc = grow(ctx, ctx->vals, (size_t)G * ctx->n_cols))) return rc;
+    if ((rc = grow(ctx, V.vals, (size_t)G * ctx->n_cols))) return rc;
     if ((rc = grow(ctx, ctx->tables, (size_t)G * 256 * 8))) return rc;
-    if ((rc = grow(ctx, ctx->bits, (size_t)ctx->n_tiles * g_words * 4))) return rc;
-    if ((rc = grow(ctx, ctx->partial, (size_t)((G + 31) / 32) * ctx->n_cols * 8))) return rc;
-    if ((rc = grow(ctx, ctx->persample, (size_t)ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, V.bits, (size_t)ctx->n_tiles * g_words * 4))) return rc;
+    if ((rc = grow(ctx, V.partial, (size_t)((G + 31) / 32) * ctx->n_cols * 8))) return rc;
+    if ((rc = grow(ctx, V.persample, (size_t)ctx->n_cols * 8))) return rc;
   }
   return UNIFRAC_OK;
 }
 
 // Device work of one variant after the embedding (no allocation, no host copy,
 // no sync).
-static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
+static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) {
   int rc;
-  cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(ctx->d_counter + 4, 0, sizeof(unsigned long long), ctx->stream);
+  ctx->cur_slot = P.variant;
+  VarBufs &V = ctx->vb[P.variant];
+  cudaError_t e =
+      cudaMemsetAsync(cur_counters(ctx), 0, 4 * sizeof(unsigned long long), ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
   OutSpec o;
   o.out = P.dst;
@@ -895,97 +947,121 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P) {
   const int variant = P.variant;
   if (P.kind == RunPlan::WEIGHTED) {
     const double *S = ctx->d_S;
-    uint32_t *bits = static_cast<uint32_t *>(ctx->bits.p);
+    uint32_t *bits = static_cast<uint32_t *>(V.bits.p);
     // dense values for the frequently present positions, sparse blocks built
     // from the counts for the rest
     const int32_t k_end = P.n_win > 0 ? P.kf_words * WORD : ctx->K;
-    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, ctx->vals.p, bits, k_end))) return rc;
+    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, V.vals.p, bits, k_end))) return rc;
     if (P.n_win > 0) {
-      uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
+      uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
       if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, bits, rcb, nullptr))) return rc;
       if ((rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words, P.n_win,
-                                  static_cast<uint32_t *>(ctx->bsize.p),
-                                  static_cast<unsigned long long *>(ctx->boff.p),
-                                  static_cast<uint2 *>(ctx->cpre.p),
-                                  static_cast<uint8_t *>(ctx->blocks.p))))
+                                  static_cast<uint32_t *>(V.bsize.p),
+                                  static_cast<unsigned long long *>(V.boff.p),
+                                  static_cast<uint2 *>(V.cpre.p),
+                                  static_cast<uint8_t *>(V.blocks.p))))
         return rc;
     }
-    record_event(ctx, ctx->ev[1]);
+    if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 1.0;
-    if ((rc = pairs_weighted(ctx, P.f64, ctx->vals.p, bits, P.kf_words,
-                             static_cast<const uint8_t *>(ctx->blocks.p),
-                             static_cast<const unsigned long long *>(ctx->boff.p), P.n_win,
-                             P.n_win > 0 ? static_cast<uint32_t *>(ctx->spart.p) : nullptr, S,
+    if ((rc = pairs_weighted(ctx, P.f64, V.vals.p, bits, P.kf_words,
+                             static_cast<const uint8_t *>(V.blocks.p),
+                             static_cast<const unsigned long long *>(V.boff.p), P.n_win,
+                             P.n_win > 0 ? static_cast<uint32_t *>(V.spart.p) : nullptr, S,
                              d_items, n_items, o)))
       return rc;
   } else if (P.kind == RunPlan::TENSOR) {
-    uint16_t *X = static_cast<uint16_t *>(ctx->vals.p);
-    uint16_t *D = static_cast<uint16_t *>(ctx->vals2.p);
-    uint32_t *kbits = static_cast<uint32_t *>(ctx->bits.p);
-    double *a = static_cast<double *>(ctx->persample.p);
-    unsigned long long *aq = static_cast<unsigned long long *>(ctx->partial.p);
+    uint16_t *X = static_cast<uint16_t *>(V.vals.p);
+    uint16_t *D = static_cast<uint16_t *>(V.vals2.p);
+    uint32_t *kbits = static_cast<uint32_t *>(V.bits.p);
+    double *a = static_cast<double *>(V.persample.p);
+    unsigned long long *aq = static_cast<unsigned long long *>(V.partial.p);
     e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "clear per-sample sums");
     if ((rc = pack_tc(ctx, cnt, flag, P.k_tc, X, D, kbits, aq))) return rc;
     unsigned long long *spart = nullptr;
     if (P.n_win > 0) {
-      uint32_t *rbits = static_cast<uint32_t *>(ctx->rbits.p);
-      uint8_t *rcb = static_cast<uint8_t *>(ctx->rc.p);
+      uint32_t *rbits = static_cast<uint32_t *>(V.rbits.p);
+      uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
       if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
       if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
-                                  static_cast<uint32_t *>(ctx->bsize.p),
-                                  static_cast<unsigned long long *>(ctx->boff.p),
-                                  static_cast<uint2 *>(ctx->cpre.p),
-                                  static_cast<uint8_t *>(ctx->blocks.p))))
+                                  static_cast<uint32_t *>(V.bsize.p),
+                                  static_cast<unsigned long long *>(V.boff.p),
+                                  static_cast<uint2 *>(V.cpre.p),
+                                  static_cast<uint8_t *>(V.blocks.p))))
         return rc;
-      spart = static_cast<unsigned long long *>(ctx->spart.p);
+      spart = static_cast<unsigned long long *>(V.spart.p);
     }
     if ((rc = finish_tc_a(ctx, aq, a))) return rc;
-    record_event(ctx, ctx->ev[1]);
+    if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 64.0;
     record_event(ctx, ctx->ev_sp[0][0]);
     if (spart &&
-        (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(ctx->rbits.p), P.kf_words,
-                                    static_cast<const uint8_t *>(ctx->blocks.p),
-                                    static_cast<const unsigned long long *>(ctx->boff.p),
+        (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(V.rbits.p), P.kf_words,
+                                    static_cast<const uint8_t *>(V.blocks.p),
+                                    static_cast<const unsigned long long *>(V.boff.p),
                                     P.n_win, spart, d_items, n_items)))
       return rc;
     record_event(ctx, ctx->ev_sp[0][1]);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, aq, spart, d_items, n_items, o))) return rc;
   } else {
-    double *a = static_cast<double *>(ctx->persample.p);
-    uint8_t *bytes = static_cast<uint8_t *>(ctx->vals.p);
+    double *a = static_cast<double *>(V.persample.p);
+    uint8_t *bytes = static_cast<uint8_t *>(V.vals.p);
     double *tables = static_cast<double *>(ctx->tables.p);
-    uint32_t *gbits = static_cast<uint32_t *>(ctx->bits.p);
+    uint32_t *gbits = static_cast<uint32_t *>(V.bits.p);
     if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
-    record_event(ctx, ctx->ev[1]);
+    if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 8.0;
     if ((rc = pairs_lookup(ctx, bytes, tables, gbits, a, d_items, n_items, o))) return rc;
   }
-  record_event(ctx, ctx->ev[2]);
+  if (!overlapped) record_event(ctx, ctx->ev[2]);
   record_event(ctx, ctx->ev_pair[variant][1]);
-  e = cudaMemcpyAsync(ctx->d_counter + 2 + variant, ctx->d_counter, sizeof(unsigned long long),
-                      cudaMemcpyDeviceToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->d_counter + 5 + variant, ctx->d_counter + 4,
-                        sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "counter copy");
   ctx->sel_unit_v[variant] = ctx->sel_unit;
   return UNIFRAC_OK;
 }
 
 // The embedding once, then each variant's packing and pair kernels.
+// With two plans and UNIFRAC_OPT_OVERLAP_VARIANTS, the second plan runs on a
+// second stream forked after the embedding and joined at the end (both are
+// captured into the same graph); the variants have separate buffers and
+// counters, and share only the read-only embedding and the output buffer,
+// which they write in disjoint halves.
 static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
   int rc;
   record_event(ctx, ctx->ev[0]);
   if ((rc = embed_counts(ctx, static_cast<uint32_t *>(ctx->cnt.p),
                          static_cast<uint8_t *>(ctx->flag.p))))
     return rc;
-  for (int i = 0; i < n_plans; ++i)
-    if ((rc = enqueue_variant(ctx, plans[i]))) return rc;
+  const bool overlap = n_plans == 2 && ctx->opt_overlap;
+  if (!overlap) {
+    for (int i = 0; i < n_plans; ++i)
+      if ((rc = enqueue_variant(ctx, plans[i], false))) return rc;
+    return UNIFRAC_OK;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ctx->stream2) {
+    e = cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "second stream");
+  }
+  record_event(ctx, ctx->ev[1]);  // the embedding alone
+  e = cudaEventRecord(ctx->ev_fork2, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork2, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
+  if ((rc = enqueue_variant(ctx, plans[0], true))) return rc;
+  cudaStream_t main_stream = ctx->stream;
+  ctx->stream = ctx->stream2;
+  rc = enqueue_variant(ctx, plans[1], true);
+  ctx->stream = main_stream;
+  e = cudaEventRecord(ctx->ev_join2, ctx->stream2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
+  if (rc) return rc;
+  record_event(ctx, ctx->ev[2]);
   return UNIFRAC_OK;
 }
 
@@ -1199,6 +1275,10 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_use_graph = (int)value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_OVERLAP_VARIANTS:
+      if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_overlap = (int)value;
+      return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_THRESHOLD:
       if (value < -1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_sparse_threshold = value;
@@ -1220,6 +1300,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
     case UNIFRAC_OPT_PERSISTENT: *value = ctx->opt_persistent; return UNIFRAC_OK;
     case UNIFRAC_OPT_CTAS_PER_SM: *value = ctx->opt_ctas_per_sm; return UNIFRAC_OK;
     case UNIFRAC_OPT_USE_GRAPH: *value = ctx->opt_use_graph; return UNIFRAC_OK;
+    case UNIFRAC_OPT_OVERLAP_VARIANTS: *value = ctx->opt_overlap; return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
       *value = ctx->opt_uw_sparse_threshold;
@@ -1252,32 +1333,40 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
   ctx->opt_use_graph = 0;
   double best = 1e300;
   int64_t best_v = cands[0].second;
-  for (auto &c : cands) {
-    int rc = unifrac_set_option(ctx, c.first, c.second);
-    if (rc) break;
+  std::vector<int64_t> tried;
+  // time one threshold (best of `repeats` runs after a warm-up run)
+  auto trial = [&](int64_t v) -> int {
+    if (std::find(tried.begin(), tried.end(), v) != tried.end()) return UNIFRAC_OK;
+    tried.push_back(v);
+    int rc = unifrac_set_option(ctx, option, v);
+    if (rc) return rc;
     double t = 1e300;
     for (int r = 0; r <= repeats; ++r) {
       rc = unifrac_run(ctx, variant, precision, 0, -1, UNIFRAC_OUT_CONDENSED, out, out_bytes);
-      if (rc) break;
+      if (rc) return rc;
       cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
-      if (e != cudaSuccess) {
-        ctx->opt_use_graph = saved_graph;
-        return cuda_fail(ctx, e, "autotune");
-      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
       if (r > 0) t = std::min(t, (double)ms);  // first run is the warm-up
     }
-    if (rc) {
-      ctx->opt_use_graph = saved_graph;
-      return rc;
-    }
     if (t < best) {
       best = t;
-      best_v = c.second;
+      best_v = v;
     }
+    return UNIFRAC_OK;
+  };
+  int rc = UNIFRAC_OK;
+  for (auto &c : cands)
+    if ((rc = trial(c.second))) break;
+  // then the thresholds 3/4 and 3/2 of the best coarse one
+  if (!rc && best_v > 0) {
+    const int64_t coarse = best_v;
+    if ((rc = trial(std::max<int64_t>(2, coarse * 3 / 4))) == UNIFRAC_OK)
+      rc = trial(coarse * 3 / 2);
   }
   ctx->opt_use_graph = saved_graph;
+  if (rc) return rc;
   return unifrac_set_option(ctx, option, best_v);
 }
 
@@ -1301,7 +1390,8 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
       if (stat == UNIFRAC_STAT_SELECTED_UPDATES) {
         unsigned long long c = 0;
-        e = cudaMemcpy(&c, ctx->d_counter, sizeof(c), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(&c, ctx->d_counter + kCounterBase + 4 * ctx->cur_slot, sizeof(c),
+                       cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
         *value = (double)c * ctx->sel_unit * (double)TILE * (double)TILE;
         return UNIFRAC_OK;
@@ -1336,16 +1426,16 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
       unsigned long long c = 0;
-      e = cudaMemcpy(&c, ctx->d_counter + 2 + v, sizeof(c), cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(&c, ctx->d_counter + kCounterBase + 4 * v, sizeof(c), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
       *value = (double)c * ctx->sel_unit_v[v] * (double)TILE * (double)TILE;
       return UNIFRAC_OK;
     }
-    case UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED:
-    case UNIFRAC_STAT_SPARSE_MS_WEIGHTED:
     case UNIFRAC_STAT_CREATE_HOST_MS: *value = ctx->create_host_ms; return UNIFRAC_OK;
     case UNIFRAC_STAT_CREATE_DEVICE_MS: *value = ctx->create_device_ms; return UNIFRAC_OK;
     case UNIFRAC_STAT_MAX_REACH: *value = (double)ctx->max_reach; return UNIFRAC_OK;
+    case UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED:
+    case UNIFRAC_STAT_SPARSE_MS_WEIGHTED:
     case UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED:
     case UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED: {
       const int v = (stat == UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED ||
@@ -1357,7 +1447,8 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       if (stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED ||
           stat == UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED) {
         unsigned long long c = 0;
-        e = cudaMemcpy(&c, ctx->d_counter + 5 + v, sizeof(c), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(&c, ctx->d_counter + kCounterBase + 4 * v + 2, sizeof(c),
+                       cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
         *value = (double)c;
         return UNIFRAC_OK;
@@ -1374,10 +1465,13 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
       DeviceGuard g(ctx->device);
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
-      unsigned long long c[2] = {0, 0};
+      unsigned long long c[kCounters] = {0};
       e = cudaMemcpy(c, ctx->d_counter, sizeof(c), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
-      *value = -(double)c[1];
+      // the error codes of both variant slots (a run of both may raise in either)
+      const unsigned long long err =
+          c[kCounterBase + 1] ? c[kCounterBase + 1] : c[kCounterBase + 4 + 1];
+      *value = -(double)err;
       return UNIFRAC_OK;
     }
     default:

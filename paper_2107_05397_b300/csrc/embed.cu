@@ -567,15 +567,15 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
     k_rare_fill<true><<<grid_fill, 256, 0, st>>>(
         ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
         ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre, blocks,
-        ctx->blocks.bytes, ctx->d_counter + 1);
+        cur_bufs(ctx).blocks.bytes, cur_counters(ctx) + 1);
   } else {
     k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
                                               ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid_fill, 256, 0, st>>>(
         ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
-        ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks, ctx->blocks.bytes,
-        ctx->d_counter + 1);
+        ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks, cur_bufs(ctx).blocks.bytes,
+        cur_counters(ctx) + 1);
   }
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();
@@ -651,7 +651,7 @@ int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, uint
   const int32_t G = ctx->K_pad / 8;
   const int32_t g_words = (G + WORD - 1) / WORD;
   const int32_t n_gblocks = (G + GR - 1) / GR;
-  double *partial = static_cast<double *>(ctx->partial.p);
+  double *partial = static_cast<double *>(cur_bufs(ctx).partial.p);
   if (G > 0 && ctx->n_tiles > 0) {
     k_lookup_tables<<<G, 256, 0, st>>>(ctx->K, ctx->d_len_perm, tables);
     dim3 grid(ctx->n_tiles, n_gblocks);

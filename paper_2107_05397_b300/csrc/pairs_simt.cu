@@ -702,7 +702,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
-        1.0, S, 0, o, ctx->d_counter);
+        1.0, S, 0, o, cur_counters(ctx));
     ctx->stat_launches += 1;
   } else {
     const bool sparse = n_win > 0;
@@ -714,8 +714,8 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
       k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
           items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-          ctx->blocks.bytes, ctx->n_tiles, nullptr, spart,
-          ctx->d_counter + 4);
+          cur_bufs(ctx).blocks.bytes, ctx->n_tiles, nullptr, spart,
+          cur_counters(ctx) + 2);
       ctx->stat_launches += 1;
     }
     record_event(ctx, ctx->ev_sp[1][1]);
@@ -725,7 +725,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
         sparse ? spart : nullptr, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
-        ctx->d_counter);
+        cur_counters(ctx));
     ctx->stat_launches += 1;
   }
   e = cudaGetLastError();
@@ -744,8 +744,8 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
   k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
       items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-      ctx->blocks.bytes, ctx->n_tiles, ctx->d_qperm, spart,
-      ctx->d_counter + 4);
+      cur_bufs(ctx).blocks.bytes, ctx->n_tiles, ctx->d_qperm, spart,
+      cur_counters(ctx) + 2);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel");
@@ -763,7 +763,7 @@ int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lookup kernel attribute");
   k_pairs_lookup<<<n_items, kThreads, smem, ctx->stream>>>(items, bytes, ctx->n_cols, tables,
-                                                           gbits, g_words, a, o, ctx->d_counter);
+                                                           gbits, g_words, a, o, cur_counters(ctx));
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lookup pair kernel");

@@ -542,7 +542,7 @@ int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *
       cudaFuncSetAttribute(k_pairs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core kernel attribute");
   k_pairs_tc<<<n_items, TC_THREADS, TC_SMEM, ctx->stream>>>(
-      mx, md, items, kbits, k_words, ctx->n_cols, aq, spart, o, ctx->d_counter);
+      mx, md, items, kbits, k_words, ctx->n_cols, aq, spart, o, cur_counters(ctx));
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core pair kernel");

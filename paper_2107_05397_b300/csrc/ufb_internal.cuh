@@ -49,6 +49,18 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Work buffers of one variant's packing and pair kernels.  Each variant slot
+// (0 unweighted, 1 weighted normalized) has its own set, so the two variants
+// of one call can run concurrently on two streams.
+struct VarBufs {
+  DevBuf vals, vals2, bits, persample, partial, rc, bsize, boff, blocks, cpre, spart, rbits;
+};
+
+// Device counters: [0, kCounterBase) unused; slot s (variant) owns
+// kCounterBase + 4 s + {0: selected units, 1: error code, 2: sparse updates}.
+constexpr int kCounterBase = 8;
+constexpr int kCounters = kCounterBase + 8;
+
 }  // namespace ufb
 
 struct unifrac_ctx {
@@ -99,7 +111,7 @@ struct unifrac_ctx {
   // ---- statistics
   double stat_pair_branch = 0, stat_useful = 0;
   double stat_launches = 0, stat_tile_pairs = 0;
-  unsigned long long *d_counter = nullptr;  // [8] device counters
+  unsigned long long *d_counter = nullptr;  // [kCounters] device counters
   double sel_unit = 1.0;                    // branches per counted selection unit
   double sel_unit_v[2] = {1.0, 1.0};        // same, last run of each variant
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -117,6 +129,7 @@ struct unifrac_ctx {
   int opt_persistent = -1;  // -1 auto
   int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
+  int opt_overlap = 1;                // both variants of one call on two streams
   int64_t opt_sparse_threshold = -1;  // presence count below which a branch runs sparse
   int64_t opt_uw_sparse_threshold = -1;  // same, unweighted tensor-core form
   float sp_scale = 1.0f;              // fixed-point scale of the sparse sums (power of 2)
@@ -129,6 +142,10 @@ struct unifrac_ctx {
   // ---- CUDA graph of the last run (UNIFRAC_OPT_USE_GRAPH)
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // second stream of an overlapped two-variant run, and its fork / join
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  int cur_slot = 0;                   // variant slot being enqueued
   cudaGraphExec_t graph_exec = nullptr;
   int gk_variant = -1, gk_precision = -1, gk_layout = -1;
   int32_t gk_s0 = 0, gk_s1 = 0;
@@ -138,10 +155,18 @@ struct unifrac_ctx {
   bool capturing = false;
 
   // ---- work buffers (grown on demand)
-  ufb::DevBuf cnt, flag, vals, vals2, bits, partial, persample, items, studies, stage, tables,
-      rc, bsize, boff, blocks, spart, rbits, cpre;
+  ufb::DevBuf cnt, flag, items, studies, stage, tables;
+  ufb::VarBufs vb[2];
   size_t device_bytes = 0;
 };
+
+namespace ufb {
+// buffers and counters of the variant slot being enqueued
+inline VarBufs &cur_bufs(unifrac_ctx *ctx) { return ctx->vb[ctx->cur_slot]; }
+inline unsigned long long *cur_counters(unifrac_ctx *ctx) {
+  return ctx->d_counter + kCounterBase + 4 * ctx->cur_slot;
+}
+}  // namespace ufb
 
 namespace ufb {
 

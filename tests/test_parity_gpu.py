@@ -402,6 +402,37 @@ def test_both_variants_in_one_run(small, precision, layout):
     np.testing.assert_array_equal(host, np.concatenate([uw, wn]).astype(np.float64))
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_both_overlapped_equals_serial(small, graph):
+    """UNIFRAC_BOTH with the variants on two streams is bit-identical to the
+    serial run (both variants with a sparse part, eager and graph replay)."""
+    import torch
+    w, _ = small
+    with ub.Context(w.tree, w.table) as ctx:
+        ctx.set_option(ub.OPT_SPARSE_THRESHOLD, 24)
+        ctx.set_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD, 12)
+        ctx.set_option(ub.OPT_USE_GRAPH, graph)
+        ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0)
+        serial = ctx.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED).cpu().numpy()
+        ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 1)
+        assert ctx.get_option(ub.OPT_OVERLAP_VARIANTS) == 1
+        for _ in range(3):
+            over = ctx.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(over.cpu().numpy(), serial)
+        assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
+        assert ctx.stat(ub.STAT_SPARSE_UPDATES_WEIGHTED) > 0
+        assert ctx.stat(ub.STAT_SPARSE_UPDATES_UNWEIGHTED) > 0
+        assert ctx.stat(ub.STAT_SELECTED_WEIGHTED) > 0
+        for sp, pair in ((ub.STAT_SPARSE_MS_WEIGHTED, ub.STAT_PAIR_MS_WEIGHTED),
+                         (ub.STAT_SPARSE_MS_UNWEIGHTED, ub.STAT_PAIR_MS_UNWEIGHTED)):
+            # the sparse kernel is timed inside its variant's pair phase
+            assert 0.0 < ctx.stat(sp) <= ctx.stat(pair)
+    host = run(w.tree, w.table, ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, host=True,
+               options={ub.OPT_SPARSE_THRESHOLD: 24, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 12})
+    np.testing.assert_array_equal(host, serial.astype(np.float64))
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_paper_scale_workload_sampled_rows(variant):
     """25,000 samples on a 200,000-tip tree (EMP-sized; about 396k kept
