@@ -165,8 +165,16 @@ void study_items(int32_t study, int32_t n, int32_t tile0, int layout, int32_t s0
   if (n <= 0) return;
   if (n == 1 && layout != UNIFRAC_OUT_FULL) return;
   const int32_t T = (n + TILE - 1) / TILE;
-  for (int32_t I = 0; I < T; ++I) {
-    for (int32_t J = I; J < T; ++J) {
+  // Tile pairs in blocks of kOrderBlock x kOrderBlock tiles: the CTAs resident
+  // at one time (about one block) then share their row tiles and their column
+  // tiles, so each operand slice comes from DRAM once per block and is reused
+  // from L2 (row by row, every CTA of a wave would stream its own column
+  // tile).  The set of pairs is the same in any order.
+  constexpr int32_t kOrderBlock = 12;
+  for (int32_t BI = 0; BI < T; BI += kOrderBlock)
+  for (int32_t BJ = BI; BJ < T; BJ += kOrderBlock)
+  for (int32_t I = BI; I < std::min(T, BI + kOrderBlock); ++I) {
+    for (int32_t J = std::max(I, BJ); J < std::min(T, BJ + kOrderBlock); ++J) {
       bool need = (I == J && layout == UNIFRAC_OUT_FULL);
       if (!need) {
         // differences delta = lj - li of pairs li < lj in the tile pair
