@@ -80,11 +80,12 @@ def measured_peaks():
 
 # source files each pair kernel is built from (traffic records are void once
 # any of them changes)
+# (capi.cu orders the tile pairs, which shapes the L2 reuse and so the traffic)
 KERNEL_SOURCES = {
-    "k_pairs_tc": ("pairs_tc.cu", "epilogue.cuh", "ufb_internal.cuh"),
-    "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"),
-    "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh"),
-    "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh"),
+    "k_pairs_tc": ("pairs_tc.cu", "epilogue.cuh", "ufb_internal.cuh", "capi.cu"),
+    "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh", "capi.cu"),
+    "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh", "capi.cu"),
+    "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh", "capi.cu"),
 }
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -445,12 +446,18 @@ def main():
     entry("k_pairs_tc", uw_ms - mean(sp_uw_ms), 6.0 * mean(sel_uw), "tensor", tc_peak, "TFLOP/s",
           "3 BF16 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)",
           "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)")
-    entry("k_pairs_sparse<true>", mean(sp_uw_ms), 2.0 * mean(sp_uw_n), "alu", alu_peak, "TFLOP/s",
-          "2 ops (compare-free add of q_b, index) per co-present pair-branch", alu_src)
+    # sparse kernels: one shared-memory atomic add per co-present pair-branch;
+    # the shared-memory unit takes one 32-lane wavefront per cycle per SM
+    atom_peak = sms * 32 * sm_max * 1e6 / 1e12
+    atom_src = (f"{sms} SMs x 32 shared-memory atomic lanes x {sm_max:.0f} MHz (one 32-lane "
+                "wavefront per cycle per SM)")
+    entry("k_pairs_sparse<true>", mean(sp_uw_ms), mean(sp_uw_n), "smem_atomic", atom_peak,
+          "T updates/s", "1 shared-memory u64 add of q_b per co-present pair-branch", atom_src)
     entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms), 2.0 * mean(sel_wn), "alu", alu_peak,
           "TFLOP/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
-    entry("k_pairs_sparse<false>", mean(sp_wn_ms), 2.0 * mean(sp_wn_n), "alu", alu_peak,
-          "TFLOP/s", "2 ops (min, add) per co-present pair-branch", alu_src)
+    entry("k_pairs_sparse<false>", mean(sp_wn_ms), mean(sp_wn_n), "smem_atomic", atom_peak,
+          "T updates/s", "1 shared-memory u32 add of min(V_i, V_j) per co-present pair-branch",
+          atom_src)
     roofline = max(kernels, key=lambda k: k["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
