@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--streamed-chunk", type=int, default=256,
+                    help="stripes per chunk of the streamed-output measurement")
+    ap.add_argument("--mantel-perms", type=int, default=999,
+                    help="permutations of the Mantel-test measurement (0 = skip it)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="run the two variants one after the other in the headline loop")
     ap.add_argument("--sparse-fraction", type=float, default=None,
@@ -543,6 +547,8 @@ def main():
 
     # the device memory of the timed context is released before the
     # end-to-end and per-study runs create contexts of their own
+    tuned_opts = {o: ctx.get_option(o) for o in (ub.OPT_SPARSE_THRESHOLD,
+                                                 ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD)}
     ctx.close()
     torch.cuda.empty_cache()
 
@@ -575,6 +581,109 @@ def main():
                        "s_create_run_destroy": [round(float(x), 5) for x in med],
                        "includes": "create (validation, host prep, upload) + one run of both "
                                    "variants + D2H of both condensed matrices + destroy"}
+
+    # streamed output: both matrices into host memory, computed in chunks of
+    # stripes (only two chunks on the device), copies and merge overlapped
+    if rank == 0 and not args.no_e2e and w.table.study_offsets is None:
+        nst = N // 2
+        chunk = max(1, min(nst, args.streamed_chunk))
+        with ub.Context(w.tree, w.table, stream=stream) as sctx:
+            for k_, v_ in tuned_opts.items():
+                sctx.set_option(k_, v_)
+            res_s = np.empty(2 * nb_cond // 4, np.float32)
+            sctx.run_streamed(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, chunk, out=res_s)  # warm-up
+            ts_ = []
+            for rep in range(3):
+                t0 = time.perf_counter()
+                sctx.run_streamed(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, chunk, out=res_s)
+                ts_.append(time.perf_counter() - t0)
+        t_s = float(np.median(ts_))
+        line["streamed"] = {"value": units_per_step / t_s, "unit": UNIT, "s_per_call": t_s,
+                            "chunk_stripes": chunk, "chunks": -(-nst // chunk),
+                            "includes": "both variants into host memory (condensed), stripes "
+                                        "computed chunk by chunk, D2H and host merge overlapped "
+                                        "with the next chunk"}
+        del res_s
+
+    # PCoA of the weighted matrix (full layout, FP32) on the device: the
+    # ordination the distance matrix feeds
+    if rank == 0 and not args.no_e2e and w.table.study_offsets is None:
+        k_pc, it_pc = 10, 12
+        with ub.Context(w.tree, w.table, stream=stream) as pctx:
+            for k_, v_ in tuned_opts.items():
+                pctx.set_option(k_, v_)
+            Dfull = pctx.run(ub.WEIGHTED_NORMALIZED, ub.MIXED, ub.OUT_FULL)
+            torch.cuda.synchronize()
+        ub.unifrac_pcoa(Dfull, k=k_pc, iters=it_pc, seed=1)  # warm-up
+        tp_ = []
+        for rep in range(3):
+            t0 = time.perf_counter()
+            lam_pc, _ = ub.unifrac_pcoa(Dfull, k=k_pc, iters=it_pc, seed=1)
+            tp_.append(time.perf_counter() - t0)
+        t_p = float(np.median(tp_))
+        # device traffic: D read and A written once, A read once per product
+        dev_bytes = (2 + it_pc + 1) * 4.0 * N * N
+        line["pcoa"] = {"s_per_call": t_p, "n": N, "k": k_pc, "iters": it_pc,
+                        "eigenvalues_top3": [float(x) for x in lam_pc[:3]],
+                        "device_stream_gbs": dev_bytes / t_p / 1e9,
+                        "includes": "A = -1/2 D o D on the device, subspace iteration (cuBLAS "
+                                    "SGEMM products, host FP64 centring / CholeskyQR2 / Jacobi), "
+                                    "wall time of the synchronous call"}
+        del Dfull
+        torch.cuda.empty_cache()
+
+    # Mantel test, Pearson and Spearman, between the unweighted and weighted
+    # matrices of this workload (full layout, FP32): the downstream comparison
+    # of two distance matrices, with args.mantel_perms permutations
+    if rank == 0 and not args.no_e2e and w.table.study_offsets is None and args.mantel_perms > 0:
+        with ub.Context(w.tree, w.table, stream=stream) as mctx:
+            for k_, v_ in tuned_opts.items():
+                mctx.set_option(k_, v_)
+            Xu = mctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL)
+            Xw = mctx.run(ub.WEIGHTED_NORMALIZED, ub.MIXED, ub.OUT_FULL)
+            torch.cuda.synchronize()
+        m_perm = args.mantel_perms
+        perms = np.random.default_rng(5).permuted(
+            np.tile(np.arange(N, dtype=np.int32), (m_perm, 1)), axis=1)
+        mres = {}
+        for method in ("pearson", "spearman"):
+            ub.unifrac_mantel(Xu, Xw, perms[:8], method)  # warm-up
+            tm_ = []
+            for rep in range(2):
+                t0 = time.perf_counter()
+                r_m, _, p_m = ub.unifrac_mantel(Xu, Xw, perms, method)
+                tm_.append(time.perf_counter() - t0)
+            mres[method] = {"s_per_call": float(np.median(tm_)), "r": r_m, "p": p_m}
+        P_ = N * (N - 1) // 2
+        alg = (m_perm + 1) * 2.0 * P_ * 4  # x and y value of every pair, per permutation
+        t_pear = mres["pearson"]["s_per_call"]
+        hbm = (peaks or {}).get("hbm_gbs") or 6400.0
+        ach = alg / t_pear / 1e9
+        mantel = {"n": N, "permutations": m_perm, **mres,
+                  "roofline": {"kernel": "k_mantel_cross<float,2>", "bound": "hbm",
+                               "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                               "work": "the x and y value of every pair once per permutation "
+                                       "(2 x 4 bytes x P pairs)",
+                               "timed": "whole synchronous Pearson call (moments, upload of "
+                                        "the permutations, cross sums, reduction)"}}
+        if not args.no_cpu_baseline:
+            from oracle import mantel as om
+            n_c, m_c = min(1500, N), 4
+            rng_c = np.random.default_rng(6)
+            iu = np.triu_indices(n_c, 1)
+            xc = Xu.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
+            yc = Xw.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
+            pc = np.array([rng_c.permutation(n_c) for _ in range(m_c)])
+            t0 = time.perf_counter()
+            om.mantel(xc, yc, n_c, pc, "pearson")
+            t_c = time.perf_counter() - t0
+            per = t_c / ((m_c + 1) * (n_c * (n_c - 1) // 2))
+            mantel["cpu_baseline"] = {
+                "kind": "oracle", "cores": 1, "sample": f"Pearson, n = {n_c}, {m_c} permutations",
+                "s_per_pair_permutation": per, "est_s_per_call": per * (m_perm + 1) * P_}
+        line["mantel"] = mantel
+        del Xu, Xw
+        torch.cuda.empty_cache()
 
     if rank == 0 and w.table.study_offsets is not None and not args.no_per_study:
         # the same studies with one context and one launch sequence per study,

@@ -151,6 +151,28 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
                 int32_t stripe_start, int32_t stripe_stop, int layout,
                 void *out, size_t out_bytes);
 
+/*
+ * unifrac_run_streamed -- the whole matrix into HOST memory, computed in
+ * chunks of `chunk_stripes` stripes so that only two chunks live on the device
+ * (for sample counts whose matrix exceeds device memory).  Section II of the
+ * paper: the matrix is computed as a set of stripes that are merged into the
+ * final matrix afterwards.
+ *
+ *   layout   UNIFRAC_OUT_CONDENSED or UNIFRAC_OUT_FULL (as unifrac_run; with
+ *            UNIFRAC_BOTH the unweighted matrix first, then the weighted one)
+ *   host_out caller-owned host buffer of >= unifrac_output_bytes(layout)
+ *            (x2 for UNIFRAC_BOTH) bytes; pinned or pageable
+ *
+ * Each chunk's stripes are computed into a device buffer, copied to pinned
+ * host memory on a copy stream while the next chunk computes, and scattered
+ * into host_out by host threads.  The values are those of unifrac_run.
+ * Single-study contexts only (UNIFRAC_E_UNSUPPORTED otherwise).  Synchronous:
+ * returns when host_out is complete.  Keeps two device and two pinned host
+ * chunk buffers in the context until it is destroyed.
+ */
+int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layout,
+                         void *host_out, size_t out_bytes, int32_t chunk_stripes);
+
 /* Frees the context and its device buffers (synchronises its stream first).
  * NULL-safe. */
 void unifrac_destroy(unifrac_ctx *ctx);
@@ -173,11 +195,12 @@ int unifrac_output_bytes(const unifrac_ctx *ctx, int precision, int layout,
 enum unifrac_option {
   UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL = 0, /* 0 auto (tensor core), 1 tensor core,
                                               2 bit-packed lookup (FP64 sums) */
-  UNIFRAC_OPT_WEIGHTED_FLUSH = 1,         /* FP32 branches per flush into the compensated total, 16..4096 */
-  UNIFRAC_OPT_PERSISTENT = 2,             /* 0 one CTA per tile pair, 1 persistent
-                                              work queue (default for many studies) */
-  UNIFRAC_OPT_CTAS_PER_SM = 3,            /* persistent grid = SMs x this, 1..8 */
-  UNIFRAC_OPT_USE_GRAPH = 4,              /* 1 = capture the level loop in a CUDA graph */
+  UNIFRAC_OPT_WEIGHTED_FLUSH = 1,         /* weighted mixed kernel: selected branches summed
+                                              in registers before each add into the FP32
+                                              running totals (shared memory), 16..4096 */
+  /* 2, 3: unused */
+  UNIFRAC_OPT_USE_GRAPH = 4,              /* 1 = capture a run (all its launches) in a CUDA
+                                              graph and replay it while nothing changes */
   UNIFRAC_OPT_SPARSE_THRESHOLD = 5,       /* weighted mixed kernel: branches present in fewer
                                               samples than this run through the sparse phase;
                                               -1 auto (largest study / 4), 0 all dense */
@@ -207,6 +230,74 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  */
 int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
                      size_t out_bytes, int repeats);
+
+/*
+ * unifrac_pcoa -- principal coordinates analysis of a distance matrix, the
+ * ordination the UniFrac matrix feeds (the paper, Sections I and II).
+ * Classical PCoA: A = -1/2 (D o D), B = J A J with J = I - 11^T / n; returns
+ * the k largest eigenvalues of B (descending) and the coordinates
+ * U_k sqrt(max(lambda_k, 0)).
+ *
+ *   dist       DEVICE pointer, the full n x n matrix (unifrac_run with
+ *              UNIFRAC_OUT_FULL), float (UNIFRAC_MIXED) or double (UNIFRAC_FP64);
+ *              not modified
+ *   k          1 <= k <= n components
+ *   iters      subspace iterations (>= 0; 12 is ample for the leading
+ *              components of UniFrac matrices)
+ *   seed       seed of the random start (results are reproducible)
+ *   eigvals    HOST double[k]
+ *   coords     HOST double[n * k], row-major (sample i: coords[i * k .. + k))
+ *   cuda_stream  stream for the device work (NULL = legacy default stream)
+ *
+ * Method: subspace iteration with min(n, 2k + 16) columns; the products with A on
+ * the device (FP32 A, cuBLAS SGEMM), the n x m centring, orthonormalisation
+ * and the small eigenproblem on host threads in FP64.  Allocates about
+ * 4 n^2 bytes of device memory for A while it runs (UNIFRAC_E_OOM if that
+ * fails).  Synchronous.  Errors: UNIFRAC_E_INVALID_ARG, UNIFRAC_E_OOM,
+ * UNIFRAC_E_CUDA.  No context needed.
+ */
+int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t k, int32_t iters,
+                 uint64_t seed, double *eigvals, double *coords, void *cuda_stream);
+
+/*
+ * unifrac_mantel -- the Mantel test between two distance matrices (the paper,
+ * Section III): the correlation of the pair distances of x and y, Pearson or
+ * Spearman (Pearson on average ranks, ties sharing the mean of their
+ * positions), and its two-sided permutation p-value.  Over the pairs i < j:
+ *   r = sum (x - mean x)(y - mean y) / sqrt(sum (x - mean x)^2 sum (y - mean y)^2);
+ * permutation pi gives r_pi with y(pi(i), pi(j)) in place of y(i, j);
+ *   p = (1 + #{m : |r_m| >= |r|}) / (n_perms + 1).
+ *
+ *   x, y       DEVICE pointers, full n x n matrices (unifrac_run with
+ *              UNIFRAC_OUT_FULL layout), float (UNIFRAC_MIXED) or double
+ *              (UNIFRAC_FP64), 16-byte aligned, not modified; only the strict
+ *              upper triangle of x is read, and y must be symmetric (whole
+ *              rows of y are read).  Values finite.
+ *   n          3 <= n <= UNIFRAC_MANTEL_MAX_SAMPLES
+ *   perms      HOST int32 [n_perms x n], row m a permutation of 0 .. n-1
+ *              (validated; the caller draws them, so results are reproducible
+ *              and comparable across implementations); NULL if n_perms == 0
+ *   method     enum unifrac_mantel_method
+ *   r          HOST double: the statistic (NaN if either matrix is constant)
+ *   perm_stats HOST double[n_perms] (may be NULL): r_m of each permutation
+ *   p_value    HOST double: the p-value (NaN if n_perms == 0 or r is NaN)
+ *   cuda_stream  stream for the device work (NULL = legacy default stream)
+ *
+ * Sums are FP64 (UNIFRAC_MIXED: FP32 products summed over at most
+ * ceil(n / 1024) pairs before FP64).  Rows of y are staged in shared memory
+ * (two buffers while 2 (n + 8) sizeof(T) <= 220 KB, else one, else y is
+ * gathered from global memory); the environment variable
+ * UNIFRAC_MANTEL_SMEM_BYTES lowers that 220 KB budget.  Allocates device memory while it runs:
+ * about 12 n_perms n bytes, plus for Spearman two rank matrices of the input
+ * type and about 16 n^2 bytes of sort buffers.  Synchronous.  Errors:
+ * UNIFRAC_E_INVALID_ARG (bad size, enum, pointer, alignment or permutation),
+ * UNIFRAC_E_OOM, UNIFRAC_E_CUDA.  No context needed.
+ */
+enum unifrac_mantel_method { UNIFRAC_MANTEL_PEARSON = 0, UNIFRAC_MANTEL_SPEARMAN = 1 };
+#define UNIFRAC_MANTEL_MAX_SAMPLES 92682 /* n (n - 1) / 2 < 2^32 */
+int unifrac_mantel(const void *x, const void *y, int precision, int32_t n, const int32_t *perms,
+                   int32_t n_perms, int method, double *r, double *perm_stats, double *p_value,
+                   void *cuda_stream);
 
 /* Statistics of the context / its last run. */
 enum unifrac_stat {

@@ -25,10 +25,12 @@ OUT_STRIPES = 0
 OUT_CONDENSED = 1
 OUT_FULL = 2
 
+MANTEL_PEARSON = 0
+MANTEL_SPEARMAN = 1
+MANTEL_MAX_SAMPLES = 92682
+
 OPT_UNWEIGHTED_MIXED_KERNEL = 0
 OPT_WEIGHTED_FLUSH = 1
-OPT_PERSISTENT = 2
-OPT_CTAS_PER_SM = 3
 OPT_USE_GRAPH = 4
 OPT_SPARSE_THRESHOLD = 5
 OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6
@@ -60,7 +62,7 @@ STAT_MAX_REACH = 21
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",
             "unifrac_set_option", "unifrac_get_option", "unifrac_get_stat",
-            "unifrac_autotune")
+            "unifrac_autotune", "unifrac_run_streamed", "unifrac_pcoa", "unifrac_mantel")
 
 
 class UniFracError(RuntimeError):
@@ -92,6 +94,14 @@ def load() -> ctypes.CDLL:
         lib.unifrac_run.argtypes = [vp, ctypes.c_int, ctypes.c_int, i32, i32, ctypes.c_int, vp,
                                     ctypes.c_size_t]
         lib.unifrac_run.restype = ctypes.c_int
+        lib.unifrac_run_streamed.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                             ctypes.c_size_t, i32]
+        lib.unifrac_run_streamed.restype = ctypes.c_int
+        lib.unifrac_pcoa.argtypes = [vp, ctypes.c_int, i32, i32, i32, ctypes.c_uint64, vp, vp, vp]
+        lib.unifrac_pcoa.restype = ctypes.c_int
+        lib.unifrac_mantel.argtypes = [vp, vp, ctypes.c_int, i32, vp, i32, ctypes.c_int, vp, vp,
+                                       vp, vp]
+        lib.unifrac_mantel.restype = ctypes.c_int
         lib.unifrac_destroy.argtypes = [vp]
         lib.unifrac_destroy.restype = None
         lib.unifrac_strerror.argtypes = [ctypes.c_int]
@@ -210,6 +220,70 @@ def unifrac_run(ctx, variant: int, precision: int, stripe_start: int, stripe_sto
                               ctypes.c_void_p(addr), cap), ctx)
 
 
+def unifrac_run_streamed(ctx, variant: int, precision: int, layout: int, out,
+                         chunk_stripes: int) -> None:
+    """The whole matrix into the HOST array `out` (numpy / CPU tensor), in
+    chunks of `chunk_stripes` stripes; returns when complete."""
+    addr, cap = _data_ptr(out)
+    _check(load().unifrac_run_streamed(ctx, variant, precision, layout, ctypes.c_void_p(addr),
+                                       cap, int(chunk_stripes)), ctx)
+
+
+def unifrac_pcoa(dist, k: int, iters: int = 12, seed: int = 0, stream=None):
+    """Principal coordinates of the full distance matrix `dist` (torch CUDA
+    tensor, n x n or n*n, float32 or float64): (eigenvalues [k], coordinates
+    [n, k]) as FP64 numpy arrays."""
+    import torch
+    if not (isinstance(dist, torch.Tensor) and dist.is_cuda and dist.is_contiguous()):
+        raise ValueError("dist must be a contiguous CUDA tensor")
+    if dist.dtype not in (torch.float32, torch.float64):
+        raise ValueError("dist must be float32 or float64")
+    n = int(round(dist.numel() ** 0.5))
+    if n * n != dist.numel():
+        raise ValueError("dist must hold n x n values")
+    precision = FP64 if dist.dtype == torch.float64 else MIXED
+    lam = np.zeros(k, np.float64)
+    coords = np.zeros((n, k), np.float64)
+    status = load().unifrac_pcoa(ctypes.c_void_p(dist.data_ptr()), precision, n, int(k),
+                                 int(iters), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                 lam.ctypes.data_as(ctypes.c_void_p),
+                                 coords.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream))
+    _check(status)
+    return lam, coords
+
+
+def unifrac_mantel(x, y, perms, method: str = "pearson", stream=None):
+    """Mantel test between the full distance matrices `x` and `y` (torch CUDA
+    tensors, n x n or n*n, both float32 or both float64) under the caller's
+    permutations `perms` (int array [M, n], each row a permutation of
+    0 .. n-1): (r, permuted statistics [M] as FP64 numpy, two-sided p)."""
+    import torch
+    for t in (x, y):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("x and y must be contiguous CUDA tensors")
+    if x.dtype != y.dtype or x.dtype not in (torch.float32, torch.float64):
+        raise ValueError("x and y must both be float32 or both float64")
+    n = int(round(x.numel() ** 0.5))
+    if n * n != x.numel() or y.numel() != x.numel():
+        raise ValueError("x and y must hold n x n values")
+    if method not in ("pearson", "spearman"):
+        raise ValueError("method must be 'pearson' or 'spearman'")
+    perms = (np.ascontiguousarray(perms, dtype=np.int32).reshape(-1, n) if n > 0
+             else np.zeros((0, 0), np.int32))
+    m = perms.shape[0]
+    stats = np.zeros(m, np.float64)
+    r, p = ctypes.c_double(), ctypes.c_double()
+    precision = FP64 if x.dtype == torch.float64 else MIXED
+    status = load().unifrac_mantel(
+        ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), precision, n,
+        perms.ctypes.data_as(ctypes.c_void_p) if m else None, m,
+        MANTEL_SPEARMAN if method == "spearman" else MANTEL_PEARSON,
+        ctypes.byref(r), stats.ctypes.data_as(ctypes.c_void_p), ctypes.byref(p),
+        _stream_handle(stream))
+    _check(status)
+    return float(r.value), stats, float(p.value)
+
+
 def unifrac_destroy(ctx) -> None:
     if ctx:
         load().unifrac_destroy(ctx)
@@ -272,6 +346,15 @@ class Context:
             dt = torch.float64 if precision == FP64 else torch.float32
             out = torch.zeros(nbytes // (8 if precision == FP64 else 4), dtype=dt, device=device)
         unifrac_run(self.handle, variant, precision, stripe_start, stripe_stop, layout, out)
+        return out
+
+    def run_streamed(self, variant, precision, layout, chunk_stripes, out=None):
+        """Host matrix computed in chunks of stripes (numpy array returned)."""
+        if out is None:
+            nbytes = self.output_bytes(precision, layout) * (2 if variant == BOTH else 1)
+            out = np.empty(nbytes // (8 if precision == FP64 else 4),
+                           np.float64 if precision == FP64 else np.float32)
+        unifrac_run_streamed(self.handle, variant, precision, layout, out, chunk_stripes)
         return out
 
     def set_option(self, option, value) -> None:

@@ -124,8 +124,8 @@ void free_ctx(unifrac_ctx *ctx) {
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  ufb::DevBuf *bufs[] = {&ctx->cnt, &ctx->flag, &ctx->items, &ctx->studies, &ctx->stage,
-                         &ctx->tables};
+  ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
+                         &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1]};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &V : ctx->vb) {
@@ -135,6 +135,12 @@ void free_ctx(unifrac_ctx *ctx) {
       if (b->p) cudaFree(b->p);
   }
   if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->ev_chunk_done[b]) cudaEventDestroy(ctx->ev_chunk_done[b]);
+    if (ctx->ev_chunk_copied[b]) cudaEventDestroy(ctx->ev_chunk_copied[b]);
+    if (ctx->chunk_host[b]) cudaFreeHost(ctx->chunk_host[b]);
+  }
   if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
   if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   for (auto &e : ctx->ev)
@@ -811,8 +817,18 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
     const int32_t n = ctx->study_off[s + 1] - ctx->study_off[s];
     studies[s] = StudyDev{off, n, ctx->study_col0[s]};
     off += n_pairs_layout(layout, n, s0, s1);
-    study_items(s, n, ctx->study_col0[s] / TILE, layout, s0, s1, items);
   }
+  // items of the largest studies first (their tile pairs are full, the small
+  // studies' partial ones fill the last wave); outputs are placed by study,
+  // so the order changes nothing else
+  std::vector<int32_t> order(ctx->n_studies);
+  for (int32_t s = 0; s < ctx->n_studies; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return ctx->study_off[a + 1] - ctx->study_off[a] > ctx->study_off[b + 1] - ctx->study_off[b];
+  });
+  for (int32_t s : order)
+    study_items(s, ctx->study_off[s + 1] - ctx->study_off[s], ctx->study_col0[s] / TILE, layout,
+                s0, s1, items);
   int rc;
   if ((rc = grow(ctx, ctx->items, items.size() * sizeof(WorkItem)))) return rc;
   if ((rc = grow(ctx, ctx->studies, studies.size() * sizeof(StudyDev)))) return rc;
@@ -1271,14 +1287,6 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < 16 || value > 4096) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_flush = (int)value;
       return UNIFRAC_OK;
-    case UNIFRAC_OPT_PERSISTENT:
-      if (value < -1 || value > 1) return UNIFRAC_E_INVALID_ARG;
-      ctx->opt_persistent = (int)value;
-      return UNIFRAC_OK;
-    case UNIFRAC_OPT_CTAS_PER_SM:
-      if (value < 1 || value > 8) return UNIFRAC_E_INVALID_ARG;
-      ctx->opt_ctas_per_sm = (int)value;
-      return UNIFRAC_OK;
     case UNIFRAC_OPT_USE_GRAPH:
       if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_use_graph = (int)value;
@@ -1305,8 +1313,6 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
   switch (option) {
     case UNIFRAC_OPT_UNWEIGHTED_MIXED_KERNEL: *value = ctx->opt_uw_kernel; return UNIFRAC_OK;
     case UNIFRAC_OPT_WEIGHTED_FLUSH: *value = ctx->opt_flush; return UNIFRAC_OK;
-    case UNIFRAC_OPT_PERSISTENT: *value = ctx->opt_persistent; return UNIFRAC_OK;
-    case UNIFRAC_OPT_CTAS_PER_SM: *value = ctx->opt_ctas_per_sm; return UNIFRAC_OK;
     case UNIFRAC_OPT_USE_GRAPH: *value = ctx->opt_use_graph; return UNIFRAC_OK;
     case UNIFRAC_OPT_OVERLAP_VARIANTS: *value = ctx->opt_overlap; return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
@@ -1314,6 +1320,161 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
       *value = ctx->opt_uw_sparse_threshold;
       return UNIFRAC_OK;
     default: return UNIFRAC_E_INVALID_ARG;
+  }
+}
+
+// Streamed output: stripes [s0, s1) per chunk into one of two device buffers
+// (the kernels of the next chunk overlap the copy of this one on a copy
+// stream), copied to pinned host memory and merged into the caller's
+// condensed or full matrix by host threads while the GPU computes on.
+static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int layout,
+                             void *host_out, size_t out_bytes, int32_t chunk_stripes) {
+  if (!host_out || chunk_stripes < 1) return fail(ctx, UNIFRAC_E_INVALID_ARG, "output / chunk");
+  if (variant < UNIFRAC_UNWEIGHTED || variant > UNIFRAC_BOTH)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "variant");
+  if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "precision");
+  if (layout != UNIFRAC_OUT_CONDENSED && layout != UNIFRAC_OUT_FULL)
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "streamed output is condensed or full");
+  if (ctx->n_studies != 1)
+    return fail(ctx, UNIFRAC_E_UNSUPPORTED, "streamed output needs a single study");
+  {  // host threads write the result: it must be host memory
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, host_out) == cudaSuccess &&
+        attr.type == cudaMemoryTypeDevice)
+      return fail(ctx, UNIFRAC_E_INVALID_ARG, "streamed output must be host memory");
+    cudaGetLastError();
+  }
+  const int nv = variant == UNIFRAC_BOTH ? 2 : 1;
+  const int64_t n = ctx->n_samples;
+  const size_t elem = precision == UNIFRAC_FP64 ? 8 : 4;
+  const int64_t per_matrix = n_pairs_layout(layout, n, 0, 0);
+  if (out_bytes < (size_t)(per_matrix * nv) * elem)
+    return fail(ctx, UNIFRAC_E_BUFFER_TOO_SMALL, "output buffer");
+  if (layout == UNIFRAC_OUT_FULL)  // the zero diagonal (stripes hold no i == i pairs)
+    for (int v = 0; v < nv; ++v)
+      for (int64_t i = 0; i < n; ++i) {
+        if (elem == 8)
+          static_cast<double *>(host_out)[v * per_matrix + i * n + i] = 0.0;
+        else
+          static_cast<float *>(host_out)[v * per_matrix + i * n + i] = 0.f;
+      }
+  const int32_t nst = (int32_t)(n / 2);
+  if (nst == 0) return UNIFRAC_OK;
+  const int32_t chunk = std::min(chunk_stripes, nst);
+  const size_t chunk_bytes = (size_t)chunk * n * elem * nv;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->copy_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&ctx->ev_chunk_done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_chunk_copied[b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+  }
+  int rc;
+  for (int b = 0; b < 2; ++b)
+    if ((rc = grow(ctx, ctx->chunk_dev[b], chunk_bytes))) return rc;
+  if (ctx->chunk_host_bytes < chunk_bytes) {
+    for (int b = 0; b < 2; ++b) {
+      if (ctx->chunk_host[b]) cudaFreeHost(ctx->chunk_host[b]);
+      ctx->chunk_host[b] = nullptr;
+    }
+    ctx->chunk_host_bytes = 0;
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMallocHost(&ctx->chunk_host[b], chunk_bytes);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "pinned host buffer");
+    }
+    ctx->chunk_host_bytes = chunk_bytes;
+  }
+  // merge stripes [s0, s0 + rows) of chunk buffer b into the output
+  auto merge = [&](int b, int32_t s0, int32_t rows) {
+    const int T = host_threads((int64_t)rows * n);
+    run_threads(T, [&](int t) {
+      for (int v = 0; v < nv; ++v)
+        for (int32_t r = (int32_t)((int64_t)rows * t / T); r < (int32_t)((int64_t)rows * (t + 1) / T);
+             ++r) {
+          const int64_t s = s0 + r, base_in = ((int64_t)v * rows + r) * n;
+          for (int64_t k = 0; k < n; ++k) {
+            const int64_t j = (k + s + 1) % n, lo = std::min(k, j), hi = std::max(k, j);
+            if (layout == UNIFRAC_OUT_CONDENSED) {
+              const int64_t idx = v * per_matrix + lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
+              if (elem == 8)
+                static_cast<double *>(host_out)[idx] = static_cast<const double *>(ctx->chunk_host[b])[base_in + k];
+              else
+                static_cast<float *>(host_out)[idx] = static_cast<const float *>(ctx->chunk_host[b])[base_in + k];
+            } else {
+              const int64_t i1 = v * per_matrix + lo * n + hi, i2 = v * per_matrix + hi * n + lo;
+              if (elem == 8) {
+                const double x = static_cast<const double *>(ctx->chunk_host[b])[base_in + k];
+                static_cast<double *>(host_out)[i1] = x;
+                static_cast<double *>(host_out)[i2] = x;
+              } else {
+                const float x = static_cast<const float *>(ctx->chunk_host[b])[base_in + k];
+                static_cast<float *>(host_out)[i1] = x;
+                static_cast<float *>(host_out)[i2] = x;
+              }
+            }
+          }
+        }
+    });
+  };
+  const int saved_graph = ctx->opt_use_graph;
+  ctx->opt_use_graph = 0;  // every chunk has its own stripe range
+  const int32_t n_chunks = (nst + chunk - 1) / chunk;
+  rc = UNIFRAC_OK;
+  for (int32_t c = 0; c <= n_chunks && rc == UNIFRAC_OK; ++c) {
+    if (c < n_chunks) {
+      const int b = c & 1;
+      const int32_t s0 = c * chunk, s1 = std::min(nst, s0 + chunk);
+      const size_t bytes = (size_t)(s1 - s0) * n * elem * nv;
+      if (c >= 2 && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk_copied[b], 0)) != cudaSuccess) {
+        rc = cuda_fail(ctx, e, "chunk order");
+        break;
+      }
+      if ((rc = run_impl(ctx, variant, precision, s0, s1, UNIFRAC_OUT_STRIPES, ctx->chunk_dev[b].p,
+                         bytes)))
+        break;
+      e = cudaEventRecord(ctx->ev_chunk_done[b], ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_chunk_done[b], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->chunk_host[b], ctx->chunk_dev[b].p, bytes, cudaMemcpyDeviceToHost,
+                            ctx->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_chunk_copied[b], ctx->copy_stream);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(ctx, e, "chunk copy");
+        break;
+      }
+    }
+    if (c >= 1) {  // merge the previous chunk while this one computes
+      const int pb = (c - 1) & 1;
+      if ((e = cudaEventSynchronize(ctx->ev_chunk_copied[pb])) != cudaSuccess) {
+        rc = cuda_fail(ctx, e, "chunk wait");
+        break;
+      }
+      const int32_t p0 = (c - 1) * chunk;
+      merge(pb, p0, std::min(nst, p0 + chunk) - p0);
+    }
+  }
+  if (rc) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->stream);
+  }
+  ctx->opt_use_graph = saved_graph;
+  return rc;
+}
+
+int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layout,
+                         void *host_out, size_t out_bytes, int32_t chunk_stripes) {
+  if (!ctx) return UNIFRAC_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, UNIFRAC_E_CUDA, "cannot select the context's device");
+  try {
+    return run_streamed_impl(ctx, variant, precision, layout, host_out, out_bytes, chunk_stripes);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, UNIFRAC_E_OOM, "host allocation");
+  } catch (...) {
+    return fail(ctx, UNIFRAC_E_INVALID_ARG, "unexpected failure");
   }
 }
 

@@ -126,8 +126,6 @@ struct unifrac_ctx {
   int opt_flush = 256;
   double create_host_ms = 0.0;        // unifrac_create: validation and host preparation
   double create_device_ms = 0.0;      // unifrac_create: device set-up and uploads
-  int opt_persistent = -1;  // -1 auto
-  int opt_ctas_per_sm = 1;
   int opt_use_graph = 0;
   int opt_overlap = 1;                // both variants of one call on two streams
   int64_t opt_sparse_threshold = -1;  // presence count below which a branch runs sparse
@@ -146,6 +144,12 @@ struct unifrac_ctx {
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   int cur_slot = 0;                   // variant slot being enqueued
+  // unifrac_run_streamed: copy stream, its events, and the chunk buffers
+  // (two on the device, two pinned on the host), kept between calls
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_chunk_done[2] = {nullptr, nullptr}, ev_chunk_copied[2] = {nullptr, nullptr};
+  void *chunk_host[2] = {nullptr, nullptr};
+  size_t chunk_host_bytes = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int gk_variant = -1, gk_precision = -1, gk_layout = -1;
   int32_t gk_s0 = 0, gk_s1 = 0;
@@ -155,7 +159,7 @@ struct unifrac_ctx {
   bool capturing = false;
 
   // ---- work buffers (grown on demand)
-  ufb::DevBuf cnt, flag, items, studies, stage, tables;
+  ufb::DevBuf cnt, flag, items, studies, stage, tables, chunk_dev[2];
   ufb::VarBufs vb[2];
   size_t device_bytes = 0;
 };

@@ -103,3 +103,40 @@ def test_null_pointers_rejected():
     v = ctypes.c_double()
     assert lib.unifrac_get_stat(None, 0, ctypes.byref(v)) == -1
     assert lib.unifrac_set_option(None, 0, 0) == -1
+
+
+def test_binding_constants_match_header_enums():
+    """Every enumerator of include/unifrac_b300.h has the same value in the
+    binding (options, statistics, status codes, variants, precisions,
+    layouts), and the binding defines no constant the header lacks."""
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include",
+                             "unifrac_b300.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    header = {}
+    for body in re.findall(r"enum\s+\w*\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(UNIFRAC_\w+)\s*=\s*(-?\d+)", body):
+            header[name] = int(val)
+    prefix = {"OPT_": "UNIFRAC_OPT_", "STAT_": "UNIFRAC_STAT_"}
+    checked = 0
+    for attr in dir(ub):
+        for p, hp in prefix.items():
+            if attr.startswith(p):
+                assert hp + attr[len(p):] in header, attr
+                assert getattr(ub, attr) == header[hp + attr[len(p):]], attr
+                checked += 1
+    for name, val in header.items():
+        for hp, p in (("UNIFRAC_OPT_", "OPT_"), ("UNIFRAC_STAT_", "STAT_")):
+            if name.startswith(hp):
+                assert getattr(ub, p + name[len(hp):]) == val, name
+    assert header["UNIFRAC_UNWEIGHTED"] == ub.UNWEIGHTED
+    assert header["UNIFRAC_WEIGHTED_NORMALIZED"] == ub.WEIGHTED_NORMALIZED
+    assert header["UNIFRAC_BOTH"] == ub.BOTH
+    assert header["UNIFRAC_FP64"] == ub.FP64 and header["UNIFRAC_MIXED"] == ub.MIXED
+    assert header["UNIFRAC_MANTEL_PEARSON"] == ub.MANTEL_PEARSON
+    assert header["UNIFRAC_MANTEL_SPEARMAN"] == ub.MANTEL_SPEARMAN
+    m = re.search(r"#define\s+UNIFRAC_MANTEL_MAX_SAMPLES\s+(\d+)", text)
+    assert m and int(m.group(1)) == ub.MANTEL_MAX_SAMPLES
+    n = ub.MANTEL_MAX_SAMPLES
+    assert n * (n - 1) // 2 < 2**32 <= (n + 1) * n // 2  # largest n whose pair indices fit 32 bits
+    assert checked >= 25

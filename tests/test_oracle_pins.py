@@ -368,3 +368,116 @@ def test_root_branch_length_is_ignored(variant):
     t2 = synth.Tree(parent=tree.parent, length=tree.length.copy())
     t2.length[-1] = 5.0
     np.testing.assert_array_equal(oracle.unifrac_full(t2, table, variant), d1)
+
+
+# ------------------------------------------------------------------ PCoA oracle
+
+def test_pcoa_recovers_planar_configuration():
+    """Classical MDS recovers points in the plane up to a rigid motion: the
+    coordinates reproduce the distances, the two non-zero eigenvalues are the
+    squared singular values of the centred points, the rest vanish."""
+    from oracle import pcoa
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(40, 2)) * np.array([3.0, 1.0])
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    lam, C = pcoa.pcoa(D, 5)
+    Dc = np.sqrt(((C[:, None, :2] - C[None, :, :2]) ** 2).sum(-1))
+    np.testing.assert_allclose(Dc, D, atol=1e-10)
+    Xc = X - X.mean(axis=0)
+    sv = np.linalg.svd(Xc, compute_uv=False)
+    np.testing.assert_allclose(lam[:2], sv ** 2, rtol=1e-10)
+    assert np.all(np.abs(lam[2:]) < 1e-9)
+
+
+def test_pcoa_eigenvalues_sum_to_trace():
+    """sum of all eigenvalues = trace(B) = (1/n) sum_{i<j} d_ij^2."""
+    from oracle import pcoa
+    rng = np.random.default_rng(4)
+    n = 25
+    M = rng.random((n, n))
+    D = M + M.T
+    np.fill_diagonal(D, 0.0)
+    lam, _ = pcoa.pcoa(D, n)
+    iu = np.triu_indices(n, 1)
+    np.testing.assert_allclose(lam.sum(), (D[iu] ** 2).sum() / n, rtol=1e-10)
+
+
+def test_pcoa_centring_matches_sums():
+    """The double centring equals A - row means - column means + grand mean."""
+    from oracle import pcoa
+    rng = np.random.default_rng(6)
+    n = 17
+    M = rng.random((n, n))
+    D = M + M.T
+    np.fill_diagonal(D, 0.0)
+    A = -0.5 * D ** 2
+    r = A.mean(axis=1)
+    want = A - r[:, None] - r[None, :] + A.mean()
+    np.testing.assert_allclose(pcoa.double_centred(D), want, atol=1e-12)
+
+
+# ------------------------------------------------------------------ Mantel oracle
+
+def test_mantel_statistics_match_scipy():
+    from scipy import stats as sst
+    from oracle import mantel as om
+    rng = np.random.default_rng(11)
+    x = rng.random(300)
+    y = 0.5 * x + rng.random(300)
+    np.testing.assert_allclose(om.pearson(x, y), sst.pearsonr(x, y)[0], rtol=1e-12)
+    yt = np.round(y * 5) / 5  # ties
+    r_s = om.pearson(om.average_ranks(x), om.average_ranks(yt))
+    np.testing.assert_allclose(r_s, sst.spearmanr(x, yt)[0], rtol=1e-12)
+
+
+def test_mantel_permutation_matches_full_matrix():
+    """Relabelling the samples of the condensed vector equals permuting the
+    rows and columns of the full matrix; the identity changes nothing."""
+    from scipy.spatial.distance import squareform
+    from oracle import mantel as om
+    rng = np.random.default_rng(12)
+    n = 9
+    y = rng.random(n * (n - 1) // 2)
+    perm = rng.permutation(n)
+    Y = squareform(y)
+    np.testing.assert_array_equal(om.permute_condensed(y, perm, n),
+                                  squareform(Y[np.ix_(perm, perm)], checks=False))
+    np.testing.assert_array_equal(om.permute_condensed(y, np.arange(n), n), y)
+
+
+def test_mantel_exhaustive_small_case():
+    """n = 4 with all 24 relabellings: y is x relabelled by a known
+    permutation, so exactly the permutations giving back x reach r = 1."""
+    import itertools
+    from oracle import mantel as om
+    rng = np.random.default_rng(13)
+    n = 4
+    x = rng.random(6)
+    sigma = np.array([2, 0, 3, 1])
+    y = om.permute_condensed(x, sigma, n)
+    perms = np.array(list(itertools.permutations(range(n))))
+    r, stats, p = om.mantel(x, y, n, perms)
+    hits = [q for q, s in zip(perms, stats) if abs(s - 1.0) < 1e-12]
+    for q in hits:  # relabelling y by q gives x back
+        np.testing.assert_allclose(om.permute_condensed(y, q, n), x)
+    assert len(hits) >= 1
+    assert 0.0 < p <= 1.0
+
+
+def test_mantel_undefined_cases():
+    """A constant matrix has no correlation (r, r_m and p NaN); without
+    permutations there is no null distribution (p NaN, r still defined); the
+    p-value counts the identity as one of the M + 1 relabellings."""
+    from oracle import mantel as om
+    rng = np.random.default_rng(14)
+    n = 6
+    x = rng.random(15)
+    perms = np.array([rng.permutation(n) for _ in range(5)])
+    r, stats, p = om.mantel(x, np.full(15, 0.5), n, perms)
+    assert np.isnan(r) and np.isnan(p) and np.isnan(stats).all()
+    r, stats, p = om.mantel(x, x, n, perms[:0])
+    assert r == pytest.approx(1.0, abs=1e-15) and np.isnan(p) and stats.shape == (0,)
+    # y = x: each r_m is at most 1 = r, and the identity relabelling reaches it
+    ident = np.tile(np.arange(n), (3, 1))
+    r, stats, p = om.mantel(x, x, n, ident)
+    assert p == 1.0 and np.allclose(stats, 1.0)

@@ -530,3 +530,265 @@ def test_create_statistics_large_tree_exact_reach():
         assert ctx.stat(ub.STAT_USEFUL) == us
         assert ctx.stat(ub.STAT_BRANCHES_KEPT) == kept
         assert ctx.stat(ub.STAT_MAX_REACH) == reach
+
+
+# ------------------------------------------------------------------ streamed output
+
+@pytest.mark.parametrize("n", [256, 255])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_streamed_output_equals_direct(small, n, precision):
+    """unifrac_run_streamed (chunks of 7 stripes, and one chunk) gives the
+    matrices of unifrac_run, both layouts, every variant; odd and even N."""
+    import torch
+    w, _ = small
+    table = synth.dense_to_table(w.table.dense()[:, :n], w.table.feature_node) \
+        if n != w.table.n_samples else w.table
+    with ub.Context(w.tree, table) as ctx:
+        for layout in (ub.OUT_CONDENSED, ub.OUT_FULL):
+            for variant in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED, ub.BOTH):
+                direct = ctx.run(variant, precision, layout)
+                torch.cuda.synchronize()
+                direct = direct.cpu().numpy()
+                for chunk in (7, 10_000):
+                    got = ctx.run_streamed(variant, precision, layout, chunk)
+                    np.testing.assert_array_equal(got, direct)
+        assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
+
+
+def test_streamed_output_rejects_bad_calls(small):
+    import torch
+    w, _ = small
+    with ub.Context(w.tree, w.table) as ctx:
+        with pytest.raises(ub.UniFracError):
+            ctx.run_streamed(ub.UNWEIGHTED, ub.MIXED, ub.OUT_STRIPES, 4)
+        with pytest.raises(ub.UniFracError):
+            ctx.run_streamed(ub.UNWEIGHTED, ub.MIXED, ub.OUT_CONDENSED, 0)
+        dev = torch.zeros(w.table.n_samples ** 2, dtype=torch.float32, device="cuda")
+        with pytest.raises(ub.UniFracError):  # device memory
+            ctx.run_streamed(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL, 4, out=dev)
+        small_out = np.zeros(10, np.float32)
+        with pytest.raises(ub.UniFracError):
+            ctx.run_streamed(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL, 4, out=small_out)
+    rng = np.random.default_rng(5)
+    tree = synth.yule_tree(60, rng, 0.1)
+    dense = (rng.random((60, 20)) < 0.3) * rng.integers(1, 9, (60, 20))
+    table = synth.dense_to_table(dense, tree.tips())
+    table.study_offsets = np.array([0, 9, 20], np.int32)
+    with ub.Context(tree, table) as ctx:
+        with pytest.raises(ub.UniFracError):  # several studies
+            ctx.run_streamed(ub.UNWEIGHTED, ub.MIXED, ub.OUT_CONDENSED, 4)
+
+
+# ------------------------------------------------------------------ PCoA
+
+def test_pcoa_recovers_planar_configuration_on_gpu():
+    """Distances of points in the plane: two eigenvalues (the squared
+    singular values of the centred points), the rest ~0, and the first two
+    coordinates reproduce the distances."""
+    import torch
+    from oracle import pcoa as opc
+    rng = np.random.default_rng(8)
+    X = rng.normal(size=(300, 2)) * np.array([2.0, 0.7])
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    lam, C = ub.unifrac_pcoa(torch.from_numpy(D).cuda(), k=4, iters=8, seed=1)
+    sv2 = np.linalg.svd(X - X.mean(axis=0), compute_uv=False) ** 2
+    np.testing.assert_allclose(lam[:2], sv2, rtol=1e-5)
+    assert np.all(np.abs(lam[2:]) <= 1e-5 * lam[0])
+    Dc = np.sqrt(((C[:, None, :2] - C[None, :, :2]) ** 2).sum(-1))
+    np.testing.assert_allclose(Dc, D, atol=1e-4 * D.max())
+    lam_o, _ = opc.pcoa(D, 4)
+    np.testing.assert_allclose(lam[:2], lam_o[:2], rtol=1e-5)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pcoa_of_unifrac_matrix_matches_oracle(small, variant):
+    """PCoA of the GPU UniFrac matrix (FP32, full layout) against the FP64
+    oracle ordination of the same matrix: leading eigenvalues, and the
+    coordinates of well-separated components up to sign."""
+    import torch
+    from oracle import pcoa as opc
+    w, _ = small
+    n = w.table.n_samples
+    with ub.Context(w.tree, w.table) as ctx:
+        D = ctx.run(variant, ub.MIXED, ub.OUT_FULL)
+        torch.cuda.synchronize()
+        k = 6
+        lam, C = ub.unifrac_pcoa(D, k=k, iters=16, seed=7)
+        lam2, C2 = ub.unifrac_pcoa(D, k=k, iters=16, seed=7)
+    np.testing.assert_array_equal(lam, lam2)  # reproducible from the seed
+    np.testing.assert_array_equal(C, C2)
+    Dn = D.cpu().numpy().astype(np.float64).reshape(n, n)
+    lam_o, C_o = opc.pcoa(Dn, k + 1)
+    np.testing.assert_allclose(lam, lam_o[:k], rtol=2e-4, atol=1e-6 * lam_o[0])
+    for c in range(k):
+        gap = min(abs(lam_o[c] - lam_o[c + 1]), abs(lam_o[c] - lam_o[c - 1]) if c else np.inf)
+        if gap < 0.05 * lam_o[c]:
+            continue  # nearly degenerate: the axis itself is not determined
+        sgn = np.sign(np.dot(C[:, c], C_o[:, c])) or 1.0
+        np.testing.assert_allclose(sgn * C[:, c], C_o[:, c], atol=2e-3 * np.abs(C_o[:, c]).max())
+
+
+def test_pcoa_rejects_bad_arguments():
+    import torch
+    D = torch.zeros(16, dtype=torch.float32, device="cuda")
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_pcoa(D, k=5)  # k > n
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_pcoa(D, k=2, iters=-1)
+    with pytest.raises(ValueError):
+        ub.unifrac_pcoa(D.cpu(), k=2)
+
+
+# ------------------------------------------------------------------ Mantel test
+
+MANTEL_TOL = {ub.FP64: 1e-12, ub.MIXED: 2e-6}
+
+
+def _mantel_perms(n, m, seed):
+    rng = np.random.default_rng(seed)
+    return np.array([rng.permutation(n) for _ in range(m)], dtype=np.int32).reshape(m, n)
+
+
+def _point_matrices(n, seed, dtype):
+    """Two correlated Euclidean distance matrices of random points (full n x n)."""
+    import scipy.spatial.distance as ssd
+    rng = np.random.default_rng(seed)
+    a = rng.random((n, 3))
+    b = a + 0.3 * rng.random((n, 3))
+    return ssd.cdist(a, a).astype(dtype), ssd.cdist(b, b).astype(dtype)
+
+
+def _check_mantel(got, want, tol):
+    r, stats, p = got
+    r_o, stats_o, p_o = want
+    if np.isnan(r_o):
+        assert np.isnan(r) and np.isnan(p) and np.isnan(stats).all()
+        return
+    assert abs(r - r_o) <= tol, (r, r_o)
+    np.testing.assert_allclose(stats, stats_o, rtol=0, atol=tol)
+    if np.isnan(p_o):
+        assert np.isnan(p)
+    elif not np.any(np.abs(np.abs(stats_o) - abs(r_o)) <= 2 * tol):
+        assert p == p_o  # same decisions unless a statistic ties |r| within rounding
+
+
+def _mantel_oracle(X, Y, perms, method):
+    from oracle import mantel as om
+    n = X.shape[0]
+    iu = np.triu_indices(n, 1)
+    return om.mantel(X.astype(np.float64)[iu], Y.astype(np.float64)[iu], n, perms, method)
+
+
+@pytest.mark.parametrize("method", ["pearson", "spearman"])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mantel_unifrac_matrices_match_oracle(small, method, precision):
+    """Unweighted against weighted UniFrac of the same samples (the paper's
+    use: do two distance matrices of one set of samples agree?), 99
+    permutations, against the FP64 oracle on the same matrices."""
+    import torch
+    w, _ = small
+    n = w.table.n_samples
+    with ub.Context(w.tree, w.table) as ctx:
+        X = ctx.run(ub.UNWEIGHTED, precision, ub.OUT_FULL)
+        Y = ctx.run(ub.WEIGHTED_NORMALIZED, precision, ub.OUT_FULL)
+    torch.cuda.synchronize()
+    perms = _mantel_perms(n, 99, 21)
+    got = ub.unifrac_mantel(X, Y, perms, method)
+    again = ub.unifrac_mantel(X, Y, perms, method)
+    assert got[0] == again[0] and got[2] == again[2]  # deterministic
+    np.testing.assert_array_equal(got[1], again[1])
+    Xn = X.cpu().numpy().reshape(n, n)
+    Yn = Y.cpu().numpy().reshape(n, n)
+    _check_mantel(got, _mantel_oracle(Xn, Yn, perms, method), MANTEL_TOL[precision])
+    assert got[0] > 0.2  # the two UniFrac variants agree on these samples
+
+
+@pytest.mark.parametrize("budget", [None, "3000", "0"])
+@pytest.mark.parametrize("n", [3, 5, 37, 301])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mantel_staging_paths_and_ragged_sizes(n, budget, precision, monkeypatch):
+    """Every way of reading y (two shared-memory buffers, one, none) at sizes
+    whose rows start off the 16-byte grid, Pearson and Spearman."""
+    import torch
+    if budget is not None:
+        monkeypatch.setenv("UNIFRAC_MANTEL_SMEM_BYTES", budget)
+    dt = np.float64 if precision == ub.FP64 else np.float32
+    X, Y = _point_matrices(n, 30 + n, dt)
+    perms = _mantel_perms(n, 21, 31 + n)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    for method in ("pearson", "spearman"):
+        got = ub.unifrac_mantel(Xd, Yd, perms, method)
+        _check_mantel(got, _mantel_oracle(X, Y, perms, method), MANTEL_TOL[precision])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mantel_spearman_heavy_ties(precision):
+    """Distances rounded to one decimal: long runs of equal values, whose
+    members share the mean rank."""
+    import torch
+    dt = np.float64 if precision == ub.FP64 else np.float32
+    X, Y = _point_matrices(400, 41, np.float64)
+    X, Y = np.round(X, 1).astype(dt), np.round(Y, 1).astype(dt)
+    perms = _mantel_perms(400, 15, 42)
+    got = ub.unifrac_mantel(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), perms,
+                            "spearman")
+    _check_mantel(got, _mantel_oracle(X, Y, perms, "spearman"), MANTEL_TOL[precision])
+
+
+def test_mantel_degenerate_cases():
+    """Constant matrix (no correlation: NaN), no permutations (p NaN), y = x
+    with identity relabellings (r = 1, p = 1), all six relabellings of n = 3."""
+    import itertools
+    import torch
+    X, _ = _point_matrices(24, 50, np.float64)
+    Xd = torch.from_numpy(X).cuda()
+    C = torch.full((24, 24), 0.5, dtype=torch.float64, device="cuda")
+    perms = _mantel_perms(24, 5, 51)
+    _check_mantel(ub.unifrac_mantel(Xd, C, perms), _mantel_oracle(X, C.cpu().numpy(), perms,
+                                                                   "pearson"), 1e-12)
+    r, stats, p = ub.unifrac_mantel(Xd, Xd, perms[:0])
+    assert abs(r - 1.0) <= 1e-12 and np.isnan(p) and stats.shape == (0,)
+    ident = np.tile(np.arange(24, dtype=np.int32), (4, 1))
+    r, stats, p = ub.unifrac_mantel(Xd, Xd, ident)
+    assert p == 1.0 and np.allclose(stats, 1.0, atol=1e-12)
+    X3, Y3 = _point_matrices(3, 52, np.float64)
+    all3 = np.array(list(itertools.permutations(range(3))), dtype=np.int32)
+    for method in ("pearson", "spearman"):
+        got = ub.unifrac_mantel(torch.from_numpy(X3).cuda(), torch.from_numpy(Y3).cuda(), all3,
+                                method)
+        _check_mantel(got, _mantel_oracle(X3, Y3, all3, method), 1e-12)
+
+
+def test_mantel_rejects_bad_arguments():
+    import torch
+    X, Y = _point_matrices(10, 60, np.float32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    good = _mantel_perms(10, 3, 61)
+    bad = good.copy()
+    bad[1, 0] = bad[1, 1]  # not a permutation
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_mantel(Xd, Yd, bad)
+    out_of_range = good.copy()
+    out_of_range[2, 4] = 10
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_mantel(Xd, Yd, out_of_range)
+    two = torch.zeros((2, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_mantel(two, two, np.zeros((1, 2), np.int32))  # n < 3
+    with pytest.raises(ValueError):
+        ub.unifrac_mantel(Xd, Yd.double(), good)  # mixed dtypes
+    with pytest.raises(ValueError):
+        ub.unifrac_mantel(Xd.cpu(), Yd.cpu(), good)  # host tensors
+    with pytest.raises(ValueError):
+        ub.unifrac_mantel(Xd, Yd, good, method="kendall")
+
+
+def test_mantel_large_matrices_sampled_permutations():
+    """n = 12,000 (72 M pairs, rows of y staged in two 48 KB buffers): the
+    statistic and two permuted statistics against the oracle."""
+    import torch
+    n = 12000
+    X, Y = _point_matrices(n, 70, np.float32)
+    perms = _mantel_perms(n, 2, 71)
+    got = ub.unifrac_mantel(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), perms)
+    _check_mantel(got, _mantel_oracle(X, Y, perms, "pearson"), MANTEL_TOL[ub.MIXED])
