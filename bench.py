@@ -52,6 +52,8 @@ def parse():
                     help="stripes per chunk of the streamed-output measurement")
     ap.add_argument("--mantel-perms", type=int, default=999,
                     help="permutations of the Mantel-test measurement (0 = skip it)")
+    ap.add_argument("--mantel-only", action="store_true",
+                    help="run only the Mantel-test measurement on the workload (profiling)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="run the two variants one after the other in the headline loop")
     ap.add_argument("--sparse-fraction", type=float, default=None,
@@ -304,6 +306,65 @@ def reference_arm(args):
     return 0
 
 
+def mantel_leg(args, w, stream, tuned_opts, peaks):
+    """The Mantel test (Pearson and Spearman, args.mantel_perms permutations)
+    between the unweighted and weighted matrices of workload `w` (full
+    layout, FP32): the downstream comparison of two distance matrices.
+    Wall time of the synchronous calls; roofline of the whole Pearson call
+    against the HBM peak."""
+    import torch
+    from paper_2107_05397_b300 import binding as ub
+    N = w.table.n_samples
+    with ub.Context(w.tree, w.table, stream=stream) as mctx:
+        for k_, v_ in tuned_opts.items():
+            mctx.set_option(k_, v_)
+        Xu = mctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL)
+        Xw = mctx.run(ub.WEIGHTED_NORMALIZED, ub.MIXED, ub.OUT_FULL)
+        torch.cuda.synchronize()
+    m_perm = args.mantel_perms
+    perms = np.random.default_rng(5).permuted(
+        np.tile(np.arange(N, dtype=np.int32), (m_perm, 1)), axis=1)
+    mres = {}
+    for method in ("pearson", "spearman"):
+        ub.unifrac_mantel(Xu, Xw, perms[:8], method)  # warm-up
+        tm_ = []
+        for rep in range(2):
+            t0 = time.perf_counter()
+            r_m, _, p_m = ub.unifrac_mantel(Xu, Xw, perms, method)
+            tm_.append(time.perf_counter() - t0)
+        mres[method] = {"s_per_call": float(np.median(tm_)), "r": r_m, "p": p_m}
+    P_ = N * (N - 1) // 2
+    # per permutation every pair of x is read once (HBM); rows of y are staged
+    # once per batch of 16 permutations and are not counted
+    alg = (m_perm + 1) * P_ * 4.0
+    t_pear = mres["pearson"]["s_per_call"]
+    hbm = (peaks or {}).get("hbm_gbs") or 6400.0
+    ach = alg / t_pear / 1e9
+    out = {"n": N, "permutations": m_perm, **mres,
+           "roofline": {"kernel": "k_mantel_cross", "bound": "hbm", "achieved": ach, "peak": hbm,
+                        "unit": "GB/s", "frac": ach / hbm,
+                        "work": "every pair of x once per permutation (4 bytes x P pairs)",
+                        "timed": "whole synchronous Pearson call (moments, permutation "
+                                 "upload, cross sums, reduction)"}}
+    if not args.no_cpu_baseline:
+        from oracle import mantel as om
+        n_c, m_c = min(1500, N), 4
+        rng_c = np.random.default_rng(6)
+        iu = np.triu_indices(n_c, 1)
+        xc = Xu.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
+        yc = Xw.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
+        pc = np.array([rng_c.permutation(n_c) for _ in range(m_c)])
+        t0 = time.perf_counter()
+        om.mantel(xc, yc, n_c, pc, "pearson")
+        t_c = time.perf_counter() - t0
+        per = t_c / ((m_c + 1) * (n_c * (n_c - 1) // 2))
+        out["cpu_baseline"] = {
+            "kind": "oracle", "cores": 1, "sample": f"Pearson, n = {n_c}, {m_c} permutations",
+            "s_per_pair_permutation": per, "est_s_per_call": per * (m_perm + 1) * P_}
+    del Xu, Xw
+    return out
+
+
 def main():
     args = parse()
     if args.record_traffic:
@@ -341,6 +402,10 @@ def main():
                            w.description)
     N = w.table.n_samples
     stream = torch.cuda.current_stream()
+    if args.mantel_only:
+        print(json.dumps({"workload": w.name, "samples": N,
+                          "mantel": mantel_leg(args, w, stream, {}, measured_peaks())}))
+        return
     ctx = ub.Context(w.tree, w.table, stream=stream)
     nb_cond = ctx.output_bytes(ub.MIXED, ub.OUT_CONDENSED)
     out_both = torch.empty(2 * nb_cond // 4, dtype=torch.float32, device="cuda")
@@ -633,56 +698,9 @@ def main():
         torch.cuda.empty_cache()
 
     # Mantel test, Pearson and Spearman, between the unweighted and weighted
-    # matrices of this workload (full layout, FP32): the downstream comparison
-    # of two distance matrices, with args.mantel_perms permutations
+    # matrices of this workload
     if rank == 0 and not args.no_e2e and w.table.study_offsets is None and args.mantel_perms > 0:
-        with ub.Context(w.tree, w.table, stream=stream) as mctx:
-            for k_, v_ in tuned_opts.items():
-                mctx.set_option(k_, v_)
-            Xu = mctx.run(ub.UNWEIGHTED, ub.MIXED, ub.OUT_FULL)
-            Xw = mctx.run(ub.WEIGHTED_NORMALIZED, ub.MIXED, ub.OUT_FULL)
-            torch.cuda.synchronize()
-        m_perm = args.mantel_perms
-        perms = np.random.default_rng(5).permuted(
-            np.tile(np.arange(N, dtype=np.int32), (m_perm, 1)), axis=1)
-        mres = {}
-        for method in ("pearson", "spearman"):
-            ub.unifrac_mantel(Xu, Xw, perms[:8], method)  # warm-up
-            tm_ = []
-            for rep in range(2):
-                t0 = time.perf_counter()
-                r_m, _, p_m = ub.unifrac_mantel(Xu, Xw, perms, method)
-                tm_.append(time.perf_counter() - t0)
-            mres[method] = {"s_per_call": float(np.median(tm_)), "r": r_m, "p": p_m}
-        P_ = N * (N - 1) // 2
-        alg = (m_perm + 1) * 2.0 * P_ * 4  # x and y value of every pair, per permutation
-        t_pear = mres["pearson"]["s_per_call"]
-        hbm = (peaks or {}).get("hbm_gbs") or 6400.0
-        ach = alg / t_pear / 1e9
-        mantel = {"n": N, "permutations": m_perm, **mres,
-                  "roofline": {"kernel": "k_mantel_cross<float,2>", "bound": "hbm",
-                               "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                               "work": "the x and y value of every pair once per permutation "
-                                       "(2 x 4 bytes x P pairs)",
-                               "timed": "whole synchronous Pearson call (moments, upload of "
-                                        "the permutations, cross sums, reduction)"}}
-        if not args.no_cpu_baseline:
-            from oracle import mantel as om
-            n_c, m_c = min(1500, N), 4
-            rng_c = np.random.default_rng(6)
-            iu = np.triu_indices(n_c, 1)
-            xc = Xu.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
-            yc = Xw.view(N, N)[:n_c, :n_c].double().cpu().numpy()[iu]
-            pc = np.array([rng_c.permutation(n_c) for _ in range(m_c)])
-            t0 = time.perf_counter()
-            om.mantel(xc, yc, n_c, pc, "pearson")
-            t_c = time.perf_counter() - t0
-            per = t_c / ((m_c + 1) * (n_c * (n_c - 1) // 2))
-            mantel["cpu_baseline"] = {
-                "kind": "oracle", "cores": 1, "sample": f"Pearson, n = {n_c}, {m_c} permutations",
-                "s_per_pair_permutation": per, "est_s_per_call": per * (m_perm + 1) * P_}
-        line["mantel"] = mantel
-        del Xu, Xw
+        line["mantel"] = mantel_leg(args, w, stream, tuned_opts, peaks)
         torch.cuda.empty_cache()
 
     if rank == 0 and w.table.study_offsets is not None and not args.no_per_study:

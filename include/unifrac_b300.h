@@ -6,8 +6,8 @@
  * feature x sample count table placed on a rooted phylogenetic tree, compute
  * the N x N matrix of UniFrac distances, unweighted or weighted normalized,
  * optionally split into stripes of the matrix that are computed separately
- * and merged (Section II, "split the problem in smaller pieces, i.e. a set of
- * stripes").  With, for every non-root branch b and sample i,
+ * and merged (Section II divides the matrix into stripes for that purpose).
+ * With, for every non-root branch b and sample i,
  *
  *   w[b,i] = (count of sample i on the tips below b) / (total count of i)
  *   p[b,i] = 1 if w[b,i] > 0 else 0
@@ -32,7 +32,8 @@ extern "C" {
 
 typedef struct unifrac_ctx unifrac_ctx; /* opaque */
 
-/* Which distance (Section II: "both unweighted and the weighted normalized").
+/* Which distance (Section II covers the unweighted and the weighted normalized
+ * variants).
  * UNIFRAC_BOTH computes the two from one embedding pass; `out` then holds the
  * unweighted result followed by the weighted one, each of
  * unifrac_output_bytes(...) bytes. */
@@ -42,12 +43,13 @@ enum unifrac_variant {
   UNIFRAC_BOTH = 2
 };
 
-/* Arithmetic (Section II: "fp32 compute support").
+/* Arithmetic (Section II adds single-precision arithmetic to the method).
  * UNIFRAC_FP64:  double output; every sum in FP64 (max abs error vs an FP64
  *                reference <= 1e-12).
- * UNIFRAC_MIXED: float output; FP32 bulk arithmetic (weighted) or exact
- *                integer-digit BF16 tensor-core Gram (unweighted), with FP64
- *                reductions (max abs error vs FP64 <= 2e-6). */
+ * UNIFRAC_MIXED: float output; FP32 arithmetic with two-level FP32 sums
+ *                (weighted) or an exact integer-digit BF16 tensor-core Gram
+ *                with an exact integer epilogue (unweighted); one FP32
+ *                quotient per distance (max abs error vs FP64 <= 2e-6). */
 enum unifrac_precision { UNIFRAC_FP64 = 0, UNIFRAC_MIXED = 1 };
 
 /* Output layouts.  Element type is double (FP64) or float (MIXED).
@@ -249,10 +251,12 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
  *   coords     HOST double[n * k], row-major (sample i: coords[i * k .. + k))
  *   cuda_stream  stream for the device work (NULL = legacy default stream)
  *
- * Method: subspace iteration with min(n, 2k + 16) columns; the products with A on
- * the device (FP32 A, cuBLAS SGEMM), the n x m centring, orthonormalisation
- * and the small eigenproblem on host threads in FP64.  Allocates about
- * 4 n^2 bytes of device memory for A while it runs (UNIFRAC_E_OOM if that
+ * Method: subspace iteration with m = min(n, 2k + 16) columns, on the
+ * device: the products with A in FP32 (cuBLAS SGEMM), the centring terms and
+ * CholeskyQR2 orthonormalisation in FP64 (cuBLAS DSYRK / DTRSM); only m x m
+ * work (Cholesky factors, the Jacobi eigensolver of the Ritz matrix) runs on
+ * the host.  Allocates about 4 n^2 + 24 n m bytes of device memory while it
+ * runs (UNIFRAC_E_OOM if that
  * fails).  Synchronous.  Errors: UNIFRAC_E_INVALID_ARG, UNIFRAC_E_OOM,
  * UNIFRAC_E_CUDA.  No context needed.
  */
@@ -283,10 +287,11 @@ int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t k, int32_t 
  *   p_value    HOST double: the p-value (NaN if n_perms == 0 or r is NaN)
  *   cuda_stream  stream for the device work (NULL = legacy default stream)
  *
- * Sums are FP64 (UNIFRAC_MIXED: FP32 products summed over at most
- * ceil(n / 1024) pairs before FP64).  Rows of y are staged in shared memory
- * (two buffers while 2 (n + 8) sizeof(T) <= 220 KB, else one, else y is
- * gathered from global memory); the environment variable
+ * Sums are FP64 (UNIFRAC_MIXED: FP32 products, summed in FP32 per thread
+ * over at most ceil(n / 128) pairs and then over the 32 lanes of a warp,
+ * FP64 beyond).  Each row of y is staged in shared
+ * memory once per batch of 16 permutations while (n + 8) sizeof(T) <= 220 KB,
+ * else read from global memory; the environment variable
  * UNIFRAC_MANTEL_SMEM_BYTES lowers that 220 KB budget.  Allocates device memory while it runs:
  * about 12 n_perms n bytes, plus for Spearman two rank matrices of the input
  * type and about 16 n^2 bytes of sort buffers.  Synchronous.  Errors:

@@ -9,19 +9,19 @@
 // so a permuted statistic needs only the cross sum
 //   c_pi = sum_{i<j} dx(i, j) dy(pi(i), pi(j)).
 //
-// Kernel layout (k_mantel_cross): one block per (row i of x, batch of
-// kMantelBatch permutations).  For each permutation of the batch the block
-// stages the whole row pi(i) of y in shared memory (16-byte cp.async,
-// double-buffered so the next permutation's row streams in while this one is
-// used) and walks j > i: x(i, j) and pi(j) coalesced from global memory (L2
-// after the first permutation of the batch), y(pi(i), pi(j)) gathered from
-// shared memory.  A row of y is the only HBM stream per (i, permutation):
-// n^2 values per permutation, twice the P a permutation must touch; the
+// Kernel layout (k_mantel_cross, y-row-stationary): one block per (row a of
+// y, batch of kMantelBatch permutations).  The block stages row a of y in
+// shared memory once; for each permutation p of the batch it takes the row
+// i = pi_p^-1(a) of x, whose pairs (i, j > i) map to the y pairs
+// (a, pi_p(j)), and streams x(i, j > i) and pi_p(j) with coalesced loads
+// while gathering y(a, pi_p(j)) from shared memory.  Each permutation reads
+// every pair of x once (HBM) and every row of y once per batch; the
 // random gather that would otherwise hit one 32-byte sector per value is a
-// shared-memory access instead.  Rows too long for shared memory gather y
-// from global memory directly.  Per (permutation, row) block sums go to
-// `partial`, summed per permutation in a fixed order (k_sum_rows), so results
-// do not depend on scheduling.  Two-sided p = (1 + #{|r_pi| >= |r|}) / (M + 1).
+// shared-memory access instead.  Rows too long for shared memory are read
+// from global memory (the batch keeps the row in L2).  Per (permutation,
+// row) block sums go to `partial`, summed per permutation in a fixed order
+// (k_sum_rows), so results do not depend on scheduling.  Two-sided
+// p = (1 + #{|r_pi| >= |r|}) / (M + 1).
 //
 // Spearman ranks are computed on the device: the upper-triangle values are
 // sorted with their pair index (CUB radix sort), run heads found by a
@@ -42,8 +42,10 @@
 namespace ufb {
 namespace {
 
-constexpr int kMantelBatch = 8;      // permutations per block
-constexpr int kMantelThreads = 1024;
+constexpr int kMantelBatch = 16;          // permutations per block
+constexpr int kShortRowBytes = 24 * 1024;  // rows up to this: short-row launch shape
+constexpr int kShortRowThreads = 128;
+constexpr int kMantelUnroll = 4;          // loads in flight per thread and round (even)
 constexpr int kMomentBlocks = 592;
 constexpr size_t kSmemBudget = 220 * 1024;
 
@@ -84,66 +86,83 @@ __device__ __forceinline__ int stage_row(T *buf, const T *__restrict__ y, int64_
   return s;
 }
 
-// partial[p][i] = sum_{j > i} (x(i,j) - mx) (y(pi_p(i), pi_p(j)) - my) for the
-// permutations p of this block's batch.  NBUF = 2: double-buffered staging of
-// the y rows, 1: single buffer, 0: gather y from global memory.
-template <typename T, int NBUF>
-__global__ void __launch_bounds__(kMantelThreads) k_mantel_cross(
+// y-row-stationary cross sums.  Block (a, batch): row a of y is staged once
+// (NBUF = 1; NBUF = 0 reads it from global memory, where it stays in L2 for
+// the batch), then for each permutation p of the batch, with i = pi_p^-1(a),
+//   partial[p][a] = sum_{j > i} (x(i, j) - mx) (y(a, pi_p(j)) - my),
+// i.e. the pairs (i, j) of x whose relabelled y pair has a as its first
+// sample.  Over a = 0 .. n-1 the rows i = pi_p^-1(a) run over every row once,
+// so the partials of one permutation sum to its cross sum.  x(i, j > i) and
+// pi_p(j) are coalesced loads (x from HBM, each pair once per permutation;
+// the batch's permutation rows stay in L2); y(a, .) is a shared-memory
+// gather.  No barrier between permutations: per-warp sums go to red[][] and
+// are reduced once at the end.  P: permutation entry type (uint16_t while
+// n <= 65,536, else int32_t).
+template <typename T, typename P, int NBUF, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_mantel_cross(
     const T *__restrict__ x, const T *__restrict__ y, int32_t n, T mx, T my,
-    const int32_t *__restrict__ perms, int32_t n_perms, double *__restrict__ partial) {
+    const P *__restrict__ perms, const P *__restrict__ inv, int32_t n_perms,
+    double *__restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kMantelThreads / 32];
-  T *buf = reinterpret_cast<T *>(smem_raw);
-  const size_t buf_elems = ((size_t)n + 16 / sizeof(T) + 3) & ~(size_t)3;
-  const int64_t i = blockIdx.x;
+  __shared__ double red[kMantelBatch][NT / 32];
+  const int64_t a = blockIdx.x;
   const int p0 = blockIdx.y * kMantelBatch;
   const int nb = min(kMantelBatch, n_perms - p0);
-  const T *xrow = x + i * n;
-  int s_cur = 0;
+  // staged rows are centred once here (y - my), rows read from global memory
+  // are centred in the loop
+  const T *yv;
+  T yc = my;
   if (NBUF > 0) {
-    s_cur = stage_row(buf, y, perms[(int64_t)p0 * n + i], n);
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const int s = stage_row(buf, y, a, n);
     cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += NT) buf[s + k] -= my;
+    __syncthreads();
+    yv = buf + s;
+    yc = T(0);
+  } else {
+    yv = y + a * n;
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int b = 0; b < nb; ++b) {
-    const int32_t *prow = perms + (int64_t)(p0 + b) * n;
-    const T *ys = buf;
-    const int s = s_cur;
-    if (NBUF == 2) {
-      ys = buf + (b & 1) * buf_elems;
-      if (b + 1 < nb) {
-        s_cur = stage_row(buf + ((b + 1) & 1) * buf_elems, y, prow[n + i], n);
-        cp_async_commit();
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
+    const int64_t p = p0 + b;
+    const P *prow = perms + p * n;
+    const int i = (int)inv[p * n + a];
+    const T *xrow = x + (int64_t)i * n;
+    // kMantelUnroll independent (permutation entry, x) loads in flight per
+    // thread each round; slots past the row end load nothing and add 0
+    T acc0 = T(0), acc1 = T(0);
+    for (int j = i + 1 + threadIdx.x; j < n; j += kMantelUnroll * NT) {
+      int q[kMantelUnroll];
+      T xv[kMantelUnroll];
+#pragma unroll
+      for (int u = 0; u < kMantelUnroll; ++u) {
+        const int jj = j + u * NT;
+        q[u] = jj < n ? (int)prow[jj] : 0;
+        xv[u] = jj < n ? __ldg(xrow + jj) : mx;
       }
-      __syncthreads();
-    } else if (NBUF == 1) {
-      cp_async_wait<0>();
-      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kMantelUnroll; u += 2) {
+        acc0 = fma_t(xv[u] - mx, NBUF > 0 ? yv[q[u]] : yv[q[u]] - yc, acc0);
+        acc1 = fma_t(xv[u + 1] - mx, NBUF > 0 ? yv[q[u + 1]] : yv[q[u + 1]] - yc, acc1);
+      }
     }
-    const T *yrow = y + (int64_t)prow[i] * n;
-    T acc = T(0);
-    for (int64_t j = i + 1 + threadIdx.x; j < n; j += kMantelThreads) {
-      const int32_t pj = __ldg(prow + j);
-      const T yv = NBUF > 0 ? ys[pj + s] : __ldg(yrow + pj);
-      acc = fma_t(__ldg(xrow + j) - mx, yv - my, acc);
-    }
-    double v = (double)acc;
+    // warp sum in T (B300's FP64 pipe is narrow: FP64 here would bound the
+    // FP32 kernel), FP64 from the per-warp sums on
+    T v = acc0 + acc1;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();  // also: every thread is done with this buffer
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kMantelThreads / 32; ++w) t += red[w];
-      partial[(int64_t)(p0 + b) * n + i] = t;
-    }
-    if (NBUF == 1 && b + 1 < nb) {
-      s_cur = stage_row(buf, y, prow[n + i], n);
-      cp_async_commit();
-    }
-    __syncthreads();  // red[] is rewritten by the next permutation
+    if (lane == 0) red[b][warp] = (double)v;
+  }
+  __syncthreads();
+  for (int b = warp; b < nb; b += NT / 32) {
+    double v = 0.0;
+    for (int w = lane; w < NT / 32; w += 32) v += red[b][w];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) partial[(int64_t)(p0 + b) * n + a] = v;
   }
 }
 
@@ -331,16 +350,44 @@ size_t smem_budget() {
   return std::min<size_t>((size_t)b, kSmemBudget);
 }
 
-template <typename T, int NBUF>
-cudaError_t launch_cross(dim3 grid, size_t smem, cudaStream_t st, const T *x, const T *y, int32_t n,
-                         T mx, T my, const int32_t *perms, int32_t M, double *partial) {
+template <typename T, typename P, int NBUF, int MINB, int NT>
+cudaError_t launch_cross(int32_t M, size_t smem, cudaStream_t st, const T *x, const T *y, int32_t n,
+                         T mx, T my, const P *perms, const P *inv, double *partial) {
   if (smem > 0) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_mantel_cross<T, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(k_mantel_cross<T, P, NBUF, MINB, NT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_mantel_cross<T, NBUF><<<grid, kMantelThreads, smem, st>>>(x, y, n, mx, my, perms, M, partial);
-  return cudaGetLastError();
+  // gridDim.y is at most 65,535: batches beyond that in further launches
+  const int64_t batches = (M + kMantelBatch - 1) / kMantelBatch;
+  for (int64_t b0 = 0; b0 < batches; b0 += 65535) {
+    const int64_t nbat = std::min<int64_t>(65535, batches - b0);
+    const int64_t first = b0 * kMantelBatch;
+    const int32_t cnt = (int32_t)std::min<int64_t>(M - first, nbat * kMantelBatch);
+    k_mantel_cross<T, P, NBUF, MINB, NT><<<dim3(n, (unsigned)nbat), NT, smem, st>>>(
+        x, y, n, mx, my, perms + first * n, inv + first * n, cnt, partial + first * n);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Launch shape by row length (buf_bytes per staged row of y): short rows,
+// kShortRowThreads threads (several blocks per SM); long rows, 1,024
+// threads, two blocks per SM while two rows fit; rows longer than the
+// shared-memory budget are read from global memory (L2).
+template <typename T, typename P>
+cudaError_t cross_sums(int32_t n, int32_t M, cudaStream_t st, const T *x, const T *y, T mx, T my,
+                       const P *perms, const P *inv, double *partial) {
+  const size_t buf_bytes = (((size_t)n + 16 / sizeof(T) + 3) & ~(size_t)3) * sizeof(T);
+  const size_t budget = smem_budget();
+  if (buf_bytes <= kShortRowBytes && buf_bytes <= budget)
+    return launch_cross<T, P, 1, 1, kShortRowThreads>(M, buf_bytes, st, x, y, n, mx, my, perms, inv, partial);
+  if (2 * buf_bytes <= budget)
+    return launch_cross<T, P, 1, 2, 1024>(M, buf_bytes, st, x, y, n, mx, my, perms, inv, partial);
+  if (buf_bytes <= budget)
+    return launch_cross<T, P, 1, 1, 1024>(M, buf_bytes, st, x, y, n, mx, my, perms, inv, partial);
+  return launch_cross<T, P, 0, 1, 1024>(M, 0, st, x, y, n, mx, my, perms, inv, partial);
 }
 
 template <typename T>
@@ -373,31 +420,36 @@ int mantel_pearson(const T *x, const T *y, int32_t n, const int32_t *perms_host,
   sxx -= sx * sx / (double)P;
   syy -= sy * sy / (double)P;
   const double norm = std::sqrt(sxx * syy);
-  // the identity first, then the caller's permutations
+  // the identity first, then the caller's permutations, and their inverses
+  // (16-bit entries while every sample index fits)
   const int32_t M = n_perms + 1;
-  int32_t *d_perms;
+  const bool narrow = n <= 65536;
+  const size_t esz = narrow ? 2 : 4;
+  unsigned char *d_pi;
   double *partial, *cross;
-  if (!mem.alloc(&d_perms, (size_t)M * n) || !mem.alloc(&partial, (size_t)M * n) ||
+  if (!mem.alloc(&d_pi, 2 * (size_t)M * n * esz) || !mem.alloc(&partial, (size_t)M * n) ||
       !mem.alloc(&cross, (size_t)M))
     return UNIFRAC_E_OOM;
-  std::vector<int32_t> ident(n);
-  for (int32_t i = 0; i < n; ++i) ident[i] = i;
-  if (cudaMemcpyAsync(d_perms, ident.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess ||
-      (n_perms > 0 && cudaMemcpyAsync(d_perms + n, perms_host, (size_t)n_perms * n * sizeof(int32_t),
-                                      cudaMemcpyHostToDevice, st) != cudaSuccess))
+  std::vector<unsigned char> hp(2 * (size_t)M * n * esz);
+  const int64_t half = (int64_t)M * n;
+  auto put = [&](int64_t t, int32_t v) {
+    if (narrow) reinterpret_cast<uint16_t *>(hp.data())[t] = (uint16_t)v;
+    else reinterpret_cast<int32_t *>(hp.data())[t] = v;
+  };
+  for (int32_t p = 0; p < M; ++p)
+    for (int32_t i = 0; i < n; ++i) {
+      const int32_t v = p == 0 ? i : perms_host[(int64_t)(p - 1) * n + i];
+      put((int64_t)p * n + i, v);
+      put(half + (int64_t)p * n + v, i);
+    }
+  if (cudaMemcpyAsync(d_pi, hp.data(), hp.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return UNIFRAC_E_CUDA;
-  const size_t buf_bytes = (((size_t)n + 16 / sizeof(T) + 3) & ~(size_t)3) * sizeof(T);
-  const size_t budget = smem_budget();
-  const dim3 grid(n, (M + kMantelBatch - 1) / kMantelBatch);
   const T mxt = (T)mx, myt = (T)my;
-  cudaError_t e;
-  if (2 * buf_bytes <= budget)
-    e = launch_cross<T, 2>(grid, 2 * buf_bytes, st, x, y, n, mxt, myt, d_perms, M, partial);
-  else if (buf_bytes <= budget)
-    e = launch_cross<T, 1>(grid, buf_bytes, st, x, y, n, mxt, myt, d_perms, M, partial);
-  else
-    e = launch_cross<T, 0>(grid, 0, st, x, y, n, mxt, myt, d_perms, M, partial);
+  const cudaError_t e =
+      narrow ? cross_sums<T, uint16_t>(n, M, st, x, y, mxt, myt, reinterpret_cast<const uint16_t *>(d_pi),
+                                       reinterpret_cast<const uint16_t *>(d_pi) + half, partial)
+             : cross_sums<T, int32_t>(n, M, st, x, y, mxt, myt, reinterpret_cast<const int32_t *>(d_pi),
+                                      reinterpret_cast<const int32_t *>(d_pi) + half, partial);
   if (e != cudaSuccess) return UNIFRAC_E_CUDA;
   k_sum_rows<<<M, 256, 0, st>>>(partial, n, cross);
   std::vector<double> c(M);

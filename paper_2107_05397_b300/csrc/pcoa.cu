@@ -10,18 +10,18 @@
 // m = 2k + 16 columns: Y = B Q, Q = orth(Y), repeated; then the
 // Rayleigh-Ritz step T = Q^T B Q, T = W diag(theta) W^T, U = Q W.
 //
-// Device: the n x n work -- A = -1/2 D o D in FP32 with FP64 row sums (one
-// pass over D), and every A Q product (cuBLAS SGEMM, the one plain GEMM of
-// the path).  Host threads: the n x m work in FP64 -- the centring terms,
-// orthonormalisation by shifted CholeskyQR2 (a Cholesky factor of the Gram
-// matrix Y^T Y, twice; the first shifted by a tiny multiple of its trace so
-// that a rank-deficient Y still factors), and the m x m eigenproblem by the
-// cyclic Jacobi method.
+// Device: A = -1/2 D o D in FP32 with FP64 row sums (one pass over D), every
+// A Q product (cuBLAS SGEMM, the pass over A that bounds the iteration), and
+// the n x m FP64 work -- the centring terms, orthonormalisation by shifted
+// CholeskyQR2 (the Gram matrix Y^T Y by DSYRK, its m x m Cholesky factor R on
+// the host, Y R^-1 by DTRSM; twice, the first factor shifted by a tiny
+// multiple of the trace so that a rank-deficient Y still factors) and the
+// Ritz products.  Host: only m x m work (Cholesky, the eigenproblem of
+// Q^T B Q by the cyclic Jacobi method).
 #include <cublas_v2.h>
 
 #include <algorithm>
 #include <cmath>
-#include <thread>
 #include <vector>
 
 #include "ufb_internal.cuh"
@@ -63,78 +63,50 @@ uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-template <typename F>
-void parallel_rows(int64_t n, F &&fn) {  // fn(lo, hi, thread) over row ranges
-  const unsigned hw = std::thread::hardware_concurrency();
-  const int T = n < 4096 ? 1 : (int)std::max(1u, std::min(32u, hw ? hw : 1u));
-  std::vector<std::thread> th;
-  for (int t = 1; t < T; ++t) th.emplace_back(fn, n * t / T, n * (t + 1) / T, t);
-  fn((int64_t)0, n / T, 0);
-  for (auto &x : th) x.join();
+// Y = Yf - r s^T - 1 t^T + g 1 s^T in FP64 (column-major n x m): the
+// double-centring terms of B Q = J A J Q added to the product A Q.
+__global__ void k_centre(const float *__restrict__ Yf, const double *__restrict__ r,
+                         const double *__restrict__ st, double g, int64_t n, int m,
+                         double *__restrict__ Y) {
+  const int64_t total = n * m;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = x % n;
+    const int j = (int)(x / n);
+    const double sj = st[j], tj = st[m + j];
+    Y[x] = (double)Yf[x] - r[i] * sj - tj + g * sj;
+  }
 }
 
-// Gram matrix G = Y^T Y of the column-major n x m matrix Y (FP64).
-std::vector<double> gram(const std::vector<double> &Y, int64_t n, int m) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  const int T = n < 4096 ? 1 : (int)std::max(1u, std::min(32u, hw ? hw : 1u));
-  std::vector<std::vector<double>> part(T, std::vector<double>((size_t)m * m, 0.0));
-  parallel_rows(n, [&](int64_t lo, int64_t hi, int t) {
-    std::vector<double> &P = part[t];
-    for (int a = 0; a < m; ++a)
-      for (int b = a; b < m; ++b) {
-        double s = 0.0;
-        const double *ya = &Y[(size_t)a * n], *yb = &Y[(size_t)b * n];
-        for (int64_t i = lo; i < hi; ++i) s += ya[i] * yb[i];
-        P[(size_t)a * m + b] += s;
-      }
-  });
-  std::vector<double> G((size_t)m * m, 0.0);
-  for (int t = 0; t < T; ++t)
-    for (int a = 0; a < m; ++a)
-      for (int b = a; b < m; ++b) G[(size_t)a * m + b] += part[t][(size_t)a * m + b];
-  for (int a = 0; a < m; ++a)
-    for (int b = 0; b < a; ++b) G[(size_t)a * m + b] = G[(size_t)b * m + a];
-  return G;
+__global__ void k_to_float(const double *__restrict__ a, int64_t len, float *__restrict__ b) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < len;
+       x += (int64_t)gridDim.x * blockDim.x)
+    b[x] = (float)a[x];
 }
 
-// One CholeskyQR step: G = R^T R, Y <- Y R^{-1}.  shift > 0 adds
-// shift * trace(G) / m to the diagonal first.  Pivots that are not positive
-// (an exactly dependent column) become 1, leaving that column's remainder.
-void cholesky_qr(std::vector<double> &Y, int64_t n, int m, double shift) {
-  std::vector<double> G = gram(Y, n, m);
+// Upper Cholesky factor of the m x m FP64 matrix G (column-major): G = R^T R.
+// shift > 0 adds shift * trace(G) / m to the diagonal first.  Pivots that are
+// not positive (an exactly dependent column) become 1, leaving that column's
+// remainder.  Output R column-major, zero below the diagonal.
+std::vector<double> cholesky_upper(std::vector<double> G, int m, double shift) {
   double tr = 0.0;
   for (int a = 0; a < m; ++a) tr += G[(size_t)a * m + a];
   if (shift > 0.0)
     for (int a = 0; a < m; ++a) G[(size_t)a * m + a] += shift * tr / m + 1e-300;
-  std::vector<double> R((size_t)m * m, 0.0);  // upper triangular, row-major
+  std::vector<double> R((size_t)m * m, 0.0);
+  auto at = [m](std::vector<double> &M, int row, int col) -> double & { return M[(size_t)col * m + row]; };
   for (int j = 0; j < m; ++j) {
-    double d = G[(size_t)j * m + j];
-    for (int l = 0; l < j; ++l) d -= R[(size_t)l * m + j] * R[(size_t)l * m + j];
+    double d = at(G, j, j);
+    for (int l = 0; l < j; ++l) d -= at(R, l, j) * at(R, l, j);
     const double rjj = d > 0.0 ? std::sqrt(d) : 1.0;
-    R[(size_t)j * m + j] = rjj;
+    at(R, j, j) = rjj;
     for (int c = j + 1; c < m; ++c) {
-      double v = G[(size_t)j * m + c];
-      for (int l = 0; l < j; ++l) v -= R[(size_t)l * m + j] * R[(size_t)l * m + c];
-      R[(size_t)j * m + c] = v / rjj;
+      double v = at(G, j, c);
+      for (int l = 0; l < j; ++l) v -= at(R, l, j) * at(R, l, c);
+      at(R, j, c) = v / rjj;
     }
   }
-  // rows of Y solve x R = y (forward substitution)
-  parallel_rows(n, [&](int64_t lo, int64_t hi, int) {
-    std::vector<double> x(m);
-    for (int64_t i = lo; i < hi; ++i) {
-      for (int j = 0; j < m; ++j) {
-        double v = Y[(size_t)j * n + i];
-        for (int l = 0; l < j; ++l) v -= x[l] * R[(size_t)l * m + j];
-        x[j] = v / R[(size_t)j * m + j];
-      }
-      for (int j = 0; j < m; ++j) Y[(size_t)j * n + i] = x[j];
-    }
-  });
-}
-
-void orthonormalise(std::vector<double> &Y, int64_t n, int m) {
-  cholesky_qr(Y, n, m, 1e-13);
-  cholesky_qr(Y, n, m, 0.0);
+  return R;
 }
 
 // Cyclic Jacobi eigenvalue method (rotations zeroing each off-diagonal entry
@@ -184,14 +156,14 @@ std::vector<double> jacobi_eigen(std::vector<double> &T, int m, std::vector<doub
 }
 
 struct PcoaDev {
-  float *A = nullptr, *Q = nullptr, *Y = nullptr;
-  double *rowmean = nullptr;
+  float *A = nullptr, *Qf = nullptr, *Yf = nullptr;
+  double *Q = nullptr, *Y = nullptr, *r = nullptr, *ones = nullptr, *st = nullptr, *G = nullptr,
+         *U = nullptr;
   cublasHandle_t h = nullptr;
   ~PcoaDev() {
-    if (A) cudaFree(A);
-    if (Q) cudaFree(Q);
-    if (Y) cudaFree(Y);
-    if (rowmean) cudaFree(rowmean);
+    for (void *p : {(void *)A, (void *)Qf, (void *)Yf, (void *)Q, (void *)Y, (void *)r, (void *)ones,
+                    (void *)st, (void *)G, (void *)U})
+      if (p) cudaFree(p);
     if (h) cublasDestroy(h);
   }
 };
@@ -211,93 +183,134 @@ extern "C" int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t 
   const int m = std::min<int>(n, 2 * k + 16);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   PcoaDev dv;
-  const size_t nn = (size_t)n * n;
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m;
   if (cudaMalloc(&dv.A, nn * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&dv.Q, (size_t)n * m * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&dv.Y, (size_t)n * m * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&dv.rowmean, (size_t)n * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&dv.Qf, nm * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&dv.Yf, nm * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&dv.Q, nm * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.Y, nm * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.U, (size_t)n * k * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.r, (size_t)n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.ones, (size_t)n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.st, 2 * (size_t)m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.G, (size_t)m * m * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return UNIFRAC_E_OOM;
   }
   if (cublasCreate(&dv.h) != CUBLAS_STATUS_SUCCESS || cublasSetStream(dv.h, st) != CUBLAS_STATUS_SUCCESS)
     return UNIFRAC_E_CUDA;
   if (precision == UNIFRAC_FP64)
-    k_pcoa_square<double><<<n, 256, 0, st>>>(static_cast<const double *>(dist), n, dv.A, dv.rowmean);
+    k_pcoa_square<double><<<n, 256, 0, st>>>(static_cast<const double *>(dist), n, dv.A, dv.r);
   else
-    k_pcoa_square<float><<<n, 256, 0, st>>>(static_cast<const float *>(dist), n, dv.A, dv.rowmean);
+    k_pcoa_square<float><<<n, 256, 0, st>>>(static_cast<const float *>(dist), n, dv.A, dv.r);
   if (cudaGetLastError() != cudaSuccess) return UNIFRAC_E_CUDA;
-  std::vector<double> r(n);
-  if (cudaMemcpyAsync(r.data(), dv.rowmean, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+  std::vector<double> r(n), ones(n, 1.0);
+  if (cudaMemcpyAsync(r.data(), dv.r, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dv.ones, ones.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return UNIFRAC_E_CUDA;
   double g = 0.0;
   for (int32_t i = 0; i < n; ++i) g += r[i];
   g /= (double)n;
+  const int grid = 148 * 8;
+  const double d1 = 1.0, d0 = 0.0;
 
-  // random start, orthonormal columns (column-major n x m)
-  std::vector<double> Q((size_t)n * m), Y((size_t)n * m);
-  for (size_t x = 0; x < Q.size(); ++x)
-    Q[x] = (double)(splitmix64(seed ^ splitmix64(x)) >> 11) * 0x1.0p-52 - 1.0;
-  orthonormalise(Q, n, m);
-  std::vector<float> buf((size_t)n * m);
-  // Y = B Q: device product A Q, host centring terms
-  auto apply_B = [&]() -> int {
-    for (size_t x = 0; x < buf.size(); ++x) buf[x] = (float)Q[x];
-    if (cudaMemcpyAsync(dv.Q, buf.data(), buf.size() * sizeof(float), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-      return UNIFRAC_E_CUDA;
-    const float one = 1.f, zero = 0.f;
-    if (cublasSgemm(dv.h, CUBLAS_OP_N, CUBLAS_OP_N, n, m, n, &one, dv.A, n, dv.Q, n, &zero, dv.Y, n) !=
+  // Q <- Q R^-1 with Q^T Q = R^T R (CholeskyQR: Gram by DSYRK, the m x m
+  // factor on the host, the solve by DTRSM)
+  std::vector<double> Gh((size_t)m * m);
+  auto cholqr = [&](double *M, double shift) -> int {
+    if (cublasDsyrk(dv.h, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, m, n, &d1, M, n, &d0, dv.G, m) !=
         CUBLAS_STATUS_SUCCESS)
       return UNIFRAC_E_CUDA;
-    if (cudaMemcpyAsync(buf.data(), dv.Y, buf.size() * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(Gh.data(), dv.G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return UNIFRAC_E_CUDA;
-    std::vector<double> s(m, 0.0), t(m, 0.0);  // 1^T Q and r^T Q
-    for (int j = 0; j < m; ++j)
-      for (int32_t i = 0; i < n; ++i) {
-        s[j] += Q[(size_t)j * n + i];
-        t[j] += r[i] * Q[(size_t)j * n + i];
-      }
-    parallel_rows(n, [&](int64_t lo, int64_t hi, int) {
-      for (int j = 0; j < m; ++j)
-        for (int64_t i = lo; i < hi; ++i)
-          Y[(size_t)j * n + i] = (double)buf[(size_t)j * n + i] - r[i] * s[j] - t[j] + g * s[j];
-    });
+    for (int a = 0; a < m; ++a)  // mirror the upper triangle
+      for (int b = a + 1; b < m; ++b) Gh[(size_t)a * m + b] = Gh[(size_t)b * m + a];
+    std::vector<double> R = cholesky_upper(Gh, m, shift);
+    if (cudaMemcpyAsync(dv.G, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cublasDtrsm(dv.h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                    CUBLAS_DIAG_NON_UNIT, n, m, &d1, dv.G, m, M, n) != CUBLAS_STATUS_SUCCESS ||
+        cudaStreamSynchronize(st) != cudaSuccess)  // R (host) is copied before it goes out of scope
+      return UNIFRAC_E_CUDA;
     return UNIFRAC_OK;
   };
+  auto orthonormalise = [&](double *M) -> int {
+    int rc = cholqr(M, 1e-13);  // shifted first pass: factors even a rank-deficient M
+    return rc ? rc : cholqr(M, 0.0);
+  };
+  // Y = B Q = A Q - r (1^T Q) - 1 (r^T Q) + g 1 (1^T Q): the product in FP32
+  // (SGEMM), the centring terms in FP64
+  auto apply_B = [&]() -> int {
+    k_to_float<<<grid, 256, 0, st>>>(dv.Q, (int64_t)nm, dv.Qf);
+    const float one = 1.f, zero = 0.f;
+    if (cublasSgemm(dv.h, CUBLAS_OP_N, CUBLAS_OP_N, n, m, n, &one, dv.A, n, dv.Qf, n, &zero, dv.Yf, n) !=
+            CUBLAS_STATUS_SUCCESS ||
+        cublasDgemv(dv.h, CUBLAS_OP_T, n, m, &d1, dv.Q, n, dv.ones, 1, &d0, dv.st, 1) !=
+            CUBLAS_STATUS_SUCCESS ||
+        cublasDgemv(dv.h, CUBLAS_OP_T, n, m, &d1, dv.Q, n, dv.r, 1, &d0, dv.st + m, 1) !=
+            CUBLAS_STATUS_SUCCESS)
+      return UNIFRAC_E_CUDA;
+    k_centre<<<grid, 256, 0, st>>>(dv.Yf, dv.r, dv.st, g, n, m, dv.Y);
+    return cudaGetLastError() == cudaSuccess ? UNIFRAC_OK : UNIFRAC_E_CUDA;
+  };
+
+  // random start (SplitMix64 stream from the seed), orthonormal columns
+  {
+    std::vector<double> Q0(nm);
+    for (size_t x = 0; x < nm; ++x)
+      Q0[x] = (double)(splitmix64(seed ^ splitmix64(x)) >> 11) * 0x1.0p-52 - 1.0;
+    if (cudaMemcpyAsync(dv.Q, Q0.data(), nm * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return UNIFRAC_E_CUDA;
+  }
   int rc;
+  if ((rc = orthonormalise(dv.Q))) return rc;
   for (int it = 0; it < iters; ++it) {
     if ((rc = apply_B())) return rc;
-    Q.swap(Y);
-    orthonormalise(Q, n, m);
+    std::swap(dv.Q, dv.Y);
+    if ((rc = orthonormalise(dv.Q))) return rc;
   }
   // Rayleigh-Ritz: T = Q^T B Q (symmetrised), eigenpairs, U = Q W
   if ((rc = apply_B())) return rc;
-  std::vector<double> T((size_t)m * m, 0.0);
+  if (cublasDgemm(dv.h, CUBLAS_OP_T, CUBLAS_OP_N, m, m, n, &d1, dv.Q, n, dv.Y, n, &d0, dv.G, m) !=
+      CUBLAS_STATUS_SUCCESS)
+    return UNIFRAC_E_CUDA;
+  std::vector<double> Th((size_t)m * m);
+  if (cudaMemcpyAsync(Th.data(), dv.G, Th.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return UNIFRAC_E_CUDA;
+  std::vector<double> T((size_t)m * m);
   for (int a = 0; a < m; ++a)
-    for (int b = a; b < m; ++b) {
-      double v = 0.0;
-      for (int32_t i = 0; i < n; ++i) v += 0.5 * (Q[(size_t)a * n + i] * Y[(size_t)b * n + i] +
-                                                  Q[(size_t)b * n + i] * Y[(size_t)a * n + i]);
-      T[(size_t)a * m + b] = T[(size_t)b * m + a] = v;
-    }
+    for (int b = 0; b < m; ++b)
+      T[(size_t)a * m + b] = 0.5 * (Th[(size_t)b * m + a] + Th[(size_t)a * m + b]);
   std::vector<double> W;
   std::vector<double> theta = jacobi_eigen(T, m, W);
   std::vector<int> order(m);
   for (int a = 0; a < m; ++a) order[a] = a;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return theta[a] > theta[b]; });
-  for (int c = 0; c < k; ++c) eigvals[c] = theta[order[c]];
-  parallel_rows(n, [&](int64_t lo, int64_t hi, int) {
-    for (int64_t i = lo; i < hi; ++i)
-      for (int c = 0; c < k; ++c) {
-        const int col = order[c];
-        double u = 0.0;
-        for (int a = 0; a < m; ++a) u += Q[(size_t)a * n + i] * W[(size_t)a * m + col];
-        coords[(size_t)i * k + c] = u * std::sqrt(std::max(theta[col], 0.0));
-      }
-  });
+  // U = Q W_k (device), coordinates U sqrt(max(theta, 0)) (host)
+  std::vector<double> Wk((size_t)m * k);  // column-major m x k
+  for (int c = 0; c < k; ++c)
+    for (int a = 0; a < m; ++a) Wk[(size_t)c * m + a] = W[(size_t)a * m + order[c]];
+  std::vector<double> Uh((size_t)n * k);
+  if (cudaMemcpyAsync(dv.G, Wk.data(), Wk.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cublasDgemm(dv.h, CUBLAS_OP_N, CUBLAS_OP_N, n, k, m, &d1, dv.Q, n, dv.G, m, &d0, dv.U, n) !=
+          CUBLAS_STATUS_SUCCESS ||
+      cudaMemcpyAsync(Uh.data(), dv.U, Uh.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return UNIFRAC_E_CUDA;
+  for (int c = 0; c < k; ++c) {
+    eigvals[c] = theta[order[c]];
+    const double sc = std::sqrt(std::max(theta[order[c]], 0.0));
+    for (int32_t i = 0; i < n; ++i) coords[(size_t)i * k + c] = Uh[(size_t)c * n + i] * sc;
+  }
   return UNIFRAC_OK;
 }

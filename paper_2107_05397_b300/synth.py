@@ -6,8 +6,8 @@ arithmetic, so both the FP64 oracle (tests) and the CUDA path (bench, tests)
 draw their inputs from here without sharing any of the method.
 
 The paper (Section II) motivates the shapes: tens of thousands of samples, a
-phylogenetic tree over the observed features, and very sparse tables ("most
-kinds of microbes are not found in most locations").  The Earth Microbiome
+phylogenetic tree over the observed features, and very sparse tables (a given
+microbe is absent from the great majority of samples).  The Earth Microbiome
 Project data it cites is not available, so these seeded generators stand in.
 
 Conventions shared with the C ABI:

@@ -703,12 +703,18 @@ def test_mantel_unifrac_matrices_match_oracle(small, method, precision):
     assert got[0] > 0.2  # the two UniFrac variants agree on these samples
 
 
-@pytest.mark.parametrize("budget", [None, "3000", "0"])
+def _row_bytes(n, precision):
+    es = 8 if precision == ub.FP64 else 4
+    return ((n + 16 // es + 3) & ~3) * es
+
+
+@pytest.mark.parametrize("budget", [None, "0"])
 @pytest.mark.parametrize("n", [3, 5, 37, 301])
 @pytest.mark.parametrize("precision", PRECISIONS)
-def test_mantel_staging_paths_and_ragged_sizes(n, budget, precision, monkeypatch):
-    """Every way of reading y (two shared-memory buffers, one, none) at sizes
-    whose rows start off the 16-byte grid, Pearson and Spearman."""
+def test_mantel_short_rows_and_ragged_sizes(n, budget, precision, monkeypatch):
+    """Short rows (the small-block launch shape; with a zero staging budget,
+    y read from global memory) at sizes whose rows start off the 16-byte
+    grid, Pearson and Spearman."""
     import torch
     if budget is not None:
         monkeypatch.setenv("UNIFRAC_MANTEL_SMEM_BYTES", budget)
@@ -719,6 +725,37 @@ def test_mantel_staging_paths_and_ragged_sizes(n, budget, precision, monkeypatch
     for method in ("pearson", "spearman"):
         got = ub.unifrac_mantel(Xd, Yd, perms, method)
         _check_mantel(got, _mantel_oracle(X, Y, perms, method), MANTEL_TOL[precision])
+
+
+_LONG_ROW_ORACLE = {}
+
+
+@pytest.mark.parametrize("shape", ["two_per_sm", "one_per_sm", "global"])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_mantel_long_row_launch_shapes(shape, precision, monkeypatch):
+    """n = 6,501 (rows past the short-row limit; 1,024-thread blocks): two
+    blocks per SM, one (budget between one and two rows), and no staging,
+    against the oracle with 3 permutations (plus a 37-permutation run that
+    spans several batches of the same launch)."""
+    import torch
+    n = 6501
+    rb = _row_bytes(n, precision)
+    if shape == "one_per_sm":
+        monkeypatch.setenv("UNIFRAC_MANTEL_SMEM_BYTES", str(rb + 64))
+    elif shape == "global":
+        monkeypatch.setenv("UNIFRAC_MANTEL_SMEM_BYTES", "0")
+    dt = np.float64 if precision == ub.FP64 else np.float32
+    X, Y = _point_matrices(n, 80, dt)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    perms = _mantel_perms(n, 37, 81)
+    r, stats, p = ub.unifrac_mantel(Xd, Yd, perms)
+    if precision not in _LONG_ROW_ORACLE:
+        _LONG_ROW_ORACLE[precision] = _mantel_oracle(X, Y, perms[:3], "pearson")
+    r_o, stats_o, _ = _LONG_ROW_ORACLE[precision]
+    _check_mantel((r, stats[:3], p), (r_o, stats_o, p), MANTEL_TOL[precision])
+    r3, stats3, _ = ub.unifrac_mantel(Xd, Yd, perms[:3])
+    assert r3 == r  # the identity's sum does not depend on the batch
+    np.testing.assert_array_equal(stats3, stats[:3])
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
