@@ -253,9 +253,10 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
  *
  * Method: subspace iteration with m = min(n, 2k + 16) columns, on the
  * device: the products with A in FP32 (cuBLAS SGEMM), the centring terms and
- * CholeskyQR2 orthonormalisation in FP64 (cuBLAS DSYRK / DTRSM); only m x m
- * work (Cholesky factors, the Jacobi eigensolver of the Ritz matrix) runs on
- * the host.  Allocates about 4 n^2 + 24 n m bytes of device memory while it
+ * CholeskyQR2 orthonormalisation in FP64 (Gram matrices and products with
+ * R^-1 by cuBLAS DGEMM); only m x m work (Cholesky factors and their
+ * inverses, the Jacobi eigensolver of the Ritz matrix) runs on the host.
+ * Allocates about 4 n^2 + 32 n m bytes of device memory while it
  * runs (UNIFRAC_E_OOM if that
  * fails).  Synchronous.  Errors: UNIFRAC_E_INVALID_ARG, UNIFRAC_E_OOM,
  * UNIFRAC_E_CUDA.  No context needed.

@@ -13,8 +13,8 @@
 // Device: A = -1/2 D o D in FP32 with FP64 row sums (one pass over D), every
 // A Q product (cuBLAS SGEMM, the pass over A that bounds the iteration), and
 // the n x m FP64 work -- the centring terms, orthonormalisation by shifted
-// CholeskyQR2 (the Gram matrix Y^T Y by DSYRK, its m x m Cholesky factor R on
-// the host, Y R^-1 by DTRSM; twice, the first factor shifted by a tiny
+// CholeskyQR2 (the Gram matrix Y^T Y and Y R^-1 by DGEMM, the m x m Cholesky
+// factor R and its inverse on the host; twice, the first factor shifted by a tiny
 // multiple of the trace so that a rank-deficient Y still factors) and the
 // Ritz products.  Host: only m x m work (Cholesky, the eigenproblem of
 // Q^T B Q by the cyclic Jacobi method).
@@ -109,6 +109,20 @@ std::vector<double> cholesky_upper(std::vector<double> G, int m, double shift) {
   return R;
 }
 
+// Inverse of the upper triangular m x m matrix R (column-major), by back
+// substitution column by column: R X = I.
+std::vector<double> upper_inverse(const std::vector<double> &R, int m) {
+  std::vector<double> X((size_t)m * m, 0.0);
+  for (int c = 0; c < m; ++c) {
+    for (int i = c; i >= 0; --i) {
+      double v = i == c ? 1.0 : 0.0;
+      for (int l = i + 1; l <= c; ++l) v -= R[(size_t)l * m + i] * X[(size_t)c * m + l];
+      X[(size_t)c * m + i] = v / R[(size_t)i * m + i];
+    }
+  }
+  return X;
+}
+
 // Cyclic Jacobi eigenvalue method (rotations zeroing each off-diagonal entry
 // in turn; Golub and Van Loan, Matrix Computations, 8.5) for the symmetric
 // m x m matrix T (row-major, destroyed).  Returns eigenvalues; V (row-major,
@@ -157,12 +171,12 @@ std::vector<double> jacobi_eigen(std::vector<double> &T, int m, std::vector<doub
 
 struct PcoaDev {
   float *A = nullptr, *Qf = nullptr, *Yf = nullptr;
-  double *Q = nullptr, *Y = nullptr, *r = nullptr, *ones = nullptr, *st = nullptr, *G = nullptr,
-         *U = nullptr;
+  double *Q = nullptr, *Y = nullptr, *W = nullptr, *r = nullptr, *ones = nullptr, *st = nullptr,
+         *G = nullptr, *U = nullptr;
   cublasHandle_t h = nullptr;
   ~PcoaDev() {
-    for (void *p : {(void *)A, (void *)Qf, (void *)Yf, (void *)Q, (void *)Y, (void *)r, (void *)ones,
-                    (void *)st, (void *)G, (void *)U})
+    for (void *p : {(void *)A, (void *)Qf, (void *)Yf, (void *)Q, (void *)Y, (void *)W, (void *)r,
+                    (void *)ones, (void *)st, (void *)G, (void *)U})
       if (p) cudaFree(p);
     if (h) cublasDestroy(h);
   }
@@ -189,6 +203,7 @@ extern "C" int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t 
       cudaMalloc(&dv.Yf, nm * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&dv.Q, nm * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&dv.Y, nm * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dv.W, nm * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&dv.U, (size_t)n * k * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&dv.r, (size_t)n * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&dv.ones, (size_t)n * sizeof(double)) != cudaSuccess ||
@@ -217,29 +232,32 @@ extern "C" int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t 
   const int grid = 148 * 8;
   const double d1 = 1.0, d0 = 0.0;
 
-  // Q <- Q R^-1 with Q^T Q = R^T R (CholeskyQR: Gram by DSYRK, the m x m
-  // factor on the host, the solve by DTRSM)
+  // M <- M R^-1 with M^T M = R^T R (CholeskyQR): the Gram matrix and the
+  // product with R^-1 are DGEMMs (their long dimension n parallelises; the
+  // triangular routines only parallelise over the m x m output), the factor
+  // and its inverse are m x m host work
   std::vector<double> Gh((size_t)m * m);
-  auto cholqr = [&](double *M, double shift) -> int {
-    if (cublasDsyrk(dv.h, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, m, n, &d1, M, n, &d0, dv.G, m) !=
+  auto cholqr = [&](double *&M, double shift) -> int {
+    if (cublasDgemm(dv.h, CUBLAS_OP_T, CUBLAS_OP_N, m, m, n, &d1, M, n, M, n, &d0, dv.G, m) !=
         CUBLAS_STATUS_SUCCESS)
       return UNIFRAC_E_CUDA;
     if (cudaMemcpyAsync(Gh.data(), dv.G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return UNIFRAC_E_CUDA;
-    for (int a = 0; a < m; ++a)  // mirror the upper triangle
-      for (int b = a + 1; b < m; ++b) Gh[(size_t)a * m + b] = Gh[(size_t)b * m + a];
-    std::vector<double> R = cholesky_upper(Gh, m, shift);
-    if (cudaMemcpyAsync(dv.G, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+    for (int a = 0; a < m; ++a)  // exact symmetry
+      for (int b = a + 1; b < m; ++b) Gh[(size_t)b * m + a] = Gh[(size_t)a * m + b];
+    const std::vector<double> Rinv = upper_inverse(cholesky_upper(Gh, m, shift), m);
+    if (cudaMemcpyAsync(dv.G, Rinv.data(), Rinv.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cublasDtrsm(dv.h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                    CUBLAS_DIAG_NON_UNIT, n, m, &d1, dv.G, m, M, n) != CUBLAS_STATUS_SUCCESS ||
-        cudaStreamSynchronize(st) != cudaSuccess)  // R (host) is copied before it goes out of scope
+        cublasDgemm(dv.h, CUBLAS_OP_N, CUBLAS_OP_N, n, m, m, &d1, M, n, dv.G, m, &d0, dv.W, n) !=
+            CUBLAS_STATUS_SUCCESS ||
+        cudaStreamSynchronize(st) != cudaSuccess)  // Rinv (host) is copied before it goes out of scope
       return UNIFRAC_E_CUDA;
+    std::swap(M, dv.W);
     return UNIFRAC_OK;
   };
-  auto orthonormalise = [&](double *M) -> int {
+  auto orthonormalise = [&](double *&M) -> int {
     int rc = cholqr(M, 1e-13);  // shifted first pass: factors even a rank-deficient M
     return rc ? rc : cholqr(M, 0.0);
   };
