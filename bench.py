@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--streamed-chunk", type=int, default=256,
+    ap.add_argument("--streamed-chunk", type=int, default=1024,
                     help="stripes per chunk of the streamed-output measurement")
     ap.add_argument("--mantel-perms", type=int, default=999,
                     help="permutations of the Mantel-test measurement (0 = skip it)")

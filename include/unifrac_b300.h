@@ -165,9 +165,11 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
  *   host_out caller-owned host buffer of >= unifrac_output_bytes(layout)
  *            (x2 for UNIFRAC_BOTH) bytes; pinned or pageable
  *
- * Each chunk's stripes are computed into a device buffer, copied to pinned
- * host memory on a copy stream while the next chunk computes, and scattered
- * into host_out by host threads.  The values are those of unifrac_run.
+ * The first chunk computes the embedding and packs the operands; later chunks
+ * reuse them and run only the pair kernels of their stripes.  Each chunk's
+ * stripes are computed into a device buffer, copied to pinned host memory on
+ * a copy stream while the next chunk computes, and merged into host_out by
+ * host threads.  The values are those of unifrac_run.
  * Single-study contexts only (UNIFRAC_E_UNSUPPORTED otherwise).  Synchronous:
  * returns when host_out is complete.  Keeps two device and two pinned host
  * chunk buffers in the context until it is destroyed.

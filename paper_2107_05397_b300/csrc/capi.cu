@@ -975,8 +975,10 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     // dense values for the frequently present positions, sparse blocks built
     // from the counts for the rest
     const int32_t k_end = P.n_win > 0 ? P.kf_words * WORD : ctx->K;
-    if ((rc = pack_weighted(ctx, cnt, flag, P.f64, V.vals.p, bits, k_end))) return rc;
-    if (P.n_win > 0) {
+    if (!ctx->reuse_prepared &&
+        (rc = pack_weighted(ctx, cnt, flag, P.f64, V.vals.p, bits, k_end)))
+      return rc;
+    if (P.n_win > 0 && !ctx->reuse_prepared) {
       uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
       if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, bits, rcb, nullptr))) return rc;
       if ((rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words, P.n_win,
@@ -1001,23 +1003,24 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     uint32_t *kbits = static_cast<uint32_t *>(V.bits.p);
     double *a = static_cast<double *>(V.persample.p);
     unsigned long long *aq = static_cast<unsigned long long *>(V.partial.p);
-    e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear per-sample sums");
-    if ((rc = pack_tc(ctx, cnt, flag, P.k_tc, X, D, kbits, aq))) return rc;
-    unsigned long long *spart = nullptr;
-    if (P.n_win > 0) {
-      uint32_t *rbits = static_cast<uint32_t *>(V.rbits.p);
-      uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
-      if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
-      if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
-                                  static_cast<uint32_t *>(V.bsize.p),
-                                  static_cast<unsigned long long *>(V.boff.p),
-                                  static_cast<uint2 *>(V.cpre.p),
-                                  static_cast<uint8_t *>(V.blocks.p))))
-        return rc;
-      spart = static_cast<unsigned long long *>(V.spart.p);
+    unsigned long long *spart = P.n_win > 0 ? static_cast<unsigned long long *>(V.spart.p) : nullptr;
+    if (!ctx->reuse_prepared) {
+      e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "clear per-sample sums");
+      if ((rc = pack_tc(ctx, cnt, flag, P.k_tc, X, D, kbits, aq))) return rc;
+      if (P.n_win > 0) {
+        uint32_t *rbits = static_cast<uint32_t *>(V.rbits.p);
+        uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
+        if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
+        if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
+                                    static_cast<uint32_t *>(V.bsize.p),
+                                    static_cast<unsigned long long *>(V.boff.p),
+                                    static_cast<uint2 *>(V.cpre.p),
+                                    static_cast<uint8_t *>(V.blocks.p))))
+          return rc;
+      }
+      if ((rc = finish_tc_a(ctx, aq, a))) return rc;
     }
-    if ((rc = finish_tc_a(ctx, aq, a))) return rc;
     if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 64.0;
@@ -1035,7 +1038,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     uint8_t *bytes = static_cast<uint8_t *>(V.vals.p);
     double *tables = static_cast<double *>(ctx->tables.p);
     uint32_t *gbits = static_cast<uint32_t *>(V.bits.p);
-    if ((rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a))) return rc;
+    if (!ctx->reuse_prepared && (rc = pack_lookup(ctx, cnt, flag, bytes, tables, gbits, a)))
+      return rc;
     if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 8.0;
@@ -1056,7 +1060,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
 static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
   int rc;
   record_event(ctx, ctx->ev[0]);
-  if ((rc = embed_counts(ctx, static_cast<uint32_t *>(ctx->cnt.p),
+  if (!ctx->reuse_prepared &&
+      (rc = embed_counts(ctx, static_cast<uint32_t *>(ctx->cnt.p),
                          static_cast<uint8_t *>(ctx->flag.p))))
     return rc;
   const bool overlap = n_plans == 2 && ctx->opt_overlap;
@@ -1157,6 +1162,25 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan *plans, int n_plans, in
   return UNIFRAC_OK;
 }
 
+// Addresses and sizes of the buffers a run prepares before its pair kernels
+// (the embedding and every variant's packed operands): equal signatures mean
+// none of them was reallocated since.
+static uint64_t prep_signature(const unifrac_ctx *ctx) {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over (address, size) pairs
+  auto mix = [&](const ufb::DevBuf &b) {
+    h = (h ^ (uint64_t)(uintptr_t)b.p) * 1099511628211ull;
+    h = (h ^ (uint64_t)b.bytes) * 1099511628211ull;
+  };
+  mix(ctx->cnt);
+  mix(ctx->flag);
+  mix(ctx->tables);
+  for (const ufb::VarBufs &V : ctx->vb)
+    for (const ufb::DevBuf *b : {&V.vals, &V.vals2, &V.bits, &V.persample, &V.partial, &V.rc, &V.bsize,
+                                 &V.boff, &V.blocks, &V.cpre, &V.rbits})
+      mix(*b);
+  return h;
+}
+
 static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe_start,
                     int32_t stripe_stop, int layout, void *out, size_t out_bytes) {
   if (variant != UNIFRAC_UNWEIGHTED && variant != UNIFRAC_WEIGHTED_NORMALIZED &&
@@ -1224,6 +1248,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
     plans[i].n_items = ctx->n_items;
     if ((rc = plan_buffers(ctx, plans[i]))) return rc;
   }
+  if (ctx->reuse_prepared && prep_signature(ctx) != ctx->prep_sig) ctx->reuse_prepared = false;
   if (!device_out && need > 0 && !whole) {  // untouched elements keep the caller's values
     cudaError_t e = cudaMemcpyAsync(dst, out, need, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stage output");
@@ -1387,36 +1412,61 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
     }
     ctx->chunk_host_bytes = chunk_bytes;
   }
-  // merge stripes [s0, s0 + rows) of chunk buffer b into the output
+  // Merge stripes [s0, s0 + rows) of chunk buffer b into the output.  Stripe
+  // s holds pair (k, (k + s + 1) mod n) at element k.  For output row rho
+  // (the smaller index) the chunk's pairs are (rho, rho + s + 1) from element
+  // rho (when rho + s + 1 < n) and (rho, rho + n - s - 1) from element
+  // rho + n - s - 1 (the wrapped ones, when rho <= s): for a fixed rho both
+  // are contiguous runs of the output row.  Work goes in 64 x 64 tiles of
+  // (rho, s), so that reads and writes both stay within a few KB.
   auto merge = [&](int b, int32_t s0, int32_t rows) {
+    constexpr int64_t kTile = 64;
+    const int64_t nrb = (n + kTile - 1) / kTile;
     const int T = host_threads((int64_t)rows * n);
     run_threads(T, [&](int t) {
       for (int v = 0; v < nv; ++v)
-        for (int32_t r = (int32_t)((int64_t)rows * t / T); r < (int32_t)((int64_t)rows * (t + 1) / T);
-             ++r) {
-          const int64_t s = s0 + r, base_in = ((int64_t)v * rows + r) * n;
-          for (int64_t k = 0; k < n; ++k) {
-            const int64_t j = (k + s + 1) % n, lo = std::min(k, j), hi = std::max(k, j);
-            if (layout == UNIFRAC_OUT_CONDENSED) {
-              const int64_t idx = v * per_matrix + lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
-              if (elem == 8)
-                static_cast<double *>(host_out)[idx] = static_cast<const double *>(ctx->chunk_host[b])[base_in + k];
-              else
-                static_cast<float *>(host_out)[idx] = static_cast<const float *>(ctx->chunk_host[b])[base_in + k];
-            } else {
-              const int64_t i1 = v * per_matrix + lo * n + hi, i2 = v * per_matrix + hi * n + lo;
-              if (elem == 8) {
-                const double x = static_cast<const double *>(ctx->chunk_host[b])[base_in + k];
-                static_cast<double *>(host_out)[i1] = x;
-                static_cast<double *>(host_out)[i2] = x;
-              } else {
-                const float x = static_cast<const float *>(ctx->chunk_host[b])[base_in + k];
-                static_cast<float *>(host_out)[i1] = x;
-                static_cast<float *>(host_out)[i2] = x;
+        for (int64_t rb = t; rb < nrb; rb += T)
+          for (int32_t sb = 0; sb < rows; sb += (int32_t)kTile) {
+            const int64_t rho1 = std::min(n, (rb + 1) * kTile);
+            const int32_t r1 = std::min(rows, sb + (int32_t)kTile);
+            for (int64_t rho = rb * kTile; rho < rho1; ++rho)
+              for (int32_t r = sb; r < r1; ++r) {
+                const int64_t s = s0 + r, in_row = ((int64_t)v * rows + r) * n;
+                for (int pass = 0; pass < 2; ++pass) {
+                  int64_t k, hi;
+                  if (pass == 0) {  // (rho, rho + s + 1) from element rho
+                    k = rho;
+                    hi = rho + s + 1;
+                    if (hi >= n) continue;
+                  } else {  // wrapped: (rho, rho + n - s - 1) from element rho + n - s - 1
+                    if (rho > s) continue;
+                    k = rho + n - s - 1;
+                    hi = k;
+                  }
+                  const int64_t lo = rho;
+                  if (layout == UNIFRAC_OUT_CONDENSED) {
+                    const int64_t idx = v * per_matrix + lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
+                    if (elem == 8)
+                      static_cast<double *>(host_out)[idx] =
+                          static_cast<const double *>(ctx->chunk_host[b])[in_row + k];
+                    else
+                      static_cast<float *>(host_out)[idx] =
+                          static_cast<const float *>(ctx->chunk_host[b])[in_row + k];
+                  } else {
+                    const int64_t i1 = v * per_matrix + lo * n + hi, i2 = v * per_matrix + hi * n + lo;
+                    if (elem == 8) {
+                      const double x = static_cast<const double *>(ctx->chunk_host[b])[in_row + k];
+                      static_cast<double *>(host_out)[i1] = x;
+                      static_cast<double *>(host_out)[i2] = x;
+                    } else {
+                      const float x = static_cast<const float *>(ctx->chunk_host[b])[in_row + k];
+                      static_cast<float *>(host_out)[i1] = x;
+                      static_cast<float *>(host_out)[i2] = x;
+                    }
+                  }
+                }
               }
-            }
           }
-        }
     });
   };
   const int saved_graph = ctx->opt_use_graph;
@@ -1432,9 +1482,13 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
         rc = cuda_fail(ctx, e, "chunk order");
         break;
       }
-      if ((rc = run_impl(ctx, variant, precision, s0, s1, UNIFRAC_OUT_STRIPES, ctx->chunk_dev[b].p,
-                         bytes)))
-        break;
+      // the first chunk embeds and packs; later ones reuse that (the pair
+      // kernels only read it), unless one of its buffers was reallocated
+      ctx->reuse_prepared = c > 0;
+      rc = run_impl(ctx, variant, precision, s0, s1, UNIFRAC_OUT_STRIPES, ctx->chunk_dev[b].p, bytes);
+      ctx->reuse_prepared = false;
+      if (rc) break;
+      if (c == 0) ctx->prep_sig = prep_signature(ctx);
       e = cudaEventRecord(ctx->ev_chunk_done[b], ctx->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_chunk_done[b], 0);
       if (e == cudaSuccess)

@@ -155,6 +155,11 @@ struct unifrac_ctx {
   int32_t gk_s0 = 0, gk_s1 = 0;
   void *gk_dst = nullptr;
   int64_t gk_opts = -1, opt_generation = 0, gk_bufs = -1, buf_generation = 0;
+  // set by the streamed run for its later chunks: the embedding and every
+  // variant's packed operands from the chunk before are still valid, so a run
+  // enqueues only the pair kernels of its stripe range
+  bool reuse_prepared = false;
+  uint64_t prep_sig = 0;  // addresses and sizes of those buffers when prepared
   double graph_launches = 0;
   bool capturing = false;
 
