@@ -105,22 +105,33 @@ def kernel_source_hash(kernel: str):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, workload: str, samples: int, thresholds: dict):
     """DRAM bytes (read + write) per launch from a committed ncu capture of the
-    bench workload, if the kernel's sources are unchanged since (else None)."""
+    same workload with the same dense / sparse split, if the kernel's sources
+    are unchanged since (else None)."""
     try:
-        rec = json.load(open(TRAFFIC_PATH)).get(kernel)
+        data = json.load(open(TRAFFIC_PATH))
     except Exception:
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
+    rec = data.get(kernel)
+    if (not rec or data.get("workload") != workload or data.get("samples") != samples
+            or data.get("thresholds") != thresholds
+            or rec.get("source_hash") != kernel_source_hash(kernel)):
         return None
     return rec.get("bytes_per_launch")
 
 
-def record_traffic(csv_path: str, workload: str, capture: str):
+def split_thresholds(sparse_fraction: float, uw_sparse_fraction: float, n_max: int) -> dict:
+    """The option values bench.py sets for the given split fractions."""
+    return {"sparse": max(1, int(round(sparse_fraction * n_max))),
+            "uw_sparse": 0 if uw_sparse_fraction == 0 else max(1, int(round(uw_sparse_fraction * n_max)))}
+
+
+def record_traffic(csv_path: str, workload: str, samples: int, capture: str, thresholds: dict):
     """Writes profiles/traffic.json from an ncu --csv capture with the metrics
     dram__bytes_read.sum and dram__bytes_write.sum: mean bytes per launch of
-    each pair kernel, with the hash of its current sources."""
+    each pair kernel, with the hash of its current sources and the split
+    thresholds of the captured run."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
@@ -136,7 +147,7 @@ def record_traffic(csv_path: str, workload: str, capture: str):
             continue
         per.setdefault(name, {}).setdefault(r[ii], 0.0)
         per[name][r[ii]] += float(r[vi].replace(",", ""))
-    out = {"workload": workload, "capture": capture}
+    out = {"workload": workload, "samples": samples, "capture": capture, "thresholds": thresholds}
     for name, launches in sorted(per.items()):
         vals = list(launches.values())
         out[name] = {"bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
@@ -368,10 +379,19 @@ def mantel_leg(args, w, stream, tuned_opts, peaks):
 def main():
     args = parse()
     if args.record_traffic:
-        return record_traffic(args.record_traffic, args.workload,
+        if args.sparse_fraction is None or args.uw_sparse_fraction is None:
+            raise SystemExit("--record-traffic needs the captured run's --sparse-fraction and "
+                             "--uw-sparse-fraction")
+        from paper_2107_05397_b300 import synth
+        tb = synth.make_workload(args.workload, n_samples=args.samples).table
+        n_max = (int(max(np.diff(tb.study_offsets))) if tb.study_offsets is not None
+                 else tb.n_samples)
+        return record_traffic(args.record_traffic, args.workload, tb.n_samples,
                               "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                               "--clock-control none -k regex:k_pairs on bench.py --workload "
-                              + args.workload)
+                              f"{args.workload} --sparse-fraction {args.sparse_fraction} "
+                              f"--uw-sparse-fraction {args.uw_sparse_fraction}",
+                              split_thresholds(args.sparse_fraction, args.uw_sparse_fraction, n_max))
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -502,6 +522,8 @@ def main():
     mean = lambda xs: float(np.mean(xs)) if xs else 0.0
     uw_ms, wn_ms = mean(pair_uw_ms), mean(pair_wn_ms)
     kernels = []
+    thresholds_now = {"sparse": ctx.get_option(ub.OPT_SPARSE_THRESHOLD),
+                      "uw_sparse": ctx.get_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD)}
 
     def entry(kernel, ms, work, bound, peak, unit, work_note, peak_note):
         if ms <= 0:
@@ -509,7 +531,8 @@ def main():
         ach = work / (ms / 1e3) / 1e12
         kernels.append({"kernel": kernel, "ms": ms, "bound": bound, "achieved": ach,
                         "peak": peak, "unit": unit, "frac": ach / peak,
-                        "traffic": recorded_traffic(kernel), "work": work_note,
+                        "traffic": recorded_traffic(kernel, w.name, N, thresholds_now),
+                        "work": work_note,
                         "peak_source": peak_note})
 
     entry("k_pairs_tc", uw_ms - mean(sp_uw_ms), 6.0 * mean(sel_uw), "tensor", tc_peak, "TFLOP/s",
