@@ -506,13 +506,40 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       const int nL = (int)(d & 0xffu), nT = (int)((d >> 8) & 0xffu);
       const bool laneJ = (d >> 16) != 0u;
       const int mL = laneJ ? 1 : kAccLd, mT = laneJ ? kAccLd : 1;  // accumulator strides
-      // copy the swept side into the scratch
+      // copy the swept side into the scratch: every load issued before the
+      // first store (one memory round trip, not one per 32 entries); the
+      // weighted lane side's first entry is loaded alongside
+      unsigned long long eb0 = 0;
+      const int b0 = nL <= 32 ? (int)(divtab[nL - 1][lane] & 0xffu) : lane;
       if constexpr (PRES) {
         const uint8_t *rT = (laneJ ? riI : riJ) + bsT;
-        for (int x = lane; x < nT; x += 32) rS[x] = __ldg(rT + x);
+        if (b0 < nL) eb0 = __ldg((laneJ ? riJ : riI) + bsL + b0);
+        uint8_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+        if (lane < nT) r0 = __ldg(rT + lane);
+        if (lane + 32 < nT) r1 = __ldg(rT + lane + 32);
+        if (lane + 64 < nT) r2 = __ldg(rT + lane + 64);
+        if (lane + 96 < nT) r3 = __ldg(rT + lane + 96);
+        if (lane < nT) rS[lane] = r0;
+        if (lane + 32 < nT) rS[lane + 32] = r1;
+        if (lane + 64 < nT) rS[lane + 64] = r2;
+        if (lane + 96 < nT) rS[lane + 96] = r3;
       } else {
         const unsigned long long *qT = (laneJ ? eI : eJ) + bsT;
-        for (int x = lane; x < nT; x += 32) eS[x] = __ldg(qT + x);
+        if (b0 < nL) eb0 = __ldg((laneJ ? eJ : eI) + bsL + b0);
+        unsigned long long t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        if (lane < nT) t0 = __ldg(qT + lane);
+        if (lane + 32 < nT) t1 = __ldg(qT + lane + 32);
+        if (lane + 64 < nT) t2 = __ldg(qT + lane + 64);
+        if (lane + 96 < nT) t3 = __ldg(qT + lane + 96);
+        // stored ready for the sweep: (accumulator offset of the row, value)
+        uint2 *eS2 = reinterpret_cast<uint2 *>(eS);
+        auto prep = [mT](unsigned long long e) {
+          return make_uint2((uint32_t)(e & 0xffu) * (uint32_t)mT, (uint32_t)(e >> 32));
+        };
+        if (lane < nT) eS2[lane] = prep(t0);
+        if (lane + 32 < nT) eS2[lane + 32] = prep(t1);
+        if (lane + 64 < nT) eS2[lane + 64] = prep(t2);
+        if (lane + 96 < nT) eS2[lane + 96] = prep(t3);
       }
       __syncwarp();
       int g, G, b;
@@ -529,18 +556,19 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       for (; b < nL; b += 32) {  // one pass when nL <= 32
         if (g < G) {
           if constexpr (PRES) {
-            const int base = (int)__ldg((laneJ ? riJ : riI) + bsL + b) * mL;
+            const int base = (int)(b < 32 ? eb0 : __ldg((laneJ ? riJ : riI) + bsL + b)) * mL;
 #pragma unroll 2
             for (int a = g; a < nT; a += G)
               atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
           } else {
-            const unsigned long long eb = __ldg((laneJ ? eJ : eI) + bsL + b);
-            const int base = (int)(uint32_t)(eb & 0xffu) * mL;
+            const unsigned long long eb = b < 32 ? eb0 : __ldg((laneJ ? eJ : eI) + bsL + b);
+            uint32_t *row = sacc + (uint32_t)(eb & 0xffu) * (uint32_t)mL;
             const uint32_t vb = (uint32_t)(eb >> 32);
-#pragma unroll 2
+            const uint2 *eS2 = reinterpret_cast<const uint2 *>(eS);
+#pragma unroll 4
             for (int a = g; a < nT; a += G) {
-              const unsigned long long e = eS[a];
-              atomicAdd(&sacc[base + (int)(uint32_t)(e & 0xffu) * mT], min(vb, (uint32_t)(e >> 32)));
+              const uint2 e = eS2[a];
+              atomicAdd(row + e.x, min(vb, e.y));
             }
           }
         }
