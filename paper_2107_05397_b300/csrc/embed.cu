@@ -62,17 +62,28 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
   const int32_t t = (int32_t)(item % n_tiles);
   uint4 s = make_uint4(0u, 0u, 0u, 0u);
   bool any = false;
-  const int32_t c1 = child_ptr[node + 1];
-  for (int32_t c = child_ptr[node]; c < c1; ++c) {
-    const int32_t ch = child_idx[c];
-    if (flag[(int64_t)ch * n_tiles + t]) {
-      any = true;
-      const uint4 v =
-          reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + (int64_t)t * TILE)[lane];
-      s.x += v.x;
-      s.y += v.y;
-      s.z += v.z;
-      s.w += v.w;
+  const int32_t c0 = child_ptr[node], c1 = child_ptr[node + 1];
+  // up to four children at a time: their indices, then their flags, then
+  // their rows, each group of loads in flight together
+  for (int32_t c = c0; c < c1; c += 4) {
+    int32_t ch[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ch[u] = c + u < c1 ? child_idx[c + u] : -1;
+    bool f[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) f[u] = ch[u] >= 0 && flag[(int64_t)ch[u] * n_tiles + t] != 0;
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = f[u] ? reinterpret_cast<const uint4 *>(cnt + (int64_t)ch[u] * ldc + (int64_t)t * TILE)[lane]
+                  : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      any |= f[u];
+      s.x += v[u].x;
+      s.y += v[u].y;
+      s.z += v[u].z;
+      s.w += v[u].w;
     }
   }
   if (lane == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
