@@ -140,3 +140,33 @@ def test_binding_constants_match_header_enums():
     n = ub.MANTEL_MAX_SAMPLES
     assert n * (n - 1) // 2 < 2**32 <= (n + 1) * n // 2  # largest n whose pair indices fit 32 bits
     assert checked >= 25
+
+
+def test_downstream_bindings_reject_host_tensors_before_the_library():
+    """PCoA and the Mantel test take device matrices: host tensors, mixed
+    dtypes, non-square sizes and unknown methods are refused in the binding,
+    with no library call (no GPU needed)."""
+    import torch
+    D = torch.zeros((6, 6), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        ub.unifrac_pcoa(D, k=2)
+    with pytest.raises(ValueError):
+        ub.unifrac_mantel(D, D, np.tile(np.arange(6, dtype=np.int32), (2, 1)))
+    with pytest.raises(ValueError):
+        ub.unifrac_mantel(D, D.double(), np.zeros((1, 6), np.int32))
+
+
+def test_mantel_declaration_matches_binding_argtypes():
+    """The ctypes prototype of unifrac_mantel has the header's eleven
+    parameters in order (pointer, pointer, int, int32, pointer, int32, int,
+    then four pointers)."""
+    import ctypes
+    lib = ub.load()
+    at = lib.unifrac_mantel.argtypes
+    assert len(at) == 11
+    assert at[2] is ctypes.c_int and at[3] is ctypes.c_int32 and at[5] is ctypes.c_int32
+    assert at[6] is ctypes.c_int
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "unifrac_b300.h")).read()
+    decl = text[text.index("int unifrac_mantel("):]
+    decl = decl[:decl.index(";")]
+    assert decl.count(",") == 10
