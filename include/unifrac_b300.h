@@ -307,6 +307,19 @@ int unifrac_mantel(const void *x, const void *y, int precision, int32_t n, const
                    int32_t n_perms, int method, double *r, double *perm_stats, double *p_value,
                    void *cuda_stream);
 
+/*
+ * unifrac_check_bounded_wait -- runs the library's bounded device-side wait
+ * (the one every mbarrier wait of the tensor-core kernel uses, there with a
+ * 1 s limit) on an mbarrier that nothing arrives at, with a limit of
+ * `limit_us` microseconds (1 .. 1,000,000), so that the wait runs out; one
+ * thread of one CTA, no copies or tensor memory involved.  *status receives
+ * the code the kernel recorded: UNIFRAC_E_DEVICE_TIMEOUT when the bound works.
+ * The call returns UNIFRAC_OK when the kernel ran to its end (the device stays
+ * usable), UNIFRAC_E_INVALID_ARG, UNIFRAC_E_OOM or UNIFRAC_E_CUDA otherwise.
+ * Synchronous.  No context needed.
+ */
+int unifrac_check_bounded_wait(uint32_t limit_us, int32_t *status, void *cuda_stream);
+
 /* Statistics of the context / its last run. */
 enum unifrac_stat {
   UNIFRAC_STAT_KERNEL_LAUNCHES = 0, /* kernels launched by the last run */

@@ -62,7 +62,8 @@ STAT_MAX_REACH = 21
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",
             "unifrac_set_option", "unifrac_get_option", "unifrac_get_stat",
-            "unifrac_autotune", "unifrac_run_streamed", "unifrac_pcoa", "unifrac_mantel")
+            "unifrac_autotune", "unifrac_run_streamed", "unifrac_pcoa", "unifrac_mantel",
+            "unifrac_check_bounded_wait")
 
 
 class UniFracError(RuntimeError):
@@ -102,6 +103,8 @@ def load() -> ctypes.CDLL:
         lib.unifrac_mantel.argtypes = [vp, vp, ctypes.c_int, i32, vp, i32, ctypes.c_int, vp, vp,
                                        vp, vp]
         lib.unifrac_mantel.restype = ctypes.c_int
+        lib.unifrac_check_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.POINTER(i32), vp]
+        lib.unifrac_check_bounded_wait.restype = ctypes.c_int
         lib.unifrac_destroy.argtypes = [vp]
         lib.unifrac_destroy.restype = None
         lib.unifrac_strerror.argtypes = [ctypes.c_int]
@@ -282,6 +285,16 @@ def unifrac_mantel(x, y, perms, method: str = "pearson", stream=None):
         _stream_handle(stream))
     _check(status)
     return float(r.value), stats, float(p.value)
+
+
+def unifrac_check_bounded_wait(limit_us: int, stream=None) -> int:
+    """Runs the device-side bounded wait on an mbarrier that nothing
+    completes; returns the status the kernel recorded (UNIFRAC_E_DEVICE_TIMEOUT
+    = -8 when the bound works)."""
+    status = ctypes.c_int32(0)
+    _check(load().unifrac_check_bounded_wait(int(limit_us), ctypes.byref(status),
+                                             _stream_handle(stream)))
+    return int(status.value)
 
 
 def unifrac_destroy(ctx) -> None:

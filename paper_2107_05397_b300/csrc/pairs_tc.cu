@@ -105,19 +105,40 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait on an mbarrier phase.  Returns false if the CTA is aborting or
-// the wait exceeded WAIT_NS (then records the timeout and raises the abort).
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int32_t *abort,
-                          unsigned long long *err) {
+// the wait exceeded limit_ns of %globaltimer (or, as a backstop, kWaitPolls
+// polls): then it records the timeout and raises the abort.
+constexpr uint64_t kWaitPolls = 1ull << 26;
+
+__device__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, volatile int32_t *abort,
+                                unsigned long long *err, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  while (true) {
+  for (uint64_t polls = 0;; ++polls) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > WAIT_NS) {
+    if (global_ns() - t0 > limit_ns || polls >= kWaitPolls) {
       *abort = 1;
       if (err) atomicExch(err, (unsigned long long)(-UNIFRAC_E_DEVICE_TIMEOUT));
       return false;
     }
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int32_t *abort,
+                                          unsigned long long *err) {
+  return mbar_wait_limit(bar, parity, abort, err, WAIT_NS);
+}
+
+// The bounded wait run out on purpose: thread 0 waits on an mbarrier that
+// nothing arrives at, with a short limit, and stores the status it recorded.
+__global__ void k_wait_check(uint64_t limit_ns, unsigned long long *err) {
+  __shared__ uint64_t bar;
+  __shared__ int32_t abort;
+  if (threadIdx.x == 0) {
+    abort = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_wait_limit(&bar, 0, &abort, err, limit_ns);
   }
 }
 
@@ -550,3 +571,26 @@ int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *
 }
 
 }  // namespace ufb
+
+extern "C" int unifrac_check_bounded_wait(uint32_t limit_us, int32_t *status, void *cuda_stream) {
+  if (!status || limit_us == 0 || limit_us > 1000000u) return UNIFRAC_E_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long *d_err = nullptr;
+  if (cudaMalloc(&d_err, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return UNIFRAC_E_OOM;
+  }
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(h), st);
+  if (e == cudaSuccess) {
+    ufb::k_wait_check<<<1, 32, 0, st>>>((uint64_t)limit_us * 1000ull, d_err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return UNIFRAC_E_CUDA;
+  *status = -(int32_t)h;
+  return UNIFRAC_OK;
+}
+

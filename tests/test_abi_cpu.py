@@ -170,3 +170,12 @@ def test_mantel_declaration_matches_binding_argtypes():
     decl = text[text.index("int unifrac_mantel("):]
     decl = decl[:decl.index(";")]
     assert decl.count(",") == 10
+
+
+def test_bounded_wait_check_rejects_bad_limits():
+    """Limits outside 1 .. 1,000,000 microseconds are refused before any
+    device call."""
+    for bad in (0, 1_000_001):
+        with pytest.raises(ub.UniFracError) as ei:
+            ub.unifrac_check_bounded_wait(bad)
+        assert ei.value.status == -1

@@ -829,3 +829,21 @@ def test_mantel_large_matrices_sampled_permutations():
     perms = _mantel_perms(n, 2, 71)
     got = ub.unifrac_mantel(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), perms)
     _check_mantel(got, _mantel_oracle(X, Y, perms, "pearson"), MANTEL_TOL[ub.MIXED])
+
+
+# ------------------------------------------------------------------ bounded device waits
+
+def test_bounded_wait_runs_out_and_device_stays_usable(small):
+    """The bounded mbarrier wait of the tensor-core kernel, run on a barrier
+    that nothing completes with a 20 ms limit, gives up and records
+    UNIFRAC_E_DEVICE_TIMEOUT; the device then computes as before."""
+    import time
+    t0 = time.perf_counter()
+    status = ub.unifrac_check_bounded_wait(20000)
+    elapsed = time.perf_counter() - t0
+    assert status == -8  # UNIFRAC_E_DEVICE_TIMEOUT
+    assert 0.02 <= elapsed < 5.0
+    w, ref = small
+    N = w.table.n_samples
+    got = run(w.tree, w.table, ub.UNWEIGHTED, ub.MIXED).reshape(N, N)
+    check_full(got, ref[ub.UNWEIGHTED], ub.MIXED)
