@@ -847,3 +847,34 @@ def test_bounded_wait_runs_out_and_device_stays_usable(small):
     N = w.table.n_samples
     got = run(w.tree, w.table, ub.UNWEIGHTED, ub.MIXED).reshape(N, N)
     check_full(got, ref[ub.UNWEIGHTED], ub.MIXED)
+
+
+def test_mantel_batches_beyond_one_launch():
+    """1,048,600 permutations of 3 samples: 65,538 batches of 16, more than
+    one launch's 65,535 grid rows, so the cross sums run as two launches.
+    Each of the six distinct relabellings is evaluated by the oracle once."""
+    import itertools
+    import torch
+    from oracle import mantel as om
+    X, Y = _point_matrices(3, 90, np.float64)
+    iu = np.triu_indices(3, 1)
+    distinct = np.array(list(itertools.permutations(range(3))), dtype=np.int32)
+    pick = np.random.default_rng(91).integers(0, 6, size=1_048_600)
+    perms = distinct[pick]
+    r, stats, p = ub.unifrac_mantel(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), perms)
+    r_o, stats6, _ = om.mantel(X[iu], Y[iu], 3, distinct)
+    assert abs(r - r_o) <= 1e-12
+    np.testing.assert_allclose(stats, stats6[pick], rtol=0, atol=1e-12)
+    hits = np.count_nonzero(np.abs(stats6[pick]) >= abs(r_o))
+    assert p == (1.0 + hits) / (len(perms) + 1.0)
+
+
+def test_pcoa_all_components():
+    """k = n (the subspace is the whole space): every eigenvalue of the
+    double-centred matrix, against the oracle."""
+    import torch
+    from oracle import pcoa as opc
+    X, _ = _point_matrices(12, 92, np.float64)
+    lam, C = ub.unifrac_pcoa(torch.from_numpy(X).cuda(), k=12, iters=4, seed=3)
+    lam_o, _ = opc.pcoa(X, 12)
+    np.testing.assert_allclose(lam, lam_o, rtol=1e-5, atol=1e-6 * abs(lam_o[0]))
