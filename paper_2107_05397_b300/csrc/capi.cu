@@ -474,139 +474,78 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
                   "sample " + std::to_string(i) + " has a total count >= 2^32");
   ctx->n_frows = (int32_t)frow_tip.size();
   // ------------------------------------------- presence counts and pruning
-  // n_b: the samples with a non-zero count below branch b.  Bitsets of those
-  // samples per node over blocks of columns: a tip's bits come from its table
-  // row (rows are column-sorted, so a block's entries are found by binary
-  // search), an internal node's are the OR of its children's (every node ORed
-  // into its parent in postorder).  Host threads take whole blocks, each with
-  // its own bitsets and counts, merged at the end.  Studies start on
-  // 128-column boundaries, so a study's count at a node is a popcount over
-  // whole 64-bit words.  The most branches one sample reaches (the exactness
-  // bound of the tensor-core path) comes from bit-sliced column counters.
+  // n_b: the samples with a non-zero count below branch b, per study, from
+  // per-node sample bitsets built on the device (tips from their table rows,
+  // internal nodes as the OR of their children, level by level), popcounted
+  // over each study's columns; with the tree's size above the tensor-core
+  // exactness bound, also the most branches one sample reaches.  The device
+  // needs the tree, its levels and the table rows for this, so they are
+  // uploaded here.
+  double dev_ms = 0.0;
   ctx->nb.assign(n_nodes, 0);
   double pair_branch = 0.0, useful = 0.0;
+  int rc;
   {
-    const int32_t W = ctx->n_cols / 64;
-    // block width: enough blocks for every thread, and at most
-    // max(16 words, ~8 MiB of bitsets) per block
-    const int T_hw = host_threads((int64_t)n_nodes * std::max(W, 1));
-    const int64_t wb_max = std::max<int64_t>(16, ((int64_t)8 << 20) / (8 * (int64_t)n_nodes));
-    int32_t WB = (int32_t)std::min<int64_t>(W, std::min<int64_t>(wb_max, (W + T_hw - 1) / T_hw));
-    WB = std::max<int32_t>(std::min<int32_t>(W, 2), WB + (WB & 1));  // whole 128-column tiles
-    const int32_t n_blocks = WB > 0 ? (W + WB - 1) / WB : 0;
-    const int T = std::max(1, std::min<int>(T_hw, n_blocks));
-    constexpr int kPlanes = 32;
+    const auto t_dev0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&ctx->device) != cudaSuccess)
+      return fail(ctx, UNIFRAC_E_CUDA, "no CUDA device");
+    const cudaError_t e =
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device attribute");
+    if ((rc = upload(ctx, &ctx->d_level_nodes, level_nodes))) return rc;
+    if ((rc = upload(ctx, &ctx->d_level_ptr, ctx->level_ptr))) return rc;
+    if ((rc = upload(ctx, &ctx->d_child_ptr, child_ptr))) return rc;
+    if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
+    if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
+    if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
+    if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
     // a sample reaches at most root branches: count exactly only when that
     // bound does not already settle the tensor-core exactness test
     const bool count_reach = (int64_t)root >= 65793;
     if (!count_reach) ctx->max_reach = root;
-    std::vector<int32_t> sw0(n_studies), sw1(n_studies);
+    std::vector<int32_t> sw(2 * (size_t)n_studies);  // 64-bit word range of each study
     for (int32_t st = 0; st < n_studies; ++st) {
-      sw0[st] = ctx->study_col0[st] / 64;
-      sw1[st] = sw0[st] + (int32_t)(((int64_t)(soff[st + 1] - soff[st]) + TILE - 1) / TILE * 2);
+      sw[2 * st] = ctx->study_col0[st] / 64;
+      sw[2 * st + 1] =
+          sw[2 * st] + (int32_t)(((int64_t)(soff[st + 1] - soff[st]) + TILE - 1) / TILE * 2);
     }
-    struct Worker {
-      std::unique_ptr<uint64_t[]> bits;
-      std::vector<int64_t> nb;
-      std::vector<std::vector<int32_t>> acc;  // per study, for the studies it touched
-      std::vector<uint64_t> planes;
-      int64_t max_reach = 0;
-    };
-    std::vector<Worker> wk(T);
-    std::atomic<int32_t> next{0};
-    run_threads(T, [&](int t) {
-      Worker &w = wk[t];
-      if (n_blocks == 0) return;
-      w.bits.reset(new uint64_t[(size_t)n_nodes * WB]);
-      w.nb.assign(n_nodes, 0);
-      w.acc.resize(n_studies);
-      uint64_t *bits = w.bits.get();
-      for (int32_t blk; (blk = next.fetch_add(1)) < n_blocks;) {
-        const int32_t b0 = blk * WB, b1 = std::min(W, b0 + WB), wb = b1 - b0;
-        std::memset(bits, 0, sizeof(uint64_t) * (size_t)n_nodes * WB);
-        for (int32_t r = 0; r < ctx->n_frows; ++r) {
-          const int32_t *c0 = fent_col.data() + frow_ptr[r], *c1 = fent_col.data() + frow_ptr[r + 1];
-          uint64_t *d = &bits[(size_t)frow_tip[r] * WB];
-          for (const int32_t *c = std::lower_bound(c0, c1, 64 * b0); c < c1 && *c < 64 * b1; ++c)
-            d[*c / 64 - b0] |= 1ull << (*c & 63);
-        }
-        for (int32_t v = 0; v < root; ++v) {  // postorder: children before parents
-          const uint64_t *src = &bits[(size_t)v * WB];
-          uint64_t *d = &bits[(size_t)parent[v] * WB];
-          for (int32_t j = 0; j < wb; ++j) d[j] |= src[j];
-        }
-        int32_t s_lo = 0;  // studies intersecting the block: [s_lo, s_hi)
-        while (s_lo < n_studies && sw1[s_lo] <= b0) ++s_lo;
-        int32_t s_hi = s_lo;
-        while (s_hi < n_studies && sw0[s_hi] < b1) ++s_hi;
-        for (int32_t st = s_lo; st < s_hi; ++st)
-          if (sw1[st] > sw0[st] && w.acc[st].empty()) w.acc[st].assign(n_nodes, 0);
-        if (count_reach) w.planes.assign((size_t)kPlanes * wb, 0ull);
-        for (int32_t v = 0; v < root; ++v) {
-          const uint64_t *d = &bits[(size_t)v * WB];
-          int64_t all = 0;
-          for (int32_t j = 0; j < wb; ++j) {
-            uint64_t x = d[j];
-            all += __builtin_popcountll(x);
-            if (!count_reach) continue;
-            for (int p = 0; x && p < kPlanes; ++p) {  // carry-save add into the planes
-              const uint64_t c = w.planes[(size_t)p * wb + j] & x;
-              w.planes[(size_t)p * wb + j] ^= x;
-              x = c;
-            }
-          }
-          if (!all) continue;
-          w.nb[v] += all;
-          for (int32_t st = s_lo; st < s_hi; ++st) {
-            const int32_t j0 = std::max(sw0[st], b0) - b0, j1 = std::min(sw1[st], b1) - b0;
-            int32_t c = 0;
-            for (int32_t j = j0; j < j1; ++j) c += __builtin_popcountll(d[j]);
-            if (c) w.acc[st][v] += c;
-          }
-        }
-        if (count_reach)
-          for (int32_t j = 0; j < wb; ++j)
-            for (int q = 0; q < 64; ++q) {
-              int64_t r = 0;
-              for (int p = 0; p < kPlanes; ++p)
-                r += (int64_t)((w.planes[(size_t)p * wb + j] >> q) & 1ull) << p;
-              w.max_reach = std::max(w.max_reach, r);
-            }
-      }
-    });
-    // merge: node counts, then per study (studies' statistics in study order)
-    std::vector<int32_t> a(n_nodes);
-    for (auto &w : wk) {
-      for (int32_t v = 0; v < root && !w.nb.empty(); ++v) ctx->nb[v] += w.nb[v];
-      ctx->max_reach = std::max(ctx->max_reach, w.max_reach);
-    }
-    for (int32_t st = 0; st < n_studies; ++st) {
-      std::fill(a.begin(), a.end(), 0);
-      bool any = false;
-      for (auto &w : wk)
-        if (st < (int32_t)w.acc.size() && !w.acc[st].empty()) {
-          any = true;
-          for (int32_t v = 0; v < root; ++v) a[v] += w.acc[st][v];
-          std::vector<int32_t>().swap(w.acc[st]);
-        }
+    std::vector<int32_t> acc;
+    int64_t reach = 0;
+    if ((rc = presence_counts(ctx, sw, count_reach, acc, &reach))) return rc;
+    if (count_reach) ctx->max_reach = reach;
+    for (int32_t st = 0; st < n_studies; ++st) {  // statistics in study order
+      const int32_t *a = acc.data() + (size_t)st * n_nodes;
       int64_t B_s = 0;
-      if (any)
-        for (int32_t v = 0; v < root; ++v)
-          if (a[v] > 0 && length[v] > 0.0) {
-            B_s++;
-            useful += 0.5 * (double)a[v] * (double)(a[v] - 1);
-          }
+      for (int32_t v = 0; v < root; ++v) {
+        ctx->nb[v] += a[v];
+        if (a[v] > 0 && length[v] > 0.0) {
+          B_s++;
+          useful += 0.5 * (double)a[v] * (double)(a[v] - 1);
+        }
+      }
       const double n_s = (double)(soff[st + 1] - soff[st]);
       pair_branch += 0.5 * n_s * (n_s - 1.0) * (double)B_s;
     }
+    dev_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_dev0).count();
   }
   ctx->stat_pair_branch = pair_branch;
   ctx->stat_useful = useful;
+  // kept branches by presence count, descending, ties in node order: a
+  // stable counting sort (counts are at most n_samples)
   std::vector<int32_t> perm;
-  for (int32_t v = 0; v < root; ++v)
-    if (ctx->nb[v] > 0 && length[v] > 0.0) perm.push_back(v);
-  std::stable_sort(perm.begin(), perm.end(),
-                   [&](int32_t x, int32_t y) { return ctx->nb[x] > ctx->nb[y]; });
+  {
+    std::vector<int64_t> start((size_t)n_samples + 2, 0);
+    int64_t kept = 0;
+    for (int32_t v = 0; v < root; ++v)
+      if (ctx->nb[v] > 0 && length[v] > 0.0) {
+        start[(size_t)(n_samples - ctx->nb[v]) + 1]++;  // bucket n_samples - nb: larger counts first
+        kept++;
+      }
+    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+    perm.resize((size_t)kept);
+    for (int32_t v = 0; v < root; ++v)
+      if (ctx->nb[v] > 0 && length[v] > 0.0) perm[(size_t)start[(size_t)(n_samples - ctx->nb[v])]++] = v;
+  }
   ctx->K = (int32_t)perm.size();
   ctx->nb_perm.resize(perm.size());
   for (size_t k = 0; k < perm.size(); ++k) ctx->nb_perm[k] = ctx->nb[perm[k]];
@@ -676,22 +615,10 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       for (int32_t col = 0; col < ctx->n_cols; ++col) S[col] += part[c][col];
   }
   for (int32_t c = 0; c < ctx->n_cols; ++c) S[c] *= inv_total[c];
-  ctx->create_host_ms = ms_since(t_create0);
+  ctx->create_host_ms = ms_since(t_create0) - dev_ms;
 
   // ---------------------------------------------------------------- device
-  if (cudaGetDevice(&ctx->device) != cudaSuccess)
-    return fail(ctx, UNIFRAC_E_CUDA, "no CUDA device");
-  cudaError_t e =
-      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "device attribute");
-  int rc;
-  if ((rc = upload(ctx, &ctx->d_level_nodes, level_nodes))) return rc;
-  if ((rc = upload(ctx, &ctx->d_level_ptr, ctx->level_ptr))) return rc;
-  if ((rc = upload(ctx, &ctx->d_child_ptr, child_ptr))) return rc;
-  if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
-  if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
-  if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
-  if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
+  cudaError_t e;
   if ((rc = upload(ctx, &ctx->d_fent_cnt, fent_cnt))) return rc;
   if ((rc = upload(ctx, &ctx->d_inv_total, inv_total))) return rc;
   if ((rc = upload(ctx, &ctx->d_S, S))) return rc;

@@ -15,6 +15,8 @@
 // whose children are all zero are neither read nor written (the sparse-aware
 // step: most features are absent from most samples).  Counts are summed as
 // exact integers; the division by the sample total happens once, in packing.
+#include <algorithm>
+
 #include "ufb_internal.cuh"
 
 namespace ufb {
@@ -591,6 +593,174 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
   ctx->stat_launches += 3;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse blocks");
+  return UNIFRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Presence counts at create: bits[v][w] (u64, W words per node) has bit c of
+// word w set when column 64 w + c has a non-zero count below node v.  Tips
+// from their table rows, internal nodes as the OR of their children level by
+// level (the embedding's level structure), then per node and study the
+// popcount over the study's words, and per column the number of nodes it
+// reaches.
+
+namespace {
+
+__global__ void k_pres_tips(int32_t n_frows, const int32_t *__restrict__ frow_tip,
+                            const int64_t *__restrict__ frow_ptr,
+                            const int32_t *__restrict__ fent_col, unsigned long long *bits,
+                            int32_t W) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_frows) return;
+  unsigned long long *row = bits + (int64_t)frow_tip[r] * W;
+  for (int64_t e = frow_ptr[r] + lane; e < frow_ptr[r + 1]; e += 32) {
+    const int32_t c = fent_col[e];
+    atomicOr(row + (c >> 6), 1ull << (c & 63));
+  }
+}
+
+__global__ void k_pres_level(const int32_t *__restrict__ nodes, int32_t n_level,
+                             const int32_t *__restrict__ child_ptr,
+                             const int32_t *__restrict__ child_idx, unsigned long long *bits,
+                             int32_t W) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (int64_t)n_level * W) return;
+  const int32_t node = nodes[x / W];
+  const int32_t w = (int32_t)(x % W);
+  unsigned long long s = 0ull;
+  for (int32_t c = child_ptr[node]; c < child_ptr[node + 1]; ++c)
+    s |= bits[(int64_t)child_idx[c] * W + w];
+  bits[(int64_t)node * W + w] = s;
+}
+
+// Levels [L0, L1) in one launch: CTA b owns words [32 b, 32 b + 32) of every
+// node and walks the levels in order, a barrier between levels (a level reads
+// only what earlier levels wrote for the same words).  Plain loads: the data
+// were written by this CTA.
+__global__ void __launch_bounds__(1024) k_pres_levels_tail(
+    const int32_t *__restrict__ nodes, const int32_t *__restrict__ level_ptr, int32_t L0,
+    int32_t L1, const int32_t *__restrict__ child_ptr, const int32_t *__restrict__ child_idx,
+    unsigned long long *bits, int32_t W) {
+  const int32_t w0 = blockIdx.x * 32;
+  for (int32_t L = L0; L < L1; ++L) {
+    const int32_t lo = level_ptr[L], hi = level_ptr[L + 1];
+    for (int64_t x = threadIdx.x; x < (int64_t)(hi - lo) * 32; x += blockDim.x) {
+      const int32_t node = nodes[lo + (int32_t)(x >> 5)];
+      const int32_t w = w0 + (int32_t)(x & 31);
+      if (w >= W) continue;
+      unsigned long long s = 0ull;
+      for (int32_t c = child_ptr[node]; c < child_ptr[node + 1]; ++c)
+        s |= bits[(int64_t)child_idx[c] * W + w];
+      bits[(int64_t)node * W + w] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// acc[s][v] = samples of study s with a non-zero count below node v (one warp
+// per node; sw[2 s], sw[2 s + 1]: the study's word range).
+__global__ void k_pres_counts(const unsigned long long *__restrict__ bits, int32_t W,
+                              int32_t n_count, int32_t n_studies, const int32_t *__restrict__ sw,
+                              int32_t *__restrict__ acc, int32_t n_nodes) {
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= n_count) return;
+  const unsigned long long *row = bits + v * W;
+  for (int32_t s = 0; s < n_studies; ++s) {
+    int c = 0;
+    for (int32_t w = sw[2 * s] + lane; w < sw[2 * s + 1]; w += 32) c += __popcll(row[w]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) acc[(int64_t)s * n_nodes + v] = c;
+  }
+}
+
+// reach[c] += nodes of [v0, v1) whose bitset has column c (blockIdx.y takes a
+// slice of the nodes; a warp's 32 columns share one word).
+__global__ void k_pres_reach(const unsigned long long *__restrict__ bits, int32_t W,
+                             int32_t n_count, int32_t n_cols, int32_t *__restrict__ reach) {
+  const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cols) return;
+  const int32_t v0 = (int32_t)((int64_t)n_count * blockIdx.y / gridDim.y);
+  const int32_t v1 = (int32_t)((int64_t)n_count * (blockIdx.y + 1) / gridDim.y);
+  const int32_t w = c >> 6, b = c & 63;
+  int32_t r = 0;
+  for (int32_t v = v0; v < v1; ++v) r += (int32_t)((bits[(int64_t)v * W + w] >> b) & 1ull);
+  if (r) atomicAdd(reach + c, r);
+}
+
+struct PresTemp {
+  void *p[4] = {nullptr, nullptr, nullptr, nullptr};
+  ~PresTemp() {
+    for (void *q : p)
+      if (q) cudaFree(q);
+  }
+};
+
+}  // namespace
+
+int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count_reach,
+                    std::vector<int32_t> &acc, int64_t *max_reach) {
+  const int32_t n_nodes = ctx->n_nodes, root = n_nodes - 1, S = ctx->n_studies;
+  const int32_t W = ctx->n_cols / 64;
+  acc.assign((size_t)S * n_nodes, 0);
+  if (W == 0 || root == 0) return UNIFRAC_OK;
+  cudaStream_t st = ctx->stream;
+  PresTemp tmp;
+  unsigned long long *bits;
+  int32_t *d_sw, *d_acc, *d_reach;
+  if (cudaMalloc(&tmp.p[0], (size_t)n_nodes * W * 8) != cudaSuccess ||
+      cudaMalloc(&tmp.p[1], sw.size() * 4) != cudaSuccess ||
+      cudaMalloc(&tmp.p[2], acc.size() * 4) != cudaSuccess ||
+      cudaMalloc(&tmp.p[3], (size_t)ctx->n_cols * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, UNIFRAC_E_OOM, "presence bitsets");
+  }
+  bits = static_cast<unsigned long long *>(tmp.p[0]);
+  d_sw = static_cast<int32_t *>(tmp.p[1]);
+  d_acc = static_cast<int32_t *>(tmp.p[2]);
+  d_reach = static_cast<int32_t *>(tmp.p[3]);
+  cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)n_nodes * W * 8, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_sw, sw.data(), sw.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "presence set-up");
+  if (ctx->n_frows > 0)
+    k_pres_tips<<<(unsigned)(((int64_t)ctx->n_frows * 32 + 255) / 256), 256, 0, st>>>(
+        ctx->n_frows, ctx->d_frow_tip, ctx->d_frow_ptr, ctx->d_fent_col, bits, W);
+  constexpr int32_t kTailNodes = 1024;
+  int32_t L0 = 0;
+  while (L0 < ctx->n_levels && ctx->level_ptr[L0 + 1] - ctx->level_ptr[L0] > kTailNodes) ++L0;
+  for (int L = 0; L < L0; ++L) {
+    const int32_t lo = ctx->level_ptr[L], hi = ctx->level_ptr[L + 1];
+    const int64_t items = (int64_t)(hi - lo) * W;
+    if (items == 0) continue;
+    k_pres_level<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(
+        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, bits, W);
+  }
+  if (L0 < ctx->n_levels)
+    k_pres_levels_tail<<<(unsigned)((W + 31) / 32), 1024, 0, st>>>(
+        ctx->d_level_nodes, ctx->d_level_ptr, L0, ctx->n_levels, ctx->d_child_ptr,
+        ctx->d_child_idx, bits, W);
+  k_pres_counts<<<(unsigned)(((int64_t)root * 32 + 255) / 256), 256, 0, st>>>(bits, W, root, S, d_sw,
+                                                                              d_acc, n_nodes);
+  std::vector<int32_t> reach;
+  if (count_reach) {
+    reach.assign(ctx->n_cols, 0);
+    e = cudaMemsetAsync(d_reach, 0, (size_t)ctx->n_cols * 4, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "presence reach");
+    const unsigned slices = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, root / 4096 + 1));
+    k_pres_reach<<<dim3((unsigned)((ctx->n_cols + 255) / 256), slices), 256, 0, st>>>(
+        bits, W, root, ctx->n_cols, d_reach);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(acc.data(), d_acc, acc.size() * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && count_reach)
+    e = cudaMemcpyAsync(reach.data(), d_reach, reach.size() * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "presence kernels");
+  if (count_reach)
+    for (int32_t c = 0; c < ctx->n_cols; ++c) *max_reach = std::max<int64_t>(*max_reach, reach[c]);
   return UNIFRAC_OK;
 }
 

@@ -190,6 +190,12 @@ int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes);
 // embedding (K1) ------------------------------------------------------------
 // Fills cnt[node][col] (u32 counts below each branch) and flag[node][tile]
 // (1 if any column of the tile is non-zero) for every non-root node.
+// Per node and study, the samples with a non-zero count below the node
+// (acc[s * n_nodes + v], v < root), from device bitsets; with count_reach
+// also the most nodes one column reaches (*max_reach).  Needs the tree, level
+// and table rows on the device; synchronises the context's stream.
+int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count_reach,
+                    std::vector<int32_t> &acc, int64_t *max_reach);
 int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 
 // packing ---------------------------------------------------------------------
