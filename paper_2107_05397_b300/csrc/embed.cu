@@ -38,13 +38,20 @@ __global__ void k_tip_rows(int32_t n_frows, const int32_t *__restrict__ frow_tip
   const int32_t tip = frow_tip[warp];
   const int64_t lo = frow_ptr[warp], hi = frow_ptr[warp + 1];
   uint32_t *row = cnt + (int64_t)tip * ldc;
-  for (int64_t e = lo + lane; e < hi; e += 32) {
-    const int32_t t = ent_col[e] / TILE;
-    if (e == lo || ent_col[e - 1] / TILE != t) {
-      uint4 *p = reinterpret_cast<uint4 *>(row + (int64_t)t * TILE);
-#pragma unroll 4
-      for (int q = 0; q < TILE / 4; ++q) p[q] = make_uint4(0u, 0u, 0u, 0u);
-      flag[(int64_t)tip * n_tiles + t] = 1;
+  // clear each tile the row touches: the whole warp writes one tile (32
+  // lanes x 16 bytes) per step, tiles found by a ballot over 32 entries
+  for (int64_t base = lo; base < hi; base += 32) {
+    const int64_t e = base + lane;
+    int32_t t = -1;
+    bool first = false;
+    if (e < hi) {
+      t = ent_col[e] / TILE;
+      first = e == lo || ent_col[e - 1] / TILE != t;
+    }
+    for (uint32_t m = __ballot_sync(0xffffffffu, first); m; m &= m - 1) {
+      const int32_t ts = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
+      reinterpret_cast<uint4 *>(row + (int64_t)ts * TILE)[lane] = make_uint4(0u, 0u, 0u, 0u);
+      if (lane == 0) flag[(int64_t)tip * n_tiles + ts] = 1;
     }
   }
   __syncwarp();
