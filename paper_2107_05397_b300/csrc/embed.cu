@@ -59,44 +59,45 @@ __global__ void k_tip_rows(int32_t n_frows, const int32_t *__restrict__ frow_tip
 }
 
 // One level: for every (node of the level, column tile), sum the flagged
-// children's tiles.  A warp owns one (node, tile): 32 lanes x uint4 = 128 columns.
+// children's tiles.  A warp owns one node and 32 consecutive tiles: lane l
+// ORs the children's flags of tile 32 g + l (and keeps which children had
+// the tile, for nodes of at most 32 children), then the warp sums the rows of
+// each flagged tile together (32 lanes x uint4 = 128 columns).  Sparse levels
+// cost one warp per 32 tiles instead of one per tile.
 __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
                         const int32_t *__restrict__ child_ptr,
                         const int32_t *__restrict__ child_idx, uint32_t *cnt,
                         uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+  const int32_t n_groups = (n_tiles + 31) / 32;
   const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (item >= (int64_t)n_level * n_tiles) return;
-  const int32_t node = nodes[item / n_tiles];
-  const int32_t t = (int32_t)(item % n_tiles);
-  uint4 s = make_uint4(0u, 0u, 0u, 0u);
-  bool any = false;
+  if (item >= (int64_t)n_level * n_groups) return;  // whole warps
+  const int32_t node = nodes[item / n_groups];
+  const int32_t t = (int32_t)(item % n_groups) * 32 + lane;
   const int32_t c0 = child_ptr[node], c1 = child_ptr[node + 1];
-  // up to four children at a time: their indices, then their flags, then
-  // their rows, each group of loads in flight together
-  for (int32_t c = c0; c < c1; c += 4) {
-    int32_t ch[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) ch[u] = c + u < c1 ? child_idx[c + u] : -1;
-    bool f[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) f[u] = ch[u] >= 0 && flag[(int64_t)ch[u] * n_tiles + t] != 0;
-    uint4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      v[u] = f[u] ? reinterpret_cast<const uint4 *>(cnt + (int64_t)ch[u] * ldc + (int64_t)t * TILE)[lane]
-                  : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      any |= f[u];
-      s.x += v[u].x;
-      s.y += v[u].y;
-      s.z += v[u].z;
-      s.w += v[u].w;
+  const bool few = c1 - c0 <= 32;
+  uint32_t fmask = 0;  // children (by position) that have tile t
+  if (t < n_tiles)
+    for (int32_t c = c0; c < c1; ++c)
+      if (flag[(int64_t)child_idx[c] * n_tiles + t]) fmask |= few ? 1u << (c - c0) : 1u;
+  if (t < n_tiles) flag[(int64_t)node * n_tiles + t] = fmask ? 1 : 0;
+  for (uint32_t m = __ballot_sync(0xffffffffu, fmask != 0); m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    const int32_t ts = (int32_t)(item % n_groups) * 32 + src;
+    const uint32_t fm = __shfl_sync(0xffffffffu, fmask, src);
+    uint4 s = make_uint4(0u, 0u, 0u, 0u);
+    for (int32_t c = c0; c < c1; ++c) {
+      const int32_t ch = child_idx[c];
+      if (few ? ((fm >> (c - c0)) & 1u) != 0u : flag[(int64_t)ch * n_tiles + ts] != 0) {
+        const uint4 v = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + (int64_t)ts * TILE)[lane];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+      }
     }
+    reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)ts * TILE)[lane] = s;
   }
-  if (lane == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
-  if (any) reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)t * TILE)[lane] = s;
 }
 
 // The upper levels hold few nodes each, too few to fill the GPU one launch per
@@ -792,7 +793,7 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
   while (L0 < ctx->n_levels && ctx->level_ptr[L0 + 1] - ctx->level_ptr[L0] > kTailNodes) ++L0;
   for (int L = 0; L < L0 && ctx->n_tiles > 0; ++L) {
     const int32_t lo = ctx->level_ptr[L], hi = ctx->level_ptr[L + 1];
-    const int64_t items = (int64_t)(hi - lo) * ctx->n_tiles;
+    const int64_t items = (int64_t)(hi - lo) * ((ctx->n_tiles + 31) / 32);
     if (items == 0) continue;
     const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_level<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(
