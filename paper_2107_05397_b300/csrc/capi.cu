@@ -79,8 +79,28 @@ struct DeviceGuard {
   }
 };
 
+// Allocator that leaves new elements of trivial type uninitialised: resize()
+// of a large array that threads then fill costs no serial zeroing pass.
 template <typename T>
-int upload(unifrac_ctx *ctx, T **dst, const std::vector<T> &src) {
+struct NoInit : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <typename U>
+  NoInit(const NoInit<U> &) {}
+  template <typename U, typename... Args>
+  void construct(U *p, Args &&...args) {
+    if constexpr (sizeof...(Args) == 0)
+      ::new (static_cast<void *>(p)) U;
+    else
+      ::new (static_cast<void *>(p)) U(std::forward<Args>(args)...);
+  }
+};
+
+template <typename T, typename A>
+int upload(unifrac_ctx *ctx, T **dst, const std::vector<T, A> &src) {
   size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (inputs)");
@@ -339,8 +359,8 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<int64_t> total(n_samples, 0);
   std::vector<int32_t> frow_tip;
   std::vector<int64_t> frow_ptr(1, 0);
-  std::vector<int32_t> fent_col;
-  std::vector<uint32_t> fent_cnt;
+  std::vector<int32_t, NoInit<int32_t>> fent_col;  // filled by threads after resize()
+  std::vector<uint32_t, NoInit<uint32_t>> fent_cnt;
   std::vector<std::pair<int32_t, int32_t>> row;  // (sample, count)
   // Parallel pass for the usual table: every row's sample indices strictly
   // increasing and in range, counts >= 0.  Threads check their rows and write
