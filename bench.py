@@ -88,12 +88,26 @@ def measured_peaks():
 # any of them changes)
 # (capi.cu orders the tile pairs, which shapes the L2 reuse and so the traffic)
 KERNEL_SOURCES = {
-    "k_pairs_tc": ("pairs_tc.cu", "epilogue.cuh", "ufb_internal.cuh", "capi.cu"),
-    "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh", "capi.cu"),
-    "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh", "capi.cu"),
-    "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh", "capi.cu"),
+    "k_pairs_tc": ("pairs_tc.cu", "epilogue.cuh", "ufb_internal.cuh"),
+    "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"),
+    "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh"),
+    "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh"),
 }
+# functions of capi.cu that plan the pair launches (work items, their order,
+# buffer sizes): part of every pair kernel's record
+PLANNING_FUNCTIONS = ("void study_items(", "static int plan_items(", "static int plan_buffers(")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def planning_source() -> bytes:
+    """The text of the launch-planning functions of capi.cu (each from its
+    signature to the closing brace at column 0)."""
+    text = open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", "capi.cu")).read()
+    out = []
+    for sig in PLANNING_FUNCTIONS:
+        i = text.index(sig)
+        out.append(text[i:text.index("\n}\n", i) + 3])
+    return "".join(out).encode()
 
 
 def kernel_source_hash(kernel: str):
@@ -102,6 +116,7 @@ def kernel_source_hash(kernel: str):
                                             "ufb_internal.cuh")):
         with open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", name), "rb") as f:
             h.update(f.read())
+    h.update(planning_source())
     return h.hexdigest()[:16]
 
 
