@@ -79,26 +79,6 @@ struct DeviceGuard {
   }
 };
 
-// Allocator that leaves new elements of trivial type uninitialised: resize()
-// of a large array that threads then fill costs no serial zeroing pass.
-template <typename T>
-struct NoInit : std::allocator<T> {
-  template <typename U>
-  struct rebind {
-    using other = NoInit<U>;
-  };
-  NoInit() = default;
-  template <typename U>
-  NoInit(const NoInit<U> &) {}
-  template <typename U, typename... Args>
-  void construct(U *p, Args &&...args) {
-    if constexpr (sizeof...(Args) == 0)
-      ::new (static_cast<void *>(p)) U;
-    else
-      ::new (static_cast<void *>(p)) U(std::forward<Args>(args)...);
-  }
-};
-
 template <typename T, typename A>
 int upload(unifrac_ctx *ctx, T **dst, const std::vector<T, A> &src) {
   size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
@@ -110,6 +90,27 @@ int upload(unifrac_ctx *ctx, T **dst, const std::vector<T, A> &src) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upload inputs");
   }
   return UNIFRAC_OK;
+}
+
+// Upload of `count` elements straight from the caller's array.
+template <typename T>
+int upload_raw(unifrac_ctx *ctx, T **dst, const T *src, size_t count) {
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (inputs)");
+  ctx->device_bytes += bytes;
+  if (count) {
+    e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload inputs");
+  }
+  return UNIFRAC_OK;
+}
+
+// Sample indices of the table entries to embedding columns, in place.
+__global__ void k_map_columns(int32_t *ent, int64_t n, const int32_t *__restrict__ col_of_sample) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    ent[e] = col_of_sample[ent[e]];
 }
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
@@ -359,23 +360,23 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<int64_t> total(n_samples, 0);
   std::vector<int32_t> frow_tip;
   std::vector<int64_t> frow_ptr(1, 0);
-  std::vector<int32_t, NoInit<int32_t>> fent_col;  // filled by threads after resize()
-  std::vector<uint32_t, NoInit<uint32_t>> fent_cnt;
+  std::vector<int32_t> fent_col;   // entry columns and counts, unless `direct`
+  std::vector<uint32_t> fent_cnt;
   std::vector<std::pair<int32_t, int32_t>> row;  // (sample, count)
   // Parallel pass for the usual table: every row's sample indices strictly
-  // increasing and in range, counts >= 0.  Threads check their rows and write
-  // the entries in place (CSR positions), with per-thread sample totals added
-  // in thread order (integers); explicit zeros, if any, are squeezed out
-  // afterwards.  Any other table takes the sequential pass below, which
-  // reports what is wrong.
-  bool table_done = false;
+  // increasing and in range, counts >= 0.  Threads check their rows (reading
+  // only) and add per-thread sample totals, summed in thread order
+  // (integers).  Without explicit zeros the caller's indices and counts are
+  // the entry arrays themselves (`direct`: uploaded as they are, sample
+  // indices mapped to embedding columns on the device); with zeros they are
+  // copied without them.  Any other table takes the sequential pass below,
+  // which reports what is wrong.
+  bool table_done = false, direct = false;
   {
     const int T = host_threads(nnz);
     std::vector<uint8_t> bad(T, 0);
     std::vector<int64_t> zeros(T, 0);
     std::vector<std::vector<int64_t>> tot(T);
-    fent_col.resize((size_t)nnz);
-    fent_cnt.resize((size_t)nnz);
     run_threads(T, [&](int t) {
       std::vector<int64_t> &tt = tot[t];
       tt.assign(n_samples, 0);
@@ -393,8 +394,6 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
             bad[t] = 1;
             return;
           }
-          fent_col[e] = ctx->col_of_sample[i];
-          fent_cnt[e] = (uint32_t)counts[e];
           tt[i] += counts[e];
           z += counts[e] == 0;
         }
@@ -404,14 +403,19 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     if (std::find(bad.begin(), bad.end(), 1) == bad.end() && indptr[0] == 0 &&
         indptr[n_features] == nnz) {
       const bool has_zeros = std::accumulate(zeros.begin(), zeros.end(), (int64_t)0) > 0;
+      direct = !has_zeros;
       int64_t out = 0;
+      if (has_zeros) {
+        fent_col.reserve((size_t)nnz);
+        fent_cnt.reserve((size_t)nnz);
+      }
       for (int32_t f = 0; f < n_features; ++f) {
         const int64_t start_f = out;
         if (has_zeros) {
           for (int64_t e = indptr[f]; e < indptr[f + 1]; ++e)
-            if (fent_cnt[e] != 0) {
-              fent_col[out] = fent_col[e];
-              fent_cnt[out] = fent_cnt[e];
+            if (counts[e] != 0) {
+              fent_col.push_back(ctx->col_of_sample[indices[e]]);
+              fent_cnt.push_back((uint32_t)counts[e]);
               ++out;
             }
         } else {
@@ -422,14 +426,9 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
           frow_ptr.push_back(out);
         }
       }
-      fent_col.resize(out);
-      fent_cnt.resize(out);
       for (int t = 0; t < T; ++t)
         for (int32_t i = 0; i < n_samples; ++i) total[i] += tot[t][i];
       table_done = true;
-    } else {
-      fent_col.clear();
-      fent_cnt.clear();
     }
   }
   if (!table_done) {
@@ -518,7 +517,23 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
     if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
     if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
-    if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
+    if (!direct) {
+      if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
+    } else {  // the caller's sample indices, mapped to columns when studies add padding
+      if ((rc = upload_raw(ctx, &ctx->d_fent_col, indices, (size_t)nnz))) return rc;
+      if (n_studies > 1 && nnz > 0) {
+        int32_t *d_map = nullptr;
+        if ((rc = upload_raw(ctx, &d_map, ctx->col_of_sample.data(), ctx->col_of_sample.size())))
+          return rc;
+        k_map_columns<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 148 * 32), 256>>>(
+            ctx->d_fent_col, nnz, d_map);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 == cudaSuccess) e2 = cudaDeviceSynchronize();
+        cudaFree(d_map);
+        ctx->device_bytes -= std::max<size_t>(ctx->col_of_sample.size() * 4, 16);
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "column map");
+      }
+    }
     // a sample reaches at most root branches: count exactly only when that
     // bound does not already settle the tensor-core exactness test
     const bool count_reach = (int64_t)root >= 65793;
@@ -619,7 +634,8 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     const int kChunks = R >= 4096 ? 64 : 1;
     std::vector<std::vector<double>> part(kChunks);
     std::atomic<int> next_chunk{0};
-    run_threads(std::min(kChunks, host_threads((int64_t)fent_col.size())), [&](int) {
+    const int64_t n_ent = direct ? nnz : (int64_t)fent_col.size();
+    run_threads(std::min(kChunks, host_threads(n_ent)), [&](int) {
       for (int c; (c = next_chunk.fetch_add(1)) < kChunks;) {
         std::vector<double> &P = part[c];
         P.assign(ctx->n_cols, 0.0);
@@ -627,7 +643,10 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
              r < (int32_t)((int64_t)R * (c + 1) / kChunks); ++r) {
           const double dep = depth[frow_tip[r]];
           for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e)
-            P[fent_col[e]] += (double)fent_cnt[e] * dep;
+            if (direct)
+              P[ctx->col_of_sample[indices[e]]] += (double)counts[e] * dep;
+            else
+              P[fent_col[e]] += (double)fent_cnt[e] * dep;
         }
       }
     });
@@ -639,7 +658,12 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
 
   // ---------------------------------------------------------------- device
   cudaError_t e;
-  if ((rc = upload(ctx, &ctx->d_fent_cnt, fent_cnt))) return rc;
+  if (!direct) {
+    if ((rc = upload(ctx, &ctx->d_fent_cnt, fent_cnt))) return rc;
+  } else if ((rc = upload_raw(ctx, &ctx->d_fent_cnt, reinterpret_cast<const uint32_t *>(counts),
+                              (size_t)nnz))) {  // counts >= 0: the same bits as u32
+    return rc;
+  }
   if ((rc = upload(ctx, &ctx->d_inv_total, inv_total))) return rc;
   if ((rc = upload(ctx, &ctx->d_S, S))) return rc;
   if ((rc = upload(ctx, &ctx->d_perm, perm))) return rc;
