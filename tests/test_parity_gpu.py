@@ -878,3 +878,58 @@ def test_pcoa_all_components():
     lam, C = ub.unifrac_pcoa(torch.from_numpy(X).cuda(), k=12, iters=4, seed=3)
     lam_o, _ = opc.pcoa(X, 12)
     np.testing.assert_allclose(lam, lam_o, rtol=1e-5, atol=1e-6 * abs(lam_o[0]))
+
+
+# ------------------------------------------------------------------ table forms at create
+
+def _with_explicit_zeros(table, seed):
+    """The same table with explicit zero counts inserted in about half of the
+    rows (at sample ids the row does not use), rows kept sorted."""
+    rng = np.random.default_rng(seed)
+    ip, ix, ct = [0], [], []
+    for f in range(table.n_features):
+        lo, hi = int(table.indptr[f]), int(table.indptr[f + 1])
+        idx, cnt = list(table.indices[lo:hi]), list(table.counts[lo:hi])
+        if rng.random() < 0.5:
+            free = np.setdiff1d(np.arange(table.n_samples), idx)
+            for s in rng.choice(free, size=min(3, len(free)), replace=False):
+                idx.append(int(s))
+                cnt.append(0)
+        order = np.argsort(idx, kind="stable")
+        ix += [idx[k] for k in order]
+        ct += [cnt[k] for k in order]
+        ip.append(len(ix))
+    return synth.Table(table.n_features, table.n_samples, np.array(ip, np.int64),
+                       np.array(ix, np.int32), np.array(ct, np.int32), table.feature_node,
+                       table.study_offsets)
+
+
+def _with_shuffled_rows(table, seed):
+    """The same table with every row's entries in a random order."""
+    rng = np.random.default_rng(seed)
+    ix, ct = table.indices.copy(), table.counts.copy()
+    for f in range(table.n_features):
+        lo, hi = int(table.indptr[f]), int(table.indptr[f + 1])
+        p = rng.permutation(hi - lo) + lo
+        ix[lo:hi], ct[lo:hi] = table.indices[p], table.counts[p]
+    return synth.Table(table.n_features, table.n_samples, table.indptr.copy(), ix, ct,
+                       table.feature_node, table.study_offsets)
+
+
+@pytest.mark.parametrize("studies", [1, 3])
+@pytest.mark.parametrize("form", ["zeros", "shuffled"])
+def test_table_forms_give_the_same_matrices(small, form, studies):
+    """Explicit zero counts (copied without them) and unsorted rows (the
+    sequential pass) give exactly the matrices of the canonical table (whose
+    entries are uploaded as they are), with one study and with three."""
+    w, _ = small
+    table = w.table
+    if studies > 1:
+        n = table.n_samples
+        table = synth.Table(table.n_features, n, table.indptr, table.indices, table.counts,
+                            table.feature_node, np.array([0, n // 3, 2 * n // 3, n], np.int32))
+    other = _with_explicit_zeros(table, 95) if form == "zeros" else _with_shuffled_rows(table, 96)
+    for variant in VARIANTS:
+        a = run(w.tree, table, variant, ub.MIXED, layout=ub.OUT_CONDENSED)
+        b = run(w.tree, other, variant, ub.MIXED, layout=ub.OUT_CONDENSED)
+        np.testing.assert_array_equal(a, b)
