@@ -115,9 +115,13 @@ enum unifrac_status {
  *  out            receives the new context.
  *
  * Every input is copied; the caller keeps ownership and may free its buffers
- * when the call returns.  Host-side work: validation, node levels, per-branch
- * presence counts (which branches any sample reaches), the branch order and
- * the tensor-core length digits; O(n + nnz + size of the presence sets).
+ * when the call returns.  Work: validation and per-sample totals (host
+ * threads, O(n + nnz)); the tree, its levels and the table uploaded (a
+ * canonical table -- rows strictly increasing, no explicit zeros -- as
+ * passed); per-branch presence counts per study (which samples reach each
+ * branch) from device bitsets (O(n x samples / 64) words); the branch order,
+ * tensor-core length digits and per-sample weighted sums on the host.
+ * Synchronous; uses the current device.
  */
 int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
                    int32_t n_features, const int32_t *feature_node,
