@@ -122,18 +122,20 @@ def kernel_source_hash(kernel: str):
 
 def recorded_traffic(kernel: str, workload: str, samples: int, thresholds: dict):
     """DRAM bytes (read + write) per launch from a committed ncu capture of the
-    same workload with the same dense / sparse split, if the kernel's sources
-    are unchanged since (else None)."""
+    same workload and sample count with the same dense / sparse split, if the
+    kernel's sources are unchanged since (else None).  profiles/traffic.json
+    holds one record per captured split."""
     try:
-        data = json.load(open(TRAFFIC_PATH))
+        records = json.load(open(TRAFFIC_PATH)).get("records", [])
     except Exception:
         return None
-    rec = data.get(kernel)
-    if (not rec or data.get("workload") != workload or data.get("samples") != samples
-            or data.get("thresholds") != thresholds
-            or rec.get("source_hash") != kernel_source_hash(kernel)):
-        return None
-    return rec.get("bytes_per_launch")
+    for data in records:
+        rec = data.get(kernel)
+        if (rec and data.get("workload") == workload and data.get("samples") == samples
+                and data.get("thresholds") == thresholds
+                and rec.get("source_hash") == kernel_source_hash(kernel)):
+            return rec.get("bytes_per_launch")
+    return None
 
 
 def split_thresholds(sparse_fraction: float, uw_sparse_fraction: float, n_max: int) -> dict:
@@ -143,10 +145,11 @@ def split_thresholds(sparse_fraction: float, uw_sparse_fraction: float, n_max: i
 
 
 def record_traffic(csv_path: str, workload: str, samples: int, capture: str, thresholds: dict):
-    """Writes profiles/traffic.json from an ncu --csv capture with the metrics
-    dram__bytes_read.sum and dram__bytes_write.sum: mean bytes per launch of
-    each pair kernel, with the hash of its current sources and the split
-    thresholds of the captured run."""
+    """Adds to profiles/traffic.json the record of an ncu --csv capture with the
+    metrics dram__bytes_read.sum and dram__bytes_write.sum: mean bytes per
+    launch of each pair kernel, with the hash of its current sources, for the
+    workload, sample count and split thresholds of the captured run (replacing
+    an earlier record of the same three)."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
@@ -167,8 +170,14 @@ def record_traffic(csv_path: str, workload: str, samples: int, capture: str, thr
         vals = list(launches.values())
         out[name] = {"bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
                      "source_hash": kernel_source_hash(name)}
+    try:  # keep the records of other workloads and splits
+        records = json.load(open(TRAFFIC_PATH)).get("records", [])
+    except Exception:
+        records = []
+    records = [r for r in records if (r.get("workload"), r.get("samples"), r.get("thresholds"))
+               != (workload, samples, thresholds)] + [out]
     with open(TRAFFIC_PATH, "w") as f:
-        json.dump(out, f, indent=1)
+        json.dump({"records": records}, f, indent=1)
         f.write("\n")
     print(json.dumps(out))
 
