@@ -162,6 +162,7 @@ void free_ctx(unifrac_ctx *ctx) {
     if (ctx->ev_chunk_copied[b]) cudaEventDestroy(ctx->ev_chunk_copied[b]);
     if (ctx->chunk_host[b]) cudaFreeHost(ctx->chunk_host[b]);
   }
+  if (ctx->ev_first_done) cudaEventDestroy(ctx->ev_first_done);
   if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
   if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   for (auto &e : ctx->ev)
@@ -1022,12 +1023,27 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
   return UNIFRAC_OK;
 }
 
+// The first result's copy to host memory, ordered after its kernels on the
+// context's (current) stream, run on the copy stream (see
+// unifrac_ctx::early_host).
+static int enqueue_early_copy(unifrac_ctx *ctx) {
+  if (!ctx->early_host) return UNIFRAC_OK;
+  cudaError_t e = cudaEventRecord(ctx->ev_first_done, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_first_done, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->early_host, ctx->early_dev, ctx->early_bytes, cudaMemcpyDeviceToHost,
+                        ctx->copy_stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy first result to host");
+  return UNIFRAC_OK;
+}
+
 // The embedding once, then each variant's packing and pair kernels.
-// With two plans and UNIFRAC_OPT_OVERLAP_VARIANTS, the second plan runs on a
-// second stream forked after the embedding and joined at the end (both are
-// captured into the same graph); the variants have separate buffers and
-// counters, and share only the read-only embedding and the output buffer,
-// which they write in disjoint halves.
+// With two plans and UNIFRAC_OPT_OVERLAP_VARIANTS, the first plan runs on a
+// high-priority second stream forked after the embedding and joined at the
+// end, the second on the context's stream (both are captured into the same
+// graph); the variants have separate buffers and counters, and share only the
+// read-only embedding and the output buffer, which they write in disjoint
+// halves.
 static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
   int rc;
   record_event(ctx, ctx->ev[0]);
@@ -1037,13 +1053,21 @@ static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
     return rc;
   const bool overlap = n_plans == 2 && ctx->opt_overlap;
   if (!overlap) {
-    for (int i = 0; i < n_plans; ++i)
+    for (int i = 0; i < n_plans; ++i) {
       if ((rc = enqueue_variant(ctx, plans[i], false))) return rc;
+      if (i == 0 && (rc = enqueue_early_copy(ctx))) return rc;
+    }
     return UNIFRAC_OK;
   }
   cudaError_t e = cudaSuccess;
   if (!ctx->stream2) {
-    e = cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking);
+    // the first plan (the unweighted variant of UNIFRAC_BOTH, the shorter)
+    // runs here at the highest priority, so that it finishes first and its
+    // result can be copied out while the second still computes
+    int lo_pri = 0, hi_pri = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi_pri);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "second stream");
@@ -1052,11 +1076,12 @@ static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
   e = cudaEventRecord(ctx->ev_fork2, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork2, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
-  if ((rc = enqueue_variant(ctx, plans[0], true))) return rc;
   cudaStream_t main_stream = ctx->stream;
   ctx->stream = ctx->stream2;
-  rc = enqueue_variant(ctx, plans[1], true);
+  rc = enqueue_variant(ctx, plans[0], true);
+  if (!rc) rc = enqueue_early_copy(ctx);
   ctx->stream = main_stream;
+  if (!rc) rc = enqueue_variant(ctx, plans[1], true);
   e = cudaEventRecord(ctx->ev_join2, ctx->stream2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
@@ -1195,7 +1220,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   RunPlan &P = plans[0];
 
   // where does `out` live?
-  bool device_out = false;
+  bool device_out = false, pinned_out = false;
   if (need > 0) {
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, out);
@@ -1204,6 +1229,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
       attr.type = cudaMemoryTypeUnregistered;
     }
     device_out = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    pinned_out = attr.type == cudaMemoryTypeHost;
   }
   const bool whole = (layout == UNIFRAC_OUT_STRIPES) ||
                      (s0 == 0 && (ctx->n_studies > 1 || s1 == ctx->n_samples / 2));
@@ -1226,12 +1252,32 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   }
 
   const bool use_graph = ctx->opt_use_graph && device_out;
+  size_t copied = 0;  // bytes of the result already on their way to host memory
   if (use_graph && graph_key_matches(ctx, P, variant)) {
     if ((rc = graph_launch(ctx))) return rc;
     ctx->stat_launches = ctx->graph_launches;
   } else {
     ctx->stat_launches = 0;
-    if ((rc = enqueue_run(ctx, plans, n_plans))) return rc;
+    // into pinned host memory, the first of two results is copied while the
+    // second computes
+    const bool early = !device_out && pinned_out && n_plans == 2 && one > 0;
+    if (early) {
+      cudaError_t e = cudaSuccess;
+      if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !ctx->ev_first_done)
+        e = cudaEventCreateWithFlags(&ctx->ev_first_done, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+      ctx->early_host = out;
+      ctx->early_dev = dst;
+      ctx->early_bytes = one;
+    }
+    rc = enqueue_run(ctx, plans, n_plans);
+    ctx->early_host = nullptr;
+    if (rc) {
+      if (early) cudaStreamSynchronize(ctx->copy_stream);
+      return rc;
+    }
+    if (early) copied = one;
     if (use_graph) {  // this run executed eagerly; later identical runs replay the graph
       ctx->graph_launches = ctx->stat_launches;
       if ((rc = graph_capture(ctx, plans, n_plans, variant))) return rc;
@@ -1247,9 +1293,11 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
 
   cudaError_t e;
   if (!device_out && need > 0) {
-    e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(static_cast<char *>(out) + copied, static_cast<const char *>(dst) + copied,
+                        need - copied, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
     e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && copied) e = cudaStreamSynchronize(ctx->copy_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
   }
   e = cudaGetLastError();

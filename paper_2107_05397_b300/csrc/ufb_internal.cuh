@@ -147,6 +147,13 @@ struct unifrac_ctx {
   // unifrac_run_streamed: copy stream, its events, and the chunk buffers
   // (two on the device, two pinned on the host), kept between calls
   cudaStream_t copy_stream = nullptr;
+  // host output of UNIFRAC_BOTH: the first result's copy to host_part0
+  // (bytes, from dev_part0) starts on copy_stream as soon as its kernels end,
+  // while the second variant computes
+  void *early_host = nullptr;
+  const void *early_dev = nullptr;
+  size_t early_bytes = 0;
+  cudaEvent_t ev_first_done = nullptr;
   cudaEvent_t ev_chunk_done[2] = {nullptr, nullptr}, ev_chunk_copied[2] = {nullptr, nullptr};
   void *chunk_host[2] = {nullptr, nullptr};
   size_t chunk_host_bytes = 0;

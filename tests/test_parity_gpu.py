@@ -31,10 +31,15 @@ def run(tree, table, variant, precision, layout=ub.OUT_FULL, s0=0, s1=-1, host=F
     with ub.Context(tree, table) as ctx:
         for k, v in (options or {}).items():
             ctx.set_option(k, v)
-        if host:
+        if host:  # True: pageable host memory; "pinned": page-locked
             nbytes = ctx.output_bytes(precision, layout, s0, s1) * (2 if variant == ub.BOTH else 1)
-            out = np.zeros(nbytes // (8 if precision == ub.FP64 else 4),
-                           np.float64 if precision == ub.FP64 else np.float32)
+            dt = np.float64 if precision == ub.FP64 else np.float32
+            n = nbytes // (8 if precision == ub.FP64 else 4)
+            if host == "pinned":
+                out = torch.zeros(n, dtype=torch.float64 if dt is np.float64 else torch.float32,
+                                  pin_memory=True).numpy()
+            else:
+                out = np.zeros(n, dt)
             ctx.run(variant, precision, layout, s0, s1, out=out)
             return out.astype(np.float64)
         out = ctx.run(variant, precision, layout, s0, s1)
@@ -398,8 +403,9 @@ def test_both_variants_in_one_run(small, precision, layout):
         uw = ctx.run(ub.UNWEIGHTED, precision, layout).cpu().numpy()
         wn = ctx.run(ub.WEIGHTED_NORMALIZED, precision, layout).cpu().numpy()
     np.testing.assert_array_equal(both, np.concatenate([uw, wn]))
-    host = run(w.tree, w.table, ub.BOTH, precision, layout, host=True)
-    np.testing.assert_array_equal(host, np.concatenate([uw, wn]).astype(np.float64))
+    for kind in (True, "pinned"):  # pinned: the first result's copy overlaps the second
+        host = run(w.tree, w.table, ub.BOTH, precision, layout, host=kind)
+        np.testing.assert_array_equal(host, np.concatenate([uw, wn]).astype(np.float64))
 
 
 @pytest.mark.parametrize("graph", [0, 1])
@@ -428,9 +434,12 @@ def test_both_overlapped_equals_serial(small, graph):
                          (ub.STAT_SPARSE_MS_UNWEIGHTED, ub.STAT_PAIR_MS_UNWEIGHTED)):
             # the sparse kernel is timed inside its variant's pair phase
             assert 0.0 < ctx.stat(sp) <= ctx.stat(pair)
-    host = run(w.tree, w.table, ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, host=True,
-               options={ub.OPT_SPARSE_THRESHOLD: 24, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 12})
-    np.testing.assert_array_equal(host, serial.astype(np.float64))
+    for kind in (True, "pinned"):
+        for overlap in (0, 1):
+            host = run(w.tree, w.table, ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, host=kind,
+                       options={ub.OPT_SPARSE_THRESHOLD: 24, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 12,
+                                ub.OPT_OVERLAP_VARIANTS: overlap})
+            np.testing.assert_array_equal(host, serial.astype(np.float64))
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
