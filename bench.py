@@ -111,11 +111,18 @@ def planning_source() -> bytes:
 
 
 def kernel_source_hash(kernel: str):
+    """Hash of what a pair kernel's launches depend on: its source files (the
+    shared header without the host-only context struct) and the
+    launch-planning functions."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES.get(kernel, ("pairs_simt.cu", "pairs_tc.cu", "epilogue.cuh",
                                             "ufb_internal.cuh")):
-        with open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2107_05397_b300", "csrc", name)) as f:
+            text = f.read()
+        if name == "ufb_internal.cuh" and "struct unifrac_ctx {" in text:
+            i = text.index("struct unifrac_ctx {")
+            text = text[:i] + text[text.index("\n};\n", i) + 4:]
+        h.update(text.encode())
     h.update(planning_source())
     return h.hexdigest()[:16]
 
