@@ -32,9 +32,12 @@
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include "ufb_internal.cuh"
@@ -283,6 +286,18 @@ __global__ void k_zero_diag(T *R, int32_t n) {
     R[i * n + i] = T(0);
 }
 
+// fn(lo, hi) over [0, n) in contiguous ranges on host threads (one thread
+// below 64 rows).
+template <typename F>
+void host_parallel(int64_t n, F &&fn) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int T = n < 64 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(std::min(32u, hw ? hw : 1u), n));
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(fn, n * t / T, n * (t + 1) / T);
+  fn((int64_t)0, n / T);
+  for (auto &x : th) x.join();
+}
+
 // Device allocations released together when the call returns.
 struct Cuda {
   std::vector<void *> ptrs;
@@ -430,19 +445,22 @@ int mantel_pearson(const T *x, const T *y, int32_t n, const int32_t *perms_host,
   if (!mem.alloc(&d_pi, 2 * (size_t)M * n * esz) || !mem.alloc(&partial, (size_t)M * n) ||
       !mem.alloc(&cross, (size_t)M))
     return UNIFRAC_E_OOM;
-  std::vector<unsigned char> hp(2 * (size_t)M * n * esz);
+  const size_t hp_bytes = 2 * (size_t)M * n * esz;
+  std::unique_ptr<unsigned char[]> hp(new unsigned char[hp_bytes]);  // every byte written below
   const int64_t half = (int64_t)M * n;
   auto put = [&](int64_t t, int32_t v) {
-    if (narrow) reinterpret_cast<uint16_t *>(hp.data())[t] = (uint16_t)v;
-    else reinterpret_cast<int32_t *>(hp.data())[t] = v;
+    if (narrow) reinterpret_cast<uint16_t *>(hp.get())[t] = (uint16_t)v;
+    else reinterpret_cast<int32_t *>(hp.get())[t] = v;
   };
-  for (int32_t p = 0; p < M; ++p)
-    for (int32_t i = 0; i < n; ++i) {
-      const int32_t v = p == 0 ? i : perms_host[(int64_t)(p - 1) * n + i];
-      put((int64_t)p * n + i, v);
-      put(half + (int64_t)p * n + v, i);
-    }
-  if (cudaMemcpyAsync(d_pi, hp.data(), hp.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+  host_parallel(M, [&](int64_t p0, int64_t p1) {  // permutation rows and their inverses
+    for (int64_t p = p0; p < p1; ++p)
+      for (int32_t i = 0; i < n; ++i) {
+        const int32_t v = p == 0 ? i : perms_host[(p - 1) * n + i];
+        put(p * n + i, v);
+        put(half + p * n + v, i);
+      }
+  });
+  if (cudaMemcpyAsync(d_pi, hp.get(), hp_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return UNIFRAC_E_CUDA;
   const T mxt = (T)mx, myt = (T)my;
   const cudaError_t e =
@@ -518,15 +536,22 @@ extern "C" int unifrac_mantel(const void *x, const void *y, int precision, int32
     return UNIFRAC_E_INVALID_ARG;
   }
   try {
-    std::vector<uint8_t> seen(n);  // every row a permutation of 0 .. n-1
-    for (int32_t p = 0; p < n_perms; ++p) {
-      std::fill(seen.begin(), seen.end(), 0);
-      for (int32_t i = 0; i < n; ++i) {
-        const int32_t v = perms[(int64_t)p * n + i];
-        if (v < 0 || v >= n || seen[v]) return UNIFRAC_E_INVALID_ARG;
-        seen[v] = 1;
+    std::atomic<bool> bad{false};  // every row a permutation of 0 .. n-1
+    host_parallel(n_perms, [&](int64_t p0, int64_t p1) {
+      std::vector<uint8_t> seen(n);
+      for (int64_t p = p0; p < p1 && !bad.load(std::memory_order_relaxed); ++p) {
+        std::fill(seen.begin(), seen.end(), 0);
+        for (int32_t i = 0; i < n; ++i) {
+          const int32_t v = perms[p * n + i];
+          if (v < 0 || v >= n || seen[v]) {
+            bad = true;
+            return;
+          }
+          seen[v] = 1;
+        }
       }
-    }
+    });
+    if (bad) return UNIFRAC_E_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == UNIFRAC_FP64)
       return mantel_impl<double>(static_cast<const double *>(x), static_cast<const double *>(y), n,
