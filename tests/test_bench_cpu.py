@@ -1,0 +1,82 @@
+"""Host logic of bench.py (no GPU): the DRAM-traffic records behind
+roofline.traffic and the split thresholds they are keyed to."""
+import json
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), ".."))
+import bench  # noqa: E402
+
+
+def _csv(path, rows):
+    """An ncu --csv launch list with the two DRAM metrics (values in bytes)."""
+    with open(path, "w") as f:
+        f.write('"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n')
+        for launch, kernel, rd, wr in rows:
+            f.write(f'"{launch}","{kernel}(args)","dram__bytes_read.sum","byte","{rd}"\n')
+            f.write(f'"{launch}","{kernel}(args)","dram__bytes_write.sum","byte","{wr}"\n')
+
+
+def test_split_thresholds_follow_the_option_rounding():
+    assert bench.split_thresholds(0.375, 0.0234375, 4096) == {"sparse": 1536, "uw_sparse": 96}
+    assert bench.split_thresholds(0.375, 0.0, 4096) == {"sparse": 1536, "uw_sparse": 0}
+    assert bench.split_thresholds(1e-9, 1e-9, 100) == {"sparse": 1, "uw_sparse": 1}
+
+
+def test_traffic_records_are_keyed_to_workload_samples_split_and_sources(tmp_path, monkeypatch):
+    """One record per (workload, samples, split): a second split adds a
+    record, the same split replaces its record, and a lookup with any other
+    key -- or after a kernel's sources change -- finds nothing."""
+    path = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(path))
+    csv1 = tmp_path / "a.csv"
+    _csv(csv1, [("1", "void ufb::k_pairs_sparse<0>", 100, 20),
+                ("2", "void ufb::k_pairs_sparse<0>", 300, 40),
+                ("3", "ufb::k_pairs_tc", 1000, 10)])
+    t96 = {"sparse": 1536, "uw_sparse": 96}
+    t128 = {"sparse": 1536, "uw_sparse": 128}
+    bench.record_traffic(str(csv1), "w", 4096, "cap", t96)
+    # mean over launches of read + write
+    assert bench.recorded_traffic("k_pairs_sparse<false>", "w", 4096, t96) == 230.0
+    assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t96) == 1010.0
+    for key in (("w2", 4096, t96), ("w", 2048, t96), ("w", 4096, t128)):
+        assert bench.recorded_traffic("k_pairs_tc", *key) is None
+    csv2 = tmp_path / "b.csv"
+    _csv(csv2, [("1", "ufb::k_pairs_tc", 500, 0)])
+    bench.record_traffic(str(csv2), "w", 4096, "cap", t128)
+    assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t128) == 500.0
+    assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t96) == 1010.0
+    bench.record_traffic(str(csv2), "w", 4096, "cap", t96)  # replaces the first record
+    assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t96) == 500.0
+    assert len(json.load(open(path))["records"]) == 2
+    # a changed source hash voids the record
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda kernel: "changed")
+    assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t96) is None
+
+
+def test_kernel_hash_ignores_the_host_context_struct(tmp_path, monkeypatch):
+    """The hash covers the kernel sources and the launch-planning functions,
+    not the host-only context struct of the shared header."""
+    h0 = bench.kernel_source_hash("k_pairs_sparse<false>")
+    src = open(os.path.join(bench.ROOT, "paper_2107_05397_b300", "csrc", "ufb_internal.cuh")).read()
+    assert "struct unifrac_ctx {" in src
+    plan = bench.planning_source().decode()
+    for sig in bench.PLANNING_FUNCTIONS:
+        assert sig in plan
+    assert h0 == bench.kernel_source_hash("k_pairs_sparse<true>")  # same sources
+    assert h0 != bench.kernel_source_hash("k_pairs_tc")
+
+
+@pytest.mark.parametrize("kernel", sorted(bench.KERNEL_SOURCES))
+def test_committed_traffic_has_every_pair_kernel(kernel):
+    """profiles/traffic.json holds, for every pair kernel, records of the bench
+    workload with bytes per launch and a source hash (null in the bench line
+    once the sources move on)."""
+    records = json.load(open(bench.TRAFFIC_PATH))["records"]
+    mine = [r for r in records if kernel in r and r.get("workload") == bench.DEFAULT_WORKLOAD]
+    assert mine
+    for r in mine:
+        assert r[kernel]["bytes_per_launch"] > 0 and len(r[kernel]["source_hash"]) == 16
+        assert set(r["thresholds"]) == {"sparse", "uw_sparse"}
