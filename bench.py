@@ -586,7 +586,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+bf16(int digits)+f64 reductions", "data": "synthetic",
+        "dtype": "f32+bf16(int digits), integer sums", "data": "synthetic",
         "config": {"workload": args.workload if args.samples is None
                    else f"{args.workload} truncated to {N} samples", "samples": N,
                    "studies": 1 if w.table.study_offsets is None
