@@ -879,6 +879,11 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
     }
     P.k_tc = std::min<int32_t>(ctx->K_pad, std::max<int32_t>(64, (kf + 63) / 64 * 64));
+    // the sparse kernel sums 12-bit halves of q in 32-bit counters: exact
+    // while fewer than 2^20 positions are sparse
+    constexpr int32_t kMaxSparsePositions = (1 << 20) - 64;
+    if (ctx->K - P.k_tc > kMaxSparsePositions)
+      P.k_tc = std::min<int32_t>(ctx->K_pad, (ctx->K - kMaxSparsePositions + 63) / 64 * 64);
     const int32_t n_words = ctx->K_pad / WORD;
     P.kf_words = P.k_tc / WORD;
     P.n_win = P.k_tc >= ctx->K ? 0 : (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;

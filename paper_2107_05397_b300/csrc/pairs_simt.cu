@@ -363,13 +363,16 @@ constexpr int kSmall = 16;         // pairs a single lane walks alone
 constexpr int kAccLd = TILE + 1;   // padded accumulator row
 
 // PRES = false: weighted form, entries carry V; 32-bit accumulators (spart u32).
-// PRES = true:  unweighted form, entries are presences; adds q[k] into 64-bit
-//               accumulators (spart u64), exact -- the tensor-core epilogue adds
-//               it to its digit sums.
+// PRES = true:  unweighted form, entries are presences; adds the 24-bit q[k]
+//               as two 12-bit halves into two 32-bit shared planes (32-bit
+//               shared atomics are native; a half-sum stays below 2^32 while
+//               fewer than 2^20 branches are summed), combined into 64-bit
+//               spart at the end, exact -- the tensor-core epilogue adds it to
+//               its digit sums.
 template <bool PRES>
 struct SparseCfg {
   using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
-  static constexpr size_t kAccBytes = ((size_t)TILE * kAccLd * sizeof(Acc) + 15) / 16 * 16;
+  static constexpr size_t kAccBytes = ((size_t)TILE * kAccLd * 4 * (PRES ? 2 : 1) + 15) / 16 * 16;
   // the swept side of one incidence per warp: TILE entries of 8 (weighted) or
   // 1 (unweighted) bytes
   static constexpr size_t kScratch = (size_t)TILE * (PRES ? 1 : 8);
@@ -387,7 +390,8 @@ __global__ void __launch_bounds__(kSpThreads, 1)
                    unsigned long long *__restrict__ n_updates) {
   using Acc = typename SparseCfg<PRES>::Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Acc *sacc = reinterpret_cast<Acc *>(smem_raw);  // [TILE][kAccLd]
+  uint32_t *sacc = reinterpret_cast<uint32_t *>(smem_raw);  // [TILE][kAccLd] (PRES: low halves)
+  uint32_t *sacc_hi = sacc + TILE * kAccLd;                 // PRES: high halves
   // (p / n, p % n) for lanes p < 32 and n = 1..32: group and row of a lane when
   // the lane side has n rows; gtab[n-1] = 32 / n groups; fillv[n-1] = lanes a
   // lane side of n rows keeps busy (n > 32: n / passes) -- no divisions later
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   unsigned long long *eS = reinterpret_cast<unsigned long long *>(scr);  // weighted
   uint8_t *rS = scr;                                                     // unweighted
   unsigned long long my_updates = 0;
-  for (int x = tid; x < TILE * kAccLd; x += kSpThreads) sacc[x] = Acc(0);
+  for (int x = tid; x < TILE * kAccLd * (PRES ? 2 : 1); x += kSpThreads) sacc[x] = 0u;
   {
     const int n = tid / 32 + 1, p = tid % 32;  // kSpThreads == 32 * 32
     divtab[n - 1][p] = (uint16_t)(((p / n) << 8) | (p % n));
@@ -470,8 +474,11 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       for (int a = 0; a < nI; ++a) {
         if constexpr (PRES) {
           const int ra = (int)__ldg(riI + sI + a) * kAccLd;
-          for (int b = 0; b < nJ; ++b)
-            atomicAdd(&sacc[ra + (int)__ldg(riJ + sJ + b)], (unsigned long long)qk);
+          for (int b = 0; b < nJ; ++b) {
+            const int idx = ra + (int)__ldg(riJ + sJ + b);
+            atomicAdd(&sacc[idx], qk & 0xfffu);
+            atomicAdd(&sacc_hi[idx], qk >> 12);
+          }
         } else {
           const unsigned long long ea = __ldg(eI + sI + a);
           const int ra = (int)(uint32_t)(ea & 0xffu) * kAccLd;
@@ -558,8 +565,11 @@ __global__ void __launch_bounds__(kSpThreads, 1)
           if constexpr (PRES) {
             const int base = (int)(b < 32 ? eb0 : __ldg((laneJ ? riJ : riI) + bsL + b)) * mL;
 #pragma unroll 2
-            for (int a = g; a < nT; a += G)
-              atomicAdd(&sacc[base + (int)rS[a] * mT], (unsigned long long)bq);
+            for (int a = g; a < nT; a += G) {
+              const int idx = base + (int)rS[a] * mT;
+              atomicAdd(&sacc[idx], bq & 0xfffu);
+              atomicAdd(&sacc_hi[idx], bq >> 12);
+            }
           } else {
             const unsigned long long eb = b < 32 ? eb0 : __ldg((laneJ ? eJ : eI) + bsL + b);
             uint32_t *row = sacc + (uint32_t)(eb & 0xffu) * (uint32_t)mL;
@@ -579,7 +589,13 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   }
   __syncthreads();
   Acc *dst = spart + (int64_t)blockIdx.x * TILE * TILE;
-  for (int x = tid; x < TILE * TILE; x += kSpThreads) dst[x] = sacc[(x / TILE) * kAccLd + x % TILE];
+  for (int x = tid; x < TILE * TILE; x += kSpThreads) {
+    const int q = (x / TILE) * kAccLd + x % TILE;
+    if constexpr (PRES)
+      dst[x] = ((unsigned long long)sacc_hi[q] << 12) + (unsigned long long)sacc[q];
+    else
+      dst[x] = sacc[q];
+  }
   // pair updates done (statistics)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) my_updates += __shfl_xor_sync(0xffffffffu, my_updates, off);
