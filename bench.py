@@ -574,8 +574,10 @@ def main():
     atom_peak = sms * 32 * sm_max * 1e6 / 1e12
     atom_src = (f"{sms} SMs x 32 shared-memory atomic lanes x {sm_max:.0f} MHz (one 32-lane "
                 "wavefront per cycle per SM)")
-    entry("k_pairs_sparse<true>", mean(sp_uw_ms), mean(sp_uw_n), "smem_atomic", atom_peak,
-          "T updates/s", "1 shared-memory u64 add of q_b per co-present pair-branch", atom_src)
+    # the unweighted form adds q_b as two 12-bit halves: two lane-ops per update
+    entry("k_pairs_sparse<true>", mean(sp_uw_ms), mean(sp_uw_n), "smem_atomic", atom_peak / 2,
+          "T updates/s", "2 shared-memory u32 adds (12-bit halves of q_b) per co-present "
+          "pair-branch", atom_src + ", halved: two atomic lane-ops per update")
     entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms), 2.0 * mean(sel_wn), "alu", alu_peak,
           "TFLOP/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
     entry("k_pairs_sparse<false>", mean(sp_wn_ms), mean(sp_wn_n), "smem_atomic", atom_peak,
