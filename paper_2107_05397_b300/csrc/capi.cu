@@ -773,9 +773,29 @@ struct RunPlan {
   enum Kind { WEIGHTED, TENSOR, LOOKUP } kind;
   int32_t kf_words = 0, n_win = 0;
   int32_t k_tc = 0;  // tensor-core positions (TENSOR)
+  int32_t sp_parts = 1;  // parts of each tile pair's sparse sums (WEIGHTED)
+  bool shares_gpu = false;  // runs beside the other variant on a second stream
   void *dst = nullptr;
   int32_t n_items = 0;
 };
+
+// Parts per tile pair of the weighted sparse kernel (one CTA per SM): the
+// fewest that fill the last wave of tile pairs x parts, each part costing
+// about 1% extra (its own accumulator set-up and partial sums).
+static int32_t sparse_parts(int32_t n_items, int sms) {
+  if (n_items <= 0 || sms <= 0) return 1;
+  int32_t best = 1;
+  double best_t = 1e300;
+  for (int32_t p = 1; p <= 8; ++p) {
+    const double waves = std::ceil((double)n_items * p / sms);
+    const double t = waves / p * (1.0 + 0.01 * p);
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = p;
+    }
+  }
+  return best;
+}
 
 static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   // the work list depends only on (layout, stripe range): rebuild when it changes
@@ -865,7 +885,10 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       if ((rc = grow(ctx, V.cpre, nblk * (kRareWin / WORD + 1) * 8))) return rc;
       if ((rc = grow(ctx, V.boff, (nblk + 1) * 8))) return rc;
       if ((rc = grow(ctx, V.blocks, bound))) return rc;
-      if ((rc = grow(ctx, V.spart, (size_t)std::max(P.n_items, 1) * TILE * TILE * 4)))
+      // beside the other variant, whose kernels fill the last wave anyway,
+      // parts would only add their fixed costs
+      P.sp_parts = P.shares_gpu ? 1 : sparse_parts(P.n_items, ctx->sm_count);
+      if ((rc = grow(ctx, V.spart, (size_t)std::max(P.n_items, 1) * P.sp_parts * TILE * TILE * 4)))
         return rc;
     }
   } else if (P.kind == RunPlan::TENSOR) {
@@ -971,8 +994,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     if ((rc = pairs_weighted(ctx, P.f64, V.vals.p, bits, P.kf_words,
                              static_cast<const uint8_t *>(V.blocks.p),
                              static_cast<const unsigned long long *>(V.boff.p), P.n_win,
-                             P.n_win > 0 ? static_cast<uint32_t *>(V.spart.p) : nullptr, S,
-                             d_items, n_items, o)))
+                             P.n_win > 0 ? static_cast<uint32_t *>(V.spart.p) : nullptr,
+                             P.sp_parts, S, d_items, n_items, o)))
       return rc;
   } else if (P.kind == RunPlan::TENSOR) {
     uint16_t *X = static_cast<uint16_t *>(V.vals.p);
@@ -1248,6 +1271,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
   for (int i = 0; i < n_plans; ++i) {
     plans[i].dst = static_cast<char *>(dst) + (size_t)i * one;
     plans[i].n_items = ctx->n_items;
+    plans[i].shares_gpu = n_plans == 2 && ctx->opt_overlap;
     if ((rc = plan_buffers(ctx, plans[i]))) return rc;
   }
   if (ctx->reuse_prepared && prep_signature(ctx) != ctx->prep_sig) ctx->reuse_prepared = false;

@@ -169,13 +169,14 @@ struct MinAcc<double> {
 // Hybrid split (FP32 form): positions [0, 32*kf_words) are the frequently
 // present branches and run through the dense register tile here; the rest,
 // present in few samples, were summed by k_pairs_sparse<false> into spart
-// (per tile pair, 32-bit fixed point, scale 1 / sp_inv), added in the epilogue.
+// (sp_parts partial sums per tile pair, 32-bit fixed point, scale 1 / sp_inv),
+// added in the epilogue.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
     k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
-                     int32_t kf_words, const uint32_t *__restrict__ spart, double sp_inv,
-                     const double *__restrict__ S,
+                     int32_t kf_words, const uint32_t *__restrict__ spart, int32_t sp_parts,
+                     double sp_inv, const double *__restrict__ S,
                      int32_t flush, OutSpec o, unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sbuf = reinterpret_cast<T *>(smem_raw);  // [2 stages][BK][2 sides][TILE]
@@ -312,8 +313,13 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
         if constexpr (sizeof(T) == 4) {
           const float den = (float)Si + Sj_f[qj];
           float M = tot[i * TILE + j];
-          if (sparse)
-            M = __fmaf_rn((float)spart[(int64_t)blockIdx.x * TILE * TILE + i * TILE + j], sp_inv_f, M);
+          if (sparse) {
+            // the parts' integer sums add exactly (their total is below 2^31)
+            const uint32_t *sp = spart + (int64_t)blockIdx.x * TILE * TILE + i * TILE + j;
+            uint32_t q = 0;
+            for (int p = 0; p < sp_parts; ++p) q += sp[(int64_t)p * gridDim.x * TILE * TILE];
+            M = __fmaf_rn((float)q, sp_inv_f, M);
+          }
           put_pair(o, sd, li, lj, ratio01_f32(__fmaf_rn(-2.f, M, den), den));
         } else {
           const double den = Si + S[colJ + j];
@@ -341,8 +347,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
 // that lanes on one column of different rows use different banks; it is
 // copied to spart at the end.
 //
-// A CTA of 32 warps per tile pair; each warp walks its own bitmap words
-// (kf_words + warp, + 32, ...) with no CTA-wide barrier in the loop.  For a
+// A CTA of 32 warps per (tile pair, part): part p of n_parts takes the bitmap
+// words kf_words + 32 p + warp, + 32 n_parts, ... (each warp its own, with no
+// CTA-wide barrier in the loop) and writes its own partial sums, so that the
+// tile pairs x parts fill the SMs' waves evenly.  For a
 // word, the rank of its first flagged row in the window's block is the
 // popcount of the block's earlier words; lane l takes the branch of bit l when
 // it is flagged in both tiles.  A weighted entry is one 8-byte (value, row)
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
                    int32_t n_words, int32_t kf_words, int32_t k_words, int32_t n_win,
                    const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
                    unsigned long long blocks_cap, int32_t n_tiles,
-                   const uint32_t *__restrict__ qlen,
+                   const uint32_t *__restrict__ qlen, int32_t n_parts,
                    typename SparseCfg<PRES>::Acc *__restrict__ spart,
                    unsigned long long *__restrict__ n_updates) {
   using Acc = typename SparseCfg<PRES>::Acc;
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   // blocks that did not fit their buffer were not written (the fill reported
   // it): read none of them
   const int w_end = boff[(int64_t)n_tiles * n_win] > blocks_cap ? kf_words : k_words;
-  for (int w = kf_words + warp; w < w_end; w += kSpWarps) {
+  for (int w = kf_words + (int)blockIdx.y * kSpWarps + warp; w < w_end; w += kSpWarps * n_parts) {
     const uint32_t mI = __ldg(bI + w), mJ = __ldg(bJ + w);
     const uint32_t both = mI & mJ;
     if (both == 0u) continue;  // warp-uniform
@@ -588,7 +596,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     }
   }
   __syncthreads();
-  Acc *dst = spart + (int64_t)blockIdx.x * TILE * TILE;
+  Acc *dst = spart + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TILE * TILE;
   for (int x = tid; x < TILE * TILE; x += kSpThreads) {
     const int q = (x / TILE) * kAccLd + x % TILE;
     if constexpr (PRES)
@@ -732,8 +740,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
                    int32_t kf_words, const uint8_t *blocks, const unsigned long long *boff,
-                   int32_t n_win, uint32_t *spart, const double *S, const WorkItem *items,
-                   int32_t n_items, const OutSpec &o) {
+                   int32_t n_win, uint32_t *spart, int32_t sp_parts, const double *S,
+                   const WorkItem *items, int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
   const size_t elem = f64 ? sizeof(double) : sizeof(float);
@@ -746,7 +754,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
-        1.0, S, 0, o, cur_counters(ctx));
+        1, 1.0, S, 0, o, cur_counters(ctx));
     ctx->stat_launches += 1;
   } else {
     const bool sparse = n_win > 0;
@@ -756,9 +764,9 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
       e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSm);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
-      k_pairs_sparse<false><<<n_items, kSpThreads, kSm, ctx->stream>>>(
+      k_pairs_sparse<false><<<dim3(n_items, sp_parts), kSpThreads, kSm, ctx->stream>>>(
           items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-          cur_bufs(ctx).blocks.bytes, ctx->n_tiles, nullptr, spart,
+          cur_bufs(ctx).blocks.bytes, ctx->n_tiles, nullptr, sp_parts, spart,
           cur_counters(ctx) + 2);
       ctx->stat_launches += 1;
     }
@@ -768,7 +776,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
         items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
-        sparse ? spart : nullptr, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
+        sparse ? spart : nullptr, sp_parts, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
         cur_counters(ctx));
     ctx->stat_launches += 1;
   }
@@ -788,7 +796,7 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
   k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
       items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-      cur_bufs(ctx).blocks.bytes, ctx->n_tiles, ctx->d_qperm, spart,
+      cur_bufs(ctx).blocks.bytes, ctx->n_tiles, ctx->d_qperm, 1, spart,
       cur_counters(ctx) + 2);
   ctx->stat_launches += 1;
   e = cudaGetLastError();

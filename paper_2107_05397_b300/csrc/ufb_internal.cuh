@@ -243,12 +243,13 @@ int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t 
 int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a);
 
 // pair kernels ------------------------------------------------------------
-// spart: [n_items][TILE * TILE] u32 partial sums of the sparse kernel.
+// spart: [sp_parts][n_items][TILE * TILE] u32 partial sums of the sparse
+// kernel (part p sums the bitmap words 32 p + warp modulo 32 sp_parts).
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
                    const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
                    const unsigned long long *boff, int32_t n_win, uint32_t *spart,
-                   const double *S, const WorkItem *items, int32_t n_items,
-                   const OutSpec &o);
+                   int32_t sp_parts, const double *S, const WorkItem *items,
+                   int32_t n_items, const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,
                  const uint32_t *gbits, const double *a, const WorkItem *items,
                  int32_t n_items, const OutSpec &o);
