@@ -786,7 +786,7 @@ static int32_t sparse_parts(int32_t n_items, int sms) {
   if (n_items <= 0 || sms <= 0) return 1;
   int32_t best = 1;
   double best_t = 1e300;
-  for (int32_t p = 1; p <= 8; ++p) {
+  for (int32_t p = 1; p <= kMaxSparseParts; ++p) {
     const double waves = std::ceil((double)n_items * p / sms);
     const double t = waves / p * (1.0 + 0.01 * p);
     if (t < best_t - 1e-9) {

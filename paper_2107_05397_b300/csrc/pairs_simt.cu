@@ -317,7 +317,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
             // the parts' integer sums add exactly (their total is below 2^31)
             const uint32_t *sp = spart + (int64_t)blockIdx.x * TILE * TILE + i * TILE + j;
             uint32_t q = 0;
-            for (int p = 0; p < sp_parts; ++p) q += sp[(int64_t)p * gridDim.x * TILE * TILE];
+#pragma unroll
+            for (int p = 0; p < kMaxSparseParts; ++p)  // loads issued together
+              if (p < sp_parts) q += sp[(int64_t)p * gridDim.x * TILE * TILE];
             M = __fmaf_rn((float)q, sp_inv_f, M);
           }
           put_pair(o, sd, li, lj, ratio01_f32(__fmaf_rn(-2.f, M, den), den));
@@ -521,53 +523,57 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       const int nL = (int)(d & 0xffu), nT = (int)((d >> 8) & 0xffu);
       const bool laneJ = (d >> 16) != 0u;
       const int mL = laneJ ? 1 : kAccLd, mT = laneJ ? kAccLd : 1;  // accumulator strides
-      // copy the swept side into the scratch: every load issued before the
-      // first store (one memory round trip, not one per 32 entries); the
-      // weighted lane side's first entry is loaded alongside
-      unsigned long long eb0 = 0;
-      const int b0 = nL <= 32 ? (int)(divtab[nL - 1][lane] & 0xffu) : lane;
-      if constexpr (PRES) {
-        const uint8_t *rT = (laneJ ? riI : riJ) + bsT;
-        if (b0 < nL) eb0 = __ldg((laneJ ? riJ : riI) + bsL + b0);
-        uint8_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-        if (lane < nT) r0 = __ldg(rT + lane);
-        if (lane + 32 < nT) r1 = __ldg(rT + lane + 32);
-        if (lane + 64 < nT) r2 = __ldg(rT + lane + 64);
-        if (lane + 96 < nT) r3 = __ldg(rT + lane + 96);
-        if (lane < nT) rS[lane] = r0;
-        if (lane + 32 < nT) rS[lane + 32] = r1;
-        if (lane + 64 < nT) rS[lane + 64] = r2;
-        if (lane + 96 < nT) rS[lane + 96] = r3;
-      } else {
-        const unsigned long long *qT = (laneJ ? eI : eJ) + bsT;
-        if (b0 < nL) eb0 = __ldg((laneJ ? eJ : eI) + bsL + b0);
-        unsigned long long t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-        if (lane < nT) t0 = __ldg(qT + lane);
-        if (lane + 32 < nT) t1 = __ldg(qT + lane + 32);
-        if (lane + 64 < nT) t2 = __ldg(qT + lane + 64);
-        if (lane + 96 < nT) t3 = __ldg(qT + lane + 96);
-        // stored ready for the sweep: (accumulator offset of the row, value)
-        uint2 *eS2 = reinterpret_cast<uint2 *>(eS);
-        auto prep = [mT](unsigned long long e) {
-          return make_uint2((uint32_t)(e & 0xffu) * (uint32_t)mT, (uint32_t)(e >> 32));
-        };
-        if (lane < nT) eS2[lane] = prep(t0);
-        if (lane + 32 < nT) eS2[lane + 32] = prep(t1);
-        if (lane + 64 < nT) eS2[lane + 64] = prep(t2);
-        if (lane + 96 < nT) eS2[lane + 96] = prep(t3);
-      }
-      __syncwarp();
-      int g, G, b;
+      // lane (g, b) of the sweep: one divtab / gtab read, before the scratch
+      // stores (which would force a re-read)
+      int g = 0, G = 1, b = lane;
       if (nL <= 32) {
         const uint32_t t0 = divtab[nL - 1][lane];
         g = (int)(t0 >> 8);
         b = (int)(t0 & 0xffu);
         G = gtab[nL - 1];
-      } else {
-        g = 0;
-        b = lane;
-        G = 1;
       }
+      // copy the swept side into the scratch: every load issued before the
+      // first store (one memory round trip, not one per 32 entries), the
+      // lane side's first entry alongside; entries past 32 behind
+      // warp-uniform branches (most swept sides have at most 32)
+      unsigned long long eb0 = 0;
+      if constexpr (PRES) {
+        const uint8_t *rT = (laneJ ? riI : riJ) + bsT;
+        if (b < nL) eb0 = __ldg((laneJ ? riJ : riI) + bsL + b);
+        if (nT <= 32) {
+          if (lane < nT) rS[lane] = __ldg(rT + lane);
+        } else {
+          uint8_t r0 = __ldg(rT + lane), r1 = 0, r2 = 0, r3 = 0;
+          if (lane + 32 < nT) r1 = __ldg(rT + lane + 32);
+          if (lane + 64 < nT) r2 = __ldg(rT + lane + 64);
+          if (lane + 96 < nT) r3 = __ldg(rT + lane + 96);
+          rS[lane] = r0;
+          if (lane + 32 < nT) rS[lane + 32] = r1;
+          if (lane + 64 < nT) rS[lane + 64] = r2;
+          if (lane + 96 < nT) rS[lane + 96] = r3;
+        }
+      } else {
+        const unsigned long long *qT = (laneJ ? eI : eJ) + bsT;
+        if (b < nL) eb0 = __ldg((laneJ ? eJ : eI) + bsL + b);
+        // stored ready for the sweep: (accumulator offset of the row, value)
+        uint2 *eS2 = reinterpret_cast<uint2 *>(eS);
+        auto prep = [mT](unsigned long long e) {
+          return make_uint2((uint32_t)(e & 0xffu) * (uint32_t)mT, (uint32_t)(e >> 32));
+        };
+        if (nT <= 32) {
+          if (lane < nT) eS2[lane] = prep(__ldg(qT + lane));
+        } else {
+          unsigned long long t0 = __ldg(qT + lane), t1 = 0, t2 = 0, t3 = 0;
+          if (lane + 32 < nT) t1 = __ldg(qT + lane + 32);
+          if (lane + 64 < nT) t2 = __ldg(qT + lane + 64);
+          if (lane + 96 < nT) t3 = __ldg(qT + lane + 96);
+          eS2[lane] = prep(t0);
+          if (lane + 32 < nT) eS2[lane + 32] = prep(t1);
+          if (lane + 64 < nT) eS2[lane + 64] = prep(t2);
+          if (lane + 96 < nT) eS2[lane + 96] = prep(t3);
+        }
+      }
+      __syncwarp();
       for (; b < nL; b += 32) {  // one pass when nL <= 32
         if (g < G) {
           if constexpr (PRES) {

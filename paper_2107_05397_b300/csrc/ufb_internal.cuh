@@ -244,7 +244,9 @@ int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a);
 
 // pair kernels ------------------------------------------------------------
 // spart: [sp_parts][n_items][TILE * TILE] u32 partial sums of the sparse
-// kernel (part p sums the bitmap words 32 p + warp modulo 32 sp_parts).
+// kernel (part p sums the bitmap words 32 p + warp modulo 32 sp_parts),
+// 1 <= sp_parts <= kMaxSparseParts.
+constexpr int kMaxSparseParts = 8;
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
                    const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
                    const unsigned long long *boff, int32_t n_win, uint32_t *spart,
