@@ -95,7 +95,8 @@ KERNEL_SOURCES = {
 }
 # functions of capi.cu that plan the pair launches (work items, their order,
 # buffer sizes): part of every pair kernel's record
-PLANNING_FUNCTIONS = ("void study_items(", "static int plan_items(", "static int plan_buffers(")
+PLANNING_FUNCTIONS = ("void study_items(", "static int plan_items(", "static int plan_buffers(",
+                      "static int32_t sparse_parts(")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
 
