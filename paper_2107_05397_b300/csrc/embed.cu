@@ -81,9 +81,37 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
     for (int32_t c = c0; c < c1; ++c)
       if (flag[(int64_t)child_idx[c] * n_tiles + t]) fmask |= few ? 1u << (c - c0) : 1u;
   if (t < n_tiles) flag[(int64_t)node * n_tiles + t] = fmask ? 1 : 0;
-  for (uint32_t m = __ballot_sync(0xffffffffu, fmask != 0); m; m &= m - 1) {
+  const int32_t gbase = (int32_t)(item % n_groups) * 32;
+  uint32_t m = __ballot_sync(0xffffffffu, fmask != 0);
+  if (c1 - c0 == 2) {
+    // two children (nearly every node of a binary tree): two flagged tiles
+    // per pass, the four child rows' loads issued before either store
+    const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
+    const uint4 *r0 = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc) + lane;
+    const uint4 *r1 = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc) + lane;
+    uint4 *rn = reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc) + lane;
+    constexpr int kQ = TILE / 4;  // uint4 per tile row
+    while (m) {
+      const int sa = __ffs(m) - 1;
+      m &= m - 1;
+      const int sb = m ? __ffs(m) - 1 : -1;
+      if (m) m &= m - 1;
+      const uint32_t fa = __shfl_sync(0xffffffffu, fmask, sa);
+      const uint32_t fb = __shfl_sync(0xffffffffu, fmask, sb < 0 ? sa : sb);
+      const int64_t oa = (int64_t)(gbase + sa) * kQ, ob = (int64_t)(gbase + (sb < 0 ? sa : sb)) * kQ;
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      const uint4 a0 = (fa & 1u) ? __ldg(r0 + oa) : z;
+      const uint4 a1 = (fa & 2u) ? __ldg(r1 + oa) : z;
+      const uint4 b0 = (sb >= 0 && (fb & 1u)) ? __ldg(r0 + ob) : z;
+      const uint4 b1 = (sb >= 0 && (fb & 2u)) ? __ldg(r1 + ob) : z;
+      rn[oa] = make_uint4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+      if (sb >= 0) rn[ob] = make_uint4(b0.x + b1.x, b0.y + b1.y, b0.z + b1.z, b0.w + b1.w);
+    }
+    return;
+  }
+  for (; m; m &= m - 1) {
     const int src = __ffs(m) - 1;
-    const int32_t ts = (int32_t)(item % n_groups) * 32 + src;
+    const int32_t ts = gbase + src;
     const uint32_t fm = __shfl_sync(0xffffffffu, fmask, src);
     uint4 s = make_uint4(0u, 0u, 0u, 0u);
     for (int32_t c = c0; c < c1; ++c) {
@@ -105,8 +133,9 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
 // the 32 columns 128 t + 32 q .. +31, and each warp takes four nodes of a
 // level at a time (eight lanes x 16 bytes per node); __syncthreads separates
 // the levels, since a level reads only what earlier levels wrote for the same
-// columns.  Global memory is read with plain (coherent) loads.  A node's flag
-// is the same for the four quarters of its tile, so their stores agree.
+// columns.  Global memory is read with plain (coherent) loads; a child row
+// whose flag is clear is read but not used (every row is allocated).  A node's
+// flag is the same for the four quarters of its tile, so their stores agree.
 constexpr int kTailThreads = 1024;
 
 __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
@@ -123,16 +152,33 @@ __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
       const int32_t node = nodes[i];
       uint4 s = make_uint4(0u, 0u, 0u, 0u);
       bool any = false;
-      const int32_t c1 = child_ptr[node + 1];
-      for (int32_t c = child_ptr[node]; c < c1; ++c) {
-        const int32_t ch = child_idx[c];
-        if (flag[(int64_t)ch * n_tiles + t]) {
-          any = true;
-          const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
-          s.x += v.x;
-          s.y += v.y;
-          s.z += v.z;
-          s.w += v.w;
+      const int32_t c0 = child_ptr[node], c1 = child_ptr[node + 1];
+      if (c1 - c0 == 2) {
+        // two children: both rows loaded beside their flags (near the root
+        // both children nearly always hold the tile), then selected
+        const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
+        const uint8_t f0 = flag[(int64_t)ch0 * n_tiles + t], f1 = flag[(int64_t)ch1 * n_tiles + t];
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc + col);
+        const uint4 v1 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc + col);
+        any = (f0 | f1) != 0;
+        if (f0) s = v0;
+        if (f1) {
+          s.x += v1.x;
+          s.y += v1.y;
+          s.z += v1.z;
+          s.w += v1.w;
+        }
+      } else {
+        for (int32_t c = c0; c < c1; ++c) {
+          const int32_t ch = child_idx[c];
+          if (flag[(int64_t)ch * n_tiles + t]) {
+            any = true;
+            const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+          }
         }
       }
       if (l8 == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
