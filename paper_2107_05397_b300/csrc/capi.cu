@@ -140,7 +140,8 @@ void free_ctx(unifrac_ctx *ctx) {
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->d_level_nodes, ctx->d_level_ptr, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
-                  ctx->d_frow_ptr,    ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
+                  ctx->d_frow_ptr,    ctx->d_tchunk_row, ctx->d_tchunk_lo,
+                  ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_S,           ctx->d_perm,
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
@@ -493,6 +494,16 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       return fail(ctx, UNIFRAC_E_BAD_TABLE,
                   "sample " + std::to_string(i) + " has a total count >= 2^32");
   ctx->n_frows = (int32_t)frow_tip.size();
+  std::vector<int32_t> tchunk_row;
+  std::vector<int64_t> tchunk_lo;
+  tchunk_row.reserve(frow_tip.size() + (size_t)(frow_ptr.back() / ctx->tip_chunk) + 1);
+  tchunk_lo.reserve(tchunk_row.capacity());
+  for (int32_t r = 0; r < ctx->n_frows; ++r)
+    for (int64_t lo = frow_ptr[r]; lo < frow_ptr[r + 1]; lo += ctx->tip_chunk) {
+      tchunk_row.push_back(r);
+      tchunk_lo.push_back(lo);
+    }
+  ctx->n_tchunks = (int64_t)tchunk_row.size();
   // ------------------------------------------- presence counts and pruning
   // n_b: the samples with a non-zero count below branch b, per study, from
   // per-node sample bitsets built on the device (tips from their table rows,
@@ -518,6 +529,8 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     if ((rc = upload(ctx, &ctx->d_child_idx, child_idx))) return rc;
     if ((rc = upload(ctx, &ctx->d_frow_tip, frow_tip))) return rc;
     if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
+    if ((rc = upload(ctx, &ctx->d_tchunk_row, tchunk_row))) return rc;
+    if ((rc = upload(ctx, &ctx->d_tchunk_lo, tchunk_lo))) return rc;
     if (!direct) {
       if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
     } else {  // the caller's sample indices, mapped to columns when studies add padding

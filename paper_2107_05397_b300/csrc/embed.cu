@@ -25,28 +25,35 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
-// Tip rows: one warp per table row (a feature on a tip).  Each 128-column tile
-// that holds an entry is zeroed, flagged and then receives the counts.
-__global__ void k_tip_rows(int32_t n_frows, const int32_t *__restrict__ frow_tip,
+// Tip rows, in chunks of at most `chunk` entries of one table row (a feature
+// on a tip), one warp per chunk: rows are uneven (a common feature has an
+// entry in nearly every sample), chunks are not.  Two launches: k_tip_zero
+// zeroes and flags every 128-column tile a row touches, each tile by the
+// chunk that holds the row's first entry in it, then k_tip_scatter writes
+// the counts (two chunks of a row can share a tile, so every zeroing must
+// come before any count).
+__global__ void k_tip_zero(int64_t n_chunks, const int32_t *__restrict__ chunk_row,
+                           const int64_t *__restrict__ chunk_lo, int64_t chunk,
+                           const int32_t *__restrict__ frow_tip,
                            const int64_t *__restrict__ frow_ptr,
-                           const int32_t *__restrict__ ent_col,
-                           const uint32_t *__restrict__ ent_cnt, uint32_t *cnt,
-                           uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+                           const int32_t *__restrict__ ent_col, uint32_t *cnt, uint8_t *flag,
+                           int64_t ldc, int32_t n_tiles) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= n_frows) return;
-  const int32_t tip = frow_tip[warp];
-  const int64_t lo = frow_ptr[warp], hi = frow_ptr[warp + 1];
+  if (warp >= n_chunks) return;
+  const int32_t r = chunk_row[warp];
+  const int64_t lo = chunk_lo[warp], rlo = frow_ptr[r], hi = min(frow_ptr[r + 1], lo + chunk);
+  const int32_t tip = frow_tip[r];
   uint32_t *row = cnt + (int64_t)tip * ldc;
-  // clear each tile the row touches: the whole warp writes one tile (32
-  // lanes x 16 bytes) per step, tiles found by a ballot over 32 entries
+  // the whole warp writes one tile (32 lanes x 16 bytes) per step, tiles
+  // found by a ballot over 32 entries
   for (int64_t base = lo; base < hi; base += 32) {
     const int64_t e = base + lane;
     int32_t t = -1;
     bool first = false;
     if (e < hi) {
       t = ent_col[e] / TILE;
-      first = e == lo || ent_col[e - 1] / TILE != t;
+      first = e == rlo || ent_col[e - 1] / TILE != t;
     }
     for (uint32_t m = __ballot_sync(0xffffffffu, first); m; m &= m - 1) {
       const int32_t ts = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
@@ -54,7 +61,21 @@ __global__ void k_tip_rows(int32_t n_frows, const int32_t *__restrict__ frow_tip
       if (lane == 0) flag[(int64_t)tip * n_tiles + ts] = 1;
     }
   }
-  __syncwarp();
+}
+
+__global__ void k_tip_scatter(int64_t n_chunks, const int32_t *__restrict__ chunk_row,
+                              const int64_t *__restrict__ chunk_lo, int64_t chunk,
+                              const int32_t *__restrict__ frow_tip,
+                              const int64_t *__restrict__ frow_ptr,
+                              const int32_t *__restrict__ ent_col,
+                              const uint32_t *__restrict__ ent_cnt, uint32_t *cnt, int64_t ldc) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_chunks) return;
+  const int32_t r = chunk_row[warp];
+  const int64_t lo = chunk_lo[warp], hi = min(frow_ptr[r + 1], lo + chunk);
+  uint32_t *row = cnt + (int64_t)frow_tip[r] * ldc;
+#pragma unroll 4
   for (int64_t e = lo + lane; e < hi; e += 32) row[ent_col[e]] = ent_cnt[e];
 }
 
@@ -824,13 +845,17 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
   cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)ctx->n_nodes * ctx->n_tiles, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset flags");
   ctx->stat_launches += 1;
-  if (ctx->n_frows > 0 && ctx->n_tiles > 0) {
-    const int64_t threads = (int64_t)ctx->n_frows * 32;
-    const int blocks = (int)((threads + 255) / 256);
-    k_tip_rows<<<blocks, 256, 0, st>>>(ctx->n_frows, ctx->d_frow_tip, ctx->d_frow_ptr,
-                                       ctx->d_fent_col, ctx->d_fent_cnt, cnt, flag, ldc,
-                                       ctx->n_tiles);
-    ctx->stat_launches += 1;
+  if (ctx->n_tchunks > 0 && ctx->n_tiles > 0) {
+    const int64_t blocks = (ctx->n_tchunks * 32 + 255) / 256;
+    k_tip_zero<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
+                                                 ctx->d_tchunk_lo, ctx->tip_chunk, ctx->d_frow_tip,
+                                                 ctx->d_frow_ptr, ctx->d_fent_col, cnt, flag, ldc,
+                                                 ctx->n_tiles);
+    k_tip_scatter<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
+                                                    ctx->d_tchunk_lo, ctx->tip_chunk,
+                                                    ctx->d_frow_tip, ctx->d_frow_ptr,
+                                                    ctx->d_fent_col, ctx->d_fent_cnt, cnt, ldc);
+    ctx->stat_launches += 2;
   }
   // one launch per level while the levels are large, then the rest in one
   // launch (levels from the first with at most kTailNodes nodes)

@@ -90,6 +90,11 @@ struct unifrac_ctx {
   int32_t n_frows = 0;
   int32_t *d_frow_tip = nullptr;      // [n_frows] tip node of the row
   int64_t *d_frow_ptr = nullptr;      // [n_frows+1]
+  // tip rows cut into chunks of at most tip_chunk entries, one warp each
+  // (a common feature has an entry in nearly every sample)
+  int64_t n_tchunks = 0, tip_chunk = 256;
+  int32_t *d_tchunk_row = nullptr;    // [n_tchunks] row of the chunk
+  int64_t *d_tchunk_lo = nullptr;     // [n_tchunks] its first entry
   int32_t *d_fent_col = nullptr;      // [nnz'] embedding column (sorted per row)
   uint32_t *d_fent_cnt = nullptr;     // [nnz'] count (> 0)
   double *d_inv_total = nullptr;      // [n_cols] 1 / C_i (0 for empty or padding)

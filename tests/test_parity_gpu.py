@@ -152,6 +152,25 @@ def test_deep_caterpillar_tree(variant, precision):
     check_full(got, ref, precision)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_common_features_span_several_tip_chunks(variant, precision):
+    """Table rows longer than the embedding's 256-entry row chunks: features
+    present in every sample, in 90 % and in 60 % of them (chunk ends inside
+    128-column tiles, so two chunks share a tile), beside sparse ones."""
+    rng = np.random.default_rng(31)
+    tree = synth.yule_tree(300, rng, 0.1)
+    tips = tree.tips()
+    N = 700
+    dense = (rng.random((tips.shape[0], N)) < 0.03) * rng.integers(1, 20, (tips.shape[0], N))
+    for f, p in ((0, 1.0), (1, 0.9), (2, 0.9), (3, 0.6), (40, 1.0)):
+        dense[f] = (rng.random(N) < p) * rng.integers(1, 50, N)
+    table = synth.dense_to_table(dense, tips)
+    ref = oracle.unifrac_full(tree, table, variant)
+    got = run(tree, table, variant, precision).reshape(N, N)
+    check_full(got, ref, precision)
+
+
 def test_star_tree_disjoint_samples_unweighted_is_one():
     F, N = 200, 64
     tree = synth.star_tree(F, 0.25)
