@@ -140,7 +140,7 @@ void free_ctx(unifrac_ctx *ctx) {
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->d_level_nodes, ctx->d_level_ptr, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
-                  ctx->d_frow_ptr,    ctx->d_tchunk_row, ctx->d_tchunk_lo,
+                  ctx->d_frow_ptr,    ctx->d_tchunk_row, ctx->d_tchunk_lo, ctx->d_pmask,
                   ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_S,           ctx->d_perm,
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
@@ -531,6 +531,12 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     if ((rc = upload(ctx, &ctx->d_frow_ptr, frow_ptr))) return rc;
     if ((rc = upload(ctx, &ctx->d_tchunk_row, tchunk_row))) return rc;
     if ((rc = upload(ctx, &ctx->d_tchunk_lo, tchunk_lo))) return rc;
+    {
+      const size_t pm_bytes = std::max<size_t>((size_t)ctx->n_nodes * ctx->n_tiles * 16, 16);
+      const cudaError_t em = cudaMalloc(reinterpret_cast<void **>(&ctx->d_pmask), pm_bytes);
+      if (em != cudaSuccess) return cuda_fail(ctx, em, "device allocation (presence masks)");
+      ctx->device_bytes += pm_bytes;
+    }
     if (!direct) {
       if ((rc = upload(ctx, &ctx->d_fent_col, fent_col))) return rc;
     } else {  // the caller's sample indices, mapped to columns when studies add padding

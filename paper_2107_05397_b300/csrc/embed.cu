@@ -25,6 +25,14 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
+// Presence mask of a 128-column tile row held as one uint4 per lane (lane l:
+// columns 4 l .. 4 l + 3): word w has bit l set when column 4 l + w is
+// non-zero.  Every lane of the warp must call it.
+__device__ __forceinline__ uint4 nonzero_mask(const uint4 &v) {
+  return make_uint4(__ballot_sync(0xffffffffu, v.x != 0u), __ballot_sync(0xffffffffu, v.y != 0u),
+                    __ballot_sync(0xffffffffu, v.z != 0u), __ballot_sync(0xffffffffu, v.w != 0u));
+}
+
 // Tip rows, in chunks of at most `chunk` entries of one table row (a feature
 // on a tip), one warp per chunk: rows are uneven (a common feature has an
 // entry in nearly every sample), chunks are not.  Two launches: k_tip_zero
@@ -37,7 +45,7 @@ __global__ void k_tip_zero(int64_t n_chunks, const int32_t *__restrict__ chunk_r
                            const int32_t *__restrict__ frow_tip,
                            const int64_t *__restrict__ frow_ptr,
                            const int32_t *__restrict__ ent_col, uint32_t *cnt, uint8_t *flag,
-                           int64_t ldc, int32_t n_tiles) {
+                           uint4 *pmask, int64_t ldc, int32_t n_tiles) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_chunks) return;
@@ -58,7 +66,10 @@ __global__ void k_tip_zero(int64_t n_chunks, const int32_t *__restrict__ chunk_r
     for (uint32_t m = __ballot_sync(0xffffffffu, first); m; m &= m - 1) {
       const int32_t ts = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
       reinterpret_cast<uint4 *>(row + (int64_t)ts * TILE)[lane] = make_uint4(0u, 0u, 0u, 0u);
-      if (lane == 0) flag[(int64_t)tip * n_tiles + ts] = 1;
+      if (lane == 0) {
+        flag[(int64_t)tip * n_tiles + ts] = 1;
+        pmask[(int64_t)tip * n_tiles + ts] = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
   }
 }
@@ -68,15 +79,24 @@ __global__ void k_tip_scatter(int64_t n_chunks, const int32_t *__restrict__ chun
                               const int32_t *__restrict__ frow_tip,
                               const int64_t *__restrict__ frow_ptr,
                               const int32_t *__restrict__ ent_col,
-                              const uint32_t *__restrict__ ent_cnt, uint32_t *cnt, int64_t ldc) {
+                              const uint32_t *__restrict__ ent_cnt, uint32_t *cnt,
+                              uint32_t *pmask_w, int64_t ldc, int32_t n_tiles) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_chunks) return;
   const int32_t r = chunk_row[warp];
   const int64_t lo = chunk_lo[warp], hi = min(frow_ptr[r + 1], lo + chunk);
-  uint32_t *row = cnt + (int64_t)frow_tip[r] * ldc;
+  const int32_t tip = frow_tip[r];
+  uint32_t *row = cnt + (int64_t)tip * ldc;
+  uint32_t *pm = pmask_w + (int64_t)tip * n_tiles * 4;
 #pragma unroll 4
-  for (int64_t e = lo + lane; e < hi; e += 32) row[ent_col[e]] = ent_cnt[e];
+  for (int64_t e = lo + lane; e < hi; e += 32) {
+    const int32_t c = ent_col[e];
+    const uint32_t v = ent_cnt[e];
+    row[c] = v;
+    // column 4 l + w of a tile is bit l of the tile's mask word w
+    if (v) atomicOr(pm + (int64_t)(c / TILE) * 4 + (c & 3), 1u << ((c % TILE) >> 2));
+  }
 }
 
 // One level: for every (node of the level, column tile), sum the flagged
@@ -88,7 +108,7 @@ __global__ void k_tip_scatter(int64_t n_chunks, const int32_t *__restrict__ chun
 __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
                         const int32_t *__restrict__ child_ptr,
                         const int32_t *__restrict__ child_idx, uint32_t *cnt,
-                        uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+                        uint8_t *flag, uint4 *pmask, int64_t ldc, int32_t n_tiles) {
   const int32_t n_groups = (n_tiles + 31) / 32;
   const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -125,8 +145,16 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
       const uint4 a1 = (fa & 2u) ? __ldg(r1 + oa) : z;
       const uint4 b0 = (sb >= 0 && (fb & 1u)) ? __ldg(r0 + ob) : z;
       const uint4 b1 = (sb >= 0 && (fb & 2u)) ? __ldg(r1 + ob) : z;
-      rn[oa] = make_uint4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
-      if (sb >= 0) rn[ob] = make_uint4(b0.x + b1.x, b0.y + b1.y, b0.z + b1.z, b0.w + b1.w);
+      const uint4 sumA = make_uint4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+      const uint4 sumB = make_uint4(b0.x + b1.x, b0.y + b1.y, b0.z + b1.z, b0.w + b1.w);
+      rn[oa] = sumA;
+      if (sb >= 0) rn[ob] = sumB;
+      const uint4 ma = nonzero_mask(sumA);
+      if (lane == 0) pmask[(int64_t)node * n_tiles + gbase + sa] = ma;
+      if (sb >= 0) {  // warp-uniform
+        const uint4 mb = nonzero_mask(sumB);
+        if (lane == 0) pmask[(int64_t)node * n_tiles + gbase + sb] = mb;
+      }
     }
     return;
   }
@@ -146,6 +174,8 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
       }
     }
     reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)ts * TILE)[lane] = s;
+    const uint4 ms = nonzero_mask(s);
+    if (lane == 0) pmask[(int64_t)node * n_tiles + ts] = ms;
   }
 }
 
@@ -156,54 +186,71 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
 // the levels, since a level reads only what earlier levels wrote for the same
 // columns.  Global memory is read with plain (coherent) loads; a child row
 // whose flag is clear is read but not used (every row is allocated).  A node's
-// flag is the same for the four quarters of its tile, so their stores agree.
+// flag is the same for the four quarters of its tile, so their stores agree;
+// each quarter writes its own byte of every word of the presence mask.
 constexpr int kTailThreads = 1024;
 
 __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
     const int32_t *__restrict__ nodes, const int32_t *__restrict__ level_ptr, int32_t L0,
     int32_t L1, const int32_t *__restrict__ child_ptr, const int32_t *__restrict__ child_idx,
-    uint32_t *cnt, uint8_t *flag, int64_t ldc, int32_t n_tiles) {
+    uint32_t *cnt, uint8_t *flag, uint8_t *pmask_b, int64_t ldc, int32_t n_tiles) {
   const int t = blockIdx.x >> 2, q = blockIdx.x & 3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, l8 = lane & 7;
   const int64_t col = (int64_t)t * TILE + q * 32 + l8 * 4;
   for (int L = L0; L < L1; ++L) {
     const int32_t lo = level_ptr[L], hi = level_ptr[L + 1];
-    for (int32_t i = lo + warp * 4 + g; i < hi; i += (kTailThreads / 32) * 4) {
-      const int32_t node = nodes[i];
+    // warp-uniform trip count (the mask ballots need every lane)
+    for (int32_t i0 = lo + warp * 4; i0 < hi; i0 += (kTailThreads / 32) * 4) {
+      const int32_t i = i0 + g;
+      const bool act = i < hi;
+      int32_t node = 0;
       uint4 s = make_uint4(0u, 0u, 0u, 0u);
       bool any = false;
-      const int32_t c0 = child_ptr[node], c1 = child_ptr[node + 1];
-      if (c1 - c0 == 2) {
-        // two children: both rows loaded beside their flags (near the root
-        // both children nearly always hold the tile), then selected
-        const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
-        const uint8_t f0 = flag[(int64_t)ch0 * n_tiles + t], f1 = flag[(int64_t)ch1 * n_tiles + t];
-        const uint4 v0 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc + col);
-        const uint4 v1 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc + col);
-        any = (f0 | f1) != 0;
-        if (f0) s = v0;
-        if (f1) {
-          s.x += v1.x;
-          s.y += v1.y;
-          s.z += v1.z;
-          s.w += v1.w;
-        }
-      } else {
-        for (int32_t c = c0; c < c1; ++c) {
-          const int32_t ch = child_idx[c];
-          if (flag[(int64_t)ch * n_tiles + t]) {
-            any = true;
-            const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
-            s.x += v.x;
-            s.y += v.y;
-            s.z += v.z;
-            s.w += v.w;
+      if (act) {
+        node = nodes[i];
+        const int32_t c0 = child_ptr[node], c1 = child_ptr[node + 1];
+        if (c1 - c0 == 2) {
+          // two children: both rows loaded beside their flags (near the root
+          // both children nearly always hold the tile), then selected
+          const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
+          const uint8_t f0 = flag[(int64_t)ch0 * n_tiles + t], f1 = flag[(int64_t)ch1 * n_tiles + t];
+          const uint4 v0 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc + col);
+          const uint4 v1 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc + col);
+          any = (f0 | f1) != 0;
+          if (f0) s = v0;
+          if (f1) {
+            s.x += v1.x;
+            s.y += v1.y;
+            s.z += v1.z;
+            s.w += v1.w;
+          }
+        } else {
+          for (int32_t c = c0; c < c1; ++c) {
+            const int32_t ch = child_idx[c];
+            if (flag[(int64_t)ch * n_tiles + t]) {
+              any = true;
+              const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
+              s.x += v.x;
+              s.y += v.y;
+              s.z += v.z;
+              s.w += v.w;
+            }
           }
         }
+        if (l8 == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
+        if (any) *reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + col) = s;
       }
-      if (l8 == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
-      if (any) *reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + col) = s;
+      // this quarter's bits of the tile's presence mask: bits 8 q .. 8 q + 7
+      // of each word, i.e. byte q (lanes of group g are ballot bits 8 g ..)
+      const uint4 m = nonzero_mask(s);
+      if (act && any && l8 == 0) {
+        uint8_t *pb = pmask_b + ((int64_t)node * n_tiles + t) * 16 + q;
+        pb[0] = (uint8_t)(m.x >> (8 * g));
+        pb[4] = (uint8_t)(m.y >> (8 * g));
+        pb[8] = (uint8_t)(m.z >> (8 * g));
+        pb[12] = (uint8_t)(m.w >> (8 * g));
+      }
     }
     __syncthreads();
   }
@@ -435,8 +482,9 @@ __global__ void __launch_bounds__(1024) k_scan_sizes(int64_t n, const uint32_t *
 
 // Fill: one warp per chunk of 32 positions of a block, at the offsets
 // cpre gives; the chunk's flagged rows get their rowstart entries and their
-// non-zero columns, compacted with four ballots (column 4l + w of lane l),
-// reading the counts cnt[perm[k]][col].  VALUES: entries also carry
+// non-zero columns, compacted with four ballots (column 4l + w of lane l)
+// over the counts cnt[perm[k]][col] (VALUES), or read as the row's presence
+// mask, which holds those four ballots (presence).  VALUES: entries also carry
 // round(v * scale) with v = len_k * (cnt * (1 / C_col)) in FP32, the same
 // roundings as the dense packing; scale is a power of two.
 template <bool VALUES>
@@ -444,6 +492,7 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
                             const uint32_t *__restrict__ bits, int32_t n_words,
                             const uint8_t *__restrict__ rc, int32_t k_pad,
                             const uint32_t *__restrict__ cnt, int64_t ldc,
+                            const uint4 *__restrict__ pmask,
                             const int32_t *__restrict__ perm,
                             const double *__restrict__ len_perm,
                             const double *__restrict__ inv_total, float scale,
@@ -513,23 +562,39 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
         m &= m - 1;
       }
     }
+    // VALUES: the counts (lane l: columns 4 l .. 4 l + 3); presence: the
+    // row's mask alone (16 bytes, the same for every lane)
     uint4 cv[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
       cv[g] = make_uint4(0u, 0u, 0u, 0u);
-      if (src[g] >= 0)
-        cv[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[kc + src[g]] * ldc +
-                                                 t * TILE + 4 * lane);
+      if (src[g] >= 0) {
+        if constexpr (VALUES)
+          cv[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[kc + src[g]] * ldc +
+                                                   t * TILE + 4 * lane);
+        else
+          cv[g] = pmask[(int64_t)perm[kc + src[g]] * n_tiles + t];
+      }
     }
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
       if (src[g] < 0) break;
       const uint32_t base = __shfl_sync(0xffffffffu, my_e, src[g]);
-      const uint32_t cc[4] = {cv[g].x, cv[g].y, cv[g].z, cv[g].w};
-      const uint32_t B0 = __ballot_sync(0xffffffffu, cc[0] != 0u);
-      const uint32_t B1 = __ballot_sync(0xffffffffu, cc[1] != 0u);
-      const uint32_t B2 = __ballot_sync(0xffffffffu, cc[2] != 0u);
-      const uint32_t B3 = __ballot_sync(0xffffffffu, cc[3] != 0u);
+      uint32_t cc[4] = {cv[g].x, cv[g].y, cv[g].z, cv[g].w};
+      uint32_t B0, B1, B2, B3;
+      if constexpr (VALUES) {
+        B0 = __ballot_sync(0xffffffffu, cc[0] != 0u);
+        B1 = __ballot_sync(0xffffffffu, cc[1] != 0u);
+        B2 = __ballot_sync(0xffffffffu, cc[2] != 0u);
+        B3 = __ballot_sync(0xffffffffu, cc[3] != 0u);
+      } else {
+        B0 = cc[0];
+        B1 = cc[1];
+        B2 = cc[2];
+        B3 = cc[3];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) cc[w] = (cc[w] >> lane) & 1u;
+      }
       const uint32_t c0 = __popc(B0), c1 = __popc(B1), c2 = __popc(B2);
       const uint32_t pos[4] = {(uint32_t)__popc(B0 & lt), c0 + (uint32_t)__popc(B1 & lt),
                                c0 + c1 + (uint32_t)__popc(B2 & lt),
@@ -555,19 +620,18 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
 // Block (column tile t, KR positions), warp w per bitmap word: lane l tests
 // position 32 w + l, the ballot is the (t, word) bitmap word (p0 is a multiple
 // of 32; words below it belong to the dense packing); then the flagged
-// positions' rows are read four at a time (16 bytes per lane) for the row's
-// count of non-zero columns rc and, when aq is given, aq[col] += q_k for every
-// column where branch k is present.
+// positions' presence masks (16 bytes each) are read four at a time for the
+// row's count of non-zero columns rc and, when aq is given, aq[col] += q_k for
+// every column where branch k is present.
 __global__ void __launch_bounds__(256) k_pack_rare(
     int32_t K, int32_t p0, const int32_t *__restrict__ perm, const uint32_t *__restrict__ qperm,
-    const uint32_t *__restrict__ cnt, const uint8_t *__restrict__ flag, int64_t ldc,
+    const uint4 *__restrict__ pmask, const uint8_t *__restrict__ flag,
     int32_t n_tiles, uint32_t *__restrict__ bits, int32_t n_words, uint8_t *__restrict__ rc,
     int32_t k_pad, unsigned long long *__restrict__ aq) {
   __shared__ unsigned long long red[kWarpsPerBlock][TILE];
   const int t = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kw = p0 + blockIdx.y * KR + w * WORD;  // first position of this warp's word
-  const int64_t col = (int64_t)t * TILE + lane * 4;
   const int k = kw + lane;
   const int32_t b = k < K ? perm[k] : 0;
   const bool fl = k < K && flag[(int64_t)b * n_tiles + t];
@@ -586,28 +650,29 @@ __global__ void __launch_bounds__(256) k_pack_rare(
         m &= m - 1;
       }
     }
+    // the row's presence mask (16 bytes, the same for every lane) instead of
+    // its 512 bytes of counts: bit lane of word w is column 4 lane + w
     uint4 c[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       c[u] = make_uint4(0u, 0u, 0u, 0u);
       if (src[u] >= 0) {
         const int32_t bu = __shfl_sync(0xffffffffu, b, src[u]);
-        c[u] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)bu * ldc + col);
+        c[u] = pmask[(int64_t)bu * n_tiles + t];
       }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       if (src[u] < 0) break;
       const int kk = kw + src[u];
-      const unsigned long long q = aq ? qperm[kk] : 0ull;
-      acc[0] += c[u].x ? q : 0ull;
-      acc[1] += c[u].y ? q : 0ull;
-      acc[2] += c[u].z ? q : 0ull;
-      acc[3] += c[u].w ? q : 0ull;
-      const int nz = __popc(__ballot_sync(0xffffffffu, c[u].x != 0u)) +
-                     __popc(__ballot_sync(0xffffffffu, c[u].y != 0u)) +
-                     __popc(__ballot_sync(0xffffffffu, c[u].z != 0u)) +
-                     __popc(__ballot_sync(0xffffffffu, c[u].w != 0u));
+      if (aq) {
+        const unsigned long long q = qperm[kk];
+        acc[0] += ((c[u].x >> lane) & 1u) ? q : 0ull;
+        acc[1] += ((c[u].y >> lane) & 1u) ? q : 0ull;
+        acc[2] += ((c[u].z >> lane) & 1u) ? q : 0ull;
+        acc[3] += ((c[u].w >> lane) & 1u) ? q : 0ull;
+      }
+      const int nz = __popc(c[u].x) + __popc(c[u].y) + __popc(c[u].z) + __popc(c[u].w);
       if (lane == 0) rc[(int64_t)t * k_pad + kk] = (uint8_t)nz;
     }
   }
@@ -629,9 +694,10 @@ int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_
   const int32_t p0 = kf_words * WORD;
   if (p0 >= ctx->K || ctx->n_tiles == 0) return UNIFRAC_OK;
   dim3 grid(ctx->n_tiles, (ctx->K - p0 + KR - 1) / KR);
-  k_pack_rare<<<grid, 256, 0, ctx->stream>>>(ctx->K, p0, ctx->d_perm, ctx->d_qperm, cnt, flag,
-                                             ctx->n_cols, ctx->n_tiles, bits, ctx->K_pad / WORD,
-                                             rc, ctx->K_pad, aq);
+  (void)cnt;  // the presence masks of the embedding stand in for the counts
+  k_pack_rare<<<grid, 256, 0, ctx->stream>>>(ctx->K, p0, ctx->d_perm, ctx->d_qperm, ctx->d_pmask,
+                                             flag, ctx->n_tiles, bits, ctx->K_pad / WORD, rc,
+                                             ctx->K_pad, aq);
   ctx->stat_launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse packing");
@@ -654,7 +720,8 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<true><<<grid_fill, 256, 0, st>>>(
         ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
-        ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre, blocks,
+        ctx->d_pmask, ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre,
+        blocks,
         cur_bufs(ctx).blocks.bytes, cur_counters(ctx) + 1);
   } else {
     k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
@@ -662,7 +729,8 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid_fill, 256, 0, st>>>(
         ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
-        ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks, cur_bufs(ctx).blocks.bytes,
+        ctx->d_pmask, ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks,
+        cur_bufs(ctx).blocks.bytes,
         cur_counters(ctx) + 1);
   }
   ctx->stat_launches += 3;
@@ -849,12 +917,14 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
     const int64_t blocks = (ctx->n_tchunks * 32 + 255) / 256;
     k_tip_zero<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
                                                  ctx->d_tchunk_lo, ctx->tip_chunk, ctx->d_frow_tip,
-                                                 ctx->d_frow_ptr, ctx->d_fent_col, cnt, flag, ldc,
-                                                 ctx->n_tiles);
+                                                 ctx->d_frow_ptr, ctx->d_fent_col, cnt, flag,
+                                                 ctx->d_pmask, ldc, ctx->n_tiles);
     k_tip_scatter<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
                                                     ctx->d_tchunk_lo, ctx->tip_chunk,
                                                     ctx->d_frow_tip, ctx->d_frow_ptr,
-                                                    ctx->d_fent_col, ctx->d_fent_cnt, cnt, ldc);
+                                                    ctx->d_fent_col, ctx->d_fent_cnt, cnt,
+                                                    reinterpret_cast<uint32_t *>(ctx->d_pmask),
+                                                    ldc, ctx->n_tiles);
     ctx->stat_launches += 2;
   }
   // one launch per level while the levels are large, then the rest in one
@@ -868,14 +938,15 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
     if (items == 0) continue;
     const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_level<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(
-        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, flag, ldc,
-        ctx->n_tiles);
+        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, flag,
+        ctx->d_pmask, ldc, ctx->n_tiles);
     ctx->stat_launches += 1;
   }
   if (L0 < ctx->n_levels && ctx->n_tiles > 0) {
     k_levels_tail<<<(unsigned)ctx->n_tiles * 4, kTailThreads, 0, st>>>(
         ctx->d_level_nodes, ctx->d_level_ptr, L0, ctx->n_levels, ctx->d_child_ptr,
-        ctx->d_child_idx, cnt, flag, ldc, ctx->n_tiles);
+        ctx->d_child_idx, cnt, flag, reinterpret_cast<uint8_t *>(ctx->d_pmask), ldc,
+        ctx->n_tiles);
     ctx->stat_launches += 1;
   }
   e = cudaGetLastError();

@@ -95,6 +95,10 @@ struct unifrac_ctx {
   int64_t n_tchunks = 0, tip_chunk = 256;
   int32_t *d_tchunk_row = nullptr;    // [n_tchunks] row of the chunk
   int64_t *d_tchunk_lo = nullptr;     // [n_tchunks] its first entry
+  // [n_nodes][n_tiles] presence masks written by the embedding beside the
+  // counts, valid where the tile is flagged: word w has bit l set when
+  // column 4 l + w of the tile holds a non-zero count
+  uint4 *d_pmask = nullptr;
   int32_t *d_fent_col = nullptr;      // [nnz'] embedding column (sorted per row)
   uint32_t *d_fent_cnt = nullptr;     // [nnz'] count (> 0)
   double *d_inv_total = nullptr;      // [n_cols] 1 / C_i (0 for empty or padding)
