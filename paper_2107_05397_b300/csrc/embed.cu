@@ -335,20 +335,22 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
 }
 
 // Lookup packing.  Block (column tile t, group block gb) of 128 threads, one
-// column each.  Group g holds positions 8g..8g+7; the byte of (g, col) has bit
+// column each, reading the presence masks of the flagged rows.  Group g holds positions 8g..8g+7; the byte of (g, col) has bit
 // j set when branch 8g+j is present in col.  Also the (t, g) group bitmap and
 // FP64 partial sums of a_col = sum_k len_k p[k][col] per group block.
 constexpr int GR = 32;  // groups per block
 
 __global__ void __launch_bounds__(128) k_pack_lookup(
     int32_t K, int32_t G, const int32_t *__restrict__ perm,
-    const double *__restrict__ len_perm, const uint32_t *__restrict__ cnt,
-    const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_cols, int32_t n_tiles,
+    const double *__restrict__ len_perm, const uint4 *__restrict__ pmask,
+    const uint8_t *__restrict__ flag, int32_t n_cols, int32_t n_tiles,
     uint8_t *__restrict__ bytes, uint32_t *__restrict__ gbits, int32_t g_words,
     double *__restrict__ partial) {
   const int t = blockIdx.x;
   const int g0 = blockIdx.y * GR;
   const int64_t col = (int64_t)t * TILE + threadIdx.x;
+  // this column in the presence masks: bit threadIdx.x / 4 of word threadIdx.x % 4
+  const int mw = threadIdx.x & 3, mb = threadIdx.x >> 2;
   double a = 0.0;
   uint32_t gword = 0;
   for (int gi = 0; gi < GR; ++gi) {
@@ -363,7 +365,9 @@ __global__ void __launch_bounds__(128) k_pack_lookup(
         const int32_t b = perm[k];
         if (flag[(int64_t)b * n_tiles + t]) {
           anyflag = true;
-          if (cnt[(int64_t)b * ldc + col] != 0u) {
+          const uint4 pm = pmask[(int64_t)b * n_tiles + t];
+          const uint32_t word = mw == 0 ? pm.x : mw == 1 ? pm.y : mw == 2 ? pm.z : pm.w;
+          if ((word >> mb) & 1u) {
             byte |= 1u << j;
             a += len_perm[k];
           }
@@ -978,6 +982,7 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bo
 
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, uint8_t *bytes,
                 double *tables, uint32_t *gbits, double *a) {
+  (void)cnt;  // the embedding's presence masks stand in for the counts
   cudaStream_t st = ctx->stream;
   const int32_t G = ctx->K_pad / 8;
   const int32_t g_words = (G + WORD - 1) / WORD;
@@ -986,9 +991,9 @@ int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, uint
   if (G > 0 && ctx->n_tiles > 0) {
     k_lookup_tables<<<G, 256, 0, st>>>(ctx->K, ctx->d_len_perm, tables);
     dim3 grid(ctx->n_tiles, n_gblocks);
-    k_pack_lookup<<<grid, 128, 0, st>>>(ctx->K, G, ctx->d_perm, ctx->d_len_perm, cnt, flag,
-                                        ctx->n_cols, ctx->n_cols, ctx->n_tiles, bytes, gbits,
-                                        g_words, partial);
+    k_pack_lookup<<<grid, 128, 0, st>>>(ctx->K, G, ctx->d_perm, ctx->d_len_perm, ctx->d_pmask,
+                                        flag, ctx->n_cols, ctx->n_tiles, bytes, gbits, g_words,
+                                        partial);
     ctx->stat_launches += 2;
   }
   if (ctx->n_cols > 0) {

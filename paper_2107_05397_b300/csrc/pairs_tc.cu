@@ -379,8 +379,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Packing for the tensor-core path.  Block (column tile t, 4 K-tiles) of 256
-// threads: reads 64 branch rows x 128 columns of counts per K-tile, transposes
-// through shared memory and writes sample-major BF16 rows of X (0/1) and of the
+// threads: reads the presence masks of 64 branch rows x 128 columns per K-tile
+// (16 bytes per row; word w, bit l is column 4 l + w), transposes through
+// shared memory and writes sample-major BF16 rows of X (0/1) and of the
 // three digit planes; K-tiles with no presence in the tile are not written
 // (the pair kernel never reads them) and get a 0 bit in the K-tile bitmap.
 // aq[col] += sum_k q_k p[k][col] (exact integers).
@@ -388,8 +389,8 @@ constexpr int PK_KT = 4;
 
 __global__ void __launch_bounds__(256)
     k_pack_tc(int32_t K, int32_t K_pad, int32_t dig_ld, const int32_t *__restrict__ perm,
-              const uint8_t *__restrict__ digits, const uint32_t *__restrict__ cnt,
-              const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_cols, int32_t n_tiles,
+              const uint8_t *__restrict__ digits, const uint4 *__restrict__ pmask,
+              const uint8_t *__restrict__ flag, int32_t n_cols, int32_t n_tiles,
               uint16_t *__restrict__ X, uint16_t *__restrict__ D, uint32_t *__restrict__ kbits,
               int32_t k_words, unsigned long long *__restrict__ aq) {
   __shared__ uint8_t pres[TC_BK][TILE + 16];
@@ -421,18 +422,17 @@ __global__ void __launch_bounds__(256)
       const int k = kt * TC_BK + r;
       const int32_t b = (k < K) ? perm[k] : -1;
       const bool valid = b >= 0 && flag[(int64_t)b * n_tiles + t];
-      uint32_t anyr = 0;
+      uint4 pm = make_uint4(0u, 0u, 0u, 0u);
+      if (valid) pm = pmask[(int64_t)b * n_tiles + t];
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)b * ldc + (int64_t)t * TILE + c0 + q);
-        pres[r][c0 + q + 0] = v.x != 0u;
-        pres[r][c0 + q + 1] = v.y != 0u;
-        pres[r][c0 + q + 2] = v.z != 0u;
-        pres[r][c0 + q + 3] = v.w != 0u;
-        anyr |= v.x | v.y | v.z | v.w;
+        const int l = (c0 + q) >> 2;
+        pres[r][c0 + q + 0] = (pm.x >> l) & 1u;
+        pres[r][c0 + q + 1] = (pm.y >> l) & 1u;
+        pres[r][c0 + q + 2] = (pm.z >> l) & 1u;
+        pres[r][c0 + q + 3] = (pm.w >> l) & 1u;
       }
-      if (anyr) any = 1;
+      if (pm.x | pm.y | pm.z | pm.w) any = 1;
     }
     __syncthreads();
     if (any) {
@@ -526,8 +526,9 @@ int pack_tc(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t 
   ctx->stat_launches += 1;
   if (ctx->n_tiles > 0 && n_kt > 0) {
     dim3 grid(ctx->n_tiles, (n_kt + PK_KT - 1) / PK_KT);
-    k_pack_tc<<<grid, 256, 0, st>>>(ctx->K, k_tc, ctx->K_pad, ctx->d_perm, ctx->d_digits, cnt,
-                                    flag, ctx->n_cols, ctx->n_cols, ctx->n_tiles, X, D, kbits,
+    (void)cnt;  // the embedding's presence masks stand in for the counts
+    k_pack_tc<<<grid, 256, 0, st>>>(ctx->K, k_tc, ctx->K_pad, ctx->d_perm, ctx->d_digits,
+                                    ctx->d_pmask, flag, ctx->n_cols, ctx->n_tiles, X, D, kbits,
                                     k_words, aq);
     ctx->stat_launches += 1;
   }
