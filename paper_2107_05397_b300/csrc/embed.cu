@@ -874,7 +874,7 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
   if (ctx->n_frows > 0)
     k_pres_tips<<<(unsigned)(((int64_t)ctx->n_frows * 32 + 255) / 256), 256, 0, st>>>(
         ctx->n_frows, ctx->d_frow_tip, ctx->d_frow_ptr, ctx->d_fent_col, bits, W);
-  constexpr int32_t kTailNodes = 1024;
+  constexpr int32_t kTailNodes = 256;
   int32_t L0 = 0;
   while (L0 < ctx->n_levels && ctx->level_ptr[L0 + 1] - ctx->level_ptr[L0] > kTailNodes) ++L0;
   for (int L = 0; L < L0; ++L) {
@@ -933,7 +933,7 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
   }
   // one launch per level while the levels are large, then the rest in one
   // launch (levels from the first with at most kTailNodes nodes)
-  constexpr int32_t kTailNodes = 1024;
+  constexpr int32_t kTailNodes = 256;
   int32_t L0 = 0;
   while (L0 < ctx->n_levels && ctx->level_ptr[L0 + 1] - ctx->level_ptr[L0] > kTailNodes) ++L0;
   for (int L = 0; L < L0 && ctx->n_tiles > 0; ++L) {
