@@ -335,9 +335,10 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
 }
 
 // Lookup packing.  Block (column tile t, group block gb) of 128 threads, one
-// column each, reading the presence masks of the flagged rows.  Group g holds positions 8g..8g+7; the byte of (g, col) has bit
-// j set when branch 8g+j is present in col.  Also the (t, g) group bitmap and
-// FP64 partial sums of a_col = sum_k len_k p[k][col] per group block.
+// column each, reading the presence masks of the flagged rows.  Group g holds
+// positions 8g..8g+7; the byte of (g, col) has bit j set when branch 8g+j is
+// present in col.  Also the (t, g) group bitmap and FP64 partial sums of
+// a_col = sum_k len_k p[k][col] per group block.
 constexpr int GR = 32;  // groups per block
 
 __global__ void __launch_bounds__(128) k_pack_lookup(
