@@ -121,6 +121,8 @@ enum unifrac_status {
  * passed); per-branch presence counts per study (which samples reach each
  * branch) from device bitsets (O(n x samples / 64) words); the branch order,
  * tensor-core length digits and per-sample weighted sums on the host.
+ * Allocates, besides the uploaded inputs, the per-run presence masks of the
+ * embedding: 16 bytes per (node, 128-column tile).
  * Synchronous; uses the current device.
  */
 int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
@@ -149,9 +151,10 @@ int unifrac_create(int32_t n_nodes, const int32_t *parent, const double *length,
  *                 (twice that for UNIFRAC_BOTH).
  *
  * Pipeline (all on the device): embedding of every branch (level-synchronous
- * postorder sums, skipping all-zero branch tiles), packing for the chosen
- * kernel, the pair kernel, and the epilogue writing `out`.  Work buffers are
- * allocated on first use and kept in the context.
+ * postorder sums, skipping all-zero branch tiles, with a presence mask per
+ * non-zero tile), packing for the chosen kernel, the pair kernel, and the
+ * epilogue writing `out`.  Work buffers are allocated on first use and kept
+ * in the context.
  */
 int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
                 int32_t stripe_start, int32_t stripe_stop, int layout,
