@@ -24,7 +24,9 @@
  * sums run over every non-root branch b of the tree.  Readings where the
  * paper is silent: the root branch is ignored (length treated as 0); a zero
  * denominator (both samples empty, only zero-length branches, i == j) gives
- * d = 0; explicit zero counts are absent features.
+ * d = 0; explicit zero counts are absent features; a duplicate (feature,
+ * sample) entry or two features on one tip make the table invalid (rejected,
+ * not summed).
  *
  * Steps, in the order of the definition:
  *   1. per sample, place each feature's count on its tip node;
@@ -98,6 +100,32 @@ static int oracle_prepare(int32_t n_nodes, const int32_t *parent,
   for (int32_t f = 0; f < n_features; ++f)
     if (indptr[f + 1] < indptr[f]) return ORACLE_E_TABLE;
   int64_t nnz = indptr[n_features];
+  /* A (feature, sample) cell appears at most once, and a tip carries at most
+   * one feature (a tip is one taxon): a second entry for the same cell, or a
+   * second feature on the same tip, is a malformed table, not a sum. */
+  {
+    int32_t *last_feature = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n_samples + 1));
+    char *tip_used = (char *)calloc((size_t)n_nodes, 1);
+    if (!last_feature || !tip_used) {
+      free(last_feature);
+      free(tip_used);
+      return ORACLE_E_OOM;
+    }
+    for (int32_t s = 0; s < n_samples; ++s) last_feature[s] = -1;
+    int bad = 0;
+    for (int32_t f = 0; f < n_features && !bad; ++f) {
+      if (tip_used[feature_node[f]]) bad = 1;
+      tip_used[feature_node[f]] = 1;
+      for (int64_t e = indptr[f]; e < indptr[f + 1] && !bad; ++e) {
+        int32_t s = indices[e];
+        if (s < 0 || s >= n_samples || last_feature[s] == f) bad = 1;
+        else last_feature[s] = f;
+      }
+    }
+    free(last_feature);
+    free(tip_used);
+    if (bad) return ORACLE_E_TABLE;
+  }
   in->n_nodes = n_nodes;
   in->parent = parent;
   in->length = length;

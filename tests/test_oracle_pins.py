@@ -359,6 +359,34 @@ def test_invalid_inputs_rejected():
         oracle.unifrac_full(tree, internal, UW)
 
 
+def test_duplicate_cells_and_shared_tips_rejected():
+    """A table with one (feature, sample) cell listed twice, or with two
+    features on one tip, is malformed and rejected; it is not read as the sum
+    of the entries (the readings of the problem statement for duplicates and
+    for a tip as one taxon)."""
+    tree = synth.Tree(parent=np.array([2, 2, -1], np.int32), length=np.ones(3))
+    fnode = np.array([0, 1], np.int32)
+    ok = synth.Table(n_features=2, n_samples=2, indptr=np.array([0, 2, 3], np.int64),
+                     indices=np.array([0, 1, 1], np.int32),
+                     counts=np.array([3, 1, 2], np.int32), feature_node=fnode)
+    d = oracle.unifrac_full(tree, ok, WN)
+    # sample 0: feature 0 only (w = 1, 0 on tips 0, 1); sample 1: features 0
+    # and 1 with counts 1 and 2 (w = 1/3, 2/3): (2/3 + 2/3) / (4/3 + 2/3)
+    assert d[0, 1] == pytest.approx(2.0 / 3.0, abs=1e-15)
+    for variant in (UW, WN):
+        dup = synth.Table(n_features=2, n_samples=2, indptr=np.array([0, 3, 4], np.int64),
+                          indices=np.array([0, 1, 1, 1], np.int32),
+                          counts=np.array([3, 1, 1, 2], np.int32), feature_node=fnode)
+        with pytest.raises(ValueError):
+            oracle.unifrac_full(tree, dup, variant)
+        shared = synth.Table(n_features=2, n_samples=2, indptr=np.array([0, 1, 2], np.int64),
+                             indices=np.array([0, 1], np.int32),
+                             counts=np.array([3, 1], np.int32),
+                             feature_node=np.array([0, 0], np.int32))
+        with pytest.raises(ValueError):
+            oracle.unifrac_full(tree, shared, variant)
+
+
 @pytest.mark.parametrize("variant", [UW, WN])
 def test_root_branch_length_is_ignored(variant):
     """Reading of the paper's silence on the root: its length never counts."""
@@ -462,6 +490,35 @@ def test_mantel_exhaustive_small_case():
         np.testing.assert_allclose(om.permute_condensed(y, q, n), x)
     assert len(hits) >= 1
     assert 0.0 < p <= 1.0
+
+
+def test_mantel_p_value_is_two_sided():
+    """With n = 3 the three pairs are (0,1), (0,2), (1,2); relabelling the
+    samples by pi sends the pair without sample c to the pair without pi(c),
+    so the six permutations realise all six orders of the pair vector.  For
+    x = y = (1, 2, 3) the statistics are the Pearson correlations of (1, 2, 3)
+    with its six orders, which are 1, 1/2, 1/2, -1/2, -1/2, -1 (the sample
+    reversal gives -1).  A two-sided count |r_m| >= |r| = 1 takes the identity
+    and the reversal: p = 3/7.  The one-sided counts r_m >= r and r_m <= r
+    would give 2/7; for y = reversed x (r = -1) the one-sided count r_m >= r
+    would give 7/7, the two-sided one 3/7 again."""
+    import itertools
+    from oracle import mantel as om
+    n = 3
+    x = np.array([1.0, 2.0, 3.0])
+    perms = np.array(list(itertools.permutations(range(n))))
+    r, stats, p = om.mantel(x, x.copy(), n, perms)
+    assert r == 1.0
+    assert sorted(stats.tolist()) == pytest.approx([-1.0, -0.5, -0.5, 0.5, 0.5, 1.0], abs=1e-15)
+    rev = [k for k, q in enumerate(perms) if list(q) == [2, 1, 0]][0]
+    assert stats[rev] == pytest.approx(-1.0, abs=1e-15)
+    assert p == pytest.approx(3.0 / 7.0, abs=1e-15)
+    r, stats, p = om.mantel(x, x[::-1].copy(), n, perms)
+    assert r == pytest.approx(-1.0, abs=1e-15)
+    assert p == pytest.approx(3.0 / 7.0, abs=1e-15)
+    # without the reversal only the identity reaches |r|: p = 2/(M + 1)
+    r, stats, p = om.mantel(x, x.copy(), n, perms[[k for k in range(6) if k != rev]])
+    assert p == pytest.approx(2.0 / 6.0, abs=1e-15)
 
 
 def test_mantel_undefined_cases():
