@@ -566,19 +566,30 @@ def test_create_statistics_large_tree_exact_reach():
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_streamed_output_equals_direct(small, n, precision):
     """unifrac_run_streamed (chunks of 7 stripes, and one chunk) gives the
-    matrices of unifrac_run, both layouts, every variant; odd and even N."""
+    matrices of the FP64 oracle element by element within the precision's
+    tolerance, and bit for bit those of unifrac_run, both layouts, every
+    variant; odd and even N."""
     import torch
-    w, _ = small
+    w, ref_small = small
     table = synth.dense_to_table(w.table.dense()[:, :n], w.table.feature_node) \
         if n != w.table.n_samples else w.table
+    ref = {v: (ref_small[v] if n == w.table.n_samples else oracle.unifrac_full(w.tree, table, v))
+           for v in VARIANTS}
+    iu = np.triu_indices(n, 1)
     with ub.Context(w.tree, table) as ctx:
         for layout in (ub.OUT_CONDENSED, ub.OUT_FULL):
+            want = {v: (ref[v][iu] if layout == ub.OUT_CONDENSED else ref[v].reshape(-1))
+                    for v in VARIANTS}
+            want[ub.BOTH] = np.concatenate([want[ub.UNWEIGHTED], want[ub.WEIGHTED_NORMALIZED]])
             for variant in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED, ub.BOTH):
                 direct = ctx.run(variant, precision, layout)
                 torch.cuda.synchronize()
                 direct = direct.cpu().numpy()
                 for chunk in (7, 10_000):
                     got = ctx.run_streamed(variant, precision, layout, chunk)
+                    assert got.shape == want[variant].shape
+                    err = float(np.max(np.abs(got.astype(np.float64) - want[variant])))
+                    assert err <= TOL[precision], f"max abs err {err:.3e}"
                     np.testing.assert_array_equal(got, direct)
         assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
 
