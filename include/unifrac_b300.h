@@ -386,12 +386,17 @@ int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
  * Work space: one fixed device array of UNIFRAC_NOALLOC_MAX_CELLS 32-bit
  * counts inside the library (4 MB, held by every GPU that loads the library
  * until the process exits).  n_nodes * n_samples above that, or n_samples above
- * UNIFRAC_NOALLOC_MAX_SAMPLES, returns UNIFRAC_E_UNSUPPORTED.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) with
- * that device current; make the first call on each device before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race and
- * corrupt each other's results -- serialise them (one stream, or events).
- * Nothing carries over between calls.  Allocates no device or host memory.
+ * UNIFRAC_NOALLOC_MAX_SAMPLES, returns UNIFRAC_E_UNSUPPORTED.  Every call made
+ * outside stream capture looks up that array's device address
+ * (cudaGetSymbolAddress) with the current device; a call on a capturing stream
+ * uses the address of the last earlier call on that device, and is refused
+ * with UNIFRAC_E_UNSUPPORTED when there was none: make one call on each device
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race and corrupt each other's results -- serialise them (one
+ * stream, or events).  Nothing carries over between calls.  Allocates no
+ * device or host memory.  Returns UNIFRAC_E_CUDA when a launch fails (that
+ * launch's own status; an error left pending by earlier unrelated work is not
+ * reported or cleared).
  */
 #define UNIFRAC_NOALLOC_MAX_CELLS (1u << 20)
 #define UNIFRAC_NOALLOC_MAX_SAMPLES 4096

@@ -10,9 +10,11 @@
 //
 // This entry point allocates nothing: its only work space is the file-scope
 // array `g_noalloc_scratch` below (UNIFRAC_NOALLOC_MAX_CELLS u32 counts, 4 MB),
-// which every GPU that loads this library holds until the process exits.  Its device address is looked up once per device, on the
-// first call made with that device current; make that first call before any
-// stream capture.  All calls share the array: calls that overlap on the GPU
+// which every GPU that loads this library holds until the process exits.  Its
+// device address is looked up with the device current on every call made
+// outside stream capture; a call enqueued on a capturing stream uses the
+// address found by the last earlier call on that device (and is refused if
+// there was none), so make one call on each device before any stream capture.  All calls share the array: calls that overlap on the GPU
 // (different streams, or the same stream from several host threads without
 // ordering) race and corrupt each other's results.  Nothing needs clearing
 // between calls: the first kernel overwrites every cell it later reads.
@@ -52,18 +54,28 @@ __global__ void k_noalloc_embed(int32_t n_nodes, const int32_t *__restrict__ par
   }
 }
 
-// One warp per pair (i < j): FP64 sums over the non-root branches of the
-// definition, warp-reduced; writes d into both halves of the full matrix and
-// the zero diagonal.
+// One warp per pair i <= j of the upper triangle, diagonal included: warp t
+// of the N (N + 1) / 2 takes row i, the largest with
+// off(i) = i N - i (i - 1) / 2 <= t, and j = i + t - off(i).  FP64 sums over
+// the non-root branches of the definition, warp-reduced; writes d into both
+// halves of the full matrix, 0 on the diagonal.
+__device__ __forceinline__ int64_t tri_offset(int64_t i, int64_t N) { return i * N - i * (i - 1) / 2; }
+
 __global__ void k_noalloc_pairs(int variant, int32_t n_nodes, const double *__restrict__ length,
                                 int32_t n_samples, const uint32_t *__restrict__ scratch,
                                 double *__restrict__ out) {
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t N = n_samples;
-  if (warp >= N * N) return;
-  const int i = (int)(warp / N), j = (int)(warp % N);
-  if (i > j) return;
+  if (t >= N * (N + 1) / 2) return;
+  // closed-form row (a root of i^2 - (2N + 1) i + 2t = 0), then exact
+  // integer correction of the rounding
+  const double b = 2.0 * (double)N + 1.0;
+  int64_t i = (int64_t)((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+  i = i < 0 ? 0 : (i >= N ? N - 1 : i);
+  while (i > 0 && tri_offset(i, N) > t) --i;
+  while (i + 1 < N && tri_offset(i + 1, N) <= t) ++i;
+  const int64_t j = i + (t - tri_offset(i, N));
   if (i == j) {
     if (lane == 0) out[i * N + i] = 0.0;
     return;
@@ -71,10 +83,10 @@ __global__ void k_noalloc_pairs(int variant, int32_t n_nodes, const double *__re
   const uint32_t *root = scratch + (size_t)(n_nodes - 1) * n_samples;
   const double ci = (double)root[i], cj = (double)root[j];
   double num = 0.0, den = 0.0;
-  for (int32_t b = lane; b < n_nodes - 1; b += 32) {
-    const double L = length[b];
-    const uint32_t xi = scratch[(size_t)b * n_samples + i];
-    const uint32_t xj = scratch[(size_t)b * n_samples + j];
+  for (int32_t br = lane; br < n_nodes - 1; br += 32) {
+    const double L = length[br];
+    const uint32_t xi = scratch[(size_t)br * n_samples + i];
+    const uint32_t xj = scratch[(size_t)br * n_samples + j];
     if (variant == UNIFRAC_UNWEIGHTED) {
       const bool pi = xi != 0u, pj = xj != 0u;
       num += (pi != pj) ? L : 0.0;
@@ -115,10 +127,17 @@ extern "C" int unifrac_dense_noalloc(int variant, int32_t n_nodes, const int32_t
     return UNIFRAC_E_UNSUPPORTED;  // beyond the fixed work space of this entry point
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return UNIFRAC_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // The array's device address: looked up again on every call made outside
+  // stream capture (a device reset loads the module again, possibly at
+  // another address), the cached value used while the stream is capturing.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return UNIFRAC_E_CUDA;
   uint32_t *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
+      if (cap != cudaStreamCaptureStatusNone) return UNIFRAC_E_UNSUPPORTED;  // see the header
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
         return UNIFRAC_E_CUDA;
@@ -126,11 +145,19 @@ extern "C" int unifrac_dense_noalloc(int variant, int32_t n_nodes, const int32_t
     }
     scratch = g_scratch_ptr[dev];
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  k_noalloc_embed<<<(n_samples + 127) / 128, 128, 0, st>>>(n_nodes, parent, n_samples, tip_counts,
-                                                         scratch);
-  const int64_t warps = (int64_t)n_samples * n_samples;
-  k_noalloc_pairs<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-      variant, n_nodes, length, n_samples, scratch, out);
-  return cudaGetLastError() == cudaSuccess ? UNIFRAC_OK : UNIFRAC_E_CUDA;
+  // each launch's own status (cudaLaunchKernel returns it): an error left
+  // pending by unrelated earlier work is neither reported nor cleared here,
+  // and the second kernel is not launched when the first one failed
+  {
+    void *args[] = {&n_nodes, (void *)&parent, &n_samples, (void *)&tip_counts, &scratch};
+    if (cudaLaunchKernel((const void *)k_noalloc_embed, dim3((n_samples + 127) / 128), dim3(128),
+                         args, 0, st) != cudaSuccess)
+      return UNIFRAC_E_CUDA;
+  }
+  const int64_t warps = (int64_t)n_samples * (n_samples + 1) / 2;
+  void *args[] = {&variant, &n_nodes, (void *)&length, &n_samples, &scratch, &out};
+  if (cudaLaunchKernel((const void *)k_noalloc_pairs, dim3((unsigned)((warps * 32 + 255) / 256)),
+                       dim3(256), args, 0, st) != cudaSuccess)
+    return UNIFRAC_E_CUDA;
+  return UNIFRAC_OK;
 }
