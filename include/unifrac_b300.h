@@ -250,9 +250,9 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
  * U_k sqrt(max(lambda_k, 0)).
  *
  *   dist       DEVICE pointer, the full n x n matrix (unifrac_run with
- *              UNIFRAC_OUT_FULL), float (UNIFRAC_MIXED) or double (UNIFRAC_FP64);
- *              not modified
- *   k          1 <= k <= n components
+ *              UNIFRAC_OUT_FULL), float (UNIFRAC_MIXED) or double (UNIFRAC_FP64),
+ *              symmetric, 16-byte aligned; not modified
+ *   k          1 <= k <= min(n, UNIFRAC_PCOA_MAX_K) components
  *   iters      subspace iterations (>= 0; 12 is ample for the leading
  *              components of UniFrac matrices)
  *   seed       seed of the random start (results are reproducible)
@@ -260,16 +260,20 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
  *   coords     HOST double[n * k], row-major (sample i: coords[i * k .. + k))
  *   cuda_stream  stream for the device work (NULL = legacy default stream)
  *
- * Method: subspace iteration with m = min(n, 2k + 16) columns, on the
- * device: the products with A in FP32 (cuBLAS SGEMM), the centring terms and
- * CholeskyQR2 orthonormalisation in FP64 (Gram matrices and products with
- * R^-1 by cuBLAS DGEMM); only m x m work (Cholesky factors and their
- * inverses, the Jacobi eigensolver of the Ritz matrix) runs on the host.
- * Allocates about 4 n^2 + 32 n m bytes of device memory while it
- * runs (UNIFRAC_E_OOM if that
- * fails).  Synchronous.  Errors: UNIFRAC_E_INVALID_ARG, UNIFRAC_E_OOM,
- * UNIFRAC_E_CUDA.  No context needed.
+ * Method: subspace iteration with m = min(n, 2k + 16) columns, all products
+ * on the device in the library's own kernels.  A is never stored: each
+ * product A Q streams D once (its column panels, A being symmetric) and forms
+ * -1/2 d^2 on the fly, FP32 sums within chunks of rows and FP64 across
+ * chunks; the centring terms, the CholeskyQR2 orthonormalisation (Gram
+ * matrices and products with R^-1) and the Ritz products in FP64.  Only m x m
+ * work (Cholesky factors and their inverses, the Jacobi eigensolver of the
+ * Ritz matrix) runs on the host.  Allocates O(n m) device memory while it
+ * runs (about 4 n m (c + 2) + 40 n m bytes, c <= 16 chunks; UNIFRAC_E_OOM if
+ * that fails).  Synchronous.  Errors: UNIFRAC_E_INVALID_ARG (sizes, k,
+ * precision, NULL or misaligned pointers), UNIFRAC_E_OOM, UNIFRAC_E_CUDA.
+ * No context needed.
  */
+#define UNIFRAC_PCOA_MAX_K 384
 int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t k, int32_t iters,
                  uint64_t seed, double *eigvals, double *coords, void *cuda_stream);
 
