@@ -4,9 +4,14 @@
 One step = the whole hot path over one synthetic study, one C-ABI call: the
 branch embedding (level-synchronous postorder sums), packing, and the pair
 kernels of BOTH variants (unweighted on tensor cores, weighted normalized on
-the CUDA cores), in mixed precision, writing the condensed N(N-1)/2 matrices.  The metric is
-pair-branch updates per second: each variant counts C(N,2) * B, B the branches
-kept after pruning (observed below, non-zero length).
+the CUDA cores), in mixed precision, writing both full N x N FP32 matrices
+(the default workload: 50,000 samples on a 200,000-tip tree, 2 x 10 GB).  The
+metric is pair-branch updates per second: each variant counts C(N,2) * B, B
+the branches kept after pruning (observed below, non-zero length).
+
+Under torchrun (N > 1) one study is split into contiguous stripe ranges of
+equal pair count, one per rank (no collective in the computation; the timing
+is reduced after the timed region): strong scaling of one fixed matrix.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded row sample of the same workload instead.
@@ -28,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "tips32768_samples4096"
+DEFAULT_WORKLOAD = "tips200000_samples50000"
 METRIC = "UniFrac pair-branch updates/s (both variants, mixed precision)"
 UNIT = "pair-branch updates/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -41,15 +46,26 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--cpu-rows", type=int, default=256,
-                    help="rows of the oracle's bounded sample")
+    ap.add_argument("--cpu-rows", type=int, default=2,
+                    help="rows of the oracle's bounded sample (cpu_baseline)")
+    ap.add_argument("--layout", default="full", choices=["full", "condensed"],
+                    help="output layout of the timed step")
+    ap.add_argument("--fp64-stripes", type=int, default=64,
+                    help="stripes of the plain FP64 measurement (extrapolated to the matrix)")
+    ap.add_argument("--serial-steps", type=int, default=5,
+                    help="steps of the per-kernel timing loop (variants one after the other)")
+    ap.add_argument("--tune-repeats", type=int, default=1,
+                    help="timed runs per autotuner candidate")
+    ap.add_argument("--tuned-cache", default=None,
+                    help="autotuner cache file (default: the package's tuned.json)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--streamed-chunk", type=int, default=1024,
-                    help="stripes per chunk of the streamed-output measurement")
+    ap.add_argument("--streamed-chunk", type=int, default=0,
+                    help="stripes per chunk of the streamed-output measurement (0: the "
+                         "faster of 1,024 and 4,096)")
     ap.add_argument("--mantel-perms", type=int, default=999,
                     help="permutations of the Mantel-test measurement (0 = skip it)")
     ap.add_argument("--mantel-only", action="store_true",
@@ -314,6 +330,10 @@ def baseline_study(w):
 
 
 def reference_arm(args):
+    """The FP64 oracle as it stands on the host cores: each step is one seeded
+    row of the workload's largest study against every column, the two
+    variants alternating step by step (the oracle embeds every column each
+    call, so a step is several seconds at 50,000 samples)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
@@ -323,26 +343,33 @@ def reference_arm(args):
     w = synth.Workload(w0.name, w0.tree, sub, w0.description)
     N = w.table.n_samples
     B = kept_branches(w)
+    import oracle
     rng = np.random.default_rng(7)
-    rows = np.sort(rng.choice(N, size=min(args.cpu_rows, N), replace=False))
-    for _ in range(max(0, min(args.warmup, 1))):
-        oracle_sample(w, rows[:1])
+    rows = rng.choice(N, size=max(1, args.steps + min(args.warmup, 1)), replace=True)
+    variants = (oracle.UNWEIGHTED, oracle.WEIGHTED_NORMALIZED)
+    k = 0
+    for _ in range(min(args.warmup, 1)):
+        oracle.unifrac_rows(w.tree, w.table, variants[k % 2], rows[k:k + 1])
+        k += 1
     times = []
     threads = 1
-    for _ in range(args.steps):
-        _, dt, threads = oracle_sample(w, rows)
-        times.append(dt)
-    units = 2.0 * len(rows) * (N - 1) * B
+    for step in range(args.steps):
+        t0 = time.perf_counter()
+        _, threads = oracle.unifrac_rows(w.tree, w.table, variants[step % 2], rows[k:k + 1])
+        times.append(time.perf_counter() - t0)
+        k += 1
+    units = 1.0 * (N - 1) * B  # one row, one variant per step
     value = units * len(times) / sum(times)
+    sample = (f"1 seeded row x {N} columns per step, variants alternating "
+              f"(unweighted, weighted normalized)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "samples": N, "branches": B,
-                   "sample": f"{len(rows)} seeded rows x {N} columns, both variants"},
+        "config": {"workload": args.workload, "samples": N, "branches": B, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{len(rows)} rows x {N} columns x 2 variants per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -408,6 +435,90 @@ def mantel_leg(args, w, stream, tuned_opts, peaks):
     return out
 
 
+def pipe_peaks():
+    """Measured FP32 and FP64 FMA rates of this GPU (ops/s), the ALU ceilings."""
+    from paper_2107_05397_b300 import binding as ub
+    return (ub.unifrac_measure_peak(ub.PEAK_FP32_FMA), ub.unifrac_measure_peak(ub.PEAK_FP64_FMA))
+
+
+def row_values(out, v, layout, N, rows):
+    """Rows `rows` of variant v's matrix (FP64 numpy [len(rows), N]) from the
+    device output of a BOTH run (full: contiguous rows; condensed: gathered)."""
+    import torch
+    if layout == "full":
+        M = out[v * N * N:(v + 1) * N * N].view(N, N)
+        return M.index_select(0, torch.as_tensor(rows, device=out.device)).double().cpu().numpy()
+    P = N * (N - 1) // 2
+    vec = out[v * P:(v + 1) * P]
+    res = np.zeros((len(rows), N))
+    for r, i in enumerate(rows):
+        j = np.arange(N)
+        a, b = np.minimum(i, j), np.maximum(i, j)
+        idx = a * N - a * (a + 1) // 2 + (b - a - 1)
+        g = vec[torch.as_tensor(np.where(i == j, 0, idx), device=out.device)].double().cpu().numpy()
+        res[r] = np.where(i == j, 0.0, g)
+    return res
+
+
+def fp64_leg(args, w, stream, flush, units_full, rows_check=16):
+    """The plain FP64 path (bit-packed lookup unweighted, FP64 min-sum
+    weighted) on the same GPU, over a seeded range of args.fp64_stripes
+    stripes, both variants one after the other (CUDA events), extrapolated to
+    the whole matrix by the ratio of 128 x 128 tile pairs; per-kernel
+    fractions against the measured FP64 rate; the range's values checked on
+    seeded pairs against the oracle."""
+    import torch
+    import oracle
+    from paper_2107_05397_b300 import binding as ub
+    from paper_2107_05397_b300 import replicas
+    N = w.table.n_samples
+    S = replicas.n_stripes(N)
+    width = max(1, min(args.fp64_stripes, S))
+    s0 = int(np.random.default_rng(8).integers(0, S - width + 1))
+    s1 = s0 + width
+    T = -(-N // 128)
+    res = {"stripes": [s0, s1], "extrapolated": True}
+    with ub.Context(w.tree, w.table, stream=stream) as c:
+        c.set_option(ub.OPT_OVERLAP_VARIANTS, 0)
+        out = c.run(ub.BOTH, ub.FP64, ub.OUT_STRIPES, s0, s1)  # warm-up (allocates)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.run(ub.BOTH, ub.FP64, ub.OUT_STRIPES, s0, s1, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tiles = c.stat(ub.STAT_TILE_PAIRS)
+        uw_ms = c.stat(ub.STAT_PAIR_MS_UNWEIGHTED)
+        wn_ms = c.stat(ub.STAT_PAIR_MS_WEIGHTED)
+        sel_uw = c.stat(ub.STAT_SELECTED_UNWEIGHTED)
+        sel_wn = c.stat(ub.STAT_SELECTED_WEIGHTED)
+        got = out.view(2, s1 - s0, N).cpu().numpy()
+        dev_err = c.stat(ub.STAT_DEVICE_ERROR)
+        del out
+    torch.cuda.empty_cache()
+    full_tiles = T * (T + 1) / 2
+    ms_full = ms * full_tiles / max(tiles, 1.0)
+    res.update({"ms_range": ms, "tile_pairs_range": tiles, "tile_pairs_full": full_tiles,
+                "ms_per_step": ms_full, "value": units_full / (ms_full / 1e3),
+                "device_error": dev_err,
+                "extrapolation": "range time x (tile pairs of the matrix / tile pairs of the "
+                                 "range); embedding and packing counted once per range"})
+    rng = np.random.default_rng(9)
+    ss = rng.integers(0, s1 - s0, size=rows_check)
+    kk = rng.integers(0, N, size=rows_check)
+    jj = (kk + s0 + ss + 1) % N
+    errs = {}
+    for name, v in (("unweighted", 0), ("weighted_normalized", 1)):
+        ref = oracle.unifrac_pairs(w.tree, w.table, v, kk, jj)
+        errs[name] = float(np.max(np.abs(got[v][ss, kk] - ref)))
+    res["max_abs_err_vs_oracle"] = errs
+    res["kernel_ms"] = {"k_pairs_lookup": uw_ms, "k_pairs_weighted<double>": wn_ms}
+    res["_work"] = {"lookup_group_adds": sel_uw / 8.0, "weighted_fp64_updates": sel_wn}
+    return res
+
+
 def main():
     args = parse()
     if args.record_traffic:
@@ -420,14 +531,16 @@ def main():
                  else tb.n_samples)
         return record_traffic(args.record_traffic, args.workload, tb.n_samples,
                               "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
-                              "--clock-control none -k regex:k_pairs on bench.py --workload "
-                              f"{args.workload} --sparse-fraction {args.sparse_fraction} "
-                              f"--uw-sparse-fraction {args.uw_sparse_fraction}",
+                              "--clock-control none -k regex:^<kernel> -s <skip> -c 1 on "
+                              f"bench.py --workload {args.workload} --sparse-fraction "
+                              f"{args.sparse_fraction} --uw-sparse-fraction "
+                              f"{args.uw_sparse_fraction}, one ncu call per kernel",
                               split_thresholds(args.sparse_fraction, args.uw_sparse_fraction, n_max))
     if args.impl == "reference":
         return reference_arm(args)
     import torch
     from paper_2107_05397_b300 import binding as ub
+    from paper_2107_05397_b300 import replicas
     from paper_2107_05397_b300 import synth
 
     rank, world, local_rank = env_rank()
@@ -445,9 +558,9 @@ def main():
         torch.cuda.synchronize()
 
     w = synth.make_workload(args.workload, n_samples=args.samples)
-    if w.table.study_offsets is not None and world > 1:
+    batched = w.table.study_offsets is not None
+    if batched and world > 1:
         # independent studies: each rank takes its share (no data-path collective)
-        from paper_2107_05397_b300 import replicas
         sizes = [int(x) for x in np.diff(w.table.study_offsets)]
         w = synth.Workload(w.name, w.tree,
                            select_studies(w.table, replicas.shard_studies(sizes, rank, world)),
@@ -458,26 +571,35 @@ def main():
         print(json.dumps({"workload": w.name, "samples": N,
                           "mantel": mantel_leg(args, w, stream, {}, measured_peaks())}))
         return
+    layout = ub.OUT_FULL if (args.layout == "full") else ub.OUT_CONDENSED
+    # one study on several ranks: contiguous stripe ranges of equal pair count
+    s0, s1 = (0, -1)
+    if not batched and world > 1:
+        s0, s1 = replicas.shard_stripes(N, rank, world)
     ctx = ub.Context(w.tree, w.table, stream=stream)
-    nb_cond = ctx.output_bytes(ub.MIXED, ub.OUT_CONDENSED)
-    out_both = torch.empty(2 * nb_cond // 4, dtype=torch.float32, device="cuda")
-    out_uw, out_wn = out_both[: nb_cond // 4], out_both[nb_cond // 4:]
+    nb_out = ctx.output_bytes(ub.MIXED, layout)
+    out_both = torch.empty(2 * nb_out // 4, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     pair_branch = ctx.stat(ub.STAT_PAIR_BRANCH)
-    units_per_step = 2.0 * pair_branch  # both variants
+    if s1 >= 0:  # this rank's share of the pairs
+        mine = sum(replicas.stripe_pairs(N, s) for s in range(s0, s1))
+        units_per_step = 2.0 * pair_branch * mine / max(N * (N - 1) // 2, 1)
+    else:
+        units_per_step = 2.0 * pair_branch  # both variants
 
     def step(precision=ub.MIXED, out=out_both):
         # both variants from one embedding pass, one C-ABI call
-        ctx.run(ub.BOTH, precision, ub.OUT_CONDENSED, out=out)
+        ctx.run(ub.BOTH, precision, layout, s0, s1, out=out)
         return ctx.stat(ub.STAT_KERNEL_LAUNCHES)
 
     tuned = {}
-    if not args.no_autotune:  # the library's own tuner, before the timed region
+    if not args.no_autotune:  # the library's own tuner (cached per shape), before timing
         from paper_2107_05397_b300 import autotune
+        cache = args.tuned_cache or autotune.DEFAULT_CACHE
         for v in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED):
-            rec = autotune.tune(ctx, v, ub.MIXED)
-            tuned.update({k: rec[k] for k in rec if k != "cached"})
-    n_max = int(max(np.diff(w.table.study_offsets))) if w.table.study_offsets is not None else N
+            rec = autotune.tune(ctx, v, ub.MIXED, cache_path=cache, repeats=args.tune_repeats)
+            tuned.update(rec)
+    n_max = int(max(np.diff(w.table.study_offsets))) if batched else N
     if args.sparse_fraction is not None:
         ctx.set_option(ub.OPT_SPARSE_THRESHOLD, max(1, int(round(args.sparse_fraction * n_max))))
         tuned["sparse_fraction"] = args.sparse_fraction
@@ -520,11 +642,11 @@ def main():
             launches += n
         barrier()
         t_wall = time.perf_counter() - t_wall0
-        # per-kernel times for the rooflines: the same steps with the variants
-        # one after the other, so that no kernel shares the GPU with another
+        # per-kernel times for the rooflines: steps with the variants one after
+        # the other, so that no kernel shares the GPU with another
         ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0)
         step()
-        for _ in range(args.steps):
+        for _ in range(max(1, min(args.steps, args.serial_steps))):
             ms, _n = timed_step()
             serial_ms.append(ms)
             pair_uw_ms.append(ctx.stat(ub.STAT_PAIR_MS_UNWEIGHTED))
@@ -538,68 +660,78 @@ def main():
         ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0 if args.no_overlap else 1)
     clk = clocks.summary()
     dev_err = ctx.stat(ub.STAT_DEVICE_ERROR)
-    from paper_2107_05397_b300 import replicas
     total_ms, units_all = replicas.reduce_timing(float(sum(step_ms)), units_per_step * args.steps,
                                                  dist, device="cuda")
     ms_per_step = total_ms / args.steps
     value = units_all / (total_ms / 1e3)
 
-    # live per-kernel times (CUDA events recorded by the library on its stream)
-    # and the algorithmic work of each launch
+    # live per-kernel times (CUDA events recorded by the library on its
+    # stream) and the algorithmic work of each launch, against measured pipe
+    # rates: the FP32 FMA rate for the CUDA-core kernels (one FP32 operation
+    # per lane and cycle), the cuBLAS BF16 rate for the tensor-core kernel
+    fp32_rate, fp64_rate = pipe_peaks()
+    alu_peak = fp32_rate / 1e12
+    alu_src = ("measured FP32 FMA issue rate (unifrac_measure_peak: full-occupancy FFMA chains, "
+               "CUDA events)")
+    long_step = ms_per_step >= 100.0
+    tc_peak = (peaks or {}).get("bf16_tflops_sustained" if long_step else "bf16_tflops",
+                                1401.4 if long_step else 1791.5)
+    tc_src = ("measured cuBLAS bf16 " + ("sustained (kernel timed inside a step of "
+                                         f"{ms_per_step:.0f} ms)" if long_step else "burst")
+              + " (MEASURED_PEAKS.json)")
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = sms * 128 * sm_max * 1e6 / 1e12
-    alu_src = f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock, MEASURED_PEAKS.json)"
-    tc_peak = (peaks or {}).get("bf16_tflops", 1766.4)
     mean = lambda xs: float(np.mean(xs)) if xs else 0.0
     uw_ms, wn_ms = mean(pair_uw_ms), mean(pair_wn_ms)
     kernels = []
     thresholds_now = {"sparse": ctx.get_option(ub.OPT_SPARSE_THRESHOLD),
                       "uw_sparse": ctx.get_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD)}
 
-    def entry(kernel, ms, work, bound, peak, unit, work_note, peak_note):
+    def entry(kernel, ms, work, bound, peak, unit, work_note, peak_note, **extra):
         if ms <= 0:
             return
         ach = work / (ms / 1e3) / 1e12
         kernels.append({"kernel": kernel, "ms": ms, "bound": bound, "achieved": ach,
                         "peak": peak, "unit": unit, "frac": ach / peak,
                         "traffic": recorded_traffic(kernel, w.name, N, thresholds_now),
-                        "work": work_note,
-                        "peak_source": peak_note})
+                        "work": work_note, "peak_source": peak_note, **extra})
 
     entry("k_pairs_tc", uw_ms - mean(sp_uw_ms), 6.0 * mean(sel_uw), "tensor", tc_peak, "TFLOP/s",
-          "3 BF16 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)",
-          "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)")
-    # sparse kernels: one shared-memory atomic add per co-present pair-branch;
-    # the shared-memory unit takes one 32-lane wavefront per cycle per SM
-    atom_peak = sms * 32 * sm_max * 1e6 / 1e12
-    atom_src = (f"{sms} SMs x 32 shared-memory atomic lanes x {sm_max:.0f} MHz (one 32-lane "
-                "wavefront per cycle per SM)")
-    # the unweighted form adds q_b as two 12-bit halves: two lane-ops per update
-    entry("k_pairs_sparse<true>", mean(sp_uw_ms), mean(sp_uw_n), "smem_atomic", atom_peak / 2,
-          "T updates/s", "2 shared-memory u32 adds (12-bit halves of q_b) per co-present "
-          "pair-branch", atom_src + ", halved: two atomic lane-ops per update")
+          "3 BF16 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)", tc_src)
+    # the shared-memory atomic unit (one 32-lane wavefront per cycle per SM):
+    # a secondary ceiling of the sparse kernels' implementation
+    atom = sms * 32 * sm_max * 1e6
+    entry("k_pairs_sparse<true>", mean(sp_uw_ms), mean(sp_uw_n), "alu", alu_peak, "T ops/s",
+          "1 add of len_b per co-present pair-branch (the unweighted update)", alu_src,
+          smem_atomic_frac=(2.0 * mean(sp_uw_n) / (mean(sp_uw_ms) / 1e3) / atom
+                            if mean(sp_uw_ms) > 0 else None))
     entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms), 2.0 * mean(sel_wn), "alu", alu_peak,
-          "TFLOP/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
-    entry("k_pairs_sparse<false>", mean(sp_wn_ms), mean(sp_wn_n), "smem_atomic", atom_peak,
-          "T updates/s", "1 shared-memory u32 add of min(V_i, V_j) per co-present pair-branch",
-          atom_src)
+          "T ops/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
+    entry("k_pairs_sparse<false>", mean(sp_wn_ms), 2.0 * mean(sp_wn_n), "alu", alu_peak,
+          "T ops/s", "2 ops (min, add) per co-present pair-branch (the weighted update)", alu_src,
+          smem_atomic_frac=(mean(sp_wn_n) / (mean(sp_wn_ms) / 1e3) / atom
+                            if mean(sp_wn_ms) > 0 else None))
     roofline = max(kernels, key=lambda k: k["ms"])
+    layout_name = "full" if layout == ub.OUT_FULL else "condensed"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if (world > 1 and not batched) else "weak",
+        "vs_baseline": None,
         "dtype": "f32+bf16(int digits), integer sums", "data": "synthetic",
         "config": {"workload": args.workload if args.samples is None
                    else f"{args.workload} truncated to {N} samples", "samples": N,
-                   "studies": 1 if w.table.study_offsets is None
-                   else int(len(w.table.study_offsets) - 1),
+                   "studies": 1 if not batched else int(len(w.table.study_offsets) - 1),
                    "branches_kept": ctx.stat(ub.STAT_BRANCHES_KEPT),
-                   "levels": ctx.stat(ub.STAT_LEVELS), "layout": "condensed",
-                   "parallelism": (f"studies sharded over {world} GPUs"
-                                   if w.table.study_offsets is not None and world > 1
-                                   else f"replicas x{world}"),
-                   "l2": "flushed (512 MB write) before every timed step",
+                   "levels": ctx.stat(ub.STAT_LEVELS), "layout": layout_name,
+                   "output_bytes": 2 * nb_out,
+                   "stripes": ("all stripes in one call (the device holds the whole matrix)"
+                               if s1 < 0 else f"stripes [{s0}, {s1}) of this rank"),
+                   "parallelism": (f"studies sharded over {world} GPUs" if batched and world > 1
+                                   else f"stripe ranges over {world} GPUs" if world > 1
+                                   else "1 GPU"),
+                   "l2": "flushed (512 MB write) before every timed step; inputs and outputs "
+                         "are far larger than L2",
                    "description": w.description},
         "roofline": roofline,
         "kernels": kernels,
@@ -613,32 +745,13 @@ def main():
                                  "the GPU); ms_per_step is the headline loop, variants "
                                  "overlapped on two streams" if not args.no_overlap else
                                  "variants one after the other in both loops"},
+        "measured_pipes": {"fp32_fma_tops": fp32_rate / 1e12, "fp64_fma_tops": fp64_rate / 1e12,
+                           "sm_mhz_median": clk.get("sm_mhz")},
         "tuned_options": tuned, "graph_replay": not args.no_graph,
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
         "wall_s_timed_loop": t_wall,
         "device_error": dev_err,
     }
-
-    if rank == 0 and not args.no_fp64:
-        # the plain FP64 path (lookup unweighted + FP64 weighted) on the same GPU
-        try:
-            out64 = torch.empty(nb_cond, dtype=torch.float64, device="cuda")
-            step(ub.FP64, out64)
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(ub.FP64, out64)
-            e1.record(stream)
-            e1.synchronize()
-            ms64 = e0.elapsed_time(e1)
-            line["fp64_plain"] = {"ms_per_step": ms64,
-                                  "value": units_per_step / (ms64 / 1e3),
-                                  "mixed_speedup": ms64 / ms_per_step}
-            del out64
-        except (ub.UniFracError, torch.OutOfMemoryError) as exc:
-            line["fp64_plain"] = {"skipped": str(exc)}
-            torch.cuda.empty_cache()
 
     if rank == 0 and not args.no_cpu_baseline:
         s_idx, sub, block0 = baseline_study(w)
@@ -653,42 +766,64 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"{len(rows)} seeded rows x {Ns} columns of study "
                                           f"{s_idx}, both variants ({dt:.1f} s)"}
-        # error of this run's outputs on the same rows
-        errs = {}
-        for name, v, t in (("unweighted", 0, out_uw), ("weighted_normalized", 1, out_wn)):
-            got = t.cpu().numpy().astype(np.float64)
-            e = 0.0
-            for r, i in enumerate(rows):
-                j = np.arange(Ns)
-                a_, b_ = np.minimum(i, j), np.maximum(i, j)
-                idx = block0 + a_ * Ns - a_ * (a_ + 1) // 2 + (b_ - a_ - 1)
-                vals = np.where(i == j, 0.0, got[np.where(i == j, block0, idx)])
-                e = max(e, float(np.max(np.abs(vals - ref[v][r]))))
-            errs[name] = e
-        line["max_abs_err_vs_oracle"] = errs
+        if not batched and s1 < 0:
+            # error of this run's outputs on the same rows
+            line["max_abs_err_vs_oracle"] = {
+                name: float(np.max(np.abs(row_values(out_both, v, layout_name, N, rows)
+                                          - ref[v])))
+                for name, v in (("unweighted", 0), ("weighted_normalized", 1))}
 
-    # the device memory of the timed context is released before the
-    # end-to-end and per-study runs create contexts of their own
+    # the device memory of the timed context is released before the FP64,
+    # end-to-end and downstream legs create contexts of their own
     tuned_opts = {o: ctx.get_option(o) for o in (ub.OPT_SPARSE_THRESHOLD,
                                                  ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD)}
     ctx.close()
+    del out_both
     torch.cuda.empty_cache()
 
+    if rank == 0 and not args.no_fp64 and not batched:
+        try:
+            f64 = fp64_leg(args, w, stream, flush, 2.0 * pair_branch)
+            work = f64.pop("_work")
+            km = f64["kernel_ms"]
+            f64["mixed_speedup"] = f64["ms_per_step"] / ms_per_step
+            f64_peak = fp64_rate / 1e12
+            f64_src = ("measured FP64 FMA issue rate (unifrac_measure_peak: full-occupancy DFMA "
+                       "chains, CUDA events)")
+            for kern, ms_k, ops, note in (
+                    ("k_pairs_lookup", km["k_pairs_lookup"], work["lookup_group_adds"],
+                     "1 FP64 add of a table entry per pair and selected 8-branch group"),
+                    ("k_pairs_weighted<double>", km["k_pairs_weighted<double>"],
+                     2.0 * work["weighted_fp64_updates"],
+                     "2 FP64 ops (min, add) per selected pair-branch")):
+                if ms_k > 0:
+                    ach = ops / (ms_k / 1e3) / 1e12
+                    kernels.append({"kernel": kern, "ms": ms_k, "bound": "alu", "achieved": ach,
+                                    "peak": f64_peak, "unit": "T ops/s", "frac": ach / f64_peak,
+                                    "traffic": None, "work": note, "peak_source": f64_src,
+                                    "timed": f"FP64 run over stripes {f64['stripes']}"})
+            line["fp64_plain"] = f64
+        except (ub.UniFracError, torch.OutOfMemoryError) as exc:
+            line["fp64_plain"] = {"skipped": str(exc)}
+            torch.cuda.empty_cache()
+    nb_cond = None
     # end to end through the public API with host buffers
     if rank == 0 and not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         host_in = [pin(w.tree.parent), pin(w.tree.length), pin(w.table.feature_node),
                    pin(w.table.indptr), pin(w.table.indices), pin(w.table.counts)]
         h2d = int(sum(a.nbytes for a in host_in))
-        res = torch.empty(2 * nb_cond // 4, dtype=torch.float32).pin_memory().numpy()
+        res = torch.empty(2 * nb_out // 4, dtype=torch.float32).pin_memory().numpy()
         e2e_t, parts, create_parts = [], [], []
         for rep in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = ub.unifrac_create(*host_in, n_samples=N, stream=stream,
                                   study_offsets=w.table.study_offsets)
+            for k_, v_ in tuned_opts.items():
+                ub.unifrac_set_option(h, k_, v_)
             t1 = time.perf_counter()
-            ub.unifrac_run(h, ub.BOTH, ub.MIXED, 0, -1, ub.OUT_CONDENSED, res)
+            ub.unifrac_run(h, ub.BOTH, ub.MIXED, 0, -1, layout, res)
             t2 = time.perf_counter()
             # the create breakdown (host-side values, read outside the timing)
             create_parts.append((ub.unifrac_get_stat(h, ub.STAT_CREATE_HOST_MS),
@@ -702,40 +837,49 @@ def main():
         t_e2e = float(np.median(e2e_t))
         med = np.median(np.array(parts), axis=0)
         cmed = np.median(np.array(create_parts), axis=0)
-        line["e2e"] = {"value": units_per_step / t_e2e, "unit": UNIT,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(2 * nb_cond),
+        line["e2e"] = {"value": 2.0 * pair_branch / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(2 * nb_out),
                        "s_per_step": t_e2e,
                        "s_create_run_destroy": [round(float(x), 5) for x in med],
                        "create_ms_host_device": [round(float(x), 2) for x in cmed],
-                       "includes": "create (validation, host prep, upload) + one run of both "
-                                   "variants + D2H of both condensed matrices + destroy"}
+                       "includes": f"create (validation, host prep, upload) + one run of both "
+                                   f"variants into pinned host memory ({layout_name} layout, "
+                                   f"D2H inside) + destroy"}
 
-    # streamed output: both matrices into host memory, computed in chunks of
-    # stripes (only two chunks on the device), copies and merge overlapped
-    if rank == 0 and not args.no_e2e and w.table.study_offsets is None:
-        nst = N // 2
-        chunk = max(1, min(nst, args.streamed_chunk))
-        with ub.Context(w.tree, w.table, stream=stream) as sctx:
-            for k_, v_ in tuned_opts.items():
-                sctx.set_option(k_, v_)
-            res_s = np.empty(2 * nb_cond // 4, np.float32)
-            sctx.run_streamed(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, chunk, out=res_s)  # warm-up
-            ts_ = []
-            for rep in range(3):
-                t0 = time.perf_counter()
-                sctx.run_streamed(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, chunk, out=res_s)
-                ts_.append(time.perf_counter() - t0)
-        t_s = float(np.median(ts_))
-        line["streamed"] = {"value": units_per_step / t_s, "unit": UNIT, "s_per_call": t_s,
-                            "chunk_stripes": chunk, "chunks": -(-nst // chunk),
-                            "includes": "both variants into host memory (condensed), stripes "
-                                        "computed chunk by chunk, D2H and host merge overlapped "
-                                        "with the next chunk"}
-        del res_s
+        # streamed output: both matrices into host memory, computed in chunks
+        # of stripes (only two chunks on the device), copies and merge
+        # overlapped; the chunk width is the faster of two candidates
+        if not batched:
+            nst = replicas.n_stripes(N)
+            cands = ([args.streamed_chunk] if args.streamed_chunk > 0
+                     else sorted({min(nst, 1024), min(nst, 4096)}))
+            with ub.Context(w.tree, w.table, stream=stream) as sctx:
+                for k_, v_ in tuned_opts.items():
+                    sctx.set_option(k_, v_)
+                sctx.run_streamed(ub.BOTH, ub.MIXED, layout, cands[0], out=res)  # warm-up
+                trial = {}
+                for c_ in cands:
+                    t0 = time.perf_counter()
+                    sctx.run_streamed(ub.BOTH, ub.MIXED, layout, c_, out=res)
+                    trial[c_] = time.perf_counter() - t0
+                chunk = min(trial, key=trial.get)
+                ts_ = []
+                for rep in range(2):
+                    t0 = time.perf_counter()
+                    sctx.run_streamed(ub.BOTH, ub.MIXED, layout, chunk, out=res)
+                    ts_.append(time.perf_counter() - t0)
+            t_s = float(np.median(ts_))
+            line["streamed"] = {"value": 2.0 * pair_branch / t_s, "unit": UNIT, "s_per_call": t_s,
+                                "chunk_stripes": chunk, "chunks": -(-nst // chunk),
+                                "candidates_s": {str(k_): round(v_, 4) for k_, v_ in trial.items()},
+                                "includes": f"both variants into host memory ({layout_name}), "
+                                            "stripes computed chunk by chunk, D2H and host merge "
+                                            "overlapped with the next chunk"}
+        del res
 
     # PCoA of the weighted matrix (full layout, FP32) on the device: the
     # ordination the distance matrix feeds
-    if rank == 0 and not args.no_e2e and w.table.study_offsets is None:
+    if rank == 0 and not args.no_e2e and not batched:
         k_pc, it_pc = 10, 12
         with ub.Context(w.tree, w.table, stream=stream) as pctx:
             for k_, v_ in tuned_opts.items():
@@ -754,19 +898,19 @@ def main():
         line["pcoa"] = {"s_per_call": t_p, "n": N, "k": k_pc, "iters": it_pc,
                         "eigenvalues_top3": [float(x) for x in lam_pc[:3]],
                         "device_stream_gbs": dev_bytes / t_p / 1e9,
-                        "includes": "A = -1/2 D o D on the device, subspace iteration (cuBLAS "
-                                    "SGEMM products, host FP64 centring / CholeskyQR2 / Jacobi), "
-                                    "wall time of the synchronous call"}
+                        "includes": "A = -1/2 D o D on the device, subspace iteration (products "
+                                    "with A and the orthonormalisation on the device), wall time "
+                                    "of the synchronous call"}
         del Dfull
         torch.cuda.empty_cache()
 
     # Mantel test, Pearson and Spearman, between the unweighted and weighted
     # matrices of this workload
-    if rank == 0 and not args.no_e2e and w.table.study_offsets is None and args.mantel_perms > 0:
+    if rank == 0 and not args.no_e2e and not batched and args.mantel_perms > 0:
         line["mantel"] = mantel_leg(args, w, stream, tuned_opts, peaks)
         torch.cuda.empty_cache()
 
-    if rank == 0 and w.table.study_offsets is not None and not args.no_per_study:
+    if rank == 0 and batched and not args.no_per_study:
         # the same studies with one context and one launch sequence per study,
         # one study at a time (device memory), each run timed with events
         per = 0.0
@@ -778,14 +922,14 @@ def main():
                 if not args.no_autotune:
                     from paper_2107_05397_b300 import autotune
                     for v in (ub.UNWEIGHTED, ub.WEIGHTED_NORMALIZED):
-                        autotune.tune(c, v, ub.MIXED)
-                o_ = torch.empty(2 * c.output_bytes(ub.MIXED, ub.OUT_CONDENSED) // 4, device="cuda")
-                c.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, out=o_)
+                        autotune.tune(c, v, ub.MIXED, repeats=args.tune_repeats)
+                o_ = torch.empty(2 * c.output_bytes(ub.MIXED, layout) // 4, device="cuda")
+                c.run(ub.BOTH, ub.MIXED, layout, out=o_)
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                c.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, out=o_)
+                c.run(ub.BOTH, ub.MIXED, layout, out=o_)
                 e1.record(stream)
                 e1.synchronize()
                 per += e0.elapsed_time(e1)
@@ -797,7 +941,6 @@ def main():
 
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

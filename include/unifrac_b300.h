@@ -331,6 +331,22 @@ int unifrac_mantel(const void *x, const void *y, int precision, int32_t n, const
  */
 int unifrac_check_bounded_wait(uint32_t limit_us, int32_t *status, void *cuda_stream);
 
+/*
+ * unifrac_measure_peak -- the measured issue rate of one arithmetic pipe of
+ * the current device, the ceiling against which the pair kernels' work is
+ * reported (the paper names no hardware model; the weighted kernel is bound
+ * by FP32 operations, the plain FP64 kernels by FP64 operations, Section II).
+ * A full-occupancy grid (a multiple of the SM count) runs chains of fused
+ * multiply-adds on eight independent accumulators per thread for about 20 ms;
+ * *ops_per_s receives FMA instructions per second (one FMA = one operation),
+ * best of three timed launches (CUDA events on `cuda_stream`).  Allocates a
+ * few KB of device memory while it runs.  Synchronous.  Errors:
+ * UNIFRAC_E_INVALID_ARG (unknown pipe, NULL output), UNIFRAC_E_OOM,
+ * UNIFRAC_E_CUDA.  No context needed.
+ */
+enum unifrac_peak_pipe { UNIFRAC_PEAK_FP32_FMA = 0, UNIFRAC_PEAK_FP64_FMA = 1 };
+int unifrac_measure_peak(int pipe, double *ops_per_s, void *cuda_stream);
+
 /* Statistics of the context / its last run. */
 enum unifrac_stat {
   UNIFRAC_STAT_KERNEL_LAUNCHES = 0, /* kernels launched by the last run */

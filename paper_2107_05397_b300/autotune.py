@@ -20,6 +20,9 @@ from typing import Optional
 
 from . import binding as ub
 
+# the package's cache of settings tuned on the GPUs this library is measured on
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
 
 def _bucket(x: float) -> int:
     return int(2 ** math.ceil(math.log2(max(1.0, float(x)))))
@@ -37,18 +40,6 @@ def shape_key(ctx: "ub.Context", variant: int, precision: int) -> str:
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     kept = ctx.stat(ub.STAT_BRANCHES_KEPT)
     return (f"v{variant}-p{precision}-n{_bucket(_max_study(ctx))}-b{_bucket(kept)}-sm{sms}")
-
-
-def get_option(ctx: "ub.Context", option: int) -> int:
-    lib = ub.load()
-    lib.unifrac_get_option.argtypes = [ctypes.c_void_p, ctypes.c_int,
-                                       ctypes.POINTER(ctypes.c_int64)]
-    lib.unifrac_get_option.restype = ctypes.c_int
-    v = ctypes.c_int64()
-    rc = lib.unifrac_get_option(ctx.handle, option, ctypes.byref(v))
-    if rc:
-        raise ub.UniFracError(rc, ub.unifrac_strerror(rc))
-    return int(v.value)
 
 
 def tune(ctx: "ub.Context", variant: int, precision: int,
@@ -82,9 +73,9 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
         raise ub.UniFracError(rc, ub.unifrac_strerror(rc) + ": " + ub.unifrac_last_error(ctx.handle))
     rec = {}
     if variant == ub.WEIGHTED_NORMALIZED and precision == ub.MIXED:
-        rec["sparse_fraction"] = get_option(ctx, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)
+        rec["sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)
     if variant == ub.UNWEIGHTED and precision == ub.MIXED:
-        rec["uw_sparse_fraction"] = get_option(ctx, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD) / max(n, 1)
+        rec["uw_sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD) / max(n, 1)
     if cache_path:
         cache[key] = rec
         tmp = cache_path + ".tmp"

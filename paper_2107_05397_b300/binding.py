@@ -63,7 +63,10 @@ EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerro
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",
             "unifrac_set_option", "unifrac_get_option", "unifrac_get_stat",
             "unifrac_autotune", "unifrac_run_streamed", "unifrac_pcoa", "unifrac_mantel",
-            "unifrac_check_bounded_wait")
+            "unifrac_check_bounded_wait", "unifrac_measure_peak")
+
+PEAK_FP32_FMA = 0
+PEAK_FP64_FMA = 1
 
 
 class UniFracError(RuntimeError):
@@ -105,6 +108,8 @@ def load() -> ctypes.CDLL:
         lib.unifrac_mantel.restype = ctypes.c_int
         lib.unifrac_check_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.POINTER(i32), vp]
         lib.unifrac_check_bounded_wait.restype = ctypes.c_int
+        lib.unifrac_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+        lib.unifrac_measure_peak.restype = ctypes.c_int
         lib.unifrac_destroy.argtypes = [vp]
         lib.unifrac_destroy.restype = None
         lib.unifrac_strerror.argtypes = [ctypes.c_int]
@@ -295,6 +300,14 @@ def unifrac_check_bounded_wait(limit_us: int, stream=None) -> int:
     _check(load().unifrac_check_bounded_wait(int(limit_us), ctypes.byref(status),
                                              _stream_handle(stream)))
     return int(status.value)
+
+
+def unifrac_measure_peak(pipe: int, stream=None) -> float:
+    """Measured FMA instructions per second of one pipe (PEAK_FP32_FMA or
+    PEAK_FP64_FMA) of the current device."""
+    v = ctypes.c_double()
+    _check(load().unifrac_measure_peak(int(pipe), ctypes.byref(v), _stream_handle(stream)))
+    return float(v.value)
 
 
 def unifrac_destroy(ctx) -> None:

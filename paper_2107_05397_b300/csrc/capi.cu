@@ -1599,6 +1599,25 @@ int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layou
   }
 }
 
+// Frees the packing and pair-kernel work buffers of one variant slot (they
+// are allocated again, at the size the next run needs, on first use).
+static void release_variant_buffers(unifrac_ctx *ctx, int slot) {
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
+  VarBufs &V = ctx->vb[slot];
+  DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
+                     &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits};
+  for (DevBuf *b : vbufs)
+    if (b->p) {
+      cudaFree(b->p);
+      ctx->device_bytes -= b->bytes;
+      b->p = nullptr;
+      b->bytes = 0;
+    }
+  ctx->buf_generation++;  // a captured graph holds the old addresses
+  ctx->reuse_prepared = false;
+}
+
 int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, size_t out_bytes,
                      int repeats) {
   if (!ctx || !out || repeats < 1) return UNIFRAC_E_INVALID_ARG;
@@ -1633,6 +1652,13 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
     double t = 1e300;
     for (int r = 0; r <= repeats; ++r) {
       rc = unifrac_run(ctx, variant, precision, 0, -1, UNIFRAC_OUT_CONDENSED, out, out_bytes);
+      if (rc == UNIFRAC_E_OOM) {
+        // this candidate's buffers do not fit beside the rest: skip it and
+        // give back what it allocated
+        cudaGetLastError();
+        release_variant_buffers(ctx, variant);
+        return UNIFRAC_OK;
+      }
       if (rc) return rc;
       cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
@@ -1656,7 +1682,11 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
       rc = trial(coarse * 3 / 2);
   }
   ctx->opt_use_graph = saved_graph;
+  // the candidates' buffers were sized for the largest of them: release them,
+  // the next run allocates what the chosen setting needs
+  release_variant_buffers(ctx, variant);
   if (rc) return rc;
+  if (best >= 1e300) return fail(ctx, UNIFRAC_E_OOM, "autotune: no candidate fits in device memory");
   return unifrac_set_option(ctx, option, best_v);
 }
 

@@ -20,7 +20,9 @@ Conventions shared with the C ABI:
 from __future__ import annotations
 
 import dataclasses
+import hashlib
 import math
+import os
 from typing import Optional
 
 import numpy as np
@@ -214,7 +216,12 @@ def _draw_features(rng: np.random.Generator, cdf: Optional[np.ndarray],
     seen = np.empty(0, dtype=np.int64)
     while True:
         m = 2 * k + 64
-        draw = np.searchsorted(cdf, rng.random(m) * cdf[-1], side="right")
+        u = rng.random(m) * cdf[-1]
+        # inverse CDF; the needles are searched in sorted order (same result,
+        # fewer cache misses on a large cdf)
+        order = np.argsort(u)
+        draw = np.empty(m, dtype=np.int64)
+        draw[order] = np.searchsorted(cdf, u[order], side="right")
         draw = np.minimum(draw, n_features - 1)
         cat = np.concatenate([seen, draw])
         _, first = np.unique(cat, return_index=True)
@@ -329,8 +336,68 @@ BATCHED = {
 }
 
 
+def _cache_path(name: str, n_samples: Optional[int]) -> Optional[str]:
+    """File of a named workload in the cache directory (environment variable
+    UNIFRAC_SYNTH_CACHE, default a folder under the system temp directory;
+    "off" disables it), keyed by this module's source so that any change to a
+    generator starts a new entry."""
+    d = os.environ.get("UNIFRAC_SYNTH_CACHE")
+    if d == "off":
+        return None
+    if not d:
+        import tempfile
+        d = os.path.join(tempfile.gettempdir(), "unifrac_synth_cache")
+    with open(os.path.abspath(__file__), "rb") as f:
+        key = hashlib.sha256(f.read()).hexdigest()[:16]
+    return os.path.join(d, f"{name}-{n_samples}-{key}.npz")
+
+
+def _save(path: str, w: Workload) -> None:
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp.npz"
+        t = w.table
+        np.savez(tmp, parent=w.tree.parent, length=w.tree.length, indptr=t.indptr,
+                 indices=t.indices, counts=t.counts, feature_node=t.feature_node,
+                 study_offsets=(np.empty(0, np.int32) if t.study_offsets is None
+                                else t.study_offsets),
+                 meta=np.array([t.n_features, t.n_samples], np.int64),
+                 description=np.array(w.description))
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _load(path: str, name: str) -> Optional[Workload]:
+    try:
+        z = np.load(path)
+        so = z["study_offsets"]
+        table = Table(n_features=int(z["meta"][0]), n_samples=int(z["meta"][1]),
+                      indptr=z["indptr"], indices=z["indices"], counts=z["counts"],
+                      feature_node=z["feature_node"],
+                      study_offsets=None if so.shape[0] == 0 else so)
+        return Workload(name=name, tree=Tree(parent=z["parent"], length=z["length"]),
+                        table=table, description=str(z["description"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
-    """Build a named seeded workload; n_samples optionally truncates N."""
+    """Build a named seeded workload; n_samples optionally truncates N.  The
+    large ones take a minute or more to draw, so they are kept in a cache
+    folder (see _cache_path) and read back by later processes."""
+    path = _cache_path(name, n_samples)
+    if path and os.path.exists(path):
+        w = _load(path, name)
+        if w is not None:
+            return w
+    w = _make_workload(name, n_samples)
+    if path and w.table.nnz >= 1_000_000:
+        _save(path, w)
+    return w
+
+
+def _make_workload(name: str, n_samples: Optional[int] = None) -> Workload:
     if name in BATCHED:
         return make_batched(name)
     p = WORKLOADS[name]

@@ -69,13 +69,18 @@ def test_kernel_hash_ignores_the_host_context_struct(tmp_path, monkeypatch):
     assert h0 != bench.kernel_source_hash("k_pairs_tc")
 
 
+def bench_workloads():
+    from paper_2107_05397_b300 import synth
+    return set(synth.WORKLOADS) | set(synth.BATCHED)
+
+
 @pytest.mark.parametrize("kernel", sorted(bench.KERNEL_SOURCES))
 def test_committed_traffic_has_every_pair_kernel(kernel):
-    """profiles/traffic.json holds, for every pair kernel, records of the bench
-    workload with bytes per launch and a source hash (null in the bench line
-    once the sources move on)."""
+    """profiles/traffic.json holds, for every pair kernel, records with bytes
+    per launch and a source hash (null in the bench line once the sources
+    move on, or for another workload, sample count or split)."""
     records = json.load(open(bench.TRAFFIC_PATH))["records"]
-    mine = [r for r in records if kernel in r and r.get("workload") == bench.DEFAULT_WORKLOAD]
+    mine = [r for r in records if kernel in r and r.get("workload") in bench_workloads()]
     assert mine
     for r in mine:
         assert r[kernel]["bytes_per_launch"] > 0 and len(r[kernel]["source_hash"]) == 16
