@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-persistent", action="store_true",
+                    help="pair kernels with one CTA per work item instead of the persistent "
+                         "work queue")
     ap.add_argument("--streamed-chunk", type=int, default=0,
                     help="stripes per chunk of the streamed-output measurement (0: the "
                          "faster of 1,024 and 4,096)")
@@ -609,6 +612,7 @@ def main():
         tuned["uw_sparse_fraction"] = f
     if not args.no_graph:
         ctx.set_option(ub.OPT_USE_GRAPH, 1)
+    ctx.set_option(ub.OPT_PERSISTENT, 0 if args.no_persistent else 1)
     for _ in range(args.warmup):
         step()
     barrier()
@@ -748,6 +752,7 @@ def main():
         "measured_pipes": {"fp32_fma_tops": fp32_rate / 1e12, "fp64_fma_tops": fp64_rate / 1e12,
                            "sm_mhz_median": clk.get("sm_mhz")},
         "tuned_options": tuned, "graph_replay": not args.no_graph,
+        "persistent_work_queue": not args.no_persistent,
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
         "wall_s_timed_loop": t_wall,
         "device_error": dev_err,
@@ -776,7 +781,10 @@ def main():
     # the device memory of the timed context is released before the FP64,
     # end-to-end and downstream legs create contexts of their own
     tuned_opts = {o: ctx.get_option(o) for o in (ub.OPT_SPARSE_THRESHOLD,
-                                                 ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD)}
+                                                 ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD,
+                                                 ub.OPT_SPARSE_LANE_PAIRS,
+                                                 ub.OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
+                                                 ub.OPT_WEIGHTED_FLUSH)}
     ctx.close()
     del out_both
     torch.cuda.empty_cache()

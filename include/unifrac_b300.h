@@ -219,9 +219,19 @@ enum unifrac_option {
                                               -1 auto (largest study / 16 above 8,192
                                               samples in total, else all tensor core),
                                               0 all tensor */
-  UNIFRAC_OPT_OVERLAP_VARIANTS = 7  /* UNIFRAC_BOTH: 1 (default) runs the two variants'
+  UNIFRAC_OPT_OVERLAP_VARIANTS = 7, /* UNIFRAC_BOTH: 1 (default) runs the two variants'
                                        packing and pair kernels on two streams after the
                                        shared embedding; 0 one after the other */
+  UNIFRAC_OPT_SPARSE_LANE_PAIRS = 8, /* weighted sparse pair kernel: a branch whose rows in
+                                        the two tiles give at most this many pairs is walked
+                                        by one lane, a larger one by a whole warp; 0 .. 4096,
+                                        default 32 */
+  UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS = 9, /* the same for the unweighted sparse kernel */
+  UNIFRAC_OPT_PERSISTENT = 10 /* 1 (default): each mixed-precision pair kernel runs as one
+                                 persistent launch, as many CTAs as fit on the GPU at once,
+                                 each pulling (study, tile pair) work items from a device
+                                 counter in the order of the work list (largest studies
+                                 first); 0: one CTA per work item */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
@@ -229,15 +239,21 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
 /*
  * unifrac_autotune -- pick the kernel settings of one (variant, precision)
  * for this context by timing candidates on the device, and keep the fastest
- * as the context's options.  Candidates: the dense / sparse split of the
- * weighted mixed kernel (UNIFRAC_OPT_SPARSE_THRESHOLD at 1/16 .. 3/4 of the
- * largest study) and of the unweighted tensor-core kernel
- * (UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD: all tensor core, 1/32 .. 1/4),
- * then 3/4 and 3/2 of the best of those.  Each candidate runs `repeats` times (>= 1, after one warm-up run) into
- * `out`, a DEVICE buffer of at least unifrac_output_bytes(ctx, precision,
- * UNIFRAC_OUT_CONDENSED, 0, -1) bytes whose contents are overwritten; the
- * time compared is embedding + packing + pair kernels (CUDA events).
- * Synchronises the context's stream.  FP64 has nothing to tune (returns 0).
+ * as the context's options.  One option at a time, the others held at their
+ * current values: the dense / sparse split (UNIFRAC_OPT_SPARSE_THRESHOLD at
+ * 1/16 .. 3/4 of the largest study, weighted; UNIFRAC_OPT_UNWEIGHTED_SPARSE_
+ * THRESHOLD all tensor core or 1/32 .. 1/4, unweighted; then 3/4 and 3/2 of
+ * the best), the single-lane incidence bound of the sparse kernels
+ * (UNIFRAC_OPT_SPARSE_LANE_PAIRS / UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS
+ * 16, 32, 64, when the split has a sparse part) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
+ * 128, 256, 512).  Each candidate runs `repeats` times (>= 1, after one
+ * warm-up run) into `out`, a DEVICE buffer of at least
+ * unifrac_output_bytes(ctx, precision, UNIFRAC_OUT_CONDENSED, 0, -1) bytes
+ * whose contents are overwritten; the time compared is embedding + packing +
+ * pair kernels (CUDA events).  A candidate whose work buffers do not fit in
+ * device memory is skipped; the variant's work buffers are released at the
+ * end (the next run allocates what the chosen settings need).  Synchronises
+ * the context's stream.  FP64 has nothing to tune (returns 0).
  */
 int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out,
                      size_t out_bytes, int repeats);

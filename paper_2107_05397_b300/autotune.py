@@ -7,8 +7,10 @@ JSON file, so later contexts of similar shape start tuned without re-timing:
     key = variant, precision, largest-study bucket (power of 2), kept-branch
           bucket (power of 2), SM count
 
-The weighted split is stored as a fraction of the largest study so that it
-carries over between sizes in the same bucket.
+The dense / sparse splits are stored as fractions of the largest study so
+that they carry over between sizes in the same bucket; the sparse kernels'
+single-lane incidence bound and the weighted register flush length are
+stored as they are.
 """
 from __future__ import annotations
 
@@ -22,6 +24,12 @@ from . import binding as ub
 
 # the package's cache of settings tuned on the GPUs this library is measured on
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+# options cached by value (name in the cache -> option id)
+_PLAIN_OPTIONS = {"lane_pairs": ub.OPT_SPARSE_LANE_PAIRS,
+                  "uw_lane_pairs": ub.OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
+                  "flush": ub.OPT_WEIGHTED_FLUSH}
 
 
 def _bucket(x: float) -> int:
@@ -60,6 +68,9 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
             f = rec["uw_sparse_fraction"]
             ctx.set_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD,
                            0 if f == 0 else max(2, int(round(f * n))))
+        for name, opt in _PLAIN_OPTIONS.items():
+            if name in rec:
+                ctx.set_option(opt, int(rec[name]))
         return dict(rec, cached=True)
     nbytes = ctx.output_bytes(precision, ub.OUT_CONDENSED)
     out = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device="cuda")
@@ -76,6 +87,10 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
         rec["sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)
     if variant == ub.UNWEIGHTED and precision == ub.MIXED:
         rec["uw_sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD) / max(n, 1)
+    if precision == ub.MIXED:
+        mine = (("lane_pairs", "flush") if variant == ub.WEIGHTED_NORMALIZED else ("uw_lane_pairs",))
+        for name in mine:
+            rec[name] = ub.unifrac_get_option(ctx.handle, _PLAIN_OPTIONS[name])
     if cache_path:
         cache[key] = rec
         tmp = cache_path + ".tmp"

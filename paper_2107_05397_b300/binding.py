@@ -35,6 +35,9 @@ OPT_USE_GRAPH = 4
 OPT_SPARSE_THRESHOLD = 5
 OPT_UNWEIGHTED_SPARSE_THRESHOLD = 6
 OPT_OVERLAP_VARIANTS = 7
+OPT_SPARSE_LANE_PAIRS = 8
+OPT_UNWEIGHTED_SPARSE_LANE_PAIRS = 9
+OPT_PERSISTENT = 10
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1

@@ -975,6 +975,9 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
   VarBufs &V = ctx->vb[P.variant];
   cudaError_t e =
       cudaMemsetAsync(cur_counters(ctx), 0, 4 * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(ctx->d_counter + 4 * ctx->cur_slot, 0, 4 * sizeof(unsigned long long),
+                        ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reset counters");
   OutSpec o;
   o.out = P.dst;
@@ -1012,7 +1015,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     ctx->sel_unit = 1.0;
     if ((rc = pairs_weighted(ctx, P.f64, V.vals.p, bits, P.kf_words,
                              static_cast<const uint8_t *>(V.blocks.p),
-                             static_cast<const unsigned long long *>(V.boff.p), P.n_win,
+                             static_cast<const unsigned long long *>(V.boff.p),
+                             static_cast<const uint2 *>(V.cpre.p), P.n_win,
                              P.n_win > 0 ? static_cast<uint32_t *>(V.spart.p) : nullptr,
                              P.sp_parts, S, d_items, n_items, o)))
       return rc;
@@ -1048,7 +1052,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
         (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(V.rbits.p), P.kf_words,
                                     static_cast<const uint8_t *>(V.blocks.p),
                                     static_cast<const unsigned long long *>(V.boff.p),
-                                    P.n_win, spart, d_items, n_items)))
+                                    static_cast<const uint2 *>(V.cpre.p), P.n_win, spart, d_items,
+                                    n_items)))
       return rc;
     record_event(ctx, ctx->ev_sp[0][1]);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, aq, spart, d_items, n_items, o))) return rc;
@@ -1391,6 +1396,15 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < -1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_sparse_threshold = value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_PERSISTENT:
+      if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_persistent = (int)value;
+      return UNIFRAC_OK;
+    case UNIFRAC_OPT_SPARSE_LANE_PAIRS:
+    case UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS:
+      if (value < 0 || value > 4096) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_lane_pairs[option == UNIFRAC_OPT_SPARSE_LANE_PAIRS ? 1 : 0] = (int)value;
+      return UNIFRAC_OK;
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
       if (value < -1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_uw_sparse_threshold = value;
@@ -1408,6 +1422,9 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
     case UNIFRAC_OPT_USE_GRAPH: *value = ctx->opt_use_graph; return UNIFRAC_OK;
     case UNIFRAC_OPT_OVERLAP_VARIANTS: *value = ctx->opt_overlap; return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
+    case UNIFRAC_OPT_SPARSE_LANE_PAIRS: *value = ctx->opt_lane_pairs[1]; return UNIFRAC_OK;
+    case UNIFRAC_OPT_PERSISTENT: *value = ctx->opt_persistent; return UNIFRAC_OK;
+    case UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS: *value = ctx->opt_lane_pairs[0]; return UNIFRAC_OK;
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
       *value = ctx->opt_uw_sparse_threshold;
       return UNIFRAC_OK;
@@ -1626,37 +1643,23 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
   if (precision != UNIFRAC_FP64 && precision != UNIFRAC_MIXED) return UNIFRAC_E_INVALID_ARG;
   if (precision == UNIFRAC_FP64) return UNIFRAC_OK;
   DeviceGuard g(ctx->device);
-  std::vector<std::pair<int, int64_t>> cands;  // (option, value)
-  int option;
-  if (variant == UNIFRAC_WEIGHTED_NORMALIZED) {
-    option = UNIFRAC_OPT_SPARSE_THRESHOLD;
-    const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
-    for (int64_t num : {1, 2, 4, 8, 12}) cands.push_back({option, std::max<int64_t>(2, n * num / 16)});
-  } else {
-    option = UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD;
-    const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
-    cands.push_back({option, 0});  // everything on the tensor cores
-    for (int64_t num : {1, 2, 4, 8}) cands.push_back({option, std::max<int64_t>(2, n * num / 32)});
-  }
+  const bool weighted = variant == UNIFRAC_WEIGHTED_NORMALIZED;
+  const int split_opt = weighted ? UNIFRAC_OPT_SPARSE_THRESHOLD : UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD;
+  const int64_t n = std::max<int32_t>(ctx->max_study_n, 1);
   const int saved_graph = ctx->opt_use_graph;
   ctx->opt_use_graph = 0;
-  double best = 1e300;
-  int64_t best_v = cands[0].second;
-  std::vector<int64_t> tried;
-  // time one threshold (best of `repeats` runs after a warm-up run)
-  auto trial = [&](int64_t v) -> int {
-    if (std::find(tried.begin(), tried.end(), v) != tried.end()) return UNIFRAC_OK;
-    tried.push_back(v);
+  // time one setting of one option (best of `repeats` runs after a warm-up
+  // run); a setting whose buffers do not fit in device memory is skipped
+  auto timed = [&](int option, int64_t v, double *t) -> int {
+    *t = 1e300;
     int rc = unifrac_set_option(ctx, option, v);
     if (rc) return rc;
-    double t = 1e300;
     for (int r = 0; r <= repeats; ++r) {
       rc = unifrac_run(ctx, variant, precision, 0, -1, UNIFRAC_OUT_CONDENSED, out, out_bytes);
       if (rc == UNIFRAC_E_OOM) {
-        // this candidate's buffers do not fit beside the rest: skip it and
-        // give back what it allocated
         cudaGetLastError();
         release_variant_buffers(ctx, variant);
+        *t = 1e300;
         return UNIFRAC_OK;
       }
       if (rc) return rc;
@@ -1664,30 +1667,58 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
       if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2]);
-      if (r > 0) t = std::min(t, (double)ms);  // first run is the warm-up
-    }
-    if (t < best) {
-      best = t;
-      best_v = v;
+      if (r > 0) *t = std::min(*t, (double)ms);  // first run is the warm-up
     }
     return UNIFRAC_OK;
   };
-  int rc = UNIFRAC_OK;
-  for (auto &c : cands)
-    if ((rc = trial(c.second))) break;
-  // then the thresholds 3/4 and 3/2 of the best coarse one
-  if (!rc && best_v > 0) {
-    const int64_t coarse = best_v;
-    if ((rc = trial(std::max<int64_t>(2, coarse * 3 / 4))) == UNIFRAC_OK)
-      rc = trial(coarse * 3 / 2);
+  // one option at a time, the others held at their current (tuned) values
+  auto tune = [&](int option, std::vector<int64_t> vals, bool refine) -> int {
+    double best = 1e300;
+    int64_t best_v = vals[0];
+    std::vector<int64_t> tried;
+    auto one = [&](int64_t v) -> int {
+      if (std::find(tried.begin(), tried.end(), v) != tried.end()) return UNIFRAC_OK;
+      tried.push_back(v);
+      double t;
+      int rc = timed(option, v, &t);
+      if (!rc && t < best) {
+        best = t;
+        best_v = v;
+      }
+      return rc;
+    };
+    int rc = UNIFRAC_OK;
+    for (int64_t v : vals)
+      if ((rc = one(v))) return rc;
+    if (refine && best_v > 0) {  // then 3/4 and 3/2 of the best coarse value
+      const int64_t coarse = best_v;
+      if ((rc = one(std::max<int64_t>(2, coarse * 3 / 4)))) return rc;
+      if ((rc = one(coarse * 3 / 2))) return rc;
+    }
+    if (best >= 1e300) return fail(ctx, UNIFRAC_E_OOM, "autotune: no candidate fits in device memory");
+    return unifrac_set_option(ctx, option, best_v);
+  };
+  std::vector<int64_t> split;
+  if (weighted) {
+    for (int64_t num : {1, 2, 4, 8, 12}) split.push_back(std::max<int64_t>(2, n * num / 16));
+  } else {
+    split.push_back(0);  // everything on the tensor cores
+    for (int64_t num : {1, 2, 4, 8}) split.push_back(std::max<int64_t>(2, n * num / 32));
   }
+  int rc = tune(split_opt, split, true);
+  int64_t th = 0;
+  if (!rc) rc = unifrac_get_option(ctx, split_opt, &th);
+  // incidences a lane walks alone (when the chosen split has a sparse part)
+  if (!rc && th != 0)
+    rc = tune(weighted ? UNIFRAC_OPT_SPARSE_LANE_PAIRS : UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
+              {16, 32, 64}, false);
+  // branches summed in registers before each FP32 running-total update
+  if (!rc && weighted) rc = tune(UNIFRAC_OPT_WEIGHTED_FLUSH, {128, 256, 512}, false);
   ctx->opt_use_graph = saved_graph;
   // the candidates' buffers were sized for the largest of them: release them,
-  // the next run allocates what the chosen setting needs
+  // the next run allocates what the chosen settings need
   release_variant_buffers(ctx, variant);
-  if (rc) return rc;
-  if (best >= 1e300) return fail(ctx, UNIFRAC_E_OOM, "autotune: no candidate fits in device memory");
-  return unifrac_set_option(ctx, option, best_v);
+  return rc;
 }
 
 int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {

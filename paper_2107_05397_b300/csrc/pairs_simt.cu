@@ -173,7 +173,8 @@ struct MinAcc<double> {
 // added in the epilogue.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
-    k_pairs_weighted(const WorkItem *__restrict__ items, const T *__restrict__ vals,
+    k_pairs_weighted(const WorkItem *__restrict__ items, int32_t n_items,
+                     unsigned int *__restrict__ queue, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
                      int32_t kf_words, const uint32_t *__restrict__ spart, int32_t sp_parts,
                      double sp_inv, const double *__restrict__ S,
@@ -185,11 +186,21 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
   float *tot = reinterpret_cast<float *>(smem_raw + sizeof(T) * 2 * BK * 2 * TILE +
                                          sizeof(int32_t) * kWinWords * WORD);
   __shared__ int32_t list_n;
+  __shared__ int32_t s_item;
   const bool sparse = (sizeof(T) == 4) && spart != nullptr;
-
-  const WorkItem it = items[blockIdx.x];
-  const StudyDev sd = o.studies[it.study];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  unsigned long long nsel = 0;
+
+  // work items: the next tile pair from the device queue (persistent grid),
+  // or this CTA's own (one CTA per item)
+  for (int iter = 0;; ++iter) {
+  if (tid == 0)
+    s_item = queue ? (int32_t)atomicAdd(queue, 1u) : (iter == 0 ? (int32_t)blockIdx.x : n_items);
+  __syncthreads();
+  const int32_t item = s_item;
+  if (item >= n_items) break;
+  const WorkItem it = items[item];
+  const StudyDev sd = o.studies[it.study];
   const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
   const uint32_t *bJ = bits + (int64_t)it.tile_j * n_words;
   const int64_t colI = (int64_t)it.tile_i * TILE, colJ = (int64_t)it.tile_j * TILE;
@@ -212,7 +223,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
   // warps start their flush counters staggered, so the flushes of one warp
   // overlap the min / add work of the others
   int since_flush = (sizeof(T) == 4) ? (tid >> 5) * (flush / (kThreads / 32)) : 0;
-  unsigned long long nsel = 0;
 
   auto load_stage = [&](int s, int buf, int n) {
     for (int c = tid; c < BK * 2 * CPR; c += kThreads) {
@@ -288,8 +298,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
   }
   flush_part();
 
-  if (tid == 0 && counter) atomicAdd(counter, nsel);
-
   // epilogue: d = (S_i + S_j - 2 M) / (S_i + S_j); FP32 in the FP32 form
   // (each term is within a few roundings of its exact value and the
   // difference is taken once, so the error stays a few units of 2^-24 of
@@ -315,11 +323,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
           float M = tot[i * TILE + j];
           if (sparse) {
             // the parts' integer sums add exactly (their total is below 2^31)
-            const uint32_t *sp = spart + (int64_t)blockIdx.x * TILE * TILE + i * TILE + j;
+            const uint32_t *sp = spart + (int64_t)item * TILE * TILE + i * TILE + j;
             uint32_t q = 0;
 #pragma unroll
             for (int p = 0; p < kMaxSparseParts; ++p)  // loads issued together
-              if (p < sp_parts) q += sp[(int64_t)p * gridDim.x * TILE * TILE];
+              if (p < sp_parts) q += sp[(int64_t)p * n_items * TILE * TILE];
             M = __fmaf_rn((float)q, sp_inv_f, M);
           }
           put_pair(o, sd, li, lj, ratio01_f32(__fmaf_rn(-2.f, M, den), den));
@@ -332,6 +340,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
       }
     }
   }
+  __syncthreads();  // shared memory and s_item free for the next item
+  }  // work items
+  if (tid == 0 && counter) atomicAdd(counter, nsel);
 }
 
 // ----------------------------------------------------------------------------
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
 // word, the rank of its first flagged row in the window's block is the
 // popcount of the block's earlier words; lane l takes the branch of bit l when
 // it is flagged in both tiles.  A weighted entry is one 8-byte (value, row)
-// word.  An incidence of at most kSmall pairs is walked by its lane alone,
+// word.  An incidence of at most lane_pairs pairs (an option) is walked by its lane alone,
 // reading the blocks (read-only loads through L1).  A larger one is walked by
 // the whole warp: one tile's rows (the "lane side") are held in registers,
 // lane (g, b) = (lane / nL, lane % nL) holding row b, and the other tile's
@@ -369,7 +380,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
 constexpr int kSpThreads = 1024;
 static_assert(kRareWin == kWinWords * WORD, "sparse blocks: one window is kWinWords bitmap words");
 constexpr int kSpWarps = kSpThreads / 32;
-constexpr int kSmall = 16;         // pairs a single lane walks alone
 constexpr int kAccLd = TILE + 1;   // padded accumulator row
 
 // PRES = false: weighted form, entries carry V; 32-bit accumulators (spart u32).
@@ -391,11 +401,13 @@ struct SparseCfg {
 
 template <bool PRES>
 __global__ void __launch_bounds__(kSpThreads, 1)
-    k_pairs_sparse(const WorkItem *__restrict__ items, const uint32_t *__restrict__ bits,
+    k_pairs_sparse(const WorkItem *__restrict__ items, int32_t n_items,
+                   unsigned int *__restrict__ queue, const uint32_t *__restrict__ bits,
                    int32_t n_words, int32_t kf_words, int32_t k_words, int32_t n_win,
                    const uint8_t *__restrict__ blocks, const unsigned long long *__restrict__ boff,
                    unsigned long long blocks_cap, int32_t n_tiles,
-                   const uint32_t *__restrict__ qlen, int32_t n_parts,
+                   const uint2 *__restrict__ cpre,
+                   const uint32_t *__restrict__ qlen, int32_t n_parts, int32_t lane_pairs,
                    typename SparseCfg<PRES>::Acc *__restrict__ spart,
                    unsigned long long *__restrict__ n_updates) {
   using Acc = typename SparseCfg<PRES>::Acc;
@@ -409,13 +421,12 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   __shared__ uint8_t gtab[32];
   __shared__ uint8_t fillv[TILE];
 
-  const WorkItem it = items[blockIdx.x];
+  __shared__ int32_t s_unit;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *scr = smem_raw + SparseCfg<PRES>::kAccBytes + warp * SparseCfg<PRES>::kScratch;
   unsigned long long *eS = reinterpret_cast<unsigned long long *>(scr);  // weighted
   uint8_t *rS = scr;                                                     // unweighted
   unsigned long long my_updates = 0;
-  for (int x = tid; x < TILE * kAccLd * (PRES ? 2 : 1); x += kSpThreads) sacc[x] = 0u;
   {
     const int n = tid / 32 + 1, p = tid % 32;  // kSpThreads == 32 * 32
     divtab[n - 1][p] = (uint16_t)(((p / n) << 8) | (p % n));
@@ -425,8 +436,19 @@ __global__ void __launch_bounds__(kSpThreads, 1)
       fillv[tid] = (uint8_t)(m <= 32 ? (32 / m) * m : m / ((m + 31) / 32));
     }
   }
+  // work units (tile pair, part), unit u = part * n_items + item: the next
+  // from the device queue (persistent grid), or this CTA's own
+  const int32_t n_units = n_items * n_parts;
+  for (int iter = 0;; ++iter) {
+  if (tid == 0)
+    s_unit = queue ? (int32_t)atomicAdd(queue, 1u)
+                   : (iter == 0 ? (int32_t)(blockIdx.y * n_items + blockIdx.x) : n_units);
+  for (int x = tid; x < TILE * kAccLd * (PRES ? 2 : 1); x += kSpThreads) sacc[x] = 0u;
   __syncthreads();
-
+  const int32_t unit = s_unit;
+  if (unit >= n_units) break;
+  const int32_t item = unit % n_items, part = unit / n_items;
+  const WorkItem it = items[item];
   const int64_t tI = it.tile_i, tJ = it.tile_j;
   const uint32_t *bI = bits + tI * n_words;
   const uint32_t *bJ = bits + tJ * n_words;
@@ -434,33 +456,47 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   // blocks that did not fit their buffer were not written (the fill reported
   // it): read none of them
   const int w_end = boff[(int64_t)n_tiles * n_win] > blocks_cap ? kf_words : k_words;
-  for (int w = kf_words + (int)blockIdx.y * kSpWarps + warp; w < w_end; w += kSpWarps * n_parts) {
-    const uint32_t mI = __ldg(bI + w), mJ = __ldg(bJ + w);
+  // Per word with a branch present in both tiles, what its incidences need
+  // comes from loads that depend only on the word: the rows of the window's
+  // block before the word and the block's total rows (cpre, written when the
+  // blocks were sized) and the block's byte offset.  A flagged row's rank is
+  // then that base plus a popcount; its row start and entries follow in two
+  // more loads.  The next word's bitmap words are loaded before this word's
+  // incidences are walked.
+  const int w_step = kSpWarps * n_parts;
+  int w = kf_words + part * kSpWarps + warp;
+  uint32_t nmI = 0, nmJ = 0;
+  if (w < w_end) {
+    nmI = __ldg(bI + w);
+    nmJ = __ldg(bJ + w);
+  }
+  for (; w < w_end; w += w_step) {
+    const uint32_t mI = nmI, mJ = nmJ;
+    if (w + w_step < w_end) {
+      nmI = __ldg(bI + w + w_step);
+      nmJ = __ldg(bJ + w + w_step);
+    }
     const uint32_t both = mI & mJ;
     if (both == 0u) continue;  // warp-uniform
-    const int j = (w - kf_words) / kWinWords;
-    const int wq = (w - kf_words) - j * kWinWords;
-    const int w0 = kf_words + j * kWinWords;
-    // rows of the window's blocks before this word
-    int cI = 0, cJ = 0;
-    if (lane < wq) {
-      cI = __popc(__ldg(bI + w0 + lane));
-      cJ = __popc(__ldg(bJ + w0 + lane));
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      cI += __shfl_xor_sync(0xffffffffu, cI, off);
-      cJ += __shfl_xor_sync(0xffffffffu, cJ, off);
-    }
-    const uint8_t *blkI = blocks + boff[tI * n_win + j];
-    const uint8_t *blkJ = blocks + boff[tJ * n_win + j];
-    const uint4 hI = __ldg(reinterpret_cast<const uint4 *>(blkI));
-    const uint4 hJ = __ldg(reinterpret_cast<const uint4 *>(blkJ));
+    const int jw = (w - kf_words) / kWinWords;
+    const int wq = (w - kf_words) - jw * kWinWords;
+    const int64_t itI = tI * n_win + jw, itJ = tJ * n_win + jw;
+    const uint32_t cI = __ldg(&cpre[itI * (kWinWords + 1) + wq].x);
+    const uint32_t cJ = __ldg(&cpre[itJ * (kWinWords + 1) + wq].x);
+    const uint32_t nrI = __ldg(&cpre[itI * (kWinWords + 1) + kWinWords].x);
+    const uint32_t nrJ = __ldg(&cpre[itJ * (kWinWords + 1) + kWinWords].x);
+    // block layout: 16-byte header, rowstart[rows + 1], entries at a 16-byte
+    // aligned offset
+    const uint8_t *blkI = blocks + __ldg(boff + itI);
+    const uint8_t *blkJ = blocks + __ldg(boff + itJ);
     const uint32_t *rsI = reinterpret_cast<const uint32_t *>(blkI) + 4;
     const uint32_t *rsJ = reinterpret_cast<const uint32_t *>(blkJ) + 4;
-    const uint8_t *riI = blkI + hI.z, *riJ = blkJ + hJ.z;  // presence entries
-    const unsigned long long *eI = reinterpret_cast<const unsigned long long *>(blkI + hI.z);
-    const unsigned long long *eJ = reinterpret_cast<const unsigned long long *>(blkJ + hJ.z);
+    const uint32_t offI = (16u + 4u * (nrI + 1u) + 15u) & ~15u;
+    const uint32_t offJ = (16u + 4u * (nrJ + 1u) + 15u) & ~15u;
+    const uint8_t *riI = blkI + offI, *riJ = blkJ + offJ;  // presence entries
+    const unsigned long long *eI = reinterpret_cast<const unsigned long long *>(blkI + offI);
+    const unsigned long long *eJ = reinterpret_cast<const unsigned long long *>(blkJ + offJ);
+    struct { uint32_t x; } hI{nrI}, hJ{nrJ};
 
     int nI = 0, nJ = 0;
     uint32_t sI = 0, sJ = 0;
@@ -480,7 +516,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     }
     const int total = nI * nJ;
     my_updates += (unsigned long long)total;
-    if (total > 0 && total <= kSmall) {
+    if (total > 0 && total <= lane_pairs) {
       for (int a = 0; a < nI; ++a) {
         if constexpr (PRES) {
           const int ra = (int)__ldg(riI + sI + a) * kAccLd;
@@ -502,7 +538,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     }
     // warp-walked incidences: the owning lane picks the lane side (the tile
     // whose row count fills more lanes) and packs the descriptor
-    const bool is_big = total > kSmall;
+    const bool is_big = total > lane_pairs;
     uint32_t desc = 0, sL = 0, sT = 0;
     if (is_big) {
       const bool lJ = fillv[nJ - 1] >= fillv[nI - 1];
@@ -602,7 +638,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     }
   }
   __syncthreads();
-  Acc *dst = spart + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TILE * TILE;
+  Acc *dst = spart + (int64_t)unit * TILE * TILE;
   for (int x = tid; x < TILE * TILE; x += kSpThreads) {
     const int q = (x / TILE) * kAccLd + x % TILE;
     if constexpr (PRES)
@@ -610,6 +646,8 @@ __global__ void __launch_bounds__(kSpThreads, 1)
     else
       dst[x] = sacc[q];
   }
+  __syncthreads();  // the accumulator is cleared for the next unit
+  }  // work units
   // pair updates done (statistics)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) my_updates += __shfl_xor_sync(0xffffffffu, my_updates, off);
@@ -746,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
                    int32_t kf_words, const uint8_t *blocks, const unsigned long long *boff,
-                   int32_t n_win, uint32_t *spart, int32_t sp_parts, const double *S,
+                   const uint2 *cpre, int32_t n_win, uint32_t *spart, int32_t sp_parts, const double *S,
                    const WorkItem *items, int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
@@ -759,8 +797,8 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const double *>(vals), ctx->n_cols, bits, n_words, n_words, nullptr,
-        1, 1.0, S, 0, o, cur_counters(ctx));
+        items, n_items, nullptr, static_cast<const double *>(vals), ctx->n_cols, bits, n_words,
+        n_words, nullptr, 1, 1.0, S, 0, o, cur_counters(ctx));
     ctx->stat_launches += 1;
   } else {
     const bool sparse = n_win > 0;
@@ -770,9 +808,14 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
       e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSm);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse weighted kernel attribute");
-      k_pairs_sparse<false><<<dim3(n_items, sp_parts), kSpThreads, kSm, ctx->stream>>>(
-          items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-          cur_bufs(ctx).blocks.bytes, ctx->n_tiles, nullptr, sp_parts, spart,
+      unsigned int *q = cur_queue(ctx, 1);
+      const dim3 grid = q ? dim3(pair_grid(ctx, k_pairs_sparse<false>, kSpThreads, kSm,
+                                           (int64_t)n_items * sp_parts))
+                          : dim3(n_items, sp_parts);
+      k_pairs_sparse<false><<<grid, kSpThreads, kSm, ctx->stream>>>(
+          items, n_items, q, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+          cur_bufs(ctx).blocks.bytes, ctx->n_tiles, cpre, nullptr, sp_parts, ctx->opt_lane_pairs[1],
+          spart,
           cur_counters(ctx) + 2);
       ctx->stat_launches += 1;
     }
@@ -780,8 +823,10 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
-    k_pairs_weighted<float><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
+    unsigned int *q = cur_queue(ctx, 0);
+    k_pairs_weighted<float><<<pair_grid(ctx, k_pairs_weighted<float>, kThreads, smem, n_items),
+                              kThreads, smem, ctx->stream>>>(
+        items, n_items, q, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
         sparse ? spart : nullptr, sp_parts, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
         cur_counters(ctx));
     ctx->stat_launches += 1;
@@ -792,7 +837,8 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
 }
 
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
-                          const uint8_t *blocks, const unsigned long long *boff, int32_t n_win,
+                          const uint8_t *blocks, const unsigned long long *boff,
+                          const uint2 *cpre, int32_t n_win,
                           unsigned long long *spart, const WorkItem *items, int32_t n_items) {
   if (n_items <= 0 || n_win <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
@@ -800,9 +846,12 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   cudaError_t e =
       cudaFuncSetAttribute(k_pairs_sparse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSm);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel attribute");
-  k_pairs_sparse<true><<<n_items, kSpThreads, kSm, ctx->stream>>>(
-      items, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
-      cur_bufs(ctx).blocks.bytes, ctx->n_tiles, ctx->d_qperm, 1, spart,
+  unsigned int *q = cur_queue(ctx, 1);
+  k_pairs_sparse<true><<<pair_grid(ctx, k_pairs_sparse<true>, kSpThreads, kSm, n_items),
+                         kSpThreads, kSm, ctx->stream>>>(
+      items, n_items, q, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+      cur_bufs(ctx).blocks.bytes, ctx->n_tiles, cpre, ctx->d_qperm, 1, ctx->opt_lane_pairs[0],
+      spart,
       cur_counters(ctx) + 2);
   ctx->stat_launches += 1;
   e = cudaGetLastError();

@@ -60,7 +60,11 @@ struct TcShared {
   uint8_t stage[TC_STAGES][STAGE_BYTES];  // A | B0 | B1 | B2, each 1024-aligned
   uint64_t full[TC_STAGES];
   uint64_t empty[TC_STAGES];
-  uint64_t done;
+  uint64_t done;           // MMA -> epilogue: an item's accumulators are complete
+  uint64_t tmem_free;      // epilogue -> MMA: the accumulators have been read back
+  uint64_t item_full[2];   // producer -> MMA, epilogue: a work item is in the ring slot
+  uint64_t item_empty[2];  // MMA + epilogue warps -> producer: the slot has been read
+  int32_t item_ring[2];
   uint32_t tmem_base;
   int32_t abort;
   int32_t issued;
@@ -85,6 +89,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -206,23 +214,27 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Work items: with a device queue the grid is persistent (one CTA per SM)
+// and each CTA pulls tile pairs until the queue runs dry; without one, the
+// CTA takes item blockIdx.x only.  Warp 0 (producer) fetches each item into a
+// two-slot ring in shared memory and streams its K-tiles through the stage
+// ring, running ahead into the next item while the epilogue of the current
+// one runs; warp 1 (MMA) waits for the epilogue to release the accumulators
+// (tmem_free) before the first MMA of the next item.  The stage ring's
+// sequence number runs on across items, so its phases stay consistent.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_d,
-               const WorkItem *__restrict__ items, const uint32_t *__restrict__ kbits,
-               int32_t k_words, int32_t n_cols, const unsigned long long *__restrict__ aq,
+               const WorkItem *__restrict__ items, int32_t n_items, unsigned int *__restrict__ queue,
+               const uint32_t *__restrict__ kbits, int32_t k_words, int32_t n_cols,
+               const unsigned long long *__restrict__ aq,
                const unsigned long long *__restrict__ spart, OutSpec o,
                unsigned long long *__restrict__ counter) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcShared &sh = *reinterpret_cast<TcShared *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WorkItem it = items[blockIdx.x];
-  const uint32_t *bI = kbits + (int64_t)it.tile_i * k_words;
-  const uint32_t *bJ = kbits + (int64_t)it.tile_j * k_words;
   unsigned long long *err = counter ? counter + 1 : nullptr;
-
-  int n_sel = 0;
-  for (int w = 0; w < k_words; ++w) n_sel += __popc(bI[w] & bJ[w]);
+  constexpr int kEpiWarps = TC_THREADS / 32 - 2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -230,6 +242,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&sh.empty[s], 1);
     }
     mbar_init(&sh.done, 1);
+    mbar_init(&sh.tmem_free, kEpiWarps);
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(&sh.item_full[r], 1);
+      mbar_init(&sh.item_empty[r], 1 + kEpiWarps);
+    }
     sh.abort = 0;
     sh.issued = 0;
     sh.consumed = 0;
@@ -247,114 +264,181 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = sh.tmem_base;
   volatile int32_t *abort = &sh.abort;
+  auto selected = [&](const WorkItem &it) {
+    const uint32_t *bI = kbits + (int64_t)it.tile_i * k_words;
+    const uint32_t *bJ = kbits + (int64_t)it.tile_j * k_words;
+    int n = 0;
+    for (int w = 0; w < k_words; ++w) n += __popc(bI[w] & bJ[w]);
+    return n;
+  };
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
-    if (lane == 0 && n_sel > 0) {
-      int i = 0;
-      bool go = true;
-      for (int w = 0; w < k_words && go; ++w) {
-        uint32_t m = bI[w] & bJ[w];
-        while (m && go) {
-          const int kt = w * 32 + __ffs(m) - 1;
-          m &= m - 1;
-          const int s = i % TC_STAGES;
-          if (i >= TC_STAGES && !mbar_wait(&sh.empty[s], ((i / TC_STAGES) - 1) & 1, abort, err)) {
-            go = false;
-            break;
-          }
-          mbar_arrive_expect_tx(&sh.full[s], STAGE_BYTES);
-          uint8_t *st = sh.stage[s];
-          tma_load_2d(st, &map_x, kt * TC_BK, it.tile_i * TC_BM, &sh.full[s]);
+    if (lane == 0) {
+      int i = 0;  // stage-ring sequence number, across items
+      for (int t = 0;; ++t) {
+        const int slot = t & 1;
+        if (t >= 2 && !mbar_wait(&sh.item_empty[slot], ((t >> 1) - 1) & 1, abort, err)) break;
+        int32_t item = n_items;
+        if (!*abort)
+          item = queue ? (int32_t)atomicAdd(queue, 1u) : (t == 0 ? (int32_t)blockIdx.x : n_items);
+        sh.item_ring[slot] = item;
+        mbar_arrive(&sh.item_full[slot]);
+        if (item >= n_items) break;
+        const WorkItem it = items[item];
+        const uint32_t *bI = kbits + (int64_t)it.tile_i * k_words;
+        const uint32_t *bJ = kbits + (int64_t)it.tile_j * k_words;
+        bool go = true;
+        for (int w = 0; w < k_words && go; ++w) {
+          uint32_t m = bI[w] & bJ[w];
+          while (m && go) {
+            const int kt = w * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            const int s = i % TC_STAGES;
+            if (i >= TC_STAGES &&
+                !mbar_wait(&sh.empty[s], ((i / TC_STAGES) - 1) & 1, abort, err)) {
+              go = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&sh.full[s], STAGE_BYTES);
+            uint8_t *st = sh.stage[s];
+            tma_load_2d(st, &map_x, kt * TC_BK, it.tile_i * TC_BM, &sh.full[s]);
 #pragma unroll
-          for (int p = 0; p < TC_PLANES; ++p)
-            tma_load_2d(st + A_BYTES + p * B_BYTES, &map_d, kt * TC_BK,
-                        p * n_cols + it.tile_j * TC_BN, &sh.full[s]);
-          ++i;
-          sh.issued = i;
+            for (int p = 0; p < TC_PLANES; ++p)
+              tma_load_2d(st + A_BYTES + p * B_BYTES, &map_d, kt * TC_BK,
+                          p * n_cols + it.tile_j * TC_BN, &sh.full[s]);
+            ++i;
+            sh.issued = i;
+          }
         }
+        if (!go) break;
       }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0 && n_sel > 0) {
-      int i = 0;
-      bool go = true;
-      for (int w = 0; w < k_words && go; ++w) {
-        uint32_t m = bI[w] & bJ[w];
-        while (m && go) {
-          m &= m - 1;
-          const int s = i % TC_STAGES;
-          if (!mbar_wait(&sh.full[s], (i / TC_STAGES) & 1, abort, err)) {
-            go = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t base = smem_u32(sh.stage[s]);
-          const uint64_t da = sdesc_sw128(base);
-#pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-#pragma unroll
-            for (int p = 0; p < TC_PLANES; ++p) {
-              const uint64_t db = sdesc_sw128(base + A_BYTES + p * B_BYTES);
-              // +2 = 32 bytes (16 BF16) along K inside the swizzled row
-              mma_bf16(tmem + p * TC_BN, da + 2 * kk, db + 2 * kk, (i > 0 || kk > 0) ? 1u : 0u);
+    if (lane == 0) {
+      int i = 0;         // stage-ring sequence number, across items
+      int tc_items = 0;  // items with selected K-tiles so far
+      for (int t = 0;; ++t) {
+        const int slot = t & 1;
+        if (!mbar_wait(&sh.item_full[slot], (t >> 1) & 1, abort, err)) break;
+        const int32_t item = sh.item_ring[slot];
+        mbar_arrive(&sh.item_empty[slot]);
+        if (item >= n_items) break;
+        const WorkItem it = items[item];
+        const uint32_t *bI = kbits + (int64_t)it.tile_i * k_words;
+        const uint32_t *bJ = kbits + (int64_t)it.tile_j * k_words;
+        if (selected(it) == 0) continue;
+        // the accumulators are free once the epilogue has read the last item's
+        if (tc_items > 0 && !mbar_wait(&sh.tmem_free, (tc_items - 1) & 1, abort, err)) break;
+        tc_fence_after();
+        bool go = true;
+        int first = 1;
+        for (int w = 0; w < k_words && go; ++w) {
+          uint32_t m = bI[w] & bJ[w];
+          while (m && go) {
+            m &= m - 1;
+            const int s = i % TC_STAGES;
+            if (!mbar_wait(&sh.full[s], (i / TC_STAGES) & 1, abort, err)) {
+              go = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t base = smem_u32(sh.stage[s]);
+            const uint64_t da = sdesc_sw128(base);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
+              for (int p = 0; p < TC_PLANES; ++p) {
+                const uint64_t db = sdesc_sw128(base + A_BYTES + p * B_BYTES);
+                // +2 = 32 bytes (16 BF16) along K inside the swizzled row
+                mma_bf16(tmem + p * TC_BN, da + 2 * kk, db + 2 * kk,
+                         (first && kk == 0) ? 0u : 1u);
+              }
+            }
+            first = 0;
+            mma_commit(&sh.empty[s]);
+            ++i;
+            sh.consumed = i;
           }
-          mma_commit(&sh.empty[s]);
-          ++i;
-          sh.consumed = i;
         }
+        if (!go) break;
+        mma_commit(&sh.done);  // arrives when every MMA issued above has completed
+        ++tc_items;
       }
-      mma_commit(&sh.done);  // arrives when every MMA issued above has completed
     }
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are this warp's rows
     const int row = q * 32 + lane;
-    bool ok = true;
-    if (n_sel > 0) {
-      ok = mbar_wait(&sh.done, 0, abort, err);
-      ok = __all_sync(0xffffffffu, ok);
-      tc_fence_after();
-    }
-    const StudyDev sd = o.studies[it.study];
-    const int64_t colI = (int64_t)it.tile_i * TC_BM, colJ = (int64_t)it.tile_j * TC_BN;
-    const int li = (int)(colI + row) - sd.col0;
-    const unsigned long long ai = aq[colI + row];
-    for (int c = 0; c < TC_BN / 32; ++c) {
-      uint32_t r0[32], r1[32], r2[32];
-      if (n_sel > 0 && ok) {
-        const uint32_t t = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32);
-        tmem_ld32(t, r0);
-        tmem_ld32(t + TC_BN, r1);
-        tmem_ld32(t + 2 * TC_BN, r2);
-        tmem_ld_wait();
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) r0[j] = r1[j] = r2[j] = 0u;
+    int tc_items = 0;
+    unsigned long long nsel = 0;
+    for (int t = 0;; ++t) {
+      const int slot = t & 1;
+      const bool got = __all_sync(0xffffffffu,
+                                  mbar_wait(&sh.item_full[slot], (t >> 1) & 1, abort, err));
+      if (!got) break;
+      const int32_t item = sh.item_ring[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.item_empty[slot]);
+      if (item >= n_items) break;
+      const WorkItem it = items[item];
+      const int n_sel = selected(it);
+      nsel += (unsigned long long)n_sel;
+      bool ok = true;
+      if (n_sel > 0) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&sh.done, tc_items & 1, abort, err));
+        tc_fence_after();
+        if (!ok) break;
       }
-      if (li >= sd.n) continue;
+      const StudyDev sd = o.studies[it.study];
+      const int64_t colI = (int64_t)it.tile_i * TC_BM, colJ = (int64_t)it.tile_j * TC_BN;
+      const int li = (int)(colI + row) - sd.col0;
+      const unsigned long long ai = aq[colI + row];
+      for (int c = 0; c < TC_BN / 32; ++c) {
+        uint32_t r0[32], r1[32], r2[32];
+        if (n_sel > 0) {
+          const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32);
+          tmem_ld32(tq, r0);
+          tmem_ld32(tq + TC_BN, r1);
+          tmem_ld32(tq + 2 * TC_BN, r2);
+          tmem_ld_wait();
+          if (c == TC_BN / 32 - 1) {
+            // every accumulator column of this warp's rows is in registers:
+            // the next item's MMAs may overwrite them
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.tmem_free);
+          }
+        } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = c * 32 + j;
-        const int lj = (int)(colJ + col) - sd.col0;
-        if (lj >= sd.n) continue;
-        if (li < lj) {
-          // all sums in units of the 24-bit lengths, exact 64-bit integers:
-          // G = 65536 G1 + 256 G2 + G3 (+ sparse part), A = a_i + a_j
-          unsigned long long g = ((unsigned long long)__float2uint_rn(__uint_as_float(r0[j])) << 16) +
-                                 ((unsigned long long)__float2uint_rn(__uint_as_float(r1[j])) << 8) +
-                                 (unsigned long long)__float2uint_rn(__uint_as_float(r2[j]));
-          if (spart) g += spart[(int64_t)blockIdx.x * TC_BM * TC_BN + row * TC_BN + col];
-          const unsigned long long A = ai + aq[colJ + col];
-          const float d = ratio01_f32((float)(A - 2 * g), (float)(A - g));
-          put_pair(o, sd, li, lj, d);
-        } else if (li == lj) {
-          put_diag(o, sd, li);
+          for (int j = 0; j < 32; ++j) r0[j] = r1[j] = r2[j] = 0u;
+        }
+        if (li >= sd.n) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = c * 32 + j;
+          const int lj = (int)(colJ + col) - sd.col0;
+          if (lj >= sd.n) continue;
+          if (li < lj) {
+            // all sums in units of the 24-bit lengths, exact 64-bit integers:
+            // G = 65536 G1 + 256 G2 + G3 (+ sparse part), A = a_i + a_j
+            unsigned long long g =
+                ((unsigned long long)__float2uint_rn(__uint_as_float(r0[j])) << 16) +
+                ((unsigned long long)__float2uint_rn(__uint_as_float(r1[j])) << 8) +
+                (unsigned long long)__float2uint_rn(__uint_as_float(r2[j]));
+            if (spart) g += spart[(int64_t)item * TC_BM * TC_BN + row * TC_BN + col];
+            const unsigned long long A = ai + aq[colJ + col];
+            const float d = ratio01_f32((float)(A - 2 * g), (float)(A - g));
+            put_pair(o, sd, li, lj, d);
+          } else if (li == lj) {
+            put_diag(o, sd, li);
+          }
         }
       }
+      if (n_sel > 0) ++tc_items;
     }
+    if (warp == 2 && lane == 0 && counter) atomicAdd(counter, nsel);
   }
 
   tc_fence_before();
@@ -375,7 +459,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  "r"(TMEM_COLS)
                  : "memory");
   }
-  if (threadIdx.x == 0 && counter) atomicAdd(counter, (unsigned long long)n_sel);
 }
 
 // Packing for the tensor-core path.  Block (column tile t, 4 K-tiles) of 256
@@ -563,8 +646,10 @@ int pairs_tc(unifrac_ctx *ctx, int32_t k_tc, const uint16_t *X, const uint16_t *
   cudaError_t e =
       cudaFuncSetAttribute(k_pairs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core kernel attribute");
-  k_pairs_tc<<<n_items, TC_THREADS, TC_SMEM, ctx->stream>>>(
-      mx, md, items, kbits, k_words, ctx->n_cols, aq, spart, o, cur_counters(ctx));
+  unsigned int *q = cur_queue(ctx, 0);
+  k_pairs_tc<<<pair_grid(ctx, k_pairs_tc, TC_THREADS, TC_SMEM, n_items), TC_THREADS, TC_SMEM,
+               ctx->stream>>>(mx, md, items, n_items, q, kbits, k_words, ctx->n_cols, aq, spart,
+                              o, cur_counters(ctx));
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core pair kernel");

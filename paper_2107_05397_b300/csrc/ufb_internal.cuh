@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -56,8 +57,10 @@ struct VarBufs {
   DevBuf vals, vals2, bits, persample, partial, rc, bsize, boff, blocks, cpre, spart, rbits;
 };
 
-// Device counters: [0, kCounterBase) unused; slot s (variant) owns
-// kCounterBase + 4 s + {0: selected units, 1: error code, 2: sparse updates}.
+// Device counters: slot s (variant) owns the work queues 4 s + {0: dense /
+// tensor-core / lookup pair kernel, 1: sparse pair kernel} (read as 32-bit
+// counters) and kCounterBase + 4 s + {0: selected units, 1: error code,
+// 2: sparse updates}; all are cleared at the start of the slot's run.
 constexpr int kCounterBase = 8;
 constexpr int kCounters = kCounterBase + 8;
 
@@ -133,6 +136,10 @@ struct unifrac_ctx {
   // ---- options
   int opt_uw_kernel = 0;
   int opt_flush = 256;
+  int opt_persistent = 1;  // pair kernels: persistent grid over a device work queue
+  // sparse kernels (slot 0 unweighted, 1 weighted): incidences of at most
+  // this many pairs are walked by one lane
+  int opt_lane_pairs[2] = {32, 32};
   double create_host_ms = 0.0;        // unifrac_create: validation and host preparation
   double create_device_ms = 0.0;      // unifrac_create: device set-up and uploads
   int opt_use_graph = 0;
@@ -191,6 +198,23 @@ inline VarBufs &cur_bufs(unifrac_ctx *ctx) { return ctx->vb[ctx->cur_slot]; }
 inline unsigned long long *cur_counters(unifrac_ctx *ctx) {
   return ctx->d_counter + kCounterBase + 4 * ctx->cur_slot;
 }
+// work queue k of the slot being enqueued, or nullptr when the pair kernels
+// run one CTA per work item (UNIFRAC_OPT_PERSISTENT = 0)
+inline unsigned int *cur_queue(unifrac_ctx *ctx, int k) {
+  return ctx->opt_persistent ? reinterpret_cast<unsigned int *>(ctx->d_counter + 4 * ctx->cur_slot + k)
+                             : nullptr;
+}
+// CTAs of a pair kernel launch: one per work unit, or (persistent) as many as
+// are resident at once, at most one per unit
+template <typename K>
+inline int pair_grid(unifrac_ctx *ctx, K kernel, int threads, size_t smem, int64_t units) {
+  if (!ctx->opt_persistent) return (int)units;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return (int)std::min<int64_t>(units, (int64_t)per_sm * ctx->sm_count);
+}
 }  // namespace ufb
 
 namespace ufb {
@@ -236,7 +260,8 @@ int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_
               uint32_t *bits, uint8_t *rc, unsigned long long *aq);
 // Unweighted sparse pairs (u64 per pair) of positions >= 32 * kf_words.
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
-                          const uint8_t *blocks, const unsigned long long *boff, int32_t n_win,
+                          const uint8_t *blocks, const unsigned long long *boff,
+                          const uint2 *cpre, int32_t n_win,
                           unsigned long long *spart, const WorkItem *items, int32_t n_items);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
@@ -258,7 +283,8 @@ int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a);
 constexpr int kMaxSparseParts = 8;
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
                    const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
-                   const unsigned long long *boff, int32_t n_win, uint32_t *spart,
+                   const unsigned long long *boff, const uint2 *cpre, int32_t n_win,
+                   uint32_t *spart,
                    int32_t sp_parts, const double *S, const WorkItem *items,
                    int32_t n_items, const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,

@@ -317,6 +317,57 @@ def test_unweighted_tensor_sparse_split(small, threshold, case):
     check_full(got, r, ub.MIXED)
 
 
+def test_sparse_lane_bound_changes_nothing(small):
+    """The sparse kernels' single-lane incidence bound only moves work between
+    two paths that add the same exact integers: every bound gives bit-identical
+    matrices (all positions sparse), equal to the oracle's within tolerance."""
+    w, ref = small
+    N = w.table.n_samples
+    for variant, th_opt, lane_opt in (
+            (ub.WEIGHTED_NORMALIZED, ub.OPT_SPARSE_THRESHOLD, ub.OPT_SPARSE_LANE_PAIRS),
+            (ub.UNWEIGHTED, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD,
+             ub.OPT_UNWEIGHTED_SPARSE_LANE_PAIRS)):
+        outs = []
+        for lane in (0, 1, 16, 64, 4096):
+            got = run(w.tree, w.table, variant, ub.MIXED,
+                      options={th_opt: 10**9, lane_opt: lane}).reshape(N, N)
+            check_full(got, ref[variant], ub.MIXED)
+            outs.append(got)
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_persistent_work_queue_equals_one_cta_per_item(variant):
+    """Pair kernels pulling work items from a device queue (persistent grid)
+    and one CTA per item compute each tile pair the same way: bit-identical
+    matrices, several studies, dense and sparse parts both in use, and equal
+    to the oracle within tolerance."""
+    rng = np.random.default_rng(57)
+    tree = synth.yule_tree(700, rng, 0.1)
+    sizes = [300, 5, 129, 0, 260, 1]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    N = int(offs[-1])
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], N)) < 0.04) * rng.integers(1, 30, (tips.shape[0], N))
+    table = synth.dense_to_table(dense, tips)
+    table.study_offsets = offs
+    opts = {ub.OPT_SPARSE_THRESHOLD: 40, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 20}
+    outs = []
+    for persistent in (0, 1):
+        outs.append(run(tree, table, variant, ub.MIXED, ub.OUT_CONDENSED,
+                        options={**opts, ub.OPT_PERSISTENT: persistent}))
+    np.testing.assert_array_equal(outs[0], outs[1])
+    pos = 0
+    for s, n in enumerate(sizes):
+        m = n * (n - 1) // 2
+        if n > 1:
+            sub = synth.dense_to_table(dense[:, offs[s]:offs[s + 1]], tips)
+            ref = oracle.unifrac_full(tree, sub, variant)
+            check_full(condensed_to_full(outs[1][pos:pos + m], n), ref, ub.MIXED)
+        pos += m
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_unweighted_mixed_kernel_choice(small, kernel):
     """Both unweighted mixed-precision kernels (tensor-core Gram, bit-packed
@@ -405,6 +456,9 @@ def test_autotune_and_cache(small, tmp_path):
         with ub.Context(w.tree, w.table) as ctx:
             rec = autotune.tune(ctx, variant, ub.MIXED, cache_path=cache)
             assert rec["cached"] is False
+            if variant == ub.WEIGHTED_NORMALIZED:
+                assert rec["flush"] in (128, 256, 512)
+                assert rec["lane_pairs"] == ctx.get_option(ub.OPT_SPARSE_LANE_PAIRS)
             got = ctx.run(variant, ub.MIXED, ub.OUT_FULL).cpu().numpy().astype(np.float64)
             check_full(got.reshape(N, N), ref[variant], ub.MIXED)
         with ub.Context(w.tree, w.table) as ctx:
