@@ -784,7 +784,8 @@ def main():
                                                  ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD,
                                                  ub.OPT_SPARSE_LANE_PAIRS,
                                                  ub.OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
-                                                 ub.OPT_WEIGHTED_FLUSH)}
+                                                 ub.OPT_WEIGHTED_FLUSH, ub.OPT_RARE_LIST,
+                                                 ub.OPT_UNWEIGHTED_RARE_LIST)}
     ctx.close()
     del out_both
     torch.cuda.empty_cache()

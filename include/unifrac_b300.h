@@ -225,13 +225,20 @@ enum unifrac_option {
   UNIFRAC_OPT_SPARSE_LANE_PAIRS = 8, /* weighted sparse pair kernel: a branch whose rows in
                                         the two tiles give at most this many pairs is walked
                                         by one lane, a larger one by a whole warp; 0 .. 4096,
-                                        default 32 */
+                                        default 128 (unweighted 64) */
   UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS = 9, /* the same for the unweighted sparse kernel */
-  UNIFRAC_OPT_PERSISTENT = 10 /* 1 (default): each mixed-precision pair kernel runs as one
-                                 persistent launch, as many CTAs as fit on the GPU at once,
-                                 each pulling (study, tile pair) work items from a device
-                                 counter in the order of the work list (largest studies
-                                 first); 0: one CTA per work item */
+  UNIFRAC_OPT_PERSISTENT = 10, /* 1 (default): each mixed-precision pair kernel runs as one
+                                  persistent launch, as many CTAs as fit on the GPU at once,
+                                  each pulling (study, tile pair) work items from a device
+                                  counter in the order of the work list (largest studies
+                                  first); 0: one CTA per work item */
+  UNIFRAC_OPT_RARE_LIST = 11,  /* weighted mixed kernel: branches of the sparse part present
+                                  in at most this many samples (all studies together) are
+                                  taken branch by branch -- every pair of the samples
+                                  holding one -- instead of by the sparse kernel's walk of
+                                  each tile pair's bitmap words; 0 .. 4096, 0 off, default
+                                  256; the sums are the same exact integers */
+  UNIFRAC_OPT_UNWEIGHTED_RARE_LIST = 12 /* the same for the unweighted sparse part */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
@@ -245,7 +252,9 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * THRESHOLD all tensor core or 1/32 .. 1/4, unweighted; then 3/4 and 3/2 of
  * the best), the single-lane incidence bound of the sparse kernels
  * (UNIFRAC_OPT_SPARSE_LANE_PAIRS / UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS
- * 16, 32, 64, when the split has a sparse part) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
+ * 32, 64, 128, 256, when the split has a sparse part), the per-branch list
+ * bound (UNIFRAC_OPT_RARE_LIST / UNIFRAC_OPT_UNWEIGHTED_RARE_LIST 0, 64, 256,
+ * 1024, likewise) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
  * 128, 256, 512).  Each candidate runs `repeats` times (>= 1, after one
  * warm-up run) into `out`, a DEVICE buffer of at least
  * unifrac_output_bytes(ctx, precision, UNIFRAC_OUT_CONDENSED, 0, -1) bytes

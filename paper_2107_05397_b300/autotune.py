@@ -29,7 +29,9 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.
 # options cached by value (name in the cache -> option id)
 _PLAIN_OPTIONS = {"lane_pairs": ub.OPT_SPARSE_LANE_PAIRS,
                   "uw_lane_pairs": ub.OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
-                  "flush": ub.OPT_WEIGHTED_FLUSH}
+                  "flush": ub.OPT_WEIGHTED_FLUSH,
+                  "rare_list": ub.OPT_RARE_LIST,
+                  "uw_rare_list": ub.OPT_UNWEIGHTED_RARE_LIST}
 
 
 def _bucket(x: float) -> int:
@@ -88,7 +90,8 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
     if variant == ub.UNWEIGHTED and precision == ub.MIXED:
         rec["uw_sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD) / max(n, 1)
     if precision == ub.MIXED:
-        mine = (("lane_pairs", "flush") if variant == ub.WEIGHTED_NORMALIZED else ("uw_lane_pairs",))
+        mine = (("lane_pairs", "flush", "rare_list") if variant == ub.WEIGHTED_NORMALIZED
+                else ("uw_lane_pairs", "uw_rare_list"))
         for name in mine:
             rec[name] = ub.unifrac_get_option(ctx.handle, _PLAIN_OPTIONS[name])
     if cache_path:

@@ -38,6 +38,8 @@ OPT_OVERLAP_VARIANTS = 7
 OPT_SPARSE_LANE_PAIRS = 8
 OPT_UNWEIGHTED_SPARSE_LANE_PAIRS = 9
 OPT_PERSISTENT = 10
+OPT_RARE_LIST = 11
+OPT_UNWEIGHTED_RARE_LIST = 12
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1

@@ -147,12 +147,14 @@ void free_ctx(unifrac_ctx *ctx) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
-                         &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1]};
+                         &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1],
+                         &ctx->item_of};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto &V : ctx->vb) {
     ufb::DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
-                            &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits};
+                            &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
+                            &V.vlist, &V.voff};
     for (auto *b : vbufs)
       if (b->p) cudaFree(b->p);
   }
@@ -791,6 +793,7 @@ struct RunPlan {
   bool f64;
   enum Kind { WEIGHTED, TENSOR, LOOKUP } kind;
   int32_t kf_words = 0, n_win = 0;
+  int32_t vr_words = 0;  // positions from 32 vr_words on are listed per branch (if < K)
   int32_t k_tc = 0;  // tensor-core positions (TENSOR)
   int32_t sp_parts = 1;  // parts of each tile pair's sparse sums (WEIGHTED)
   bool shares_gpu = false;  // runs beside the other variant on a second stream
@@ -843,6 +846,12 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   int rc;
   if ((rc = grow(ctx, ctx->items, items.size() * sizeof(WorkItem)))) return rc;
   if ((rc = grow(ctx, ctx->studies, studies.size() * sizeof(StudyDev)))) return rc;
+  // the work item of each (row tile, column tile), for the per-branch pairs
+  // of the very rarely present positions
+  std::vector<int32_t> item_of((size_t)ctx->n_tiles * ctx->n_tiles, -1);
+  for (size_t x = 0; x < items.size(); ++x)
+    item_of[(size_t)items[x].tile_i * ctx->n_tiles + items[x].tile_j] = (int32_t)x;
+  if ((rc = grow(ctx, ctx->item_of, std::max<size_t>(item_of.size(), 1) * sizeof(int32_t)))) return rc;
   cudaError_t e;
   if (!items.empty()) {
     e = cudaMemcpyAsync(ctx->items.p, items.data(), items.size() * sizeof(WorkItem),
@@ -852,12 +861,51 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   e = cudaMemcpyAsync(ctx->studies.p, studies.data(), studies.size() * sizeof(StudyDev),
                       cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload studies");
+  if (!item_of.empty()) {
+    e = cudaMemcpyAsync(ctx->item_of.p, item_of.data(), item_of.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload item table");
+  }
   // pageable sources: the copies above are staged before returning
   ctx->n_items = (int32_t)items.size();
   ctx->items_valid = true;
   ctx->items_layout = layout;
   ctx->items_s0 = s0;
   ctx->items_s1 = s1;
+  return UNIFRAC_OK;
+}
+
+// The sparse range [32 kf_words, K) splits at 32 vr_words: positions present
+// in at most the variant's rare-list bound of samples (all studies; they are last, positions go
+// by presence count descending) from the first such word on are listed per
+// branch.  Grows the lists and uploads their offsets (prefix sums of the
+// presence counts) when the split moved.  Returns the entries listed.
+static int plan_lists(unifrac_ctx *ctx, RunPlan &P, VarBufs &V, size_t entry_bytes) {
+  const int32_t k_words = (ctx->K + WORD - 1) / WORD;
+  P.vr_words = k_words;
+  const int64_t bound = ctx->opt_rare_list[P.variant == UNIFRAC_WEIGHTED_NORMALIZED ? 1 : 0];
+  if (bound > 0) {
+    int32_t pv = ctx->K;
+    while (pv > P.kf_words * WORD && ctx->nb_perm[pv - 1] <= bound) --pv;
+    P.vr_words = std::max(P.kf_words, (pv + WORD - 1) / WORD);
+  }
+  const int32_t p_list = P.vr_words * WORD;
+  if (p_list >= ctx->K) return UNIFRAC_OK;
+  std::vector<long long> voff((size_t)(ctx->K - p_list) + 1, 0);
+  for (int32_t k = p_list; k < ctx->K; ++k)
+    voff[(size_t)(k - p_list) + 1] = voff[(size_t)(k - p_list)] + ctx->nb_perm[k];
+  int rc;
+  const int64_t old_bytes = (int64_t)V.voff.bytes;
+  if ((rc = grow(ctx, V.vlist, std::max<size_t>((size_t)voff.back(), 1) * entry_bytes))) return rc;
+  if ((rc = grow(ctx, V.voff, voff.size() * sizeof(long long)))) return rc;
+  if (V.voff_pv != p_list || (int64_t)V.voff.bytes != old_bytes) {
+    // on the context's stream, after earlier work that may read the old
+    // offsets (a pageable source: staged before the call returns)
+    cudaError_t e = cudaMemcpyAsync(V.voff.p, voff.data(), voff.size() * sizeof(long long),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload list offsets");
+    V.voff_pv = p_list;
+  }
   return UNIFRAC_OK;
 }
 
@@ -882,16 +930,22 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       while (kf < ctx->K && ctx->nb_perm[kf] >= th) ++kf;
       P.kf_words = kf / WORD;
     }
-    P.n_win = (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    P.vr_words = (ctx->K + WORD - 1) / WORD;
+    const bool has_sparse = P.kf_words < n_words && P.kf_words * WORD < ctx->K;
+    if (has_sparse && (rc = plan_lists(ctx, P, V, 8))) return rc;
+    P.n_win = (P.vr_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    if (!has_sparse) P.n_win = (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    const bool listed = P.vr_words * WORD < ctx->K;
     // dense values for the positions below the split only (all of them when
     // there is no sparse part)
-    const size_t dense_rows = P.n_win > 0 ? (size_t)P.kf_words * WORD : (size_t)ctx->K_pad;
+    const size_t dense_rows =
+        (P.n_win > 0 || listed) ? (size_t)P.kf_words * WORD : (size_t)ctx->K_pad;
     if ((rc = grow(ctx, V.vals, std::max<size_t>(dense_rows, 1) * ctx->n_cols * elem))) return rc;
-    if (P.n_win > 0) {
+    if (P.n_win > 0 || listed) {
       // upper bound of the sparse blocks: every sample is in one tile, so a
       // branch has at most n_b entries and min(n_b, tiles) flagged rows
       uint64_t rows = 0, ents = 0;
-      for (int32_t k = P.kf_words * WORD; k < ctx->K; ++k) {
+      for (int32_t k = P.kf_words * WORD; k < std::min(ctx->K, P.vr_words * WORD); ++k) {
         rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
         ents += (uint64_t)ctx->nb_perm[k];
       }
@@ -928,7 +982,11 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
       P.k_tc = std::min<int32_t>(ctx->K_pad, (ctx->K - kMaxSparsePositions + 63) / 64 * 64);
     const int32_t n_words = ctx->K_pad / WORD;
     P.kf_words = P.k_tc / WORD;
-    P.n_win = P.k_tc >= ctx->K ? 0 : (n_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    P.vr_words = (ctx->K + WORD - 1) / WORD;
+    if (P.k_tc < ctx->K && (rc = plan_lists(ctx, P, V, 4))) return rc;
+    const bool listed = P.vr_words * WORD < ctx->K;
+    P.n_win = P.k_tc >= ctx->K ? 0 : (P.vr_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
+    (void)n_words;
     const int32_t n_kt = P.k_tc / 64;
     const int32_t k_words = (n_kt + 31) / 32;
     const size_t plane = (size_t)ctx->n_cols * P.k_tc * 2;
@@ -937,9 +995,9 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
     if ((rc = grow(ctx, V.bits, (size_t)ctx->n_tiles * k_words * 4))) return rc;
     if ((rc = grow(ctx, V.partial, (size_t)ctx->n_cols * 8))) return rc;
     if ((rc = grow(ctx, V.persample, (size_t)ctx->n_cols * 8))) return rc;
-    if (P.n_win > 0) {
+    if (P.n_win > 0 || listed) {
       uint64_t rows = 0, ents = 0;
-      for (int32_t k = P.kf_words * WORD; k < ctx->K; ++k) {
+      for (int32_t k = P.kf_words * WORD; k < std::min(ctx->K, P.vr_words * WORD); ++k) {
         rows += (uint64_t)std::min<int64_t>(ctx->nb_perm[k], ctx->n_tiles);
         ents += (uint64_t)ctx->nb_perm[k];
       }
@@ -996,28 +1054,39 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     uint32_t *bits = static_cast<uint32_t *>(V.bits.p);
     // dense values for the frequently present positions, sparse blocks built
     // from the counts for the rest
-    const int32_t k_end = P.n_win > 0 ? P.kf_words * WORD : ctx->K;
+    // positions [32 vr_words, K) are listed per branch
+    const bool listed = !P.f64 && P.vr_words * WORD < ctx->K;
+    const bool sparse = P.n_win > 0 || listed;
+    const int32_t k_end = sparse ? P.kf_words * WORD : ctx->K;
     if (!ctx->reuse_prepared &&
         (rc = pack_weighted(ctx, cnt, flag, P.f64, V.vals.p, bits, k_end)))
       return rc;
-    if (P.n_win > 0 && !ctx->reuse_prepared) {
+    if (sparse && !ctx->reuse_prepared) {
       uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
       if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, bits, rcb, nullptr))) return rc;
-      if ((rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words, P.n_win,
+      if (P.n_win > 0 &&
+          (rc = build_rare_blocks(ctx, true, cnt, bits, rcb, P.kf_words,
+                                  std::min(ctx->K, P.vr_words * WORD), P.n_win,
                                   static_cast<uint32_t *>(V.bsize.p),
                                   static_cast<unsigned long long *>(V.boff.p),
                                   static_cast<uint2 *>(V.cpre.p),
                                   static_cast<uint8_t *>(V.blocks.p))))
         return rc;
+      if (listed &&
+          (rc = list_fill(ctx, true, cnt, flag, P.vr_words * WORD,
+                          static_cast<const long long *>(V.voff.p), V.vlist.p)))
+        return rc;
     }
     if (!overlapped) record_event(ctx, ctx->ev[1]);
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 1.0;
-    if ((rc = pairs_weighted(ctx, P.f64, V.vals.p, bits, P.kf_words,
+    if ((rc = pairs_weighted(ctx, P.f64, V.vals.p, bits, P.kf_words, P.vr_words,
                              static_cast<const uint8_t *>(V.blocks.p),
                              static_cast<const unsigned long long *>(V.boff.p),
                              static_cast<const uint2 *>(V.cpre.p), P.n_win,
-                             P.n_win > 0 ? static_cast<uint32_t *>(V.spart.p) : nullptr,
+                             static_cast<const long long *>(V.voff.p),
+                             listed ? V.vlist.p : nullptr,
+                             sparse ? static_cast<uint32_t *>(V.spart.p) : nullptr,
                              P.sp_parts, S, d_items, n_items, o)))
       return rc;
   } else if (P.kind == RunPlan::TENSOR) {
@@ -1026,20 +1095,29 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     uint32_t *kbits = static_cast<uint32_t *>(V.bits.p);
     double *a = static_cast<double *>(V.persample.p);
     unsigned long long *aq = static_cast<unsigned long long *>(V.partial.p);
-    unsigned long long *spart = P.n_win > 0 ? static_cast<unsigned long long *>(V.spart.p) : nullptr;
+    const bool listed = P.vr_words * WORD < ctx->K && P.k_tc < ctx->K;
+    const bool sparse = P.n_win > 0 || listed;
+    unsigned long long *spart = sparse ? static_cast<unsigned long long *>(V.spart.p) : nullptr;
     if (!ctx->reuse_prepared) {
       e = cudaMemsetAsync(aq, 0, (size_t)ctx->n_cols * 8, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "clear per-sample sums");
       if ((rc = pack_tc(ctx, cnt, flag, P.k_tc, X, D, kbits, aq))) return rc;
-      if (P.n_win > 0) {
+      if (sparse) {
         uint32_t *rbits = static_cast<uint32_t *>(V.rbits.p);
         uint8_t *rcb = static_cast<uint8_t *>(V.rc.p);
+        // presence sums a_col over every sparse position, listed ones included
         if ((rc = pack_rare(ctx, cnt, flag, P.kf_words, rbits, rcb, aq))) return rc;
-        if ((rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words, P.n_win,
+        if (P.n_win > 0 &&
+            (rc = build_rare_blocks(ctx, false, cnt, rbits, rcb, P.kf_words,
+                                    std::min(ctx->K, P.vr_words * WORD), P.n_win,
                                     static_cast<uint32_t *>(V.bsize.p),
                                     static_cast<unsigned long long *>(V.boff.p),
                                     static_cast<uint2 *>(V.cpre.p),
                                     static_cast<uint8_t *>(V.blocks.p))))
+          return rc;
+        if (listed &&
+            (rc = list_fill(ctx, false, cnt, flag, P.vr_words * WORD,
+                            static_cast<const long long *>(V.voff.p), V.vlist.p)))
           return rc;
       }
       if ((rc = finish_tc_a(ctx, aq, a))) return rc;
@@ -1050,10 +1128,11 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     record_event(ctx, ctx->ev_sp[0][0]);
     if (spart &&
         (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(V.rbits.p), P.kf_words,
-                                    static_cast<const uint8_t *>(V.blocks.p),
+                                    P.vr_words, static_cast<const uint8_t *>(V.blocks.p),
                                     static_cast<const unsigned long long *>(V.boff.p),
-                                    static_cast<const uint2 *>(V.cpre.p), P.n_win, spart, d_items,
-                                    n_items)))
+                                    static_cast<const uint2 *>(V.cpre.p), P.n_win,
+                                    static_cast<const long long *>(V.voff.p),
+                                    listed ? V.vlist.p : nullptr, spart, d_items, n_items)))
       return rc;
     record_event(ctx, ctx->ev_sp[0][1]);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, aq, spart, d_items, n_items, o))) return rc;
@@ -1224,7 +1303,7 @@ static uint64_t prep_signature(const unifrac_ctx *ctx) {
   mix(ctx->tables);
   for (const ufb::VarBufs &V : ctx->vb)
     for (const ufb::DevBuf *b : {&V.vals, &V.vals2, &V.bits, &V.persample, &V.partial, &V.rc, &V.bsize,
-                                 &V.boff, &V.blocks, &V.cpre, &V.rbits})
+                                 &V.boff, &V.blocks, &V.cpre, &V.rbits, &V.vlist, &V.voff})
       mix(*b);
   return h;
 }
@@ -1400,6 +1479,11 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < 0 || value > 1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_persistent = (int)value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_RARE_LIST:
+    case UNIFRAC_OPT_UNWEIGHTED_RARE_LIST:
+      if (value < 0 || value > 4096) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_rare_list[option == UNIFRAC_OPT_RARE_LIST ? 1 : 0] = value;
+      return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_LANE_PAIRS:
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS:
       if (value < 0 || value > 4096) return UNIFRAC_E_INVALID_ARG;
@@ -1424,6 +1508,8 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
     case UNIFRAC_OPT_SPARSE_THRESHOLD: *value = ctx->opt_sparse_threshold; return UNIFRAC_OK;
     case UNIFRAC_OPT_SPARSE_LANE_PAIRS: *value = ctx->opt_lane_pairs[1]; return UNIFRAC_OK;
     case UNIFRAC_OPT_PERSISTENT: *value = ctx->opt_persistent; return UNIFRAC_OK;
+    case UNIFRAC_OPT_RARE_LIST: *value = ctx->opt_rare_list[1]; return UNIFRAC_OK;
+    case UNIFRAC_OPT_UNWEIGHTED_RARE_LIST: *value = ctx->opt_rare_list[0]; return UNIFRAC_OK;
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS: *value = ctx->opt_lane_pairs[0]; return UNIFRAC_OK;
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
       *value = ctx->opt_uw_sparse_threshold;
@@ -1623,7 +1709,8 @@ static void release_variant_buffers(unifrac_ctx *ctx, int slot) {
   if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
   VarBufs &V = ctx->vb[slot];
   DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
-                     &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits};
+                     &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
+                     &V.vlist, &V.voff};
   for (DevBuf *b : vbufs)
     if (b->p) {
       cudaFree(b->p);
@@ -1631,6 +1718,7 @@ static void release_variant_buffers(unifrac_ctx *ctx, int slot) {
       b->p = nullptr;
       b->bytes = 0;
     }
+  V.voff_pv = -1;
   ctx->buf_generation++;  // a captured graph holds the old addresses
   ctx->reuse_prepared = false;
 }
@@ -1711,7 +1799,11 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
   // incidences a lane walks alone (when the chosen split has a sparse part)
   if (!rc && th != 0)
     rc = tune(weighted ? UNIFRAC_OPT_SPARSE_LANE_PAIRS : UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
-              {16, 32, 64}, false);
+              {32, 64, 128, 256}, false);
+  // presence bound of the per-branch lists of the very rarely present positions
+  if (!rc && th != 0)
+    rc = tune(weighted ? UNIFRAC_OPT_RARE_LIST : UNIFRAC_OPT_UNWEIGHTED_RARE_LIST,
+              {0, 64, 256, 1024}, false);
   // branches summed in registers before each FP32 running-total update
   if (!rc && weighted) rc = tune(UNIFRAC_OPT_WEIGHTED_FLUSH, {128, 256, 512}, false);
   ctx->opt_use_graph = saved_graph;

@@ -710,8 +710,8 @@ int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_
 }
 
 int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
-                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint2 *cpre, uint8_t *blocks) {
+                      const uint8_t *rc, int32_t kf_words, int32_t k_end, int32_t n_win,
+                      uint32_t *bsize, unsigned long long *boff, uint2 *cpre, uint8_t *blocks) {
   cudaStream_t st = ctx->stream;
   const int64_t items = (int64_t)ctx->n_tiles * n_win;
   if (items <= 0) return UNIFRAC_OK;
@@ -720,20 +720,20 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
   const unsigned grid = (unsigned)((items * 32 + 255) / 256);
   const unsigned grid_fill = (unsigned)((items * kChunks * 32 + 255) / 256);
   if (values) {
-    k_rare_sizes<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+    k_rare_sizes<true><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc,
                                              ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<true><<<grid_fill, 256, 0, st>>>(
-        ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
         ctx->d_pmask, ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre,
         blocks,
         cur_bufs(ctx).blocks.bytes, cur_counters(ctx) + 1);
   } else {
-    k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc,
+    k_rare_sizes<false><<<grid, 256, 0, st>>>(ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc,
                                               ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid_fill, 256, 0, st>>>(
-        ctx->n_tiles, n_win, p0, ctx->K, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
         ctx->d_pmask, ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks,
         cur_bufs(ctx).blocks.bytes,
         cur_counters(ctx) + 1);

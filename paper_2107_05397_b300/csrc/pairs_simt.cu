@@ -655,6 +655,136 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 }
 
 // ----------------------------------------------------------------------------
+// very rarely present branches: one list per branch, all pairs of its samples
+//
+// Positions [pv, K) hold branches present in so few samples (at most the
+// UNIFRAC_OPT_RARE_LIST bound, all studies together) that walking their bitmap
+// words for every tile pair costs far more than their few co-present pairs.
+// They are taken branch by branch instead: k_list_fill writes, for position
+// k, one entry per sample where the branch is present (the global embedding
+// column; weighted: with V = round(v * 2^s), the same value the sparse blocks
+// carry), at offsets voff[k - pv] (host prefix sums of the presence counts);
+// k_pairs_list adds, for every pair of those samples, min(V_a, V_b)
+// (weighted) or q_k (unweighted) into the partial sums of the tile pair that
+// holds the pair (global atomics; item_of maps a (row tile, column tile) pair
+// to its work item, -1 when this run does not compute it).  The integer sums
+// are those the sparse kernel would have made, so the result is unchanged.
+
+constexpr int kListWarps = 8;
+
+template <bool VALUES>
+__global__ void __launch_bounds__(kListWarps * 32)
+    k_list_fill(int32_t pv, int32_t K, const int32_t *__restrict__ perm,
+                const uint8_t *__restrict__ flag, const uint4 *__restrict__ pmask, int32_t n_tiles,
+                const uint32_t *__restrict__ cnt, int64_t ldc, const double *__restrict__ len_perm,
+                const double *__restrict__ inv_total, float scale,
+                const long long *__restrict__ voff, uint32_t *__restrict__ cols,
+                unsigned long long *__restrict__ ents) {
+  const int64_t k = pv + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  const int32_t b = perm[k];
+  const long long base = voff[k - pv], cap = voff[k - pv + 1] - base;
+  const uint32_t lt = (1u << lane) - 1u;
+  float L = 0.f;
+  if constexpr (VALUES) L = (float)len_perm[k];
+  long long n = 0;  // entries written so far (warp-uniform)
+  for (int t0 = 0; t0 < n_tiles; t0 += 32) {
+    const int t = t0 + lane;
+    const bool fl = t < n_tiles && flag[(int64_t)b * n_tiles + t];
+    uint32_t m = __ballot_sync(0xffffffffu, fl);
+    while (m) {
+      const int tt = t0 + __ffs(m) - 1;
+      m &= m - 1;
+      // bit l of word w of the mask: column 4 l + w of the tile
+      const uint4 pm = pmask[(int64_t)b * n_tiles + tt];
+      const uint32_t wv[4] = {pm.x, pm.y, pm.z, pm.w};
+      uint32_t mine = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) mine += (wv[w] >> lane) & 1u;
+      uint32_t before = mine;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, before, off);
+        if (lane >= off) before += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
+      before -= mine;
+      uint32_t q = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        if (!((wv[w] >> lane) & 1u)) continue;
+        const long long at = n + before + q++;
+        if (at >= cap) continue;  // defensive: never past the branch's share
+        const int64_t col = (int64_t)tt * TILE + 4 * lane + w;
+        if constexpr (VALUES) {
+          const float inv = (float)inv_total[col];
+          const float v = L * ((float)cnt[(int64_t)b * ldc + col] * inv);
+          ents[base + at] = ((unsigned long long)__float2uint_rn(v * scale) << 32) |
+                            (unsigned long long)(uint32_t)col;
+        } else {
+          cols[base + at] = (uint32_t)col;
+        }
+      }
+      n += total;
+      (void)lt;
+    }
+  }
+}
+
+template <bool PRES>
+__global__ void __launch_bounds__(kListWarps * 32)
+    k_pairs_list(int32_t pv, int32_t K, const long long *__restrict__ voff,
+                 const uint32_t *__restrict__ cols, const unsigned long long *__restrict__ ents,
+                 const uint32_t *__restrict__ qlen, const int32_t *__restrict__ item_of,
+                 int32_t n_tiles, typename SparseCfg<PRES>::Acc *__restrict__ spart,
+                 unsigned long long *__restrict__ n_updates) {
+  const int64_t k = pv + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  const long long base = voff[k - pv];
+  const int m = (int)(voff[k - pv + 1] - base);
+  uint32_t q = 0;
+  if constexpr (PRES) q = qlen[k];
+  unsigned long long done = 0;
+  for (int i = 0; i < m - 1; ++i) {
+    uint32_t ci;
+    uint32_t vi = 0;
+    if constexpr (PRES) {
+      ci = __ldg(cols + base + i);
+    } else {
+      const unsigned long long e = __ldg(ents + base + i);
+      ci = (uint32_t)e;
+      vi = (uint32_t)(e >> 32);
+    }
+    for (int j = i + 1 + lane; j < m; j += 32) {
+      uint32_t cj;
+      uint32_t vj = 0;
+      if constexpr (PRES) {
+        cj = __ldg(cols + base + j);
+      } else {
+        const unsigned long long e = __ldg(ents + base + j);
+        cj = (uint32_t)e;
+        vj = (uint32_t)(e >> 32);
+      }
+      const uint32_t lo = min(ci, cj), hi = max(ci, cj);
+      if (hi >= (uint32_t)n_tiles * TILE) continue;  // defensive: a column must exist
+      const int32_t item = item_of[(int64_t)(lo / TILE) * n_tiles + hi / TILE];
+      if (item < 0) continue;
+      const int64_t at = (int64_t)item * TILE * TILE + (lo % TILE) * TILE + hi % TILE;
+      if constexpr (PRES)
+        atomicAdd(&spart[at], (unsigned long long)q);
+      else
+        atomicAdd(&spart[at], min(vi, vj));
+      ++done;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
+  if (lane == 0 && n_updates && done) atomicAdd(n_updates, done);
+}
+
+// ----------------------------------------------------------------------------
 // unweighted, bit-packed lookup (FP64 sums)
 
 constexpr int BG = 8;                              // groups per stage
@@ -783,8 +913,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
-                   int32_t kf_words, const uint8_t *blocks, const unsigned long long *boff,
-                   const uint2 *cpre, int32_t n_win, uint32_t *spart, int32_t sp_parts, const double *S,
+                   int32_t kf_words, int32_t vr_words, const uint8_t *blocks,
+                   const unsigned long long *boff, const uint2 *cpre, int32_t n_win,
+                   const long long *voff, const void *list, uint32_t *spart, int32_t sp_parts, const double *S,
                    const WorkItem *items, int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
@@ -801,9 +932,18 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
         n_words, nullptr, 1, 1.0, S, 0, o, cur_counters(ctx));
     ctx->stat_launches += 1;
   } else {
-    const bool sparse = n_win > 0;
+    // a sparse part exists when some positions are neither dense nor listed
+    // (n_win > 0) or some are listed; the listed ones add into the sparse
+    // kernel's partial sums (part 0), so those are written or cleared first
+    const bool listed = list != nullptr && vr_words * WORD < ctx->K;
+    const bool sparse = n_win > 0 || listed;
     record_event(ctx, ctx->ev_sp[1][0]);
-    if (sparse) {
+    if (sparse && n_win <= 0) {
+      e = cudaMemsetAsync(spart, 0, (size_t)n_items * sp_parts * TILE * TILE * sizeof(uint32_t),
+                          ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "clear sparse sums");
+    }
+    if (n_win > 0) {
       constexpr size_t kSm = SparseCfg<false>::kSmem;
       e = cudaFuncSetAttribute(k_pairs_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSm);
@@ -813,11 +953,15 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
                                            (int64_t)n_items * sp_parts))
                           : dim3(n_items, sp_parts);
       k_pairs_sparse<false><<<grid, kSpThreads, kSm, ctx->stream>>>(
-          items, n_items, q, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+          items, n_items, q, bits, n_words, kf_words, vr_words, n_win, blocks, boff,
           cur_bufs(ctx).blocks.bytes, ctx->n_tiles, cpre, nullptr, sp_parts, ctx->opt_lane_pairs[1],
           spart,
           cur_counters(ctx) + 2);
       ctx->stat_launches += 1;
+    }
+    if (listed) {
+      int rc = pairs_list(ctx, false, vr_words * WORD, voff, list, spart);
+      if (rc) return rc;
     }
     record_event(ctx, ctx->ev_sp[1][1]);
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
@@ -837,10 +981,17 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
 }
 
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
-                          const uint8_t *blocks, const unsigned long long *boff,
-                          const uint2 *cpre, int32_t n_win,
-                          unsigned long long *spart, const WorkItem *items, int32_t n_items) {
-  if (n_items <= 0 || n_win <= 0) return UNIFRAC_OK;
+                          int32_t vr_words, const uint8_t *blocks, const unsigned long long *boff,
+                          const uint2 *cpre, int32_t n_win, const long long *voff,
+                          const void *list, unsigned long long *spart, const WorkItem *items,
+                          int32_t n_items) {
+  const bool listed = list != nullptr && vr_words * WORD < ctx->K;
+  if (n_items <= 0 || (n_win <= 0 && !listed)) return UNIFRAC_OK;
+  if (n_win <= 0) {  // only listed positions: their sums start from zero
+    cudaError_t e = cudaMemsetAsync(spart, 0, (size_t)n_items * TILE * TILE * 8, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear sparse sums");
+    return pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
+  }
   const int32_t n_words = ctx->K_pad / WORD;
   constexpr size_t kSm = SparseCfg<true>::kSmem;
   cudaError_t e =
@@ -849,13 +1000,55 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   unsigned int *q = cur_queue(ctx, 1);
   k_pairs_sparse<true><<<pair_grid(ctx, k_pairs_sparse<true>, kSpThreads, kSm, n_items),
                          kSpThreads, kSm, ctx->stream>>>(
-      items, n_items, q, bits, n_words, kf_words, (ctx->K + WORD - 1) / WORD, n_win, blocks, boff,
+      items, n_items, q, bits, n_words, kf_words, vr_words, n_win, blocks, boff,
       cur_bufs(ctx).blocks.bytes, ctx->n_tiles, cpre, ctx->d_qperm, 1, ctx->opt_lane_pairs[0],
       spart,
       cur_counters(ctx) + 2);
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel");
+  if (listed) return pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
+  return UNIFRAC_OK;
+}
+
+int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag, int32_t pv,
+              const long long *voff, void *list) {
+  const int64_t n = (int64_t)ctx->K - pv;
+  if (n <= 0) return UNIFRAC_OK;
+  const unsigned grid = (unsigned)((n + kListWarps - 1) / kListWarps);
+  if (values)
+    k_list_fill<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+        pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
+        ctx->n_tiles, cnt, ctx->n_cols, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, voff,
+        nullptr, static_cast<unsigned long long *>(list));
+  else
+    k_list_fill<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+        pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
+        ctx->n_tiles, cnt, ctx->n_cols, nullptr, nullptr, 1.f, voff,
+        static_cast<uint32_t *>(list), nullptr);
+  ctx->stat_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch lists");
+  return UNIFRAC_OK;
+}
+
+int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, const long long *voff,
+               const void *list, void *spart) {
+  const int64_t n = (int64_t)ctx->K - pv;
+  if (n <= 0) return UNIFRAC_OK;
+  const unsigned grid = (unsigned)((n + kListWarps - 1) / kListWarps);
+  const int32_t *item_of = static_cast<const int32_t *>(ctx->item_of.p);
+  if (presence)
+    k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+        pv, ctx->K, voff, static_cast<const uint32_t *>(list), nullptr, ctx->d_qperm, item_of,
+        ctx->n_tiles, static_cast<unsigned long long *>(spart), cur_counters(ctx) + 2);
+  else
+    k_pairs_list<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+        pv, ctx->K, voff, nullptr, static_cast<const unsigned long long *>(list), nullptr, item_of,
+        ctx->n_tiles, static_cast<uint32_t *>(spart), cur_counters(ctx) + 2);
+  ctx->stat_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch pairs");
   return UNIFRAC_OK;
 }
 

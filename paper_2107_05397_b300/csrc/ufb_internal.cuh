@@ -55,6 +55,8 @@ struct DevBuf {
 // of one call can run concurrently on two streams.
 struct VarBufs {
   DevBuf vals, vals2, bits, persample, partial, rc, bsize, boff, blocks, cpre, spart, rbits;
+  DevBuf vlist, voff;  // very rarely present positions: lists, offsets
+  int32_t voff_pv = -1;  // first listed position the offsets in voff were made for
 };
 
 // Device counters: slot s (variant) owns the work queues 4 s + {0: dense /
@@ -137,9 +139,12 @@ struct unifrac_ctx {
   int opt_uw_kernel = 0;
   int opt_flush = 256;
   int opt_persistent = 1;  // pair kernels: persistent grid over a device work queue
+  // branches present in at most this many samples (slot 0 unweighted, 1
+  // weighted) are summed from per-branch lists instead of the sparse kernel
+  int64_t opt_rare_list[2] = {256, 256};
   // sparse kernels (slot 0 unweighted, 1 weighted): incidences of at most
   // this many pairs are walked by one lane
-  int opt_lane_pairs[2] = {32, 32};
+  int opt_lane_pairs[2] = {64, 128};
   double create_host_ms = 0.0;        // unifrac_create: validation and host preparation
   double create_device_ms = 0.0;      // unifrac_create: device set-up and uploads
   int opt_use_graph = 0;
@@ -188,6 +193,7 @@ struct unifrac_ctx {
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, items, studies, stage, tables, chunk_dev[2];
+  ufb::DevBuf item_of;  // [n_tiles x n_tiles] work item of each tile pair, -1 if none
   ufb::VarBufs vb[2];
   size_t device_bytes = 0;
 };
@@ -244,25 +250,34 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag);
 // multiple of 32).
 int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
                   bool f64, void *vals, uint32_t *bits, int32_t k_end);
-// Sparse blocks of positions >= 32 * kf_words, one per (tile, window of
+// Sparse blocks of positions [32 * kf_words, k_end), one per (tile, window of
 // kRareWin positions): sizes, byte offsets boff[n_tiles * n_win + 1] and fill.
-// Values come from vals (weighted) or, when vals is null, presences from cnt.
-// values: weighted blocks (fixed-point values round(v * sp_scale)); else
-// presence blocks.  Both read the counts.
+// values: weighted blocks (fixed-point values round(v * sp_scale)) from the
+// counts; else presence blocks from the presence masks.
 // cpre: [n_tiles * n_win][kRareWin / 32 + 1] (rows, entries) before each
 // chunk of 32 positions of a block, totals last.
 int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
-                      const uint8_t *rc, int32_t kf_words, int32_t n_win, uint32_t *bsize,
-                      unsigned long long *boff, uint2 *cpre, uint8_t *blocks);
+                      const uint8_t *rc, int32_t kf_words, int32_t k_end, int32_t n_win,
+                      uint32_t *bsize, unsigned long long *boff, uint2 *cpre, uint8_t *blocks);
 // Packing of positions >= 32 * kf_words for the sparse kernels: bitmap words,
 // row non-zero counts and, when aq is given, aq[col] += q_k.
 int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t kf_words,
               uint32_t *bits, uint8_t *rc, unsigned long long *aq);
 // Unweighted sparse pairs (u64 per pair) of positions >= 32 * kf_words.
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
-                          const uint8_t *blocks, const unsigned long long *boff,
-                          const uint2 *cpre, int32_t n_win,
-                          unsigned long long *spart, const WorkItem *items, int32_t n_items);
+                          int32_t vr_words, const uint8_t *blocks, const unsigned long long *boff,
+                          const uint2 *cpre, int32_t n_win, const long long *voff,
+                          const void *list, unsigned long long *spart, const WorkItem *items,
+                          int32_t n_items);
+// Very rarely present positions [pv, K), one list per position (voff: host
+// prefix sums of their presence counts): the columns where each is present
+// (values: with the fixed-point value of the sparse blocks, u64 (V << 32) |
+// column; else u32 columns), and the pairs of each list added into the
+// sparse partial sums of their tile pairs (ctx->item_of).
+int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag, int32_t pv,
+              const long long *voff, void *list);
+int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, const long long *voff,
+               const void *list, void *spart);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
@@ -282,9 +297,9 @@ int finish_tc_a(unifrac_ctx *ctx, const unsigned long long *aq, double *a);
 // 1 <= sp_parts <= kMaxSparseParts.
 constexpr int kMaxSparseParts = 8;
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
-                   const uint32_t *bits, int32_t kf_words, const uint8_t *blocks,
-                   const unsigned long long *boff, const uint2 *cpre, int32_t n_win,
-                   uint32_t *spart,
+                   const uint32_t *bits, int32_t kf_words, int32_t vr_words,
+                   const uint8_t *blocks, const unsigned long long *boff, const uint2 *cpre,
+                   int32_t n_win, const long long *voff, const void *list, uint32_t *spart,
                    int32_t sp_parts, const double *S, const WorkItem *items,
                    int32_t n_items, const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,

@@ -338,6 +338,53 @@ def test_sparse_lane_bound_changes_nothing(small):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_rare_branch_lists_change_nothing(variant, small):
+    """Branches present in few samples summed from per-branch lists (every
+    pair of their samples) instead of the sparse kernel's walk: the same exact
+    integers, so bit-identical matrices for every list bound -- off, some,
+    every sparse position listed -- on one study, several studies and a stripe
+    range of a study; equal to the oracle within tolerance."""
+    th_opt, list_opt = ((ub.OPT_SPARSE_THRESHOLD, ub.OPT_RARE_LIST)
+                        if variant == ub.WEIGHTED_NORMALIZED else
+                        (ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD, ub.OPT_UNWEIGHTED_RARE_LIST))
+    w, ref = small
+    N = w.table.n_samples
+    outs = []
+    for bound in (0, 3, 12, 4096):
+        got = run(w.tree, w.table, variant, ub.MIXED,
+                  options={th_opt: 10**9, list_opt: bound}).reshape(N, N)
+        check_full(got, ref[variant], ub.MIXED)
+        outs.append(got)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    # several studies (pairs only within a study) and a stripe range
+    rng = np.random.default_rng(58)
+    tree = synth.yule_tree(700, rng, 0.1)
+    sizes = [300, 5, 129, 0, 260, 1]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    tips = tree.tips()
+    dense = (rng.random((tips.shape[0], int(offs[-1]))) < 0.04) * \
+        rng.integers(1, 30, (tips.shape[0], int(offs[-1])))
+    table = synth.dense_to_table(dense, tips)
+    table.study_offsets = offs
+    multi = [run(tree, table, variant, ub.MIXED, ub.OUT_CONDENSED,
+                 options={th_opt: 40, list_opt: bound}) for bound in (0, 8, 4096)]
+    for o in multi[1:]:
+        np.testing.assert_array_equal(o, multi[0])
+    one = synth.dense_to_table(dense[:, :300], tips)
+    ref1 = oracle.unifrac_full(tree, one, variant)
+    check_full(condensed_to_full(multi[1][:300 * 299 // 2], 300), ref1, ub.MIXED)
+    stripes = [run(tree, one, variant, ub.MIXED, ub.OUT_STRIPES, 40, 77,
+                   options={th_opt: 30, list_opt: bound}) for bound in (0, 8, 4096)]
+    for o in stripes[1:]:
+        np.testing.assert_array_equal(o, stripes[0])
+    blk = stripes[1].reshape(77 - 40, 300)
+    k = np.arange(300)
+    for si, s_ in enumerate(range(40, 77)):
+        np.testing.assert_allclose(blk[si], ref1[k, (k + s_ + 1) % 300], rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_persistent_work_queue_equals_one_cta_per_item(variant):
     """Pair kernels pulling work items from a device queue (persistent grid)
     and one CTA per item compute each tile pair the same way: bit-identical
