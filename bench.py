@@ -111,11 +111,13 @@ KERNEL_SOURCES = {
     "k_pairs_weighted<float>": ("pairs_simt.cu", "epilogue.cuh", "ufb_internal.cuh"),
     "k_pairs_sparse<false>": ("pairs_simt.cu", "ufb_internal.cuh"),
     "k_pairs_sparse<true>": ("pairs_simt.cu", "ufb_internal.cuh"),
+    "k_pairs_list<false>": ("pairs_simt.cu", "ufb_internal.cuh"),
+    "k_pairs_list<true>": ("pairs_simt.cu", "ufb_internal.cuh"),
 }
 # functions of capi.cu that plan the pair launches (work items, their order,
 # buffer sizes): part of every pair kernel's record
 PLANNING_FUNCTIONS = ("void study_items(", "static int plan_items(", "static int plan_buffers(",
-                      "static int32_t sparse_parts(")
+                      "static int32_t sparse_parts(", "static int plan_lists(")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -183,6 +185,8 @@ def record_traffic(csv_path: str, workload: str, samples: int, capture: str, thr
     h = rows[hdr]
     ki, ii, mi, vi = (h.index("Kernel Name"), h.index("ID"), h.index("Metric Name"),
                       h.index("Metric Value"))
+    ui = h.index("Metric Unit") if "Metric Unit" in h else None
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     per = {}
     for r in rows[hdr + 1:]:
         if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
@@ -190,8 +194,9 @@ def record_traffic(csv_path: str, workload: str, samples: int, capture: str, thr
         name = r[ki].split("(")[0].split("::")[-1].replace("<1>", "<true>").replace("<0>", "<false>")
         if name not in KERNEL_SOURCES:
             continue
-        per.setdefault(name, {}).setdefault(r[ii], 0.0)
-        per[name][r[ii]] += float(r[vi].replace(",", ""))
+        unit = scale.get(r[ui], 1.0) if ui is not None else 1.0
+        per.setdefault(name, {}).setdefault((r[ii], r[ki]), 0.0)
+        per[name][(r[ii], r[ki])] += float(r[vi].replace(",", "")) * unit
     out = {"workload": workload, "samples": samples, "capture": capture, "thresholds": thresholds}
     for name, launches in sorted(per.items()):
         vals = list(launches.values())
@@ -533,11 +538,15 @@ def main():
         n_max = (int(max(np.diff(tb.study_offsets))) if tb.study_offsets is not None
                  else tb.n_samples)
         return record_traffic(args.record_traffic, args.workload, tb.n_samples,
-                              "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
-                              "--clock-control none -k regex:^<kernel> -s <skip> -c 1 on "
-                              f"bench.py --workload {args.workload} --sparse-fraction "
-                              f"{args.sparse_fraction} --uw-sparse-fraction "
-                              f"{args.uw_sparse_fraction}, one ncu call per kernel",
+                              "one ncu call per pair-kernel family <k> (k_pairs_sparse, "
+                              "k_pairs_weighted, k_pairs_tc, k_pairs_list): ncu --metrics "
+                              "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                              "--clock-control none -k regex:<k> -c 6 --csv python bench.py "
+                              f"--workload {args.workload} --steps 1 --warmup 1 --no-e2e "
+                              "--no-fp64 --no-cpu-baseline --mantel-perms 0 --no-graph "
+                              "--no-overlap (settings from the package's tuned cache: split "
+                              f"fractions {args.sparse_fraction} weighted, "
+                              f"{args.uw_sparse_fraction} unweighted)",
                               split_thresholds(args.sparse_fraction, args.uw_sparse_fraction, n_max))
     if args.impl == "reference":
         return reference_arm(args)
@@ -622,6 +631,7 @@ def main():
         step()
     step_ms, pair_wn_ms, pair_uw_ms, sel_wn, sel_uw = [], [], [], [], []
     sp_uw_ms, sp_wn_ms, sp_uw_n, sp_wn_n, serial_ms = [], [], [], [], []
+    li_uw_ms, li_wn_ms, li_uw_n, li_wn_n = [], [], [], []
     launches = 0
     peaks = measured_peaks()
 
@@ -661,6 +671,10 @@ def main():
             sp_wn_ms.append(ctx.stat(ub.STAT_SPARSE_MS_WEIGHTED))
             sp_uw_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_UNWEIGHTED))
             sp_wn_n.append(ctx.stat(ub.STAT_SPARSE_UPDATES_WEIGHTED))
+            li_uw_ms.append(ctx.stat(ub.STAT_LIST_MS_UNWEIGHTED))
+            li_wn_ms.append(ctx.stat(ub.STAT_LIST_MS_WEIGHTED))
+            li_uw_n.append(ctx.stat(ub.STAT_LIST_UPDATES_UNWEIGHTED))
+            li_wn_n.append(ctx.stat(ub.STAT_LIST_UPDATES_WEIGHTED))
         ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0 if args.no_overlap else 1)
     clk = clocks.summary()
     dev_err = ctx.stat(ub.STAT_DEVICE_ERROR)
@@ -700,7 +714,8 @@ def main():
                         "traffic": recorded_traffic(kernel, w.name, N, thresholds_now),
                         "work": work_note, "peak_source": peak_note, **extra})
 
-    entry("k_pairs_tc", uw_ms - mean(sp_uw_ms), 6.0 * mean(sel_uw), "tensor", tc_peak, "TFLOP/s",
+    entry("k_pairs_tc", uw_ms - mean(sp_uw_ms) - mean(li_uw_ms), 6.0 * mean(sel_uw), "tensor",
+          tc_peak, "TFLOP/s",
           "3 BF16 digit planes x 2 flops per selected pair-branch (64-branch K-tiles)", tc_src)
     # the shared-memory atomic unit (one 32-lane wavefront per cycle per SM):
     # a secondary ceiling of the sparse kernels' implementation
@@ -709,12 +724,22 @@ def main():
           "1 add of len_b per co-present pair-branch (the unweighted update)", alu_src,
           smem_atomic_frac=(2.0 * mean(sp_uw_n) / (mean(sp_uw_ms) / 1e3) / atom
                             if mean(sp_uw_ms) > 0 else None))
-    entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms), 2.0 * mean(sel_wn), "alu", alu_peak,
+    entry("k_pairs_weighted<float>", wn_ms - mean(sp_wn_ms) - mean(li_wn_ms), 2.0 * mean(sel_wn),
+          "alu", alu_peak,
           "T ops/s", "2 FP32 ops (min, add) per selected pair-branch", alu_src)
     entry("k_pairs_sparse<false>", mean(sp_wn_ms), 2.0 * mean(sp_wn_n), "alu", alu_peak,
           "T ops/s", "2 ops (min, add) per co-present pair-branch (the weighted update)", alu_src,
           smem_atomic_frac=(mean(sp_wn_n) / (mean(sp_wn_ms) / 1e3) / atom
                             if mean(sp_wn_ms) > 0 else None))
+    # per-branch lists of the very rarely present branches: each pair update is
+    # a read-modify-write of one partial sum in device memory (4 bytes each
+    # way weighted, 8 unweighted), the branches' entries read once besides
+    hbm = (peaks or {}).get("hbm_gbs") or 6400.0
+    for kern, ms_l, n_l, b_upd in (("k_pairs_list<true>", mean(li_uw_ms), mean(li_uw_n), 16.0),
+                                   ("k_pairs_list<false>", mean(li_wn_ms), mean(li_wn_n), 8.0)):
+        entry(kern, ms_l, n_l * b_upd * 1e3, "hbm", hbm, "GB/s",  # entry() divides by 1e12
+              f"{b_upd:g} bytes per co-present pair-branch update (a read and a write of one "
+              "partial sum, global atomics)", "measured copy bandwidth (MEASURED_PEAKS.json)")
     roofline = max(kernels, key=lambda k: k["ms"])
     layout_name = "full" if layout == ub.OUT_FULL else "condensed"
     line = {

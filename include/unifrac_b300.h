@@ -254,7 +254,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * (UNIFRAC_OPT_SPARSE_LANE_PAIRS / UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS
  * 32, 64, 128, 256, when the split has a sparse part), the per-branch list
  * bound (UNIFRAC_OPT_RARE_LIST / UNIFRAC_OPT_UNWEIGHTED_RARE_LIST 0, 64, 256,
- * 1024, likewise) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
+ * 1024, likewise; both then 3/4 and 3/2 of the best) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
  * 128, 256, 512).  Each candidate runs `repeats` times (>= 1, after one
  * warm-up run) into `out`, a DEVICE buffer of at least
  * unifrac_output_bytes(ctx, precision, UNIFRAC_OUT_CONDENSED, 0, -1) bytes
@@ -395,15 +395,20 @@ enum unifrac_stat {
   UNIFRAC_STAT_SELECTED_UNWEIGHTED = 13, /* UNIFRAC_STAT_SELECTED_UPDATES of the last */
   UNIFRAC_STAT_SELECTED_WEIGHTED = 14,   /*   unweighted / weighted run (dense part)  */
   UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED = 15, /* device time of the sparse pair kernel of */
-  UNIFRAC_STAT_SPARSE_MS_WEIGHTED = 16,   /*   the last run of each variant (ms)     */
+  UNIFRAC_STAT_SPARSE_MS_WEIGHTED = 16,   /*   the last run of each variant (ms), the
+                                             per-branch lists excluded              */
   UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED = 17, /* pair updates it did (co-present      */
   UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED = 18,   /*   (pair, branch) of the sparse part) */
   UNIFRAC_STAT_CREATE_HOST_MS = 19,   /* unifrac_create: validation and host preparation (ms) */
   UNIFRAC_STAT_CREATE_DEVICE_MS = 20, /* unifrac_create: device set-up and uploads (ms) */
-  UNIFRAC_STAT_MAX_REACH = 21         /* most non-root branches one sample reaches: exact
+  UNIFRAC_STAT_MAX_REACH = 21,        /* most non-root branches one sample reaches: exact
                                          when the tree has >= 65,793 of them, else that
                                          count (an upper bound; the tensor-core path
                                          needs < 65,793) */
+  UNIFRAC_STAT_LIST_MS_UNWEIGHTED = 22, /* device time of the per-branch list pairs (the     */
+  UNIFRAC_STAT_LIST_MS_WEIGHTED = 23,   /*   very rarely present branches) of the last run  */
+  UNIFRAC_STAT_LIST_UPDATES_UNWEIGHTED = 24, /* co-present (pair, branch) updates they made */
+  UNIFRAC_STAT_LIST_UPDATES_WEIGHTED = 25
 };
 int unifrac_get_stat(const unifrac_ctx *ctx, int stat, double *value);
 

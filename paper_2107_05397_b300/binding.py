@@ -63,6 +63,10 @@ STAT_SPARSE_UPDATES_WEIGHTED = 18
 STAT_CREATE_HOST_MS = 19
 STAT_CREATE_DEVICE_MS = 20
 STAT_MAX_REACH = 21
+STAT_LIST_MS_UNWEIGHTED = 22
+STAT_LIST_MS_WEIGHTED = 23
+STAT_LIST_UPDATES_UNWEIGHTED = 24
+STAT_LIST_UPDATES_WEIGHTED = 25
 
 EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerror",
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",

@@ -173,9 +173,10 @@ void free_ctx(unifrac_ctx *ctx) {
   for (auto &pr : ctx->ev_pair)
     for (auto &e : pr)
       if (e) cudaEventDestroy(e);
-  for (auto &pr : ctx->ev_sp)
-    for (auto &e : pr)
-      if (e) cudaEventDestroy(e);
+  for (auto *set : {&ctx->ev_sp, &ctx->ev_list})
+    for (auto &pr : *set)
+      for (auto &e : pr)
+        if (e) cudaEventDestroy(e);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -709,11 +710,12 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       e = cudaEventCreate(&ev);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
     }
-  for (auto &pr : ctx->ev_sp)
-    for (auto &ev : pr) {
-      e = cudaEventCreate(&ev);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
-    }
+  for (auto *set : {&ctx->ev_sp, &ctx->ev_list})
+    for (auto &pr : *set)
+      for (auto &ev : pr) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event");
+      }
   ctx->create_device_ms = ms_since(t_create0) - ctx->create_host_ms;
   return UNIFRAC_OK;
 }
@@ -1126,6 +1128,10 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
     record_event(ctx, ctx->ev_pair[variant][0]);
     ctx->sel_unit = 64.0;
     record_event(ctx, ctx->ev_sp[0][0]);
+    if (!spart) {  // an empty list phase
+      record_event(ctx, ctx->ev_list[0][0]);
+      record_event(ctx, ctx->ev_list[0][1]);
+    }
     if (spart &&
         (rc = pairs_sparse_presence(ctx, static_cast<const uint32_t *>(V.rbits.p), P.kf_words,
                                     P.vr_words, static_cast<const uint8_t *>(V.blocks.p),
@@ -1799,11 +1805,11 @@ int unifrac_autotune(unifrac_ctx *ctx, int variant, int precision, void *out, si
   // incidences a lane walks alone (when the chosen split has a sparse part)
   if (!rc && th != 0)
     rc = tune(weighted ? UNIFRAC_OPT_SPARSE_LANE_PAIRS : UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS,
-              {32, 64, 128, 256}, false);
+              {32, 64, 128, 256}, true);
   // presence bound of the per-branch lists of the very rarely present positions
   if (!rc && th != 0)
     rc = tune(weighted ? UNIFRAC_OPT_RARE_LIST : UNIFRAC_OPT_UNWEIGHTED_RARE_LIST,
-              {0, 64, 256, 1024}, false);
+              {0, 64, 256, 1024}, true);
   // branches summed in registers before each FP32 running-total update
   if (!rc && weighted) rc = tune(UNIFRAC_OPT_WEIGHTED_FLUSH, {128, 256, 512}, false);
   ctx->opt_use_graph = saved_graph;
@@ -1880,26 +1886,45 @@ int unifrac_get_stat(const unifrac_ctx *ctx_c, int stat, double *value) {
     case UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED:
     case UNIFRAC_STAT_SPARSE_MS_WEIGHTED:
     case UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED:
-    case UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED: {
+    case UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED:
+    case UNIFRAC_STAT_LIST_MS_UNWEIGHTED:
+    case UNIFRAC_STAT_LIST_MS_WEIGHTED:
+    case UNIFRAC_STAT_LIST_UPDATES_UNWEIGHTED:
+    case UNIFRAC_STAT_LIST_UPDATES_WEIGHTED: {
       const int v = (stat == UNIFRAC_STAT_SPARSE_MS_UNWEIGHTED ||
-                     stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED) ? 0 : 1;
+                     stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED ||
+                     stat == UNIFRAC_STAT_LIST_MS_UNWEIGHTED ||
+                     stat == UNIFRAC_STAT_LIST_UPDATES_UNWEIGHTED) ? 0 : 1;
+      const bool list = stat >= UNIFRAC_STAT_LIST_MS_UNWEIGHTED;
       if (!ctx->ev_pair_valid[v]) return fail(ctx, UNIFRAC_E_INVALID_ARG, "no run of that variant");
       DeviceGuard g(ctx->device);
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
       if (stat == UNIFRAC_STAT_SPARSE_UPDATES_UNWEIGHTED ||
-          stat == UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED) {
+          stat == UNIFRAC_STAT_SPARSE_UPDATES_WEIGHTED ||
+          stat == UNIFRAC_STAT_LIST_UPDATES_UNWEIGHTED ||
+          stat == UNIFRAC_STAT_LIST_UPDATES_WEIGHTED) {
         unsigned long long c = 0;
-        e = cudaMemcpy(&c, ctx->d_counter + kCounterBase + 4 * v + 2, sizeof(c),
+        e = cudaMemcpy(&c, ctx->d_counter + kCounterBase + 4 * v + (list ? 3 : 2), sizeof(c),
                        cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "counter");
         *value = (double)c;
         return UNIFRAC_OK;
       }
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ctx->ev_sp[v][0], ctx->ev_sp[v][1]) != cudaSuccess) {
+      cudaEvent_t (&ev)[2] = list ? ctx->ev_list[v] : ctx->ev_sp[v];
+      if (cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
         cudaGetLastError();
-        ms = 0.f;  // no sparse phase in that run
+        ms = 0.f;  // no such phase in that run
+      }
+      // the sparse phase's window holds the list kernel: report the two apart
+      if (!list) {
+        float lm = 0.f;
+        if (cudaEventElapsedTime(&lm, ctx->ev_list[v][0], ctx->ev_list[v][1]) != cudaSuccess) {
+          cudaGetLastError();
+          lm = 0.f;
+        }
+        ms = std::max(0.f, ms - lm);
       }
       *value = ms;
       return UNIFRAC_OK;

@@ -924,6 +924,9 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
                       (f64 ? 0 : sizeof(float) * TILE * TILE);  // FP32 running totals
   cudaError_t e;
   if (f64) {
+    // no sparse or list phase in FP64: empty windows
+    for (cudaEvent_t ev : {ctx->ev_sp[1][0], ctx->ev_list[1][0], ctx->ev_list[1][1], ctx->ev_sp[1][1]})
+      record_event(ctx, ev);
     e = cudaFuncSetAttribute(k_pairs_weighted<double>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
@@ -959,10 +962,12 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
           cur_counters(ctx) + 2);
       ctx->stat_launches += 1;
     }
+    record_event(ctx, ctx->ev_list[1][0]);
     if (listed) {
       int rc = pairs_list(ctx, false, vr_words * WORD, voff, list, spart);
       if (rc) return rc;
     }
+    record_event(ctx, ctx->ev_list[1][1]);
     record_event(ctx, ctx->ev_sp[1][1]);
     e = cudaFuncSetAttribute(k_pairs_weighted<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -986,11 +991,24 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
                           const void *list, unsigned long long *spart, const WorkItem *items,
                           int32_t n_items) {
   const bool listed = list != nullptr && vr_words * WORD < ctx->K;
-  if (n_items <= 0 || (n_win <= 0 && !listed)) return UNIFRAC_OK;
+  if (n_items <= 0 || (n_win <= 0 && !listed)) {
+    record_event(ctx, ctx->ev_list[0][0]);  // an empty list phase
+    record_event(ctx, ctx->ev_list[0][1]);
+    return UNIFRAC_OK;
+  }
+  auto run_list = [&]() -> int {
+    record_event(ctx, ctx->ev_list[0][0]);
+    if (listed) {
+      int rc = pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
+      if (rc) return rc;
+    }
+    record_event(ctx, ctx->ev_list[0][1]);
+    return UNIFRAC_OK;
+  };
   if (n_win <= 0) {  // only listed positions: their sums start from zero
     cudaError_t e = cudaMemsetAsync(spart, 0, (size_t)n_items * TILE * TILE * 8, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "clear sparse sums");
-    return pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
+    return run_list();
   }
   const int32_t n_words = ctx->K_pad / WORD;
   constexpr size_t kSm = SparseCfg<true>::kSmem;
@@ -1007,8 +1025,7 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   ctx->stat_launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sparse unweighted kernel");
-  if (listed) return pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
-  return UNIFRAC_OK;
+  return run_list();
 }
 
 int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag, int32_t pv,
@@ -1041,11 +1058,11 @@ int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, const long long *vof
   if (presence)
     k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
         pv, ctx->K, voff, static_cast<const uint32_t *>(list), nullptr, ctx->d_qperm, item_of,
-        ctx->n_tiles, static_cast<unsigned long long *>(spart), cur_counters(ctx) + 2);
+        ctx->n_tiles, static_cast<unsigned long long *>(spart), cur_counters(ctx) + 3);
   else
     k_pairs_list<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
         pv, ctx->K, voff, nullptr, static_cast<const unsigned long long *>(list), nullptr, item_of,
-        ctx->n_tiles, static_cast<uint32_t *>(spart), cur_counters(ctx) + 2);
+        ctx->n_tiles, static_cast<uint32_t *>(spart), cur_counters(ctx) + 3);
   ctx->stat_launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch pairs");

@@ -133,6 +133,7 @@ struct unifrac_ctx {
   // pair-kernel events of the last run of each variant, and of its sparse kernel
   cudaEvent_t ev_pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t ev_sp[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t ev_list[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // per-branch list pairs
   bool ev_pair_valid[2] = {false, false};
 
   // ---- options

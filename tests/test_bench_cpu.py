@@ -56,6 +56,24 @@ def test_traffic_records_are_keyed_to_workload_samples_split_and_sources(tmp_pat
     assert bench.recorded_traffic("k_pairs_tc", "w", 4096, t96) is None
 
 
+def test_traffic_records_read_the_unit_column(tmp_path, monkeypatch):
+    """ncu prints large byte counts in Mbyte / Gbyte: the record is in bytes,
+    and launches of separate captures (each numbered from 0) stay apart."""
+    path = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(path))
+    csv1 = tmp_path / "g.csv"
+    with open(csv1, "w") as f:
+        f.write('"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n')
+        f.write('"0","ufb::k_pairs_tc(args)","dram__bytes_read.sum","Gbyte","2.5"\n')
+        f.write('"0","ufb::k_pairs_tc(args)","dram__bytes_write.sum","Mbyte","500"\n')
+        f.write('"0","void ufb::k_pairs_sparse<0>(args)","dram__bytes_read.sum","Kbyte","1"\n')
+        f.write('"0","void ufb::k_pairs_sparse<0>(args)","dram__bytes_write.sum","byte","24"\n')
+    t = {"sparse": 1, "uw_sparse": 2}
+    bench.record_traffic(str(csv1), "w", 100, "cap", t)
+    assert bench.recorded_traffic("k_pairs_tc", "w", 100, t) == 3.0e9
+    assert bench.recorded_traffic("k_pairs_sparse<false>", "w", 100, t) == 1024.0
+
+
 def test_kernel_hash_ignores_the_host_context_struct(tmp_path, monkeypatch):
     """The hash covers the kernel sources and the launch-planning functions,
     not the host-only context struct of the shared header."""

@@ -357,6 +357,22 @@ def test_rare_branch_lists_change_nothing(variant, small):
         outs.append(got)
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+    # the list phase's statistics: none listed at bound 0; with every position
+    # sparse and listed, the sparse kernel does nothing and the lists make
+    # exactly the co-present pairs sum_b C(n_b, 2)
+    lst, upd = ((ub.STAT_LIST_UPDATES_WEIGHTED, ub.STAT_SPARSE_UPDATES_WEIGHTED)
+                if variant == ub.WEIGHTED_NORMALIZED else
+                (ub.STAT_LIST_UPDATES_UNWEIGHTED, ub.STAT_SPARSE_UPDATES_UNWEIGHTED))
+    for bound in (0, 4096):
+        with ub.Context(w.tree, w.table) as ctx:
+            ctx.set_option(th_opt, 10**9)
+            ctx.set_option(list_opt, bound)
+            ctx.run(variant, ub.MIXED, ub.OUT_CONDENSED)
+            n_list, n_sparse = ctx.stat(lst), ctx.stat(upd)
+            if bound == 0:
+                assert n_list == 0 and n_sparse > 0
+            else:
+                assert n_sparse == 0 and n_list == ctx.stat(ub.STAT_USEFUL)
     # several studies (pairs only within a study) and a stripe range
     rng = np.random.default_rng(58)
     tree = synth.yule_tree(700, rng, 0.1)
