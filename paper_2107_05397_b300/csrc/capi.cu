@@ -154,7 +154,7 @@ void free_ctx(unifrac_ctx *ctx) {
   for (auto &V : ctx->vb) {
     ufb::DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
                             &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
-                            &V.vlist, &V.voff};
+                            &V.vlist, &V.voff,  &V.trec,    &V.tidx};
     for (auto *b : vbufs)
       if (b->p) cudaFree(b->p);
   }
@@ -896,9 +896,18 @@ static int plan_lists(unifrac_ctx *ctx, RunPlan &P, VarBufs &V, size_t entry_byt
   std::vector<long long> voff((size_t)(ctx->K - p_list) + 1, 0);
   for (int32_t k = p_list; k < ctx->K; ++k)
     voff[(size_t)(k - p_list) + 1] = voff[(size_t)(k - p_list)] + ctx->nb_perm[k];
+  if (voff.back() >= (1ll << 32)) {  // records hold 32-bit entry indices: no lists
+    P.vr_words = k_words;
+    return UNIFRAC_OK;
+  }
   int rc;
   const int64_t old_bytes = (int64_t)V.voff.bytes;
-  if ((rc = grow(ctx, V.vlist, std::max<size_t>((size_t)voff.back(), 1) * entry_bytes))) return rc;
+  const size_t n_ent = std::max<size_t>((size_t)voff.back(), 1);
+  V.list_entries = (unsigned long long)voff.back();
+  if ((rc = grow(ctx, V.vlist, n_ent * entry_bytes))) return rc;
+  if ((rc = grow(ctx, V.trec, n_ent * 8))) return rc;
+  // per tile: record offsets (u64, n_tiles + 1), counts and cursors (u32)
+  if ((rc = grow(ctx, V.tidx, ((size_t)ctx->n_tiles + 1) * 8 + (size_t)ctx->n_tiles * 8))) return rc;
   if ((rc = grow(ctx, V.voff, voff.size() * sizeof(long long)))) return rc;
   if (V.voff_pv != p_list || (int64_t)V.voff.bytes != old_bytes) {
     // on the context's stream, after earlier work that may read the old
@@ -985,7 +994,7 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
     const int32_t n_words = ctx->K_pad / WORD;
     P.kf_words = P.k_tc / WORD;
     P.vr_words = (ctx->K + WORD - 1) / WORD;
-    if (P.k_tc < ctx->K && (rc = plan_lists(ctx, P, V, 4))) return rc;
+    if (P.k_tc < ctx->K && (rc = plan_lists(ctx, P, V, 8))) return rc;
     const bool listed = P.vr_words * WORD < ctx->K;
     P.n_win = P.k_tc >= ctx->K ? 0 : (P.vr_words - P.kf_words + kWinWordsHost - 1) / kWinWordsHost;
     (void)n_words;
@@ -1025,6 +1034,18 @@ static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
     if ((rc = grow(ctx, V.persample, (size_t)ctx->n_cols * 8))) return rc;
   }
   return UNIFRAC_OK;
+}
+
+static ListBufs list_bufs(const unifrac_ctx *ctx, VarBufs &V) {
+  ListBufs L;
+  L.ents = static_cast<unsigned long long *>(V.vlist.p);
+  L.trec = static_cast<uint2 *>(V.trec.p);
+  char *ti = static_cast<char *>(V.tidx.p);
+  L.toff = reinterpret_cast<unsigned long long *>(ti);
+  L.tcnt = reinterpret_cast<uint32_t *>(ti + ((size_t)ctx->n_tiles + 1) * 8);
+  L.tcur = L.tcnt + ctx->n_tiles;
+  L.n_ent = V.list_entries;
+  return L;
 }
 
 // Device work of one variant after the embedding (no allocation, no host copy,
@@ -1075,8 +1096,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
                                   static_cast<uint8_t *>(V.blocks.p))))
         return rc;
       if (listed &&
-          (rc = list_fill(ctx, true, cnt, flag, P.vr_words * WORD,
-                          static_cast<const long long *>(V.voff.p), V.vlist.p)))
+          (rc = list_fill(ctx, true, cnt, flag, bits, rcb, P.vr_words * WORD,
+                          static_cast<const long long *>(V.voff.p), list_bufs(ctx, V))))
         return rc;
     }
     if (!overlapped) record_event(ctx, ctx->ev[1]);
@@ -1086,8 +1107,7 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
                              static_cast<const uint8_t *>(V.blocks.p),
                              static_cast<const unsigned long long *>(V.boff.p),
                              static_cast<const uint2 *>(V.cpre.p), P.n_win,
-                             static_cast<const long long *>(V.voff.p),
-                             listed ? V.vlist.p : nullptr,
+                             listed ? list_bufs(ctx, V) : ListBufs(),
                              sparse ? static_cast<uint32_t *>(V.spart.p) : nullptr,
                              P.sp_parts, S, d_items, n_items, o)))
       return rc;
@@ -1118,8 +1138,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
                                     static_cast<uint8_t *>(V.blocks.p))))
           return rc;
         if (listed &&
-            (rc = list_fill(ctx, false, cnt, flag, P.vr_words * WORD,
-                            static_cast<const long long *>(V.voff.p), V.vlist.p)))
+            (rc = list_fill(ctx, false, cnt, flag, rbits, rcb, P.vr_words * WORD,
+                            static_cast<const long long *>(V.voff.p), list_bufs(ctx, V))))
           return rc;
       }
       if ((rc = finish_tc_a(ctx, aq, a))) return rc;
@@ -1137,8 +1157,8 @@ static int enqueue_variant(unifrac_ctx *ctx, const RunPlan &P, bool overlapped) 
                                     P.vr_words, static_cast<const uint8_t *>(V.blocks.p),
                                     static_cast<const unsigned long long *>(V.boff.p),
                                     static_cast<const uint2 *>(V.cpre.p), P.n_win,
-                                    static_cast<const long long *>(V.voff.p),
-                                    listed ? V.vlist.p : nullptr, spart, d_items, n_items)))
+                                    listed ? list_bufs(ctx, V) : ListBufs(), spart, d_items,
+                                    n_items)))
       return rc;
     record_event(ctx, ctx->ev_sp[0][1]);
     if ((rc = pairs_tc(ctx, P.k_tc, X, D, kbits, aq, spart, d_items, n_items, o))) return rc;
@@ -1309,7 +1329,8 @@ static uint64_t prep_signature(const unifrac_ctx *ctx) {
   mix(ctx->tables);
   for (const ufb::VarBufs &V : ctx->vb)
     for (const ufb::DevBuf *b : {&V.vals, &V.vals2, &V.bits, &V.persample, &V.partial, &V.rc, &V.bsize,
-                                 &V.boff, &V.blocks, &V.cpre, &V.rbits, &V.vlist, &V.voff})
+                                 &V.boff, &V.blocks, &V.cpre, &V.rbits, &V.vlist, &V.voff,
+                                 &V.trec, &V.tidx})
       mix(*b);
   return h;
 }
@@ -1716,7 +1737,7 @@ static void release_variant_buffers(unifrac_ctx *ctx, int slot) {
   VarBufs &V = ctx->vb[slot];
   DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
                      &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
-                     &V.vlist, &V.voff};
+                     &V.vlist, &V.voff,  &V.trec,    &V.tidx};
   for (DevBuf *b : vbufs)
     if (b->p) {
       cudaFree(b->p);

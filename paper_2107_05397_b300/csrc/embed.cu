@@ -709,6 +709,14 @@ int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_
   return UNIFRAC_OK;
 }
 
+int scan_sizes(unifrac_ctx *ctx, int64_t n, const uint32_t *sizes, unsigned long long *offs) {
+  k_scan_sizes<<<1, 1024, 0, ctx->stream>>>(n, sizes, offs);
+  ctx->stat_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan");
+  return UNIFRAC_OK;
+}
+
 int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint32_t *bits,
                       const uint8_t *rc, int32_t kf_words, int32_t k_end, int32_t n_win,
                       uint32_t *bsize, unsigned long long *boff, uint2 *cpre, uint8_t *blocks) {

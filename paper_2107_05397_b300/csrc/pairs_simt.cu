@@ -660,17 +660,48 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 // Positions [pv, K) hold branches present in so few samples (at most the
 // UNIFRAC_OPT_RARE_LIST bound, all studies together) that walking their bitmap
 // words for every tile pair costs far more than their few co-present pairs.
-// They are taken branch by branch instead: k_list_fill writes, for position
-// k, one entry per sample where the branch is present (the global embedding
-// column; weighted: with V = round(v * 2^s), the same value the sparse blocks
-// carry), at offsets voff[k - pv] (host prefix sums of the presence counts);
-// k_pairs_list adds, for every pair of those samples, min(V_a, V_b)
-// (weighted) or q_k (unweighted) into the partial sums of the tile pair that
-// holds the pair (global atomics; item_of maps a (row tile, column tile) pair
-// to its work item, -1 when this run does not compute it).  The integer sums
+// They are taken branch by branch instead.  k_list_fill writes, for position
+// k, one entry per sample where the branch is present, ascending by column:
+// u64 (value << 32) | column, the value being V = round(v * 2^s) (weighted,
+// the value the sparse blocks carry) or the 24-bit length q_k (unweighted), at
+// offsets voff[k - pv] (host prefix sums of the presence counts).  Beside it,
+// a tile-major index: one record (entry, end of its branch's list) per entry,
+// grouped by the entry's column tile (offsets toff from the row counts rc of
+// the sparse packing, which cover these positions too).  k_pairs_list walks
+// the records in that order: for the entry p of a record, every later entry q
+// of its branch (a larger column) gives the pair (p, q), whose
+// min(V_p, V_q) (weighted) or q_k (unweighted) is added into the partial sums
+// of the tile pair (tile of p, tile of q) with a global atomic (item_of maps a
+// tile pair to its work item, -1 when this run does not compute it).  Records
+// are taken in order, so the atomics of the warps in flight land in the
+// partial sums of one or two row tiles, which stay in L2.  The integer sums
 // are those the sparse kernel would have made, so the result is unchanged.
 
 constexpr int kListWarps = 8;
+
+// Entries of the listed positions in each column tile: tcnt[t] = sum over
+// k in [pv, K) of rc[t][k] (the tile's non-zero columns of position k), taken
+// only where the tile's bitmap flags k: the packing writes rc nowhere else.
+__global__ void __launch_bounds__(256) k_list_tile_counts(int32_t pv, int32_t K, int32_t k_pad,
+                                                          const uint32_t *__restrict__ bits,
+                                                          int32_t n_words,
+                                                          const uint8_t *__restrict__ rc,
+                                                          uint32_t *__restrict__ tcnt) {
+  __shared__ uint32_t red[8];
+  const int64_t t = blockIdx.x;
+  uint32_t s = 0;
+  for (int32_t k = pv + threadIdx.x; k < K; k += blockDim.x)
+    if ((bits[t * n_words + k / WORD] >> (k % WORD)) & 1u) s += rc[t * k_pad + k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    tcnt[t] = tot;
+  }
+}
 
 template <bool VALUES>
 __global__ void __launch_bounds__(kListWarps * 32)
@@ -678,16 +709,21 @@ __global__ void __launch_bounds__(kListWarps * 32)
                 const uint8_t *__restrict__ flag, const uint4 *__restrict__ pmask, int32_t n_tiles,
                 const uint32_t *__restrict__ cnt, int64_t ldc, const double *__restrict__ len_perm,
                 const double *__restrict__ inv_total, float scale,
-                const long long *__restrict__ voff, uint32_t *__restrict__ cols,
-                unsigned long long *__restrict__ ents) {
+                const uint32_t *__restrict__ qlen, const long long *__restrict__ voff,
+                unsigned long long *__restrict__ ents, const unsigned long long *__restrict__ toff,
+                uint32_t *__restrict__ tcur, uint2 *__restrict__ trec, unsigned long long n_ent) {
   const int64_t k = pv + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= K) return;
   const int32_t b = perm[k];
   const long long base = voff[k - pv], cap = voff[k - pv + 1] - base;
-  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t end = (uint32_t)(base + cap);
   float L = 0.f;
-  if constexpr (VALUES) L = (float)len_perm[k];
+  uint32_t q = 0;
+  if constexpr (VALUES)
+    L = (float)len_perm[k];
+  else
+    q = qlen[k];
   long long n = 0;  // entries written so far (warp-uniform)
   for (int t0 = 0; t0 < n_tiles; t0 += 32) {
     const int t = t0 + lane;
@@ -710,73 +746,80 @@ __global__ void __launch_bounds__(kListWarps * 32)
       }
       const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
       before -= mine;
-      uint32_t q = 0;
+      // this (branch, tile) chunk's place among the tile's records
+      uint32_t slot = 0;
+      if (lane == 0 && total) slot = atomicAdd(&tcur[tt], total);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      const unsigned long long tbase = toff[tt];
+      const unsigned long long tend = toff[tt + 1];
+      uint32_t j = 0;
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
         if (!((wv[w] >> lane) & 1u)) continue;
-        const long long at = n + before + q++;
+        const uint32_t r = before + j++;
+        const long long at = n + r;
         if (at >= cap) continue;  // defensive: never past the branch's share
         const int64_t col = (int64_t)tt * TILE + 4 * lane + w;
+        uint32_t val;
         if constexpr (VALUES) {
           const float inv = (float)inv_total[col];
           const float v = L * ((float)cnt[(int64_t)b * ldc + col] * inv);
-          ents[base + at] = ((unsigned long long)__float2uint_rn(v * scale) << 32) |
-                            (unsigned long long)(uint32_t)col;
+          val = __float2uint_rn(v * scale);
         } else {
-          cols[base + at] = (uint32_t)col;
+          val = q;
         }
+        ents[base + at] = ((unsigned long long)val << 32) | (unsigned long long)(uint32_t)col;
+        const unsigned long long rp = tbase + slot + r;
+        if (rp < tend && rp < n_ent) trec[rp] = make_uint2((uint32_t)(base + at), end);
       }
       n += total;
-      (void)lt;
     }
   }
 }
 
+// Persistent: each warp takes 32 records at a time from the queue, in record
+// (column tile) order, and walks each record's later entries with its lanes.
 template <bool PRES>
 __global__ void __launch_bounds__(kListWarps * 32)
-    k_pairs_list(int32_t pv, int32_t K, const long long *__restrict__ voff,
-                 const uint32_t *__restrict__ cols, const unsigned long long *__restrict__ ents,
-                 const uint32_t *__restrict__ qlen, const int32_t *__restrict__ item_of,
-                 int32_t n_tiles, typename SparseCfg<PRES>::Acc *__restrict__ spart,
+    k_pairs_list(const unsigned long long *__restrict__ toff, int32_t n_tiles,
+                 const uint2 *__restrict__ trec, const unsigned long long *__restrict__ ents,
+                 unsigned long long n_ent, const int32_t *__restrict__ item_of,
+                 typename SparseCfg<PRES>::Acc *__restrict__ spart, unsigned int *__restrict__ queue,
                  unsigned long long *__restrict__ n_updates) {
-  const int64_t k = pv + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (k >= K) return;
-  const long long base = voff[k - pv];
-  const int m = (int)(voff[k - pv + 1] - base);
-  uint32_t q = 0;
-  if constexpr (PRES) q = qlen[k];
+  // defensive: never past the records written (one per entry)
+  const unsigned long long n_rec = min(toff[n_tiles], n_ent);
+  const uint32_t cols = (uint32_t)n_tiles * TILE;
   unsigned long long done = 0;
-  for (int i = 0; i < m - 1; ++i) {
-    uint32_t ci;
-    uint32_t vi = 0;
-    if constexpr (PRES) {
-      ci = __ldg(cols + base + i);
-    } else {
-      const unsigned long long e = __ldg(ents + base + i);
-      ci = (uint32_t)e;
-      vi = (uint32_t)(e >> 32);
-    }
-    for (int j = i + 1 + lane; j < m; j += 32) {
-      uint32_t cj;
-      uint32_t vj = 0;
-      if constexpr (PRES) {
-        cj = __ldg(cols + base + j);
-      } else {
-        const unsigned long long e = __ldg(ents + base + j);
-        cj = (uint32_t)e;
-        vj = (uint32_t)(e >> 32);
+  for (;;) {
+    unsigned long long r0 = 0;
+    if (lane == 0) r0 = 32ull * atomicAdd(queue, 1u);
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    if (r0 >= n_rec) break;
+    const uint32_t n_here = (uint32_t)min(32ull, n_rec - r0);
+    const uint2 mine = lane < (int)n_here ? trec[r0 + lane] : make_uint2(0u, 0u);
+    for (uint32_t x = 0; x < n_here; ++x) {
+      const uint32_t g = __shfl_sync(0xffffffffu, mine.x, x);
+      const uint32_t end = __shfl_sync(0xffffffffu, mine.y, x);
+      if (g >= end || end > n_ent) continue;  // defensive: a record must lie in the lists
+      const unsigned long long ep = __ldg(ents + g);
+      const uint32_t cp = (uint32_t)ep, vp = (uint32_t)(ep >> 32);
+      if (cp >= cols) continue;  // defensive: a column must exist
+      const int64_t row = (int64_t)(cp / TILE) * n_tiles;
+      const uint32_t a = (cp % TILE) * TILE;
+      for (uint32_t q = g + 1 + lane; q < end; q += 32) {
+        const unsigned long long eq = __ldg(ents + q);
+        const uint32_t cq = (uint32_t)eq;
+        if (cq >= cols) continue;
+        const int32_t item = item_of[row + cq / TILE];
+        if (item < 0) continue;
+        const int64_t at = (int64_t)item * TILE * TILE + a + cq % TILE;
+        if constexpr (PRES)
+          atomicAdd(&spart[at], (unsigned long long)vp);
+        else
+          atomicAdd(&spart[at], min(vp, (uint32_t)(eq >> 32)));
+        ++done;
       }
-      const uint32_t lo = min(ci, cj), hi = max(ci, cj);
-      if (hi >= (uint32_t)n_tiles * TILE) continue;  // defensive: a column must exist
-      const int32_t item = item_of[(int64_t)(lo / TILE) * n_tiles + hi / TILE];
-      if (item < 0) continue;
-      const int64_t at = (int64_t)item * TILE * TILE + (lo % TILE) * TILE + hi % TILE;
-      if constexpr (PRES)
-        atomicAdd(&spart[at], (unsigned long long)q);
-      else
-        atomicAdd(&spart[at], min(vi, vj));
-      ++done;
     }
   }
 #pragma unroll
@@ -915,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
                    int32_t kf_words, int32_t vr_words, const uint8_t *blocks,
                    const unsigned long long *boff, const uint2 *cpre, int32_t n_win,
-                   const long long *voff, const void *list, uint32_t *spart, int32_t sp_parts, const double *S,
+                   ListBufs list, uint32_t *spart, int32_t sp_parts, const double *S,
                    const WorkItem *items, int32_t n_items, const OutSpec &o) {
   if (n_items <= 0) return UNIFRAC_OK;
   const int32_t n_words = ctx->K_pad / WORD;
@@ -938,7 +981,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     // a sparse part exists when some positions are neither dense nor listed
     // (n_win > 0) or some are listed; the listed ones add into the sparse
     // kernel's partial sums (part 0), so those are written or cleared first
-    const bool listed = list != nullptr && vr_words * WORD < ctx->K;
+    const bool listed = list.ents != nullptr && vr_words * WORD < ctx->K;
     const bool sparse = n_win > 0 || listed;
     record_event(ctx, ctx->ev_sp[1][0]);
     if (sparse && n_win <= 0) {
@@ -964,7 +1007,7 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     }
     record_event(ctx, ctx->ev_list[1][0]);
     if (listed) {
-      int rc = pairs_list(ctx, false, vr_words * WORD, voff, list, spart);
+      int rc = pairs_list(ctx, false, vr_words * WORD, list, spart);
       if (rc) return rc;
     }
     record_event(ctx, ctx->ev_list[1][1]);
@@ -987,10 +1030,9 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
 
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
                           int32_t vr_words, const uint8_t *blocks, const unsigned long long *boff,
-                          const uint2 *cpre, int32_t n_win, const long long *voff,
-                          const void *list, unsigned long long *spart, const WorkItem *items,
-                          int32_t n_items) {
-  const bool listed = list != nullptr && vr_words * WORD < ctx->K;
+                          const uint2 *cpre, int32_t n_win, ListBufs list,
+                          unsigned long long *spart, const WorkItem *items, int32_t n_items) {
+  const bool listed = list.ents != nullptr && vr_words * WORD < ctx->K;
   if (n_items <= 0 || (n_win <= 0 && !listed)) {
     record_event(ctx, ctx->ev_list[0][0]);  // an empty list phase
     record_event(ctx, ctx->ev_list[0][1]);
@@ -999,7 +1041,7 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   auto run_list = [&]() -> int {
     record_event(ctx, ctx->ev_list[0][0]);
     if (listed) {
-      int rc = pairs_list(ctx, true, vr_words * WORD, voff, list, spart);
+      int rc = pairs_list(ctx, true, vr_words * WORD, list, spart);
       if (rc) return rc;
     }
     record_event(ctx, ctx->ev_list[0][1]);
@@ -1028,41 +1070,57 @@ int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_wor
   return run_list();
 }
 
-int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag, int32_t pv,
-              const long long *voff, void *list) {
+int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag,
+              const uint32_t *bits, const uint8_t *rc, int32_t pv, const long long *voff,
+              ListBufs L) {
   const int64_t n = (int64_t)ctx->K - pv;
-  if (n <= 0) return UNIFRAC_OK;
+  if (n <= 0 || ctx->n_tiles <= 0) return UNIFRAC_OK;
+  cudaStream_t st = ctx->stream;
+  // records per column tile (from the sparse packing's row counts), their
+  // offsets, and zeroed fill cursors
+  k_list_tile_counts<<<ctx->n_tiles, 256, 0, st>>>(pv, ctx->K, ctx->K_pad, bits,
+                                                   ctx->K_pad / WORD, rc, L.tcnt);
+  int rc_ = scan_sizes(ctx, ctx->n_tiles, L.tcnt, L.toff);
+  if (rc_) return rc_;
+  cudaError_t e = cudaMemsetAsync(L.tcur, 0, (size_t)ctx->n_tiles * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear list cursors");
   const unsigned grid = (unsigned)((n + kListWarps - 1) / kListWarps);
   if (values)
-    k_list_fill<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+    k_list_fill<true><<<grid, kListWarps * 32, 0, st>>>(
         pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
-        ctx->n_tiles, cnt, ctx->n_cols, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, voff,
-        nullptr, static_cast<unsigned long long *>(list));
+        ctx->n_tiles, cnt, ctx->n_cols, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, nullptr,
+        voff, L.ents, L.toff, L.tcur, L.trec, L.n_ent);
   else
-    k_list_fill<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
+    k_list_fill<false><<<grid, kListWarps * 32, 0, st>>>(
         pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
-        ctx->n_tiles, cnt, ctx->n_cols, nullptr, nullptr, 1.f, voff,
-        static_cast<uint32_t *>(list), nullptr);
-  ctx->stat_launches += 1;
-  cudaError_t e = cudaGetLastError();
+        ctx->n_tiles, cnt, ctx->n_cols, nullptr, nullptr, 1.f, ctx->d_qperm, voff, L.ents, L.toff,
+        L.tcur, L.trec, L.n_ent);
+  ctx->stat_launches += 2;
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch lists");
   return UNIFRAC_OK;
 }
 
-int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, const long long *voff,
-               const void *list, void *spart) {
+int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *spart) {
   const int64_t n = (int64_t)ctx->K - pv;
-  if (n <= 0) return UNIFRAC_OK;
-  const unsigned grid = (unsigned)((n + kListWarps - 1) / kListWarps);
+  if (n <= 0 || ctx->n_tiles <= 0) return UNIFRAC_OK;
   const int32_t *item_of = static_cast<const int32_t *>(ctx->item_of.p);
+  // the list queue: the slot's third 32-bit queue counter (cleared with the others)
+  unsigned int *queue = reinterpret_cast<unsigned int *>(ctx->d_counter + 4 * ctx->cur_slot + 2);
+  int per_sm = 0;
+  if (presence)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_list<true>, kListWarps * 32, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_list<false>, kListWarps * 32, 0);
+  const unsigned grid = (unsigned)(std::max(per_sm, 1) * ctx->sm_count);
   if (presence)
     k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
-        pv, ctx->K, voff, static_cast<const uint32_t *>(list), nullptr, ctx->d_qperm, item_of,
-        ctx->n_tiles, static_cast<unsigned long long *>(spart), cur_counters(ctx) + 3);
+        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of,
+        static_cast<unsigned long long *>(spart), queue, cur_counters(ctx) + 3);
   else
     k_pairs_list<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
-        pv, ctx->K, voff, nullptr, static_cast<const unsigned long long *>(list), nullptr, item_of,
-        ctx->n_tiles, static_cast<uint32_t *>(spart), cur_counters(ctx) + 3);
+        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of, static_cast<uint32_t *>(spart),
+        queue, cur_counters(ctx) + 3);
   ctx->stat_launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch pairs");

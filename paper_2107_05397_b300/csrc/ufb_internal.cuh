@@ -56,7 +56,9 @@ struct DevBuf {
 struct VarBufs {
   DevBuf vals, vals2, bits, persample, partial, rc, bsize, boff, blocks, cpre, spart, rbits;
   DevBuf vlist, voff;  // very rarely present positions: lists, offsets
+  DevBuf trec, tidx;   // their tile-major records; per-tile offsets, counts, cursors
   int32_t voff_pv = -1;  // first listed position the offsets in voff were made for
+  unsigned long long list_entries = 0;  // entries of the lists of the last plan
 };
 
 // Device counters: slot s (variant) owns the work queues 4 s + {0: dense /
@@ -264,21 +266,34 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
 // row non-zero counts and, when aq is given, aq[col] += q_k.
 int pack_rare(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, int32_t kf_words,
               uint32_t *bits, uint8_t *rc, unsigned long long *aq);
-// Unweighted sparse pairs (u64 per pair) of positions >= 32 * kf_words.
+// Exclusive scan of n u32 sizes into u64 offsets, offs[n] = total (one CTA).
+int scan_sizes(unifrac_ctx *ctx, int64_t n, const uint32_t *sizes, unsigned long long *offs);
+// Buffers of the per-branch lists (see list_fill below).
+struct ListBufs {
+  unsigned long long *ents = nullptr;  // entries, voff order
+  uint2 *trec = nullptr;               // tile-major records
+  unsigned long long *toff = nullptr;  // [n_tiles + 1] record offsets per tile
+  uint32_t *tcnt = nullptr;            // [n_tiles] records per tile
+  uint32_t *tcur = nullptr;            // [n_tiles] fill cursors
+  unsigned long long n_ent = 0;        // entries of all lists
+};
+// Unweighted sparse pairs (u64 per pair) of positions [32 kf_words,
+// 32 vr_words), then the listed ones.
 int pairs_sparse_presence(unifrac_ctx *ctx, const uint32_t *bits, int32_t kf_words,
                           int32_t vr_words, const uint8_t *blocks, const unsigned long long *boff,
-                          const uint2 *cpre, int32_t n_win, const long long *voff,
-                          const void *list, unsigned long long *spart, const WorkItem *items,
-                          int32_t n_items);
+                          const uint2 *cpre, int32_t n_win, ListBufs list,
+                          unsigned long long *spart, const WorkItem *items, int32_t n_items);
 // Very rarely present positions [pv, K), one list per position (voff: host
-// prefix sums of their presence counts): the columns where each is present
-// (values: with the fixed-point value of the sparse blocks, u64 (V << 32) |
-// column; else u32 columns), and the pairs of each list added into the
-// sparse partial sums of their tile pairs (ctx->item_of).
-int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag, int32_t pv,
-              const long long *voff, void *list);
-int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, const long long *voff,
-               const void *list, void *spart);
+// prefix sums of their presence counts): u64 (value << 32) | column for every
+// column where the position is present, value = the fixed-point value of the
+// sparse blocks (values) or the 24-bit length q_k; a tile-major record per
+// entry (entry index, end of its list) with per-tile offsets; the pairs of
+// each list added into the sparse partial sums of their tile pairs
+// (ctx->item_of), records taken in tile order.
+int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t *flag,
+              const uint32_t *bits, const uint8_t *rc, int32_t pv, const long long *voff,
+              ListBufs L);
+int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *spart);
 // Bit-packed presence bytes [K_pad/8][n_cols], per-group length tables
 // [K_pad/8][256] (FP64), group bitmaps and a_col = sum_k len_k p[k][col].
 int pack_lookup(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag,
@@ -300,7 +315,7 @@ constexpr int kMaxSparseParts = 8;
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals,
                    const uint32_t *bits, int32_t kf_words, int32_t vr_words,
                    const uint8_t *blocks, const unsigned long long *boff, const uint2 *cpre,
-                   int32_t n_win, const long long *voff, const void *list, uint32_t *spart,
+                   int32_t n_win, ListBufs list, uint32_t *spart,
                    int32_t sp_parts, const double *S, const WorkItem *items,
                    int32_t n_items, const OutSpec &o);
 int pairs_lookup(unifrac_ctx *ctx, const uint8_t *bytes, const double *tables,

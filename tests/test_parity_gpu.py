@@ -338,6 +338,28 @@ def test_sparse_lane_bound_changes_nothing(small):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_rare_branch_lists_ignore_dirty_device_memory(variant, small):
+    """The list index counts only flagged (tile, position) cells: with the
+    device memory the library's buffers come from first filled with 0xFF
+    bytes and freed, every list bound still gives the oracle's matrix."""
+    import torch
+    th_opt, list_opt = ((ub.OPT_SPARSE_THRESHOLD, ub.OPT_RARE_LIST)
+                        if variant == ub.WEIGHTED_NORMALIZED else
+                        (ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD, ub.OPT_UNWEIGHTED_RARE_LIST))
+    w, ref = small
+    N = w.table.n_samples
+    for bound in (12, 4096):
+        torch.cuda.empty_cache()
+        dirty = torch.full((1 << 28,), 255, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        del dirty
+        torch.cuda.empty_cache()
+        got = run(w.tree, w.table, variant, ub.MIXED,
+                  options={th_opt: 10**9, list_opt: bound}).reshape(N, N)
+        check_full(got, ref[variant], ub.MIXED)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_rare_branch_lists_change_nothing(variant, small):
     """Branches present in few samples summed from per-branch lists (every
     pair of their samples) instead of the sparse kernel's walk: the same exact
@@ -357,9 +379,18 @@ def test_rare_branch_lists_change_nothing(variant, small):
         outs.append(got)
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
-    # the list phase's statistics: none listed at bound 0; with every position
-    # sparse and listed, the sparse kernel does nothing and the lists make
-    # exactly the co-present pairs sum_b C(n_b, 2)
+    # the list phase's statistics: none listed at bound 0; with every sparse
+    # position listed, the sparse kernel does nothing and the lists make
+    # exactly the co-present pairs sum_b C(n_b, 2) of those positions -- all
+    # kept branches weighted; all but the 64 most present unweighted (the
+    # tensor cores always take one K-tile of 64 positions)
+    P = _presence(w.tree, w.table)
+    n = w.tree.n_nodes
+    nb = P[:n - 1].sum(axis=1)
+    nb = np.sort(nb[(nb > 0) & (w.tree.length[:n - 1] > 0)])[::-1].astype(np.float64)
+    if variant == ub.UNWEIGHTED:
+        nb = nb[64:]
+    want = float(np.sum(nb * (nb - 1) / 2))
     lst, upd = ((ub.STAT_LIST_UPDATES_WEIGHTED, ub.STAT_SPARSE_UPDATES_WEIGHTED)
                 if variant == ub.WEIGHTED_NORMALIZED else
                 (ub.STAT_LIST_UPDATES_UNWEIGHTED, ub.STAT_SPARSE_UPDATES_UNWEIGHTED))
@@ -372,7 +403,7 @@ def test_rare_branch_lists_change_nothing(variant, small):
             if bound == 0:
                 assert n_list == 0 and n_sparse > 0
             else:
-                assert n_sparse == 0 and n_list == ctx.stat(ub.STAT_USEFUL)
+                assert n_sparse == 0 and n_list == want
     # several studies (pairs only within a study) and a stripe range
     rng = np.random.default_rng(58)
     tree = synth.yule_tree(700, rng, 0.1)
