@@ -238,7 +238,15 @@ enum unifrac_option {
                                   holding one -- instead of by the sparse kernel's walk of
                                   each tile pair's bitmap words; 0 .. 4096, 0 off, default
                                   256; the sums are the same exact integers */
-  UNIFRAC_OPT_UNWEIGHTED_RARE_LIST = 12 /* the same for the unweighted sparse part */
+  UNIFRAC_OPT_UNWEIGHTED_RARE_LIST = 12, /* the same for the unweighted sparse part */
+  UNIFRAC_OPT_COPY_RANGES = 13 /* output in pinned host memory, one study's whole matrix
+                                  (layout FULL or CONDENSED, range (0, -1)): the weighted
+                                  variant's dense pair kernel runs as this many launches
+                                  over consecutive row blocks of the work list, and the
+                                  part of the matrix each one completes is copied to host
+                                  memory while the next computes; 1 .. 64, default 8;
+                                  1 copies the whole matrix after the last kernel.  The
+                                  results are the same for every value. */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);

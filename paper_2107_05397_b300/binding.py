@@ -40,6 +40,7 @@ OPT_UNWEIGHTED_SPARSE_LANE_PAIRS = 9
 OPT_PERSISTENT = 10
 OPT_RARE_LIST = 11
 OPT_UNWEIGHTED_RARE_LIST = 12
+OPT_COPY_RANGES = 13
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1

@@ -160,6 +160,8 @@ void free_ctx(unifrac_ctx *ctx) {
   }
   if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (cudaEvent_t ev : ctx->cc_ev)
+    if (ev) cudaEventDestroy(ev);
   for (int b = 0; b < 2; ++b) {
     if (ctx->ev_chunk_done[b]) cudaEventDestroy(ctx->ev_chunk_done[b]);
     if (ctx->ev_chunk_copied[b]) cudaEventDestroy(ctx->ev_chunk_copied[b]);
@@ -870,6 +872,7 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   }
   // pageable sources: the copies above are staged before returning
   ctx->n_items = (int32_t)items.size();
+  ctx->h_items = std::move(items);
   ctx->items_valid = true;
   ctx->items_layout = layout;
   ctx->items_s0 = s0;
@@ -1315,6 +1318,77 @@ static int graph_capture(unifrac_ctx *ctx, const RunPlan *plans, int n_plans, in
   return UNIFRAC_OK;
 }
 
+extern "C++" {
+namespace ufb {
+int enqueue_range_copy(unifrac_ctx *ctx, int c) {
+  cudaStream_t cs = ctx->copy_stream;
+  cudaError_t e = cudaEventRecord(ctx->cc_ev[(size_t)c], ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->cc_ev[(size_t)c], 0);
+  const int64_t n = ctx->cc_samples;
+  const int64_t r0 = std::min<int64_t>(n, (int64_t)ctx->cc_tiles[(size_t)c] * TILE);
+  const int64_t r1 = std::min<int64_t>(n, (int64_t)ctx->cc_tiles[(size_t)c + 1] * TILE);
+  const size_t el = ctx->cc_elem;
+  if (e == cudaSuccess && r1 > r0) {
+    if (ctx->cc_layout == UNIFRAC_OUT_FULL) {
+      // rows [r0, r1) from column r0 on, and their mirror: rows [r1, n) of
+      // columns [r0, r1); the columns before r0 came with earlier ranges
+      const size_t pitch = (size_t)n * el, at = ((size_t)r0 * n + r0) * el;
+      e = cudaMemcpy2DAsync(ctx->cc_host + at, pitch, ctx->cc_dev + at, pitch,
+                            (size_t)(n - r0) * el, (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess && n > r1) {
+        const size_t at2 = ((size_t)r1 * n + r0) * el;
+        e = cudaMemcpy2DAsync(ctx->cc_host + at2, pitch, ctx->cc_dev + at2, pitch,
+                              (size_t)(r1 - r0) * el, (size_t)(n - r1), cudaMemcpyDeviceToHost, cs);
+      }
+    } else {  // condensed: row i of the upper triangle starts at i n - i (i + 1) / 2
+      auto row_at = [n](int64_t i) { return (size_t)(i * n - i * (i + 1) / 2); };
+      const size_t a = row_at(r0), b = row_at(r1);
+      if (b > a)
+        e = cudaMemcpyAsync(ctx->cc_host + a * el, ctx->cc_dev + a * el, (b - a) * el,
+                            cudaMemcpyDeviceToHost, cs);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy a row range to host");
+  return UNIFRAC_OK;
+}
+}  // namespace ufb
+}  // extern "C++"
+
+// The item ranges of a chunked host copy.  A range may end before item x
+// when no item from x on has a smaller row tile than item x (then every tile
+// row above item x's is complete once the items before x are done); the
+// work list goes by block rows of tiles, so these cuts are the starts of its
+// block rows.  Of them, those nearest to equal shares of the items.
+static void plan_copy_ranges(unifrac_ctx *ctx, int ranges) {
+  ctx->cc_items.assign(1, 0);
+  ctx->cc_tiles.assign(1, 0);
+  const std::vector<WorkItem> &it = ctx->h_items;
+  const int64_t n = (int64_t)it.size();
+  std::vector<int32_t> suffix_min((size_t)n + 1, INT32_MAX);
+  for (int64_t x = n - 1; x >= 0; --x)
+    suffix_min[(size_t)x] = std::min(suffix_min[(size_t)x + 1], it[(size_t)x].tile_i);
+  std::vector<int32_t> cuts;  // valid cuts, ascending
+  for (int64_t x = 1; x < n; ++x)
+    if (it[(size_t)x].tile_i > it[(size_t)x - 1].tile_i && suffix_min[(size_t)x] == it[(size_t)x].tile_i)
+      cuts.push_back((int32_t)x);
+  const int32_t tile0 = ctx->study_col0[0] / TILE;
+  size_t v = 0;
+  for (int c = 1; c < ranges && v < cuts.size(); ++c) {
+    const int64_t target = (int64_t)c * n / ranges;
+    while (v + 1 < cuts.size() && cuts[v + 1] <= target) ++v;
+    // the nearer of the cuts around the target
+    size_t pick = v;
+    if (v + 1 < cuts.size() && cuts[v + 1] - target < target - cuts[v]) pick = v + 1;
+    const int32_t x = cuts[pick];
+    if (x <= ctx->cc_items.back()) continue;
+    ctx->cc_items.push_back(x);
+    ctx->cc_tiles.push_back(it[(size_t)x].tile_i - tile0);
+  }
+  ctx->cc_items.push_back((int32_t)n);
+  ctx->cc_tiles.push_back((int32_t)((ctx->cc_samples + TILE - 1) / TILE));
+  ctx->cc_n = (int)ctx->cc_items.size() - 1;
+}
+
 // Addresses and sizes of the buffers a run prepares before its pair kernels
 // (the embedding and every variant's packed operands): equal signatures mean
 // none of them was reallocated since.
@@ -1412,6 +1486,7 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
 
   const bool use_graph = ctx->opt_use_graph && device_out;
   size_t copied = 0;  // bytes of the result already on their way to host memory
+  bool ranged = false;  // the last variant's bytes go out range by range
   if (use_graph && graph_key_matches(ctx, P, variant)) {
     if ((rc = graph_launch(ctx))) return rc;
     ctx->stat_launches = ctx->graph_launches;
@@ -1430,10 +1505,36 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
       ctx->early_dev = dst;
       ctx->early_bytes = one;
     }
+    // into pinned host memory, one study's whole matrix: the weighted
+    // variant's dense kernel in ranges of rows, each range's rows copied out
+    // while the next computes
+    const RunPlan &last = plans[n_plans - 1];
+    ranged = !device_out && pinned_out && one > 0 && ctx->opt_copy_ranges > 1 && whole &&
+             ctx->n_studies == 1 && last.kind == RunPlan::WEIGHTED &&
+             (layout == UNIFRAC_OUT_FULL || layout == UNIFRAC_OUT_CONDENSED);
+    if (ranged) {
+      cudaError_t e = cudaSuccess;
+      if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+      ctx->cc_samples = ctx->n_samples;
+      plan_copy_ranges(ctx, ctx->opt_copy_ranges);
+      while (ctx->cc_ev.size() < (size_t)ctx->cc_n) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy range events");
+        ctx->cc_ev.push_back(ev);
+      }
+      ctx->cc_variant = last.variant;
+      ctx->cc_host = static_cast<char *>(out) + (size_t)(n_plans - 1) * one;
+      ctx->cc_dev = static_cast<const char *>(dst) + (size_t)(n_plans - 1) * one;
+      ctx->cc_elem = precision == UNIFRAC_FP64 ? sizeof(double) : sizeof(float);
+      ctx->cc_layout = layout;
+    }
     rc = enqueue_run(ctx, plans, n_plans);
     ctx->early_host = nullptr;
+    ctx->cc_variant = -1;
     if (rc) {
-      if (early) cudaStreamSynchronize(ctx->copy_stream);
+      if (early || ranged) cudaStreamSynchronize(ctx->copy_stream);
       return rc;
     }
     if (early) copied = one;
@@ -1452,11 +1553,15 @@ static int run_impl(unifrac_ctx *ctx, int variant, int precision, int32_t stripe
 
   cudaError_t e;
   if (!device_out && need > 0) {
-    e = cudaMemcpyAsync(static_cast<char *>(out) + copied, static_cast<const char *>(dst) + copied,
-                        need - copied, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
+    const size_t end = need - (ranged ? one : 0);  // the rest is on its way already
+    if (end > copied) {
+      e = cudaMemcpyAsync(static_cast<char *>(out) + copied,
+                          static_cast<const char *>(dst) + copied, end - copied,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "copy result to host");
+    }
     e = cudaStreamSynchronize(ctx->stream);
-    if (e == cudaSuccess && copied) e = cudaStreamSynchronize(ctx->copy_stream);
+    if (e == cudaSuccess && (copied || ranged)) e = cudaStreamSynchronize(ctx->copy_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
   }
   e = cudaGetLastError();
@@ -1520,6 +1625,10 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < -1) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_uw_sparse_threshold = value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_COPY_RANGES:
+      if (value < 1 || value > 64) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_copy_ranges = (int)value;
+      return UNIFRAC_OK;
     default:
       return UNIFRAC_E_INVALID_ARG;
   }
@@ -1541,6 +1650,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
     case UNIFRAC_OPT_UNWEIGHTED_SPARSE_THRESHOLD:
       *value = ctx->opt_uw_sparse_threshold;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_COPY_RANGES: *value = ctx->opt_copy_ranges; return UNIFRAC_OK;
     default: return UNIFRAC_E_INVALID_ARG;
   }
 }

@@ -173,8 +173,8 @@ struct MinAcc<double> {
 // added in the epilogue.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
-    k_pairs_weighted(const WorkItem *__restrict__ items, int32_t n_items,
-                     unsigned int *__restrict__ queue, const T *__restrict__ vals,
+    k_pairs_weighted(const WorkItem *__restrict__ items, int32_t n_items, int32_t item0,
+                     int32_t item1, unsigned int *__restrict__ queue, const T *__restrict__ vals,
                      int64_t ldv, const uint32_t *__restrict__ bits, int32_t n_words,
                      int32_t kf_words, const uint32_t *__restrict__ spart, int32_t sp_parts,
                      double sp_inv, const double *__restrict__ S,
@@ -191,14 +191,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4) ? 2 : 1)
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   unsigned long long nsel = 0;
 
-  // work items: the next tile pair from the device queue (persistent grid),
-  // or this CTA's own (one CTA per item)
+  // work items [item0, item1) (n_items in all: the stride of the sparse
+  // partial sums): the next tile pair from the device queue (persistent
+  // grid), or this CTA's own (one CTA per item)
   for (int iter = 0;; ++iter) {
   if (tid == 0)
-    s_item = queue ? (int32_t)atomicAdd(queue, 1u) : (iter == 0 ? (int32_t)blockIdx.x : n_items);
+    s_item = item0 + (queue ? (int32_t)atomicAdd(queue, 1u)
+                            : (iter == 0 ? (int32_t)blockIdx.x : item1 - item0));
   __syncthreads();
   const int32_t item = s_item;
-  if (item >= n_items) break;
+  if (item >= item1) break;
   const WorkItem it = items[item];
   const StudyDev sd = o.studies[it.study];
   const uint32_t *bI = bits + (int64_t)it.tile_i * n_words;
@@ -953,6 +955,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// The dense weighted kernel over all work items: one launch, or, when this
+// variant's matrix goes to host memory range by range (unifrac_ctx::cc_*),
+// one launch per range of items, each followed by the copy of what it
+// completed.  launch(a, b) enqueues the kernel over items [a, b).
+template <typename L>
+int dense_ranges(unifrac_ctx *ctx, int32_t n_items, L launch) {
+  const bool ranges = ctx->cc_variant == ctx->cur_slot && ctx->cc_n > 0 && !ctx->capturing &&
+                      ctx->cc_items.size() == (size_t)ctx->cc_n + 1 &&
+                      ctx->cc_items.back() == n_items;
+  const int n = ranges ? ctx->cc_n : 1;
+  for (int c = 0; c < n; ++c) {
+    const int32_t a = ranges ? ctx->cc_items[c] : 0, b = ranges ? ctx->cc_items[c + 1] : n_items;
+    if (b > a) {
+      const cudaError_t e = launch(a, b);
+      ctx->stat_launches += 1;
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel");
+    }
+    if (ranges) {
+      const int rc = enqueue_range_copy(ctx, c);
+      if (rc) return rc;
+    }
+  }
+  return UNIFRAC_OK;
+}
+
 }  // namespace
 
 int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t *bits,
@@ -973,10 +1000,12 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
     e = cudaFuncSetAttribute(k_pairs_weighted<double>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
-    k_pairs_weighted<double><<<n_items, kThreads, smem, ctx->stream>>>(
-        items, n_items, nullptr, static_cast<const double *>(vals), ctx->n_cols, bits, n_words,
-        n_words, nullptr, 1, 1.0, S, 0, o, cur_counters(ctx));
-    ctx->stat_launches += 1;
+    return dense_ranges(ctx, n_items, [&](int32_t a, int32_t b) {
+      k_pairs_weighted<double><<<b - a, kThreads, smem, ctx->stream>>>(
+          items, n_items, a, b, nullptr, static_cast<const double *>(vals), ctx->n_cols, bits,
+          n_words, n_words, nullptr, 1, 1.0, S, 0, o, cur_counters(ctx));
+      return cudaGetLastError();
+    });
   } else {
     // a sparse part exists when some positions are neither dense nor listed
     // (n_win > 0) or some are listed; the listed ones add into the sparse
@@ -1016,12 +1045,19 @@ int pairs_weighted(unifrac_ctx *ctx, bool f64, const void *vals, const uint32_t 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted kernel attribute");
     unsigned int *q = cur_queue(ctx, 0);
-    k_pairs_weighted<float><<<pair_grid(ctx, k_pairs_weighted<float>, kThreads, smem, n_items),
-                              kThreads, smem, ctx->stream>>>(
-        items, n_items, q, static_cast<const float *>(vals), ctx->n_cols, bits, n_words, kf_words,
-        sparse ? spart : nullptr, sp_parts, 1.0 / (double)ctx->sp_scale, S, ctx->opt_flush, o,
-        cur_counters(ctx));
-    ctx->stat_launches += 1;
+    return dense_ranges(ctx, n_items, [&](int32_t a, int32_t b) {
+      // each range's queue starts at 0 (the first was cleared with the others)
+      if (q && a > 0) {
+        const cudaError_t m = cudaMemsetAsync(q, 0, sizeof(unsigned int), ctx->stream);
+        if (m != cudaSuccess) return m;
+      }
+      k_pairs_weighted<float><<<pair_grid(ctx, k_pairs_weighted<float>, kThreads, smem, b - a),
+                                kThreads, smem, ctx->stream>>>(
+          items, n_items, a, b, q, static_cast<const float *>(vals), ctx->n_cols, bits, n_words,
+          kf_words, sparse ? spart : nullptr, sp_parts, 1.0 / (double)ctx->sp_scale, S,
+          ctx->opt_flush, o, cur_counters(ctx));
+      return cudaGetLastError();
+    });
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "weighted pair kernel");

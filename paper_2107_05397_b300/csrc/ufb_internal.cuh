@@ -145,6 +145,7 @@ struct unifrac_ctx {
   // branches present in at most this many samples (slot 0 unweighted, 1
   // weighted) are summed from per-branch lists instead of the sparse kernel
   int64_t opt_rare_list[2] = {256, 256};
+  int opt_copy_ranges = 8;  // launches of the weighted dense kernel into pinned host output
   // sparse kernels (slot 0 unweighted, 1 weighted): incidences of at most
   // this many pairs are walked by one lane
   int opt_lane_pairs[2] = {64, 128};
@@ -178,6 +179,22 @@ struct unifrac_ctx {
   const void *early_dev = nullptr;
   size_t early_bytes = 0;
   cudaEvent_t ev_first_done = nullptr;
+  // host output of one study's whole matrix (full or condensed): the weighted
+  // variant's pair kernel runs as cc_n launches over consecutive ranges of
+  // work items, [cc_items[c], cc_items[c+1]), each completing the rows of
+  // tile rows [cc_tiles[c], cc_tiles[c+1]); the parts of the matrix a range
+  // completes go to host memory on copy_stream while the next computes.
+  // cc_variant < 0: off.
+  int cc_variant = -1;
+  int cc_n = 0;
+  std::vector<int32_t> cc_items, cc_tiles;
+  std::vector<cudaEvent_t> cc_ev;
+  char *cc_host = nullptr;      // the variant's matrix in host memory
+  const char *cc_dev = nullptr;  // ... and on the device
+  size_t cc_elem = 4;
+  int cc_layout = 0;
+  int64_t cc_samples = 0;
+  std::vector<ufb::WorkItem> h_items;  // host copy of the work list (tile-row order per study)
   cudaEvent_t ev_chunk_done[2] = {nullptr, nullptr}, ev_chunk_copied[2] = {nullptr, nullptr};
   void *chunk_host[2] = {nullptr, nullptr};
   size_t chunk_host_bytes = 0;
@@ -229,6 +246,9 @@ inline int pair_grid(unifrac_ctx *ctx, K kernel, int threads, size_t smem, int64
 namespace ufb {
 
 int fail(unifrac_ctx *ctx, int code, const std::string &msg);
+// After launch range c of the chunked variant: the rows that range completed
+// are copied to host memory on the copy stream, ordered after the launch.
+int enqueue_range_copy(unifrac_ctx *ctx, int c);
 // Event record on the context's stream; while a CUDA graph is being captured
 // the record becomes a graph node (external event record), so replays
 // record the event too and it can be queried afterwards.

@@ -279,6 +279,45 @@ def test_large_workload_sampled_rows(large, variant, precision):
         assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
 
 
+@pytest.mark.parametrize("layout", [ub.OUT_FULL, ub.OUT_CONDENSED])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_host_copy_ranges_change_nothing(large, precision, layout):
+    """Into pinned host memory the weighted matrix leaves in row ranges, each
+    copied while the next computes (UNIFRAC_OPT_COPY_RANGES): 4,096 samples
+    (32 tiles, three block rows) give several ranges; every range count gives
+    the matrices of a device-memory run bit for bit, and sampled rows agree
+    with the oracle."""
+    import torch
+    w = large
+    N = w.table.n_samples
+    with ub.Context(w.tree, w.table) as ctx:
+        dev = ctx.run(ub.BOTH, precision, layout)
+        torch.cuda.synchronize()
+        dev = dev.cpu().numpy()
+        dt = torch.float64 if precision == ub.FP64 else torch.float32
+        for ranges in (1, 3, 8, 64):
+            ctx.set_option(ub.OPT_COPY_RANGES, ranges)
+            assert ctx.get_option(ub.OPT_COPY_RANGES) == ranges
+            host = torch.full((dev.size,), -1.0, dtype=dt, pin_memory=True).numpy()
+            ctx.run(ub.BOTH, precision, layout, out=host)
+            np.testing.assert_array_equal(host, dev)
+        with pytest.raises(ub.UniFracError):
+            ctx.set_option(ub.OPT_COPY_RANGES, 0)
+    half = dev.size // 2
+    rows = np.array([5, N // 2 + 3, N - 1])
+    for v, part in ((ub.UNWEIGHTED, dev[:half]), (ub.WEIGHTED_NORMALIZED, dev[half:])):
+        ref, _ = oracle.unifrac_rows(w.tree, w.table, v, rows)
+        for r, i in enumerate(rows):
+            if layout == ub.OUT_FULL:
+                vals = part.reshape(N, N)[i].astype(np.float64)
+            else:
+                j = np.arange(N)
+                a, b = np.minimum(i, j), np.maximum(i, j)
+                idx = a * N - a * (a + 1) // 2 + (b - a - 1)
+                vals = np.where(i == j, 0.0, part[np.where(i == j, 0, idx)]).astype(np.float64)
+            assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
+
+
 @pytest.mark.parametrize("threshold", [0, 1, 40, 10**9])
 @pytest.mark.parametrize("case", [0, 1])
 def test_weighted_dense_sparse_split(small, threshold, case):
@@ -578,12 +617,16 @@ def test_both_variants_in_one_run(small, precision, layout):
 @pytest.mark.parametrize("graph", [0, 1])
 def test_both_overlapped_equals_serial(small, graph):
     """UNIFRAC_BOTH with the variants on two streams is bit-identical to the
-    serial run (both variants with a sparse part, eager and graph replay)."""
+    serial run (both variants with a sparse-kernel part -- per-branch lists
+    off, or every sparse branch of these 256 samples would be listed -- eager
+    and graph replay)."""
     import torch
     w, _ = small
+    opts = {ub.OPT_SPARSE_THRESHOLD: 24, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 12,
+            ub.OPT_RARE_LIST: 0, ub.OPT_UNWEIGHTED_RARE_LIST: 0}
     with ub.Context(w.tree, w.table) as ctx:
-        ctx.set_option(ub.OPT_SPARSE_THRESHOLD, 24)
-        ctx.set_option(ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD, 12)
+        for k, v in opts.items():
+            ctx.set_option(k, v)
         ctx.set_option(ub.OPT_USE_GRAPH, graph)
         ctx.set_option(ub.OPT_OVERLAP_VARIANTS, 0)
         serial = ctx.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED).cpu().numpy()
@@ -604,8 +647,7 @@ def test_both_overlapped_equals_serial(small, graph):
     for kind in (True, "pinned"):
         for overlap in (0, 1):
             host = run(w.tree, w.table, ub.BOTH, ub.MIXED, ub.OUT_CONDENSED, host=kind,
-                       options={ub.OPT_SPARSE_THRESHOLD: 24, ub.OPT_UNWEIGHTED_SPARSE_THRESHOLD: 12,
-                                ub.OPT_OVERLAP_VARIANTS: overlap})
+                       options={**opts, ub.OPT_OVERLAP_VARIANTS: overlap})
             np.testing.assert_array_equal(host, serial.astype(np.float64))
 
 
