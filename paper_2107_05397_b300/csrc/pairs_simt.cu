@@ -680,6 +680,14 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 // are those the sparse kernel would have made, so the result is unchanged.
 
 constexpr int kListWarps = 8;
+// CTAs of the persistent list kernel per SM.  Its atomics land in the
+// partial sums of the tile pairs of the records in flight (32 per warp, in
+// column-tile order); with as many CTAs as fit (8 per SM) those records span
+// a dozen column tiles at 50,000 samples, whose partial sums (hundreds of MB)
+// overflow L2 and make the list kernels DRAM-bound; at 2 per SM they span
+// about three (measured on B300: 2x faster there, the same at 4,096 and
+// 25,000 samples).
+constexpr int kListBlocksPerSm = 2;
 
 // Entries of the listed positions in each column tile: tcnt[t] = sum over
 // k in [pv, K) of rc[t][k] (the tile's non-zero columns of position k), taken
@@ -1143,12 +1151,9 @@ int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *sp
   const int32_t *item_of = static_cast<const int32_t *>(ctx->item_of.p);
   // the list queue: the slot's third 32-bit queue counter (cleared with the others)
   unsigned int *queue = reinterpret_cast<unsigned int *>(ctx->d_counter + 4 * ctx->cur_slot + 2);
-  int per_sm = 0;
-  if (presence)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_list<true>, kListWarps * 32, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_list<false>, kListWarps * 32, 0);
-  const unsigned grid = (unsigned)(std::max(per_sm, 1) * ctx->sm_count);
+  // kListBlocksPerSm CTAs per SM: the records in flight (32 per warp) then
+  // span a few column tiles, whose partial sums stay in L2
+  const unsigned grid = (unsigned)(kListBlocksPerSm * ctx->sm_count);
   if (presence)
     k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
         L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of,
