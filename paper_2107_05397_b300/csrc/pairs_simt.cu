@@ -680,14 +680,17 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 // are those the sparse kernel would have made, so the result is unchanged.
 
 constexpr int kListWarps = 8;
-// CTAs of the persistent list kernel per SM.  Its atomics land in the
-// partial sums of the tile pairs of the records in flight (32 per warp, in
-// column-tile order); with as many CTAs as fit (8 per SM) those records span
-// a dozen column tiles at 50,000 samples, whose partial sums (hundreds of MB)
-// overflow L2 and make the list kernels DRAM-bound; at 2 per SM they span
-// about three (measured on B300: 2x faster there, the same at 4,096 and
-// 25,000 samples).
-constexpr int kListBlocksPerSm = 2;
+// CTAs of the persistent list kernel per SM, and records a warp takes at a
+// time.  Its atomics land in the partial sums of the tile pairs of the
+// records in flight (in column-tile order); with as many CTAs as fit (8 per
+// SM) and 32 records per warp those span a dozen column tiles at 50,000
+// samples, whose partial sums (hundreds of MB) overflow L2 and make the list
+// kernels DRAM-bound.  4 x 8 warps x 16 records per SM keep about three
+// column tiles in flight (measured on B300: 2x faster at 50,000 samples,
+// the same at 4,096 and 25,000), with warps enough to cover the loads'
+// latency.
+constexpr int kListBlocksPerSm = 4;
+constexpr uint32_t kListGrab = 16;
 
 // Entries of the listed positions in each column tile: tcnt[t] = sum over
 // k in [pv, K) of rc[t][k] (the tile's non-zero columns of position k), taken
@@ -736,15 +739,30 @@ __global__ void __launch_bounds__(kListWarps * 32)
     q = qlen[k];
   long long n = 0;  // entries written so far (warp-uniform)
   for (int t0 = 0; t0 < n_tiles; t0 += 32) {
+    // lane l: tile t0 + l -- its presence mask, its entries, and (one atomic
+    // per tile, all the chunk's at once) their place among the tile's records
     const int t = t0 + lane;
     const bool fl = t < n_tiles && flag[(int64_t)b * n_tiles + t];
+    uint4 my_pm = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t my_slot = 0;
+    unsigned long long my_tbase = 0, my_tend = 0;
+    if (fl) {
+      my_pm = pmask[(int64_t)b * n_tiles + t];
+      const uint32_t cnt_t = __popc(my_pm.x) + __popc(my_pm.y) + __popc(my_pm.z) + __popc(my_pm.w);
+      if (cnt_t) my_slot = atomicAdd(&tcur[t], cnt_t);
+      my_tbase = toff[t];
+      my_tend = toff[t + 1];
+    }
     uint32_t m = __ballot_sync(0xffffffffu, fl);
     while (m) {
-      const int tt = t0 + __ffs(m) - 1;
+      const int src = __ffs(m) - 1;
+      const int tt = t0 + src;
       m &= m - 1;
       // bit l of word w of the mask: column 4 l + w of the tile
-      const uint4 pm = pmask[(int64_t)b * n_tiles + tt];
-      const uint32_t wv[4] = {pm.x, pm.y, pm.z, pm.w};
+      const uint32_t wv[4] = {__shfl_sync(0xffffffffu, my_pm.x, src),
+                              __shfl_sync(0xffffffffu, my_pm.y, src),
+                              __shfl_sync(0xffffffffu, my_pm.z, src),
+                              __shfl_sync(0xffffffffu, my_pm.w, src)};
       uint32_t mine = 0;
 #pragma unroll
       for (int w = 0; w < 4; ++w) mine += (wv[w] >> lane) & 1u;
@@ -757,11 +775,9 @@ __global__ void __launch_bounds__(kListWarps * 32)
       const uint32_t total = __shfl_sync(0xffffffffu, before, 31);
       before -= mine;
       // this (branch, tile) chunk's place among the tile's records
-      uint32_t slot = 0;
-      if (lane == 0 && total) slot = atomicAdd(&tcur[tt], total);
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      const unsigned long long tbase = toff[tt];
-      const unsigned long long tend = toff[tt + 1];
+      const uint32_t slot = __shfl_sync(0xffffffffu, my_slot, src);
+      const unsigned long long tbase = __shfl_sync(0xffffffffu, my_tbase, src);
+      const unsigned long long tend = __shfl_sync(0xffffffffu, my_tend, src);
       uint32_t j = 0;
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
@@ -787,8 +803,9 @@ __global__ void __launch_bounds__(kListWarps * 32)
   }
 }
 
-// Persistent: each warp takes 32 records at a time from the queue, in record
-// (column tile) order, and walks each record's later entries with its lanes.
+// Persistent: each warp takes kListGrab records at a time from the queue, in
+// record (column tile) order, and walks each record's later entries with its
+// lanes.
 template <bool PRES>
 __global__ void __launch_bounds__(kListWarps * 32)
     k_pairs_list(const unsigned long long *__restrict__ toff, int32_t n_tiles,
@@ -803,10 +820,10 @@ __global__ void __launch_bounds__(kListWarps * 32)
   unsigned long long done = 0;
   for (;;) {
     unsigned long long r0 = 0;
-    if (lane == 0) r0 = 32ull * atomicAdd(queue, 1u);
+    if (lane == 0) r0 = (unsigned long long)kListGrab * atomicAdd(queue, 1u);
     r0 = __shfl_sync(0xffffffffu, r0, 0);
     if (r0 >= n_rec) break;
-    const uint32_t n_here = (uint32_t)min(32ull, n_rec - r0);
+    const uint32_t n_here = (uint32_t)min((unsigned long long)kListGrab, n_rec - r0);
     const uint2 mine = lane < (int)n_here ? trec[r0 + lane] : make_uint2(0u, 0u);
     for (uint32_t x = 0; x < n_here; ++x) {
       const uint32_t g = __shfl_sync(0xffffffffu, mine.x, x);
@@ -1151,8 +1168,8 @@ int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *sp
   const int32_t *item_of = static_cast<const int32_t *>(ctx->item_of.p);
   // the list queue: the slot's third 32-bit queue counter (cleared with the others)
   unsigned int *queue = reinterpret_cast<unsigned int *>(ctx->d_counter + 4 * ctx->cur_slot + 2);
-  // kListBlocksPerSm CTAs per SM: the records in flight (32 per warp) then
-  // span a few column tiles, whose partial sums stay in L2
+  // kListBlocksPerSm CTAs per SM: the records in flight (kListGrab per warp)
+  // then span a few column tiles, whose partial sums stay in L2
   const unsigned grid = (unsigned)(kListBlocksPerSm * ctx->sm_count);
   if (presence)
     k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
