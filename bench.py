@@ -876,9 +876,13 @@ def main():
                        "s_per_step": t_e2e,
                        "s_create_run_destroy": [round(float(x), 5) for x in med],
                        "create_ms_host_device": [round(float(x), 2) for x in cmed],
+                       "s_first_step": round(float(e2e_t[0]), 5),
                        "includes": f"create (validation, host prep, upload) + one run of both "
                                    f"variants into pinned host memory ({layout_name} layout, "
-                                   f"D2H inside) + destroy"}
+                                   f"D2H inside) + destroy; median of 3 steps, the later two "
+                                   f"taking the device blocks the step before freed from the "
+                                   f"library's block cache (s_first_step: the first, which "
+                                   f"allocates them)"}
 
         # streamed output: both matrices into host memory, computed in chunks
         # of stripes (only two chunks on the device), copies and merge
@@ -910,6 +914,9 @@ def main():
                                             "stripes computed chunk by chunk, D2H and host merge "
                                             "overlapped with the next chunk"}
         del res
+        # the freed contexts' blocks back to the driver before the framework
+        # allocations of the legs below
+        ub.unifrac_release_cached_memory(-1)
 
     # PCoA of the weighted matrix (full layout, FP32) on the device: the
     # ordination the distance matrix feeds

@@ -184,8 +184,9 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
 int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layout,
                          void *host_out, size_t out_bytes, int32_t chunk_stripes);
 
-/* Frees the context and its device buffers (synchronises its stream first).
- * NULL-safe. */
+/* Frees the context and its device buffers (synchronises the device first).
+ * Buffers of 64 MiB and more go to the library's cache of device blocks
+ * (unifrac_set_memory_cache) rather than back to the driver.  NULL-safe. */
 void unifrac_destroy(unifrac_ctx *ctx);
 
 /* Static message for a status code (never NULL).  The most recent failure of a
@@ -462,6 +463,35 @@ int unifrac_dense_noalloc(int variant, int32_t n_nodes, const int32_t *parent,
                           const double *length, int32_t n_samples,
                           const uint32_t *tip_counts, double *out,
                           void *cuda_stream);
+
+/*
+ * The library's cache of device blocks.  A context's work buffers at large
+ * sizes run to about 125 GB (50,000 samples on a 400,000-node tree); giving
+ * them back to the driver and taking them again costs tens of milliseconds
+ * per context.  Buffers of 64 MiB and more that a context frees (on
+ * unifrac_destroy, or when a run needs a larger one) are kept, per device,
+ * and a later context or run takes one of about the same size (at most 1/8
+ * larger) back.  A taken block holds whatever its last user left; the
+ * library never reads device memory it has not written.  When the driver
+ * cannot satisfy an allocation, the library releases the device's cache and
+ * tries once more.  Memory of other users of the device (for instance a
+ * framework's own allocator) is not covered by that retry: release the cache
+ * before large allocations of your own.
+ *
+ * unifrac_set_memory_cache -- most bytes the cache may hold on `device`
+ *   (-1 as `device`: the current device): max_bytes >= 0 (0 turns caching
+ *   off; blocks over the new cap are freed at once) or -1 for the default,
+ *   half the device's memory.  UNIFRAC_E_INVALID_ARG for max_bytes < -1 or a
+ *   device that cannot be selected.
+ * unifrac_release_cached_memory -- frees every cached block of `device`
+ *   (-1: of every device).  Contexts that exist keep their own buffers.
+ * unifrac_cached_memory -- bytes the cache holds on `device` (-1: current)
+ *   into *bytes.
+ * All three are thread-safe and leave the caller's current device as it was.
+ */
+int unifrac_set_memory_cache(int device, int64_t max_bytes);
+int unifrac_release_cached_memory(int device);
+int unifrac_cached_memory(int device, int64_t *bytes);
 
 #ifdef __cplusplus
 }

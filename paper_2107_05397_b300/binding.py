@@ -73,7 +73,8 @@ EXPORTED = ("unifrac_create", "unifrac_run", "unifrac_destroy", "unifrac_strerro
             "unifrac_last_error", "unifrac_n_stripes", "unifrac_output_bytes",
             "unifrac_set_option", "unifrac_get_option", "unifrac_get_stat",
             "unifrac_autotune", "unifrac_run_streamed", "unifrac_pcoa", "unifrac_mantel",
-            "unifrac_check_bounded_wait", "unifrac_measure_peak")
+            "unifrac_check_bounded_wait", "unifrac_measure_peak", "unifrac_set_memory_cache",
+            "unifrac_release_cached_memory", "unifrac_cached_memory")
 
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
@@ -137,6 +138,12 @@ def load() -> ctypes.CDLL:
         lib.unifrac_get_option.restype = ctypes.c_int
         lib.unifrac_get_stat.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.unifrac_get_stat.restype = ctypes.c_int
+        lib.unifrac_set_memory_cache.argtypes = [ctypes.c_int, i64]
+        lib.unifrac_set_memory_cache.restype = ctypes.c_int
+        lib.unifrac_release_cached_memory.argtypes = [ctypes.c_int]
+        lib.unifrac_release_cached_memory.restype = ctypes.c_int
+        lib.unifrac_cached_memory.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        lib.unifrac_cached_memory.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -318,6 +325,25 @@ def unifrac_measure_peak(pipe: int, stream=None) -> float:
     v = ctypes.c_double()
     _check(load().unifrac_measure_peak(int(pipe), ctypes.byref(v), _stream_handle(stream)))
     return float(v.value)
+
+
+def unifrac_set_memory_cache(max_bytes: int, device: int = -1) -> None:
+    """Most bytes the library's cache of device blocks may hold on a device
+    (-1: the current one); 0 turns it off, -1 restores the default (half the
+    device's memory)."""
+    _check(load().unifrac_set_memory_cache(int(device), int(max_bytes)))
+
+
+def unifrac_release_cached_memory(device: int = -1) -> None:
+    """Frees every block the cache holds on a device (-1: on every device)."""
+    _check(load().unifrac_release_cached_memory(int(device)))
+
+
+def unifrac_cached_memory(device: int = -1) -> int:
+    """Bytes the cache holds on a device (-1: the current one)."""
+    v = ctypes.c_int64()
+    _check(load().unifrac_cached_memory(int(device), ctypes.byref(v)))
+    return int(v.value)
 
 
 def unifrac_destroy(ctx) -> None:

@@ -43,14 +43,15 @@ int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (b.bytes >= bytes) return UNIFRAC_OK;
   if (b.p) {
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    // no work of this context (any of its streams) may still use the block
+    cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before reallocation");
-    cudaFree(b.p);
+    dev_free(b.p);
     ctx->device_bytes -= b.bytes;
     b.p = nullptr;
     b.bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = dev_alloc(&b.p, bytes);
   if (e != cudaSuccess) {
     b.p = nullptr;
     return cuda_fail(ctx, e, "device allocation");
@@ -82,7 +83,7 @@ struct DeviceGuard {
 template <typename T, typename A>
 int upload(unifrac_ctx *ctx, T **dst, const std::vector<T, A> &src) {
   size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  cudaError_t e = dev_alloc(reinterpret_cast<void **>(dst), bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (inputs)");
   ctx->device_bytes += bytes;
   if (!src.empty()) {
@@ -96,7 +97,7 @@ int upload(unifrac_ctx *ctx, T **dst, const std::vector<T, A> &src) {
 template <typename T>
 int upload_raw(unifrac_ctx *ctx, T **dst, const T *src, size_t count) {
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  cudaError_t e = dev_alloc(reinterpret_cast<void **>(dst), bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (inputs)");
   ctx->device_bytes += bytes;
   if (count) {
@@ -138,25 +139,26 @@ void run_threads(int T, F &&fn) {
 void free_ctx(unifrac_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
+  // every stream of the context idle before its blocks go back to the cache
+  cudaDeviceSynchronize();
   void *ptrs[] = {ctx->d_level_nodes, ctx->d_level_ptr, ctx->d_child_ptr, ctx->d_child_idx, ctx->d_frow_tip,
                   ctx->d_frow_ptr,    ctx->d_tchunk_row, ctx->d_tchunk_lo, ctx->d_pmask,
                   ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_S,           ctx->d_perm,
                   ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
                          &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1],
                          &ctx->item_of};
   for (auto *b : bufs)
-    if (b->p) cudaFree(b->p);
+    if (b->p) dev_free(b->p);
   for (auto &V : ctx->vb) {
     ufb::DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
                             &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
                             &V.vlist, &V.voff,  &V.trec,    &V.tidx};
     for (auto *b : vbufs)
-      if (b->p) cudaFree(b->p);
+      if (b->p) dev_free(b->p);
   }
   if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -538,7 +540,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
     if ((rc = upload(ctx, &ctx->d_tchunk_lo, tchunk_lo))) return rc;
     {
       const size_t pm_bytes = std::max<size_t>((size_t)ctx->n_nodes * ctx->n_tiles * 16, 16);
-      const cudaError_t em = cudaMalloc(reinterpret_cast<void **>(&ctx->d_pmask), pm_bytes);
+      const cudaError_t em = dev_alloc(reinterpret_cast<void **>(&ctx->d_pmask), pm_bytes);
       if (em != cudaSuccess) return cuda_fail(ctx, em, "device allocation (presence masks)");
       ctx->device_bytes += pm_bytes;
     }
@@ -554,7 +556,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
             ctx->d_fent_col, nnz, d_map);
         cudaError_t e2 = cudaGetLastError();
         if (e2 == cudaSuccess) e2 = cudaDeviceSynchronize();
-        cudaFree(d_map);
+        dev_free(d_map);
         ctx->device_bytes -= std::max<size_t>(ctx->col_of_sample.size() * 4, 16);
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "column map");
       }
@@ -1842,15 +1844,14 @@ int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layou
 // Frees the packing and pair-kernel work buffers of one variant slot (they
 // are allocated again, at the size the next run needs, on first use).
 static void release_variant_buffers(unifrac_ctx *ctx, int slot) {
-  cudaStreamSynchronize(ctx->stream);
-  if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
+  cudaDeviceSynchronize();
   VarBufs &V = ctx->vb[slot];
   DevBuf *vbufs[] = {&V.vals, &V.vals2, &V.bits,   &V.persample, &V.partial, &V.rc,
                      &V.bsize, &V.boff, &V.blocks, &V.cpre,      &V.spart,   &V.rbits,
                      &V.vlist, &V.voff,  &V.trec,    &V.tidx};
   for (DevBuf *b : vbufs)
     if (b->p) {
-      cudaFree(b->p);
+      dev_free(b->p);
       ctx->device_bytes -= b->bytes;
       b->p = nullptr;
       b->bytes = 0;

@@ -866,10 +866,10 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
   PresTemp tmp;
   unsigned long long *bits;
   int32_t *d_sw, *d_acc, *d_reach;
-  if (cudaMalloc(&tmp.p[0], (size_t)n_nodes * W * 8) != cudaSuccess ||
-      cudaMalloc(&tmp.p[1], sw.size() * 4) != cudaSuccess ||
-      cudaMalloc(&tmp.p[2], acc.size() * 4) != cudaSuccess ||
-      cudaMalloc(&tmp.p[3], (size_t)ctx->n_cols * 4) != cudaSuccess) {
+  if (dev_malloc_retry(&tmp.p[0], (size_t)n_nodes * W * 8) != cudaSuccess ||
+      dev_malloc_retry(&tmp.p[1], sw.size() * 4) != cudaSuccess ||
+      dev_malloc_retry(&tmp.p[2], acc.size() * 4) != cudaSuccess ||
+      dev_malloc_retry(&tmp.p[3], (size_t)ctx->n_cols * 4) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, UNIFRAC_E_OOM, "presence bitsets");
   }

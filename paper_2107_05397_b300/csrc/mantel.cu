@@ -307,7 +307,7 @@ struct Cuda {
   template <typename U>
   bool alloc(U **p, size_t count) {
     void *q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(U)) != cudaSuccess) return false;
+    if (dev_malloc_retry(&q, std::max<size_t>(count, 1) * sizeof(U)) != cudaSuccess) return false;
     ptrs.push_back(q);
     *p = static_cast<U *>(q);
     return true;

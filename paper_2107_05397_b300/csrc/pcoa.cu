@@ -491,17 +491,17 @@ extern "C" int unifrac_pcoa(const void *dist, int precision, int32_t n, int32_t 
   const size_t nm = (size_t)n * m;
   const XtzShape g_mm = xtz_shape(n, m, m, sms), g_m2 = xtz_shape(n, m, 2, sms);
   const size_t p_len = std::max((size_t)g_mm.blocks * m * m, (size_t)g_m2.blocks * m * 2);
-  if (cudaMalloc(&dv.Qt, (size_t)n * mp * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&dv.Yp, (size_t)kc * n * mp * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&dv.Q, nm * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.Y, nm * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.W, nm * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.U, (size_t)n * k * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.r, (size_t)n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.R2, 2 * (size_t)n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.st, 2 * (size_t)m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.G, (size_t)m * m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dv.P, p_len * sizeof(double)) != cudaSuccess) {
+  if (dev_malloc_retry((void **)&dv.Qt, (size_t)n * mp * sizeof(float)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.Yp, (size_t)kc * n * mp * sizeof(float)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.Q, nm * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.Y, nm * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.W, nm * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.U, (size_t)n * k * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.r, (size_t)n * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.R2, 2 * (size_t)n * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.st, 2 * (size_t)m * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.G, (size_t)m * m * sizeof(double)) != cudaSuccess ||
+      dev_malloc_retry((void **)&dv.P, p_len * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return UNIFRAC_E_OOM;
   }

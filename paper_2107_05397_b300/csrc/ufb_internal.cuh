@@ -246,6 +246,16 @@ inline int pair_grid(unifrac_ctx *ctx, K kernel, int threads, size_t smem, int64
 namespace ufb {
 
 int fail(unifrac_ctx *ctx, int code, const std::string &msg);
+// Device blocks of the contexts, through the process-wide cache of large
+// blocks (devcache.cu): dev_alloc takes a cached block of about the size or
+// allocates one (releasing the cache and retrying once when the device is
+// full); dev_free returns a block of dev_alloc -- only when no device work can
+// still use it -- to the cache, or frees it.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+// cudaMalloc for a call's own temporaries (freed with cudaFree), releasing the
+// cache and retrying once when the device is full.
+cudaError_t dev_malloc_retry(void **p, size_t bytes);
 // After launch range c of the chunked variant: the rows that range completed
 // are copied to host memory on the copy stream, ordered after the launch.
 int enqueue_range_copy(unifrac_ctx *ctx, int c);

@@ -17,3 +17,16 @@ def pytest_configure(config):
 def has_gpu():
     import torch
     return torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _release_device_block_cache():
+    """After each test module that used the library on a GPU, the library's
+    cache of device blocks goes back to the driver, so that later framework
+    allocations find the device as the library's contexts left it."""
+    yield
+    torch = sys.modules.get("torch")
+    ub = sys.modules.get("paper_2107_05397_b300.binding")
+    if torch is None or ub is None or not torch.cuda.is_available():
+        return
+    ub.unifrac_release_cached_memory(-1)

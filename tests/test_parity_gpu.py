@@ -279,6 +279,42 @@ def test_large_workload_sampled_rows(large, variant, precision):
         assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
 
 
+def test_device_block_cache_reuse_changes_nothing(large):
+    """Contexts take the work buffers earlier contexts freed (the library's
+    cache of device blocks, dirty) and give the same matrices bit for bit;
+    the blocks are reused, not piled up; a cap of 0 turns the cache off and
+    releasing it empties it."""
+    import torch
+    w = large
+    ub.unifrac_release_cached_memory(-1)
+    ub.unifrac_set_memory_cache(-1)
+    assert ub.unifrac_cached_memory() == 0
+
+    def one_run():
+        with ub.Context(w.tree, w.table) as ctx:
+            out = ctx.run(ub.BOTH, ub.MIXED, ub.OUT_CONDENSED)
+            torch.cuda.synchronize()
+            return out.cpu().numpy()
+
+    cold = one_run()
+    held = ub.unifrac_cached_memory()
+    assert held >= 64 << 20  # the counts array alone is about 1 GB here
+    for _ in range(2):
+        np.testing.assert_array_equal(one_run(), cold)
+        assert ub.unifrac_cached_memory() == held
+    ub.unifrac_set_memory_cache(0)
+    assert ub.unifrac_cached_memory() == 0
+    np.testing.assert_array_equal(one_run(), cold)
+    assert ub.unifrac_cached_memory() == 0
+    ub.unifrac_set_memory_cache(-1)
+    np.testing.assert_array_equal(one_run(), cold)
+    assert ub.unifrac_cached_memory() == held
+    ub.unifrac_release_cached_memory(-1)
+    assert ub.unifrac_cached_memory() == 0
+    with pytest.raises(ub.UniFracError):
+        ub.unifrac_set_memory_cache(-2)
+
+
 @pytest.mark.parametrize("layout", [ub.OUT_FULL, ub.OUT_CONDENSED])
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_host_copy_ranges_change_nothing(large, precision, layout):
