@@ -11,6 +11,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <future>
 #include <memory>
 #include <new>
 #include <numeric>
@@ -511,6 +512,42 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
       tchunk_lo.push_back(lo);
     }
   ctx->n_tchunks = (int64_t)tchunk_row.size();
+  // Per-column weighted sums S_col = sum_b v[b][col] through the tip-depth
+  // identity (every count below a branch is a tip count, and a tip's count
+  // appears once for every branch on its root path):
+  // S_i = (1 / C_i) * sum_f c_fi * depth(tip_f), FP64, entries in row order;
+  // fixed for the context, so computed once here -- on a background task
+  // while the device phase below runs (it reads only the table rows and the
+  // tip depths, which nothing changes meanwhile).
+  // (64 fixed chunks of rows, summed in chunk order: the same result
+  // whatever the number of host threads)
+  auto s_task = std::async(std::launch::async, [&]() {
+    std::vector<double> S(ctx->n_cols, 0.0);
+    const int32_t R = ctx->n_frows;
+    const int kChunks = R >= 4096 ? 64 : 1;
+    std::vector<std::vector<double>> part(kChunks);
+    std::atomic<int> next_chunk{0};
+    const int64_t n_ent = direct ? nnz : (int64_t)fent_col.size();
+    run_threads(std::min(kChunks, host_threads(n_ent)), [&](int) {
+      for (int c; (c = next_chunk.fetch_add(1)) < kChunks;) {
+        std::vector<double> &P = part[c];
+        P.assign(ctx->n_cols, 0.0);
+        for (int32_t r = (int32_t)((int64_t)R * c / kChunks);
+             r < (int32_t)((int64_t)R * (c + 1) / kChunks); ++r) {
+          const double dep = depth[frow_tip[r]];
+          for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e)
+            if (direct)
+              P[ctx->col_of_sample[indices[e]]] += (double)counts[e] * dep;
+            else
+              P[fent_col[e]] += (double)fent_cnt[e] * dep;
+        }
+      }
+    });
+    for (int c = 0; c < kChunks; ++c)
+      for (int32_t col = 0; col < ctx->n_cols; ++col) S[col] += part[c][col];
+    return S;
+  });
+
   // ------------------------------------------- presence counts and pruning
   // n_b: the samples with a non-zero count below branch b, per study, from
   // per-node sample bitsets built on the device (tips from their table rows,
@@ -648,38 +685,7 @@ static int create_impl(int32_t n_nodes, const int32_t *parent, const double *len
   std::vector<double> inv_total(ctx->n_cols, 0.0);
   for (int32_t i = 0; i < n_samples; ++i)
     if (total[i] > 0) inv_total[ctx->col_of_sample[i]] = 1.0 / (double)total[i];
-  // Per-column weighted sums S_col = sum_b v[b][col] through the tip-depth
-  // identity (every count below a branch is a tip count, and a tip's count
-  // appears once for every branch on its root path):
-  // S_i = (1 / C_i) * sum_f c_fi * depth(tip_f), FP64, entries in row order;
-  // fixed for the context, so computed once here.
-  // (64 fixed chunks of rows, summed in chunk order: the same result
-  // whatever the number of host threads)
-  std::vector<double> S(ctx->n_cols, 0.0);
-  {
-    const int32_t R = ctx->n_frows;
-    const int kChunks = R >= 4096 ? 64 : 1;
-    std::vector<std::vector<double>> part(kChunks);
-    std::atomic<int> next_chunk{0};
-    const int64_t n_ent = direct ? nnz : (int64_t)fent_col.size();
-    run_threads(std::min(kChunks, host_threads(n_ent)), [&](int) {
-      for (int c; (c = next_chunk.fetch_add(1)) < kChunks;) {
-        std::vector<double> &P = part[c];
-        P.assign(ctx->n_cols, 0.0);
-        for (int32_t r = (int32_t)((int64_t)R * c / kChunks);
-             r < (int32_t)((int64_t)R * (c + 1) / kChunks); ++r) {
-          const double dep = depth[frow_tip[r]];
-          for (int64_t e = frow_ptr[r]; e < frow_ptr[r + 1]; ++e)
-            if (direct)
-              P[ctx->col_of_sample[indices[e]]] += (double)counts[e] * dep;
-            else
-              P[fent_col[e]] += (double)fent_cnt[e] * dep;
-        }
-      }
-    });
-    for (int c = 0; c < kChunks; ++c)
-      for (int32_t col = 0; col < ctx->n_cols; ++col) S[col] += part[c][col];
-  }
+  std::vector<double> S = s_task.get();  // the sums of the task above, times 1 / C_i here
   for (int32_t c = 0; c < ctx->n_cols; ++c) S[c] *= inv_total[c];
   ctx->create_host_ms = ms_since(t_create0) - dev_ms;
 
