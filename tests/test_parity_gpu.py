@@ -279,6 +279,32 @@ def test_large_workload_sampled_rows(large, variant, precision):
         assert np.max(np.abs(vals - ref[r])) <= TOL[precision]
 
 
+@pytest.mark.parametrize("layout", [ub.OUT_FULL, ub.OUT_CONDENSED])
+def test_host_copy_ranges_ragged_matrix(layout):
+    """Row-range host copies of a matrix whose last tile is partial (1,700
+    samples: 14 tiles, two block rows of the work list): bit-identical to a
+    device-memory run for 1, 2, 5 and 64 ranges, equal to the oracle."""
+    import torch
+    rng = np.random.default_rng(1700)
+    tree, table = synth.random_case(rng, 200, 1700, density=0.04, general=True,
+                                    empty_samples=3)
+    N = table.n_samples
+    ref = {v: oracle.unifrac_full(tree, table, v) for v in VARIANTS}
+    with ub.Context(tree, table) as ctx:
+        dev = ctx.run(ub.BOTH, ub.MIXED, layout)
+        torch.cuda.synchronize()
+        dev = dev.cpu().numpy()
+        for ranges in (1, 2, 5, 64):
+            ctx.set_option(ub.OPT_COPY_RANGES, ranges)
+            host = torch.full((dev.size,), -1.0, dtype=torch.float32, pin_memory=True).numpy()
+            ctx.run(ub.BOTH, ub.MIXED, layout, out=host)
+            np.testing.assert_array_equal(host, dev)
+    half = dev.size // 2
+    for v, part in ((ub.UNWEIGHTED, dev[:half]), (ub.WEIGHTED_NORMALIZED, dev[half:])):
+        got = part.reshape(N, N) if layout == ub.OUT_FULL else condensed_to_full(part, N)
+        check_full(got.astype(np.float64), ref[v], ub.MIXED)
+
+
 def test_device_block_cache_reuse_changes_nothing(large):
     """Contexts take the work buffers earlier contexts freed (the library's
     cache of device blocks, dirty) and give the same matrices bit for bit;
