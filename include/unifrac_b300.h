@@ -245,7 +245,8 @@ enum unifrac_option {
                                   variant's dense pair kernel runs as this many launches
                                   over consecutive row blocks of the work list, and the
                                   part of the matrix each one completes is copied to host
-                                  memory while the next computes; 1 .. 64, default 8;
+                                  memory while the next computes; 1 .. 64, default 32
+                                  (at most one per block row of 12 tiles);
                                   1 copies the whole matrix after the last kernel.  The
                                   results are the same for every value. */
 };

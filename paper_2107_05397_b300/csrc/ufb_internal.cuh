@@ -145,7 +145,7 @@ struct unifrac_ctx {
   // branches present in at most this many samples (slot 0 unweighted, 1
   // weighted) are summed from per-branch lists instead of the sparse kernel
   int64_t opt_rare_list[2] = {256, 256};
-  int opt_copy_ranges = 8;  // launches of the weighted dense kernel into pinned host output
+  int opt_copy_ranges = 32;  // launches of the weighted dense kernel into pinned host output
   // sparse kernels (slot 0 unweighted, 1 weighted): incidences of at most
   // this many pairs are walked by one lane
   int opt_lane_pairs[2] = {64, 128};
