@@ -669,15 +669,17 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 // offsets voff[k - pv] (host prefix sums of the presence counts).  Beside it,
 // a tile-major index: one record (entry, end of its branch's list) per entry,
 // grouped by the entry's column tile (offsets toff from the row counts rc of
-// the sparse packing, which cover these positions too).  k_pairs_list walks
+// the sparse packing, which cover these positions too, taken where the tile's
+// bitmap flags the position).  k_pairs_list walks
 // the records in that order: for the entry p of a record, every later entry q
 // of its branch (a larger column) gives the pair (p, q), whose
 // min(V_p, V_q) (weighted) or q_k (unweighted) is added into the partial sums
 // of the tile pair (tile of p, tile of q) with a global atomic (item_of maps a
 // tile pair to its work item, -1 when this run does not compute it).  Records
-// are taken in order, so the atomics of the warps in flight land in the
-// partial sums of one or two row tiles, which stay in L2.  The integer sums
-// are those the sparse kernel would have made, so the result is unchanged.
+// are taken in order by a grid sized so that the records in flight span a few
+// column tiles (kListBlocksPerSm, kListGrab): the atomics then land in
+// partial sums that stay in L2.  The integer sums are those the sparse kernel
+// would have made, so the result is unchanged.
 
 constexpr int kListWarps = 8;
 // CTAs of the persistent list kernel per SM, and records a warp takes at a
