@@ -132,10 +132,24 @@ def planning_source() -> bytes:
     return "".join(out).encode()
 
 
+def code_only(text: str) -> str:
+    """C++ source without // comments and blank lines (so that edits of the
+    comments do not void a measurement)."""
+    out = []
+    for line in text.splitlines():
+        i = line.find("//")
+        if i >= 0 and line[:i].count('"') % 2 == 0:
+            line = line[:i]
+        line = line.rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
 def kernel_source_hash(kernel: str):
     """Hash of what a pair kernel's launches depend on: its source files (the
     shared header without the host-only context struct) and the
-    launch-planning functions."""
+    launch-planning functions, comments left out."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES.get(kernel, ("pairs_simt.cu", "pairs_tc.cu", "epilogue.cuh",
                                             "ufb_internal.cuh")):
@@ -144,8 +158,8 @@ def kernel_source_hash(kernel: str):
         if name == "ufb_internal.cuh" and "struct unifrac_ctx {" in text:
             i = text.index("struct unifrac_ctx {")
             text = text[:i] + text[text.index("\n};\n", i) + 4:]
-        h.update(text.encode())
-    h.update(planning_source())
+        h.update(code_only(text).encode())
+    h.update(code_only(planning_source().decode()).encode())
     return h.hexdigest()[:16]
 
 
