@@ -793,6 +793,7 @@ def main():
         "tuned_options": tuned, "graph_replay": not args.no_graph,
         "persistent_work_queue": not args.no_persistent,
         "useful_fraction": ctx.stat(ub.STAT_USEFUL) / max(pair_branch, 1.0),
+        "device_gb_held": round(ctx.stat(ub.STAT_DEVICE_BYTES) / 1e9, 2),
         "wall_s_timed_loop": t_wall,
         "device_error": dev_err,
     }

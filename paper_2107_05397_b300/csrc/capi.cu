@@ -146,7 +146,8 @@ void free_ctx(unifrac_ctx *ctx) {
                   ctx->d_frow_ptr,    ctx->d_tchunk_row, ctx->d_tchunk_lo, ctx->d_pmask,
                   ctx->d_fent_col,  ctx->d_fent_cnt,  ctx->d_inv_total,
                   ctx->d_S,           ctx->d_perm,
-                  ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm};
+                  ctx->d_len_perm,    ctx->d_digits,    ctx->d_counter,   ctx->d_qperm,
+                  ctx->d_slot};
   for (void *p : ptrs)
     if (p) dev_free(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
@@ -935,7 +936,9 @@ static int plan_lists(unifrac_ctx *ctx, RunPlan &P, VarBufs &V, size_t entry_byt
 static int plan_buffers(unifrac_ctx *ctx, RunPlan &P) {
   int rc;
   VarBufs &V = ctx->vb[P.variant];
-  if ((rc = grow(ctx, ctx->cnt, (size_t)ctx->n_nodes * ctx->n_cols * sizeof(uint32_t)))) return rc;
+  // counts only where a node has some in a column tile (the create-time slots)
+  if ((rc = grow(ctx, ctx->cnt, (size_t)std::max<int64_t>(ctx->n_slots, 1) * TILE * sizeof(uint32_t))))
+    return rc;
   if ((rc = grow(ctx, ctx->flag, (size_t)ctx->n_nodes * ctx->n_tiles))) return rc;
   if (P.kind == RunPlan::WEIGHTED) {
     const size_t elem = P.f64 ? 8 : 4;

@@ -44,15 +44,15 @@ __global__ void k_tip_zero(int64_t n_chunks, const int32_t *__restrict__ chunk_r
                            const int64_t *__restrict__ chunk_lo, int64_t chunk,
                            const int32_t *__restrict__ frow_tip,
                            const int64_t *__restrict__ frow_ptr,
-                           const int32_t *__restrict__ ent_col, uint32_t *cnt, uint8_t *flag,
-                           uint4 *pmask, int64_t ldc, int32_t n_tiles) {
+                           const int32_t *__restrict__ ent_col, uint32_t *cnt,
+                           const uint32_t *__restrict__ slot, uint8_t *flag, uint4 *pmask,
+                           int32_t n_tiles) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_chunks) return;
   const int32_t r = chunk_row[warp];
   const int64_t lo = chunk_lo[warp], rlo = frow_ptr[r], hi = min(frow_ptr[r + 1], lo + chunk);
   const int32_t tip = frow_tip[r];
-  uint32_t *row = cnt + (int64_t)tip * ldc;
   // the whole warp writes one tile (32 lanes x 16 bytes) per step, tiles
   // found by a ballot over 32 entries
   for (int64_t base = lo; base < hi; base += 32) {
@@ -65,7 +65,8 @@ __global__ void k_tip_zero(int64_t n_chunks, const int32_t *__restrict__ chunk_r
     }
     for (uint32_t m = __ballot_sync(0xffffffffu, first); m; m &= m - 1) {
       const int32_t ts = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
-      reinterpret_cast<uint4 *>(row + (int64_t)ts * TILE)[lane] = make_uint4(0u, 0u, 0u, 0u);
+      uint32_t *tr = count_tile(cnt, slot, tip, ts, n_tiles);
+      if (tr) reinterpret_cast<uint4 *>(tr)[lane] = make_uint4(0u, 0u, 0u, 0u);
       if (lane == 0) {
         flag[(int64_t)tip * n_tiles + ts] = 1;
         pmask[(int64_t)tip * n_tiles + ts] = make_uint4(0u, 0u, 0u, 0u);
@@ -80,20 +81,21 @@ __global__ void k_tip_scatter(int64_t n_chunks, const int32_t *__restrict__ chun
                               const int64_t *__restrict__ frow_ptr,
                               const int32_t *__restrict__ ent_col,
                               const uint32_t *__restrict__ ent_cnt, uint32_t *cnt,
-                              uint32_t *pmask_w, int64_t ldc, int32_t n_tiles) {
+                              const uint32_t *__restrict__ slot, uint32_t *pmask_w,
+                              int32_t n_tiles) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n_chunks) return;
   const int32_t r = chunk_row[warp];
   const int64_t lo = chunk_lo[warp], hi = min(frow_ptr[r + 1], lo + chunk);
   const int32_t tip = frow_tip[r];
-  uint32_t *row = cnt + (int64_t)tip * ldc;
   uint32_t *pm = pmask_w + (int64_t)tip * n_tiles * 4;
 #pragma unroll 4
   for (int64_t e = lo + lane; e < hi; e += 32) {
     const int32_t c = ent_col[e];
     const uint32_t v = ent_cnt[e];
-    row[c] = v;
+    uint32_t *tr = count_tile(cnt, slot, tip, c / TILE, n_tiles);
+    if (tr) tr[c % TILE] = v;
     // column 4 l + w of a tile is bit l of the tile's mask word w
     if (v) atomicOr(pm + (int64_t)(c / TILE) * 4 + (c & 3), 1u << ((c % TILE) >> 2));
   }
@@ -108,7 +110,8 @@ __global__ void k_tip_scatter(int64_t n_chunks, const int32_t *__restrict__ chun
 __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
                         const int32_t *__restrict__ child_ptr,
                         const int32_t *__restrict__ child_idx, uint32_t *cnt,
-                        uint8_t *flag, uint4 *pmask, int64_t ldc, int32_t n_tiles) {
+                        const uint32_t *__restrict__ slot, uint8_t *flag, uint4 *pmask,
+                        int32_t n_tiles) {
   const int32_t n_groups = (n_tiles + 31) / 32;
   const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -128,10 +131,11 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
     // two children (nearly every node of a binary tree): two flagged tiles
     // per pass, the four child rows' loads issued before either store
     const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
-    const uint4 *r0 = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc) + lane;
-    const uint4 *r1 = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc) + lane;
-    uint4 *rn = reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc) + lane;
-    constexpr int kQ = TILE / 4;  // uint4 per tile row
+    // a child's tile, or nullptr when it has no counts there
+    auto child = [&](int32_t ch, bool has, int32_t t) -> const uint4 * {
+      const uint32_t *p = has ? count_tile(cnt, slot, ch, t, n_tiles) : nullptr;
+      return p ? reinterpret_cast<const uint4 *>(p) + lane : nullptr;
+    };
     while (m) {
       const int sa = __ffs(m) - 1;
       m &= m - 1;
@@ -139,16 +143,23 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
       if (m) m &= m - 1;
       const uint32_t fa = __shfl_sync(0xffffffffu, fmask, sa);
       const uint32_t fb = __shfl_sync(0xffffffffu, fmask, sb < 0 ? sa : sb);
-      const int64_t oa = (int64_t)(gbase + sa) * kQ, ob = (int64_t)(gbase + (sb < 0 ? sa : sb)) * kQ;
+      const int32_t ta = gbase + sa, tb = gbase + (sb < 0 ? sa : sb);
       const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      const uint4 a0 = (fa & 1u) ? __ldg(r0 + oa) : z;
-      const uint4 a1 = (fa & 2u) ? __ldg(r1 + oa) : z;
-      const uint4 b0 = (sb >= 0 && (fb & 1u)) ? __ldg(r0 + ob) : z;
-      const uint4 b1 = (sb >= 0 && (fb & 2u)) ? __ldg(r1 + ob) : z;
+      const uint4 *pa0 = child(ch0, fa & 1u, ta), *pa1 = child(ch1, fa & 2u, ta);
+      const uint4 *pb0 = child(ch0, sb >= 0 && (fb & 1u), tb);
+      const uint4 *pb1 = child(ch1, sb >= 0 && (fb & 2u), tb);
+      const uint4 a0 = pa0 ? __ldg(pa0) : z;
+      const uint4 a1 = pa1 ? __ldg(pa1) : z;
+      const uint4 b0 = pb0 ? __ldg(pb0) : z;
+      const uint4 b1 = pb1 ? __ldg(pb1) : z;
       const uint4 sumA = make_uint4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
       const uint4 sumB = make_uint4(b0.x + b1.x, b0.y + b1.y, b0.z + b1.z, b0.w + b1.w);
-      rn[oa] = sumA;
-      if (sb >= 0) rn[ob] = sumB;
+      uint32_t *na = count_tile(cnt, slot, node, ta, n_tiles);
+      if (na) reinterpret_cast<uint4 *>(na)[lane] = sumA;
+      if (sb >= 0) {
+        uint32_t *nb = count_tile(cnt, slot, node, tb, n_tiles);
+        if (nb) reinterpret_cast<uint4 *>(nb)[lane] = sumB;
+      }
       const uint4 ma = nonzero_mask(sumA);
       if (lane == 0) pmask[(int64_t)node * n_tiles + gbase + sa] = ma;
       if (sb >= 0) {  // warp-uniform
@@ -165,15 +176,19 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
     uint4 s = make_uint4(0u, 0u, 0u, 0u);
     for (int32_t c = c0; c < c1; ++c) {
       const int32_t ch = child_idx[c];
-      if (few ? ((fm >> (c - c0)) & 1u) != 0u : flag[(int64_t)ch * n_tiles + ts] != 0) {
-        const uint4 v = reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + (int64_t)ts * TILE)[lane];
+      const uint32_t *ct = (few ? ((fm >> (c - c0)) & 1u) != 0u : flag[(int64_t)ch * n_tiles + ts] != 0)
+                               ? count_tile(cnt, slot, ch, ts, n_tiles)
+                               : nullptr;
+      if (ct) {
+        const uint4 v = reinterpret_cast<const uint4 *>(ct)[lane];
         s.x += v.x;
         s.y += v.y;
         s.z += v.z;
         s.w += v.w;
       }
     }
-    reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + (int64_t)ts * TILE)[lane] = s;
+    uint32_t *nt = count_tile(cnt, slot, node, ts, n_tiles);
+    if (nt) reinterpret_cast<uint4 *>(nt)[lane] = s;
     const uint4 ms = nonzero_mask(s);
     if (lane == 0) pmask[(int64_t)node * n_tiles + ts] = ms;
   }
@@ -184,8 +199,8 @@ __global__ void k_level(const int32_t *__restrict__ nodes, int32_t n_level,
 // the 32 columns 128 t + 32 q .. +31, and each warp takes four nodes of a
 // level at a time (eight lanes x 16 bytes per node); __syncthreads separates
 // the levels, since a level reads only what earlier levels wrote for the same
-// columns.  Global memory is read with plain (coherent) loads; a child row
-// whose flag is clear is read but not used (every row is allocated).  A node's
+// columns.  Global memory is read with plain (coherent) loads, and only the
+// tiles of children that have counts there.  A node's
 // flag is the same for the four quarters of its tile, so their stores agree;
 // each quarter writes its own byte of every word of the presence mask.
 constexpr int kTailThreads = 1024;
@@ -193,11 +208,12 @@ constexpr int kTailThreads = 1024;
 __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
     const int32_t *__restrict__ nodes, const int32_t *__restrict__ level_ptr, int32_t L0,
     int32_t L1, const int32_t *__restrict__ child_ptr, const int32_t *__restrict__ child_idx,
-    uint32_t *cnt, uint8_t *flag, uint8_t *pmask_b, int64_t ldc, int32_t n_tiles) {
+    uint32_t *cnt, const uint32_t *__restrict__ slot, uint8_t *flag, uint8_t *pmask_b,
+    int32_t n_tiles) {
   const int t = blockIdx.x >> 2, q = blockIdx.x & 3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, l8 = lane & 7;
-  const int64_t col = (int64_t)t * TILE + q * 32 + l8 * 4;
+  const int off = q * 32 + l8 * 4;  // this lane's 4 columns within the tile
   for (int L = L0; L < L1; ++L) {
     const int32_t lo = level_ptr[L], hi = level_ptr[L + 1];
     // warp-uniform trip count (the mask ballots need every lane)
@@ -215,22 +231,21 @@ __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
           // both children nearly always hold the tile), then selected
           const int32_t ch0 = child_idx[c0], ch1 = child_idx[c0 + 1];
           const uint8_t f0 = flag[(int64_t)ch0 * n_tiles + t], f1 = flag[(int64_t)ch1 * n_tiles + t];
-          const uint4 v0 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch0 * ldc + col);
-          const uint4 v1 = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch1 * ldc + col);
+          const uint32_t *p0 = f0 ? count_tile(cnt, slot, ch0, t, n_tiles) : nullptr;
+          const uint32_t *p1 = f1 ? count_tile(cnt, slot, ch1, t, n_tiles) : nullptr;
+          const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+          const uint4 v0 = p0 ? *reinterpret_cast<const uint4 *>(p0 + off) : z;
+          const uint4 v1 = p1 ? *reinterpret_cast<const uint4 *>(p1 + off) : z;
           any = (f0 | f1) != 0;
-          if (f0) s = v0;
-          if (f1) {
-            s.x += v1.x;
-            s.y += v1.y;
-            s.z += v1.z;
-            s.w += v1.w;
-          }
+          s = make_uint4(v0.x + v1.x, v0.y + v1.y, v0.z + v1.z, v0.w + v1.w);
         } else {
           for (int32_t c = c0; c < c1; ++c) {
             const int32_t ch = child_idx[c];
             if (flag[(int64_t)ch * n_tiles + t]) {
               any = true;
-              const uint4 v = *reinterpret_cast<const uint4 *>(cnt + (int64_t)ch * ldc + col);
+              const uint32_t *pc = count_tile(cnt, slot, ch, t, n_tiles);
+              if (!pc) continue;
+              const uint4 v = *reinterpret_cast<const uint4 *>(pc + off);
               s.x += v.x;
               s.y += v.y;
               s.z += v.z;
@@ -239,7 +254,10 @@ __global__ void __launch_bounds__(kTailThreads) k_levels_tail(
           }
         }
         if (l8 == 0) flag[(int64_t)node * n_tiles + t] = any ? 1 : 0;
-        if (any) *reinterpret_cast<uint4 *>(cnt + (int64_t)node * ldc + col) = s;
+        if (any) {
+          uint32_t *pn = count_tile(cnt, slot, node, t, n_tiles);
+          if (pn) *reinterpret_cast<uint4 *>(pn + off) = s;
+        }
       }
       // this quarter's bits of the tile's presence mask: bits 8 q .. 8 q + 7
       // of each word, i.e. byte q (lanes of group g are ballot bits 8 g ..)
@@ -270,7 +288,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_pack_weighted(
     int32_t K, int32_t k_end, const int32_t *__restrict__ perm,
     const double *__restrict__ len_perm, const uint32_t *__restrict__ cnt,
-    const uint8_t *__restrict__ flag, int64_t ldc, int32_t n_tiles,
+    const uint8_t *__restrict__ flag, const uint32_t *__restrict__ slot, int32_t n_tiles,
     const double *__restrict__ inv_total, T *__restrict__ vals, int64_t ldv,
     uint32_t *__restrict__ bits, int32_t n_words) {
   const int t = blockIdx.x;
@@ -305,7 +323,8 @@ __global__ void __launch_bounds__(256) k_pack_weighted(
       c[u] = make_uint4(0u, 0u, 0u, 0u);
       if (src[u] >= 0) {
         const int32_t bu = __shfl_sync(0xffffffffu, b, src[u]);
-        c[u] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)bu * ldc + col);
+        const uint32_t *pc = count_tile(cnt, slot, bu, t, n_tiles);
+        if (pc) c[u] = *reinterpret_cast<const uint4 *>(pc + lane * 4);
       }
     }
 #pragma unroll
@@ -496,7 +515,8 @@ template <bool VALUES>
 __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t K,
                             const uint32_t *__restrict__ bits, int32_t n_words,
                             const uint8_t *__restrict__ rc, int32_t k_pad,
-                            const uint32_t *__restrict__ cnt, int64_t ldc,
+                            const uint32_t *__restrict__ cnt,
+                            const uint32_t *__restrict__ slot,
                             const uint4 *__restrict__ pmask,
                             const int32_t *__restrict__ perm,
                             const double *__restrict__ len_perm,
@@ -574,10 +594,10 @@ __global__ void k_rare_fill(int32_t n_tiles, int32_t n_win, int32_t p0, int32_t 
     for (int g = 0; g < 8; ++g) {
       cv[g] = make_uint4(0u, 0u, 0u, 0u);
       if (src[g] >= 0) {
-        if constexpr (VALUES)
-          cv[g] = *reinterpret_cast<const uint4 *>(cnt + (int64_t)perm[kc + src[g]] * ldc +
-                                                   t * TILE + 4 * lane);
-        else
+        if constexpr (VALUES) {
+          const uint32_t *pc = count_tile(cnt, slot, perm[kc + src[g]], t, n_tiles);
+          if (pc) cv[g] = *reinterpret_cast<const uint4 *>(pc + 4 * lane);
+        } else
           cv[g] = pmask[(int64_t)perm[kc + src[g]] * n_tiles + t];
       }
     }
@@ -732,7 +752,7 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
                                              ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<true><<<grid_fill, 256, 0, st>>>(
-        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->d_slot,
         ctx->d_pmask, ctx->d_perm, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, boff, cpre,
         blocks,
         cur_bufs(ctx).blocks.bytes, cur_counters(ctx) + 1);
@@ -741,7 +761,7 @@ int build_rare_blocks(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const 
                                               ctx->K_pad, bsize, cpre);
     k_scan_sizes<<<1, 1024, 0, st>>>(items, bsize, boff);
     k_rare_fill<false><<<grid_fill, 256, 0, st>>>(
-        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->n_cols,
+        ctx->n_tiles, n_win, p0, k_end, bits, n_words, rc, ctx->K_pad, cnt, ctx->d_slot,
         ctx->d_pmask, ctx->d_perm, nullptr, nullptr, 1.f, boff, cpre, blocks,
         cur_bufs(ctx).blocks.bytes,
         cur_counters(ctx) + 1);
@@ -846,8 +866,46 @@ __global__ void k_pres_reach(const unsigned long long *__restrict__ bits, int32_
   if (r) atomicAdd(reach + c, r);
 }
 
+// Slot map of the compact counts: a (node, tile) has counts when its bitset
+// has a sample in the tile's two 64-bit words.  One warp per node, 32 tiles
+// at a time: k_slot_counts counts the node's tiles, and after a scan of those
+// counts (the node's first slot), k_slot_fill numbers them in tile order.
+__global__ void k_slot_counts(const unsigned long long *__restrict__ bits, int32_t W,
+                              int32_t n_nodes, int32_t n_tiles, uint32_t *__restrict__ n_of) {
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= n_nodes) return;
+  const unsigned long long *row = bits + v * W;
+  uint32_t c = 0;
+  for (int32_t t0 = 0; t0 < n_tiles; t0 += 32) {
+    const int32_t t = t0 + lane;
+    const bool has = t < n_tiles && (row[2 * t] | row[2 * t + 1]) != 0ull;
+    c += __popc(__ballot_sync(0xffffffffu, has));
+  }
+  if (lane == 0) n_of[v] = c;
+}
+
+__global__ void k_slot_fill(const unsigned long long *__restrict__ bits, int32_t W,
+                            int32_t n_nodes, int32_t n_tiles,
+                            const unsigned long long *__restrict__ first,
+                            uint32_t *__restrict__ slot) {
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= n_nodes) return;
+  const unsigned long long *row = bits + v * W;
+  unsigned long long next = first[v];
+  for (int32_t t0 = 0; t0 < n_tiles; t0 += 32) {
+    const int32_t t = t0 + lane;
+    const bool has = t < n_tiles && (row[2 * t] | row[2 * t + 1]) != 0ull;
+    const uint32_t m = __ballot_sync(0xffffffffu, has);
+    if (t < n_tiles)
+      slot[v * n_tiles + t] = has ? (uint32_t)(next + __popc(m & ((1u << lane) - 1u))) : kNoSlot;
+    next += __popc(m);
+  }
+}
+
 struct PresTemp {
-  void *p[4] = {nullptr, nullptr, nullptr, nullptr};
+  void *p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ~PresTemp() {
     for (void *q : p)
       if (q) cudaFree(q);
@@ -861,7 +919,18 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
   const int32_t n_nodes = ctx->n_nodes, root = n_nodes - 1, S = ctx->n_studies;
   const int32_t W = ctx->n_cols / 64;
   acc.assign((size_t)S * n_nodes, 0);
-  if (W == 0 || root == 0) return UNIFRAC_OK;
+  // the slot map of the compact counts, [n_nodes][n_tiles]
+  const int64_t cells = (int64_t)n_nodes * ctx->n_tiles;
+  if (cells >= (int64_t)kNoSlot)
+    return fail(ctx, UNIFRAC_E_UNSUPPORTED, "nodes x column tiles must stay below 2^32 - 1");
+  {
+    const cudaError_t ea = dev_alloc(reinterpret_cast<void **>(&ctx->d_slot),
+                                     (size_t)std::max<int64_t>(cells, 4) * 4);
+    if (ea != cudaSuccess) return cuda_fail(ctx, ea, "device allocation (count slots)");
+    ctx->device_bytes += (size_t)std::max<int64_t>(cells, 4) * 4;
+    ctx->n_slots = 0;
+  }
+  if (W == 0) return UNIFRAC_OK;
   cudaStream_t st = ctx->stream;
   PresTemp tmp;
   unsigned long long *bits;
@@ -869,7 +938,9 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
   if (dev_malloc_retry(&tmp.p[0], (size_t)n_nodes * W * 8) != cudaSuccess ||
       dev_malloc_retry(&tmp.p[1], sw.size() * 4) != cudaSuccess ||
       dev_malloc_retry(&tmp.p[2], acc.size() * 4) != cudaSuccess ||
-      dev_malloc_retry(&tmp.p[3], (size_t)ctx->n_cols * 4) != cudaSuccess) {
+      dev_malloc_retry(&tmp.p[3], (size_t)ctx->n_cols * 4) != cudaSuccess ||
+      dev_malloc_retry(&tmp.p[4], (size_t)n_nodes * 4) != cudaSuccess ||
+      dev_malloc_retry(&tmp.p[5], ((size_t)n_nodes + 1) * 8) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, UNIFRAC_E_OOM, "presence bitsets");
   }
@@ -897,10 +968,19 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
     k_pres_levels_tail<<<(unsigned)((W + 31) / 32), 1024, 0, st>>>(
         ctx->d_level_nodes, ctx->d_level_ptr, L0, ctx->n_levels, ctx->d_child_ptr,
         ctx->d_child_idx, bits, W);
-  k_pres_counts<<<(unsigned)(((int64_t)root * 32 + 255) / 256), 256, 0, st>>>(bits, W, root, S, d_sw,
-                                                                              d_acc, n_nodes);
+  {
+    uint32_t *n_of = static_cast<uint32_t *>(tmp.p[4]);
+    unsigned long long *first = static_cast<unsigned long long *>(tmp.p[5]);
+    const unsigned g = (unsigned)(((int64_t)n_nodes * 32 + 255) / 256);
+    k_slot_counts<<<g, 256, 0, st>>>(bits, W, n_nodes, ctx->n_tiles, n_of);
+    k_scan_sizes<<<1, 1024, 0, st>>>(n_nodes, n_of, first);
+    k_slot_fill<<<g, 256, 0, st>>>(bits, W, n_nodes, ctx->n_tiles, first, ctx->d_slot);
+  }
+  if (root > 0)
+    k_pres_counts<<<(unsigned)(((int64_t)root * 32 + 255) / 256), 256, 0, st>>>(
+        bits, W, root, S, d_sw, d_acc, n_nodes);
   std::vector<int32_t> reach;
-  if (count_reach) {
+  if (count_reach && root > 0) {
     reach.assign(ctx->n_cols, 0);
     e = cudaMemsetAsync(d_reach, 0, (size_t)ctx->n_cols * 4, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "presence reach");
@@ -911,18 +991,23 @@ int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count
   e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(acc.data(), d_acc, acc.size() * 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && count_reach)
+  if (e == cudaSuccess && count_reach && root > 0)
     e = cudaMemcpyAsync(reach.data(), d_reach, reach.size() * 4, cudaMemcpyDeviceToHost, st);
+  unsigned long long n_slots = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n_slots, static_cast<unsigned long long *>(tmp.p[5]) + n_nodes, 8,
+                        cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "presence kernels");
-  if (count_reach)
+  ctx->n_slots = (int64_t)n_slots;
+  if (count_reach && root > 0)
     for (int32_t c = 0; c < ctx->n_cols; ++c) *max_reach = std::max<int64_t>(*max_reach, reach[c]);
   return UNIFRAC_OK;
 }
 
 int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
   cudaStream_t st = ctx->stream;
-  const int64_t ldc = ctx->n_cols;
+  const uint32_t *slot = ctx->d_slot;
   cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)ctx->n_nodes * ctx->n_tiles, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset flags");
   ctx->stat_launches += 1;
@@ -930,14 +1015,14 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
     const int64_t blocks = (ctx->n_tchunks * 32 + 255) / 256;
     k_tip_zero<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
                                                  ctx->d_tchunk_lo, ctx->tip_chunk, ctx->d_frow_tip,
-                                                 ctx->d_frow_ptr, ctx->d_fent_col, cnt, flag,
-                                                 ctx->d_pmask, ldc, ctx->n_tiles);
+                                                 ctx->d_frow_ptr, ctx->d_fent_col, cnt, slot,
+                                                 flag, ctx->d_pmask, ctx->n_tiles);
     k_tip_scatter<<<(unsigned)blocks, 256, 0, st>>>(ctx->n_tchunks, ctx->d_tchunk_row,
                                                     ctx->d_tchunk_lo, ctx->tip_chunk,
                                                     ctx->d_frow_tip, ctx->d_frow_ptr,
-                                                    ctx->d_fent_col, ctx->d_fent_cnt, cnt,
+                                                    ctx->d_fent_col, ctx->d_fent_cnt, cnt, slot,
                                                     reinterpret_cast<uint32_t *>(ctx->d_pmask),
-                                                    ldc, ctx->n_tiles);
+                                                    ctx->n_tiles);
     ctx->stat_launches += 2;
   }
   // one launch per level while the levels are large, then the rest in one
@@ -951,14 +1036,14 @@ int embed_counts(unifrac_ctx *ctx, uint32_t *cnt, uint8_t *flag) {
     if (items == 0) continue;
     const int64_t blocks = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_level<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(
-        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, flag,
-        ctx->d_pmask, ldc, ctx->n_tiles);
+        ctx->d_level_nodes + lo, hi - lo, ctx->d_child_ptr, ctx->d_child_idx, cnt, slot, flag,
+        ctx->d_pmask, ctx->n_tiles);
     ctx->stat_launches += 1;
   }
   if (L0 < ctx->n_levels && ctx->n_tiles > 0) {
     k_levels_tail<<<(unsigned)ctx->n_tiles * 4, kTailThreads, 0, st>>>(
         ctx->d_level_nodes, ctx->d_level_ptr, L0, ctx->n_levels, ctx->d_child_ptr,
-        ctx->d_child_idx, cnt, flag, reinterpret_cast<uint8_t *>(ctx->d_pmask), ldc,
+        ctx->d_child_idx, cnt, slot, flag, reinterpret_cast<uint8_t *>(ctx->d_pmask),
         ctx->n_tiles);
     ctx->stat_launches += 1;
   }
@@ -976,11 +1061,11 @@ int pack_weighted(unifrac_ctx *ctx, const uint32_t *cnt, const uint8_t *flag, bo
     dim3 grid(ctx->n_tiles, (k_end + KR - 1) / KR);
     if (f64)
       k_pack_weighted<double><<<grid, 256, 0, st>>>(
-          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->d_slot, ctx->n_tiles,
           ctx->d_inv_total, static_cast<double *>(vals), ctx->n_cols, bits, n_words);
     else
       k_pack_weighted<float><<<grid, 256, 0, st>>>(
-          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->n_cols, ctx->n_tiles,
+          ctx->K, k_end, ctx->d_perm, ctx->d_len_perm, cnt, flag, ctx->d_slot, ctx->n_tiles,
           ctx->d_inv_total, static_cast<float *>(vals), ctx->n_cols, bits, n_words);
     ctx->stat_launches += 1;
   }

@@ -722,7 +722,8 @@ template <bool VALUES>
 __global__ void __launch_bounds__(kListWarps * 32)
     k_list_fill(int32_t pv, int32_t K, const int32_t *__restrict__ perm,
                 const uint8_t *__restrict__ flag, const uint4 *__restrict__ pmask, int32_t n_tiles,
-                const uint32_t *__restrict__ cnt, int64_t ldc, const double *__restrict__ len_perm,
+                const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ cslot,
+                const double *__restrict__ len_perm,
                 const double *__restrict__ inv_total, float scale,
                 const uint32_t *__restrict__ qlen, const long long *__restrict__ voff,
                 unsigned long long *__restrict__ ents, const unsigned long long *__restrict__ toff,
@@ -791,7 +792,8 @@ __global__ void __launch_bounds__(kListWarps * 32)
         uint32_t val;
         if constexpr (VALUES) {
           const float inv = (float)inv_total[col];
-          const float v = L * ((float)cnt[(int64_t)b * ldc + col] * inv);
+          const uint32_t *pc = count_tile(cnt, cslot, b, tt, n_tiles);
+          const float v = pc ? L * ((float)pc[col % TILE] * inv) : 0.f;
           val = __float2uint_rn(v * scale);
         } else {
           val = q;
@@ -1151,12 +1153,12 @@ int list_fill(unifrac_ctx *ctx, bool values, const uint32_t *cnt, const uint8_t 
   if (values)
     k_list_fill<true><<<grid, kListWarps * 32, 0, st>>>(
         pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
-        ctx->n_tiles, cnt, ctx->n_cols, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, nullptr,
+        ctx->n_tiles, cnt, ctx->d_slot, ctx->d_len_perm, ctx->d_inv_total, ctx->sp_scale, nullptr,
         voff, L.ents, L.toff, L.tcur, L.trec, L.n_ent);
   else
     k_list_fill<false><<<grid, kListWarps * 32, 0, st>>>(
         pv, ctx->K, ctx->d_perm, flag, reinterpret_cast<const uint4 *>(ctx->d_pmask),
-        ctx->n_tiles, cnt, ctx->n_cols, nullptr, nullptr, 1.f, ctx->d_qperm, voff, L.ents, L.toff,
+        ctx->n_tiles, cnt, ctx->d_slot, nullptr, nullptr, 1.f, ctx->d_qperm, voff, L.ents, L.toff,
         L.tcur, L.trec, L.n_ent);
   ctx->stat_launches += 2;
   e = cudaGetLastError();

@@ -20,6 +20,25 @@ constexpr int WORD = 32;
 // Positions per window of the weighted kernel's sparse phase (32 bitmap words).
 constexpr int kRareWin = 1024;
 
+// Counts of the embedding are held only for the (node, column tile) pairs
+// that have a non-zero count: slot[node * n_tiles + t] is the tile's row of
+// TILE u32 counts in the compact array, kNoSlot where the node has no count in
+// the tile (fixed at create from the table's presence; the embedding never
+// writes or reads there).  count_tile returns the tile's counts, or nullptr
+// for kNoSlot: every caller skips the tile then (or reads zeros), so a tile
+// without a slot is never addressed.
+constexpr uint32_t kNoSlot = 0xffffffffu;
+__device__ __forceinline__ uint32_t *count_tile(uint32_t *cnt, const uint32_t *slot,
+                                                int64_t node, int64_t t, int32_t n_tiles) {
+  const uint32_t s = slot[node * n_tiles + t];
+  return s == kNoSlot ? nullptr : cnt + (int64_t)s * TILE;
+}
+__device__ __forceinline__ const uint32_t *count_tile(const uint32_t *cnt, const uint32_t *slot,
+                                                      int64_t node, int64_t t, int32_t n_tiles) {
+  const uint32_t s = slot[node * n_tiles + t];
+  return s == kNoSlot ? nullptr : cnt + (int64_t)s * TILE;
+}
+
 // One 128 x 128 block of sample pairs, I-tile <= J-tile, both in one study.
 struct WorkItem {
   int32_t tile_i;  // global column tile of the rows
@@ -106,6 +125,10 @@ struct unifrac_ctx {
   // counts, valid where the tile is flagged: word w has bit l set when
   // column 4 l + w of the tile holds a non-zero count
   uint4 *d_pmask = nullptr;
+  // [n_nodes][n_tiles] slot of each (node, tile) in the compact counts array
+  // (kNoSlot: no count there), and the number of slots; set at create
+  uint32_t *d_slot = nullptr;
+  int64_t n_slots = 0;
   int32_t *d_fent_col = nullptr;      // [nnz'] embedding column (sorted per row)
   uint32_t *d_fent_cnt = nullptr;     // [nnz'] count (> 0)
   double *d_inv_total = nullptr;      // [n_cols] 1 / C_i (0 for empty or padding)
