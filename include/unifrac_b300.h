@@ -467,7 +467,8 @@ int unifrac_dense_noalloc(int variant, int32_t n_nodes, const int32_t *parent,
 
 /*
  * The library's cache of device blocks.  A context's work buffers at large
- * sizes run to about 125 GB (50,000 samples on a 400,000-node tree); giving
+ * sizes run to tens of GB (about 65 GB at 50,000 samples on a 400,000-node
+ * tree, with the full output staged for host memory); giving
  * them back to the driver and taking them again costs tens of milliseconds
  * per context.  Buffers of 64 MiB and more that a context frees (on
  * unifrac_destroy, or when a run needs a larger one) are kept, per device,

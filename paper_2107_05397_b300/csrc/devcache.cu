@@ -1,8 +1,9 @@
 // Process-wide cache of large device blocks.
 //
-// A context's work buffers at 50,000 samples are about 125 GB (the counts
-// array alone is 80 GB); freeing them takes tens of milliseconds and
-// allocating them again a few more, per context.  Blocks of at least
+// A context's work buffers at 50,000 samples are tens of GB (the 20 GB
+// output stage, 18 GB of counts, 15 GB of partial sums, ...); freeing them
+// takes tens of milliseconds and allocating them again a few more, per
+// context.  Blocks of at least
 // kMinCached bytes that a context frees are kept here instead, per device,
 // and a later allocation of about the same size takes one back.  The cache
 // holds at most a cap of bytes per device (default: half the device's

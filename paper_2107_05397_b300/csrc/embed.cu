@@ -9,11 +9,14 @@
 // The tree is in postorder, so a node's children are finished before it.  The
 // kernels here are level-synchronous: level 0 holds the tips, level L the nodes
 // whose highest child is on level L-1, and one launch sums the children of all
-// nodes of one level.  Data is branch-major (a row of n_cols u32 counts per
-// node), processed in 128-column tiles by one warp each (16-byte loads); a
-// (node, tile) flag records whether the tile has any non-zero count, and tiles
-// whose children are all zero are neither read nor written (the sparse-aware
-// step: most features are absent from most samples).  Counts are summed as
+// nodes of one level.  Counts are held per (node, 128-column tile) for the
+// tiles where the node has a non-zero count (the create-time slot map gives
+// each such tile its row of 128 u32 in a compact array; 22 % of the tiles at
+// 50,000 samples on a 400,000-node tree), processed by one warp per tile
+// (16-byte loads); a (node, tile) flag records whether the tile has any
+// non-zero count, and tiles whose children are all zero are neither read nor
+// written (the sparse-aware step: most features are absent from most
+// samples).  Counts are summed as
 // exact integers; the division by the sample total happens once, in packing.
 #include <algorithm>
 
