@@ -290,10 +290,12 @@ int cuda_fail(unifrac_ctx *ctx, cudaError_t e, const char *what);
 int grow(unifrac_ctx *ctx, DevBuf &b, size_t bytes);
 
 // embedding (K1) ------------------------------------------------------------
-// Fills cnt[node][col] (u32 counts below each branch) and flag[node][tile]
-// (1 if any column of the tile is non-zero) for every non-root node.
+// Fills the counts below each branch (u32, the 128 of a (node, column tile)
+// at its slot of the compact array, count_tile) and flag[node][tile] (1 if
+// any column of the tile is non-zero) for every node.
 // Per node and study, the samples with a non-zero count below the node
-// (acc[s * n_nodes + v], v < root), from device bitsets; with count_reach
+// (acc[s * n_nodes + v], v < root), from device bitsets, and from the same
+// bitsets the slot map of the compact counts (ctx->d_slot, n_slots); with count_reach
 // also the most nodes one column reaches (*max_reach).  Needs the tree, level
 // and table rows on the device; synchronises the context's stream.
 int presence_counts(unifrac_ctx *ctx, const std::vector<int32_t> &sw, bool count_reach,
