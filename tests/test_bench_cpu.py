@@ -103,3 +103,14 @@ def test_committed_traffic_has_every_pair_kernel(kernel):
     for r in mine:
         assert r[kernel]["bytes_per_launch"] > 0 and len(r[kernel]["source_hash"]) == 16
         assert set(r["thresholds"]) == {"sparse", "uw_sparse"}
+
+
+def test_traffic_hash_ignores_comments_only():
+    """Records are keyed to the kernels' code: comments and blank lines do
+    not change the key, code does (and a // inside a string is code)."""
+    import bench
+    base = 'int a = 1;  // one\n\n  const char *s = "x//y";\n// whole-line comment\n'
+    same = 'int a = 1;\n  const char *s = "x//y";  // other words\n'
+    assert bench.code_only(base) == bench.code_only(same)
+    assert bench.code_only(base) != bench.code_only(base.replace("a = 1", "a = 2"))
+    assert '"x//y"' in bench.code_only(base)
