@@ -138,7 +138,9 @@ def code_only(text: str) -> str:
     out = []
     for line in text.splitlines():
         i = line.find("//")
-        if i >= 0 and line[:i].count('"') % 2 == 0:
+        while i >= 0 and line[:i].count('"') % 2 == 1:  # inside a string literal
+            i = line.find("//", i + 2)
+        if i >= 0:
             line = line[:i]
         line = line.rstrip()
         if line:
