@@ -162,7 +162,8 @@ void free_ctx(unifrac_ctx *ctx) {
     for (auto *b : vbufs)
       if (b->p) dev_free(b->p);
   }
-  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+  for (cudaStream_t s : ctx->stream2)
+    if (s) cudaStreamDestroy(s);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (cudaEvent_t ev : ctx->cc_ev)
     if (ev) cudaEventDestroy(ev);
@@ -1210,8 +1211,7 @@ static int enqueue_early_copy(unifrac_ctx *ctx) {
 
 // The embedding once, then each variant's packing and pair kernels.
 // With two plans and UNIFRAC_OPT_OVERLAP_VARIANTS, the first plan runs on a
-// high-priority second stream forked after the embedding and joined at the
-// end, the second on the context's stream (both are captured into the same
+// second stream forked after the embedding and joined at the end, the second on the context's stream (both are captured into the same
 // graph); the variants have separate buffers and counters, and share only the
 // read-only embedding and the output buffer, which they write in disjoint
 // halves.
@@ -1231,29 +1231,36 @@ static int enqueue_run(unifrac_ctx *ctx, const RunPlan *plans, int n_plans) {
     return UNIFRAC_OK;
   }
   cudaError_t e = cudaSuccess;
-  if (!ctx->stream2) {
-    // the first plan (the unweighted variant of UNIFRAC_BOTH, the shorter)
-    // runs here at the highest priority, so that it finishes first and its
-    // result can be copied out while the second still computes
+  // The first plan (the unweighted variant of UNIFRAC_BOTH, the shorter) runs
+  // on the second stream.  When its result is copied to host memory while the
+  // second plan computes, that stream has the highest priority, so that the
+  // first plan finishes early and the copy hides behind the second.  Otherwise
+  // both streams have the same priority: the hardware then fills each
+  // variant's idle tails with the other's blocks, which a priority order
+  // prevents (about 20 ms of 820 on the 50,000-sample matrix).
+  const int pri = ctx->early_host ? 1 : 0;
+  if (!ctx->stream2[pri]) {
     int lo_pri = 0, hi_pri = 0;
     e = cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
     if (e == cudaSuccess)
-      e = cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi_pri);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "second stream");
+      e = cudaStreamCreateWithPriority(&ctx->stream2[pri], cudaStreamNonBlocking,
+                                       pri ? hi_pri : lo_pri);
   }
+  if (e == cudaSuccess && !ctx->ev_fork2) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->ev_join2) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "second stream");
+  cudaStream_t s2 = ctx->stream2[pri];
   record_event(ctx, ctx->ev[1]);  // the embedding alone
   e = cudaEventRecord(ctx->ev_fork2, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork2, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ctx->ev_fork2, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fork");
   cudaStream_t main_stream = ctx->stream;
-  ctx->stream = ctx->stream2;
+  ctx->stream = s2;
   rc = enqueue_variant(ctx, plans[0], true);
   if (!rc) rc = enqueue_early_copy(ctx);
   ctx->stream = main_stream;
   if (!rc) rc = enqueue_variant(ctx, plans[1], true);
-  e = cudaEventRecord(ctx->ev_join2, ctx->stream2);
+  e = cudaEventRecord(ctx->ev_join2, s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
   if (rc) return rc;

@@ -188,8 +188,9 @@ struct unifrac_ctx {
   // ---- CUDA graph of the last run (UNIFRAC_OPT_USE_GRAPH)
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // second stream of an overlapped two-variant run, and its fork / join
-  cudaStream_t stream2 = nullptr;
+  // second stream of an overlapped two-variant run ([0] normal priority,
+  // [1] the device's highest), and its fork / join
+  cudaStream_t stream2[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   int cur_slot = 0;                   // variant slot being enqueued
   // unifrac_run_streamed: copy stream, its events, and the chunk buffers
