@@ -68,7 +68,7 @@ def parse():
                          "work queue")
     ap.add_argument("--streamed-chunk", type=int, default=0,
                     help="stripes per chunk of the streamed-output measurement (0: the "
-                         "faster of 1,024 and 4,096)")
+                         "fastest of 2,048, 4,096 and 8,192)")
     ap.add_argument("--mantel-perms", type=int, default=999,
                     help="permutations of the Mantel-test measurement (0 = skip it)")
     ap.add_argument("--mantel-only", action="store_true",
@@ -907,7 +907,7 @@ def main():
         if not batched:
             nst = replicas.n_stripes(N)
             cands = ([args.streamed_chunk] if args.streamed_chunk > 0
-                     else sorted({min(nst, 1024), min(nst, 4096)}))
+                     else sorted({min(nst, 2048), min(nst, 4096), min(nst, 8192)}))
             with ub.Context(w.tree, w.table, stream=stream) as sctx:
                 for k_, v_ in tuned_opts.items():
                     sctx.set_option(k_, v_)

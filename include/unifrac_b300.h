@@ -174,12 +174,18 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
  *
  * The first chunk computes the embedding and packs the operands; later chunks
  * reuse them and run only the pair kernels of their stripes.  Each chunk's
- * stripes are computed into a device buffer, copied to pinned host memory on
- * a copy stream while the next chunk computes, and merged into host_out by
- * host threads.  The values are those of unifrac_run.
+ * stripes are computed into a device buffer and rewritten there as the row
+ * runs of the matrix (in row i, the columns i + s and i - s of the chunk's
+ * stripes s), which a copy stream moves while the next chunk computes:
+ * page-locked host_out in the full layout takes them directly (2D copies of
+ * the rows whose runs do not wrap past the last column; host threads place
+ * the few that do); otherwise they go to a pinned buffer and host threads
+ * copy each run into host_out (UNIFRAC_OPT_HOST_THREADS).  The values are
+ * those of unifrac_run.
  * Single-study contexts only (UNIFRAC_E_UNSUPPORTED otherwise).  Synchronous:
- * returns when host_out is complete.  Keeps two device and two pinned host
- * chunk buffers in the context until it is destroyed.
+ * returns when host_out is complete.  Keeps two device chunk buffers, two
+ * device row-run buffers (twice a chunk each) and two pinned host buffers
+ * (twice a chunk each) in the context until it is destroyed.
  */
 int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layout,
                          void *host_out, size_t out_bytes, int32_t chunk_stripes);
@@ -240,7 +246,7 @@ enum unifrac_option {
                                   each tile pair's bitmap words; 0 .. 4096, 0 off, default
                                   256; the sums are the same exact integers */
   UNIFRAC_OPT_UNWEIGHTED_RARE_LIST = 12, /* the same for the unweighted sparse part */
-  UNIFRAC_OPT_COPY_RANGES = 13 /* output in pinned host memory, one study's whole matrix
+  UNIFRAC_OPT_COPY_RANGES = 13, /* output in pinned host memory, one study's whole matrix
                                   (layout FULL or CONDENSED, range (0, -1)): the weighted
                                   variant's dense pair kernel runs as this many launches
                                   over consecutive row blocks of the work list, and the
@@ -249,6 +255,11 @@ enum unifrac_option {
                                   (at most one per block row of 12 tiles);
                                   1 copies the whole matrix after the last kernel.  The
                                   results are the same for every value. */
+  UNIFRAC_OPT_HOST_THREADS = 14 /* host threads of unifrac_run_streamed's stripe merge:
+                                   0 (default) = the CPUs this process may run on
+                                   (its affinity mask and cgroup CPU quota), at
+                                   most 32; 1 .. 256 = that many.  The results are
+                                   the same for every value. */
 };
 int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value);
 int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);

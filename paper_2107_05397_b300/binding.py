@@ -41,6 +41,7 @@ OPT_PERSISTENT = 10
 OPT_RARE_LIST = 11
 OPT_UNWEIGHTED_RARE_LIST = 12
 OPT_COPY_RANGES = 13
+OPT_HOST_THREADS = 14
 
 STAT_KERNEL_LAUNCHES = 0
 STAT_PAIR_BRANCH = 1

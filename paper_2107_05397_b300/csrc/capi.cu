@@ -4,12 +4,16 @@
 // Section II of the paper frames the problem: a table of microbiome profiles
 // that is sparse, a phylogenetic tree over its features, and the all-pairs
 // UniFrac distance matrix, computable in stripes that merge into the whole.
+#include <sched.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <thread>
 #include <climits>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <future>
 #include <memory>
@@ -121,10 +125,38 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 
 // Host threads for the O(entries) preparation: one below ~64k entries, else
 // up to the hardware's count (at most 32).
+// CPUs this process may run on: its affinity mask, lowered to a cgroup CPU
+// quota where one is set (cgroup v2 cpu.max, else v1 cfs_quota_us /
+// cfs_period_us).  More threads than that only queue behind each other.
+static int usable_cpus() {
+  static const int n = [] {
+    int c = 0;
+    cpu_set_t set;
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) c = CPU_COUNT(&set);
+    if (c <= 0) c = (int)std::max(1u, std::thread::hardware_concurrency());
+    long long quota = -1, period = 0;
+    if (FILE *f = std::fopen("/sys/fs/cgroup/cpu.max", "r")) {
+      char q[32] = {0};
+      if (std::fscanf(f, "%31s %lld", q, &period) == 2 && std::strcmp(q, "max") != 0)
+        quota = std::atoll(q);
+      std::fclose(f);
+    } else if (FILE *fq = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_quota_us", "r")) {
+      if (std::fscanf(fq, "%lld", &quota) != 1) quota = -1;
+      std::fclose(fq);
+      if (FILE *fp = std::fopen("/sys/fs/cgroup/cpu/cpu.cfs_period_us", "r")) {
+        if (std::fscanf(fp, "%lld", &period) != 1) period = 0;
+        std::fclose(fp);
+      }
+    }
+    if (quota > 0 && period > 0) c = std::min<long long>(c, std::max(1LL, (quota + period - 1) / period));
+    return c;
+  }();
+  return n;
+}
+
 int host_threads(int64_t work) {
   if (work < (1 << 16)) return 1;
-  const unsigned hw = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(32u, hw ? hw : 1u));
+  return std::max(1, std::min(32, usable_cpus()));
 }
 
 // Runs fn(0) .. fn(T-1) on T threads (fn(0) on the calling thread).
@@ -152,7 +184,7 @@ void free_ctx(unifrac_ctx *ctx) {
     if (p) dev_free(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
                          &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1],
-                         &ctx->item_of};
+                         &ctx->chunk_rows[0], &ctx->chunk_rows[1], &ctx->item_of};
   for (auto *b : bufs)
     if (b->p) dev_free(b->p);
   for (auto &V : ctx->vb) {
@@ -1647,6 +1679,11 @@ int unifrac_set_option(unifrac_ctx *ctx, int option, int64_t value) {
       if (value < 1 || value > 64) return UNIFRAC_E_INVALID_ARG;
       ctx->opt_copy_ranges = (int)value;
       return UNIFRAC_OK;
+    case UNIFRAC_OPT_HOST_THREADS:
+      if (value < 0 || value > 256) return UNIFRAC_E_INVALID_ARG;
+      ctx->opt_host_threads = (int)value;
+      ctx->opt_generation--;  // host-side only: a captured graph stays valid
+      return UNIFRAC_OK;
     default:
       return UNIFRAC_E_INVALID_ARG;
   }
@@ -1669,6 +1706,7 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
       *value = ctx->opt_uw_sparse_threshold;
       return UNIFRAC_OK;
     case UNIFRAC_OPT_COPY_RANGES: *value = ctx->opt_copy_ranges; return UNIFRAC_OK;
+    case UNIFRAC_OPT_HOST_THREADS: *value = ctx->opt_host_threads; return UNIFRAC_OK;
     default: return UNIFRAC_E_INVALID_ARG;
   }
 }
@@ -1688,11 +1726,14 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
     return fail(ctx, UNIFRAC_E_INVALID_ARG, "streamed output is condensed or full");
   if (ctx->n_studies != 1)
     return fail(ctx, UNIFRAC_E_UNSUPPORTED, "streamed output needs a single study");
+  bool pinned = false;  // page-locked host memory: the copy engines can write it
   {  // host threads write the result: it must be host memory
     cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, host_out) == cudaSuccess &&
-        attr.type == cudaMemoryTypeDevice)
-      return fail(ctx, UNIFRAC_E_INVALID_ARG, "streamed output must be host memory");
+    if (cudaPointerGetAttributes(&attr, host_out) == cudaSuccess) {
+      if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)
+        return fail(ctx, UNIFRAC_E_INVALID_ARG, "streamed output must be host memory");
+      pinned = attr.type == cudaMemoryTypeHost;
+    }
     cudaGetLastError();
   }
   const int nv = variant == UNIFRAC_BOTH ? 2 : 1;
@@ -1724,74 +1765,114 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
   }
   int rc;
   for (int b = 0; b < 2; ++b)
-    if ((rc = grow(ctx, ctx->chunk_dev[b], chunk_bytes))) return rc;
-  if (ctx->chunk_host_bytes < chunk_bytes) {
+    if ((rc = grow(ctx, ctx->chunk_dev[b], chunk_bytes)) ||
+        (rc = grow(ctx, ctx->chunk_rows[b], 2 * chunk_bytes)))
+      return rc;
+  if (ctx->chunk_host_bytes < 2 * chunk_bytes) {
     for (int b = 0; b < 2; ++b) {
       if (ctx->chunk_host[b]) cudaFreeHost(ctx->chunk_host[b]);
       ctx->chunk_host[b] = nullptr;
     }
     ctx->chunk_host_bytes = 0;
     for (int b = 0; b < 2; ++b) {
-      e = cudaMallocHost(&ctx->chunk_host[b], chunk_bytes);
+      e = cudaMallocHost(&ctx->chunk_host[b], 2 * chunk_bytes);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pinned host buffer");
     }
-    ctx->chunk_host_bytes = chunk_bytes;
+    ctx->chunk_host_bytes = 2 * chunk_bytes;
   }
-  // Merge stripes [s0, s0 + rows) of chunk buffer b into the output.  Stripe
-  // s holds pair (k, (k + s + 1) mod n) at element k.  For output row rho
-  // (the smaller index) the chunk's pairs are (rho, rho + s + 1) from element
-  // rho (when rho + s + 1 < n) and (rho, rho + n - s - 1) from element
-  // rho + n - s - 1 (the wrapped ones, when rho <= s): for a fixed rho both
-  // are contiguous runs of the output row.  Work goes in 64 x 64 tiles of
-  // (rho, s), so that reads and writes both stay within a few KB.
-  auto merge = [&](int b, int32_t s0, int32_t rows) {
-    constexpr int64_t kTile = 64;
-    const int64_t nrb = (n + kTile - 1) / kTile;
-    const int T = host_threads((int64_t)rows * n);
+  // Place the row runs of the chunk of stripes [s0, s0 + L) held in pinned
+  // buffer b (up runs of every variant, then down runs; see stripe_rows) into
+  // the output.  Row i of the full matrix takes its up run at the cyclic
+  // columns i + s0 + 1 + t and its down run at i - s0 - L + t (mod n); a
+  // condensed row i keeps the columns above i: the up run's up to n - 1, the
+  // down run's that wrapped past n.  Host threads take blocks of rows; every
+  // piece is one contiguous copy.
+  // Full layout into page-locked memory: the copy engines write the runs
+  // straight into host_out.  Consecutive rows' runs start n + 1 elements
+  // apart, so the rows whose runs do not wrap past column n form four
+  // rectangles per variant with that pitch (up runs of rows [0, n - s1) and
+  // [n - s0 - 1, n), down runs of rows [s1, n) and [0, s0 + 1)); the runs of
+  // the L - 1 rows that wrap (up: rows [n - s1, n - s0 - 1), down: rows
+  // [s0 + 1, s1)) go to the pinned buffer and the host places them.
+  const bool direct = pinned && layout == UNIFRAC_OUT_FULL;
+  auto direct_copies = [&](int b, int32_t s0, int32_t L, const char *rows_dev) -> cudaError_t {
+    const int64_t s1 = s0 + L;
+    const size_t run = (size_t)L * elem, dpitch = (size_t)(n + 1) * elem;
+    char *stage = static_cast<char *>(ctx->chunk_host[b]);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+      char *out = static_cast<char *>(host_out) + (size_t)v * per_matrix * elem;
+      const char *U = rows_dev + (size_t)v * n * run;
+      const char *D = rows_dev + (size_t)(nv + v) * n * run;
+      struct Rect { int64_t row0, rows, col0; const char *src; };
+      const Rect rects[4] = {{0, n - s1, s0 + 1, U},
+                             {n - s0 - 1, s0 + 1, s0 + 1 - n, U},
+                             {s1, n - s1, -s1, D},
+                             {0, s0 + 1, n - s1, D}};
+      for (const Rect &r : rects) {
+        if (r.rows <= 0 || e != cudaSuccess) continue;
+        // row i's run starts at element i (n + 1) + col0
+        e = cudaMemcpy2DAsync(out + (size_t)(r.row0 * (n + 1) + r.col0) * elem, dpitch,
+                              r.src + (size_t)r.row0 * run, run, run, (size_t)r.rows,
+                              cudaMemcpyDeviceToHost, ctx->copy_stream);
+      }
+      if (L > 1 && e == cudaSuccess)
+        e = cudaMemcpyAsync(stage + (size_t)(2 * v) * (L - 1) * run, U + (size_t)(n - s1) * run,
+                            (size_t)(L - 1) * run, cudaMemcpyDeviceToHost, ctx->copy_stream);
+      if (L > 1 && e == cudaSuccess)
+        e = cudaMemcpyAsync(stage + (size_t)(2 * v + 1) * (L - 1) * run, D + (size_t)(s0 + 1) * run,
+                            (size_t)(L - 1) * run, cudaMemcpyDeviceToHost, ctx->copy_stream);
+    }
+    return e;
+  };
+  auto place_wrapped = [&](int b, int32_t s0, int32_t L) {
+    if (L <= 1) return;
+    const size_t run = (size_t)L * elem;
+    const char *stage = static_cast<const char *>(ctx->chunk_host[b]);
+    for (int v = 0; v < nv; ++v)
+      for (int side = 0; side < 2; ++side)
+        for (int64_t r = 0; r < L - 1; ++r) {
+          const int64_t i = side == 0 ? n - (s0 + L) + r : s0 + 1 + r;
+          const int64_t c0 = side == 0 ? (i + s0 + 1) % n : ((i - s0 - L) % n + n) % n;
+          const char *src = stage + ((size_t)(2 * v + side) * (L - 1) + (size_t)r) * run;
+          char *row = static_cast<char *>(host_out) + ((size_t)v * per_matrix + (size_t)i * n) * elem;
+          const int64_t first = std::min<int64_t>(L, n - c0);
+          std::memcpy(row + c0 * elem, src, first * elem);
+          if (first < L) std::memcpy(row, src + first * elem, (L - first) * elem);
+        }
+  };
+  auto merge = [&](int b, int32_t s0, int32_t L) {
+    if (direct) return place_wrapped(b, s0, L);
+    const char *up = static_cast<const char *>(ctx->chunk_host[b]);
+    const char *down = up + (size_t)nv * n * L * elem;
+    char *dst = static_cast<char *>(host_out);
+    const int T = ctx->opt_host_threads > 0 ? ctx->opt_host_threads : host_threads((int64_t)L * n);
+    const int64_t rows_per = (n + T - 1) / T;
     run_threads(T, [&](int t) {
+      const int64_t i_lo = std::min<int64_t>(n, (int64_t)t * rows_per);
+      const int64_t i_hi = std::min<int64_t>(n, i_lo + rows_per);
       for (int v = 0; v < nv; ++v)
-        for (int64_t rb = t; rb < nrb; rb += T)
-          for (int32_t sb = 0; sb < rows; sb += (int32_t)kTile) {
-            const int64_t rho1 = std::min(n, (rb + 1) * kTile);
-            const int32_t r1 = std::min(rows, sb + (int32_t)kTile);
-            for (int64_t rho = rb * kTile; rho < rho1; ++rho)
-              for (int32_t r = sb; r < r1; ++r) {
-                const int64_t s = s0 + r, in_row = ((int64_t)v * rows + r) * n;
-                for (int pass = 0; pass < 2; ++pass) {
-                  int64_t k, hi;
-                  if (pass == 0) {  // (rho, rho + s + 1) from element rho
-                    k = rho;
-                    hi = rho + s + 1;
-                    if (hi >= n) continue;
-                  } else {  // wrapped: (rho, rho + n - s - 1) from element rho + n - s - 1
-                    if (rho > s) continue;
-                    k = rho + n - s - 1;
-                    hi = k;
-                  }
-                  const int64_t lo = rho;
-                  if (layout == UNIFRAC_OUT_CONDENSED) {
-                    const int64_t idx = v * per_matrix + lo * n - lo * (lo + 1) / 2 + (hi - lo - 1);
-                    if (elem == 8)
-                      static_cast<double *>(host_out)[idx] =
-                          static_cast<const double *>(ctx->chunk_host[b])[in_row + k];
-                    else
-                      static_cast<float *>(host_out)[idx] =
-                          static_cast<const float *>(ctx->chunk_host[b])[in_row + k];
-                  } else {
-                    const int64_t i1 = v * per_matrix + lo * n + hi, i2 = v * per_matrix + hi * n + lo;
-                    if (elem == 8) {
-                      const double x = static_cast<const double *>(ctx->chunk_host[b])[in_row + k];
-                      static_cast<double *>(host_out)[i1] = x;
-                      static_cast<double *>(host_out)[i2] = x;
-                    } else {
-                      const float x = static_cast<const float *>(ctx->chunk_host[b])[in_row + k];
-                      static_cast<float *>(host_out)[i1] = x;
-                      static_cast<float *>(host_out)[i2] = x;
-                    }
-                  }
-                }
-              }
+        for (int64_t i = i_lo; i < i_hi; ++i) {
+          const char *ur = up + ((size_t)v * n + i) * L * elem;
+          const char *dr = down + ((size_t)v * n + i) * L * elem;
+          if (layout == UNIFRAC_OUT_FULL) {
+            char *row = dst + ((size_t)v * per_matrix + (size_t)i * n) * elem;
+            auto place = [&](int64_t c0, const char *src) {  // cyclic run from column c0
+              const int64_t first = std::min<int64_t>(L, n - c0);
+              std::memcpy(row + c0 * elem, src, first * elem);
+              if (first < L) std::memcpy(row, src + first * elem, (L - first) * elem);
+            };
+            place((i + s0 + 1) % n, ur);
+            place(((i - s0 - L) % n + n) % n, dr);
+          } else {
+            // (i, hi) sits at base + hi in the condensed matrix
+            const int64_t base = (int64_t)v * per_matrix + i * n - i * (i + 1) / 2 - i - 1;
+            const int64_t nu = std::min<int64_t>(L, std::max<int64_t>(0, n - i - s0 - 1));
+            if (nu > 0) std::memcpy(dst + (base + i + s0 + 1) * elem, ur, nu * elem);
+            const int64_t nd = std::min<int64_t>(L, std::max<int64_t>(0, s0 + L - i));
+            if (nd > 0) std::memcpy(dst + (base + i - s0 - L + n) * elem, dr, nd * elem);
           }
+        }
     });
   };
   const int saved_graph = ctx->opt_use_graph;
@@ -1814,11 +1895,16 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
       ctx->reuse_prepared = false;
       if (rc) break;
       if (c == 0) ctx->prep_sig = prep_signature(ctx);
+      char *rows_dev = static_cast<char *>(ctx->chunk_rows[b].p);
+      if ((rc = stripe_rows(ctx, ctx->chunk_dev[b].p, (int32_t)n, s1 - s0, s0, nv, elem == 8,
+                            rows_dev, rows_dev + bytes)))
+        break;
       e = cudaEventRecord(ctx->ev_chunk_done[b], ctx->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_chunk_done[b], 0);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->chunk_host[b], ctx->chunk_dev[b].p, bytes, cudaMemcpyDeviceToHost,
-                            ctx->copy_stream);
+        e = direct ? direct_copies(b, s0, s1 - s0, rows_dev)
+                   : cudaMemcpyAsync(ctx->chunk_host[b], rows_dev, 2 * bytes,
+                                     cudaMemcpyDeviceToHost, ctx->copy_stream);
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_chunk_copied[b], ctx->copy_stream);
       if (e != cudaSuccess) {
         rc = cuda_fail(ctx, e, "chunk copy");

@@ -169,6 +169,7 @@ struct unifrac_ctx {
   // weighted) are summed from per-branch lists instead of the sparse kernel
   int64_t opt_rare_list[2] = {256, 256};
   int opt_copy_ranges = 32;  // launches of the weighted dense kernel into pinned host output
+  int opt_host_threads = 0;  // threads of the streamed merge (0: the CPUs this process may use)
   // sparse kernels (slot 0 unweighted, 1 weighted): incidences of at most
   // this many pairs are walked by one lane
   int opt_lane_pairs[2] = {64, 128};
@@ -237,6 +238,7 @@ struct unifrac_ctx {
 
   // ---- work buffers (grown on demand)
   ufb::DevBuf cnt, flag, items, studies, stage, tables, chunk_dev[2];
+  ufb::DevBuf chunk_rows[2];  // streamed output: each chunk's stripes as row runs
   ufb::DevBuf item_of;  // [n_tiles x n_tiles] work item of each tile pair, -1 if none
   ufb::VarBufs vb[2];
   size_t device_bytes = 0;
@@ -283,6 +285,12 @@ cudaError_t dev_malloc_retry(void **p, size_t bytes);
 // After launch range c of the chunked variant: the rows that range completed
 // are copied to host memory on the copy stream, ordered after the launch.
 int enqueue_range_copy(unifrac_ctx *ctx, int c);
+// Streamed output: the chunk of L stripes [s0, s0 + L) (nv variants, one
+// after the other, n x L elements each) rewritten as the row runs of the
+// matrix, up[v][i][t] = d(i, (i + s0 + 1 + t) mod n) and
+// down[v][i][t] = d(i, (i - s0 - L + t) mod n), on the context's stream.
+int stripe_rows(unifrac_ctx *ctx, const void *chunk, int32_t n, int32_t L, int32_t s0, int nv,
+                bool f64, void *up, void *down);
 // Event record on the context's stream; while a CUDA graph is being captured
 // the record becomes a graph node (external event record), so replays
 // record the event too and it can be queried afterwards.

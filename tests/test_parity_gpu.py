@@ -846,6 +846,55 @@ def test_streamed_output_equals_direct(small, n, precision):
         assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
 
 
+@pytest.mark.parametrize("n", [256, 255])
+def test_streamed_pinned_output_equals_pageable(small, n):
+    """Into page-locked memory the full layout goes by 2D copies straight
+    into the output (the rows whose runs wrap past column n through the host):
+    the same bytes as into pageable memory, which the host places from row
+    runs; both precisions, odd and even N, chunks of 1, 7 and all stripes
+    (a ragged last chunk), and the condensed layout alongside."""
+    import torch
+    w, ref_small = small
+    table = synth.dense_to_table(w.table.dense()[:, :n], w.table.feature_node) \
+        if n != w.table.n_samples else w.table
+    with ub.Context(w.tree, table) as ctx:
+        for precision in PRECISIONS:
+            dt = torch.float64 if precision == ub.FP64 else torch.float32
+            for layout in (ub.OUT_FULL, ub.OUT_CONDENSED):
+                nb = ctx.output_bytes(precision, layout) * 2
+                for chunk in (1, 7, 10_000):
+                    pageable = ctx.run_streamed(ub.BOTH, precision, layout, chunk)
+                    pinned = torch.full((nb // dt.itemsize,), float("nan"), dtype=dt).pin_memory()
+                    got = ctx.run_streamed(ub.BOTH, precision, layout, chunk, out=pinned.numpy())
+                    np.testing.assert_array_equal(got, pageable)
+        assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
+
+
+def test_streamed_merge_threads_change_nothing(small):
+    """UNIFRAC_OPT_HOST_THREADS sets the stripe merge's host threads (0: the
+    CPUs the process may use): 1, 3 and 0 threads give the same bytes, full
+    and condensed, odd N with a ragged last chunk; values outside 0 .. 256
+    are rejected and leave the option as it was."""
+    w, _ = small
+    n = 255
+    table = synth.dense_to_table(w.table.dense()[:, :n], w.table.feature_node)
+    with ub.Context(w.tree, table) as ctx:
+        assert ctx.get_option(ub.OPT_HOST_THREADS) == 0
+        for bad in (-1, 257):
+            with pytest.raises(ub.UniFracError):
+                ctx.set_option(ub.OPT_HOST_THREADS, bad)
+        assert ctx.get_option(ub.OPT_HOST_THREADS) == 0
+        for layout in (ub.OUT_FULL, ub.OUT_CONDENSED):
+            got = {}
+            for threads in (1, 3, 0):
+                ctx.set_option(ub.OPT_HOST_THREADS, threads)
+                assert ctx.get_option(ub.OPT_HOST_THREADS) == threads
+                got[threads] = ctx.run_streamed(ub.BOTH, ub.MIXED, layout, 9)
+            np.testing.assert_array_equal(got[1], got[3])
+            np.testing.assert_array_equal(got[1], got[0])
+        assert ctx.stat(ub.STAT_DEVICE_ERROR) == 0
+
+
 def test_streamed_output_rejects_bad_calls(small):
     import torch
     w, _ = small
