@@ -1711,6 +1711,16 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value) {
   }
 }
 
+extern "C++" namespace ufb {
+// The chunk of L stripes [s0, s0 + L) (nv variants, one after the other, L x n
+// elements each) rewritten as the row runs of the matrix,
+// up[v][i][t] = d(i, (i + s0 + 1 + t) mod n) and
+// down[v][i][t] = d(i, (i - s0 - L + t) mod n), on the context's stream
+// (stripe_rows.cu).
+int stripe_rows(unifrac_ctx *ctx, const void *chunk, int32_t n, int32_t L, int32_t s0, int nv,
+                bool f64, void *up, void *down);
+}  // namespace ufb
+
 // Streamed output: stripes [s0, s1) per chunk into one of two device buffers
 // (the kernels of the next chunk overlap the copy of this one on a copy
 // stream), copied to pinned host memory and merged into the caller's

@@ -285,12 +285,6 @@ cudaError_t dev_malloc_retry(void **p, size_t bytes);
 // After launch range c of the chunked variant: the rows that range completed
 // are copied to host memory on the copy stream, ordered after the launch.
 int enqueue_range_copy(unifrac_ctx *ctx, int c);
-// Streamed output: the chunk of L stripes [s0, s0 + L) (nv variants, one
-// after the other, n x L elements each) rewritten as the row runs of the
-// matrix, up[v][i][t] = d(i, (i + s0 + 1 + t) mod n) and
-// down[v][i][t] = d(i, (i - s0 - L + t) mod n), on the context's stream.
-int stripe_rows(unifrac_ctx *ctx, const void *chunk, int32_t n, int32_t L, int32_t s0, int nv,
-                bool f64, void *up, void *down);
 // Event record on the context's stream; while a CUDA graph is being captured
 // the record becomes a graph node (external event record), so replays
 // record the event too and it can be queried afterwards.
