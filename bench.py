@@ -911,7 +911,8 @@ def main():
             with ub.Context(w.tree, w.table, stream=stream) as sctx:
                 for k_, v_ in tuned_opts.items():
                     sctx.set_option(k_, v_)
-                sctx.run_streamed(ub.BOTH, ub.MIXED, layout, cands[0], out=res)  # warm-up
+                # warm-up with the widest chunk: its buffers serve every candidate
+                sctx.run_streamed(ub.BOTH, ub.MIXED, layout, cands[-1], out=res)
                 trial = {}
                 for c_ in cands:
                     t0 = time.perf_counter()

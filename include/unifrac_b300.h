@@ -185,7 +185,9 @@ int unifrac_run(unifrac_ctx *ctx, int variant, int precision,
  * Single-study contexts only (UNIFRAC_E_UNSUPPORTED otherwise).  Synchronous:
  * returns when host_out is complete.  Keeps two device chunk buffers, two
  * device row-run buffers (twice a chunk each) and two pinned host buffers
- * (twice a chunk each) in the context until it is destroyed.
+ * (twice a chunk each; for page-locked full output only the wrapping runs,
+ * 2 (L - 1) L elements per variant for chunks of L stripes) in the context
+ * until it is destroyed.
  */
 int unifrac_run_streamed(unifrac_ctx *ctx, int variant, int precision, int layout,
                          void *host_out, size_t out_bytes, int32_t chunk_stripes);

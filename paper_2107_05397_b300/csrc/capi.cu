@@ -1778,17 +1778,22 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
     if ((rc = grow(ctx, ctx->chunk_dev[b], chunk_bytes)) ||
         (rc = grow(ctx, ctx->chunk_rows[b], 2 * chunk_bytes)))
       return rc;
-  if (ctx->chunk_host_bytes < 2 * chunk_bytes) {
+  // pinned buffers: the whole row runs of a chunk, or (page-locked full
+  // output, written by the copy engines) only the runs that wrap
+  const bool direct = pinned && layout == UNIFRAC_OUT_FULL;
+  const size_t host_bytes =
+      direct ? std::max<size_t>(16, (size_t)nv * 2 * (chunk - 1) * chunk * elem) : 2 * chunk_bytes;
+  if (ctx->chunk_host_bytes < host_bytes) {
     for (int b = 0; b < 2; ++b) {
       if (ctx->chunk_host[b]) cudaFreeHost(ctx->chunk_host[b]);
       ctx->chunk_host[b] = nullptr;
     }
     ctx->chunk_host_bytes = 0;
     for (int b = 0; b < 2; ++b) {
-      e = cudaMallocHost(&ctx->chunk_host[b], 2 * chunk_bytes);
+      e = cudaMallocHost(&ctx->chunk_host[b], host_bytes);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pinned host buffer");
     }
-    ctx->chunk_host_bytes = 2 * chunk_bytes;
+    ctx->chunk_host_bytes = host_bytes;
   }
   // Place the row runs of the chunk of stripes [s0, s0 + L) held in pinned
   // buffer b (up runs of every variant, then down runs; see stripe_rows) into
@@ -1804,7 +1809,6 @@ static int run_streamed_impl(unifrac_ctx *ctx, int variant, int precision, int l
   // [n - s0 - 1, n), down runs of rows [s1, n) and [0, s0 + 1)); the runs of
   // the L - 1 rows that wrap (up: rows [n - s1, n - s0 - 1), down: rows
   // [s0 + 1, s1)) go to the pinned buffer and the host places them.
-  const bool direct = pinned && layout == UNIFRAC_OUT_FULL;
   auto direct_copies = [&](int b, int32_t s0, int32_t L, const char *rows_dev) -> cudaError_t {
     const int64_t s1 = s0 + L;
     const size_t run = (size_t)L * elem, dpitch = (size_t)(n + 1) * elem;
