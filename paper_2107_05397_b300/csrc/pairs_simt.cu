@@ -395,9 +395,10 @@ template <bool PRES>
 struct SparseCfg {
   using Acc = typename std::conditional<PRES, unsigned long long, uint32_t>::type;
   static constexpr size_t kAccBytes = ((size_t)TILE * kAccLd * 4 * (PRES ? 2 : 1) + 15) / 16 * 16;
-  // the swept side of one incidence per warp: TILE entries of 8 (weighted) or
-  // 1 (unweighted) bytes
-  static constexpr size_t kScratch = (size_t)TILE * (PRES ? 1 : 8);
+  // the swept side of one incidence per warp: TILE entries of 1 byte
+  // (unweighted), or of 8 bytes (weighted) at interleaved positions, the
+  // largest 150 (k_pairs_sparse: two entries per 16-byte load)
+  static constexpr size_t kScratch = PRES ? (size_t)TILE : (size_t)152 * 8;
   static constexpr size_t kSmem = kAccBytes + (size_t)kSpWarps * kScratch;
 };
 
@@ -421,6 +422,8 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   // lane side of n rows keeps busy (n > 32: n / passes) -- no divisions later
   __shared__ uint16_t divtab[32][32];
   __shared__ uint8_t gtab[32];
+  // gmul[G-1] = ceil(2^16 / G): a / G = (a gmul) >> 16 exactly for a < 128
+  __shared__ uint32_t gmul[32];
   __shared__ uint8_t fillv[TILE];
 
   __shared__ int32_t s_unit;
@@ -432,7 +435,10 @@ __global__ void __launch_bounds__(kSpThreads, 1)
   {
     const int n = tid / 32 + 1, p = tid % 32;  // kSpThreads == 32 * 32
     divtab[n - 1][p] = (uint16_t)(((p / n) << 8) | (p % n));
-    if (tid < 32) gtab[tid] = (uint8_t)(32 / (tid + 1));
+    if (tid < 32) {
+      gtab[tid] = (uint8_t)(32 / (tid + 1));
+      gmul[tid] = (65536u + (uint32_t)tid) / (uint32_t)(tid + 1);  // ceil(2^16 / G)
+    }
     if (tid < TILE) {
       const int m = tid + 1;
       fillv[tid] = (uint8_t)(m <= 32 ? (32 / m) * m : m / ((m + 31) / 32));
@@ -598,17 +604,24 @@ __global__ void __launch_bounds__(kSpThreads, 1)
         auto prep = [mT](unsigned long long e) {
           return make_uint2((uint32_t)(e & 0xffu) * (uint32_t)mT, (uint32_t)(e >> 32));
         };
+        // entry a goes to position 2 ((k / 2) G + a - k G) + k % 2, k = a / G:
+        // sweep group g's entries g + 2 m G and g + (2 m + 1) G side by side
+        const uint32_t gm = gmul[G - 1];
+        auto pos = [G, gm](int a) {
+          const int k = (int)(((uint32_t)a * gm) >> 16);
+          return 2 * ((k >> 1) * G + a - k * G) + (k & 1);
+        };
         if (nT <= 32) {
-          if (lane < nT) eS2[lane] = prep(__ldg(qT + lane));
+          if (lane < nT) eS2[pos(lane)] = prep(__ldg(qT + lane));
         } else {
           unsigned long long t0 = __ldg(qT + lane), t1 = 0, t2 = 0, t3 = 0;
           if (lane + 32 < nT) t1 = __ldg(qT + lane + 32);
           if (lane + 64 < nT) t2 = __ldg(qT + lane + 64);
           if (lane + 96 < nT) t3 = __ldg(qT + lane + 96);
-          eS2[lane] = prep(t0);
-          if (lane + 32 < nT) eS2[lane + 32] = prep(t1);
-          if (lane + 64 < nT) eS2[lane + 64] = prep(t2);
-          if (lane + 96 < nT) eS2[lane + 96] = prep(t3);
+          eS2[pos(lane)] = prep(t0);
+          if (lane + 32 < nT) eS2[pos(lane + 32)] = prep(t1);
+          if (lane + 64 < nT) eS2[pos(lane + 64)] = prep(t2);
+          if (lane + 96 < nT) eS2[pos(lane + 96)] = prep(t3);
         }
       }
       __syncwarp();
@@ -626,11 +639,15 @@ __global__ void __launch_bounds__(kSpThreads, 1)
             const unsigned long long eb = b < 32 ? eb0 : __ldg((laneJ ? eJ : eI) + bsL + b);
             uint32_t *row = sacc + (uint32_t)(eb & 0xffu) * (uint32_t)mL;
             const uint32_t vb = (uint32_t)(eb >> 32);
-            const uint2 *eS2 = reinterpret_cast<const uint2 *>(eS);
-#pragma unroll 4
-            for (int a = g; a < nT; a += G) {
-              const uint2 e = eS2[a];
+            // entries a and a + G of this group in one 16-byte shared load
+            // (the shared-memory pipe is the bound): pair q = m G + g holds
+            // entries 2 m G + g and (2 m + 1) G + g
+            const uint4 *eS4 = reinterpret_cast<const uint4 *>(eS);
+#pragma unroll 1
+            for (int a = g, q = g; a < nT; a += 2 * G, q += G) {
+              const uint4 e = eS4[q];
               atomicAdd(row + e.x, min(vb, e.y));
+              if (a + G < nT) atomicAdd(row + e.z, min(vb, e.w));
             }
           }
         }
