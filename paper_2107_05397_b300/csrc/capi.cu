@@ -184,7 +184,8 @@ void free_ctx(unifrac_ctx *ctx) {
     if (p) dev_free(p);
   ufb::DevBuf *bufs[] = {&ctx->cnt,   &ctx->flag,   &ctx->items,        &ctx->studies,
                          &ctx->stage, &ctx->tables, &ctx->chunk_dev[0], &ctx->chunk_dev[1],
-                         &ctx->chunk_rows[0], &ctx->chunk_rows[1], &ctx->item_of};
+                         &ctx->chunk_rows[0], &ctx->chunk_rows[1], &ctx->item_of,
+                         &ctx->jrange};
   for (auto *b : bufs)
     if (b->p) dev_free(b->p);
   for (auto &V : ctx->vb) {
@@ -898,6 +899,24 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   for (size_t x = 0; x < items.size(); ++x)
     item_of[(size_t)items[x].tile_i * ctx->n_tiles + items[x].tile_j] = (int32_t)x;
   if ((rc = grow(ctx, ctx->item_of, std::max<size_t>(item_of.size(), 1) * sizeof(int32_t)))) return rc;
+  // per row tile, the runs of column tiles with a work item: at most two
+  // (a stripe range gives a band and its wrapped part), else the whole row
+  std::vector<int4> jrange((size_t)ctx->n_tiles, make_int4(0, 0, 0, 0));
+  for (int32_t r = 0; r < ctx->n_tiles; ++r) {
+    const int32_t *row = item_of.data() + (size_t)r * ctx->n_tiles;
+    int32_t runs[4] = {0, 0, 0, 0}, n_runs = 0;
+    for (int32_t c = 0; c < ctx->n_tiles;) {
+      if (row[c] < 0) { ++c; continue; }
+      int32_t d = c;
+      while (d < ctx->n_tiles && row[d] >= 0) ++d;
+      if (n_runs < 2) { runs[2 * n_runs] = c; runs[2 * n_runs + 1] = d; }
+      ++n_runs;
+      c = d;
+    }
+    jrange[(size_t)r] = n_runs <= 2 ? make_int4(runs[0], runs[1], runs[2], runs[3])
+                                    : make_int4(0, ctx->n_tiles, 0, 0);
+  }
+  if ((rc = grow(ctx, ctx->jrange, std::max<size_t>(jrange.size(), 1) * sizeof(int4)))) return rc;
   cudaError_t e;
   if (!items.empty()) {
     e = cudaMemcpyAsync(ctx->items.p, items.data(), items.size() * sizeof(WorkItem),
@@ -910,6 +929,9 @@ static int plan_items(unifrac_ctx *ctx, int layout, int32_t s0, int32_t s1) {
   if (!item_of.empty()) {
     e = cudaMemcpyAsync(ctx->item_of.p, item_of.data(), item_of.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->jrange.p, jrange.data(), jrange.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "upload item table");
   }
   // pageable sources: the copies above are staged before returning

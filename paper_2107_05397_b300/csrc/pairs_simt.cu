@@ -824,6 +824,28 @@ __global__ void __launch_bounds__(kListWarps * 32)
   }
 }
 
+// First index in [lo, hi] of a branch's (column-sorted) list entries whose
+// column is >= target, by the whole warp: each round the 32 lanes probe
+// evenly spaced entries and the ballot of "below" (a prefix, the entries
+// being sorted) narrows the range to one gap, so a list of up to 1,024
+// entries takes two rounds.  Warp-uniform arguments.
+__device__ __forceinline__ uint32_t list_lower(const unsigned long long *__restrict__ ents,
+                                               uint32_t lo, uint32_t hi, uint32_t target,
+                                               int lane) {
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t idx = lo + (uint32_t)lane * step;
+    const bool below = idx < hi && (uint32_t)__ldg(ents + idx) < target;
+    const uint32_t c = (uint32_t)__popc(__ballot_sync(0xffffffffu, below));
+    if (c == 0u) return lo;
+    const uint32_t nhi = min(hi, lo + c * step);
+    lo = lo + (c - 1u) * step + 1u;
+    hi = nhi;
+  }
+  const bool below = lo + (uint32_t)lane < hi && (uint32_t)__ldg(ents + lo + lane) < target;
+  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, below));
+}
+
 // Persistent: each warp takes kListGrab records at a time from the queue, in
 // record (column tile) order, and walks each record's later entries with its
 // lanes.
@@ -832,6 +854,7 @@ __global__ void __launch_bounds__(kListWarps * 32)
     k_pairs_list(const unsigned long long *__restrict__ toff, int32_t n_tiles,
                  const uint2 *__restrict__ trec, const unsigned long long *__restrict__ ents,
                  unsigned long long n_ent, const int32_t *__restrict__ item_of,
+                 const int4 *__restrict__ jrange,
                  typename SparseCfg<PRES>::Acc *__restrict__ spart, unsigned int *__restrict__ queue,
                  unsigned long long *__restrict__ n_updates) {
   const int lane = threadIdx.x & 31;
@@ -855,18 +878,31 @@ __global__ void __launch_bounds__(kListWarps * 32)
       if (cp >= cols) continue;  // defensive: a column must exist
       const int64_t row = (int64_t)(cp / TILE) * n_tiles;
       const uint32_t a = (cp % TILE) * TILE;
-      for (uint32_t q = g + 1 + lane; q < end; q += 32) {
-        const unsigned long long eq = __ldg(ents + q);
-        const uint32_t cq = (uint32_t)eq;
-        if (cq >= cols) continue;
-        const int32_t item = item_of[row + cq / TILE];
-        if (item < 0) continue;
-        const int64_t at = (int64_t)item * TILE * TILE + a + cq % TILE;
-        if constexpr (PRES)
-          atomicAdd(&spart[at], (unsigned long long)vp);
-        else
-          atomicAdd(&spart[at], min(vp, (uint32_t)(eq >> 32)));
-        ++done;
+      // the run computes, in this row of tiles, the column tiles [x, y) and
+      // [z, w) (from the work list; [0, n_tiles) when it has more runs): the
+      // later entries of the branch in those columns, found by search
+      const int4 jr = __ldg(jrange + cp / TILE);
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const uint32_t c0 = (uint32_t)(part == 0 ? jr.x : jr.z) * TILE;
+        const uint32_t c1 = (uint32_t)(part == 0 ? jr.y : jr.w) * TILE;
+        if (c1 <= c0 || c1 <= cp + 1) continue;
+        // a whole-row run (the whole matrix) needs no search
+        const uint32_t q0 = c0 <= cp + 1 ? g + 1 : list_lower(ents, g + 1, end, c0, lane);
+        const uint32_t q1 = c1 >= cols ? end : list_lower(ents, q0, end, c1, lane);
+        for (uint32_t q = q0 + lane; q < q1; q += 32) {
+          const unsigned long long eq = __ldg(ents + q);
+          const uint32_t cq = (uint32_t)eq;
+          if (cq >= cols) continue;
+          const int32_t item = item_of[row + cq / TILE];
+          if (item < 0) continue;
+          const int64_t at = (int64_t)item * TILE * TILE + a + cq % TILE;
+          if constexpr (PRES)
+            atomicAdd(&spart[at], (unsigned long long)vp);
+          else
+            atomicAdd(&spart[at], min(vp, (uint32_t)(eq >> 32)));
+          ++done;
+        }
       }
     }
   }
@@ -1187,6 +1223,7 @@ int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *sp
   const int64_t n = (int64_t)ctx->K - pv;
   if (n <= 0 || ctx->n_tiles <= 0) return UNIFRAC_OK;
   const int32_t *item_of = static_cast<const int32_t *>(ctx->item_of.p);
+  const int4 *jrange = static_cast<const int4 *>(ctx->jrange.p);
   // the list queue: the slot's third 32-bit queue counter (cleared with the others)
   unsigned int *queue = reinterpret_cast<unsigned int *>(ctx->d_counter + 4 * ctx->cur_slot + 2);
   // kListBlocksPerSm CTAs per SM: the records in flight (kListGrab per warp)
@@ -1194,12 +1231,12 @@ int pairs_list(unifrac_ctx *ctx, bool presence, int32_t pv, ListBufs L, void *sp
   const unsigned grid = (unsigned)(kListBlocksPerSm * ctx->sm_count);
   if (presence)
     k_pairs_list<true><<<grid, kListWarps * 32, 0, ctx->stream>>>(
-        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of,
+        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of, jrange,
         static_cast<unsigned long long *>(spart), queue, cur_counters(ctx) + 3);
   else
     k_pairs_list<false><<<grid, kListWarps * 32, 0, ctx->stream>>>(
-        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of, static_cast<uint32_t *>(spart),
-        queue, cur_counters(ctx) + 3);
+        L.toff, ctx->n_tiles, L.trec, L.ents, L.n_ent, item_of, jrange,
+        static_cast<uint32_t *>(spart), queue, cur_counters(ctx) + 3);
   ctx->stat_launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rare branch pairs");

@@ -240,6 +240,9 @@ struct unifrac_ctx {
   ufb::DevBuf cnt, flag, items, studies, stage, tables, chunk_dev[2];
   ufb::DevBuf chunk_rows[2];  // streamed output: each chunk's stripes as row runs
   ufb::DevBuf item_of;  // [n_tiles x n_tiles] work item of each tile pair, -1 if none
+  // [n_tiles] int4 per row tile: the column tiles [x, y) and [z, w) that hold
+  // its work items (disjoint runs of item_of's row; [0, n_tiles) if more)
+  ufb::DevBuf jrange;
   ufb::VarBufs vb[2];
   size_t device_bytes = 0;
 };
