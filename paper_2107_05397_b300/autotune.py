@@ -14,7 +14,6 @@ stored as they are.
 """
 from __future__ import annotations
 
-import ctypes
 import json
 import math
 import os
@@ -76,14 +75,7 @@ def tune(ctx: "ub.Context", variant: int, precision: int,
         return dict(rec, cached=True)
     nbytes = ctx.output_bytes(precision, ub.OUT_CONDENSED)
     out = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device="cuda")
-    lib = ub.load()
-    lib.unifrac_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
-    lib.unifrac_autotune.restype = ctypes.c_int
-    rc = lib.unifrac_autotune(ctx.handle, variant, precision, ctypes.c_void_p(out.data_ptr()),
-                              out.numel() * 4, repeats)
-    if rc:
-        raise ub.UniFracError(rc, ub.unifrac_strerror(rc) + ": " + ub.unifrac_last_error(ctx.handle))
+    ub.unifrac_autotune(ctx.handle, variant, precision, out, repeats)
     rec = {}
     if variant == ub.WEIGHTED_NORMALIZED and precision == ub.MIXED:
         rec["sparse_fraction"] = ub.unifrac_get_option(ctx.handle, ub.OPT_SPARSE_THRESHOLD) / max(n, 1)

@@ -145,6 +145,11 @@ def load() -> ctypes.CDLL:
         lib.unifrac_release_cached_memory.restype = ctypes.c_int
         lib.unifrac_cached_memory.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         lib.unifrac_cached_memory.restype = ctypes.c_int
+        lib.unifrac_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                                         ctypes.c_int]
+        lib.unifrac_autotune.restype = ctypes.c_int
+        lib.unifrac_dense_noalloc.argtypes = [ctypes.c_int, i32, vp, vp, i32, vp, vp, vp]
+        lib.unifrac_dense_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -360,6 +365,16 @@ def unifrac_get_option(ctx, option: int) -> int:
     v = ctypes.c_int64()
     _check(load().unifrac_get_option(ctx, option, ctypes.byref(v)), ctx)
     return int(v.value)
+
+
+def unifrac_autotune(ctx, variant: int, precision: int, out, repeats: int = 2) -> None:
+    """Times the kernel settings of one (variant, precision) on the device
+    and keeps the fastest as the context's options; `out` is a device buffer
+    of at least unifrac_output_bytes(ctx, precision, OUT_CONDENSED) bytes,
+    overwritten."""
+    ptr, nbytes = _data_ptr(out)
+    _check(load().unifrac_autotune(ctx, int(variant), int(precision), ctypes.c_void_p(ptr),
+                                   nbytes, int(repeats)), ctx)
 
 
 def unifrac_get_stat(ctx, stat: int) -> float:

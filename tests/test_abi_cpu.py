@@ -30,6 +30,22 @@ def test_library_exports_every_declared_symbol():
     assert set(ub.EXPORTED) <= set(names)
 
 
+def test_binding_declares_every_entry_point():
+    """binding.load() gives every declared function its ctypes signature, so
+    no other module has to (or may) set one on the shared library handle."""
+    lib = ub.load()
+    for name in declared_functions():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+
+
+def test_autotune_rejects_null_context_or_buffer():
+    lib = ub.load()
+    buf = ctypes.create_string_buffer(16)
+    assert lib.unifrac_autotune(None, ub.UNWEIGHTED, ub.MIXED, buf, 16, 2) == -1
+    assert lib.unifrac_autotune(None, ub.UNWEIGHTED, ub.MIXED, None, 16, 2) == -1
+
+
 def test_strerror_covers_codes():
     for code in range(0, -10, -1):
         s = ub.unifrac_strerror(code)
