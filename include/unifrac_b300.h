@@ -277,8 +277,8 @@ int unifrac_get_option(const unifrac_ctx *ctx, int option, int64_t *value);
  * (UNIFRAC_OPT_SPARSE_LANE_PAIRS / UNIFRAC_OPT_UNWEIGHTED_SPARSE_LANE_PAIRS
  * 32, 64, 128, 256, when the split has a sparse part), the per-branch list
  * bound (UNIFRAC_OPT_RARE_LIST / UNIFRAC_OPT_UNWEIGHTED_RARE_LIST 0, 64, 256,
- * 1024, likewise; both then 3/4 and 3/2 of the best) and, weighted, the register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH
- * 128, 256, 512).  Each candidate runs `repeats` times (>= 1, after one
+ * 1024, likewise; both then 3/4 and 3/2 of the best) and, weighted, the
+ * register flush length (UNIFRAC_OPT_WEIGHTED_FLUSH 128, 256, 512).  Each candidate runs `repeats` times (>= 1, after one
  * warm-up run) into `out`, a DEVICE buffer of at least
  * unifrac_output_bytes(ctx, precision, UNIFRAC_OUT_CONDENSED, 0, -1) bytes
  * whose contents are overwritten; the time compared is embedding + packing +

@@ -1265,7 +1265,8 @@ static int enqueue_early_copy(unifrac_ctx *ctx) {
 
 // The embedding once, then each variant's packing and pair kernels.
 // With two plans and UNIFRAC_OPT_OVERLAP_VARIANTS, the first plan runs on a
-// second stream forked after the embedding and joined at the end, the second on the context's stream (both are captured into the same
+// second stream forked after the embedding and joined at the end, the
+// second on the context's stream (both are captured into the same
 // graph); the variants have separate buffers and counters, and share only the
 // read-only embedding and the output buffer, which they write in disjoint
 // halves.

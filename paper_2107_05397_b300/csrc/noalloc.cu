@@ -14,7 +14,8 @@
 // device address is looked up with the device current on every call made
 // outside stream capture; a call enqueued on a capturing stream uses the
 // address found by the last earlier call on that device (and is refused if
-// there was none), so make one call on each device before any stream capture.  All calls share the array: calls that overlap on the GPU
+// there was none), so make one call on each device before any stream
+// capture.  All calls share the array: calls that overlap on the GPU
 // (different streams, or the same stream from several host threads without
 // ordering) race and corrupt each other's results.  Nothing needs clearing
 // between calls: the first kernel overwrites every cell it later reads.
