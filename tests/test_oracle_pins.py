@@ -3,8 +3,9 @@
 Each test checks the oracle against something fixed by the paper's problem
 statement (Section II) or by mathematics: a hand-derived worked example,
 brute-force ancestor walks, star-tree closed forms that reduce to textbook
-distances computed by scipy (Jaccard, Bray-Curtis), Faith's phylogenetic
-diversity, the tip-depth identity of the weighted denominator, and metric
+distances computed by scipy (Jaccard, Bray-Curtis), the earth mover's
+distance of the weighted numerator (a transport linear program), Faith's
+phylogenetic diversity, the tip-depth identity of the weighted denominator, and metric
 invariants.  A dropped term, wrong sign, wrong index or swapped operand in the
 oracle fails at least one of them.
 """
@@ -205,6 +206,64 @@ def test_weighted_denominator_tip_depth_identity(k):
         tot = dense[:, i].sum()
         rhs = float(np.dot(dense[:, i] / tot, dep[table.feature_node])) if tot else 0.0
         assert abs(lhs - rhs) < 1e-13
+
+
+def tip_path_lengths(tree, tips):
+    """Tree path length between every two tips: depth(a) + depth(b) minus
+    twice the depth of their deepest common ancestor (from ancestor sets)."""
+    dep = depth(tree)
+    anc = []
+    for t in tips:
+        s, v = set(), int(t)
+        while v >= 0:
+            s.add(v)
+            v = int(tree.parent[v])
+        anc.append(s)
+    n = len(tips)
+    C = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            lca_depth = max(dep[v] for v in anc[a] & anc[b])
+            C[a, b] = dep[tips[a]] + dep[tips[b]] - 2.0 * lca_depth
+    return C
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_weighted_numerator_is_earth_movers_distance(k):
+    """Weighted UniFrac's numerator sum_b len_b |w_bi - w_bj| is the earth
+    mover's (Kantorovich) distance between the two samples' relative
+    abundances on the tips, with the tree's path lengths as ground distance.
+    The transport problem is solved as a linear program (scipy's HiGHS), and
+    the denominator is the sum of the two mean tip depths, so
+    d_ij * (D_i + D_j) must equal the transport cost."""
+    from scipy.optimize import linprog
+    tree, table = cases()[k]
+    d = oracle.unifrac_full(tree, table, WN)
+    dense = table.dense().astype(float)
+    tips = table.feature_node.astype(np.int64)
+    C = tip_path_lengths(tree, tips)
+    dep = depth(tree)[tips]
+    F = len(tips)
+    # equality constraints of a transport plan T[f, g] >= 0 (row-major):
+    # rows sum to p, columns sum to q
+    A = np.zeros((2 * F, F * F))
+    for f in range(F):
+        A[f, f * F:(f + 1) * F] = 1.0
+        A[F + f, f::F] = 1.0
+    checked = 0
+    for i in range(table.n_samples):
+        for j in range(i + 1, table.n_samples):
+            ti, tj = dense[:, i].sum(), dense[:, j].sum()
+            if ti == 0 or tj == 0:
+                continue
+            p, q = dense[:, i] / ti, dense[:, j] / tj
+            res = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([p, q]), bounds=(0, None),
+                          method="highs")
+            assert res.status == 0
+            numer = d[i, j] * (float(p @ dep) + float(q @ dep))
+            assert abs(numer - res.fun) < 1e-8, (i, j, numer, res.fun)
+            checked += 1
+    assert checked >= 10
 
 
 def test_faith_pd_golden():
