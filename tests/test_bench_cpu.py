@@ -1,5 +1,6 @@
 """Host logic of bench.py (no GPU): the DRAM-traffic records behind
-roofline.traffic and the split thresholds they are keyed to."""
+roofline.traffic, the split thresholds they are keyed to, and the JSON line
+of the reference arm (the oracle timed on the host)."""
 import json
 import os
 import sys
@@ -114,3 +115,43 @@ def test_traffic_hash_ignores_comments_only():
     assert bench.code_only(base) == bench.code_only(same)
     assert bench.code_only(base) != bench.code_only(base.replace("a = 1", "a = 2"))
     assert '"x//y"' in bench.code_only(base)
+
+
+def _reference_line(env_extra=None):
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    root = os.path.join(os.path.dirname(__file__), "..")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", "tips1024_samples256", "--steps", "3", "--warmup", "1"],
+                       capture_output=True, text=True, env=env, timeout=300, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [ln for ln in r.stdout.splitlines() if ln.strip()]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """--impl reference times the oracle on the host and prints one JSON line
+    with the arm's keys: impl, metric, value, unit, steps, a cpu_baseline
+    describing the run and an e2e with no host-device bytes."""
+    lines = _reference_line()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["steps"] == 3 and line["warmup"] == 1 and line["value"] > 0
+    assert line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "tips1024_samples256"
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    """Under torchrun only rank 0 runs the oracle; the other ranks exit 0
+    without work or output."""
+    assert _reference_line({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
